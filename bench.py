@@ -1,0 +1,434 @@
+#!/usr/bin/env python3
+"""ProHD benchmark on GB300.
+
+Workload: a pair of n = m = 2,000,000 point sets in D = 256 (A ~ N(0, S),
+S = Q diag(1/i) Q^T; B the same law shifted by 0.1 sigma along a random unit
+vector, 0.1% multivariate Student-t (nu = 3) points), synthetic and seeded.
+A step is one full ProHD estimate (Algorithm 3) of that pair, resident in HBM:
+directions (centroid axis + top-8 principal components), selection
+(alpha = 0.01 per side on the centroid axis, alpha/8 per component),
+gather, and the exact Hausdorff distance of the subsets on FP16 tensor-core
+tiles with FP32 rescoring and an FP64 witness.
+
+Reported beside the throughput: relative error of the estimate against the
+exact Hausdorff distance of the full sets (same library, FP32-rescored, FP64
+witness), the speedup over that exact computation, the BF16-tile variant,
+an end-to-end number through prohd_estimate_host (host buffers, copies in the
+timed region), the roofline of the dominant kernel, and the FP64 CPU oracle
+timed on a bounded sample on the host cores.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl prohd|reference]
+"""
+from __future__ import annotations
+
+import argparse
+import ctypes
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "ProHD set-pairs/s at 2M×D256 + rel. err vs FP64 exact; speedup over GPU exact HD"
+UNIT = "set-pairs/s"
+N_POINTS = 2_000_000
+DIM = 256
+M_PCS = 8
+ALPHA = 0.01
+WORKLOAD = ("anisotropic Gaussian pair, n=m=2,000,000, D=256 (eigenvalues 1/i, random rotation); "
+            "B shifted 0.1 sigma along a random unit vector with 0.1% Student-t (nu=3) points; "
+            "ProHD with centroid axis + top-8 PCs, alpha=0.01 per side (alpha/8 per PC), FP16 tiles")
+
+
+def load_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return p, "measured"
+    except Exception:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0, "sm_max_mhz": 2070.0}, \
+            "fallback"
+
+
+# ---------------------------------------------------------------- distributed
+
+def dist_info():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def dist_init(world, use_cuda):
+    if world <= 1:
+        return None
+    import torch.distributed as dist
+
+    dist.init_process_group(backend="nccl" if use_cuda else "gloo")
+    return dist
+
+
+def barrier(dist):
+    if dist is not None:
+        dist.barrier()
+
+
+def max_over_ranks(dist, x: float, device=None) -> float:
+    if dist is None:
+        return x
+    import torch
+
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+# ---------------------------------------------------------------- clocks
+
+class ClockSampler:
+    """Samples SM clocks and throttle reasons with nvidia-smi while running."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: str):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                                          "-i", self.gpu, "-lms", "200"], stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self) -> dict | None:
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.f.close()
+        rows = []
+        with open(self.path) as f:
+            for line in f:
+                parts = [x.strip() for x in line.split(",")]
+                if len(parts) >= 9:
+                    rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return None
+        def num(x):
+            try:
+                return float(x)
+            except ValueError:
+                return None
+        sm = [num(r[1]) for r in rows if num(r[1]) is not None]
+        mx = max((num(r[2]) for r in rows if num(r[2]) is not None), default=None)
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower() == "active"})
+        load = [s for s in sm if mx and s >= 0.5 * mx] or sm
+        return {"sm_mhz": statistics.median(load) if load else None, "sm_max_mhz": mx, "reasons": reasons,
+                "samples": len(rows)}
+
+
+# ---------------------------------------------------------------- data
+
+def make_pair(seed: int, n: int):
+    from paper_2511_18207_gb300 import workloads as W
+
+    return W.anisotropic_pair(n, n, DIM, shift_sigma=0.1, t_frac=0.001, nu=3.0, seed=seed)
+
+
+# ---------------------------------------------------------------- oracle sample
+
+def oracle_sample(A, B, rows_cov: int = 200_000, rows_hd: int = 256) -> dict:
+    """Times the FP64 oracle's ProHD on a bounded sample of the workload and
+    extrapolates to the full pair: the covariance is accumulated over every
+    k-th row (time x N/rows), centroids, power iteration and the full
+    selection (projection + sort of all points) run as they are, and the
+    subset HD is run for the first `rows_hd` outer rows of each direction
+    (time x subset size / rows_hd, its cost is linear in the outer rows)."""
+    import numpy as np
+
+    import oracle
+
+    nA, nB = A.shape[0], B.shape[0]
+    N = nA + nB
+    sa = max(1, N // rows_cov)
+    t0 = time.perf_counter()
+    _, C = oracle.union_covariance(A[::sa], B[::sa])
+    rows_used = A[::sa].shape[0] + B[::sa].shape[0]
+    t_cov = (time.perf_counter() - t0) * N / rows_used
+    t0 = time.perf_counter()
+    u0 = oracle.centroid_axis(oracle.centroid(A), oracle.centroid(B))
+    U, _, _ = oracle.power_iteration(C, M_PCS, seed=0)
+    t_dir = time.perf_counter() - t0
+    dirs = np.vstack([u0[None, :], U])
+    t0 = time.perf_counter()
+    ia = oracle.select(A, dirs, oracle.k_list(nA, 1 + M_PCS, ALPHA, ALPHA / M_PCS))
+    ib = oracle.select(B, dirs, oracle.k_list(nB, 1 + M_PCS, ALPHA, ALPHA / M_PCS))
+    t_sel = time.perf_counter() - t0
+    As, Bs = A[ia], B[ib]
+    ra, rb = min(rows_hd, As.shape[0]), min(rows_hd, Bs.shape[0])
+    t0 = time.perf_counter()
+    oracle.directed_hd(As, Bs, 0, ra)
+    oracle.directed_hd(Bs, As, 0, rb)
+    t_hd_s = time.perf_counter() - t0
+    t_hd = t_hd_s * (As.shape[0] + Bs.shape[0]) / (ra + rb)
+    total = t_cov + t_dir + t_sel + t_hd
+    return {"seconds_per_pair": total, "value": 1.0 / total, "cores": oracle.num_threads(),
+            "stages_s": {"covariance": round(t_cov, 3), "centroids+power": round(t_dir, 3),
+                         "selection": round(t_sel, 3), "subset_hd": round(t_hd, 3)},
+            "sample": (f"covariance over every {sa}-th row ({rows_used} rows) scaled x{N / rows_used:.1f}; "
+                       f"centroids, power iteration and selection on all {N} points; subset HD outer loop on "
+                       f"{ra}+{rb} of {As.shape[0]}+{Bs.shape[0]} subset rows, scaled linearly"),
+            "nsel": [int(As.shape[0]), int(Bs.shape[0])]}
+
+
+# ---------------------------------------------------------------- GPU arm
+
+def gpu_arm(args):
+    import numpy as np
+    import torch
+
+    from paper_2511_18207_gb300 import prohd
+
+    rank, world, local = dist_info()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    dist = dist_init(world, True)
+    peaks, peak_src = load_peaks()
+    n = args.n
+
+    A, B = make_pair(seed=args.seed + rank, n=n)
+    At, Bt = torch.from_numpy(A).to(dev), torch.from_numpy(B).to(dev)
+    ctx = prohd.Context()
+    st = torch.cuda.current_stream()
+
+    def params(prec):
+        return prohd.default_params(m=M_PCS, alpha_c=ALPHA, precision=prec)
+
+    p16, pbf = params("fp16"), params("bf16")
+    out = torch.empty(ctypes.sizeof(prohd.Result), dtype=torch.uint8, device=dev)
+    ws_need = max(ctx.lib.prohd_estimate_workspace_size(n, n, DIM, ctypes.byref(p16)),
+                  ctx.lib.prohd_estimate_workspace_size(n, n, DIM, ctypes.byref(pbf)))
+    ws = ctx.workspace(ws_need)
+
+    visible = [v for v in os.environ.get("CUDA_VISIBLE_DEVICES", "").split(",") if v.strip()]
+    gpu_idx = visible[local] if local < len(visible) else str(local)
+    clocks = ClockSampler(gpu_idx)
+    clocks.start()
+
+    def run_steps(p, k):
+        for _ in range(k):
+            ctx.prohd_estimate(At, Bt, params=p, out=out, ws=ws)
+
+    # warm-up
+    run_steps(p16, args.warmup)
+    torch.cuda.synchronize()
+
+    # timed region: K steps, profiling phases with CUDA events on the same stream
+    ctx.profile_read(reset=True)
+    ctx.profile_enable(True)
+    l0 = ctx.launch_count()
+    barrier(dist)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(st)
+    run_steps(p16, args.steps)
+    e1.record(st)
+    torch.cuda.synchronize()
+    barrier(dist)
+    launches = ctx.launch_count() - l0
+    ctx.profile_enable(False)
+    phases = ctx.profile_read(reset=True)
+    t_ms = max_over_ranks(dist, e0.elapsed_time(e1), dev)
+    ms_step = t_ms / args.steps
+    res16 = prohd.decode_result(out)
+
+    # BF16 tiles
+    run_steps(pbf, 1)
+    torch.cuda.synchronize()
+    e0.record(st)
+    run_steps(pbf, args.steps)
+    e1.record(st)
+    torch.cuda.synchronize()
+    ms_bf = e0.elapsed_time(e1) / args.steps
+    resbf = prohd.decode_result(out)
+
+    # exact Hausdorff distance of the full sets (the comparison the metric names)
+    exact = None
+    if not args.no_exact:
+        small = torch.randn(4096, DIM, device=dev)
+        ctx.hausdorff_exact(small, small, "fp16")  # loads the kernels
+        torch.cuda.synchronize()
+        hout = torch.empty(ctypes.sizeof(prohd.HdResult), dtype=torch.uint8, device=dev)
+        hws = ctx.workspace(ctx.lib.hausdorff_exact_workspace_size(n, n, DIM, 1))
+        e0.record(st)
+        ctx.hausdorff_exact(At, Bt, "fp16", out=hout, ws=hws)
+        e1.record(st)
+        torch.cuda.synchronize()
+        exact = prohd.decode_hd(hout)
+        exact["ms"] = e0.elapsed_time(e1)
+        ws = ctx.workspace(ws_need)
+    clk = clocks.stop()
+
+    # end to end through the C ABI with host buffers (H2D copies + D2H of the result)
+    Ah = torch.from_numpy(A).pin_memory()
+    Bh = torch.from_numpy(B).pin_memory()
+    hres = prohd.Result()
+    hws_need = ctx.lib.prohd_estimate_host_workspace_size(n, n, DIM, ctypes.byref(p16))
+    ws = ctx.workspace(hws_need)
+    ctx.prohd_estimate_host(Ah, Bh, params=p16, out_host=hres, ws=ws)
+    torch.cuda.synchronize()
+    e2e_steps = max(3, min(args.steps, 10))
+    barrier(dist)
+    torch.cuda.synchronize()
+    e0.record(st)
+    for _ in range(e2e_steps):
+        ctx.prohd_estimate_host(Ah, Bh, params=p16, out_host=hres, ws=ws)
+    e1.record(st)
+    torch.cuda.synchronize()
+    e2e_ms = max_over_ranks(dist, e0.elapsed_time(e1), dev) / e2e_steps
+
+    # roofline of the dominant kernel
+    nsa, nsb = res16["nsel_a"], res16["nsel_b"]
+    cand = {}
+    for name, (ms, cnt) in phases.items():
+        if cnt:
+            cand[name] = (ms / cnt, cnt)
+    single = {k: v for k, v in cand.items() if k in ("gram", "hd_contract", "power", "project")}
+    dom = max(single, key=lambda k: single[k][0] * (2 if k == "project" else 1)) if single else None
+    roof = None
+    fp32_peak = 152 * 128 * 2 * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
+    if dom == "gram":
+        t = cand["gram"][0] / 1e3
+        fl = 2.0 * (2 * n) * DIM * DIM
+        roof = {"kernel": "gram_kernel", "bound": "alu", "achieved": fl / t / 1e12, "peak": fp32_peak,
+                "unit": "TFLOP/s", "traffic": None,
+                "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 flop x max SM clock"}
+    elif dom == "hd_contract":
+        t = cand["hd_contract"][0] / 1e3
+        fl = 2.0 * nsa * nsb * DIM
+        roof = {"kernel": "hd_tc_kernel", "bound": "tensor", "achieved": fl / t / 1e12,
+                "peak": peaks["bf16_tflops"], "unit": "TFLOP/s", "traffic": None,
+                "peak_source": f"{peak_src} bf16 burst (fp16 has the same nominal rate)"}
+    elif dom == "project":
+        t = cand["project"][0] / 2 / 1e3  # two launches (one per set) per phase
+        by = n * DIM * 4.0 + (1 + M_PCS) * n * 4.0
+        roof = {"kernel": "proj_kernel", "bound": "hbm", "achieved": by / t / 1e9, "peak": peaks["hbm_gbs"],
+                "unit": "GB/s", "traffic": None, "peak_source": f"{peak_src} copy bandwidth"}
+    elif dom == "power":
+        roof = {"kernel": "power_iter_kernel", "bound": "latency", "achieved": None, "peak": None, "unit": None,
+                "traffic": None}
+    if roof and roof.get("achieved") is not None:
+        roof["frac"] = roof["achieved"] / roof["peak"]
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu:
+        s = oracle_sample(A, B)
+        cpu = {"value": s["value"], "unit": UNIT, "cores": s["cores"], "kind": "oracle", "sample": s["sample"],
+               "stages_s": s["stages_s"]}
+
+    H = exact["H"] if exact else None
+    line = {
+        "metric": METRIC, "value": world * 1000.0 / ms_step, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f16", "data": "synthetic",
+        "config": {"workload": WORKLOAD if n == N_POINTS else WORKLOAD.replace("2,000,000", f"{n:,}"),
+                   "n_a": n, "n_b": n, "D": DIM, "m": M_PCS, "alpha": ALPHA, "tiles": "fp16",
+                   "parallelism": f"replicas x{world} (independent pairs per rank)",
+                   "l2": "inputs (4.1 GB) larger than L2; no flush"},
+        "H_hat": res16["H"], "H_exact": H, "rel_err_vs_exact": (abs(res16["H"] - H) / H) if H else None,
+        "signed_err": ((res16["H"] - H) / H) if H else None,
+        "exact_ms": exact["ms"] if exact else None,
+        "speedup_vs_gpu_exact": (exact["ms"] / ms_step) if exact else None,
+        "nsel": [nsa, nsb], "status": res16["status"], "exact_status": exact["status"] if exact else None,
+        "rescored": [res16["n_rescored_a"], res16["n_rescored_b"]],
+        "bf16": {"value": world * 1000.0 / ms_bf, "ms_per_step": ms_bf, "H_hat": resbf["H"],
+                 "rel_err_vs_exact": (abs(resbf["H"] - H) / H) if H else None,
+                 "rel_err_lowp_before_rescoring": (abs(resbf["H_lowp"] - resbf["H"]) / resbf["H"])},
+        "fp16_rel_err_lowp_before_rescoring": abs(res16["H_lowp"] - res16["H"]) / res16["H"],
+        "phases_ms_per_step": {k: round(v[0] * v[1] / args.steps, 4) for k, v in cand.items()},
+        "e2e": {"value": world * 1000.0 / e2e_ms, "unit": UNIT, "ms_per_step": e2e_ms,
+                "h2d_bytes_per_step": 2 * n * DIM * 4, "d2h_bytes_per_step": ctypes.sizeof(prohd.Result)},
+        "gpu_launches": launches,
+        "roofline": roof,
+        "cpu_baseline": cpu,
+        "clocks": clk,
+    }
+    if rank == 0:
+        print(json.dumps(line))
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+# ---------------------------------------------------------------- reference arm
+
+def reference_arm(args):
+    rank, world, _ = dist_info()
+    if rank != 0:
+        return
+    import oracle
+
+    A, B = make_pair(seed=args.seed, n=args.n)
+    for _ in range(args.warmup):
+        oracle_sample(A, B, rows_cov=50_000, rows_hd=32)
+    t0 = time.perf_counter()
+    tot = 0.0
+    last = None
+    for _ in range(args.steps):
+        last = oracle_sample(A, B)
+        tot += last["seconds_per_pair"]
+    wall = time.perf_counter() - t0
+    value = args.steps / tot
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1000.0 * tot / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64", "data": "synthetic", "impl": "reference",
+        "config": {"workload": WORKLOAD, "n_a": args.n, "n_b": args.n, "D": DIM, "m": M_PCS, "alpha": ALPHA,
+                   "parallelism": "host cores (OpenMP)"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": last["cores"], "kind": "oracle",
+                         "sample": last["sample"]},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+        "stages_s": last["stages_s"], "wall_s": wall,
+    }
+    print(json.dumps(line))
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["prohd", "reference"], default="prohd")
+    ap.add_argument("--n", type=int, default=N_POINTS, help="points per set (default: the 2M workload)")
+    ap.add_argument("--seed", type=int, default=0)
+    ap.add_argument("--no-exact", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        reference_arm(args)
+    else:
+        gpu_arm(args)
+
+
+if __name__ == "__main__":
+    main()

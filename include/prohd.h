@@ -1,0 +1,248 @@
+/*
+ * prohd.h - C ABI of the GB300 (sm_103a) ProHD library.
+ *
+ * ProHD (arxiv 2511.18207) approximates the Hausdorff distance
+ *   H(A,B) = max{ h(A,B), h(B,A) },  h(A,B) = max_{a in A} min_{b in B} ||a - b||_2   (Eq. 1)
+ * by projecting both sets onto a few directions (the centroid axis, Algorithm 1,
+ * and the top-m principal components of [A;B], Algorithm 2), keeping the k
+ * smallest and k largest projections of each set per direction, and computing
+ * the exact Hausdorff distance of the two selected subsets (Algorithm 3).
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ * - Point sets are FP32, row-major, contiguous: point i of A is A[i*D .. i*D+D-1].
+ *   1 <= n < 2^31 points per set, 1 <= D <= 1024.
+ * - Unless a parameter says "host", every array pointer is a DEVICE pointer
+ *   owned by the caller. The library never frees or retains them.
+ * - Point indices are 0-based int32 (the paper counts from 1).
+ * - `stream` is a cudaStream_t passed as void* (NULL = legacy default stream).
+ *   Calls are asynchronous on that stream: they enqueue kernels and return.
+ *   They never synchronise the device and never allocate device memory.
+ * - Scratch memory is a caller-owned device buffer `ws` of at least the size
+ *   returned by the matching *_workspace_size query, 256-byte aligned.
+ *   Its contents on entry are ignored; on return it holds intermediate data
+ *   that the next call may overwrite. Two calls that run concurrently must
+ *   not share a workspace.
+ * - Results land in device memory; read them after synchronising `stream`.
+ *   Each result struct carries a device-side status (see prohd_status): a
+ *   non-finite input value or a bounded device wait that ran out is reported
+ *   there, not as the return value.
+ * - Return value: PROHD_OK when the work was enqueued; otherwise nothing was
+ *   enqueued and prohd_last_error(ctx) describes the problem.
+ * - Every non-sequential arithmetic path in the library is on the GPU; there
+ *   is no CPU fallback.
+ */
+#ifndef PROHD_H
+#define PROHD_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  PROHD_OK = 0,
+  PROHD_EINVAL = 1,      /* invalid argument: null pointer, size out of range, bad alpha */
+  PROHD_ENOMEM = 2,      /* workspace smaller than the *_workspace_size query */
+  PROHD_ECUDA = 3,       /* a CUDA runtime call failed (message in prohd_last_error) */
+  PROHD_ETIMEOUT = 4,    /* device-side: a bounded wait in a kernel ran out */
+  PROHD_ENONFINITE = 5,  /* device-side: the input holds NaN or Inf */
+  PROHD_ENOTSUP = 6      /* valid request this build does not support (e.g. GPU older than sm_103a) */
+} prohd_status;
+
+/* Tile precision of the distance contraction (Sec. III-C, "exact HD on the subsets"). */
+enum {
+  PROHD_FP32 = 0, /* direct-difference FP32 on CUDA cores; exact to FP32 rounding */
+  PROHD_FP16 = 1, /* FP16 tensor-core tiles, FP32 accumulation, rigorous margin + FP32 rescoring */
+  PROHD_BF16 = 2  /* BF16 tensor-core tiles, same refinement */
+};
+
+/* Opaque library context: device properties, tensor-map encoder, last error text. */
+typedef struct prohd_ctx prohd_ctx;
+
+/*
+ * ProHD parameters (Algorithm 3 and Sec. IV-A).
+ *   m            number of principal components; m < 0 selects floor(sqrt(D))
+ *   alpha_c      fraction kept per side on the centroid axis, 0 < alpha_c < 1:
+ *                k_c = max(1, floor(alpha_c * n)) per set (Algorithm 1)
+ *   alpha_p      fraction per side per component; alpha_p < 0 selects alpha_c / m
+ *                (Algorithm 3: alpha' = alpha / m), k_p = max(1, floor(alpha_p * n))
+ *   power_max_iters, power_tol
+ *                power iteration stops when 1 - |<v_t, v_{t-1}>| < power_tol or
+ *                after power_max_iters steps (defaults 1000 and 1e-13)
+ *   seed         seed of the SplitMix64 start vectors of the power iteration
+ *   precision    PROHD_FP32 / PROHD_FP16 / PROHD_BF16 for the subset HD
+ *   wait_timeout_ns  limit of every bounded device wait (default 4e9 ns)
+ */
+typedef struct {
+  int32_t m;
+  int32_t precision;
+  double alpha_c;
+  double alpha_p;
+  int32_t power_max_iters;
+  int32_t reserved0;
+  double power_tol;
+  uint64_t seed;
+  int64_t wait_timeout_ns;
+  int64_t reserved[4];
+} prohd_params;
+
+/*
+ * Result of an exact Hausdorff distance (Eq. 1). Distances are FP64 values of
+ * the witness pairs; the pairs are chosen from FP32 distances (exact rescoring
+ * of every candidate the low-precision pass could not rule out).
+ *   H, h_ab, h_ba   H = max(h_ab, h_ba)
+ *   wit_a, wit_b    witness of H: index into A and index into B
+ *   ab_a, ab_b      witness of h(A,B) (a and its nearest b)
+ *   ba_b, ba_a      witness of h(B,A) (b and its nearest a)
+ *   dir             0 if h_ab >= h_ba, else 1
+ *   status          prohd_status of the device work (OK, ETIMEOUT, ENONFINITE)
+ *   H_lowp          tensor paths: H from the low-precision tiles before any
+ *                   rescoring; FP32 path: same as H
+ *   n_rescored_a/b  rows of A / columns of B rescored in FP32 (0 on the FP32 path)
+ */
+typedef struct {
+  double H, h_ab, h_ba;
+  int64_t wit_a, wit_b;
+  int64_t ab_a, ab_b;
+  int64_t ba_b, ba_a;
+  int32_t dir;
+  int32_t status;
+  double H_lowp;
+  int64_t n_rescored_a, n_rescored_b;
+} prohd_hd_result;
+
+/* Result of prohd_estimate (Algorithm 3): hd is H_hat = H(A_sel, B_sel), with
+ * witness indices mapped back to A and B; nsel_a = |I^A|, nsel_b = |I^B|. */
+typedef struct {
+  prohd_hd_result hd;
+  int64_t nsel_a, nsel_b;
+} prohd_result;
+
+/* ---------------------------------------------------------------- context */
+
+/* Creates a context bound to the current CUDA device. Checks the device is
+ * sm_103 (else PROHD_ENOTSUP). Allocates host memory only. */
+prohd_status prohd_create(prohd_ctx** out);
+void prohd_destroy(prohd_ctx* ctx);
+/* Text of the last error reported through ctx (empty string if none). */
+const char* prohd_last_error(const prohd_ctx* ctx);
+/* Fills the defaults listed above (m = -1, alpha_c = 0.01, alpha_p = -1, FP16). */
+void prohd_params_default(prohd_params* p);
+/* k = max(1, floor(alpha * n)) computed in FP64, clamped to n (Algorithms 1-2). */
+int64_t prohd_k_of(double alpha, int64_t n);
+
+/* --------------------------------------------------------- workspace sizes */
+
+size_t hausdorff_exact_workspace_size(int64_t nA, int64_t nB, int D, int precision);
+size_t prohd_directions_workspace_size(int64_t nA, int64_t nB, int D, int m);
+size_t prohd_select_workspace_size(int64_t nA, int64_t nB, int D, int ndirs);
+size_t prohd_estimate_workspace_size(int64_t nA, int64_t nB, int D, const prohd_params* p);
+/* prohd_estimate_host also stages A and B in the workspace. */
+size_t prohd_estimate_host_workspace_size(int64_t nA, int64_t nB, int D, const prohd_params* p);
+
+/* ------------------------------------------------------------ entry points */
+
+/*
+ * Exact Hausdorff distance H(A,B) (Eq. 1; the paper computes it with a Faiss
+ * flat index, Sec. III-C and IV-A "ANN-Exact").
+ *   A [nA*D], B [nB*D]   device FP32 point sets
+ *   precision            PROHD_FP32, PROHD_FP16 or PROHD_BF16 (tile dtype)
+ *   out                  device pointer to one prohd_hd_result
+ * FP16/BF16: tensor-core tiles give every point's nearest-neighbour distance
+ * up to a rigorous rounding margin; every row and column whose margin
+ * interval reaches the largest lower bound is rescored in FP32, so the result
+ * equals the FP32 path's up to FP32 rounding. Tensor paths need D <= 256.
+ */
+prohd_status hausdorff_exact(prohd_ctx* ctx, const float* A, int64_t nA, const float* B, int64_t nB,
+                             int D, int precision, prohd_hd_result* out, void* ws, size_t ws_bytes,
+                             void* stream);
+
+/*
+ * Projection directions (Algorithm 1 step 2 and Algorithm 2 step 2):
+ *   dirs[0]      centroid axis u = (ybar - xbar)/||ybar - xbar||, or e_1 when
+ *                ||ybar - xbar|| < 1e-9
+ *   dirs[1..m]   top-m principal components of the stacked set [A;B]: unit
+ *                eigenvectors of the union covariance C = (1/N) sum (z-mu)(z-mu)^T
+ *                by power iteration with deflation, largest-magnitude entry
+ *                made positive
+ *   eig[0..m-1]  their Rayleigh quotients (may be NULL)
+ * dirs is a device FP64 array [(1+m) * D]; m comes from p (m < 0: floor(sqrt D)).
+ * Centroid sums and the covariance are accumulated in FP64 across blocks.
+ */
+prohd_status prohd_directions(prohd_ctx* ctx, const float* A, int64_t nA, const float* B, int64_t nB,
+                              int D, const prohd_params* p, double* dirs, double* eig, void* ws,
+                              size_t ws_bytes, void* stream);
+
+/*
+ * Extreme selection for given directions (Algorithms 1-2, steps "argsort",
+ * "keep bottom-k and top-k", "unique"; Algorithm 3 step 4, union):
+ *   dirs       device FP64 [ndirs * D] (any vectors; the projection is x^T u)
+ *   kA, kB     HOST int64 [ndirs]: k per direction for A and for B (clamped to n)
+ *   idxA       device int32 [nA]: receives the sorted unique selected indices
+ *   nselA      device int64 scalar: receives |I^A|; same for B
+ * Point i is kept for direction d if it is among the first k of the ascending
+ * order of (x_i^T u_d, i) or of the descending order of x_i^T u_d with
+ * ascending i on ties. The order uses the FP64 projection summed over
+ * k = 0..D-1 with separately rounded products and sums, so the result is
+ * identical to a sequential FP64 full sort.
+ */
+prohd_status prohd_select(prohd_ctx* ctx, const float* A, int64_t nA, const float* B, int64_t nB,
+                          int D, const double* dirs, int ndirs, const int64_t* kA, const int64_t* kB,
+                          int32_t* idxA, int64_t* nselA, int32_t* idxB, int64_t* nselB, void* ws,
+                          size_t ws_bytes, void* stream);
+
+/*
+ * ProHD estimate H_hat(A,B) (Algorithm 3): directions, selection, and the exact
+ * Hausdorff distance of A_sel = A[I^A] and B_sel = B[I^B].
+ *   out        device pointer to one prohd_result
+ *   idxA/idxB  optional device int32 [nA]/[nB] receiving I^A, I^B (may be NULL)
+ *   dirs       optional device FP64 [(1+m) * D] receiving the directions (may be NULL)
+ */
+prohd_status prohd_estimate(prohd_ctx* ctx, const float* A, int64_t nA, const float* B, int64_t nB,
+                            int D, const prohd_params* p, prohd_result* out, int32_t* idxA,
+                            int32_t* idxB, double* dirs, void* ws, size_t ws_bytes, void* stream);
+
+/*
+ * prohd_estimate for HOST inputs: copies A_host and B_host (pinned memory
+ * recommended) into the workspace with cudaMemcpyAsync on `stream`, runs
+ * prohd_estimate, and copies the result into *out_host. Asynchronous: read
+ * *out_host after synchronising `stream`. The host buffers must stay valid
+ * until then. Uses prohd_estimate_host_workspace_size bytes of workspace.
+ */
+prohd_status prohd_estimate_host(prohd_ctx* ctx, const float* A_host, int64_t nA, const float* B_host,
+                                 int64_t nB, int D, const prohd_params* p, prohd_result* out_host,
+                                 void* ws, size_t ws_bytes, void* stream);
+
+/* ------------------------------------------------------------ observability */
+
+/* Phases timed by the profiler (one kernel each unless noted). */
+typedef enum {
+  PROHD_PH_GRAM = 0,      /* union Gram + centroid sums (gram_kernel), Algorithm 2 step 2 */
+  PROHD_PH_POWER = 1,     /* power iteration (one cluster launch) */
+  PROHD_PH_PROJECT = 2,   /* FP32 projections of both sets (two launches) */
+  PROHD_PH_SELECT = 3,    /* radix select, band, FP64 band ranking, compaction (several) */
+  PROHD_PH_GATHER = 4,    /* subset gather (two launches) */
+  PROHD_PH_HD_PREP = 5,   /* centring, scale, rounded copies (several) */
+  PROHD_PH_HD_CONTRACT = 6, /* the distance contraction: hd_tc_kernel, or the FP32 tile kernel */
+  PROHD_PH_HD_RESCORE = 7,  /* margins, candidate rescoring, FP64 witnesses (several) */
+  PROHD_PH_COUNT = 8
+} prohd_phase;
+
+/* While on, every call records a CUDA event pair on its stream around each
+ * phase (host-side event objects only; no device allocation). */
+prohd_status prohd_profile_enable(prohd_ctx* ctx, int on);
+/* Waits for the recorded events, adds their durations to per-phase totals and
+ * copies the totals: ms[PROHD_PH_COUNT] (milliseconds) and count[PROHD_PH_COUNT]
+ * (phase instances). reset != 0 clears the totals afterwards. Host arrays. */
+prohd_status prohd_profile_read(prohd_ctx* ctx, double* ms, int64_t* count, int reset);
+/* Number of kernels this library has launched in this process. */
+uint64_t prohd_launch_count(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* PROHD_H */

@@ -1,0 +1,481 @@
+// C ABI entry points (include/prohd.h): argument checks, workspace layout and
+// the order of the kernels of each call. Everything runs asynchronously on
+// the caller's stream; nothing here allocates device memory or synchronises.
+#include <math.h>
+#include <stdio.h>
+
+#include <algorithm>
+#include <new>
+
+#include "common.cuh"
+#include "internal.h"
+
+namespace prohd {
+
+std::atomic<uint64_t> g_launches{0};
+
+__global__ void set_i64_kernel(int64_t* p, int64_t v) { *p = v; }
+__global__ void zero_i32_kernel(int* p, int n) {
+  for (int i = threadIdx.x; i < n; i += blockDim.x) p[i] = 0;
+}
+__global__ void finish_estimate_kernel(prohd_result* out, const int64_t* nselA, const int64_t* nselB) {
+  out->nsel_a = *nselA;
+  out->nsel_b = *nselB;
+}
+
+cudaError_t set_i64(int64_t* p, int64_t v, cudaStream_t st) {
+  count_launch();
+  set_i64_kernel<<<1, 1, 0, st>>>(p, v);
+  return cudaGetLastError();
+}
+cudaError_t zero_i32(int* p, int n, cudaStream_t st) {
+  count_launch();
+  zero_i32_kernel<<<1, 32, 0, st>>>(p, n);
+  return cudaGetLastError();
+}
+
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                  const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+bool encode_2d(prohd_ctx* ctx, CUtensorMap* map, CUtensorMapDataType dtype, const void* base, uint64_t inner,
+               uint64_t outer, uint64_t row_bytes, uint32_t box_inner, uint32_t box_outer, CUtensorMapSwizzle swz) {
+  if (!ctx->encode_tiled) return false;
+  cuuint64_t dims[2] = {inner, outer};
+  cuuint64_t strides[1] = {row_bytes};
+  cuuint32_t box[2] = {box_inner, box_outer};
+  cuuint32_t estr[2] = {1, 1};
+  CUresult r = reinterpret_cast<EncodeTiledFn>(ctx->encode_tiled)(
+      map, dtype, 2, const_cast<void*>(base), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, swz,
+      CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS;
+}
+
+}  // namespace prohd
+
+using namespace prohd;
+
+// ---------------------------------------------------------------- helpers
+
+static prohd_status fail(prohd_ctx* ctx, prohd_status s, const char* fmt, const char* detail = "") {
+  if (ctx) {
+    char buf[512];
+    snprintf(buf, sizeof buf, fmt, detail);
+    ctx->err = buf;
+  }
+  return s;
+}
+
+static prohd_status cuda_fail(prohd_ctx* ctx, cudaError_t e) {
+  return fail(ctx, PROHD_ECUDA, "CUDA error: %s", cudaGetErrorString(e));
+}
+
+static bool bad_n(int64_t n) { return n < 1 || n >= ((int64_t)1 << 31); }
+
+static int resolve_m(const prohd_params* p, int D) {
+  return p->m < 0 ? (int)floor(sqrt((double)D)) : p->m;
+}
+static double resolve_alpha_p(const prohd_params* p, int m) {
+  return p->alpha_p < 0 ? p->alpha_c / (double)std::max(m, 1) : p->alpha_p;
+}
+
+static prohd_status check_sets(prohd_ctx* ctx, const float* A, int64_t nA, const float* B, int64_t nB, int D) {
+  if (!ctx) return PROHD_EINVAL;
+  if (!A || !B) return fail(ctx, PROHD_EINVAL, "null point-set pointer%s");
+  if (bad_n(nA) || bad_n(nB)) return fail(ctx, PROHD_EINVAL, "set sizes must be in [1, 2^31)%s");
+  if (D < 1 || D > 1024) return fail(ctx, PROHD_EINVAL, "D must be in [1, 1024]%s");
+  return PROHD_OK;
+}
+
+static prohd_status check_params(prohd_ctx* ctx, const prohd_params* p, int D) {
+  if (!p) return fail(ctx, PROHD_EINVAL, "null params%s");
+  if (!(p->alpha_c > 0.0 && p->alpha_c < 1.0)) return fail(ctx, PROHD_EINVAL, "alpha_c must be in (0, 1)%s");
+  if (p->alpha_p >= 0.0 && !(p->alpha_p > 0.0 && p->alpha_p < 1.0))
+    return fail(ctx, PROHD_EINVAL, "alpha_p must be in (0, 1) or negative for alpha_c / m%s");
+  const int m = resolve_m(p, D);
+  if (m < 0 || m > D || m > 63) return fail(ctx, PROHD_EINVAL, "m must be in [0, min(D, 63)]%s");
+  if (p->precision != PROHD_FP32 && p->precision != PROHD_FP16 && p->precision != PROHD_BF16)
+    return fail(ctx, PROHD_EINVAL, "unknown precision%s");
+  if (p->precision != PROHD_FP32 && !tc_supported_dim(D))
+    return fail(ctx, PROHD_ENOTSUP, "tensor-core precisions need D <= 256 (use PROHD_FP32)%s");
+  if (p->power_max_iters < 1) return fail(ctx, PROHD_EINVAL, "power_max_iters must be >= 1%s");
+  return PROHD_OK;
+}
+
+static prohd_status check_ws(prohd_ctx* ctx, void* ws, size_t ws_bytes, size_t need) {
+  if (!ws) return fail(ctx, PROHD_EINVAL, "null workspace%s");
+  if (reinterpret_cast<uintptr_t>(ws) & 255) return fail(ctx, PROHD_EINVAL, "workspace must be 256-byte aligned%s");
+  if (ws_bytes < need) return fail(ctx, PROHD_ENOMEM, "workspace too small%s");
+  return PROHD_OK;
+}
+
+// per-direction k for one set (Algorithms 1-3): k_c for the centroid axis, k_p for the PCs
+static void k_list(int64_t n, int nd, double alpha_c, double alpha_p, int64_t* k) {
+  for (int d = 0; d < nd; ++d) k[d] = prohd_k_of(d == 0 ? alpha_c : alpha_p, n);
+}
+static int64_t subset_bound(int64_t n, int nd, const int64_t* k) {
+  int64_t s = 0;
+  for (int d = 0; d < nd; ++d) s += 2 * std::min(k[d], n);
+  return std::min(n, s);
+}
+
+// ---------------------------------------------------------------- layouts
+
+namespace {
+
+struct HdLayout {
+  int* status;
+  int64_t *nA, *nB;
+};
+void hd_layout(Arena& a, int64_t nA, int64_t nB, int D, int precision, HdLayout& L) {
+  L.status = a.take<int>(8);
+  L.nA = a.take<int64_t>(1);
+  L.nB = a.take<int64_t>(1);
+  hd_core_layout(a, nA, nB, D, precision);
+}
+
+struct EstLayout {
+  int* status;
+  double* dirs;
+  double* eig;
+  int32_t *idxA, *idxB;
+  int64_t *nselA, *nselB;
+  float *As, *Bs;
+  int64_t boundA, boundB;
+  int nd;
+  int64_t kA[64], kB[64];
+  size_t mark_dir, mark_sel, mark_hd;  // arena offsets where each phase's scratch starts
+};
+
+void est_layout(Arena& a, int64_t nA, int64_t nB, int D, const prohd_params* p, EstLayout& L) {
+  const int m = resolve_m(p, D);
+  L.nd = 1 + m;
+  const double ap = resolve_alpha_p(p, m);
+  k_list(nA, L.nd, p->alpha_c, ap, L.kA);
+  k_list(nB, L.nd, p->alpha_c, ap, L.kB);
+  L.boundA = subset_bound(nA, L.nd, L.kA);
+  L.boundB = subset_bound(nB, L.nd, L.kB);
+  L.status = a.take<int>(8);
+  L.dirs = a.take<double>((size_t)L.nd * D);
+  L.eig = a.take<double>((size_t)std::max(m, 1));
+  L.idxA = a.take<int32_t>((size_t)nA);
+  L.idxB = a.take<int32_t>((size_t)nB);
+  L.nselA = a.take<int64_t>(1);
+  L.nselB = a.take<int64_t>(1);
+  L.As = a.take<float>((size_t)L.boundA * D);
+  L.Bs = a.take<float>((size_t)L.boundB * D);
+  // the three phases run one after another and share the rest of the arena
+  const size_t start = a.off;
+  size_t end = start;
+  L.mark_dir = L.mark_sel = L.mark_hd = (start + 255) / 256 * 256;
+  Arena t = a;
+  directions_layout(t, nA, nB, D, m);
+  end = std::max(end, t.off);
+  t = a;
+  select_layout(t, nA, nB, D, L.nd);
+  end = std::max(end, t.off);
+  t = a;
+  hd_core_layout(t, L.boundA, L.boundB, D, p->precision);
+  end = std::max(end, t.off);
+  a.off = end;
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------- C ABI
+
+extern "C" {
+
+prohd_status prohd_create(prohd_ctx** out) {
+  if (!out) return PROHD_EINVAL;
+  *out = nullptr;
+  prohd_ctx* c = new (std::nothrow) prohd_ctx();
+  if (!c) return PROHD_ENOMEM;
+  cudaError_t e = cudaGetDevice(&c->device);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, c->device);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&c->cc_major, cudaDevAttrComputeCapabilityMajor, c->device);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&c->cc_minor, cudaDevAttrComputeCapabilityMinor, c->device);
+  if (e == cudaSuccess)
+    e = cudaDeviceGetAttribute(&c->smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, c->device);
+  if (e != cudaSuccess) {
+    delete c;
+    return PROHD_ECUDA;
+  }
+  if (c->cc_major != 10 || c->cc_minor != 3) {
+    delete c;
+    return PROHD_ENOTSUP;  // the library is built for sm_103a only
+  }
+  cudaDriverEntryPointQueryResult q;
+  void* fn = nullptr;
+  if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+      q == cudaDriverEntryPointSuccess)
+    c->encode_tiled = fn;
+  *out = c;
+  return PROHD_OK;
+}
+
+void prohd_destroy(prohd_ctx* ctx) {
+  if (!ctx) return;
+  for (auto& p : ctx->pending) {
+    cudaEventDestroy(p.a);
+    cudaEventDestroy(p.b);
+  }
+  delete ctx;
+}
+
+const char* prohd_last_error(const prohd_ctx* ctx) { return ctx ? ctx->err.c_str() : "null context"; }
+
+void prohd_params_default(prohd_params* p) {
+  if (!p) return;
+  *p = prohd_params{};
+  p->m = -1;
+  p->precision = PROHD_FP16;
+  p->alpha_c = 0.01;
+  p->alpha_p = -1.0;
+  p->power_max_iters = 1000;
+  p->power_tol = 1e-13;
+  p->seed = 0;
+  p->wait_timeout_ns = kDefaultTimeoutNs;
+}
+
+int64_t prohd_k_of(double alpha, int64_t n) {
+  int64_t k = (int64_t)floor(alpha * (double)n);
+  if (k < 1) k = 1;
+  if (k > n) k = n;
+  return k;
+}
+
+size_t hausdorff_exact_workspace_size(int64_t nA, int64_t nB, int D, int precision) {
+  if (bad_n(nA) || bad_n(nB) || D < 1) return 0;
+  Arena a;
+  HdLayout L;
+  hd_layout(a, nA, nB, D, precision, L);
+  return a.off + 256;
+}
+
+size_t prohd_directions_workspace_size(int64_t nA, int64_t nB, int D, int m) {
+  Arena a;
+  a.take<int>(8);
+  directions_layout(a, nA, nB, D, m < 0 ? (int)floor(sqrt((double)D)) : m);
+  return a.off + 256;
+}
+
+size_t prohd_select_workspace_size(int64_t nA, int64_t nB, int D, int ndirs) {
+  if (bad_n(nA) || bad_n(nB) || ndirs < 1) return 0;
+  Arena a;
+  a.take<int>(8);
+  select_layout(a, nA, nB, D, ndirs);
+  return a.off + 256;
+}
+
+size_t prohd_estimate_workspace_size(int64_t nA, int64_t nB, int D, const prohd_params* p) {
+  if (!p || bad_n(nA) || bad_n(nB) || D < 1) return 0;
+  Arena a;
+  EstLayout L;
+  est_layout(a, nA, nB, D, p, L);
+  return a.off + 256;
+}
+
+size_t prohd_estimate_host_workspace_size(int64_t nA, int64_t nB, int D, const prohd_params* p) {
+  if (!p || bad_n(nA) || bad_n(nB) || D < 1) return 0;
+  Arena a;
+  a.take<float>((size_t)nA * D);
+  a.take<float>((size_t)nB * D);
+  a.take<prohd_result>(1);
+  const size_t base = a.off;
+  Arena b;
+  EstLayout L;
+  est_layout(b, nA, nB, D, p, L);
+  return base + b.off + 512;
+}
+
+prohd_status hausdorff_exact(prohd_ctx* ctx, const float* A, int64_t nA, const float* B, int64_t nB, int D,
+                             int precision, prohd_hd_result* out, void* ws, size_t ws_bytes, void* stream) {
+  prohd_status s = check_sets(ctx, A, nA, B, nB, D);
+  if (s) return s;
+  if (!out) return fail(ctx, PROHD_EINVAL, "null output%s");
+  if (precision != PROHD_FP32 && precision != PROHD_FP16 && precision != PROHD_BF16)
+    return fail(ctx, PROHD_EINVAL, "unknown precision%s");
+  if (precision != PROHD_FP32 && !tc_supported_dim(D))
+    return fail(ctx, PROHD_ENOTSUP, "tensor-core precisions need D <= 256 (use PROHD_FP32)%s");
+  if ((s = check_ws(ctx, ws, ws_bytes, hausdorff_exact_workspace_size(nA, nB, D, precision)))) return s;
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  Arena a;
+  a.base = static_cast<char*>(ws);
+  a.cap = ws_bytes;
+  HdLayout L;
+  hd_layout(a, nA, nB, D, precision, L);
+  Arena run;  // hd_core re-derives its buffers from the same offsets
+  run.base = static_cast<char*>(ws);
+  run.cap = ws_bytes;
+  run.take<int>(8);
+  run.take<int64_t>(1);
+  run.take<int64_t>(1);
+  cudaError_t e = zero_i32(L.status, 8, st);
+  if (!e) e = set_i64(L.nA, nA, st);
+  if (!e) e = set_i64(L.nB, nB, st);
+  if (!e) e = hd_core(ctx, A, L.nA, nA, B, L.nB, nB, D, precision, nullptr, nullptr, out, L.status, run,
+                      kDefaultTimeoutNs, st);
+  return e ? cuda_fail(ctx, e) : PROHD_OK;
+}
+
+prohd_status prohd_directions(prohd_ctx* ctx, const float* A, int64_t nA, const float* B, int64_t nB, int D,
+                              const prohd_params* p, double* dirs, double* eig, void* ws, size_t ws_bytes,
+                              void* stream) {
+  prohd_status s = check_sets(ctx, A, nA, B, nB, D);
+  if (s) return s;
+  if (!p) return fail(ctx, PROHD_EINVAL, "null params%s");
+  if (!dirs) return fail(ctx, PROHD_EINVAL, "null dirs%s");
+  const int m = resolve_m(p, D);
+  if (m < 0 || m > D || m > 63) return fail(ctx, PROHD_EINVAL, "m must be in [0, min(D, 63)]%s");
+  if (p->power_max_iters < 1) return fail(ctx, PROHD_EINVAL, "power_max_iters must be >= 1%s");
+  if ((s = check_ws(ctx, ws, ws_bytes, prohd_directions_workspace_size(nA, nB, D, m)))) return s;
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  Arena a;
+  a.base = static_cast<char*>(ws);
+  a.cap = ws_bytes;
+  int* status = a.take<int>(8);
+  cudaError_t e = zero_i32(status, 8, st);
+  if (!e) e = directions_run(ctx, A, nA, B, nB, D, m, p->power_max_iters, p->power_tol, p->seed, dirs, eig, status, a, st);
+  return e ? cuda_fail(ctx, e) : PROHD_OK;
+}
+
+prohd_status prohd_select(prohd_ctx* ctx, const float* A, int64_t nA, const float* B, int64_t nB, int D,
+                          const double* dirs, int ndirs, const int64_t* kA, const int64_t* kB, int32_t* idxA,
+                          int64_t* nselA, int32_t* idxB, int64_t* nselB, void* ws, size_t ws_bytes, void* stream) {
+  prohd_status s = check_sets(ctx, A, nA, B, nB, D);
+  if (s) return s;
+  if (!dirs || ndirs < 1 || ndirs > 64) return fail(ctx, PROHD_EINVAL, "need 1..64 directions%s");
+  if (!kA || !kB) return fail(ctx, PROHD_EINVAL, "null k lists%s");
+  for (int d = 0; d < ndirs; ++d)
+    if (kA[d] < 1 || kB[d] < 1) return fail(ctx, PROHD_EINVAL, "k must be >= 1%s");
+  if (!idxA || !idxB || !nselA || !nselB) return fail(ctx, PROHD_EINVAL, "null output%s");
+  if ((s = check_ws(ctx, ws, ws_bytes, prohd_select_workspace_size(nA, nB, D, ndirs)))) return s;
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  Arena a;
+  a.base = static_cast<char*>(ws);
+  a.cap = ws_bytes;
+  int* status = a.take<int>(8);
+  cudaError_t e = zero_i32(status, 8, st);
+  if (!e) e = select_run(ctx, A, nA, B, nB, D, dirs, ndirs, kA, kB, idxA, nselA, idxB, nselB, status, a, st);
+  return e ? cuda_fail(ctx, e) : PROHD_OK;
+}
+
+static prohd_status estimate_impl(prohd_ctx* ctx, const float* A, int64_t nA, const float* B, int64_t nB, int D,
+                                  const prohd_params* p, prohd_result* out, int32_t* idxA, int32_t* idxB,
+                                  double* dirs, char* wsb, size_t ws_bytes, cudaStream_t st) {
+  Arena a;
+  a.base = wsb;
+  a.cap = ws_bytes;
+  EstLayout L;
+  est_layout(a, nA, nB, D, p, L);
+  if (a.overflow()) return fail(ctx, PROHD_ENOMEM, "workspace too small%s");
+  if (idxA) L.idxA = idxA;
+  if (idxB) L.idxB = idxB;
+  if (dirs) L.dirs = dirs;
+  const int m = L.nd - 1;
+  auto phase = [&](size_t mark) {
+    Arena t;
+    t.base = wsb;
+    t.cap = ws_bytes;
+    t.off = mark;
+    return t;
+  };
+  cudaError_t e = zero_i32(L.status, 8, st);
+  if (!e) {
+    Arena t = phase(L.mark_dir);
+    e = directions_run(ctx, A, nA, B, nB, D, m, p->power_max_iters, p->power_tol, p->seed, L.dirs, L.eig, L.status, t, st);
+  }
+  if (!e) {
+    Arena t = phase(L.mark_sel);
+    e = select_run(ctx, A, nA, B, nB, D, L.dirs, L.nd, L.kA, L.kB, L.idxA, L.nselA, L.idxB, L.nselB, L.status, t, st);
+  }
+  {
+    PhaseTimer pt(ctx, PROHD_PH_GATHER, st);
+    if (!e) e = gather_rows(A, D, L.idxA, L.nselA, L.boundA, L.As, ctx->num_sms, st);
+    if (!e) e = gather_rows(B, D, L.idxB, L.nselB, L.boundB, L.Bs, ctx->num_sms, st);
+  }
+  if (!e) {
+    Arena t = phase(L.mark_hd);
+    const int64_t to = p->wait_timeout_ns > 0 ? p->wait_timeout_ns : kDefaultTimeoutNs;
+    e = hd_core(ctx, L.As, L.nselA, L.boundA, L.Bs, L.nselB, L.boundB, D, p->precision, L.idxA, L.idxB, &out->hd,
+                L.status, t, to, st);
+  }
+  if (!e) {
+    count_launch();
+    finish_estimate_kernel<<<1, 1, 0, st>>>(out, L.nselA, L.nselB);
+    e = cudaGetLastError();
+  }
+  return e ? cuda_fail(ctx, e) : PROHD_OK;
+}
+
+prohd_status prohd_estimate(prohd_ctx* ctx, const float* A, int64_t nA, const float* B, int64_t nB, int D,
+                            const prohd_params* p, prohd_result* out, int32_t* idxA, int32_t* idxB, double* dirs,
+                            void* ws, size_t ws_bytes, void* stream) {
+  prohd_status s = check_sets(ctx, A, nA, B, nB, D);
+  if (s) return s;
+  if ((s = check_params(ctx, p, D))) return s;
+  if (!out) return fail(ctx, PROHD_EINVAL, "null output%s");
+  if ((s = check_ws(ctx, ws, ws_bytes, prohd_estimate_workspace_size(nA, nB, D, p)))) return s;
+  return estimate_impl(ctx, A, nA, B, nB, D, p, out, idxA, idxB, dirs, static_cast<char*>(ws), ws_bytes,
+                       reinterpret_cast<cudaStream_t>(stream));
+}
+
+prohd_status prohd_estimate_host(prohd_ctx* ctx, const float* A_host, int64_t nA, const float* B_host, int64_t nB,
+                                 int D, const prohd_params* p, prohd_result* out_host, void* ws, size_t ws_bytes,
+                                 void* stream) {
+  prohd_status s = check_sets(ctx, A_host, nA, B_host, nB, D);
+  if (s) return s;
+  if ((s = check_params(ctx, p, D))) return s;
+  if (!out_host) return fail(ctx, PROHD_EINVAL, "null output%s");
+  if ((s = check_ws(ctx, ws, ws_bytes, prohd_estimate_host_workspace_size(nA, nB, D, p)))) return s;
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  Arena a;
+  a.base = static_cast<char*>(ws);
+  a.cap = ws_bytes;
+  float* Ad = a.take<float>((size_t)nA * D);
+  float* Bd = a.take<float>((size_t)nB * D);
+  prohd_result* od = a.take<prohd_result>(1);
+  const size_t base = (a.off + 255) / 256 * 256;
+  cudaError_t e = cudaMemcpyAsync(Ad, A_host, sizeof(float) * nA * D, cudaMemcpyHostToDevice, st);
+  if (!e) e = cudaMemcpyAsync(Bd, B_host, sizeof(float) * nB * D, cudaMemcpyHostToDevice, st);
+  if (e) return cuda_fail(ctx, e);
+  s = estimate_impl(ctx, Ad, nA, Bd, nB, D, p, od, nullptr, nullptr, nullptr, static_cast<char*>(ws) + base,
+                    ws_bytes - base, st);
+  if (s) return s;
+  e = cudaMemcpyAsync(out_host, od, sizeof(prohd_result), cudaMemcpyDeviceToHost, st);
+  return e ? cuda_fail(ctx, e) : PROHD_OK;
+}
+
+prohd_status prohd_profile_enable(prohd_ctx* ctx, int on) {
+  if (!ctx) return PROHD_EINVAL;
+  ctx->profiling = on != 0;
+  return PROHD_OK;
+}
+
+prohd_status prohd_profile_read(prohd_ctx* ctx, double* ms, int64_t* count, int reset) {
+  if (!ctx) return PROHD_EINVAL;
+  for (auto& p : ctx->pending) {
+    float t = 0.f;
+    if (cudaEventSynchronize(p.b) == cudaSuccess && cudaEventElapsedTime(&t, p.a, p.b) == cudaSuccess) {
+      ctx->ph_ms[p.phase] += t;
+      ctx->ph_count[p.phase] += 1;
+    }
+    cudaEventDestroy(p.a);
+    cudaEventDestroy(p.b);
+  }
+  ctx->pending.clear();
+  for (int i = 0; i < PROHD_PH_COUNT; ++i) {
+    if (ms) ms[i] = ctx->ph_ms[i];
+    if (count) count[i] = ctx->ph_count[i];
+    if (reset) {
+      ctx->ph_ms[i] = 0.0;
+      ctx->ph_count[i] = 0;
+    }
+  }
+  return PROHD_OK;
+}
+
+uint64_t prohd_launch_count(void) { return g_launches.load(); }
+
+}  // extern "C"

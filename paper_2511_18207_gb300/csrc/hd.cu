@@ -1,0 +1,898 @@
+// Exact Hausdorff distance H(A,B) = max{h(A,B), h(B,A)},
+// h(A,B) = max_a min_b ||a-b||_2 (Eq. 1), as one distance contraction per
+// pair of sets with the row minimum (h(A,B)) and the column minimum (h(B,A))
+// reduced in the same pass.
+//
+// Two paths:
+//  * PROHD_FP32 - CUDA-core tiles of direct differences sum_k (a_k-b_k)^2;
+//    every row/column minimum carries its argmin (packed 64-bit atomics).
+//  * PROHD_FP16 / PROHD_BF16 - tcgen05 tensor-core tiles of
+//    ||a||^2 + ||b||^2 - 2 a.b on rounded, centred, power-of-two-scaled
+//    copies of the points, FP32 accumulation in TMEM, fused row-min and
+//    column-min epilogue. A rigorous per-row margin (rounding of the copies,
+//    of the FP32 accumulation and of the epilogue) turns each low-precision
+//    minimum into an interval; every row (column) whose interval reaches the
+//    largest lower bound is rescored with the FP32 direct-difference tiles,
+//    so the result is the FP32 path's up to FP32 rounding.
+// The witness pairs' distances are finally recomputed in FP64.
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+
+#include <algorithm>
+
+#include "common.cuh"
+#include "internal.h"
+
+namespace prohd {
+
+// =====================================================================
+// FP32 direct-difference tiles (exact path and rescoring)
+// =====================================================================
+
+constexpr int kSimtBM = 128, kSimtBN = 128, kSimtBK = 16;
+
+// Persistent tile loop over rows of X (optionally a list of row ids) against
+// all rows of Y. WANT_ROW: rowbest[out_row] = min (d^2, j); WANT_COL:
+// colbest[j] = min (d^2, row id). Packed values are (float bits << 32 | idx).
+template <bool ROW_LIST, bool WANT_ROW, bool WANT_COL>
+__global__ void __launch_bounds__(256, 1)
+    simt_dist_kernel(const float* __restrict__ X, const int32_t* __restrict__ rowlist,
+                     const int64_t* __restrict__ nrows_dev, const float* __restrict__ Y,
+                     const int64_t* __restrict__ ncols_dev, int D, unsigned long long* __restrict__ rowbest,
+                     unsigned long long* __restrict__ colbest) {
+  __shared__ __align__(16) float As[kSimtBK][kSimtBM + 4];
+  __shared__ __align__(16) float Bs[kSimtBK][kSimtBN + 4];
+  __shared__ unsigned long long s_col[WANT_COL ? 16 : 1][WANT_COL ? kSimtBN : 1];
+
+  const int64_t nrows = *nrows_dev, ncols = *ncols_dev;
+  const int64_t nct = (ncols + kSimtBN - 1) / kSimtBN;
+  const int64_t ntiles = ((nrows + kSimtBM - 1) / kSimtBM) * nct;
+  const int tid = threadIdx.x, ty = tid >> 4, tx = tid & 15;
+  const int lr = tid >> 1, koff = (tid & 1) * 8;
+
+  for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+    const int64_t rt = tile / nct, ct = tile % nct;
+    const int64_t xr = rt * kSimtBM + lr, yr = ct * kSimtBN + lr;
+    const bool vx = xr < nrows, vy = yr < ncols;
+    const int64_t srcx = vx ? (ROW_LIST ? (int64_t)rowlist[xr] : xr) : 0;
+    const float* xrow = X + srcx * D;
+    const float* yrow = Y + (vy ? yr : 0) * D;
+
+    float acc[8][8];
+#pragma unroll
+    for (int i = 0; i < 8; ++i)
+#pragma unroll
+      for (int j = 0; j < 8; ++j) acc[i][j] = 0.f;
+
+    for (int k0 = 0; k0 < D; k0 += kSimtBK) {
+      float xa[8], yb[8];
+#pragma unroll
+      for (int e = 0; e < 8; ++e) {
+        int k = k0 + koff + e;
+        xa[e] = (vx && k < D) ? __ldg(xrow + k) : 0.f;
+        yb[e] = (vy && k < D) ? __ldg(yrow + k) : 0.f;
+      }
+      __syncthreads();
+#pragma unroll
+      for (int e = 0; e < 8; ++e) {
+        As[koff + e][lr] = xa[e];
+        Bs[koff + e][lr] = yb[e];
+      }
+      __syncthreads();
+#pragma unroll
+      for (int kk = 0; kk < kSimtBK; ++kk) {
+        float4 a0 = *reinterpret_cast<const float4*>(&As[kk][ty * 4]);
+        float4 a1 = *reinterpret_cast<const float4*>(&As[kk][64 + ty * 4]);
+        float4 b0 = *reinterpret_cast<const float4*>(&Bs[kk][tx * 4]);
+        float4 b1 = *reinterpret_cast<const float4*>(&Bs[kk][64 + tx * 4]);
+        float a[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
+        float b[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
+#pragma unroll
+        for (int i = 0; i < 8; ++i)
+#pragma unroll
+          for (int j = 0; j < 8; ++j) {
+            float d = a[i] - b[j];
+            acc[i][j] = fmaf(d, d, acc[i][j]);
+          }
+      }
+    }
+
+    if (WANT_ROW) {
+#pragma unroll
+      for (int i = 0; i < 8; ++i) {
+        const int r = (i < 4) ? ty * 4 + i : 64 + ty * 4 + (i - 4);
+        unsigned long long best = ~0ull;
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+          const int c = (j < 4) ? tx * 4 + j : 64 + tx * 4 + (j - 4);
+          const int64_t gc = ct * kSimtBN + c;
+          if (gc < ncols) {
+            unsigned long long p = pack_min(acc[i][j], (uint32_t)gc);
+            best = p < best ? p : best;
+          }
+        }
+#pragma unroll
+        for (int o = 1; o < 16; o <<= 1) {
+          unsigned long long w = __shfl_xor_sync(0xffffffffu, best, o);
+          best = w < best ? w : best;
+        }
+        const int64_t gr = rt * kSimtBM + r;
+        if (tx == 0 && gr < nrows && best != ~0ull) atomicMin(rowbest + gr, best);
+      }
+    }
+    if (WANT_COL) {
+#pragma unroll
+      for (int j = 0; j < 8; ++j) {
+        const int c = (j < 4) ? tx * 4 + j : 64 + tx * 4 + (j - 4);
+        unsigned long long best = ~0ull;
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+          const int r = (i < 4) ? ty * 4 + i : 64 + ty * 4 + (i - 4);
+          const int64_t gr = rt * kSimtBM + r;
+          if (gr < nrows) {
+            const uint32_t id = ROW_LIST ? (uint32_t)rowlist[gr] : (uint32_t)gr;
+            unsigned long long p = pack_min(acc[i][j], id);
+            best = p < best ? p : best;
+          }
+        }
+        s_col[ty][c] = best;
+      }
+      __syncthreads();
+      if (tid < kSimtBN) {
+        unsigned long long best = s_col[0][tid];
+#pragma unroll
+        for (int t = 1; t < 16; ++t) best = s_col[t][tid] < best ? s_col[t][tid] : best;
+        const int64_t gc = ct * kSimtBN + tid;
+        if (gc < ncols && best != ~0ull) atomicMin(colbest + gc, best);
+      }
+      __syncthreads();
+    }
+  }
+}
+
+__global__ void fill_u64_kernel(unsigned long long* p, int64_t n, unsigned long long v) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    p[i] = v;
+}
+__global__ void fill_u32_kernel(unsigned* p, int64_t n, unsigned v) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    p[i] = v;
+}
+
+// =====================================================================
+// Tensor-core path: centring shift, scale, rounded copies
+// =====================================================================
+
+// Shift s = mean of the first <= 2048 rows of A and of B (FP64 sums), a
+// common origin that keeps ||a - s|| small; distances do not depend on it.
+__global__ void hd_shift_kernel(const float* __restrict__ A, const int64_t* nA_dev, const float* __restrict__ B,
+                                const int64_t* nB_dev, int D, float* __restrict__ shift) {
+  const int64_t na = *nA_dev < 2048 ? *nA_dev : 2048, nb = *nB_dev < 2048 ? *nB_dev : 2048;
+  for (int c = threadIdx.x; c < D; c += blockDim.x) {
+    double sa = 0.0, sb = 0.0;
+    for (int64_t i = 0; i < na; ++i) sa += (double)A[i * D + c];
+    for (int64_t i = 0; i < nb; ++i) sb += (double)B[i * D + c];
+    shift[c] = (float)(0.5 * (sa / (double)na + sb / (double)nb));
+  }
+}
+
+// max |x - s| over both sets (in FP32, the same values the copies use), and
+// the non-finite input check.
+__global__ void hd_maxabs_kernel(const float* __restrict__ X, const int64_t* n_dev, int D,
+                                 const float* __restrict__ shift, float* __restrict__ maxabs, int* status) {
+  const int64_t n = *n_dev;
+  const int lane = threadIdx.x & 31;
+  const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  float m = 0.f;
+  bool bad = false;
+  for (int64_t r = warp; r < n; r += nwarps) {
+    const float* x = X + r * D;
+    for (int c = lane; c < D; c += 32) {
+      float v = x[c];
+      bad |= !isfinite(v);
+      m = fmaxf(m, fabsf(v - shift[c]));
+    }
+  }
+  m = warp_max(m);
+  if (__any_sync(0xffffffffu, bad) && lane == 0) atomicMax(status, (int)PROHD_ENONFINITE);
+  if (lane == 0) atomic_max_nonneg(maxabs, m);
+}
+
+// Scale exponent: max|x - s| * 2^sigma lies in [2^12, 2^13), so the rounded
+// values stay below 2^13 and -2x below 2^14 (FP16 range 65504).
+__device__ __forceinline__ int scale_exponent(float maxabs) {
+  if (!(maxabs > 0.f)) return 0;
+  int e;
+  frexpf(maxabs, &e);  // maxabs = f 2^e, f in [0.5, 1)
+  return max(-120, min(120, 13 - e));
+}
+
+template <int BF16>
+struct TileT;
+template <>
+struct TileT<0> {
+  using T = __half;
+  static __device__ __forceinline__ T from(float x) { return __float2half_rn(x); }
+  static __device__ __forceinline__ float to(T h) { return __half2float(h); }
+};
+template <>
+struct TileT<1> {
+  using T = __nv_bfloat16;
+  static __device__ __forceinline__ T from(float x) { return __float2bfloat16_rn(x); }
+  static __device__ __forceinline__ float to(T h) { return __bfloat162float(h); }
+};
+
+// One warp per row. Writes the rounded copy h = round((x - s) 2^sigma)
+// (times `mult`: -2 for A, 1 for B) into Xt [n_pad, Dp], ||h||^2 (FP32) into
+// norm2, and eps >= ||(x - s) - h 2^-sigma|| + rounding of x - s (original
+// units) into eps. Padding rows: zeros, norm2 = +inf, eps = 0.
+template <int BF16>
+__global__ void hd_prep_kernel(const float* __restrict__ X, const int64_t* n_dev, int64_t n_pad, int D, int Dp,
+                               const float* __restrict__ shift, const float* __restrict__ maxabs, float mult,
+                               typename TileT<BF16>::T* __restrict__ Xt, float* __restrict__ norm2,
+                               float* __restrict__ eps, float* __restrict__ maxnorm, float* __restrict__ maxeps) {
+  using TT = TileT<BF16>;
+  using T = typename TT::T;
+  const int64_t n = *n_dev;
+  const int sig = scale_exponent(*maxabs);
+  const float scale = ldexpf(1.f, sig), inv = ldexpf(1.f, -sig);
+  const int lane = threadIdx.x & 31;
+  const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  float wmaxn = 0.f, wmaxe = 0.f;
+  for (int64_t r = warp; r < n_pad; r += nwarps) {
+    T* out = Xt + r * Dp;
+    if (r < n) {
+      const float* x = X + r * D;
+      float sn = 0.f, se = 0.f, st = 0.f;
+      for (int c = lane; c < Dp; c += 32) {
+        float hv = 0.f;
+        if (c < D) {
+          float t = x[c] - shift[c];
+          T h = TT::from(t * scale);
+          hv = TT::to(h);
+          float rr = t - hv * inv;  // exact: t and hv*inv agree to the tile precision
+          sn = fmaf(hv, hv, sn);
+          se = fmaf(rr, rr, se);
+          st = fmaf(t, t, st);
+        }
+        out[c] = TT::from(hv * mult);
+      }
+      sn = warp_sum(sn);
+      se = warp_sum(se);
+      st = warp_sum(st);
+      if (lane == 0) {
+        // ||(x-s)_exact - h/scale|| <= ||t - h/scale|| + 2^-24 ||t||; the FP32
+        // sums of squares are inflated for their own rounding.
+        float e = 1.001f * (sqrtf(se) + 5.9604645e-8f * sqrtf(st)) + 1e-30f;
+        norm2[r] = sn;
+        eps[r] = e;
+        wmaxn = fmaxf(wmaxn, sqrtf(sn));
+        wmaxe = fmaxf(wmaxe, e);
+      }
+    } else {
+      for (int c = lane; c < Dp; c += 32) out[c] = TT::from(0.f);
+      if (lane == 0) {
+        norm2[r] = __int_as_float(0x7f800000);
+        eps[r] = 0.f;
+      }
+    }
+  }
+  if (lane == 0) {
+    atomic_max_nonneg(maxnorm, wmaxn);
+    atomic_max_nonneg(maxeps, wmaxe);
+  }
+}
+
+// =====================================================================
+// tcgen05 contraction with fused row-min / column-min epilogue
+// =====================================================================
+//
+// Tile: 128 rows of A x 256 rows of B, K = Dp (<= 256) in 64-element blocks.
+// A CTA owns a 128-row block of A for a whole sweep over B (rows' minima stay
+// in registers), with the A block resident in shared memory; B streams
+// through a 4-stage TMA ring in 128B-swizzled 256x64 tiles. Accumulators are
+// double-buffered in TMEM (2 x 256 columns) so the epilogue of tile t
+// overlaps the MMAs of tile t+1.
+// Warps: 0 = TMA producer, 1 = MMA issuer (and TMEM owner), 2..5 = epilogue
+// (warp w reads TMEM lanes 32*(w%4) .. +31).
+// The MMA computes v = (-2 h_a) . h_b. Epilogue per element:
+//   t = v + ||h_b||^2  -> row min (plus ||h_a||^2 at the end) = d^2 row min
+//   d2 = t + ||h_a||^2 -> warp min over 32 rows (redux.sync.min.f32),
+//   combined over the 4 epilogue warps in shared memory, then one global
+//   atomicMin per column per tile (clamped at 0 so unsigned order = float order).
+
+constexpr int kTcBM = 128, kTcBN = 256, kTcBK = 64, kTcStages = 4;
+constexpr int kTcAKBytes = kTcBM * kTcBK * 2;   // 16 KB per A K-block
+constexpr int kTcBStage = kTcBN * kTcBK * 2;    // 32 KB per B stage
+constexpr int kTcThreads = 192;
+constexpr int kTcEpiWarps = 4;
+
+struct TcSmem {
+  uint64_t b_full[kTcStages], b_empty[kTcStages];
+  uint64_t a_full, a_empty;
+  uint64_t acc_full[2], acc_empty[2];
+  uint64_t drain;
+  uint32_t tmem_base;
+  int abort;
+  float nb[2][kTcBN];
+  float col[kTcEpiWarps][kTcBN];
+};
+
+__host__ __device__ constexpr size_t tc_smem_bytes(int KB) {
+  return 1024 /*alignment slack*/ + (size_t)KB * kTcAKBytes + (size_t)kTcStages * kTcBStage + sizeof(TcSmem);
+}
+
+template <int BF16>
+__global__ void __launch_bounds__(kTcThreads, 1)
+    hd_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
+                 const float* __restrict__ nA2, const int64_t* __restrict__ nA_dev, const float* __restrict__ nB2,
+                 const int64_t* __restrict__ nB_dev, int KB, float* __restrict__ rowmin,
+                 unsigned* __restrict__ colmin, int* __restrict__ status, uint64_t timeout_ns) {
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* base = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  uint8_t* sA = base;
+  uint8_t* sB = base + (size_t)KB * kTcAKBytes;
+  TcSmem& S = *reinterpret_cast<TcSmem*>(sB + (size_t)kTcStages * kTcBStage);
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t nA = *nA_dev, nB = *nB_dev;
+  const int RB = (int)((nA + kTcBM - 1) / kTcBM), CB = (int)((nB + kTcBN - 1) / kTcBN);
+  volatile int* abort = &S.abort;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < kTcStages; ++s) {
+      mbar_init(&S.b_full[s], 1);
+      mbar_init(&S.b_empty[s], 1);
+    }
+    mbar_init(&S.a_full, 1);
+    mbar_init(&S.a_empty, 1);
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(&S.acc_full[b], 1);
+      mbar_init(&S.acc_empty[b], kTcEpiWarps);
+    }
+    mbar_init(&S.drain, 1);
+    S.abort = 0;
+    fence_mbar_init();
+  }
+  if (warp == 1) {
+    tc_alloc(&S.tmem_base, 512);
+    tc_relinquish();
+  }
+  if (warp == 0 && lane == 0) {
+    tma_prefetch_desc(&tmA);
+    tma_prefetch_desc(&tmB);
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = S.tmem_base;
+
+  if (warp == 0) {
+    // ---------------- TMA producer ----------------
+    if (lane == 0) {
+      uint32_t st = 0, ph = 0, aph = 0;
+      uint32_t armed = 0, armed_ph = 0;  // stages with a load in flight, and its phase parity
+      bool ok = true;
+      for (int rb = blockIdx.x; rb < RB && ok; rb += gridDim.x) {
+        if (!mbar_wait_bounded(&S.a_empty, aph ^ 1, abort, timeout_ns)) { ok = false; break; }
+        aph ^= 1;
+        mbar_arrive_expect_tx(&S.a_full, (uint32_t)(KB * kTcAKBytes));
+        for (int kb = 0; kb < KB; ++kb) tma_load_2d(sA + kb * kTcAKBytes, &tmA, kb * kTcBK, rb * kTcBM, &S.a_full);
+        for (int cb = 0; cb < CB && ok; ++cb) {
+          for (int kb = 0; kb < KB; ++kb) {
+            if (!mbar_wait_bounded(&S.b_empty[st], ph ^ 1, abort, timeout_ns)) { ok = false; break; }
+            mbar_arrive_expect_tx(&S.b_full[st], (uint32_t)kTcBStage);
+            tma_load_2d(sB + st * kTcBStage, &tmB, kb * kTcBK, cb * kTcBN, &S.b_full[st]);
+            armed |= 1u << st;
+            armed_ph = (armed_ph & ~(1u << st)) | (ph << st);
+            if (++st == kTcStages) { st = 0; ph ^= 1; }
+          }
+        }
+      }
+      if (!ok) {
+        // error path: let copies already issued land before the CTA exits
+        for (int s2 = 0; s2 < kTcStages; ++s2) {
+          if (!(armed >> s2 & 1u)) continue;
+          const uint64_t t0 = global_timer_ns();
+          while (!mbar_try_wait(&S.b_full[s2], (armed_ph >> s2) & 1u) && global_timer_ns() - t0 < 2000000ull) {
+          }
+        }
+        const uint64_t t0 = global_timer_ns();
+        while (!mbar_try_wait(&S.a_full, aph ^ 1) && global_timer_ns() - t0 < 2000000ull) {
+        }
+      }
+    }
+  } else if (warp == 1) {
+    // ---------------- MMA issuer ----------------
+    if (lane == 0) {
+      constexpr uint32_t idesc = idesc_f16(BF16, kTcBM, kTcBN);
+      uint32_t st = 0, ph = 0, aph = 0, ab = 0, aph2 = 0;
+      bool ok = true;
+      for (int rb = blockIdx.x; rb < RB && ok; rb += gridDim.x) {
+        if (!mbar_wait_bounded(&S.a_full, aph, abort, timeout_ns)) { ok = false; break; }
+        aph ^= 1;
+        tc_fence_after();
+        for (int cb = 0; cb < CB && ok; ++cb) {
+          if (!mbar_wait_bounded(&S.acc_empty[ab], aph2 ^ 1, abort, timeout_ns)) { ok = false; break; }
+          tc_fence_after();
+          const uint32_t d_tmem = tmem + (uint32_t)(ab * kTcBN);
+          for (int kb = 0; kb < KB; ++kb) {
+            if (!mbar_wait_bounded(&S.b_full[st], ph, abort, timeout_ns)) { ok = false; break; }
+            tc_fence_after();
+            const uint32_t a_addr = smem_u32(sA + kb * kTcAKBytes);
+            const uint32_t b_addr = smem_u32(sB + st * kTcBStage);
+#pragma unroll
+            for (int k = 0; k < kTcBK / 16; ++k)
+              tc_mma_f16(d_tmem, smem_desc_sw128(a_addr + k * 32), smem_desc_sw128(b_addr + k * 32), idesc,
+                         (kb | k) != 0);
+            tc_commit(&S.b_empty[st]);
+            if (++st == kTcStages) { st = 0; ph ^= 1; }
+          }
+          if (!ok) break;
+          tc_commit(&S.acc_full[ab]);
+          ab ^= 1;
+          if (ab == 0) aph2 ^= 1;
+        }
+        tc_commit(&S.a_empty);
+      }
+      // make sure every MMA issued by this thread has finished before exit
+      tc_commit(&S.drain);
+      uint64_t t0 = global_timer_ns();
+      while (!mbar_try_wait(&S.drain, 0) && global_timer_ns() - t0 < 1000000000ull) {
+      }
+    }
+  } else {
+    // ---------------- epilogue (warps 2..5) ----------------
+    // Every epilogue warp runs the same tile loop and reaches every named
+    // barrier even after an abort (then it only skips the work), so the
+    // barriers cannot wait on a warp that left early.
+    const int ew = warp - 2;          // 0..3
+    const int q = warp & 3;           // TMEM lane quarter this warp may access
+    const int et = threadIdx.x - 64;  // 0..127
+    uint32_t ab = 0, aph2 = 0;
+    int tcount = 0;
+    bool ok = true;
+    for (int rb = blockIdx.x; rb < RB; rb += gridDim.x) {
+      const int64_t row = (int64_t)rb * kTcBM + q * 32 + lane;
+      const float na = nA2[row];
+      float rmin = __int_as_float(0x7f800000);
+      for (int cb = 0; cb < CB; ++cb, ++tcount) {
+        const int nbuf = tcount & 1;
+        S.nb[nbuf][et] = nB2[(int64_t)cb * kTcBN + et];
+        S.nb[nbuf][et + 128] = nB2[(int64_t)cb * kTcBN + et + 128];
+        named_bar_sync(1, 128);
+        int got = 0;
+        if (ok && lane == 0) got = mbar_wait_bounded(&S.acc_full[ab], aph2, abort, timeout_ns) ? 1 : 0;
+        got = __shfl_sync(0xffffffffu, got, 0);
+        ok = ok && got;
+        if (ok) {
+          tc_fence_after();
+          const uint32_t taddr = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(ab * kTcBN);
+          float v[32];
+#pragma unroll 1
+          for (int ch = 0; ch < kTcBN / 32; ++ch) {
+            __syncwarp();
+            tc_ld_32x32b_x32(taddr + ch * 32, v);
+            tc_wait_ld();
+            float cm[32];
+#pragma unroll
+            for (int c = 0; c < 32; ++c) {
+              float t = v[c] + S.nb[nbuf][ch * 32 + c];
+              rmin = fminf(rmin, t);
+              cm[c] = redux_min_f32(t + na);
+            }
+            if (lane == 0) {
+              float4* dst = reinterpret_cast<float4*>(&S.col[ew][ch * 32]);
+#pragma unroll
+              for (int c = 0; c < 8; ++c)
+                dst[c] = make_float4(cm[4 * c], cm[4 * c + 1], cm[4 * c + 2], cm[4 * c + 3]);
+            }
+          }
+          tc_fence_before();
+          __syncwarp();
+          if (lane == 0) mbar_arrive(&S.acc_empty[ab]);
+        }
+        ab ^= 1;
+        if (ab == 0) aph2 ^= 1;
+        named_bar_sync(1, 128);
+        if (ok) {
+          for (int c = et; c < kTcBN; c += 128) {
+            float m = fminf(fminf(S.col[0][c], S.col[1][c]), fminf(S.col[2][c], S.col[3][c]));
+            m = fmaxf(m, 0.f);
+            atomicMin(colmin + (int64_t)cb * kTcBN + c, __float_as_uint(m));
+          }
+        }
+      }
+      if (ok) rowmin[row] = rmin + na;
+    }
+  }
+
+  __syncthreads();
+  if (threadIdx.x == 0 && S.abort) atomicMax(status, (int)PROHD_ETIMEOUT);
+  if (warp == 1) {
+    __syncwarp();
+    tc_fence_after();
+    tc_dealloc(tmem, 512);
+  }
+}
+
+// =====================================================================
+// Margins, candidates, finalisation
+// =====================================================================
+
+struct HdScalars {
+  float maxabs;          // max |x - s|
+  float maxnormA, maxnormB;  // max ||h|| (scaled units)
+  float maxepsA, maxepsB;    // max eps (original units)
+  float lowp_max;        // max over rows/cols of the low-precision d^2 (scaled)
+  double LB[2];          // largest lower bound of a row / column NN distance
+  int64_t ncandA, ncandB;
+};
+
+// Margin of a low-precision squared minimum r2 (scaled units) of a row whose
+// own copy has norm na and the other set's copies norms <= nbmax:
+// |d2_lowp - ||h_a - h_b||^2| <= c1 (||h_a|| + ||h_b||)^2 with
+// c1 = (2 Dp + 2 D + 16) 2^-24 (products exact, FP32 accumulation of Dp terms
+// with truncation allowed, norms summed over D terms, two epilogue roundings,
+// times 2 for safety); and ||x_true - x_copy|| <= eps in original units.
+__device__ __forceinline__ void row_interval(float r2, float norm2_self, float maxnorm_other, float eps_self,
+                                             float maxeps_other, double c1, double inv, double& lo, double& hi) {
+  double ns = sqrt((double)norm2_self);
+  double dd = c1 * (ns + (double)maxnorm_other) * (ns + (double)maxnorm_other);
+  double r = (double)r2;
+  double e = (double)eps_self + (double)maxeps_other;
+  hi = (inv * sqrt(fmax(r, 0.0) + dd) + e) * (1.0 + 1e-6) + 1e-300;
+  lo = (inv * sqrt(fmax(r - dd, 0.0)) - e) * (1.0 - 1e-6);
+}
+
+__global__ void hd_bounds_kernel(const float* __restrict__ rowmin, const float* __restrict__ nA2,
+                                 const float* __restrict__ epsA, const int64_t* nA_dev,
+                                 const unsigned* __restrict__ colmin, const float* __restrict__ nB2,
+                                 const float* __restrict__ epsB, const int64_t* nB_dev, double c1,
+                                 HdScalars* __restrict__ sc) {
+  const int64_t nA = *nA_dev, nB = *nB_dev;
+  const double inv = ldexp(1.0, -scale_exponent(sc->maxabs));
+  double lbA = 0.0, lbB = 0.0;
+  float lp = 0.f;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < nA; i += stride) {
+    double lo, hi;
+    row_interval(rowmin[i], nA2[i], sc->maxnormB, epsA[i], sc->maxepsB, c1, inv, lo, hi);
+    lbA = fmax(lbA, lo);
+    lp = fmaxf(lp, rowmin[i]);
+  }
+  for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < nB; j += stride) {
+    double lo, hi;
+    float c = __uint_as_float(colmin[j]);
+    row_interval(c, nB2[j], sc->maxnormA, epsB[j], sc->maxepsA, c1, inv, lo, hi);
+    lbB = fmax(lbB, lo);
+    lp = fmaxf(lp, c);
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    lbA = fmax(lbA, __shfl_xor_sync(0xffffffffu, lbA, o));
+    lbB = fmax(lbB, __shfl_xor_sync(0xffffffffu, lbB, o));
+  }
+  lp = warp_max(lp);
+  if ((threadIdx.x & 31) == 0) {
+    atomic_max_nonneg(&sc->LB[0], lbA);
+    atomic_max_nonneg(&sc->LB[1], lbB);
+    atomic_max_nonneg(&sc->lowp_max, lp);
+  }
+}
+
+// Appends every row (column) whose upper bound reaches the largest lower
+// bound to the candidate list.
+__global__ void hd_flag_kernel(const float* __restrict__ rowmin, const float* __restrict__ nA2,
+                               const float* __restrict__ epsA, const int64_t* nA_dev,
+                               const unsigned* __restrict__ colmin, const float* __restrict__ nB2,
+                               const float* __restrict__ epsB, const int64_t* nB_dev, double c1,
+                               HdScalars* __restrict__ sc, int32_t* __restrict__ candA, int32_t* __restrict__ candB,
+                               int64_t* __restrict__ ncandA, int64_t* __restrict__ ncandB) {
+  const int64_t nA = *nA_dev, nB = *nB_dev;
+  const double inv = ldexp(1.0, -scale_exponent(sc->maxabs));
+  const double LBa = sc->LB[0], LBb = sc->LB[1];
+  const int lane = threadIdx.x & 31;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  const int64_t start = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const int64_t endA = (nA + 31) / 32 * 32, endB = (nB + 31) / 32 * 32;
+  for (int64_t i = start; i < endA; i += stride) {
+    bool f = false;
+    if (i < nA) {
+      double lo, hi;
+      row_interval(rowmin[i], nA2[i], sc->maxnormB, epsA[i], sc->maxepsB, c1, inv, lo, hi);
+      f = hi >= LBa;
+    }
+    unsigned m = __ballot_sync(0xffffffffu, f);
+    int64_t base = 0;
+    if (lane == 0 && m) base = (int64_t)atomicAdd(reinterpret_cast<unsigned long long*>(ncandA), (unsigned long long)__popc(m));
+    base = __shfl_sync(0xffffffffu, base, 0);
+    if (f) candA[base + __popc(m & ((1u << lane) - 1))] = (int32_t)i;
+  }
+  for (int64_t j = start; j < endB; j += stride) {
+    bool f = false;
+    if (j < nB) {
+      double lo, hi;
+      row_interval(__uint_as_float(colmin[j]), nB2[j], sc->maxnormA, epsB[j], sc->maxepsA, c1, inv, lo, hi);
+      f = hi >= LBb;
+    }
+    unsigned m = __ballot_sync(0xffffffffu, f);
+    int64_t base = 0;
+    if (lane == 0 && m) base = (int64_t)atomicAdd(reinterpret_cast<unsigned long long*>(ncandB), (unsigned long long)__popc(m));
+    base = __shfl_sync(0xffffffffu, base, 0);
+    if (f) candB[base + __popc(m & ((1u << lane) - 1))] = (int32_t)j;
+  }
+}
+
+// Block-wide argmax over (value, lowest id): key = float bits << 32 | ~id.
+__device__ unsigned long long block_max_u64(unsigned long long v, unsigned long long* sh) {
+  v = warp_max_u64(v);
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  if (l == 0) sh[w] = v;
+  __syncthreads();
+  if (w == 0) {
+    v = (l < (int)(blockDim.x >> 5)) ? sh[l] : 0ull;
+    v = warp_max_u64(v);
+    if (l == 0) sh[0] = v;
+  }
+  __syncthreads();
+  v = sh[0];
+  __syncthreads();
+  return v;
+}
+
+__device__ double dist64(const float* a, const float* b, int D) {
+  double s = 0.0;
+  for (int k = threadIdx.x & 31; k < D; k += 32) {
+    double d = (double)a[k] - (double)b[k];
+    s = fma(d, d, s);
+  }
+  s = warp_sum(s);
+  return sqrt(s);
+}
+
+// One block. best arrays hold packed (d^2, nn index) per entry; ids (or the
+// identity) give the row number of each entry.
+__global__ void hd_finalize_kernel(const float* __restrict__ A, const float* __restrict__ B, int D,
+                                   const unsigned long long* __restrict__ bestA, const int32_t* __restrict__ idsA,
+                                   const int64_t* cntA_dev, const unsigned long long* __restrict__ bestB,
+                                   const int32_t* __restrict__ idsB, const int64_t* cntB_dev,
+                                   const int32_t* __restrict__ mapA, const int32_t* __restrict__ mapB,
+                                   const HdScalars* sc, const int* status, prohd_hd_result* out) {
+  __shared__ unsigned long long sh[32];
+  __shared__ int64_t s_nn[2];
+  const int64_t cA = *cntA_dev, cB = *cntB_dev;
+  unsigned long long ka = 0, kb = 0;
+  for (int64_t c = threadIdx.x; c < cA; c += blockDim.x) {
+    uint32_t id = idsA ? (uint32_t)idsA[c] : (uint32_t)c;
+    unsigned long long k = ((bestA[c] >> 32) << 32) | (unsigned long long)(~id);
+    ka = k > ka ? k : ka;
+  }
+  for (int64_t c = threadIdx.x; c < cB; c += blockDim.x) {
+    uint32_t id = idsB ? (uint32_t)idsB[c] : (uint32_t)c;
+    unsigned long long k = ((bestB[c] >> 32) << 32) | (unsigned long long)(~id);
+    kb = k > kb ? k : kb;
+  }
+  ka = block_max_u64(ka, sh);
+  kb = block_max_u64(kb, sh);
+  const uint32_t ia = ~(uint32_t)(ka & 0xffffffffu), jb = ~(uint32_t)(kb & 0xffffffffu);
+  for (int64_t c = threadIdx.x; c < cA; c += blockDim.x) {
+    uint32_t id = idsA ? (uint32_t)idsA[c] : (uint32_t)c;
+    if (id == ia) s_nn[0] = packed_idx(bestA[c]);
+  }
+  for (int64_t c = threadIdx.x; c < cB; c += blockDim.x) {
+    uint32_t id = idsB ? (uint32_t)idsB[c] : (uint32_t)c;
+    if (id == jb) s_nn[1] = packed_idx(bestB[c]);
+  }
+  __syncthreads();
+  const int64_t ja = s_nn[0], ib = s_nn[1];
+  __shared__ double s_d[2];
+  if (threadIdx.x < 32) {
+    double d = dist64(A + (int64_t)ia * D, B + ja * D, D);
+    if (threadIdx.x == 0) s_d[0] = d;
+  } else if (threadIdx.x < 64) {
+    double d = dist64(B + (int64_t)jb * D, A + ib * D, D);
+    if (threadIdx.x == 32) s_d[1] = d;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    prohd_hd_result r;
+    r.h_ab = s_d[0];
+    r.h_ba = s_d[1];
+    r.ab_a = mapA ? mapA[ia] : ia;
+    r.ab_b = mapB ? mapB[ja] : ja;
+    r.ba_b = mapB ? mapB[jb] : jb;
+    r.ba_a = mapA ? mapA[ib] : ib;
+    r.dir = (r.h_ab >= r.h_ba) ? 0 : 1;
+    r.H = r.dir == 0 ? r.h_ab : r.h_ba;
+    r.wit_a = r.dir == 0 ? r.ab_a : r.ba_a;
+    r.wit_b = r.dir == 0 ? r.ab_b : r.ba_b;
+    r.status = *status;
+    if (sc) {
+      r.H_lowp = ldexp(sqrt(fmax((double)sc->lowp_max, 0.0)), -scale_exponent(sc->maxabs));
+      r.n_rescored_a = cA;
+      r.n_rescored_b = cB;
+    } else {
+      r.H_lowp = r.H;
+      r.n_rescored_a = 0;
+      r.n_rescored_b = 0;
+    }
+    *out = r;
+  }
+}
+
+// =====================================================================
+// Host orchestration
+// =====================================================================
+
+struct HdBufs {
+  int64_t nA_pad = 0, nB_pad = 0;
+  int Dp = 0;
+  // FP32 path and rescoring
+  unsigned long long* bestA = nullptr;
+  unsigned long long* bestB = nullptr;
+  // tensor path
+  void* At = nullptr;
+  void* Bt = nullptr;
+  float *nA2 = nullptr, *nB2 = nullptr, *epsA = nullptr, *epsB = nullptr, *shift = nullptr;
+  float* rowmin = nullptr;
+  unsigned* colmin = nullptr;
+  int32_t *candA = nullptr, *candB = nullptr;
+  HdScalars* sc = nullptr;
+};
+
+bool tc_supported_dim(int D) { return D >= 1 && D <= 256; }
+
+static void layout(Arena& ws, int64_t nA_max, int64_t nB_max, int D, int precision, HdBufs& b) {
+  b.bestA = ws.take<unsigned long long>((size_t)nA_max);
+  b.bestB = ws.take<unsigned long long>((size_t)nB_max);
+  if (precision != PROHD_FP32) {
+    b.nA_pad = round_up(nA_max, kTcBM);
+    b.nB_pad = round_up(nB_max, kTcBN);
+    b.Dp = (int)round_up(D, kTcBK);
+    b.At = ws.take<uint16_t>((size_t)b.nA_pad * b.Dp, 1024);
+    b.Bt = ws.take<uint16_t>((size_t)b.nB_pad * b.Dp, 1024);
+    b.nA2 = ws.take<float>((size_t)b.nA_pad);
+    b.nB2 = ws.take<float>((size_t)b.nB_pad);
+    b.epsA = ws.take<float>((size_t)b.nA_pad);
+    b.epsB = ws.take<float>((size_t)b.nB_pad);
+    b.rowmin = ws.take<float>((size_t)b.nA_pad);
+    b.colmin = ws.take<unsigned>((size_t)b.nB_pad);
+    b.candA = ws.take<int32_t>((size_t)nA_max);
+    b.candB = ws.take<int32_t>((size_t)nB_max);
+    b.shift = ws.take<float>((size_t)D);
+    b.sc = ws.take<HdScalars>(1);
+  }
+}
+
+void hd_core_layout(Arena& ws, int64_t nA_max, int64_t nB_max, int D, int precision) {
+  HdBufs b;
+  layout(ws, nA_max, nB_max, D, precision, b);
+}
+
+template <typename K>
+static int blocks_for(K kernel, int threads, size_t smem, int num_sms) {
+  int per_sm = 0;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, threads, smem);
+  return std::max(1, per_sm) * num_sms;
+}
+
+static cudaError_t launch_simt(bool row_list, bool want_row, bool want_col, const float* X, const int32_t* rowlist,
+                               const int64_t* nrows_dev, const float* Y, const int64_t* ncols_dev, int D,
+                               unsigned long long* rowbest, unsigned long long* colbest, int num_sms, cudaStream_t st) {
+  const int grid = num_sms;
+  count_launch();
+  if (!row_list && want_row && want_col)
+    simt_dist_kernel<false, true, true><<<grid, 256, 0, st>>>(X, rowlist, nrows_dev, Y, ncols_dev, D, rowbest, colbest);
+  else if (row_list && want_row && !want_col)
+    simt_dist_kernel<true, true, false><<<grid, 256, 0, st>>>(X, rowlist, nrows_dev, Y, ncols_dev, D, rowbest, colbest);
+  else
+    return cudaErrorInvalidValue;
+  return cudaGetLastError();
+}
+
+cudaError_t hd_core(prohd_ctx* ctx, const float* A, const int64_t* nA_dev, int64_t nA_max, const float* B,
+                    const int64_t* nB_dev, int64_t nB_max, int D, int precision, const int32_t* mapA,
+                    const int32_t* mapB, prohd_hd_result* out, int* status_dev, Arena& ws, int64_t timeout_ns,
+                    cudaStream_t st) {
+  HdBufs b;
+  layout(ws, nA_max, nB_max, D, precision, b);
+  if (ws.overflow()) return cudaErrorMemoryAllocation;
+  const int nsm = ctx->num_sms;
+  cudaError_t e;
+
+  if (precision == PROHD_FP32) {
+    count_launch();
+    fill_u64_kernel<<<nsm * 4, 256, 0, st>>>(b.bestA, nA_max, ~0ull);
+    count_launch();
+    fill_u64_kernel<<<nsm * 4, 256, 0, st>>>(b.bestB, nB_max, ~0ull);
+    {
+      PhaseTimer pt(ctx, PROHD_PH_HD_CONTRACT, st);
+      if ((e = launch_simt(false, true, true, A, nullptr, nA_dev, B, nB_dev, D, b.bestA, b.bestB, nsm, st))) return e;
+    }
+    PhaseTimer pt2(ctx, PROHD_PH_HD_RESCORE, st);
+    count_launch();
+    hd_finalize_kernel<<<1, 1024, 0, st>>>(A, B, D, b.bestA, nullptr, nA_dev, b.bestB, nullptr, nB_dev, mapA, mapB,
+                                           nullptr, status_dev, out);
+    return cudaGetLastError();
+  }
+
+  if (!tc_supported_dim(D)) return cudaErrorInvalidValue;
+  const int bf16 = precision == PROHD_BF16 ? 1 : 0;
+  const int KB = b.Dp / kTcBK;
+
+  PhaseTimer pt_prep(ctx, PROHD_PH_HD_PREP, st);
+  cudaMemsetAsync(b.sc, 0, sizeof(HdScalars), st);
+  count_launch();
+  hd_shift_kernel<<<1, 256, 0, st>>>(A, nA_dev, B, nB_dev, D, b.shift);
+  count_launch();
+  hd_maxabs_kernel<<<nsm * 4, 256, 0, st>>>(A, nA_dev, D, b.shift, &b.sc->maxabs, status_dev);
+  count_launch();
+  hd_maxabs_kernel<<<nsm * 4, 256, 0, st>>>(B, nB_dev, D, b.shift, &b.sc->maxabs, status_dev);
+  if (bf16) {
+    count_launch();
+    hd_prep_kernel<1><<<nsm * 4, 256, 0, st>>>(A, nA_dev, b.nA_pad, D, b.Dp, b.shift, &b.sc->maxabs, -2.f,
+                                              (__nv_bfloat16*)b.At, b.nA2, b.epsA, &b.sc->maxnormA, &b.sc->maxepsA);
+    count_launch();
+    hd_prep_kernel<1><<<nsm * 4, 256, 0, st>>>(B, nB_dev, b.nB_pad, D, b.Dp, b.shift, &b.sc->maxabs, 1.f,
+                                              (__nv_bfloat16*)b.Bt, b.nB2, b.epsB, &b.sc->maxnormB, &b.sc->maxepsB);
+  } else {
+    count_launch();
+    hd_prep_kernel<0><<<nsm * 4, 256, 0, st>>>(A, nA_dev, b.nA_pad, D, b.Dp, b.shift, &b.sc->maxabs, -2.f,
+                                              (__half*)b.At, b.nA2, b.epsA, &b.sc->maxnormA, &b.sc->maxepsA);
+    count_launch();
+    hd_prep_kernel<0><<<nsm * 4, 256, 0, st>>>(B, nB_dev, b.nB_pad, D, b.Dp, b.shift, &b.sc->maxabs, 1.f,
+                                              (__half*)b.Bt, b.nB2, b.epsB, &b.sc->maxnormB, &b.sc->maxepsB);
+  }
+  count_launch();
+  fill_u32_kernel<<<nsm * 2, 256, 0, st>>>(b.colmin, b.nB_pad, 0x7f800000u);
+  if ((e = cudaGetLastError())) return e;
+
+  CUtensorMap tmA, tmB;
+  const CUtensorMapDataType dt = bf16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT16;
+  if (!encode_2d(ctx, &tmA, dt, b.At, (uint64_t)b.Dp, (uint64_t)b.nA_pad, (uint64_t)b.Dp * 2, kTcBK, kTcBM,
+                 CU_TENSOR_MAP_SWIZZLE_128B) ||
+      !encode_2d(ctx, &tmB, dt, b.Bt, (uint64_t)b.Dp, (uint64_t)b.nB_pad, (uint64_t)b.Dp * 2, kTcBK, kTcBN,
+                 CU_TENSOR_MAP_SWIZZLE_128B))
+    return cudaErrorInvalidValue;
+  pt_prep.stop();
+  const size_t smem = tc_smem_bytes(KB);
+  const int grid = (int)std::min<int64_t>(nsm, b.nA_pad / kTcBM);
+  PhaseTimer pt_tc(ctx, PROHD_PH_HD_CONTRACT, st);
+  if (bf16) {
+    cudaFuncSetAttribute(hd_tc_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    count_launch();
+    hd_tc_kernel<1><<<grid, kTcThreads, smem, st>>>(tmA, tmB, b.nA2, nA_dev, b.nB2, nB_dev, KB, b.rowmin, b.colmin,
+                                                    status_dev, (uint64_t)timeout_ns);
+  } else {
+    cudaFuncSetAttribute(hd_tc_kernel<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    count_launch();
+    hd_tc_kernel<0><<<grid, kTcThreads, smem, st>>>(tmA, tmB, b.nA2, nA_dev, b.nB2, nB_dev, KB, b.rowmin, b.colmin,
+                                                    status_dev, (uint64_t)timeout_ns);
+  }
+  if ((e = cudaGetLastError())) return e;
+
+  pt_tc.stop();
+  PhaseTimer pt_rs(ctx, PROHD_PH_HD_RESCORE, st);
+  const double c1 = (2.0 * b.Dp + 2.0 * D + 16.0) * 5.9604644775390625e-8;
+  count_launch();
+  hd_bounds_kernel<<<nsm * 2, 256, 0, st>>>(b.rowmin, b.nA2, b.epsA, nA_dev, b.colmin, b.nB2, b.epsB, nB_dev, c1, b.sc);
+  count_launch();
+  hd_flag_kernel<<<nsm * 2, 256, 0, st>>>(b.rowmin, b.nA2, b.epsA, nA_dev, b.colmin, b.nB2, b.epsB, nB_dev, c1, b.sc,
+                                          b.candA, b.candB, &b.sc->ncandA, &b.sc->ncandB);
+  count_launch();
+  fill_u64_kernel<<<nsm * 4, 256, 0, st>>>(b.bestA, nA_max, ~0ull);
+  count_launch();
+  fill_u64_kernel<<<nsm * 4, 256, 0, st>>>(b.bestB, nB_max, ~0ull);
+  if ((e = cudaGetLastError())) return e;
+  // rescore candidate rows of A against all of B, candidate rows of B against all of A
+  if ((e = launch_simt(true, true, false, A, b.candA, &b.sc->ncandA, B, nB_dev, D, b.bestA, nullptr, nsm, st))) return e;
+  if ((e = launch_simt(true, true, false, B, b.candB, &b.sc->ncandB, A, nA_dev, D, b.bestB, nullptr, nsm, st))) return e;
+  count_launch();
+  hd_finalize_kernel<<<1, 1024, 0, st>>>(A, B, D, b.bestA, b.candA, &b.sc->ncandA, b.bestB, b.candB, &b.sc->ncandB,
+                                         mapA, mapB, b.sc, status_dev, out);
+  return cudaGetLastError();
+}
+
+}  // namespace prohd

@@ -1,0 +1,115 @@
+// Internal host-side interfaces between the ProHD translation units.
+#pragma once
+
+#include <cuda.h>
+#include <cuda_runtime.h>
+#include <stddef.h>
+#include <stdint.h>
+
+#include <atomic>
+#include <string>
+#include <vector>
+
+#include "../../include/prohd.h"
+
+struct prohd_ctx {
+  int device = 0;
+  int num_sms = 0;
+  int cc_major = 0, cc_minor = 0;
+  int smem_optin = 0;
+  void* encode_tiled = nullptr;  // cuTensorMapEncodeTiled from the driver
+  std::string err;
+  // profiler
+  bool profiling = false;
+  struct Pending {
+    int phase;
+    cudaEvent_t a, b;
+  };
+  std::vector<Pending> pending;
+  double ph_ms[PROHD_PH_COUNT] = {};
+  int64_t ph_count[PROHD_PH_COUNT] = {};
+};
+
+namespace prohd {
+
+extern std::atomic<uint64_t> g_launches;
+inline void count_launch(int n = 1) { g_launches.fetch_add((uint64_t)n, std::memory_order_relaxed); }
+
+// Records an event pair around a phase on `st` when the context profiles.
+struct PhaseTimer {
+  prohd_ctx* ctx;
+  int phase;
+  cudaStream_t st;
+  cudaEvent_t a = nullptr;
+  PhaseTimer(prohd_ctx* c, int ph, cudaStream_t s) : ctx(c), phase(ph), st(s) {
+    if (ctx && ctx->profiling && cudaEventCreate(&a) == cudaSuccess) cudaEventRecord(a, st);
+  }
+  void stop() {
+    if (!a) return;
+    cudaEvent_t b;
+    if (cudaEventCreate(&b) == cudaSuccess) {
+      cudaEventRecord(b, st);
+      ctx->pending.push_back({phase, a, b});
+    } else {
+      cudaEventDestroy(a);
+    }
+    a = nullptr;
+  }
+  ~PhaseTimer() { stop(); }
+};
+
+// Bump allocator over the caller's workspace. With base == nullptr it only
+// measures, so the size queries and the entry points share one layout.
+struct Arena {
+  char* base = nullptr;
+  size_t off = 0;
+  size_t cap = 0;
+  template <typename T>
+  T* take(size_t count, size_t align = 256) {
+    off = (off + align - 1) / align * align;
+    T* p = base ? reinterpret_cast<T*>(base + off) : nullptr;
+    off += count * sizeof(T);
+    return p;
+  }
+  bool overflow() const { return base && off > cap; }
+};
+
+inline int64_t round_up(int64_t x, int64_t m) { return (x + m - 1) / m * m; }
+inline int64_t ceil_div(int64_t x, int64_t m) { return (x + m - 1) / m; }
+
+constexpr int64_t kDefaultTimeoutNs = 4000000000LL;
+
+// ---- distance contraction (hd.cu) ----
+// Sizes may live on the device (n*_dev) with host upper bounds (n*_max); the
+// index maps translate row numbers to caller indices for the witnesses.
+void hd_core_layout(Arena& ws, int64_t nA_max, int64_t nB_max, int D, int precision);
+cudaError_t hd_core(prohd_ctx* ctx, const float* A, const int64_t* nA_dev, int64_t nA_max, const float* B,
+                    const int64_t* nB_dev, int64_t nB_max, int D, int precision, const int32_t* mapA,
+                    const int32_t* mapB, prohd_hd_result* out, int* status_dev, Arena& ws, int64_t timeout_ns,
+                    cudaStream_t st);
+bool tc_supported_dim(int D);
+
+// ---- selection (select.cu) ----
+void select_layout(Arena& ws, int64_t nA, int64_t nB, int D, int ndirs);
+cudaError_t select_run(prohd_ctx* ctx, const float* A, int64_t nA, const float* B, int64_t nB, int D,
+                       const double* dirs, int ndirs, const int64_t* kA, const int64_t* kB, int32_t* idxA,
+                       int64_t* nselA, int32_t* idxB, int64_t* nselB, int* status_dev, Arena& ws,
+                       cudaStream_t st);
+cudaError_t gather_rows(const float* X, int D, const int32_t* idx, const int64_t* n_dev, int64_t n_max, float* out,
+                        int num_sms, cudaStream_t st);
+
+// ---- directions (directions.cu) ----
+void directions_layout(Arena& ws, int64_t nA, int64_t nB, int D, int m);
+cudaError_t directions_run(prohd_ctx* ctx, const float* A, int64_t nA, const float* B, int64_t nB, int D, int m,
+                           int max_iters, double tol, uint64_t seed, double* dirs, double* eig, int* status_dev,
+                           Arena& ws, cudaStream_t st);
+
+// ---- small utilities (api.cu) ----
+cudaError_t set_i64(int64_t* p, int64_t v, cudaStream_t st);
+cudaError_t zero_i32(int* p, int n, cudaStream_t st);
+
+// Tensor-map encoder (driver entry point fetched through the runtime).
+bool encode_2d(prohd_ctx* ctx, CUtensorMap* map, CUtensorMapDataType dtype, const void* base, uint64_t inner,
+               uint64_t outer, uint64_t row_bytes, uint32_t box_inner, uint32_t box_outer, CUtensorMapSwizzle swz);
+
+}  // namespace prohd

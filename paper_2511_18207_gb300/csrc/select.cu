@@ -1,0 +1,679 @@
+// Extreme selection (Algorithms 1-2): for every direction u_d and each set,
+// keep the k smallest and the k largest projections x_i^T u_d, then take the
+// union over directions (Algorithm 3) as sorted unique indices.
+//
+// The order is the one of the FP64 projection summed sequentially over
+// k = 0..D-1 with separately rounded products and sums, ties broken by the
+// lower index at both ends. The GPU reaches it exactly without computing FP64
+// projections for every point:
+//  1. FP32 projections q (one HBM pass over the points, cp.async-staged tiles,
+//     all directions at once) and E = (D+8) 2^-24 max||x|| ||u|| (1.01)^2, a
+//     bound on |q - p64| for every point.
+//  2. The exact k-th smallest FP32 key T (4-pass radix select over
+//     order-preserving uint32 keys, all (set, direction, side) problems at once).
+//  3. q < T - 2E: certainly among the k smallest; q > T + 2E: certainly not;
+//     the band in between is ranked by FP64 projections recomputed exactly as
+//     the sequential definition (__dmul_rn / __dadd_rn), ties by index.
+//  The largest side is the same on reversed keys.
+#include <algorithm>
+
+#include "common.cuh"
+#include "internal.h"
+
+namespace prohd {
+
+constexpr int kProjRows = 256;   // rows per tile (2 per thread)
+constexpr int kProjThreads = 128;
+constexpr int kProjK = 32;       // dims per stage
+constexpr int kProjStride = 36;  // padded row stride (floats): conflict-free 16-B reads
+
+// ---------------------------------------------------------------- projection
+
+// q[d*n + i] = fl32(x_i . u_d); rownorm max into *maxnorm; non-finite check.
+// Requires D % 4 == 0 and a 16-byte aligned base (cp.async 16 B).
+template <int ND>
+__global__ void __launch_bounds__(kProjThreads)
+    proj_kernel(const float* __restrict__ X, int64_t n, int D, const double* __restrict__ dirs, int nd,
+                float* __restrict__ q, float* __restrict__ maxnorm, int* __restrict__ status) {
+  extern __shared__ __align__(16) float psm[];
+  const int Dq = (D + kProjK - 1) / kProjK * kProjK;
+  float* us = psm;                               // [ND][Dq]
+  float* xs = psm + (size_t)ND * Dq;             // [2][kProjRows][kProjStride]
+  for (int i = threadIdx.x; i < ND * Dq; i += blockDim.x) {
+    int d = i / Dq, k = i % Dq;
+    us[i] = (d < nd && k < D) ? (float)dirs[(size_t)d * D + k] : 0.f;
+  }
+  const int t = threadIdx.x;
+  const int64_t ntiles = (n + kProjRows - 1) / kProjRows;
+  const int nchunks = Dq / kProjK;
+  float wmax = 0.f;
+  bool bad = false;
+
+  // issue the cp.async copies of chunk c of tile `tile` into buffer `buf`
+  auto issue = [&](int64_t tile, int c, int buf) {
+    float* dst = xs + (size_t)buf * kProjRows * kProjStride;
+    // 256 rows x 8 float4 = 2048 copies, 16 per thread
+#pragma unroll
+    for (int e = 0; e < 16; ++e) {
+      int idx = t + e * kProjThreads;
+      int r = idx >> 3, f = idx & 7;
+      int64_t gr = tile * kProjRows + r;
+      int k = c * kProjK + f * 4;
+      float* sp = dst + r * kProjStride + f * 4;
+      uint32_t sa = smem_u32(sp);
+      if (gr < n && k < D) {
+        const float* gp = X + gr * D + k;
+        asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(sa), "l"(gp) : "memory");
+      } else {
+        *reinterpret_cast<float4*>(sp) = make_float4(0.f, 0.f, 0.f, 0.f);
+      }
+    }
+    asm volatile("cp.async.commit_group;" ::: "memory");
+  };
+
+  __syncthreads();
+  for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+    float acc0[ND], acc1[ND];
+#pragma unroll
+    for (int d = 0; d < ND; ++d) acc0[d] = acc1[d] = 0.f;
+    float n0 = 0.f, n1 = 0.f;
+    issue(tile, 0, 0);
+    for (int c = 0; c < nchunks; ++c) {
+      if (c + 1 < nchunks) {
+        issue(tile, c + 1, (c + 1) & 1);
+        asm volatile("cp.async.wait_group 1;" ::: "memory");
+      } else {
+        asm volatile("cp.async.wait_group 0;" ::: "memory");
+      }
+      __syncthreads();
+      const float* xb = xs + (size_t)(c & 1) * kProjRows * kProjStride;
+      const float* x0p = xb + t * kProjStride;
+      const float* x1p = xb + (t + kProjThreads) * kProjStride;
+#pragma unroll
+      for (int f = 0; f < kProjK / 4; ++f) {
+        float4 a = *reinterpret_cast<const float4*>(x0p + 4 * f);
+        float4 b = *reinterpret_cast<const float4*>(x1p + 4 * f);
+        n0 = fmaf(a.x, a.x, fmaf(a.y, a.y, fmaf(a.z, a.z, fmaf(a.w, a.w, n0))));
+        n1 = fmaf(b.x, b.x, fmaf(b.y, b.y, fmaf(b.z, b.z, fmaf(b.w, b.w, n1))));
+        const float* up = us + c * kProjK + 4 * f;
+#pragma unroll
+        for (int d = 0; d < ND; ++d) {
+          float4 u = *reinterpret_cast<const float4*>(up + (size_t)d * Dq);
+          acc0[d] = fmaf(a.w, u.w, fmaf(a.z, u.z, fmaf(a.y, u.y, fmaf(a.x, u.x, acc0[d]))));
+          acc1[d] = fmaf(b.w, u.w, fmaf(b.z, u.z, fmaf(b.y, u.y, fmaf(b.x, u.x, acc1[d]))));
+        }
+      }
+      __syncthreads();
+    }
+    const int64_t r0 = tile * kProjRows + t, r1 = r0 + kProjThreads;
+    if (r0 < n) {
+#pragma unroll
+      for (int d = 0; d < ND; ++d)
+        if (d < nd) q[(size_t)d * n + r0] = acc0[d];
+      bad |= !isfinite(n0);
+      wmax = fmaxf(wmax, sqrtf(n0));
+    }
+    if (r1 < n) {
+#pragma unroll
+      for (int d = 0; d < ND; ++d)
+        if (d < nd) q[(size_t)d * n + r1] = acc1[d];
+      bad |= !isfinite(n1);
+      wmax = fmaxf(wmax, sqrtf(n1));
+    }
+  }
+  wmax = warp_max(wmax);
+  if ((threadIdx.x & 31) == 0) atomic_max_nonneg(maxnorm, wmax);
+  if (__any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0) atomicMax(status, (int)PROHD_ENONFINITE);
+}
+
+// Fallback for D % 4 != 0 or unaligned bases: warp per row, lanes over dims.
+__global__ void proj_simple_kernel(const float* __restrict__ X, int64_t n, int D, const double* __restrict__ dirs,
+                                   int nd, float* __restrict__ q, float* __restrict__ maxnorm, int* __restrict__ status) {
+  const int lane = threadIdx.x & 31;
+  const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  float wmax = 0.f;
+  bool bad = false;
+  for (int64_t r = warp; r < n; r += nw) {
+    const float* x = X + r * D;
+    float nn = 0.f;
+    for (int k = lane; k < D; k += 32) nn = fmaf(x[k], x[k], nn);
+    nn = warp_sum(nn);
+    for (int d = 0; d < nd; ++d) {
+      float s = 0.f;
+      for (int k = lane; k < D; k += 32) s = fmaf(x[k], (float)dirs[(size_t)d * D + k], s);
+      s = warp_sum(s);
+      if (lane == 0) q[(size_t)d * n + r] = s;
+    }
+    bad |= !isfinite(nn);
+    wmax = fmaxf(wmax, sqrtf(nn));
+  }
+  wmax = warp_max(wmax);
+  if (lane == 0) atomic_max_nonneg(maxnorm, wmax);
+  if (__any_sync(0xffffffffu, bad) && lane == 0) atomicMax(status, (int)PROHD_ENONFINITE);
+}
+
+// ---------------------------------------------------------------- radix select
+
+// Per problem p = set * nd + d and side s (0 = smallest, 1 = largest):
+struct SelProb {
+  uint32_t prefix[2];   // key bits fixed so far
+  int64_t rank[2];      // remaining 0-based rank inside the current prefix
+  int64_t k;            // k of this (set, direction)
+  double E;             // |q - p64| bound for this (set, direction)
+  int64_t cin[2];       // points certainly selected on each side
+  int64_t nband[2];     // band sizes
+};
+
+constexpr int kMaxDirs = 64;
+struct KList {
+  int64_t k[2 * kMaxDirs];  // k of (set, direction) p = set * nd + d, passed by value
+};
+
+__global__ void sel_init_kernel(SelProb* __restrict__ P, int nd, const KList kl, int64_t nA, int64_t nB, int D,
+                                const double* __restrict__ dirs, const float* __restrict__ maxnorm) {
+  const int p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= 2 * nd) return;
+  const int set = p / nd, d = p % nd;
+  const int64_t n = set ? nB : nA;
+  int64_t k = kl.k[p];
+  k = k < 1 ? 1 : (k > n ? n : k);
+  double un = 0.0;
+  for (int j = 0; j < D; ++j) un += dirs[(size_t)d * D + j] * dirs[(size_t)d * D + j];
+  un = sqrt(un);
+  SelProb s;
+  s.prefix[0] = s.prefix[1] = 0;
+  s.rank[0] = k - 1;
+  s.rank[1] = n - k;
+  s.k = k;
+  s.E = ((double)D + 8.0) * 5.9604644775390625e-8 * 1.0201 * (double)maxnorm[set] * un + 1e-300;
+  s.cin[0] = s.cin[1] = 0;
+  s.nband[0] = s.nband[1] = 0;
+  P[p] = s;
+}
+
+// grid (chunks, 2*nd). hist: [2*nd][2][256]
+__global__ void radix_hist_kernel(const float* __restrict__ qA, int64_t nA, const float* __restrict__ qB, int64_t nB,
+                                  int nd, const SelProb* __restrict__ P, int pass, unsigned* __restrict__ hist) {
+  __shared__ unsigned h[2][256];
+  const int p = blockIdx.y;
+  const int set = p / nd, d = p % nd;
+  const int64_t n = set ? nB : nA;
+  const float* q = (set ? qB : qA) + (size_t)d * n;
+  for (int i = threadIdx.x; i < 512; i += blockDim.x) (&h[0][0])[i] = 0;
+  __syncthreads();
+  const int shift = 24 - 8 * pass;
+  const uint32_t himask = pass == 0 ? 0u : (0xffffffffu << (32 - 8 * pass));
+  const uint32_t p0 = P[p].prefix[0], p1 = P[p].prefix[1];
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    uint32_t key = f32_key(q[i]);
+    uint32_t bin = (key >> shift) & 255u;
+    if (((key ^ p0) & himask) == 0) atomicAdd(&h[0][bin], 1u);
+    if (((key ^ p1) & himask) == 0) atomicAdd(&h[1][bin], 1u);
+  }
+  __syncthreads();
+  unsigned* g = hist + (size_t)p * 512;
+  for (int i = threadIdx.x; i < 512; i += blockDim.x) {
+    unsigned v = (&h[0][0])[i];
+    if (v) atomicAdd(g + i, v);
+  }
+}
+
+// One warp per (problem, side): pick the bin holding the target rank.
+__global__ void radix_pick_kernel(SelProb* __restrict__ P, int nprob, int pass, unsigned* __restrict__ hist) {
+  const int w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+  if (w >= nprob * 2) return;
+  const int p = w >> 1, side = w & 1;
+  unsigned* h = hist + (size_t)p * 512 + side * 256;
+  int64_t r = P[p].rank[side];
+  // each lane owns 8 consecutive bins
+  unsigned c[8];
+  unsigned tot = 0;
+#pragma unroll
+  for (int j = 0; j < 8; ++j) {
+    c[j] = h[lane * 8 + j];
+    tot += c[j];
+  }
+  unsigned incl = tot;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    unsigned v = __shfl_up_sync(0xffffffffu, incl, o);
+    if (lane >= o) incl += v;
+  }
+  const unsigned excl = incl - tot;
+  const bool mine = (int64_t)excl <= r && r < (int64_t)incl;
+  const unsigned who = __ballot_sync(0xffffffffu, mine);
+  if (who) {
+    const int src = __ffs(who) - 1;
+    if (lane == src) {
+      int64_t rr = r - (int64_t)excl;
+      int bin = 0;
+#pragma unroll
+      for (int j = 0; j < 8; ++j) {
+        if (rr < (int64_t)c[j]) { bin = lane * 8 + j; break; }
+        rr -= c[j];
+      }
+      const int shift = 24 - 8 * pass;
+      P[p].prefix[side] |= (uint32_t)bin << shift;
+      P[p].rank[side] = rr;
+    }
+  }
+  __syncwarp();
+#pragma unroll
+  for (int j = 0; j < 8; ++j) h[lane * 8 + j] = 0;
+}
+
+// ---------------------------------------------------------------- band pass
+
+// Marks certain members, counts them, and lists band members per side.
+// band lists: [2*nd][2][cap] int32
+__global__ void band_kernel(const float* __restrict__ qA, int64_t nA, const float* __restrict__ qB, int64_t nB,
+                            int nd, SelProb* __restrict__ P, uint8_t* __restrict__ maskA, uint8_t* __restrict__ maskB,
+                            int32_t* __restrict__ band, int64_t cap) {
+  const int p = blockIdx.y;
+  const int set = p / nd, d = p % nd;
+  const int64_t n = set ? nB : nA;
+  const float* q = (set ? qB : qA) + (size_t)d * n;
+  uint8_t* mask = set ? maskB : maskA;
+  const double E2 = 2.0 * P[p].E;
+  const double Tlo = (double)key_f32(P[p].prefix[0]), Thi = (double)key_f32(P[p].prefix[1]);
+  const double lo_in = Tlo - E2, lo_band = Tlo + E2, hi_in = Thi + E2, hi_band = Thi - E2;
+  int32_t* b0 = band + ((size_t)p * 2 + 0) * cap;
+  int32_t* b1 = band + ((size_t)p * 2 + 1) * cap;
+  const int lane = threadIdx.x & 31;
+  unsigned long long c0 = 0, c1 = 0;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  const int64_t end = (n + 31) / 32 * 32;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < end; i += stride) {
+    bool in0 = false, bd0 = false, in1 = false, bd1 = false;
+    if (i < n) {
+      const double v = (double)q[i];
+      in0 = v < lo_in;
+      bd0 = !in0 && v <= lo_band;
+      in1 = v > hi_in;
+      bd1 = !in1 && v >= hi_band;
+      if (in0 || in1) mask[i] = 1;
+    }
+    c0 += in0;
+    c1 += in1;
+    unsigned m0 = __ballot_sync(0xffffffffu, bd0), m1 = __ballot_sync(0xffffffffu, bd1);
+    unsigned long long base0 = 0, base1 = 0;
+    if (lane == 0 && m0) base0 = atomicAdd(reinterpret_cast<unsigned long long*>(&P[p].nband[0]), (unsigned long long)__popc(m0));
+    if (lane == 0 && m1) base1 = atomicAdd(reinterpret_cast<unsigned long long*>(&P[p].nband[1]), (unsigned long long)__popc(m1));
+    base0 = __shfl_sync(0xffffffffu, base0, 0);
+    base1 = __shfl_sync(0xffffffffu, base1, 0);
+    const unsigned below = (1u << lane) - 1;
+    if (bd0) b0[base0 + __popc(m0 & below)] = (int32_t)i;
+    if (bd1) b1[base1 + __popc(m1 & below)] = (int32_t)i;
+  }
+  c0 = warp_sum(c0);
+  c1 = warp_sum(c1);
+  if (lane == 0) {
+    if (c0) atomicAdd(reinterpret_cast<unsigned long long*>(&P[p].cin[0]), c0);
+    if (c1) atomicAdd(reinterpret_cast<unsigned long long*>(&P[p].cin[1]), c1);
+  }
+}
+
+// FP64 projection exactly as the sequential definition.
+__device__ __forceinline__ double proj64(const float* __restrict__ x, const double* __restrict__ u, int D) {
+  double s = 0.0;
+  for (int k = 0; k < D; ++k) s = __dadd_rn(s, __dmul_rn((double)x[k], u[k]));
+  return s;
+}
+
+constexpr int kBandSmem = 2048;
+
+// One block per (problem, side): rank band members by (FP64 key, index) and
+// mark the r = k - cin smallest. Small bands are ranked in shared memory by
+// counting; large bands use a radix select over the 96-bit (key, index).
+__global__ void __launch_bounds__(512)
+    band_resolve_kernel(const float* __restrict__ A, int64_t nA, const float* __restrict__ B, int64_t nB, int D,
+                        const double* __restrict__ dirs, int nd, const SelProb* __restrict__ P,
+                        const int32_t* __restrict__ band, uint64_t* __restrict__ bandkey, int64_t cap,
+                        uint8_t* __restrict__ maskA, uint8_t* __restrict__ maskB) {
+  __shared__ uint64_t sk[kBandSmem];
+  __shared__ int32_t si[kBandSmem];
+  __shared__ unsigned hist[256];
+  __shared__ int64_t s_rank;
+  __shared__ uint64_t s_prefix;
+  const int p = blockIdx.x >> 1, side = blockIdx.x & 1;
+  const int set = p / nd, d = p % nd;
+  const float* X = set ? B : A;
+  uint8_t* mask = set ? maskB : maskA;
+  const double* u = dirs + (size_t)d * D;
+  const int64_t b = P[p].nband[side];
+  const int64_t r = P[p].k - P[p].cin[side];
+  if (b == 0 || r <= 0) return;
+  const int32_t* lst = band + ((size_t)p * 2 + side) * cap;
+  uint64_t* keys = bandkey + ((size_t)p * 2 + side) * cap;
+
+  auto key_of = [&](int32_t idx) -> uint64_t {
+    uint64_t k = f64_key(proj64(X + (int64_t)idx * D, u, D));
+    return side ? ~k : k;
+  };
+
+  if (b <= kBandSmem) {
+    for (int64_t i = threadIdx.x; i < b; i += blockDim.x) {
+      si[i] = lst[i];
+      sk[i] = key_of(lst[i]);
+    }
+    __syncthreads();
+    for (int64_t i = threadIdx.x; i < b; i += blockDim.x) {
+      const uint64_t ki = sk[i];
+      const int32_t ii = si[i];
+      int64_t rank = 0;
+      for (int64_t j = 0; j < b; ++j) rank += (sk[j] < ki) || (sk[j] == ki && si[j] < ii);
+      if (rank < r) mask[ii] = 1;
+    }
+    return;
+  }
+
+  // large band: keys to global, then radix select of the r-th smallest (key, idx)
+  for (int64_t i = threadIdx.x; i < b; i += blockDim.x) keys[i] = key_of(lst[i]);
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    s_rank = r - 1;
+    s_prefix = 0;
+  }
+  __syncthreads();
+  // 8 passes over the 64-bit key
+  for (int pass = 0; pass < 8; ++pass) {
+    const int shift = 56 - 8 * pass;
+    const uint64_t him = pass == 0 ? 0ull : (~0ull << (64 - 8 * pass));
+    for (int i = threadIdx.x; i < 256; i += blockDim.x) hist[i] = 0;
+    __syncthreads();
+    const uint64_t pre = s_prefix;
+    for (int64_t i = threadIdx.x; i < b; i += blockDim.x) {
+      uint64_t k = keys[i];
+      if (((k ^ pre) & him) == 0) atomicAdd(&hist[(k >> shift) & 255], 1u);
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      int64_t rr = s_rank;
+      int bin = 0;
+      for (; bin < 256; ++bin) {
+        if (rr < (int64_t)hist[bin]) break;
+        rr -= hist[bin];
+      }
+      s_prefix = pre | ((uint64_t)bin << shift);
+      s_rank = rr;
+    }
+    __syncthreads();
+  }
+  const uint64_t kstar = s_prefix;
+  // among key == kstar, the (s_rank)-th smallest index: 4 passes over idx
+  __shared__ uint32_t s_ipre;
+  if (threadIdx.x == 0) s_ipre = 0;
+  __syncthreads();
+  for (int pass = 0; pass < 4; ++pass) {
+    const int shift = 24 - 8 * pass;
+    const uint32_t him = pass == 0 ? 0u : (0xffffffffu << (32 - 8 * pass));
+    for (int i = threadIdx.x; i < 256; i += blockDim.x) hist[i] = 0;
+    __syncthreads();
+    const uint32_t pre = s_ipre;
+    for (int64_t i = threadIdx.x; i < b; i += blockDim.x) {
+      if (keys[i] != kstar) continue;
+      uint32_t id = (uint32_t)lst[i];
+      if (((id ^ pre) & him) == 0) atomicAdd(&hist[(id >> shift) & 255], 1u);
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      int64_t rr = s_rank;
+      int bin = 0;
+      for (; bin < 256; ++bin) {
+        if (rr < (int64_t)hist[bin]) break;
+        rr -= hist[bin];
+      }
+      s_ipre = pre | ((uint32_t)bin << shift);
+      s_rank = rr;
+    }
+    __syncthreads();
+  }
+  const uint32_t istar = s_ipre;
+  for (int64_t i = threadIdx.x; i < b; i += blockDim.x) {
+    const uint64_t k = keys[i];
+    const uint32_t id = (uint32_t)lst[i];
+    if (k < kstar || (k == kstar && id <= istar)) mask[id] = 1;
+  }
+}
+
+// ---------------------------------------------------------------- compaction
+
+constexpr int kCompactItems = 4096;  // mask bytes per block
+
+__global__ void compact_count_kernel(const uint8_t* __restrict__ mask, int64_t n, unsigned* __restrict__ counts) {
+  const int64_t base = (int64_t)blockIdx.x * kCompactItems;
+  unsigned c = 0;
+  for (int i = threadIdx.x; i < kCompactItems; i += blockDim.x) {
+    int64_t g = base + i;
+    c += (g < n && mask[g]) ? 1u : 0u;
+  }
+  c = warp_sum(c);
+  __shared__ unsigned s[32];
+  if ((threadIdx.x & 31) == 0) s[threadIdx.x >> 5] = c;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    unsigned t = 0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += s[w];
+    counts[blockIdx.x] = t;
+  }
+}
+
+// single block: exclusive scan of counts -> offsets; total -> *nsel
+__global__ void compact_scan_kernel(const unsigned* __restrict__ counts, int64_t nblocks, int64_t* __restrict__ offsets,
+                                    int64_t* __restrict__ nsel) {
+  __shared__ int64_t carry;
+  __shared__ int64_t wsum[32];
+  if (threadIdx.x == 0) carry = 0;
+  __syncthreads();
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  for (int64_t base = 0; base < nblocks; base += blockDim.x) {
+    int64_t i = base + threadIdx.x;
+    int64_t v = i < nblocks ? (int64_t)counts[i] : 0;
+    int64_t incl = v;
+    for (int o = 1; o < 32; o <<= 1) {
+      int64_t t = __shfl_up_sync(0xffffffffu, incl, o);
+      if (lane >= o) incl += t;
+    }
+    if (lane == 31) wsum[w] = incl;
+    __syncthreads();
+    if (w == 0) {
+      int64_t s = lane < nw ? wsum[lane] : 0;
+      int64_t si = s;
+      for (int o = 1; o < 32; o <<= 1) {
+        int64_t t = __shfl_up_sync(0xffffffffu, si, o);
+        if (lane >= o) si += t;
+      }
+      if (lane < nw) wsum[lane] = si - s;
+    }
+    __syncthreads();
+    if (i < nblocks) offsets[i] = carry + wsum[w] + incl - v;
+    __syncthreads();
+    if (threadIdx.x == blockDim.x - 1) carry += wsum[w] + incl;
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) *nsel = carry;
+}
+
+__global__ void compact_write_kernel(const uint8_t* __restrict__ mask, int64_t n, const int64_t* __restrict__ offsets,
+                                     int32_t* __restrict__ idx) {
+  // blockDim = 1024; each thread handles 4 consecutive bytes
+  __shared__ unsigned wsum[32];
+  const int64_t base = (int64_t)blockIdx.x * kCompactItems + threadIdx.x * 4;
+  unsigned f[4], c = 0;
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    int64_t g = base + j;
+    f[j] = (g < n && mask[g]) ? 1u : 0u;
+    c += f[j];
+  }
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  unsigned incl = c;
+  for (int o = 1; o < 32; o <<= 1) {
+    unsigned t = __shfl_up_sync(0xffffffffu, incl, o);
+    if (lane >= o) incl += t;
+  }
+  if (lane == 31) wsum[w] = incl;
+  __syncthreads();
+  if (w == 0) {
+    unsigned s = wsum[lane], si = s;
+    for (int o = 1; o < 32; o <<= 1) {
+      unsigned t = __shfl_up_sync(0xffffffffu, si, o);
+      if (lane >= o) si += t;
+    }
+    wsum[lane] = si - s;
+  }
+  __syncthreads();
+  int64_t pos = offsets[blockIdx.x] + wsum[w] + incl - c;
+#pragma unroll
+  for (int j = 0; j < 4; ++j)
+    if (f[j]) idx[pos++] = (int32_t)(base + j);
+}
+
+__global__ void gather_rows_kernel(const float* __restrict__ X, int D, const int32_t* __restrict__ idx,
+                                   const int64_t* __restrict__ n_dev, float* __restrict__ out) {
+  const int64_t n = *n_dev;
+  const int lane = threadIdx.x & 31;
+  const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t r = warp; r < n; r += nw) {
+    const float* src = X + (int64_t)idx[r] * D;
+    float* dst = out + r * D;
+    for (int k = lane; k < D; k += 32) dst[k] = src[k];
+  }
+}
+
+// ---------------------------------------------------------------- host side
+
+struct SelBufs {
+  float *qA = nullptr, *qB = nullptr;
+  float* maxnorm = nullptr;  // [2]
+  SelProb* P = nullptr;
+  unsigned* hist = nullptr;
+  int32_t* band = nullptr;
+  uint64_t* bandkey = nullptr;
+  uint8_t *maskA = nullptr, *maskB = nullptr;
+  unsigned* counts = nullptr;
+  int64_t* offsets = nullptr;
+  int64_t cap = 0;
+};
+
+static void sel_layout(Arena& ws, int64_t nA, int64_t nB, int D, int nd, SelBufs& b) {
+  (void)D;
+  b.cap = std::max(nA, nB);
+  b.qA = ws.take<float>((size_t)nd * nA);
+  b.qB = ws.take<float>((size_t)nd * nB);
+  b.maxnorm = ws.take<float>(2);
+  b.P = ws.take<SelProb>((size_t)2 * nd);
+  b.hist = ws.take<unsigned>((size_t)2 * nd * 512);
+  b.band = ws.take<int32_t>((size_t)2 * nd * 2 * b.cap);
+  b.bandkey = ws.take<uint64_t>((size_t)2 * nd * 2 * b.cap);
+  b.maskA = ws.take<uint8_t>((size_t)nA);
+  b.maskB = ws.take<uint8_t>((size_t)nB);
+  const int64_t nblk = ceil_div(std::max(nA, nB), kCompactItems);
+  b.counts = ws.take<unsigned>((size_t)nblk);
+  b.offsets = ws.take<int64_t>((size_t)nblk);
+}
+
+void select_layout(Arena& ws, int64_t nA, int64_t nB, int D, int ndirs) {
+  SelBufs b;
+  sel_layout(ws, nA, nB, D, ndirs, b);
+}
+
+static cudaError_t launch_proj(const float* X, int64_t n, int D, const double* dirs, int nd, float* q, float* maxnorm,
+                               int* status, int num_sms, cudaStream_t st) {
+  const bool fast = (D % 4 == 0) && ((reinterpret_cast<uintptr_t>(X) & 15) == 0) && nd <= 32;
+  if (!fast) {
+    count_launch();
+    proj_simple_kernel<<<num_sms * 8, 256, 0, st>>>(X, n, D, dirs, nd, q, maxnorm, status);
+    return cudaGetLastError();
+  }
+  const int Dq = (int)round_up(D, kProjK);
+  auto go = [&](auto kern, int ND) -> cudaError_t {
+    size_t smem = (size_t)ND * Dq * 4 + (size_t)2 * kProjRows * kProjStride * 4;
+    if (smem > 227 * 1024) return cudaErrorInvalidValue;
+    cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    int per_sm = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kProjThreads, smem);
+    int64_t ntiles = ceil_div(n, kProjRows);
+    int grid = (int)std::min<int64_t>(ntiles, (int64_t)std::max(1, per_sm) * num_sms);
+    count_launch();
+    kern<<<grid, kProjThreads, smem, st>>>(X, n, D, dirs, nd, q, maxnorm, status);
+    return cudaGetLastError();
+  };
+  if (nd <= 3) return go(proj_kernel<3>, 3);
+  if (nd <= 5) return go(proj_kernel<5>, 5);
+  if (nd <= 9) return go(proj_kernel<9>, 9);
+  if (nd <= 13) return go(proj_kernel<13>, 13);
+  if (nd <= 17) return go(proj_kernel<17>, 17);
+  if (nd <= 24) return go(proj_kernel<24>, 24);
+  return go(proj_kernel<32>, 32);
+}
+
+static cudaError_t mark_to_indices(const uint8_t* mask, int64_t n, int32_t* idx, int64_t* nsel, unsigned* counts,
+                                   int64_t* offsets, cudaStream_t st) {
+  const int64_t nblk = ceil_div(n, kCompactItems);
+  count_launch();
+  compact_count_kernel<<<(unsigned)nblk, 256, 0, st>>>(mask, n, counts);
+  count_launch();
+  compact_scan_kernel<<<1, 1024, 0, st>>>(counts, nblk, offsets, nsel);
+  count_launch();
+  compact_write_kernel<<<(unsigned)nblk, 1024, 0, st>>>(mask, n, offsets, idx);
+  return cudaGetLastError();
+}
+
+cudaError_t select_run(prohd_ctx* ctx, const float* A, int64_t nA, const float* B, int64_t nB, int D,
+                       const double* dirs, int nd, const int64_t* kA, const int64_t* kB, int32_t* idxA,
+                       int64_t* nselA, int32_t* idxB, int64_t* nselB, int* status_dev, Arena& ws, cudaStream_t st) {
+  SelBufs b;
+  sel_layout(ws, nA, nB, D, nd, b);
+  if (ws.overflow()) return cudaErrorMemoryAllocation;
+  const int nsm = ctx->num_sms;
+  cudaError_t e;
+  if (nd > kMaxDirs) return cudaErrorInvalidValue;
+  KList kl;
+  for (int d = 0; d < nd; ++d) {
+    kl.k[d] = kA[d];
+    kl.k[nd + d] = kB[d];
+  }
+  cudaMemsetAsync(b.maxnorm, 0, 2 * sizeof(float), st);
+  cudaMemsetAsync(b.hist, 0, sizeof(unsigned) * 2 * nd * 512, st);
+  cudaMemsetAsync(b.maskA, 0, (size_t)nA, st);
+  cudaMemsetAsync(b.maskB, 0, (size_t)nB, st);
+  {
+    PhaseTimer pt(ctx, PROHD_PH_PROJECT, st);
+    if ((e = launch_proj(A, nA, D, dirs, nd, b.qA, b.maxnorm + 0, status_dev, nsm, st))) return e;
+    if ((e = launch_proj(B, nB, D, dirs, nd, b.qB, b.maxnorm + 1, status_dev, nsm, st))) return e;
+  }
+  PhaseTimer pt_sel(ctx, PROHD_PH_SELECT, st);
+  count_launch();
+  sel_init_kernel<<<1, 128, 0, st>>>(b.P, nd, kl, nA, nB, D, dirs, b.maxnorm);
+  const int64_t nmax = std::max(nA, nB);
+  const unsigned chunks = (unsigned)std::max<int64_t>(1, std::min<int64_t>(ceil_div(nmax, 256 * 16), (nsm * 8 + 2 * nd - 1) / (2 * nd)));
+  dim3 g(chunks, 2 * nd);
+  for (int pass = 0; pass < 4; ++pass) {
+    count_launch();
+    radix_hist_kernel<<<g, 256, 0, st>>>(b.qA, nA, b.qB, nB, nd, b.P, pass, b.hist);
+    count_launch();
+    radix_pick_kernel<<<(4 * nd * 32 + 127) / 128, 128, 0, st>>>(b.P, 2 * nd, pass, b.hist);
+  }
+  count_launch();
+  band_kernel<<<g, 256, 0, st>>>(b.qA, nA, b.qB, nB, nd, b.P, b.maskA, b.maskB, b.band, b.cap);
+  count_launch();
+  band_resolve_kernel<<<4 * nd, 512, 0, st>>>(A, nA, B, nB, D, dirs, nd, b.P, b.band, b.bandkey, b.cap, b.maskA,
+                                              b.maskB);
+  if ((e = cudaGetLastError())) return e;
+  if ((e = mark_to_indices(b.maskA, nA, idxA, nselA, b.counts, b.offsets, st))) return e;
+  if ((e = mark_to_indices(b.maskB, nB, idxB, nselB, b.counts, b.offsets, st))) return e;
+  return cudaGetLastError();
+}
+
+cudaError_t gather_rows(const float* X, int D, const int32_t* idx, const int64_t* n_dev, int64_t n_max, float* out,
+                        int num_sms, cudaStream_t st) {
+  (void)n_max;
+  count_launch();
+  gather_rows_kernel<<<num_sms * 8, 256, 0, st>>>(X, D, idx, n_dev, out);
+  return cudaGetLastError();
+}
+
+}  // namespace prohd

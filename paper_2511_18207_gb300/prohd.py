@@ -1,0 +1,367 @@
+"""Thin Python binding of the ProHD C ABI (``include/prohd.h``).
+
+Argument marshalling only: every step of the computation runs in the CUDA
+library ``_lib/libprohd.so``. PyTorch provides device memory (inputs,
+workspaces, result buffers) and streams. There is no fallback: if the library
+is missing or the GPU is not an sm_103 device, calls raise.
+
+Low-level calls mirror the C names (``hausdorff_exact``, ``prohd_directions``,
+``prohd_select``, ``prohd_estimate``, ``prohd_estimate_host``) and enqueue on
+the current torch stream without synchronising; the ``*_sync`` helpers wait and
+decode the device result into a dict.
+"""
+from __future__ import annotations
+
+import ctypes
+import math
+import os
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_lib", "libprohd.so")
+
+PROHD_OK, PROHD_EINVAL, PROHD_ENOMEM, PROHD_ECUDA, PROHD_ETIMEOUT, PROHD_ENONFINITE, PROHD_ENOTSUP = range(7)
+STATUS_NAMES = {0: "OK", 1: "EINVAL", 2: "ENOMEM", 3: "ECUDA", 4: "ETIMEOUT", 5: "ENONFINITE", 6: "ENOTSUP"}
+PRECISIONS = {"fp32": 0, "fp16": 1, "bf16": 2}
+
+#: every symbol include/prohd.h declares
+EXPORTS = [
+    "prohd_create", "prohd_destroy", "prohd_last_error", "prohd_params_default", "prohd_k_of",
+    "hausdorff_exact_workspace_size", "prohd_directions_workspace_size", "prohd_select_workspace_size",
+    "prohd_estimate_workspace_size", "prohd_estimate_host_workspace_size",
+    "hausdorff_exact", "prohd_directions", "prohd_select", "prohd_estimate", "prohd_estimate_host",
+    "prohd_profile_enable", "prohd_profile_read", "prohd_launch_count",
+]
+
+#: prohd_phase names, in enum order
+PHASES = ["gram", "power", "project", "select", "gather", "hd_prep", "hd_contract", "hd_rescore"]
+
+
+class Params(ctypes.Structure):
+    _fields_ = [("m", ctypes.c_int32), ("precision", ctypes.c_int32), ("alpha_c", ctypes.c_double),
+                ("alpha_p", ctypes.c_double), ("power_max_iters", ctypes.c_int32), ("reserved0", ctypes.c_int32),
+                ("power_tol", ctypes.c_double), ("seed", ctypes.c_uint64), ("wait_timeout_ns", ctypes.c_int64),
+                ("reserved", ctypes.c_int64 * 4)]
+
+
+class HdResult(ctypes.Structure):
+    _fields_ = [("H", ctypes.c_double), ("h_ab", ctypes.c_double), ("h_ba", ctypes.c_double),
+                ("wit_a", ctypes.c_int64), ("wit_b", ctypes.c_int64), ("ab_a", ctypes.c_int64),
+                ("ab_b", ctypes.c_int64), ("ba_b", ctypes.c_int64), ("ba_a", ctypes.c_int64),
+                ("dir", ctypes.c_int32), ("status", ctypes.c_int32), ("H_lowp", ctypes.c_double),
+                ("n_rescored_a", ctypes.c_int64), ("n_rescored_b", ctypes.c_int64)]
+
+
+class Result(ctypes.Structure):
+    _fields_ = [("hd", HdResult), ("nsel_a", ctypes.c_int64), ("nsel_b", ctypes.c_int64)]
+
+
+_lib = None
+_lib_lock = threading.Lock()
+
+
+def load_library(path: str = LIB_PATH):
+    """Loads the CUDA library (raises if it has not been built)."""
+    global _lib
+    with _lib_lock:
+        if _lib is not None:
+            return _lib
+        if not os.path.exists(path):
+            raise FileNotFoundError(f"{path} is missing: build it with __graft_entry__.build() "
+                                    "or python -m paper_2511_18207_gb300.build_lib")
+        lib = ctypes.CDLL(path)
+        vp, i64, i32, sz = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int, ctypes.c_size_t
+        pp = ctypes.POINTER(Params)
+        lib.prohd_create.argtypes = [ctypes.POINTER(vp)]
+        lib.prohd_create.restype = i32
+        lib.prohd_destroy.argtypes = [vp]
+        lib.prohd_destroy.restype = None
+        lib.prohd_last_error.argtypes = [vp]
+        lib.prohd_last_error.restype = ctypes.c_char_p
+        lib.prohd_params_default.argtypes = [pp]
+        lib.prohd_params_default.restype = None
+        lib.prohd_k_of.argtypes = [ctypes.c_double, i64]
+        lib.prohd_k_of.restype = i64
+        lib.hausdorff_exact_workspace_size.argtypes = [i64, i64, i32, i32]
+        lib.hausdorff_exact_workspace_size.restype = sz
+        lib.prohd_directions_workspace_size.argtypes = [i64, i64, i32, i32]
+        lib.prohd_directions_workspace_size.restype = sz
+        lib.prohd_select_workspace_size.argtypes = [i64, i64, i32, i32]
+        lib.prohd_select_workspace_size.restype = sz
+        lib.prohd_estimate_workspace_size.argtypes = [i64, i64, i32, pp]
+        lib.prohd_estimate_workspace_size.restype = sz
+        lib.prohd_estimate_host_workspace_size.argtypes = [i64, i64, i32, pp]
+        lib.prohd_estimate_host_workspace_size.restype = sz
+        lib.hausdorff_exact.argtypes = [vp, vp, i64, vp, i64, i32, i32, vp, vp, sz, vp]
+        lib.hausdorff_exact.restype = i32
+        lib.prohd_directions.argtypes = [vp, vp, i64, vp, i64, i32, pp, vp, vp, vp, sz, vp]
+        lib.prohd_directions.restype = i32
+        lib.prohd_select.argtypes = [vp, vp, i64, vp, i64, i32, vp, i32, vp, vp, vp, vp, vp, vp, vp, sz, vp]
+        lib.prohd_select.restype = i32
+        lib.prohd_estimate.argtypes = [vp, vp, i64, vp, i64, i32, pp, vp, vp, vp, vp, vp, sz, vp]
+        lib.prohd_estimate.restype = i32
+        lib.prohd_estimate_host.argtypes = [vp, vp, i64, vp, i64, i32, pp, vp, vp, sz, vp]
+        lib.prohd_estimate_host.restype = i32
+        lib.prohd_profile_enable.argtypes = [vp, i32]
+        lib.prohd_profile_enable.restype = i32
+        lib.prohd_profile_read.argtypes = [vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int64), i32]
+        lib.prohd_profile_read.restype = i32
+        lib.prohd_launch_count.argtypes = []
+        lib.prohd_launch_count.restype = ctypes.c_uint64
+        _lib = lib
+        return lib
+
+
+class ProHDError(RuntimeError):
+    pass
+
+
+def default_params(**kw) -> Params:
+    p = Params()
+    load_library().prohd_params_default(ctypes.byref(p))
+    for k, v in kw.items():
+        if v is None:
+            continue
+        if k == "precision" and isinstance(v, str):
+            v = PRECISIONS[v]
+        setattr(p, k, v)
+    return p
+
+
+def k_of(alpha: float, n: int) -> int:
+    return int(load_library().prohd_k_of(float(alpha), int(n)))
+
+
+def _torch():
+    import torch
+    return torch
+
+
+def _ptr(t):
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _check_points(t, name):
+    torch = _torch()
+    if not isinstance(t, torch.Tensor) or t.device.type != "cuda" or t.dtype != torch.float32 or t.dim() != 2:
+        raise ValueError(f"{name} must be a CUDA float32 tensor [n, D]")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+
+
+class Context:
+    """Owns a prohd_ctx and a grow-only workspace on the current device."""
+
+    def __init__(self):
+        torch = _torch()
+        lib = load_library()
+        torch.cuda.init()
+        h = ctypes.c_void_p()
+        rc = lib.prohd_create(ctypes.byref(h))
+        if rc != PROHD_OK:
+            raise ProHDError(f"prohd_create failed: {STATUS_NAMES.get(rc, rc)} (the library needs an sm_103 GPU)")
+        self.lib, self.h = lib, h
+        self.device = torch.cuda.current_device()
+        self._ws = None
+
+    def close(self):
+        if self.h:
+            self.lib.prohd_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def workspace(self, nbytes: int):
+        torch = _torch()
+        nbytes = max(int(nbytes), 256)
+        if self._ws is None or self._ws.numel() < nbytes:
+            self._ws = torch.empty(nbytes, dtype=torch.uint8, device=f"cuda:{self.device}")
+        return self._ws
+
+    def _raise(self, rc, what):
+        if rc != PROHD_OK:
+            msg = self.lib.prohd_last_error(self.h).decode()
+            raise ProHDError(f"{what}: {STATUS_NAMES.get(rc, rc)}: {msg}")
+
+    @staticmethod
+    def _stream(stream):
+        torch = _torch()
+        s = stream if stream is not None else torch.cuda.current_stream()
+        return ctypes.c_void_p(s.cuda_stream)
+
+    # ------------------------------------------------------------- profiling
+
+    def profile_enable(self, on: bool = True):
+        self._raise(self.lib.prohd_profile_enable(self.h, 1 if on else 0), "prohd_profile_enable")
+
+    def profile_read(self, reset: bool = True) -> dict:
+        """{phase: (total ms, instances)} of the calls made while profiling was on."""
+        n = len(PHASES)
+        ms = (ctypes.c_double * n)()
+        cnt = (ctypes.c_int64 * n)()
+        self._raise(self.lib.prohd_profile_read(self.h, ms, cnt, 1 if reset else 0), "prohd_profile_read")
+        return {PHASES[i]: (ms[i], cnt[i]) for i in range(n)}
+
+    def launch_count(self) -> int:
+        return int(self.lib.prohd_launch_count())
+
+    # ------------------------------------------------------------- C ABI mirrors
+
+    def hausdorff_exact(self, A, B, precision="fp16", out=None, ws=None, stream=None):
+        """Enqueues hausdorff_exact; returns the device result buffer (uint8 tensor)."""
+        torch = _torch()
+        _check_points(A, "A")
+        _check_points(B, "B")
+        prec = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
+        D = A.shape[1]
+        need = self.lib.hausdorff_exact_workspace_size(A.shape[0], B.shape[0], D, prec)
+        ws = self.workspace(need) if ws is None else ws
+        out = torch.empty(ctypes.sizeof(HdResult), dtype=torch.uint8, device=A.device) if out is None else out
+        rc = self.lib.hausdorff_exact(self.h, _ptr(A), A.shape[0], _ptr(B), B.shape[0], D, prec, _ptr(out),
+                                      _ptr(ws), ws.numel(), self._stream(stream))
+        self._raise(rc, "hausdorff_exact")
+        return out
+
+    def prohd_directions(self, A, B, m=None, seed=0, max_iters=1000, tol=1e-13, stream=None):
+        torch = _torch()
+        _check_points(A, "A")
+        _check_points(B, "B")
+        D = A.shape[1]
+        p = default_params(m=-1 if m is None else m, seed=seed, power_max_iters=max_iters, power_tol=tol)
+        mm = int(math.isqrt(D)) if m is None else m
+        dirs = torch.empty((1 + mm, D), dtype=torch.float64, device=A.device)
+        eig = torch.empty(max(mm, 1), dtype=torch.float64, device=A.device)
+        need = self.lib.prohd_directions_workspace_size(A.shape[0], B.shape[0], D, mm)
+        ws = self.workspace(need)
+        rc = self.lib.prohd_directions(self.h, _ptr(A), A.shape[0], _ptr(B), B.shape[0], D, ctypes.byref(p),
+                                       _ptr(dirs), _ptr(eig), _ptr(ws), ws.numel(), self._stream(stream))
+        self._raise(rc, "prohd_directions")
+        return dirs, eig[:mm]
+
+    def prohd_select(self, A, B, dirs, kA, kB, stream=None):
+        """Returns (idxA, nselA, idxB, nselB) device tensors (int32 indices, int64 counts)."""
+        torch = _torch()
+        _check_points(A, "A")
+        _check_points(B, "B")
+        D = A.shape[1]
+        dirs = dirs.to(device=A.device, dtype=torch.float64).contiguous()
+        nd = dirs.shape[0]
+        ka = (ctypes.c_int64 * nd)(*[int(k) for k in kA])
+        kb = (ctypes.c_int64 * nd)(*[int(k) for k in kB])
+        idxA = torch.empty(A.shape[0], dtype=torch.int32, device=A.device)
+        idxB = torch.empty(B.shape[0], dtype=torch.int32, device=A.device)
+        ns = torch.zeros(2, dtype=torch.int64, device=A.device)
+        need = self.lib.prohd_select_workspace_size(A.shape[0], B.shape[0], D, nd)
+        ws = self.workspace(need)
+        rc = self.lib.prohd_select(self.h, _ptr(A), A.shape[0], _ptr(B), B.shape[0], D, _ptr(dirs), nd, ka, kb,
+                                   _ptr(idxA), ctypes.c_void_p(ns.data_ptr()), _ptr(idxB),
+                                   ctypes.c_void_p(ns.data_ptr() + 8), _ptr(ws), ws.numel(), self._stream(stream))
+        self._raise(rc, "prohd_select")
+        return idxA, ns[0:1], idxB, ns[1:2]
+
+    def prohd_estimate(self, A, B, params: Params | None = None, out=None, idxA=None, idxB=None, dirs=None,
+                       ws=None, stream=None, **kw):
+        """Enqueues prohd_estimate; returns the device result buffer (uint8 tensor)."""
+        torch = _torch()
+        _check_points(A, "A")
+        _check_points(B, "B")
+        p = params if params is not None else default_params(**kw)
+        D = A.shape[1]
+        need = self.lib.prohd_estimate_workspace_size(A.shape[0], B.shape[0], D, ctypes.byref(p))
+        ws = self.workspace(need) if ws is None else ws
+        out = torch.empty(ctypes.sizeof(Result), dtype=torch.uint8, device=A.device) if out is None else out
+        rc = self.lib.prohd_estimate(self.h, _ptr(A), A.shape[0], _ptr(B), B.shape[0], D, ctypes.byref(p), _ptr(out),
+                                     _ptr(idxA) if idxA is not None else None,
+                                     _ptr(idxB) if idxB is not None else None,
+                                     _ptr(dirs) if dirs is not None else None, _ptr(ws), ws.numel(),
+                                     self._stream(stream))
+        self._raise(rc, "prohd_estimate")
+        return out
+
+    def prohd_estimate_host(self, A_host, B_host, params: Params | None = None, out_host=None, ws=None,
+                            stream=None, **kw):
+        """A_host, B_host: CPU float32 tensors (pinned for async copies). Returns
+        the host Result that is valid after the stream is synchronised."""
+        torch = _torch()
+        for t, nme in ((A_host, "A_host"), (B_host, "B_host")):
+            if t.device.type != "cpu" or t.dtype != torch.float32 or t.dim() != 2 or not t.is_contiguous():
+                raise ValueError(f"{nme} must be a contiguous CPU float32 tensor [n, D]")
+        p = params if params is not None else default_params(**kw)
+        D = A_host.shape[1]
+        need = self.lib.prohd_estimate_host_workspace_size(A_host.shape[0], B_host.shape[0], D, ctypes.byref(p))
+        ws = self.workspace(need) if ws is None else ws
+        out_host = Result() if out_host is None else out_host
+        rc = self.lib.prohd_estimate_host(self.h, _ptr(A_host), A_host.shape[0], _ptr(B_host), B_host.shape[0], D,
+                                          ctypes.byref(p), ctypes.byref(out_host), _ptr(ws), ws.numel(),
+                                          self._stream(stream))
+        self._raise(rc, "prohd_estimate_host")
+        return out_host
+
+
+# ----------------------------------------------------------------- decoding
+
+def _decode(buf, cls):
+    host = bytes(buf.cpu().numpy().tobytes()) if hasattr(buf, "cpu") else bytes(buf)
+    return cls.from_buffer_copy(host)
+
+
+def hd_dict(r: HdResult) -> dict:
+    return dict(H=r.H, h_ab=r.h_ab, h_ba=r.h_ba, wit_a=r.wit_a, wit_b=r.wit_b, ab=(r.ab_a, r.ab_b),
+                ba=(r.ba_b, r.ba_a), dir=r.dir, status=STATUS_NAMES.get(r.status, r.status), H_lowp=r.H_lowp,
+                n_rescored_a=r.n_rescored_a, n_rescored_b=r.n_rescored_b)
+
+
+def decode_hd(buf) -> dict:
+    return hd_dict(_decode(buf, HdResult))
+
+
+def decode_result(buf) -> dict:
+    r = _decode(buf, Result) if not isinstance(buf, Result) else buf
+    d = hd_dict(r.hd)
+    d.update(nsel_a=r.nsel_a, nsel_b=r.nsel_b)
+    return d
+
+
+_default_ctx = None
+
+
+def context() -> Context:
+    global _default_ctx
+    if _default_ctx is None:
+        _default_ctx = Context()
+    return _default_ctx
+
+
+def hausdorff_exact_sync(A, B, precision="fp16") -> dict:
+    torch = _torch()
+    out = context().hausdorff_exact(A, B, precision)
+    torch.cuda.current_stream().synchronize()
+    return decode_hd(out)
+
+
+def prohd_estimate_sync(A, B, want_indices=False, want_dirs=False, **kw) -> dict:
+    torch = _torch()
+    ctx = context()
+    idxA = torch.empty(A.shape[0], dtype=torch.int32, device=A.device) if want_indices else None
+    idxB = torch.empty(B.shape[0], dtype=torch.int32, device=A.device) if want_indices else None
+    dirs = None
+    if want_dirs:
+        D = A.shape[1]
+        m = kw.get("m")
+        m = int(math.isqrt(D)) if m is None or m < 0 else int(m)
+        dirs = torch.empty((1 + m, D), dtype=torch.float64, device=A.device)
+    out = ctx.prohd_estimate(A, B, idxA=idxA, idxB=idxB, dirs=dirs, **kw)
+    torch.cuda.current_stream().synchronize()
+    r = decode_result(out)
+    if want_dirs:
+        r["dirs"] = dirs.cpu().numpy()
+    if want_indices:
+        r["idxA"] = idxA[: r["nsel_a"]].cpu().numpy().astype(np.int64)
+        r["idxB"] = idxB[: r["nsel_b"]].cpu().numpy().astype(np.int64)
+    return r

@@ -1,0 +1,70 @@
+"""ProHD end to end (Algorithm 3) on the GPU against the oracle.
+
+Contract: the GPU's candidate sets equal the oracle's selection for the GPU's
+own directions (bit-exact), H_hat equals the oracle's exact HD of those
+subsets (relative 1e-5), and the directions agree with the oracle's."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2511_18207_gb300 import prohd
+from paper_2511_18207_gb300 import workloads as W
+
+from .gpu_util import dev, rel, torch_cuda
+
+pytestmark = pytest.mark.gpu
+
+
+def _run(A, B, m, alpha, prec="fp16", alpha_p=None):
+    torch_cuda()
+    r = prohd.prohd_estimate_sync(dev(A), dev(B), want_indices=True, want_dirs=True, m=m, alpha_c=alpha,
+                                  alpha_p=alpha_p, precision=prec)
+    assert r["status"] == "OK", r
+    dirs = r["dirs"]
+    ap = alpha / max(m, 1) if alpha_p is None else alpha_p
+    kA = oracle.k_list(A.shape[0], 1 + m, alpha, ap)
+    kB = oracle.k_list(B.shape[0], 1 + m, alpha, ap)
+    ia, ib = oracle.select(A, dirs, kA), oracle.select(B, dirs, kB)
+    np.testing.assert_array_equal(r["idxA"], ia)
+    np.testing.assert_array_equal(r["idxB"], ib)
+    assert r["nsel_a"] == ia.size and r["nsel_b"] == ib.size
+    sub = oracle.hausdorff(A[ia], B[ib])
+    assert rel(r["H"], sub["H"]) <= 1e-5, (r["H"], sub["H"])
+    # witnesses are indices into the full sets
+    d = np.sqrt(((A[r["wit_a"]].astype(np.float64) - B[r["wit_b"]]) ** 2).sum())
+    assert d == pytest.approx(r["H"], rel=1e-12)
+    return r
+
+
+@pytest.mark.parametrize("prec", ["fp16", "bf16", "fp32"])
+def test_estimate_config_small(prec):
+    # N(0,I16) vs N(0.5,I16) with 1% outliers; centroid + top-2 PCs; 2% per side
+    A, B = W.gaussian_outliers(2000, 2000, 16, seed=0)
+    r = _run(A, B, m=2, alpha=0.02, prec=prec, alpha_p=0.02)
+    o = oracle.prohd(A, B, alpha=0.02, m=2, alpha_p=0.02, seed=0)
+    # end to end against the oracle's own directions: same candidate sets here
+    np.testing.assert_array_equal(r["idxA"], o["idxA"])
+    np.testing.assert_array_equal(r["idxB"], o["idxB"])
+    assert rel(r["H"], o["H_hat"]) <= 1e-5
+
+
+def test_estimate_defaults_random_clouds():
+    A, B = W.random_clouds(20_000, 15_000, 8, seed=2)
+    _run(A, B, m=2, alpha=0.01)
+
+
+def test_estimate_mixture_d256():
+    A, B = W.mixture_pair(20_000, 256, 16, seed=1)
+    _run(A, B, m=8, alpha=0.01)
+
+
+def test_estimate_host_entry_matches_device():
+    torch = torch_cuda()
+    A, B = W.gaussian_outliers(3000, 2500, 16, seed=3)
+    c = prohd.context()
+    p = prohd.default_params(m=2, alpha_c=0.02)
+    res = c.prohd_estimate_host(torch.from_numpy(A).pin_memory(), torch.from_numpy(B).pin_memory(), params=p)
+    torch.cuda.current_stream().synchronize()
+    h = prohd.decode_result(res)
+    d = prohd.prohd_estimate_sync(dev(A), dev(B), m=2, alpha_c=0.02)
+    assert h["H"] == d["H"] and h["nsel_a"] == d["nsel_a"] and h["nsel_b"] == d["nsel_b"]
