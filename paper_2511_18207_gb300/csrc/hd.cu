@@ -653,16 +653,22 @@ __device__ double dist64(const float* a, const float* b, int D) {
 }
 
 // One block. best arrays hold packed (d^2, nn index) per entry; ids (or the
-// identity) give the row number of each entry.
-__global__ void hd_finalize_kernel(const float* __restrict__ A, const float* __restrict__ B, int D,
-                                   const unsigned long long* __restrict__ bestA, const int32_t* __restrict__ idsA,
-                                   const int64_t* cntA_dev, const unsigned long long* __restrict__ bestB,
-                                   const int32_t* __restrict__ idsB, const int64_t* cntB_dev,
-                                   const int32_t* __restrict__ mapA, const int32_t* __restrict__ mapB,
-                                   const HdScalars* sc, const int* status, prohd_hd_result* out) {
+// identity) give the row number of each entry. Every index is validated
+// before use: with non-finite input the candidate lists can be empty, and the
+// result is then NaN with the device status set.
+__global__ void hd_finalize_kernel(const float* __restrict__ A, const int64_t* nA_dev, const float* __restrict__ B,
+                                   const int64_t* nB_dev, int D, const unsigned long long* __restrict__ bestA,
+                                   const int32_t* __restrict__ idsA, const int64_t* cntA_dev,
+                                   const unsigned long long* __restrict__ bestB, const int32_t* __restrict__ idsB,
+                                   const int64_t* cntB_dev, const int32_t* __restrict__ mapA,
+                                   const int32_t* __restrict__ mapB, const HdScalars* sc, int* status,
+                                   prohd_hd_result* out) {
   __shared__ unsigned long long sh[32];
   __shared__ int64_t s_nn[2];
+  __shared__ double s_d[2];
+  const int64_t nA = *nA_dev, nB = *nB_dev;
   const int64_t cA = *cntA_dev, cB = *cntB_dev;
+  if (threadIdx.x == 0) s_nn[0] = s_nn[1] = -1;
   unsigned long long ka = 0, kb = 0;
   for (int64_t c = threadIdx.x; c < cA; c += blockDim.x) {
     uint32_t id = idsA ? (uint32_t)idsA[c] : (uint32_t)c;
@@ -676,23 +682,25 @@ __global__ void hd_finalize_kernel(const float* __restrict__ A, const float* __r
   }
   ka = block_max_u64(ka, sh);
   kb = block_max_u64(kb, sh);
-  const uint32_t ia = ~(uint32_t)(ka & 0xffffffffu), jb = ~(uint32_t)(kb & 0xffffffffu);
+  const int64_t ia = (cA > 0) ? (int64_t)(~(uint32_t)(ka & 0xffffffffu)) : -1;
+  const int64_t jb = (cB > 0) ? (int64_t)(~(uint32_t)(kb & 0xffffffffu)) : -1;
   for (int64_t c = threadIdx.x; c < cA; c += blockDim.x) {
     uint32_t id = idsA ? (uint32_t)idsA[c] : (uint32_t)c;
-    if (id == ia) s_nn[0] = packed_idx(bestA[c]);
+    if ((int64_t)id == ia && bestA[c] != ~0ull) s_nn[0] = packed_idx(bestA[c]);
   }
   for (int64_t c = threadIdx.x; c < cB; c += blockDim.x) {
     uint32_t id = idsB ? (uint32_t)idsB[c] : (uint32_t)c;
-    if (id == jb) s_nn[1] = packed_idx(bestB[c]);
+    if ((int64_t)id == jb && bestB[c] != ~0ull) s_nn[1] = packed_idx(bestB[c]);
   }
   __syncthreads();
   const int64_t ja = s_nn[0], ib = s_nn[1];
-  __shared__ double s_d[2];
+  const bool okA = ia >= 0 && ia < nA && ja >= 0 && ja < nB;
+  const bool okB = jb >= 0 && jb < nB && ib >= 0 && ib < nA;
   if (threadIdx.x < 32) {
-    double d = dist64(A + (int64_t)ia * D, B + ja * D, D);
+    double d = okA ? dist64(A + ia * D, B + ja * D, D) : __longlong_as_double(0x7ff8000000000000ll);
     if (threadIdx.x == 0) s_d[0] = d;
   } else if (threadIdx.x < 64) {
-    double d = dist64(B + (int64_t)jb * D, A + ib * D, D);
+    double d = okB ? dist64(B + jb * D, A + ib * D, D) : __longlong_as_double(0x7ff8000000000000ll);
     if (threadIdx.x == 32) s_d[1] = d;
   }
   __syncthreads();
@@ -700,14 +708,15 @@ __global__ void hd_finalize_kernel(const float* __restrict__ A, const float* __r
     prohd_hd_result r;
     r.h_ab = s_d[0];
     r.h_ba = s_d[1];
-    r.ab_a = mapA ? mapA[ia] : ia;
-    r.ab_b = mapB ? mapB[ja] : ja;
-    r.ba_b = mapB ? mapB[jb] : jb;
-    r.ba_a = mapA ? mapA[ib] : ib;
+    r.ab_a = okA ? (mapA ? mapA[ia] : ia) : -1;
+    r.ab_b = okA ? (mapB ? mapB[ja] : ja) : -1;
+    r.ba_b = okB ? (mapB ? mapB[jb] : jb) : -1;
+    r.ba_a = okB ? (mapA ? mapA[ib] : ib) : -1;
     r.dir = (r.h_ab >= r.h_ba) ? 0 : 1;
     r.H = r.dir == 0 ? r.h_ab : r.h_ba;
     r.wit_a = r.dir == 0 ? r.ab_a : r.ba_a;
     r.wit_b = r.dir == 0 ? r.ab_b : r.ba_b;
+    if (!(okA && okB) && *status == PROHD_OK) *status = PROHD_ENONFINITE;
     r.status = *status;
     if (sc) {
       r.H_lowp = ldexp(sqrt(fmax((double)sc->lowp_max, 0.0)), -scale_exponent(sc->maxabs));
@@ -813,8 +822,8 @@ cudaError_t hd_core(prohd_ctx* ctx, const float* A, const int64_t* nA_dev, int64
     }
     PhaseTimer pt2(ctx, PROHD_PH_HD_RESCORE, st);
     count_launch();
-    hd_finalize_kernel<<<1, 1024, 0, st>>>(A, B, D, b.bestA, nullptr, nA_dev, b.bestB, nullptr, nB_dev, mapA, mapB,
-                                           nullptr, status_dev, out);
+    hd_finalize_kernel<<<1, 1024, 0, st>>>(A, nA_dev, B, nB_dev, D, b.bestA, nullptr, nA_dev, b.bestB, nullptr,
+                                           nB_dev, mapA, mapB, nullptr, status_dev, out);
     return cudaGetLastError();
   }
 
@@ -890,8 +899,8 @@ cudaError_t hd_core(prohd_ctx* ctx, const float* A, const int64_t* nA_dev, int64
   if ((e = launch_simt(true, true, false, A, b.candA, &b.sc->ncandA, B, nB_dev, D, b.bestA, nullptr, nsm, st))) return e;
   if ((e = launch_simt(true, true, false, B, b.candB, &b.sc->ncandB, A, nA_dev, D, b.bestB, nullptr, nsm, st))) return e;
   count_launch();
-  hd_finalize_kernel<<<1, 1024, 0, st>>>(A, B, D, b.bestA, b.candA, &b.sc->ncandA, b.bestB, b.candB, &b.sc->ncandB,
-                                         mapA, mapB, b.sc, status_dev, out);
+  hd_finalize_kernel<<<1, 1024, 0, st>>>(A, nA_dev, B, nB_dev, D, b.bestA, b.candA, &b.sc->ncandA, b.bestB, b.candB,
+                                         &b.sc->ncandB, mapA, mapB, b.sc, status_dev, out);
   return cudaGetLastError();
 }
 
