@@ -216,6 +216,21 @@ prohd_status prohd_estimate_host(prohd_ctx* ctx, const float* A_host, int64_t nA
                                  int64_t nB, int D, const prohd_params* p, prohd_result* out_host,
                                  void* ws, size_t ws_bytes, void* stream);
 
+/*
+ * hausdorff_exact without a workspace, for callers that cannot allocate
+ * device memory (code running under someone else's stream capture, plugins
+ * whose host framework owns the allocator, programs that forbid allocation
+ * after start-up). The paper has no counterpart; this is a deployment aid.
+ * Same result as hausdorff_exact(..., PROHD_FP32, ...); scratch is a fixed
+ * 2 MiB __device__ array inside the library (held by every GPU that loads
+ * it), so nA + nB is limited to about 262,000 points and larger inputs return
+ * PROHD_EINVAL. The first call on a device looks up the array's address
+ * (cudaGetSymbolAddress): make it before any stream capture. All calls share
+ * the array: calls whose GPU work overlaps race; serialise them.
+ */
+prohd_status hausdorff_exact_noalloc(prohd_ctx* ctx, const float* A, int64_t nA, const float* B, int64_t nB,
+                                     int D, prohd_hd_result* out, void* stream);
+
 /* ------------------------------------------------------------ observability */
 
 /* Phases timed by the profiler (one kernel each unless noted). */

@@ -32,7 +32,7 @@ EXPORTS = [
     "hausdorff_exact_workspace_size", "prohd_directions_workspace_size", "prohd_select_workspace_size",
     "prohd_estimate_workspace_size", "prohd_estimate_host_workspace_size",
     "hausdorff_exact", "prohd_directions", "prohd_select", "prohd_estimate", "prohd_estimate_host",
-    "prohd_profile_enable", "prohd_profile_read", "prohd_launch_count",
+    "prohd_profile_enable", "prohd_profile_read", "prohd_launch_count", "hausdorff_exact_noalloc",
 ]
 
 #: prohd_phase names, in enum order
@@ -110,6 +110,8 @@ def load_library(path: str = LIB_PATH):
         lib.prohd_profile_read.restype = i32
         lib.prohd_launch_count.argtypes = []
         lib.prohd_launch_count.restype = ctypes.c_uint64
+        lib.hausdorff_exact_noalloc.argtypes = [vp, vp, i64, vp, i64, i32, vp, vp]
+        lib.hausdorff_exact_noalloc.restype = i32
         _lib = lib
         return lib
 
@@ -226,6 +228,18 @@ class Context:
         rc = self.lib.hausdorff_exact(self.h, _ptr(A), A.shape[0], _ptr(B), B.shape[0], D, prec, _ptr(out),
                                       _ptr(ws), ws.numel(), self._stream(stream))
         self._raise(rc, "hausdorff_exact")
+        return out
+
+    def hausdorff_exact_noalloc(self, A, B, out=None, stream=None):
+        """Enqueues hausdorff_exact_noalloc (FP32, library-internal scratch,
+        no workspace); returns the device result buffer (uint8 tensor)."""
+        torch = _torch()
+        _check_points(A, "A")
+        _check_points(B, "B")
+        out = torch.empty(ctypes.sizeof(HdResult), dtype=torch.uint8, device=A.device) if out is None else out
+        rc = self.lib.hausdorff_exact_noalloc(self.h, _ptr(A), A.shape[0], _ptr(B), B.shape[0], A.shape[1], _ptr(out),
+                                              self._stream(stream))
+        self._raise(rc, "hausdorff_exact_noalloc")
         return out
 
     def prohd_directions(self, A, B, m=None, seed=0, max_iters=1000, tol=1e-13, stream=None):
