@@ -300,11 +300,13 @@ PROHD_DEV void st_cluster_f64(uint32_t addr, double v) {
   asm volatile("st.shared::cluster.f64 [%0], %1;" ::"r"(addr), "d"(v) : "memory");
 }
 
-// Batched block sums of K values per thread (K <= 32), deterministic order.
+// Batched block sums of K values per thread (K <= KMAX), deterministic order.
 template <int KMAX>
 __device__ void block_sums(double (&v)[KMAX], int K, double* sh /*[8][KMAX]*/, double* out /*[KMAX]*/) {
   const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
-  for (int k = 0; k < K; ++k) {
+#pragma unroll
+  for (int k = 0; k < KMAX; ++k) {
+    if (k >= K) break;
     double x = warp_sum(v[k]);
     if (l == 0) sh[w * KMAX + k] = x;
   }
@@ -351,7 +353,7 @@ __global__ void __cluster_dims__(kPiCTAs, 1, 1) __launch_bounds__(kPiThreads, 1)
   __syncthreads();
   cluster_sync();
 
-  constexpr int KM = 32;  // components deflated per batched reduction
+  constexpr int KM = 8;  // components deflated per batched reduction (register-resident)
   double part[KM];
 
   for (int l = 1; l <= m; ++l) {
@@ -362,9 +364,12 @@ __global__ void __cluster_dims__(kPiCTAs, 1, 1) __launch_bounds__(kPiThreads, 1)
     for (int pass = 0; pass < 2; ++pass)
       for (int k0 = 0; k0 < np; k0 += KM) {
         const int kk = min(KM, np - k0);
+#pragma unroll
         for (int k = 0; k < KM; ++k) part[k] = 0.0;
         for (int j = tid; j < D; j += kPiThreads)
-          for (int k = 0; k < kk; ++k) part[k] += U64[(size_t)(k0 + k) * D + j] * S.v64[j];
+#pragma unroll
+          for (int k = 0; k < KM; ++k)
+            if (k < kk) part[k] += U64[(size_t)(k0 + k) * D + j] * S.v64[j];
         block_sums<KM>(part, kk, S.red_sh, S.red_out);
         for (int j = tid; j < D; j += kPiThreads) {
           double x = S.v64[j];
@@ -376,6 +381,7 @@ __global__ void __cluster_dims__(kPiCTAs, 1, 1) __launch_bounds__(kPiThreads, 1)
     {
       double nn = 0.0;
       for (int j = tid; j < D; j += kPiThreads) nn += S.v64[j] * S.v64[j];
+#pragma unroll
       for (int k = 0; k < KM; ++k) part[k] = 0.0;
       part[0] = nn;
       block_sums<KM>(part, 1, S.red_sh, S.red_out);
@@ -393,10 +399,27 @@ __global__ void __cluster_dims__(kPiCTAs, 1, 1) __launch_bounds__(kPiThreads, 1)
       // ---- w = C v for this CTA's rows, scattered to every CTA
       for (int r = r0 + warp; r < r1; r += kPiThreads / 32) {
         const float* cr = Crow + (size_t)(r - r0) * D;
-        float s = 0.f;
-        for (int c = lane; c < D; c += 32) s = fmaf(cr[c], S.v32[c], s);
-        s = warp_sum(s);
-        if (lane < kPiCTAs) st_cluster_f32(map_to_cta(&S.w_recv[buf][r], lane), s);
+        // compensated dot product (Ogita-Rump-Oishi Dot2): the FP32 result is
+        // as accurate as if it were accumulated in twice the precision, so the
+        // iterate does not jitter above the stop tolerance
+        float s = 0.f, c = 0.f;
+        for (int k = lane; k < D; k += 32) {
+          const float a = cr[k], b = S.v32[k];
+          const float p = a * b;
+          const float pe = fmaf(a, b, -p);
+          const float t = s + p;
+          const float z = t - s;
+          c += (s - (t - z)) + (p - z) + pe;
+          s = t;
+        }
+        for (int o = 16; o > 0; o >>= 1) {
+          const float so = __shfl_xor_sync(0xffffffffu, s, o), co = __shfl_xor_sync(0xffffffffu, c, o);
+          const float t = s + so;
+          const float z = t - s;
+          c += co + (s - (t - z)) + (so - z);
+          s = t;
+        }
+        if (lane < kPiCTAs) st_cluster_f32(map_to_cta(&S.w_recv[buf][r], lane), s + c);
       }
       if (rank == 0 && tid < kPiCTAs) st_cluster_s32(map_to_cta(&S.flag[buf], tid), stop_local ? 1 : 0);
       cluster_sync();
@@ -406,9 +429,12 @@ __global__ void __cluster_dims__(kPiCTAs, 1, 1) __launch_bounds__(kPiThreads, 1)
       for (int pass = 0; pass < 2; ++pass)
         for (int k0 = 0; k0 < np; k0 += KM) {
           const int kk = min(KM, np - k0);
+#pragma unroll
           for (int k = 0; k < KM; ++k) part[k] = 0.0;
           for (int j = tid; j < D; j += kPiThreads)
-            for (int k = 0; k < kk; ++k) part[k] += (double)(U32[(size_t)(k0 + k) * D + j] * w[j]);
+#pragma unroll
+            for (int k = 0; k < KM; ++k)
+              if (k < kk) part[k] += (double)(U32[(size_t)(k0 + k) * D + j] * w[j]);
           block_sums<KM>(part, kk, S.red_sh, S.red_out);
           for (int j = tid; j < D; j += kPiThreads) {
             float x = w[j];
@@ -424,6 +450,7 @@ __global__ void __cluster_dims__(kPiCTAs, 1, 1) __launch_bounds__(kPiThreads, 1)
         nn += x * x;
         dv += x * S.v64[j];
       }
+#pragma unroll
       for (int k = 0; k < KM; ++k) part[k] = 0.0;
       part[0] = nn;
       part[1] = dv;
@@ -443,9 +470,12 @@ __global__ void __cluster_dims__(kPiCTAs, 1, 1) __launch_bounds__(kPiThreads, 1)
     for (int pass = 0; pass < 2; ++pass)
       for (int k0 = 0; k0 < np; k0 += KM) {
         const int kk = min(KM, np - k0);
+#pragma unroll
         for (int k = 0; k < KM; ++k) part[k] = 0.0;
         for (int j = tid; j < D; j += kPiThreads)
-          for (int k = 0; k < kk; ++k) part[k] += U64[(size_t)(k0 + k) * D + j] * S.v64[j];
+#pragma unroll
+          for (int k = 0; k < KM; ++k)
+            if (k < kk) part[k] += U64[(size_t)(k0 + k) * D + j] * S.v64[j];
         block_sums<KM>(part, kk, S.red_sh, S.red_out);
         for (int j = tid; j < D; j += kPiThreads) {
           double x = S.v64[j];
@@ -457,6 +487,7 @@ __global__ void __cluster_dims__(kPiCTAs, 1, 1) __launch_bounds__(kPiThreads, 1)
     {
       double nn = 0.0;
       for (int j = tid; j < D; j += kPiThreads) nn += S.v64[j] * S.v64[j];
+#pragma unroll
       for (int k = 0; k < KM; ++k) part[k] = 0.0;
       part[0] = nn;
       block_sums<KM>(part, 1, S.red_sh, S.red_out);
@@ -531,6 +562,7 @@ struct DirBufs {
   float* s32 = nullptr;
   double *Gpart = nullptr, *sumApart = nullptr, *sumBpart = nullptr;
   double *G = nullptr, *sumA = nullptr, *sumB = nullptr, *C64 = nullptr;
+  double* gc_scratch = nullptr;  // tensor-core Gram partials
   float* C32 = nullptr;
   double* U64 = nullptr;
   float* U32 = nullptr;
@@ -538,9 +570,13 @@ struct DirBufs {
 
 static void dir_layout(Arena& ws, int D, int m, DirBufs& b) {
   b.s32 = ws.take<float>((size_t)D);
-  b.Gpart = ws.take<double>((size_t)kMaxSplit * D * D);
-  b.sumApart = ws.take<double>((size_t)kMaxSplit * D);
-  b.sumBpart = ws.take<double>((size_t)kMaxSplit * D);
+  if (gram_tc_supported(D)) {
+    b.gc_scratch = ws.take<double>(gram_tc_scratch_doubles(D, kMaxSms));
+  } else {
+    b.Gpart = ws.take<double>((size_t)kMaxSplit * D * D);
+    b.sumApart = ws.take<double>((size_t)kMaxSplit * D);
+    b.sumBpart = ws.take<double>((size_t)kMaxSplit * D);
+  }
   b.G = ws.take<double>((size_t)D * D);
   b.sumA = ws.take<double>((size_t)D);
   b.sumB = ws.take<double>((size_t)D);
@@ -568,20 +604,27 @@ cudaError_t directions_run(prohd_ctx* ctx, const float* A, int64_t nA, const flo
   const int nsm = ctx->num_sms;
   count_launch();
   pilot_shift_kernel<<<(D + 31) / 32, 256, 0, st>>>(A, nA, D, b.s32);
-  const int nt = (D + kGT - 1) / kGT;
-  const int ntiles = nt * (nt + 1) / 2;
-  const int64_t N = nA + nB;
-  int nsplit = (int)std::max<int64_t>(
-      1, std::min<int64_t>(std::min<int64_t>((nsm + ntiles - 1) / ntiles, ceil_div(N, 4 * kGR)), kMaxSplit));
-  cudaFuncSetAttribute(gram_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(GramSmem));
-  PhaseTimer pt_gram(ctx, PROHD_PH_GRAM, st);
-  count_launch();
-  gram_kernel<<<dim3(ntiles, nsplit), 256, sizeof(GramSmem), st>>>(A, nA, B, nB, D, b.s32, b.Gpart, b.sumApart,
-                                                                  b.sumBpart, status_dev);
-  pt_gram.stop();
-  count_launch();
-  reduce_parts_kernel<<<nsm, 256, 0, st>>>(b.Gpart, b.sumApart, b.sumBpart, nsplit, D, b.G, b.sumA, b.sumB);
-  if ((e = cudaGetLastError())) return e;
+  if (gram_tc_supported(D) && ctx->num_sms <= kMaxSms) {
+    if ((e = gram_tc_run(ctx, A, nA, B, nB, D, b.s32, b.gc_scratch, b.G, b.sumA, b.sumB, status_dev,
+                         kDefaultTimeoutNs, st)))
+      return e;
+  } else {
+    const int nt = (D + kGT - 1) / kGT;
+    const int ntiles = nt * (nt + 1) / 2;
+    const int64_t N = nA + nB;
+    // a whole number of blocks per SM wave
+    int nsplit = (int)std::max<int64_t>(
+        1, std::min<int64_t>(std::min<int64_t>(nsm / ntiles, ceil_div(N, 4 * kGR)), kMaxSplit));
+    cudaFuncSetAttribute(gram_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(GramSmem));
+    PhaseTimer pt_gram(ctx, PROHD_PH_GRAM, st);
+    count_launch();
+    gram_kernel<<<dim3(ntiles, nsplit), 256, sizeof(GramSmem), st>>>(A, nA, B, nB, D, b.s32, b.Gpart, b.sumApart,
+                                                                    b.sumBpart, status_dev);
+    pt_gram.stop();
+    count_launch();
+    reduce_parts_kernel<<<nsm, 256, 0, st>>>(b.Gpart, b.sumApart, b.sumBpart, nsplit, D, b.G, b.sumA, b.sumB);
+    if ((e = cudaGetLastError())) return e;
+  }
   count_launch();
   centroid_axis_kernel<<<1, 256, 0, st>>>(b.sumA, b.sumB, nA, nB, D, dirs);
   count_launch();

@@ -165,14 +165,28 @@ __global__ void fill_u32_kernel(unsigned* p, int64_t n, unsigned v) {
 
 // Shift s = mean of the first <= 2048 rows of A and of B (FP64 sums), a
 // common origin that keeps ||a - s|| small; distances do not depend on it.
+// One block per 32 columns, 8 row groups.
 __global__ void hd_shift_kernel(const float* __restrict__ A, const int64_t* nA_dev, const float* __restrict__ B,
                                 const int64_t* nB_dev, int D, float* __restrict__ shift) {
   const int64_t na = *nA_dev < 2048 ? *nA_dev : 2048, nb = *nB_dev < 2048 ? *nB_dev : 2048;
-  for (int c = threadIdx.x; c < D; c += blockDim.x) {
-    double sa = 0.0, sb = 0.0;
-    for (int64_t i = 0; i < na; ++i) sa += (double)A[i * D + c];
-    for (int64_t i = 0; i < nb; ++i) sb += (double)B[i * D + c];
-    shift[c] = (float)(0.5 * (sa / (double)na + sb / (double)nb));
+  __shared__ double part[2][8][33];
+  const int cl = threadIdx.x & 31, rg = threadIdx.x >> 5;
+  const int c = blockIdx.x * 32 + cl;
+  double sa = 0.0, sb = 0.0;
+  if (c < D) {
+    for (int64_t i = rg; i < na; i += 8) sa += (double)A[i * D + c];
+    for (int64_t i = rg; i < nb; i += 8) sb += (double)B[i * D + c];
+  }
+  part[0][rg][cl] = sa;
+  part[1][rg][cl] = sb;
+  __syncthreads();
+  if (rg == 0 && c < D) {
+    double ta = 0.0, tb = 0.0;
+    for (int g = 0; g < 8; ++g) {
+      ta += part[0][g][cl];
+      tb += part[1][g][cl];
+    }
+    shift[c] = (float)(0.5 * (ta / (double)na + tb / (double)nb));
   }
 }
 
@@ -226,7 +240,7 @@ struct TileT<1> {
 // One warp per row. Writes the rounded copy h = round((x - s) 2^sigma)
 // (times `mult`: -2 for A, 1 for B) into Xt [n_pad, Dp], ||h||^2 (FP32) into
 // norm2, and eps >= ||(x - s) - h 2^-sigma|| + rounding of x - s (original
-// units) into eps. Padding rows: zeros, norm2 = +inf, eps = 0.
+// units) into eps. Padding rows: zeros, norm2 = 1e30, eps = 0.
 template <int BF16>
 __global__ void hd_prep_kernel(const float* __restrict__ X, const int64_t* n_dev, int64_t n_pad, int D, int Dp,
                                const float* __restrict__ shift, const float* __restrict__ maxabs, float mult,
@@ -274,7 +288,7 @@ __global__ void hd_prep_kernel(const float* __restrict__ X, const int64_t* n_dev
     } else {
       for (int c = lane; c < Dp; c += 32) out[c] = TT::from(0.f);
       if (lane == 0) {
-        norm2[r] = __int_as_float(0x7f800000);
+        norm2[r] = 1e30f;  // padding: far from everything, finite in TMEM
         eps[r] = 0.f;
       }
     }
@@ -295,19 +309,21 @@ __global__ void hd_prep_kernel(const float* __restrict__ X, const int64_t* n_dev
 // through a 4-stage TMA ring in 128B-swizzled 256x64 tiles. Accumulators are
 // double-buffered in TMEM (2 x 256 columns) so the epilogue of tile t
 // overlaps the MMAs of tile t+1.
-// Warps: 0 = TMA producer, 1 = MMA issuer (and TMEM owner), 2..5 = epilogue
-// (warp w reads TMEM lanes 32*(w%4) .. +31).
-// The MMA computes v = (-2 h_a) . h_b. Epilogue per element:
-//   t = v + ||h_b||^2  -> row min (plus ||h_a||^2 at the end) = d^2 row min
-//   d2 = t + ||h_a||^2 -> warp min over 32 rows (redux.sync.min.f32),
-//   combined over the 4 epilogue warps in shared memory, then one global
-//   atomicMin per column per tile (clamped at 0 so unsigned order = float order).
+// Warps: 0 = TMA producer, 1 = MMA issuer (and TMEM owner), 2..9 = epilogue
+// (warp w reads TMEM lanes 32*(w%4) .. +31 and half (w-2)/4 of the columns).
+// Before a tile's MMAs the epilogue preloads its accumulator with
+// ||h_a||^2 + ||h_b||^2 (tcgen05.st), and the MMAs add (-2 h_a) . h_b, so
+// the accumulator holds the squared distance d2 of every pair. Epilogue per
+// element: row min (registers) and the warp min over 32 rows
+// (redux.sync.min.f32), combined over the four lane quarters in shared
+// memory, then one global atomicMin per column per tile (clamped at 0 so
+// unsigned order = float order).
 
 constexpr int kTcBM = 128, kTcBN = 256, kTcBK = 64, kTcStages = 4;
 constexpr int kTcAKBytes = kTcBM * kTcBK * 2;   // 16 KB per A K-block
 constexpr int kTcBStage = kTcBN * kTcBK * 2;    // 32 KB per B stage
-constexpr int kTcThreads = 192;
-constexpr int kTcEpiWarps = 4;
+constexpr int kTcEpiWarps = 8;
+constexpr int kTcThreads = (2 + kTcEpiWarps) * 32;
 
 struct TcSmem {
   uint64_t b_full[kTcStages], b_empty[kTcStages];
@@ -317,7 +333,8 @@ struct TcSmem {
   uint32_t tmem_base;
   int abort;
   float nb[2][kTcBN];
-  float col[kTcEpiWarps][kTcBN];
+  float col[2][4][kTcBN];  // [tile parity][lane quarter][column]
+  float rowx[kTcBM];        // second half's row minima at the end of a row block
 };
 
 __host__ __device__ constexpr size_t tc_smem_bytes(int KB) {
@@ -415,7 +432,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
         aph ^= 1;
         tc_fence_after();
         for (int cb = 0; cb < CB && ok; ++cb) {
-          if (!mbar_wait_bounded(&S.acc_empty[ab], aph2 ^ 1, abort, timeout_ns)) { ok = false; break; }
+          if (!mbar_wait_bounded(&S.acc_empty[ab], aph2, abort, timeout_ns)) { ok = false; break; }
           tc_fence_after();
           const uint32_t d_tmem = tmem + (uint32_t)(ab * kTcBN);
           for (int kb = 0; kb < KB; ++kb) {
@@ -425,8 +442,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
             const uint32_t b_addr = smem_u32(sB + st * kTcBStage);
 #pragma unroll
             for (int k = 0; k < kTcBK / 16; ++k)
-              tc_mma_f16(d_tmem, smem_desc_sw128(a_addr + k * 32), smem_desc_sw128(b_addr + k * 32), idesc,
-                         (kb | k) != 0);
+              tc_mma_f16(d_tmem, smem_desc_sw128(a_addr + k * 32), smem_desc_sw128(b_addr + k * 32), idesc, 1u);
             tc_commit(&S.b_empty[st]);
             if (++st == kTcStages) { st = 0; ph ^= 1; }
           }
@@ -444,68 +460,95 @@ __global__ void __launch_bounds__(kTcThreads, 1)
       }
     }
   } else {
-    // ---------------- epilogue (warps 2..5) ----------------
+    // ---------------- epilogue (warps 2..9) ----------------
     // Every epilogue warp runs the same tile loop and reaches every named
     // barrier even after an abort (then it only skips the work), so the
     // barriers cannot wait on a warp that left early.
-    const int ew = warp - 2;          // 0..3
-    const int q = warp & 3;           // TMEM lane quarter this warp may access
-    const int et = threadIdx.x - 64;  // 0..127
-    uint32_t ab = 0, aph2 = 0;
-    int tcount = 0;
+    const int ew = warp - 2;           // 0..7
+    const int q = warp & 3;            // TMEM lane quarter this warp may access
+    const int hcol = (ew >> 2) * (kTcBN / 2);  // first column of this warp's half
+    const int et = threadIdx.x - 64;   // 0..255
+    const int nrb = (int)blockIdx.x < RB ? (RB - (int)blockIdx.x + (int)gridDim.x - 1) / (int)gridDim.x : 0;
+    const int ntile = nrb * CB;
     bool ok = true;
-    for (int rb = blockIdx.x; rb < RB; rb += gridDim.x) {
-      const int64_t row = (int64_t)rb * kTcBM + q * 32 + lane;
-      const float na = nA2[row];
-      float rmin = __int_as_float(0x7f800000);
-      for (int cb = 0; cb < CB; ++cb, ++tcount) {
-        const int nbuf = tcount & 1;
-        S.nb[nbuf][et] = nB2[(int64_t)cb * kTcBN + et];
-        S.nb[nbuf][et + 128] = nB2[(int64_t)cb * kTcBN + et + 128];
-        named_bar_sync(1, 128);
-        int got = 0;
-        if (ok && lane == 0) got = mbar_wait_bounded(&S.acc_full[ab], aph2, abort, timeout_ns) ? 1 : 0;
-        got = __shfl_sync(0xffffffffu, got, 0);
-        ok = ok && got;
-        if (ok) {
-          tc_fence_after();
-          const uint32_t taddr = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(ab * kTcBN);
-          float v[32];
+    // accumulator preload for tile i into buffer buf: ||h_a||^2 + ||h_b||^2
+    auto preload = [&](int i, int buf) {
+      const int prb = (int)blockIdx.x + (i / CB) * (int)gridDim.x, pcb = i % CB;
+      S.nb[buf][et] = nB2[(int64_t)pcb * kTcBN + et];
+      named_bar_sync(1, 32 * kTcEpiWarps);
+      if (!ok) return;
+      const float na_p = nA2[(int64_t)prb * kTcBM + q * 32 + lane];
+      const uint32_t taddr = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(buf * kTcBN + hcol);
 #pragma unroll 1
-          for (int ch = 0; ch < kTcBN / 32; ++ch) {
-            __syncwarp();
-            tc_ld_32x32b_x32(taddr + ch * 32, v);
-            tc_wait_ld();
-            float cm[32];
+      for (int ch = 0; ch < kTcBN / 2 / 32; ++ch) {
+        float v[32];
 #pragma unroll
-            for (int c = 0; c < 32; ++c) {
-              float t = v[c] + S.nb[nbuf][ch * 32 + c];
-              rmin = fminf(rmin, t);
-              cm[c] = redux_min_f32(t + na);
-            }
-            if (lane == 0) {
-              float4* dst = reinterpret_cast<float4*>(&S.col[ew][ch * 32]);
-#pragma unroll
-              for (int c = 0; c < 8; ++c)
-                dst[c] = make_float4(cm[4 * c], cm[4 * c + 1], cm[4 * c + 2], cm[4 * c + 3]);
-            }
-          }
-          tc_fence_before();
+        for (int c = 0; c < 32; ++c) v[c] = na_p + S.nb[buf][hcol + ch * 32 + c];
+        __syncwarp();
+        tc_st_32x32b_x32(taddr + ch * 32, v);
+      }
+      tc_wait_st();
+    };
+    for (int i = 0; i < 2 && i < ntile; ++i) {
+      preload(i, i);
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&S.acc_empty[i]);
+    }
+    float rmin = __int_as_float(0x7f800000);
+    for (int i = 0; i < ntile; ++i) {
+      const int ab = i & 1;
+      const uint32_t par = (uint32_t)(i >> 1) & 1u;
+      const int rb = (int)blockIdx.x + (i / CB) * (int)gridDim.x, cb = i % CB;
+      int got = 0;
+      if (ok && lane == 0) got = mbar_wait_bounded(&S.acc_full[ab], par, abort, timeout_ns) ? 1 : 0;
+      got = __shfl_sync(0xffffffffu, got, 0);
+      ok = ok && got;
+      if (ok) {
+        tc_fence_after();
+        const uint32_t taddr = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(ab * kTcBN + hcol);
+        float v[32];
+#pragma unroll 1
+        for (int ch = 0; ch < kTcBN / 2 / 32; ++ch) {
           __syncwarp();
-          if (lane == 0) mbar_arrive(&S.acc_empty[ab]);
-        }
-        ab ^= 1;
-        if (ab == 0) aph2 ^= 1;
-        named_bar_sync(1, 128);
-        if (ok) {
-          for (int c = et; c < kTcBN; c += 128) {
-            float m = fminf(fminf(S.col[0][c], S.col[1][c]), fminf(S.col[2][c], S.col[3][c]));
-            m = fmaxf(m, 0.f);
-            atomicMin(colmin + (int64_t)cb * kTcBN + c, __float_as_uint(m));
+          tc_ld_32x32b_x32(taddr + ch * 32, v);
+          tc_wait_ld();
+          float cm[32];
+#pragma unroll
+          for (int c = 0; c < 32; ++c) {
+            rmin = fminf(rmin, v[c]);
+            cm[c] = redux_min_f32(v[c]);
+          }
+          if (lane == 0) {
+            float4* dst = reinterpret_cast<float4*>(&S.col[ab][q][hcol + ch * 32]);
+#pragma unroll
+            for (int c = 0; c < 8; ++c)
+              dst[c] = make_float4(cm[4 * c], cm[4 * c + 1], cm[4 * c + 2], cm[4 * c + 3]);
           }
         }
       }
-      if (ok) rowmin[row] = rmin + na;
+      // refill this buffer for tile i + 2 (the MMA waits for it)
+      if (i + 2 < ntile) preload(i + 2, ab);
+      else named_bar_sync(1, 32 * kTcEpiWarps);
+      if (ok) {
+        tc_fence_before();
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&S.acc_empty[ab]);
+      }
+      named_bar_sync(1, 32 * kTcEpiWarps);
+      if (ok) {
+        const int c = et;
+        float m = fminf(fminf(S.col[ab][0][c], S.col[ab][1][c]), fminf(S.col[ab][2][c], S.col[ab][3][c]));
+        m = fmaxf(m, 0.f);
+        atomicMin(colmin + (int64_t)cb * kTcBN + c, __float_as_uint(m));
+      }
+      if (cb == CB - 1) {
+        // the two warps of a lane quarter saw one half of the columns each
+        if (ew >= 4) S.rowx[q * 32 + lane] = rmin;
+        named_bar_sync(1, 32 * kTcEpiWarps);
+        if (ok && ew < 4) rowmin[(int64_t)rb * kTcBM + q * 32 + lane] = fminf(rmin, S.rowx[q * 32 + lane]);
+        rmin = __int_as_float(0x7f800000);
+      }
     }
   }
 
@@ -834,7 +877,7 @@ cudaError_t hd_core(prohd_ctx* ctx, const float* A, const int64_t* nA_dev, int64
   PhaseTimer pt_prep(ctx, PROHD_PH_HD_PREP, st);
   cudaMemsetAsync(b.sc, 0, sizeof(HdScalars), st);
   count_launch();
-  hd_shift_kernel<<<1, 256, 0, st>>>(A, nA_dev, B, nB_dev, D, b.shift);
+  hd_shift_kernel<<<(D + 31) / 32, 256, 0, st>>>(A, nA_dev, B, nB_dev, D, b.shift);
   count_launch();
   hd_maxabs_kernel<<<nsm * 4, 256, 0, st>>>(A, nA_dev, D, b.shift, &b.sc->maxabs, status_dev);
   count_launch();

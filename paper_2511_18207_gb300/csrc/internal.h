@@ -104,6 +104,14 @@ cudaError_t directions_run(prohd_ctx* ctx, const float* A, int64_t nA, const flo
                            int max_iters, double tol, uint64_t seed, double* dirs, double* eig, int* status_dev,
                            Arena& ws, cudaStream_t st);
 
+// ---- tensor-core Gram (gram_tc.cu) ----
+constexpr int kMaxSms = 192;  // upper bound used to size per-CTA scratch
+bool gram_tc_supported(int D);
+size_t gram_tc_scratch_doubles(int D, int num_sms);
+cudaError_t gram_tc_run(prohd_ctx* ctx, const float* A, int64_t nA, const float* B, int64_t nB, int D,
+                        const float* s32, double* scratch, double* G, double* sumA, double* sumB, int* status,
+                        int64_t timeout_ns, cudaStream_t st);
+
 // ---- small utilities (api.cu) ----
 cudaError_t set_i64(int64_t* p, int64_t v, cudaStream_t st);
 cudaError_t zero_i32(int* p, int n, cudaStream_t st);

@@ -6,9 +6,13 @@ most 16 terms before FP64, so each component of a set's mean is within
 2 ||err(ybar - xbar)|| / ||ybar - xbar||, the bound asserted below.
 Principal components are compared by angle: both sides stop when
 1 - |cos| between steps falls below tol, leaving about sqrt(2 tol)/(1 - ratio)
-each (ratio = lambda_{l+1}/lambda_l); the GPU's covariance (FP32 partial sums
-of at most 32 x 32 products, FP64 across) perturbs C by <= ~2e-6 ||C||, which
-moves component l by at most that over its eigengap."""
+each (ratio = lambda_{l+1}/lambda_l). The GPU's covariance is accumulated on
+tensor cores from an exact three-way BF16 split of every centred value (six
+products, each within ~2^-24 of z_i z_j), summed in FP32 over 512 points
+(3072 exact products; random-walk error ~sqrt(3072) 2^-24 = 3.3e-6 relative)
+and in FP64 beyond; 1e-5 ||C|| (3x that) bounds the perturbation, which moves
+component l by at most that over its eigengap and eigenvalue l by at most that
+absolutely."""
 import numpy as np
 import pytest
 
@@ -54,11 +58,11 @@ def test_directions_anisotropic(D, m):
     for l in range(1, m + 1):
         ratio = lam[l] / lam[l - 1]
         gap = min(lam[l - 1] - lam[l], lam[l - 2] - lam[l - 1] if l >= 2 else np.inf)
-        tolang = 2 * (2 * np.sqrt(2e-13) / (1 - ratio)) + 2e-6 * lam[0] / gap + 1e-6 / (1 - ratio)
+        tolang = 2 * (2 * np.sqrt(2e-13) / (1 - ratio)) + 1e-5 * lam[0] / gap + 1e-6 / (1 - ratio)
         assert _angle(g[l], o[l]) <= tolang, (l, _angle(g[l], o[l]), tolang)
         # same sign convention
         assert float(np.dot(g[l], o[l])) > 0
-    np.testing.assert_allclose(ge, oe, rtol=1e-5)
+    np.testing.assert_allclose(ge, oe, rtol=0, atol=1e-5 * oe[0])
 
 
 def test_directions_centroid_fallback_and_small():
@@ -76,4 +80,4 @@ def test_directions_config_small():
     g, ge = _gpu_dirs(A, B, 2)
     o, oe, _ = oracle.directions(A, B, m=2, seed=0)
     assert np.linalg.norm(g[0] - o[0]) <= _axis_bound(A, B)
-    np.testing.assert_allclose(ge, oe, rtol=1e-5)
+    np.testing.assert_allclose(ge, oe, rtol=0, atol=1e-5 * oe[0])
