@@ -319,12 +319,33 @@ __device__ void block_sums(double (&v)[KMAX], int K, double* sh /*[8][KMAX]*/, d
   __syncthreads();
 }
 
+// Batched block sums of K FP32 values per thread (K <= KMAX), fixed order.
+template <int KMAX>
+__device__ void block_sums_f32(float (&v)[KMAX], int K, float* sh /*[8][KMAX]*/, float* out /*[KMAX]*/) {
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+#pragma unroll
+  for (int k = 0; k < KMAX; ++k) {
+    if (k >= K) break;
+    float x = warp_sum(v[k]);
+    if (l == 0) sh[w * KMAX + k] = x;
+  }
+  __syncthreads();
+  if (threadIdx.x < K) {
+    float s = 0.f;
+    for (int ww = 0; ww < kPiThreads / 32; ++ww) s += sh[ww * KMAX + threadIdx.x];
+    out[threadIdx.x] = s;
+  }
+  __syncthreads();
+}
+
 struct PiSmem {
   float w_recv[2][kPiMaxD];
   float v32[kPiMaxD];
   double v64[kPiMaxD];
   double red_sh[8 * 32];
   double red_out[32];
+  float red_shf[8 * 32];
+  float red_outf[32];
   double lam_part[kPiCTAs];
   int flag[2];
 };
@@ -334,7 +355,8 @@ struct PiSmem {
 // copy of the finished components: [kPiCTAs][m][D].
 __global__ void __cluster_dims__(kPiCTAs, 1, 1) __launch_bounds__(kPiThreads, 1)
     power_iter_kernel(const double* __restrict__ C64, const float* __restrict__ C32, int D, int m, int maxit,
-                      double tol, uint64_t seed, int c_in_smem, double* __restrict__ dirs, double* __restrict__ eig,
+                      double tol, uint64_t seed, int c_in_smem, int u_in_smem, double* __restrict__ dirs,
+                      double* __restrict__ eig,
                       double* __restrict__ U64all, float* __restrict__ U32all) {
   extern __shared__ __align__(16) uint8_t pism[];
   PiSmem& S = *reinterpret_cast<PiSmem*>(pism);
@@ -353,8 +375,12 @@ __global__ void __cluster_dims__(kPiCTAs, 1, 1) __launch_bounds__(kPiThreads, 1)
   __syncthreads();
   cluster_sync();
 
-  constexpr int KM = 8;  // components deflated per batched reduction (register-resident)
+  constexpr int KM = 12;  // values per batched block reduction (register-resident)
   double part[KM];
+  const int rows_warp = (rows_per + kPiThreads / 32 - 1) / (kPiThreads / 32);
+  // finished components in FP32 for the per-step Gram-Schmidt: shared memory when they fit
+  float* Us = reinterpret_cast<float*>(pism + sizeof(PiSmem) + (c_in_smem ? (size_t)rows_per * D * sizeof(float) : 0));
+  float* Uf = u_in_smem ? Us : U32;
 
   for (int l = 1; l <= m; ++l) {
     const int np = l - 1;  // previous components
@@ -396,70 +422,108 @@ __global__ void __cluster_dims__(kPiCTAs, 1, 1) __launch_bounds__(kPiThreads, 1)
     bool stop_local = false;  // CTA 0's decision, sent with the next step
     for (int t = 1; t <= maxit + 1; ++t) {
       const int buf = t & 1;
-      // ---- w = C v for this CTA's rows, scattered to every CTA
-      for (int r = r0 + warp; r < r1; r += kPiThreads / 32) {
-        const float* cr = Crow + (size_t)(r - r0) * D;
-        // compensated dot product (Ogita-Rump-Oishi Dot2): the FP32 result is
-        // as accurate as if it were accumulated in twice the precision, so the
-        // iterate does not jitter above the stop tolerance
-        float s = 0.f, c = 0.f;
+      // ---- w = C v for this CTA's rows, scattered to every CTA. Each warp
+      // runs up to 4 rows (r0 + warp + 8 j) as independent compensated
+      // (Ogita-Rump-Oishi Dot2) dot products: the FP32 result is as accurate
+      // as twice-the-precision accumulation, so the iterate does not jitter
+      // above the stop tolerance.
+      for (int j0 = 0; j0 < rows_warp; j0 += 4) {
+        float sum[4] = {0.f, 0.f, 0.f, 0.f}, cmp[4] = {0.f, 0.f, 0.f, 0.f};
         for (int k = lane; k < D; k += 32) {
-          const float a = cr[k], b = S.v32[k];
-          const float p = a * b;
-          const float pe = fmaf(a, b, -p);
-          const float t = s + p;
-          const float z = t - s;
-          c += (s - (t - z)) + (p - z) + pe;
-          s = t;
+          const float b = S.v32[k];
+#pragma unroll
+          for (int u = 0; u < 4; ++u) {
+            const int r = r0 + warp + 8 * (j0 + u);
+            if (r < r1) {
+              const float a = Crow[(size_t)(r - r0) * D + k];
+              const float pr = a * b;
+              const float pe = fmaf(a, b, -pr);
+              const float tt = sum[u] + pr;
+              const float z = tt - sum[u];
+              cmp[u] += (sum[u] - (tt - z)) + (pr - z) + pe;
+              sum[u] = tt;
+            }
+          }
         }
-        for (int o = 16; o > 0; o >>= 1) {
-          const float so = __shfl_xor_sync(0xffffffffu, s, o), co = __shfl_xor_sync(0xffffffffu, c, o);
-          const float t = s + so;
-          const float z = t - s;
-          c += co + (s - (t - z)) + (so - z);
-          s = t;
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          float sv = sum[u], cv = cmp[u];
+          for (int o = 16; o > 0; o >>= 1) {
+            const float so = __shfl_xor_sync(0xffffffffu, sv, o), co = __shfl_xor_sync(0xffffffffu, cv, o);
+            const float tt = sv + so;
+            const float z = tt - sv;
+            cv += co + (sv - (tt - z)) + (so - z);
+            sv = tt;
+          }
+          const int r = r0 + warp + 8 * (j0 + u);
+          if (r < r1 && lane < kPiCTAs) st_cluster_f32(map_to_cta(&S.w_recv[buf][r], lane), sv + cv);
         }
-        if (lane < kPiCTAs) st_cluster_f32(map_to_cta(&S.w_recv[buf][r], lane), s + c);
       }
       if (rank == 0 && tid < kPiCTAs) st_cluster_s32(map_to_cta(&S.flag[buf], tid), stop_local ? 1 : 0);
       cluster_sync();
       if (S.flag[buf] || t > maxit) break;  // v holds the result of the previous step
-      // ---- Gram-Schmidt (FP32, twice) against previous components
       float* w = S.w_recv[buf];
-      for (int pass = 0; pass < 2; ++pass)
+      // ---- Gram-Schmidt (FP32, twice) against the previous components. The
+      // projections are small corrections and are reduced in FP32; the second
+      // pass shares its reduction with ||w||^2 and <w, v_old>, which warp 0
+      // sums in FP64 (FP64 arithmetic is scarce on this GPU, so only one warp
+      // does it). With orthonormal u_k, ||w - sum d_k u_k||^2 = ||w||^2 -
+      // sum d_k^2, and <u_k, v_old> vanishes to rounding.
+      const bool merged = np <= KM;
+      for (int pass = 0; pass < (merged ? 1 : 2); ++pass)
         for (int k0 = 0; k0 < np; k0 += KM) {
           const int kk = min(KM, np - k0);
+          float pf[KM];
 #pragma unroll
-          for (int k = 0; k < KM; ++k) part[k] = 0.0;
+          for (int k = 0; k < KM; ++k) pf[k] = 0.f;
           for (int j = tid; j < D; j += kPiThreads)
 #pragma unroll
             for (int k = 0; k < KM; ++k)
-              if (k < kk) part[k] += (double)(U32[(size_t)(k0 + k) * D + j] * w[j]);
-          block_sums<KM>(part, kk, S.red_sh, S.red_out);
+              if (k < kk) pf[k] = fmaf(Uf[(size_t)(k0 + k) * D + j], w[j], pf[k]);
+          block_sums_f32<KM>(pf, kk, S.red_shf, S.red_outf);
           for (int j = tid; j < D; j += kPiThreads) {
             float x = w[j];
-            for (int k = 0; k < kk; ++k) x -= (float)S.red_out[k] * U32[(size_t)(k0 + k) * D + j];
+            for (int k = 0; k < kk; ++k) x -= S.red_outf[k] * Uf[(size_t)(k0 + k) * D + j];
             w[j] = x;
           }
           __syncthreads();
         }
-      // ---- ||w||^2 and <w, v_old> in FP64
-      double nn = 0.0, dv = 0.0;
-      for (int j = tid; j < D; j += kPiThreads) {
-        const double x = (double)w[j];
-        nn += x * x;
-        dv += x * S.v64[j];
-      }
+      const int nq = merged ? np : 0;
+      {
+        float pf[KM];
 #pragma unroll
-      for (int k = 0; k < KM; ++k) part[k] = 0.0;
-      part[0] = nn;
-      part[1] = dv;
-      block_sums<KM>(part, 2, S.red_sh, S.red_out);
-      const double nw = sqrt(S.red_out[0]);
+        for (int k = 0; k < KM; ++k) pf[k] = 0.f;
+        for (int j = tid; j < D; j += kPiThreads)
+#pragma unroll
+          for (int k = 0; k < KM; ++k)
+            if (k < nq) pf[k] = fmaf(Uf[(size_t)k * D + j], w[j], pf[k]);
+        if (warp == 0) {
+          double nn = 0.0, dv = 0.0;
+          for (int j = lane; j < D; j += 32) {
+            const double x = (double)w[j];
+            nn = fma(x, x, nn);
+            dv = fma(x, S.v64[j], dv);
+          }
+          nn = warp_sum(nn);
+          dv = warp_sum(dv);
+          if (lane == 0) {
+            S.red_out[0] = nn;
+            S.red_out[1] = dv;
+          }
+        }
+        block_sums_f32<KM>(pf, nq, S.red_shf, S.red_outf);  // its barriers also publish warp 0's sums
+      }
+      double nsq = S.red_out[0];
+      for (int k = 0; k < nq; ++k) nsq -= (double)S.red_outf[k] * (double)S.red_outf[k];
+      const double nw = sqrt(fmax(nsq, 0.0));
       const double cosv = nw > 0.0 ? fabs(S.red_out[1]) / nw : 1.0;
+      // the second-pass correction is applied in FP64: an FP32 update would
+      // move ||x|| away from nw by ~1e-8 and fake convergence at the next step
       if (nw > 0.0)
         for (int j = tid; j < D; j += kPiThreads) {
-          S.v64[j] = (double)w[j] / nw;
+          double x = (double)w[j];
+          for (int k = 0; k < nq; ++k) x -= (double)S.red_outf[k] * (double)Uf[(size_t)k * D + j];
+          S.v64[j] = x / nw;
           S.v32[j] = (float)S.v64[j];
         }
       stop_local = (nw == 0.0) || (1.0 - cosv < tol);
@@ -525,7 +589,7 @@ __global__ void __cluster_dims__(kPiCTAs, 1, 1) __launch_bounds__(kPiThreads, 1)
         const double x = sgn * S.v64[j];
         S.v64[j] = x;
         U64[(size_t)np * D + j] = x;
-        U32[(size_t)np * D + j] = (float)x;
+        Uf[(size_t)np * D + j] = (float)x;
         if (rank == 0) dirs[(size_t)l * D + j] = x;
       }
       __syncthreads();
@@ -570,13 +634,11 @@ struct DirBufs {
 
 static void dir_layout(Arena& ws, int D, int m, DirBufs& b) {
   b.s32 = ws.take<float>((size_t)D);
-  if (gram_tc_supported(D)) {
-    b.gc_scratch = ws.take<double>(gram_tc_scratch_doubles(D, kMaxSms));
-  } else {
-    b.Gpart = ws.take<double>((size_t)kMaxSplit * D * D);
-    b.sumApart = ws.take<double>((size_t)kMaxSplit * D);
-    b.sumBpart = ws.take<double>((size_t)kMaxSplit * D);
-  }
+  if (gram_tc_supported(D)) b.gc_scratch = ws.take<double>(gram_tc_scratch_doubles(D, kMaxSms));
+  // CUDA-core Gram (D > 256, D % 4 != 0 or unaligned inputs)
+  b.Gpart = ws.take<double>((size_t)kMaxSplit * D * D);
+  b.sumApart = ws.take<double>((size_t)kMaxSplit * D);
+  b.sumBpart = ws.take<double>((size_t)kMaxSplit * D);
   b.G = ws.take<double>((size_t)D * D);
   b.sumA = ws.take<double>((size_t)D);
   b.sumB = ws.take<double>((size_t)D);
@@ -604,7 +666,8 @@ cudaError_t directions_run(prohd_ctx* ctx, const float* A, int64_t nA, const flo
   const int nsm = ctx->num_sms;
   count_launch();
   pilot_shift_kernel<<<(D + 31) / 32, 256, 0, st>>>(A, nA, D, b.s32);
-  if (gram_tc_supported(D) && ctx->num_sms <= kMaxSms) {
+  const bool aligned = ((reinterpret_cast<uintptr_t>(A) | reinterpret_cast<uintptr_t>(B)) & 15) == 0;
+  if (gram_tc_supported(D) && aligned && ctx->num_sms <= kMaxSms && ctx->encode_tiled) {
     if ((e = gram_tc_run(ctx, A, nA, B, nB, D, b.s32, b.gc_scratch, b.G, b.sumA, b.sumB, status_dev,
                          kDefaultTimeoutNs, st)))
       return e;
@@ -633,13 +696,15 @@ cudaError_t directions_run(prohd_ctx* ctx, const float* A, int64_t nA, const flo
   if (m > 0) {
     const int rows_per = (D + kPiCTAs - 1) / kPiCTAs;
     size_t cbytes = (size_t)rows_per * D * sizeof(float);
-    int c_in_smem = sizeof(PiSmem) + cbytes <= (size_t)200 * 1024 ? 1 : 0;
-    size_t smem = sizeof(PiSmem) + (c_in_smem ? cbytes : 0);
+    int c_in_smem = sizeof(PiSmem) + cbytes <= (size_t)160 * 1024 ? 1 : 0;
+    const size_t ubytes = (size_t)m * D * sizeof(float);
+    int u_in_smem = sizeof(PiSmem) + (c_in_smem ? cbytes : 0) + ubytes <= (size_t)200 * 1024 ? 1 : 0;
+    size_t smem = sizeof(PiSmem) + (c_in_smem ? cbytes : 0) + (u_in_smem ? ubytes : 0);
     cudaFuncSetAttribute(power_iter_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     PhaseTimer pt_pow(ctx, PROHD_PH_POWER, st);
     count_launch();
-    power_iter_kernel<<<kPiCTAs, kPiThreads, smem, st>>>(b.C64, b.C32, D, m, max_iters, tol, seed, c_in_smem, dirs,
-                                                         eig, b.U64, b.U32);
+    power_iter_kernel<<<kPiCTAs, kPiThreads, smem, st>>>(b.C64, b.C32, D, m, max_iters, tol, seed, c_in_smem,
+                                                         u_in_smem, dirs, eig, b.U64, b.U32);
     if ((e = cudaGetLastError())) return e;
   }
   return cudaSuccess;

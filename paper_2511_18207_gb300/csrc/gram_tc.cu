@@ -1,6 +1,6 @@
 // Union Gram G = sum_z (z - s)(z - s)^T and per-set sums of z - s on tcgen05
 // tensor cores (Algorithm 2 step 2: principal components of [A; B] need the
-// union covariance), for D <= 256.
+// union covariance), for D <= 256 with D % 4 == 0.
 //
 // Each FP32 centred value z is split exactly into three BF16 parts
 // z = h + m + l (h = bf16(z), m = bf16(z - h), l = bf16(z - h - m); the
@@ -11,17 +11,19 @@
 // accumulator in global memory (covariance accumulation in FP64 across rows
 // and CTAs), and a final kernel sums the CTAs in a fixed order.
 //
-// The input is row-major [points, D], i.e. the Gram's M/N index (the
-// dimension) is the contiguous one. Converter warps therefore transpose while
-// they split: they read 8 points x (32 lanes x T dims) with coalesced loads
-// and write each dimension's 8 consecutive points as one 16-byte chunk of a
-// K-major, 128B-swizzled BF16 tile [dims x 64 points] (the layout the
-// distance contraction also feeds to tcgen05.mma).
+// Pipeline per CTA: a TMA warp streams FP32 tiles [64 points x up to 256
+// dims] through a two-stage ring; eight converter warps read them from shared
+// memory, centre, split and transpose them into one K-major, 128B-swizzled
+// BF16 stage [dims x 64 points] x {h, m, l} (the operand layout of the
+// distance contraction); one thread issues the 24 MMAs of a chunk; four
+// epilogue warps move finished 512-point partials from TMEM into FP64.
 //
 // Work split: CTAs of type 0 own output rows 0..127 against all Dp columns,
 // type 1 (when Dp > 128) rows 128..Dp-1 against columns 128..Dp-1; each type
-// covers all points, with CTA counts in proportion to their work per point.
-// Warps: 0..7 converters, 8 MMA issuer (and TMEM owner), 9..12 epilogue.
+// covers all points, with CTA counts in proportion to their work per point,
+// and every CTA's points lie in one set (A or B).
+// Warps: 0..7 converters, 8 MMA issuer (and TMEM owner), 9..12 epilogue,
+// 13 TMA producer.
 #include <cuda_bf16.h>
 
 #include <algorithm>
@@ -34,76 +36,90 @@ namespace prohd {
 constexpr int kGcPts = 64;          // points per chunk (one 128-byte K row of BF16)
 constexpr int kGcConv = 8;          // converter warps, 8 points each
 constexpr int kGcEpi = 4;
-constexpr int kGcThreads = (kGcConv + 1 + kGcEpi) * 32;
+constexpr int kGcMmaWarp = kGcConv;
+constexpr int kGcTmaWarp = kGcConv + 1 + kGcEpi;
+constexpr int kGcThreads = (kGcTmaWarp + 1) * 32;
 constexpr int kGcFlush = 8;         // chunks per FP32 accumulation in TMEM (512 points)
 constexpr int kGcMaxRows = 256;
 
-// Kahan-compensated s += (z + e) with compensation c.
-__device__ __forceinline__ void kahan_add(float& s, float& c, float z, float e) {
-  const float y = (z - c) + e;
+// Kahan-compensated s += x with compensation c.
+__device__ __forceinline__ void kahan_add(float& s, float& c, float x) {
+  const float y = x - c;
   const float t = s + y;
   c = (t - s) - y;
   s = t;
 }
 
 struct GcSmem {
-  uint64_t full[2], empty[2], acc_full[2], acc_empty[2], drain;
+  uint64_t ffull[2], fempty[2], bfull, bempty, acc_full[2], acc_empty[2], drain;
   uint32_t tmem_base;
   int abort;
 };
 
 __host__ __device__ constexpr size_t gc_tile_bytes(int rows) { return (size_t)rows * 128; }
-__host__ __device__ constexpr size_t gc_smem_bytes(int rows) {
-  return 1024 + 2 * 3 * gc_tile_bytes(rows) + sizeof(GcSmem);
+__host__ __device__ constexpr size_t gc_stage_bytes(int bw) { return (size_t)kGcPts * bw * 4; }
+__host__ __device__ constexpr size_t gc_smem_bytes(int rows, int bw) {
+  return 1024 + 3 * gc_tile_bytes(rows) + 2 * gc_stage_bytes(bw) + sizeof(GcSmem);
 }
 
 struct GcParams {
-  const float* A;
-  const float* B;
   int64_t nA, nB;
   int D, Dp;
   const float* s32;   // pilot shift [D]
   int nc0;            // CTAs of type 0 (the rest are type 1)
-  int rows0, rows1;   // tile rows loaded by each type (>= 128)
+  int ncA0, ncA1;     // CTAs of each type that read set A (the rest read B)
+  int rows0, rows1;   // tile rows (dims) of each type (>= 128, zero padded)
   int N0, N1;         // output columns of each type
+  int bw0, bw1;       // FP32 box width (dims) of each type
   double* gacc;       // [gridDim][256 x 128] FP64 partials, element (col, row) at col*128 + row
-  double* sums;       // [nc0][kGcConv][2][Dp] FP64 per-warp set sums of z - s
+  double* sums;       // [gridDim][kGcConv][2][Dp] FP64 per-warp set sums of z - s
   int* status;
   uint64_t timeout_ns;
 };
 
-// 13 warps: one SMSP holds 4 of them, so 16384 / (4 x 32) = 128 registers per thread at most.
-__global__ void __maxnreg__(128) gram_tc_kernel(const GcParams p) {
+// 14 warps: one SMSP holds 4 of them, so 16384 / (4 x 32) = 128 registers per thread at most.
+__global__ void __maxnreg__(128)
+    gram_tc_kernel(const GcParams p, const __grid_constant__ CUtensorMap tmA0, const __grid_constant__ CUtensorMap tmB0,
+                   const __grid_constant__ CUtensorMap tmA1, const __grid_constant__ CUtensorMap tmB1) {
   extern __shared__ uint8_t smem_raw[];
   uint8_t* base = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   const bool type0 = (int)blockIdx.x < p.nc0;
-  const int rows = type0 ? p.rows0 : p.rows1;     // tile rows (dims loaded, zero padded)
+  const int rows = type0 ? p.rows0 : p.rows1;  // tile rows (dims loaded, zero padded)
   const int N = type0 ? p.N0 : p.N1;
-  const int dim0 = type0 ? 0 : 128;               // first dimension loaded
+  const int dim0 = type0 ? 0 : 128;            // first dimension loaded
+  const int bw = type0 ? p.bw0 : p.bw1;
   const size_t tb = gc_tile_bytes(rows);
-  uint8_t* tiles = base;                           // [2][3][rows x 128 B]
-  GcSmem& S = *reinterpret_cast<GcSmem*>(base + 2 * 3 * tb);
+  uint8_t* tiles = base;                                   // [3][rows x 128 B]
+  float* stage = reinterpret_cast<float*>(base + 3 * tb);  // [2][64][bw]
+  GcSmem& S = *reinterpret_cast<GcSmem*>(base + 3 * tb + 2 * gc_stage_bytes(bw));
   volatile int* abort = &S.abort;
 
-  const int64_t Ntot = p.nA + p.nB;
-  const int nct = type0 ? p.nc0 : (int)gridDim.x - p.nc0;
+  // this CTA's set and point range
   const int ci = type0 ? (int)blockIdx.x : (int)blockIdx.x - p.nc0;
-  const int64_t p0 = Ntot * ci / nct, p1 = Ntot * (ci + 1) / nct;
+  const int nct = type0 ? p.nc0 : (int)gridDim.x - p.nc0;
+  const int ncA = type0 ? p.ncA0 : p.ncA1;
+  const bool setA = ci < ncA;
+  const int64_t n = setA ? p.nA : p.nB;
+  const int cj = setA ? ci : ci - ncA, ncj = setA ? ncA : nct - ncA;
+  const int64_t p0 = n * cj / ncj, p1 = n * (cj + 1) / ncj;
   const int nchunks = (int)((p1 - p0 + kGcPts - 1) / kGcPts);
+  const CUtensorMap* tm = type0 ? (setA ? &tmA0 : &tmB0) : (setA ? &tmA1 : &tmB1);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < 2; ++s) {
-      mbar_init(&S.full[s], kGcConv);
-      mbar_init(&S.empty[s], 1);
+      mbar_init(&S.ffull[s], 1);
+      mbar_init(&S.fempty[s], kGcConv);
       mbar_init(&S.acc_full[s], 1);
       mbar_init(&S.acc_empty[s], kGcEpi);
     }
+    mbar_init(&S.bfull, kGcConv);
+    mbar_init(&S.bempty, 1);
     mbar_init(&S.drain, 1);
     S.abort = 0;
     fence_mbar_init();
   }
-  if (warp == kGcConv) {
+  if (warp == kGcMmaWarp) {
     tc_alloc(&S.tmem_base, 512);
     tc_relinquish();
   }
@@ -112,133 +128,125 @@ __global__ void __maxnreg__(128) gram_tc_kernel(const GcParams p) {
   tc_fence_after();
   const uint32_t tmem = S.tmem_base;
 
-  if (warp < kGcConv) {
-    // ---------------- converters: load, centre, split, transpose ----------------
+  if (warp == kGcTmaWarp) {
+    // ---------------- TMA producer: FP32 point tiles into the 2-stage ring ----------------
+    if (lane == 0) {
+      tma_prefetch_desc(tm);
+      const uint32_t bytes = (uint32_t)gc_stage_bytes(bw);
+      uint32_t armed = 0;
+      for (int c = 0; c < nchunks; ++c) {
+        const int f = c & 1;
+        if (!mbar_wait_bounded(&S.fempty[f], ((uint32_t)(c >> 1) & 1u) ^ 1u, abort, p.timeout_ns)) break;
+        mbar_arrive_expect_tx(&S.ffull[f], bytes);
+        tma_load_2d(stage + (size_t)f * kGcPts * bw, tm, dim0, (int)(p0 + (int64_t)c * kGcPts), &S.ffull[f]);
+        armed = (uint32_t)c + 1;
+      }
+      if (*abort) {
+        // error path: let the copies already issued land before the CTA exits
+        for (uint32_t c = armed >= 2 ? armed - 2 : 0; c < armed; ++c) {
+          const uint64_t t0 = global_timer_ns();
+          while (!mbar_try_wait(&S.ffull[c & 1], (c >> 1) & 1u) && global_timer_ns() - t0 < 2000000ull) {
+          }
+        }
+      }
+    }
+  } else if (warp < kGcConv) {
+    // ---------------- converters: centre, split, transpose ----------------
     const int T = rows / 32;  // dims per lane: dim = dim0 + lane + 32 t
-    float sA[8], cA[8], sB[8], cB[8];
-#pragma unroll
-    for (int t = 0; t < 8; ++t) sA[t] = cA[t] = sB[t] = cB[t] = 0.f;
-    float shift[8];
+    float ss[8], sc[8], shift[8];
 #pragma unroll
     for (int t = 0; t < 8; ++t) {
+      ss[t] = sc[t] = 0.f;
       const int d = dim0 + lane + 32 * t;
       shift[t] = (t < T && d < p.D) ? p.s32[d] : 0.f;
     }
     bool bad = false;
-    uint32_t ph = 0;
     for (int c = 0; c < nchunks; ++c) {
-      const int s = c & 1;
+      const int f = c & 1;
       int got = 1;
-      if (lane == 0) got = mbar_wait_bounded(&S.empty[s], ph ^ 1, abort, p.timeout_ns) ? 1 : 0;
+      if (lane == 0) {
+        got = mbar_wait_bounded(&S.bempty, ((uint32_t)c & 1u) ^ 1u, abort, p.timeout_ns) &&
+              mbar_wait_bounded(&S.ffull[f], (uint32_t)(c >> 1) & 1u, abort, p.timeout_ns);
+      }
       got = __shfl_sync(0xffffffffu, got, 0);
       if (!got) break;
+      const float* st = stage + (size_t)f * kGcPts * bw + (size_t)(warp * 8) * bw;
       const int64_t pt0 = p0 + (int64_t)c * kGcPts + warp * 8;
-      const float* zrow[8];
 #pragma unroll
-      for (int i = 0; i < 8; ++i) {
-        const int64_t pt = pt0 + i;
-        zrow[i] = nullptr;
-        if (pt < p1) zrow[i] = pt < p.nA ? p.A + pt * p.D : p.B + (pt - p.nA) * p.D;
-      }
-      uint8_t* tH = tiles + (size_t)(s * 3 + 0) * tb;
-      uint8_t* tM = tiles + (size_t)(s * 3 + 1) * tb;
-      uint8_t* tL = tiles + (size_t)(s * 3 + 2) * tb;
-      // two halves of at most 4 dims per lane keep the staging in registers
+      for (int t = 0; t < 8; ++t) {
+        if (t >= T) break;
+        const int d = dim0 + lane + 32 * t;
+        const int dl = lane + 32 * t;  // column inside the staged box
+        const bool vd = d < p.D && dl < bw;
+        uint32_t hv[4], mv[4], lv[4];
+        float part = 0.f;
 #pragma unroll
-      for (int half = 0; half < 2; ++half) {
-        if (half * 4 >= T) break;
-        float x[8][4];
+        for (int i = 0; i < 8; i += 2) {
+          float h2[2], m2[2], l2[2];
 #pragma unroll
-        for (int i = 0; i < 8; ++i)
-#pragma unroll
-          for (int u = 0; u < 4; ++u) {
-            const int t = half * 4 + u;
-            const int d = dim0 + lane + 32 * t;
-            x[i][u] = (zrow[i] && t < T && d < p.D) ? __ldg(zrow[i] + d) : 0.f;
+          for (int j = 0; j < 2; ++j) {
+            const bool v = vd && pt0 + i + j < p1;
+            const float xv = v ? st[(size_t)(i + j) * bw + dl] : 0.f;
+            const float z = v ? xv - shift[t] : 0.f;
+            bad |= !isfinite(xv);
+            part += z;
+            const __nv_bfloat16 h = __float2bfloat16_rn(z);
+            const float r1 = z - __bfloat162float(h);
+            const __nv_bfloat16 m = __float2bfloat16_rn(r1);
+            h2[j] = __bfloat162float(h);
+            m2[j] = __bfloat162float(m);
+            l2[j] = r1 - m2[j];
           }
-#pragma unroll
-        for (int u = 0; u < 4; ++u) {
-          const int t = half * 4 + u;
-          if (t >= T) break;
-          const int d = dim0 + lane + 32 * t;
-          const bool vd = d < p.D;
-          uint32_t hv[4], mv[4], lv[4];
-#pragma unroll
-          for (int i = 0; i < 8; i += 2) {
-            float h2[2], m2[2], l2[2];
-#pragma unroll
-            for (int j = 0; j < 2; ++j) {
-              const int64_t pt = pt0 + i + j;
-              const bool v = vd && pt < p1;
-              const float xv = x[i + j][u];
-              const float z = v ? xv - shift[t] : 0.f;
-              bad |= v && !isfinite(xv);
-              const __nv_bfloat16 h = __float2bfloat16_rn(z);
-              const float r1 = z - __bfloat162float(h);
-              const __nv_bfloat16 m = __float2bfloat16_rn(r1);
-              const float r2 = r1 - __bfloat162float(m);
-              h2[j] = __bfloat162float(h);
-              m2[j] = __bfloat162float(m);
-              l2[j] = r2;
-              if (type0 && v) {
-                // exact error of the centring (two-sum), folded into Kahan sums of z + e
-                const float bb = z - xv;
-                const float e = (xv - (z - bb)) + (-shift[t] - bb);
-                if (pt < p.nA) kahan_add(sA[t], cA[t], z, e);
-                else kahan_add(sB[t], cB[t], z, e);
-              }
-            }
-            __nv_bfloat162 hh = __floats2bfloat162_rn(h2[0], h2[1]);
-            __nv_bfloat162 mm = __floats2bfloat162_rn(m2[0], m2[1]);
-            __nv_bfloat162 ll = __floats2bfloat162_rn(l2[0], l2[1]);
-            hv[i / 2] = *reinterpret_cast<uint32_t*>(&hh);
-            mv[i / 2] = *reinterpret_cast<uint32_t*>(&mm);
-            lv[i / 2] = *reinterpret_cast<uint32_t*>(&ll);
-          }
-          const int row = lane + 32 * t;
-          const size_t off = (size_t)row * 128 + (size_t)((warp ^ (row & 7)) * 16);
-          *reinterpret_cast<uint4*>(tH + off) = make_uint4(hv[0], hv[1], hv[2], hv[3]);
-          *reinterpret_cast<uint4*>(tM + off) = make_uint4(mv[0], mv[1], mv[2], mv[3]);
-          *reinterpret_cast<uint4*>(tL + off) = make_uint4(lv[0], lv[1], lv[2], lv[3]);
+          __nv_bfloat162 hh = __floats2bfloat162_rn(h2[0], h2[1]);
+          __nv_bfloat162 mm = __floats2bfloat162_rn(m2[0], m2[1]);
+          __nv_bfloat162 ll = __floats2bfloat162_rn(l2[0], l2[1]);
+          hv[i / 2] = *reinterpret_cast<uint32_t*>(&hh);
+          mv[i / 2] = *reinterpret_cast<uint32_t*>(&mm);
+          lv[i / 2] = *reinterpret_cast<uint32_t*>(&ll);
         }
+        kahan_add(ss[t], sc[t], part);
+        const int row = lane + 32 * t;
+        const size_t off = (size_t)row * 128 + (size_t)((warp ^ (row & 7)) * 16);
+        *reinterpret_cast<uint4*>(tiles + off) = make_uint4(hv[0], hv[1], hv[2], hv[3]);
+        *reinterpret_cast<uint4*>(tiles + tb + off) = make_uint4(mv[0], mv[1], mv[2], mv[3]);
+        *reinterpret_cast<uint4*>(tiles + 2 * tb + off) = make_uint4(lv[0], lv[1], lv[2], lv[3]);
       }
       fence_proxy_async();
       __syncwarp();
-      if (lane == 0) mbar_arrive(&S.full[s]);
-      if (s == 1) ph ^= 1;
+      if (lane == 0) {
+        mbar_arrive(&S.fempty[f]);
+        mbar_arrive(&S.bfull);
+      }
     }
-    if (type0) {
-      double* out = p.sums + ((size_t)blockIdx.x * kGcConv + warp) * 2 * p.Dp;
+    double* out = p.sums + ((size_t)blockIdx.x * kGcConv + warp) * 2 * p.Dp;
 #pragma unroll
-      for (int t = 0; t < 8; ++t) {
-        const int d = lane + 32 * t;
-        if (t < T && d < p.Dp) {
-          out[d] = (double)sA[t] - (double)cA[t];
-          out[p.Dp + d] = (double)sB[t] - (double)cB[t];
-        }
+    for (int t = 0; t < 8; ++t) {
+      const int d = dim0 + lane + 32 * t;
+      if (t < T && d < p.Dp) {
+        const double v = type0 ? (double)ss[t] - (double)sc[t] : 0.0;
+        out[(setA ? 0 : p.Dp) + d] = v;
+        out[(setA ? p.Dp : 0) + d] = 0.0;
       }
     }
     if (__any_sync(0xffffffffu, bad) && lane == 0) atomicMax(p.status, (int)PROHD_ENONFINITE);
-  } else if (warp == kGcConv) {
+  } else if (warp == kGcMmaWarp) {
     // ---------------- MMA issuer ----------------
     if (lane == 0) {
       const uint32_t idesc = idesc_f16(1, 128, N);
       // products (A part, B part): hh, hm, mh, hl, lh, mm
       const int pa[6] = {0, 0, 1, 0, 2, 1};
       const int pb[6] = {0, 1, 0, 2, 0, 1};
-      uint32_t ph = 0, ab = 0, aph = 0;
-      bool ok = true;
+      uint32_t ab = 0, aph = 0;
       int in_acc = 0;
-      for (int c = 0; c < nchunks && ok; ++c) {
-        const int s = c & 1;
+      for (int c = 0; c < nchunks; ++c) {
         if (in_acc == 0) {
-          if (!mbar_wait_bounded(&S.acc_empty[ab], aph ^ 1, abort, p.timeout_ns)) { ok = false; break; }
+          if (!mbar_wait_bounded(&S.acc_empty[ab], aph ^ 1, abort, p.timeout_ns)) break;
           tc_fence_after();
         }
-        if (!mbar_wait_bounded(&S.full[s], ph, abort, p.timeout_ns)) { ok = false; break; }
+        if (!mbar_wait_bounded(&S.bfull, (uint32_t)c & 1u, abort, p.timeout_ns)) break;
         tc_fence_after();
         const uint32_t d_tmem = tmem + ab * 256;
-        const uint32_t t0 = smem_u32(tiles + (size_t)(s * 3) * tb);
+        const uint32_t t0 = smem_u32(tiles);
 #pragma unroll
         for (int q = 0; q < 6; ++q) {
           const uint32_t a_addr = t0 + (uint32_t)(pa[q] * tb);
@@ -248,8 +256,7 @@ __global__ void __maxnreg__(128) gram_tc_kernel(const GcParams p) {
             tc_mma_f16(d_tmem, smem_desc_sw128(a_addr + k * 32), smem_desc_sw128(b_addr + k * 32), idesc,
                        (in_acc | q | k) != 0);
         }
-        tc_commit(&S.empty[s]);
-        if (s == 1) ph ^= 1;
+        tc_commit(&S.bempty);
         if (++in_acc == kGcFlush || c == nchunks - 1) {
           tc_commit(&S.acc_full[ab]);
           in_acc = 0;
@@ -270,7 +277,7 @@ __global__ void __maxnreg__(128) gram_tc_kernel(const GcParams p) {
     const int nflush = (nchunks + kGcFlush - 1) / kGcFlush;
     uint32_t ab = 0, aph = 0;
     bool ok = true;
-    for (int f = 0; f < nflush; ++f) {
+    for (int fl = 0; fl < nflush; ++fl) {
       int got = 0;
       if (ok && lane == 0) got = mbar_wait_bounded(&S.acc_full[ab], aph, abort, p.timeout_ns) ? 1 : 0;
       got = __shfl_sync(0xffffffffu, got, 0);
@@ -279,15 +286,18 @@ __global__ void __maxnreg__(128) gram_tc_kernel(const GcParams p) {
       tc_fence_after();
       const uint32_t taddr = tmem + ((uint32_t)(q * 32) << 16) + ab * 256;
       for (int cc = 0; cc < N / 32; ++cc) {
+        // issue the 32 loads of the running FP64 sums before any add, so
+        // their L2 latency overlaps instead of chaining load-add-store
+        double acc[32];
+        double* col0 = g + (size_t)(cc * 32) * 128 + row;
+#pragma unroll
+        for (int c = 0; c < 32; ++c) acc[c] = fl == 0 ? 0.0 : __ldcg(col0 + (size_t)c * 128);
         float v[32];
         __syncwarp();
         tc_ld_32x32b_x32(taddr + cc * 32, v);
         tc_wait_ld();
 #pragma unroll
-        for (int c = 0; c < 32; ++c) {
-          double* dst = g + (size_t)(cc * 32 + c) * 128 + row;
-          *dst = (f == 0 ? 0.0 : *dst) + (double)v[c];
-        }
+        for (int c = 0; c < 32; ++c) __stcg(col0 + (size_t)c * 128, acc[c] + (double)v[c]);
       }
       tc_fence_before();
       __syncwarp();
@@ -301,7 +311,7 @@ __global__ void __maxnreg__(128) gram_tc_kernel(const GcParams p) {
 
   __syncthreads();
   if (threadIdx.x == 0 && S.abort) atomicMax(p.status, (int)PROHD_ETIMEOUT);
-  if (warp == kGcConv) {
+  if (warp == kGcMmaWarp) {
     __syncwarp();
     tc_fence_after();
     tc_dealloc(tmem, 512);
@@ -340,7 +350,7 @@ __global__ void gram_tc_reduce_kernel(const GcParams p, int ncta, double* __rest
   }
 }
 
-bool gram_tc_supported(int D) { return D >= 1 && D <= kGcMaxRows; }
+bool gram_tc_supported(int D) { return D >= 4 && D <= kGcMaxRows && D % 4 == 0; }
 
 size_t gram_tc_scratch_doubles(int D, int num_sms) {
   const int Dp = (int)round_up(D, 64);
@@ -352,8 +362,6 @@ cudaError_t gram_tc_run(prohd_ctx* ctx, const float* A, int64_t nA, const float*
                         int64_t timeout_ns, cudaStream_t st) {
   const int nsm = ctx->num_sms;
   GcParams p;
-  p.A = A;
-  p.B = B;
   p.nA = nA;
   p.nB = nB;
   p.D = D;
@@ -363,25 +371,48 @@ cudaError_t gram_tc_run(prohd_ctx* ctx, const float* A, int64_t nA, const float*
   p.rows0 = std::max(128, p.Dp);
   p.N1 = p.Dp > 128 ? p.Dp - 128 : 0;
   p.rows1 = 128;
+  p.bw0 = (int)std::min<int64_t>(256, round_up(D, 32));
+  p.bw1 = p.N1 > 0 ? (int)round_up(D - 128, 32) : 32;
+  const int grid = nsm;
   if (p.N1 > 0) {
     // CTA counts in proportion to work per point (output columns)
     p.nc0 = (int)std::lround((double)nsm * p.N0 / (double)(p.N0 + p.N1));
-    p.nc0 = std::min(std::max(p.nc0, 1), nsm - 1);
+    p.nc0 = std::min(std::max(p.nc0, 2), nsm - 2);
   } else {
     p.nc0 = nsm;
   }
+  auto split = [&](int nct) {
+    int a = (int)std::lround((double)nct * (double)nA / (double)(nA + nB));
+    return std::min(std::max(a, 1), nct - 1);
+  };
+  p.ncA0 = split(p.nc0);
+  p.ncA1 = p.N1 > 0 ? split(grid - p.nc0) : 0;
   p.gacc = scratch;
   p.sums = scratch + (size_t)nsm * 256 * 128;
   p.status = status;
   p.timeout_ns = (uint64_t)timeout_ns;
-  const size_t smem = gc_smem_bytes(p.rows0);
+  CUtensorMap tA0, tB0, tA1, tB1;
+  const uint64_t rowb = (uint64_t)D * 4;
+  if (!encode_2d(ctx, &tA0, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, A, (uint64_t)D, (uint64_t)nA, rowb, p.bw0, kGcPts,
+                 CU_TENSOR_MAP_SWIZZLE_NONE) ||
+      !encode_2d(ctx, &tB0, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, B, (uint64_t)D, (uint64_t)nB, rowb, p.bw0, kGcPts,
+                 CU_TENSOR_MAP_SWIZZLE_NONE))
+    return cudaErrorInvalidValue;
+  tA1 = tA0;
+  tB1 = tB0;
+  if (p.N1 > 0 &&
+      (!encode_2d(ctx, &tA1, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, A, (uint64_t)D, (uint64_t)nA, rowb, p.bw1, kGcPts,
+                  CU_TENSOR_MAP_SWIZZLE_NONE) ||
+       !encode_2d(ctx, &tB1, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, B, (uint64_t)D, (uint64_t)nB, rowb, p.bw1, kGcPts,
+                  CU_TENSOR_MAP_SWIZZLE_NONE)))
+    return cudaErrorInvalidValue;
+  const size_t smem = std::max(gc_smem_bytes(p.rows0, p.bw0), gc_smem_bytes(p.rows1, p.bw1));
   cudaError_t e = cudaFuncSetAttribute(gram_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e) return e;
-  const int grid = p.N1 > 0 ? nsm : p.nc0;
   {
     PhaseTimer pt(ctx, PROHD_PH_GRAM, st);
     count_launch();
-    gram_tc_kernel<<<grid, kGcThreads, smem, st>>>(p);
+    gram_tc_kernel<<<grid, kGcThreads, smem, st>>>(p, tA0, tB0, tA1, tB1);
     if ((e = cudaGetLastError())) return e;
   }
   count_launch();

@@ -45,7 +45,7 @@ def _gpu_dirs(A, B, m, seed=0):
     return d.cpu().numpy(), e.cpu().numpy()
 
 
-@pytest.mark.parametrize("D,m", [(8, 2), (32, 4), (64, 8), (256, 8), (100, 5)])
+@pytest.mark.parametrize("D,m", [(8, 2), (32, 4), (64, 8), (256, 8), (100, 5), (13, 3), (300, 4)])
 def test_directions_anisotropic(D, m):
     # anisotropic Gaussian with eigenvalues 1/i: well separated top components
     A, B = W.anisotropic_pair(6000, 5000, D, seed=D)
