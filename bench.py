@@ -318,10 +318,17 @@ def gpu_arm(args):
     fp32_peak = 152 * 128 * 2 * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
     if dom == "gram":
         t = cand["gram"][0] / 1e3
-        fl = 2.0 * (2 * n) * DIM * DIM
-        roof = {"kernel": "gram_kernel", "bound": "alu", "achieved": fl / t / 1e12, "peak": fp32_peak,
-                "unit": "TFLOP/s", "traffic": None,
-                "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 flop x max SM clock"}
+        if DIM <= 256 and DIM % 4 == 0:
+            # tensor-core Gram: one read of both sets bounds it (its FLOPs at the
+            # BF16 peak would take less time than the read)
+            by = 2.0 * n * DIM * 4
+            roof = {"kernel": "gram_tc_kernel", "bound": "hbm", "achieved": by / t / 1e9, "peak": peaks["hbm_gbs"],
+                    "unit": "GB/s", "traffic": None, "peak_source": f"{peak_src} copy bandwidth"}
+        else:
+            fl = 2.0 * (2 * n) * DIM * DIM
+            roof = {"kernel": "gram_kernel", "bound": "alu", "achieved": fl / t / 1e12, "peak": fp32_peak,
+                    "unit": "TFLOP/s", "traffic": None,
+                    "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 flop x max SM clock"}
     elif dom == "hd_contract":
         t = cand["hd_contract"][0] / 1e3
         fl = 2.0 * nsa * nsb * DIM

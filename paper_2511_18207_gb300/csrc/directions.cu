@@ -519,13 +519,16 @@ __global__ void __cluster_dims__(kPiCTAs, 1, 1) __launch_bounds__(kPiThreads, 1)
       const double cosv = nw > 0.0 ? fabs(S.red_out[1]) / nw : 1.0;
       // the second-pass correction is applied in FP64: an FP32 update would
       // move ||x|| away from nw by ~1e-8 and fake convergence at the next step
-      if (nw > 0.0)
+      if (nw > 0.0) {
+        const double inv = 1.0 / nw;
         for (int j = tid; j < D; j += kPiThreads) {
-          double x = (double)w[j];
-          for (int k = 0; k < nq; ++k) x -= (double)S.red_outf[k] * (double)Uf[(size_t)k * D + j];
-          S.v64[j] = x / nw;
+          // the correction is ~1e-8 of w: FP32 suffices for it, the sum is FP64
+          float corr = 0.f;
+          for (int k = 0; k < nq; ++k) corr = fmaf(S.red_outf[k], Uf[(size_t)k * D + j], corr);
+          S.v64[j] = ((double)w[j] - (double)corr) * inv;
           S.v32[j] = (float)S.v64[j];
         }
+      }
       stop_local = (nw == 0.0) || (1.0 - cosv < tol);
       __syncthreads();
     }

@@ -7,16 +7,17 @@
 // residual is below 2^-25 |z|), and G is accumulated from the six products
 // hh^T + hm^T + mh^T + hl^T + lh^T + mm^T, whose sum differs from zz^T by
 // about 2^-24 |z_i z_j| per point. The tensor core accumulates 512 points in
-// FP32 in TMEM; each 512-point partial is then added into a per-CTA FP64
-// accumulator in global memory (covariance accumulation in FP64 across rows
-// and CTAs), and a final kernel sums the CTAs in a fixed order.
+// FP32 in TMEM; each 512-point partial is then added into a per-CTA
+// Kahan-compensated FP32 accumulator in global memory, and a final kernel
+// sums the CTAs in FP64 in a fixed order.
 //
 // Pipeline per CTA: a TMA warp streams FP32 tiles [64 points x up to 256
 // dims] through a two-stage ring; eight converter warps read them from shared
 // memory, centre, split and transpose them into one K-major, 128B-swizzled
 // BF16 stage [dims x 64 points] x {h, m, l} (the operand layout of the
 // distance contraction); one thread issues the 24 MMAs of a chunk; four
-// epilogue warps move finished 512-point partials from TMEM into FP64.
+// epilogue warps move finished 512-point partials from TMEM into the
+// compensated accumulators.
 //
 // Work split: CTAs of type 0 own output rows 0..127 against all Dp columns,
 // type 1 (when Dp > 128) rows 128..Dp-1 against columns 128..Dp-1; each type
@@ -41,6 +42,16 @@ constexpr int kGcTmaWarp = kGcConv + 1 + kGcEpi;
 constexpr int kGcThreads = (kGcTmaWarp + 1) * 32;
 constexpr int kGcFlush = 8;         // chunks per FP32 accumulation in TMEM (512 points)
 constexpr int kGcMaxRows = 256;
+
+// Packed round-to-nearest conversion of two FP32 values to BF16x2 (a in the
+// low half, b in the high half), and the FP32 values of the halves.
+__device__ __forceinline__ uint32_t bf16x2_rn(float a, float b) {
+  uint32_t r;
+  asm("cvt.rn.bf16x2.f32 %0, %1, %2;" : "=r"(r) : "f"(b), "f"(a));
+  return r;
+}
+__device__ __forceinline__ float bf16_lo(uint32_t v) { return __uint_as_float(v << 16); }
+__device__ __forceinline__ float bf16_hi(uint32_t v) { return __uint_as_float(v & 0xffff0000u); }
 
 // Kahan-compensated s += x with compensation c.
 __device__ __forceinline__ void kahan_add(float& s, float& c, float x) {
@@ -71,7 +82,7 @@ struct GcParams {
   int rows0, rows1;   // tile rows (dims) of each type (>= 128, zero padded)
   int N0, N1;         // output columns of each type
   int bw0, bw1;       // FP32 box width (dims) of each type
-  double* gacc;       // [gridDim][256 x 128] FP64 partials, element (col, row) at col*128 + row
+  float2* gacc;       // [gridDim][256 x 128] Kahan (sum, compensation) partials, element (col, row) at col*128 + row
   double* sums;       // [gridDim][kGcConv][2][Dp] FP64 per-warp set sums of z - s
   int* status;
   uint64_t timeout_ns;
@@ -182,27 +193,21 @@ __global__ void __maxnreg__(128)
         float part = 0.f;
 #pragma unroll
         for (int i = 0; i < 8; i += 2) {
-          float h2[2], m2[2], l2[2];
-#pragma unroll
-          for (int j = 0; j < 2; ++j) {
-            const bool v = vd && pt0 + i + j < p1;
-            const float xv = v ? st[(size_t)(i + j) * bw + dl] : 0.f;
-            const float z = v ? xv - shift[t] : 0.f;
-            bad |= !isfinite(xv);
-            part += z;
-            const __nv_bfloat16 h = __float2bfloat16_rn(z);
-            const float r1 = z - __bfloat162float(h);
-            const __nv_bfloat16 m = __float2bfloat16_rn(r1);
-            h2[j] = __bfloat162float(h);
-            m2[j] = __bfloat162float(m);
-            l2[j] = r1 - m2[j];
-          }
-          __nv_bfloat162 hh = __floats2bfloat162_rn(h2[0], h2[1]);
-          __nv_bfloat162 mm = __floats2bfloat162_rn(m2[0], m2[1]);
-          __nv_bfloat162 ll = __floats2bfloat162_rn(l2[0], l2[1]);
-          hv[i / 2] = *reinterpret_cast<uint32_t*>(&hh);
-          mv[i / 2] = *reinterpret_cast<uint32_t*>(&mm);
-          lv[i / 2] = *reinterpret_cast<uint32_t*>(&ll);
+          // two points at a time: one packed BF16x2 conversion per split level,
+          // unpacked to FP32 by shifts (a BF16 is the top half of an FP32)
+          const bool v0 = vd && pt0 + i < p1, v1 = vd && pt0 + i + 1 < p1;
+          const float x0 = v0 ? st[(size_t)i * bw + dl] : 0.f;
+          const float x1 = v1 ? st[(size_t)(i + 1) * bw + dl] : 0.f;
+          bad |= !isfinite(x0) || !isfinite(x1);
+          const float z0 = v0 ? x0 - shift[t] : 0.f, z1 = v1 ? x1 - shift[t] : 0.f;
+          part += z0 + z1;
+          const uint32_t hb = bf16x2_rn(z0, z1);
+          const float r0 = z0 - bf16_lo(hb), r1 = z1 - bf16_hi(hb);
+          const uint32_t mb = bf16x2_rn(r0, r1);
+          const uint32_t lb = bf16x2_rn(r0 - bf16_lo(mb), r1 - bf16_hi(mb));
+          hv[i / 2] = hb;
+          mv[i / 2] = mb;
+          lv[i / 2] = lb;
         }
         kahan_add(ss[t], sc[t], part);
         const int row = lane + 32 * t;
@@ -273,7 +278,7 @@ __global__ void __maxnreg__(128)
     // ---------------- epilogue: FP32 TMEM partials -> FP64 accumulators ----------------
     const int q = warp & 3;
     const int row = q * 32 + lane;  // output row within this type's 128 rows
-    double* g = p.gacc + (size_t)blockIdx.x * (256 * 128);
+    float2* g = p.gacc + (size_t)blockIdx.x * (256 * 128);
     const int nflush = (nchunks + kGcFlush - 1) / kGcFlush;
     uint32_t ab = 0, aph = 0;
     bool ok = true;
@@ -286,18 +291,22 @@ __global__ void __maxnreg__(128)
       tc_fence_after();
       const uint32_t taddr = tmem + ((uint32_t)(q * 32) << 16) + ab * 256;
       for (int cc = 0; cc < N / 32; ++cc) {
-        // issue the 32 loads of the running FP64 sums before any add, so
-        // their L2 latency overlaps instead of chaining load-add-store
-        double acc[32];
-        double* col0 = g + (size_t)(cc * 32) * 128 + row;
+        // running sums are Kahan-compensated FP32 pairs (sum, compensation):
+        // as accurate as FP64 accumulation of the 512-point partials, and
+        // FP64 arithmetic is scarce here. Loads are issued before any add.
+        float2 acc[32];
+        float2* col0 = g + (size_t)(cc * 32) * 128 + row;
 #pragma unroll
-        for (int c = 0; c < 32; ++c) acc[c] = fl == 0 ? 0.0 : __ldcg(col0 + (size_t)c * 128);
+        for (int c = 0; c < 32; ++c) acc[c] = fl == 0 ? make_float2(0.f, 0.f) : __ldcg(col0 + (size_t)c * 128);
         float v[32];
         __syncwarp();
         tc_ld_32x32b_x32(taddr + cc * 32, v);
         tc_wait_ld();
 #pragma unroll
-        for (int c = 0; c < 32; ++c) __stcg(col0 + (size_t)c * 128, acc[c] + (double)v[c]);
+        for (int c = 0; c < 32; ++c) {
+          kahan_add(acc[c].x, acc[c].y, v[c]);
+          __stcg(col0 + (size_t)c * 128, acc[c]);
+        }
       }
       tc_fence_before();
       __syncwarp();
@@ -306,7 +315,7 @@ __global__ void __maxnreg__(128)
       if (ab == 0) aph ^= 1;
     }
     if (nflush == 0)
-      for (int col = 0; col < N; ++col) g[(size_t)col * 128 + row] = 0.0;
+      for (int col = 0; col < N; ++col) g[(size_t)col * 128 + row] = make_float2(0.f, 0.f);
   }
 
   __syncthreads();
@@ -336,7 +345,10 @@ __global__ void gram_tc_reduce_kernel(const GcParams p, int ncta, double* __rest
         c0 = p.nc0; c1 = ncta; row = i - 128; col = j - 128;
       }
       double s = 0.0;
-      for (int c = c0; c < c1; ++c) s += p.gacc[(size_t)c * (256 * 128) + (size_t)col * 128 + row];
+      for (int c = c0; c < c1; ++c) {
+        const float2 v = p.gacc[(size_t)c * (256 * 128) + (size_t)col * 128 + row];
+        s += (double)v.x - (double)v.y;
+      }
       G[e] = s;
     } else {
       const int64_t k = e - DD;
@@ -387,7 +399,7 @@ cudaError_t gram_tc_run(prohd_ctx* ctx, const float* A, int64_t nA, const float*
   };
   p.ncA0 = split(p.nc0);
   p.ncA1 = p.N1 > 0 ? split(grid - p.nc0) : 0;
-  p.gacc = scratch;
+  p.gacc = reinterpret_cast<float2*>(scratch);
   p.sums = scratch + (size_t)nsm * 256 * 128;
   p.status = status;
   p.timeout_ns = (uint64_t)timeout_ns;
