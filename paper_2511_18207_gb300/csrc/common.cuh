@@ -113,20 +113,33 @@ PROHD_DEV bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
   return ok != 0;
 }
 
-// Bounded wait: returns false (and sets *abort) once `deadline_ns` of global
-// time has passed or another thread has raised *abort. The fast path is one
-// try_wait; the timer is read only while spinning.
+// try_wait that may suspend the thread until the phase completes or about
+// `hint_ns` have passed, so a waiting warp does not spin on issue slots.
+PROHD_DEV bool mbar_try_wait_suspend(uint64_t* bar, uint32_t parity, uint32_t hint_ns) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\t"
+      "selp.b32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity), "r"(hint_ns)
+      : "memory");
+  return ok != 0;
+}
+
+// Bounded wait: returns false (and sets *abort) once `timeout_ns` of global
+// time has passed or another thread has raised *abort. After one fast check
+// the thread suspends in try_wait (woken when the phase completes), checking
+// the abort flag and the timer between suspensions.
 PROHD_DEV bool mbar_wait_bounded(uint64_t* bar, uint32_t parity, volatile int* abort, uint64_t timeout_ns) {
   if (mbar_try_wait(bar, parity)) return true;
-  uint64_t t0 = global_timer_ns();
-  for (uint32_t it = 1;; ++it) {
-    if (mbar_try_wait(bar, parity)) return true;
-    if ((it & 255u) == 0) {
-      if (*abort) return false;
-      if (global_timer_ns() - t0 > timeout_ns) {
-        *abort = 1;
-        return false;
-      }
+  const uint64_t t0 = global_timer_ns();
+  for (;;) {
+    if (mbar_try_wait_suspend(bar, parity, 20000u)) return true;
+    if (*abort) return false;
+    if (global_timer_ns() - t0 > timeout_ns) {
+      *abort = 1;
+      return false;
     }
   }
 }
