@@ -11,11 +11,14 @@
 // Kahan-compensated FP32 accumulator in global memory, and a final kernel
 // sums the CTAs in FP64 in a fixed order.
 //
-// Pipeline per CTA: a TMA warp streams FP32 tiles [64 points x up to 256
-// dims] through a two-stage ring; eight converter warps read them from shared
-// memory, centre, split and transpose them into one K-major, 128B-swizzled
-// BF16 stage [dims x 64 points] x {h, m, l} (the operand layout of the
-// distance contraction); one thread issues the 24 MMAs of a chunk; four
+// Pipeline per CTA: a TMA warp streams FP32 tiles [64 points x rows dims]
+// through a two-stage ring (dims past D arrive as zeros); eight converter
+// warps read them from shared memory, centre, split and transpose them into
+// one K-major, 128B-swizzled BF16 stage [dims x 64 points] x {h, m, l} (the
+// operand layout of the distance contraction); one thread issues the MMAs
+// slice by slice (16 points per slice, two converter warps per slice), and
+// each slice is handed back to its converters as soon as its MMAs complete,
+// so the conversion of the next chunk overlaps the MMAs of this one; four
 // epilogue warps move finished 512-point partials from TMEM into the
 // compensated accumulators.
 //
@@ -61,16 +64,18 @@ __device__ __forceinline__ void kahan_add(float& s, float& c, float x) {
   s = t;
 }
 
+constexpr int kGcSlices = kGcPts / 16;  // K-steps of one chunk
+
 struct GcSmem {
-  uint64_t ffull[2], fempty[2], bfull, bempty, acc_full[2], acc_empty[2], drain;
+  uint64_t ffull[2], fempty[2], sfull[kGcSlices], sempty[kGcSlices], acc_full[2], acc_empty[2], drain;
   uint32_t tmem_base;
   int abort;
 };
 
 __host__ __device__ constexpr size_t gc_tile_bytes(int rows) { return (size_t)rows * 128; }
-__host__ __device__ constexpr size_t gc_stage_bytes(int bw) { return (size_t)kGcPts * bw * 4; }
-__host__ __device__ constexpr size_t gc_smem_bytes(int rows, int bw) {
-  return 1024 + 3 * gc_tile_bytes(rows) + 2 * gc_stage_bytes(bw) + sizeof(GcSmem);
+__host__ __device__ constexpr size_t gc_stage_bytes(int rows) { return (size_t)kGcPts * rows * 4; }
+__host__ __device__ constexpr size_t gc_smem_bytes(int rows) {
+  return 1024 + 3 * gc_tile_bytes(rows) + 2 * gc_stage_bytes(rows) + sizeof(GcSmem);
 }
 
 struct GcParams {
@@ -79,14 +84,90 @@ struct GcParams {
   const float* s32;   // pilot shift [D]
   int nc0;            // CTAs of type 0 (the rest are type 1)
   int ncA0, ncA1;     // CTAs of each type that read set A (the rest read B)
-  int rows0, rows1;   // tile rows (dims) of each type (>= 128, zero padded)
+  int rows0, rows1;   // tile rows (dims) of each type, 128, 192 or 256; also the FP32 box width
   int N0, N1;         // output columns of each type
-  int bw0, bw1;       // FP32 box width (dims) of each type
   float2* gacc;       // [gridDim][256 x 128] Kahan (sum, compensation) partials, element (col, row) at col*128 + row
   double* sums;       // [gridDim][kGcConv][2][Dp] FP64 per-warp set sums of z - s
   int* status;
   uint64_t timeout_ns;
 };
+
+// Splits two FP32 values exactly enough into BF16 triples (see the file
+// comment) and returns the packed pairs (point i in the low half).
+__device__ __forceinline__ void gc_split_pair(float z0, float z1, uint32_t& h, uint32_t& m, uint32_t& l) {
+  // one packed BF16x2 conversion per split level, unpacked to FP32 by
+  // shifts (a BF16 is the top half of an FP32)
+  h = bf16x2_rn(z0, z1);
+  const float r0 = z0 - bf16_lo(h), r1 = z1 - bf16_hi(h);
+  m = bf16x2_rn(r0, r1);
+  l = bf16x2_rn(r0 - bf16_lo(m), r1 - bf16_hi(m));
+}
+
+// One converter warp's share of a chunk: 8 points x 32T dims from the FP32
+// stage (row stride 32T floats) into the three BF16 tiles. `st` points at
+// this warp's first point and this lane's dimension, `dst` at this lane's
+// 16-byte slot in row `lane` of the h tile (rows lane + 32 t sit 4096 t
+// bytes further). Only the first `nv` points are real when !FULL; the rest
+// contribute zeros. Dimensions past D were zero-filled by the copy and have
+// a zero shift.
+template <int T, bool FULL>
+__device__ __forceinline__ void gc_convert(const float* __restrict__ st, uint8_t* __restrict__ dst,
+                                           const float (&shift)[8], float (&ss)[8], float (&sc)[8], int nv) {
+  constexpr int BW = 32 * T;
+  constexpr int TB = 4096 * T;  // bytes of one BF16 tile (32T rows x 128 B)
+#pragma unroll
+  for (int t = 0; t < T; ++t) {
+    float z[8];
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+      const float x = st[i * BW + 32 * t];
+      z[i] = (FULL || i < nv) ? x - shift[t] : 0.f;
+    }
+    kahan_add(ss[t], sc[t], ((z[0] + z[1]) + (z[2] + z[3])) + ((z[4] + z[5]) + (z[6] + z[7])));
+    uint32_t h[4], m[4], l[4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) gc_split_pair(z[2 * i], z[2 * i + 1], h[i], m[i], l[i]);
+    uint8_t* o = dst + t * 4096;
+    *reinterpret_cast<uint4*>(o) = make_uint4(h[0], h[1], h[2], h[3]);
+    *reinterpret_cast<uint4*>(o + TB) = make_uint4(m[0], m[1], m[2], m[3]);
+    *reinterpret_cast<uint4*>(o + 2 * TB) = make_uint4(l[0], l[1], l[2], l[3]);
+  }
+}
+
+// All chunks of one converter warp (slice `warp / 2` of every chunk).
+template <int T>
+__device__ __forceinline__ bool gc_converter(GcSmem& S, const float* stage, uint8_t* tiles, int warp, int lane,
+                                             int nchunks, int64_t p0, int64_t p1, const float (&shift)[8],
+                                             float (&ss)[8], float (&sc)[8], uint64_t timeout_ns) {
+  constexpr int BW = 32 * T;
+  volatile int* abort = &S.abort;
+  const int s = warp >> 1;
+  const float* st0 = stage + (size_t)(warp * 8) * BW + lane;
+  uint8_t* dst = tiles + lane * 128 + ((warp ^ (lane & 7)) * 16);
+  for (int c = 0; c < nchunks; ++c) {
+    const int f = c & 1;
+    int got = 1;
+    if (lane == 0) {
+      got = mbar_wait_bounded(&S.sempty[s], ((uint32_t)c & 1u) ^ 1u, abort, timeout_ns) &&
+            mbar_wait_bounded(&S.ffull[f], (uint32_t)(c >> 1) & 1u, abort, timeout_ns);
+    }
+    got = __shfl_sync(0xffffffffu, got, 0);
+    if (!got) return false;
+    const float* st = st0 + (size_t)f * kGcPts * BW;
+    const int64_t left = p1 - (p0 + (int64_t)c * kGcPts + warp * 8);
+    if (left >= 8)
+      gc_convert<T, true>(st, dst, shift, ss, sc, 8);
+    else
+      gc_convert<T, false>(st, dst, shift, ss, sc, left > 0 ? (int)left : 0);
+    fence_proxy_async();
+    __syncwarp();
+    if (lane == 0) {
+      mbar_arrive(&S.fempty[f]);
+      mbar_arrive(&S.sfull[s]);
+    }
+  }
+  return true;
+}
 
 // 14 warps: one SMSP holds 4 of them, so 16384 / (4 x 32) = 128 registers per thread at most.
 __global__ void __maxnreg__(128)
@@ -95,14 +176,13 @@ __global__ void __maxnreg__(128)
   extern __shared__ uint8_t smem_raw[];
   uint8_t* base = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   const bool type0 = (int)blockIdx.x < p.nc0;
-  const int rows = type0 ? p.rows0 : p.rows1;  // tile rows (dims loaded, zero padded)
+  const int rows = type0 ? p.rows0 : p.rows1;  // tile rows (dims loaded, zero padded) = FP32 box width
   const int N = type0 ? p.N0 : p.N1;
   const int dim0 = type0 ? 0 : 128;            // first dimension loaded
-  const int bw = type0 ? p.bw0 : p.bw1;
   const size_t tb = gc_tile_bytes(rows);
   uint8_t* tiles = base;                                   // [3][rows x 128 B]
-  float* stage = reinterpret_cast<float*>(base + 3 * tb);  // [2][64][bw]
-  GcSmem& S = *reinterpret_cast<GcSmem*>(base + 3 * tb + 2 * gc_stage_bytes(bw));
+  float* stage = reinterpret_cast<float*>(base + 3 * tb);  // [2][64][rows]
+  GcSmem& S = *reinterpret_cast<GcSmem*>(base + 3 * tb + 2 * gc_stage_bytes(rows));
   volatile int* abort = &S.abort;
 
   // this CTA's set and point range
@@ -124,8 +204,10 @@ __global__ void __maxnreg__(128)
       mbar_init(&S.acc_full[s], 1);
       mbar_init(&S.acc_empty[s], kGcEpi);
     }
-    mbar_init(&S.bfull, kGcConv);
-    mbar_init(&S.bempty, 1);
+    for (int s = 0; s < kGcSlices; ++s) {
+      mbar_init(&S.sfull[s], kGcConv / kGcSlices);
+      mbar_init(&S.sempty[s], 1);
+    }
     mbar_init(&S.drain, 1);
     S.abort = 0;
     fence_mbar_init();
@@ -143,13 +225,13 @@ __global__ void __maxnreg__(128)
     // ---------------- TMA producer: FP32 point tiles into the 2-stage ring ----------------
     if (lane == 0) {
       tma_prefetch_desc(tm);
-      const uint32_t bytes = (uint32_t)gc_stage_bytes(bw);
+      const uint32_t bytes = (uint32_t)gc_stage_bytes(rows);
       uint32_t armed = 0;
       for (int c = 0; c < nchunks; ++c) {
         const int f = c & 1;
         if (!mbar_wait_bounded(&S.fempty[f], ((uint32_t)(c >> 1) & 1u) ^ 1u, abort, p.timeout_ns)) break;
         mbar_arrive_expect_tx(&S.ffull[f], bytes);
-        tma_load_2d(stage + (size_t)f * kGcPts * bw, tm, dim0, (int)(p0 + (int64_t)c * kGcPts), &S.ffull[f]);
+        tma_load_2d(stage + (size_t)f * kGcPts * rows, tm, dim0, (int)(p0 + (int64_t)c * kGcPts), &S.ffull[f]);
         armed = (uint32_t)c + 1;
       }
       if (*abort) {
@@ -171,62 +253,20 @@ __global__ void __maxnreg__(128)
       const int d = dim0 + lane + 32 * t;
       shift[t] = (t < T && d < p.D) ? p.s32[d] : 0.f;
     }
+    if (T == 8)
+      gc_converter<8>(S, stage, tiles, warp, lane, nchunks, p0, p1, shift, ss, sc, p.timeout_ns);
+    else if (T == 6)
+      gc_converter<6>(S, stage, tiles, warp, lane, nchunks, p0, p1, shift, ss, sc, p.timeout_ns);
+    else
+      gc_converter<4>(S, stage, tiles, warp, lane, nchunks, p0, p1, shift, ss, sc, p.timeout_ns);
+    // A non-finite coordinate makes its dimension's running sum non-finite
+    // (so does an FP32 overflow of the sum, which would also ruin G).
     bool bad = false;
-    for (int c = 0; c < nchunks; ++c) {
-      const int f = c & 1;
-      int got = 1;
-      if (lane == 0) {
-        got = mbar_wait_bounded(&S.bempty, ((uint32_t)c & 1u) ^ 1u, abort, p.timeout_ns) &&
-              mbar_wait_bounded(&S.ffull[f], (uint32_t)(c >> 1) & 1u, abort, p.timeout_ns);
-      }
-      got = __shfl_sync(0xffffffffu, got, 0);
-      if (!got) break;
-      const float* st = stage + (size_t)f * kGcPts * bw + (size_t)(warp * 8) * bw;
-      const int64_t pt0 = p0 + (int64_t)c * kGcPts + warp * 8;
-#pragma unroll
-      for (int t = 0; t < 8; ++t) {
-        if (t >= T) break;
-        const int d = dim0 + lane + 32 * t;
-        const int dl = lane + 32 * t;  // column inside the staged box
-        const bool vd = d < p.D && dl < bw;
-        uint32_t hv[4], mv[4], lv[4];
-        float part = 0.f;
-#pragma unroll
-        for (int i = 0; i < 8; i += 2) {
-          // two points at a time: one packed BF16x2 conversion per split level,
-          // unpacked to FP32 by shifts (a BF16 is the top half of an FP32)
-          const bool v0 = vd && pt0 + i < p1, v1 = vd && pt0 + i + 1 < p1;
-          const float x0 = v0 ? st[(size_t)i * bw + dl] : 0.f;
-          const float x1 = v1 ? st[(size_t)(i + 1) * bw + dl] : 0.f;
-          bad |= !isfinite(x0) || !isfinite(x1);
-          const float z0 = v0 ? x0 - shift[t] : 0.f, z1 = v1 ? x1 - shift[t] : 0.f;
-          part += z0 + z1;
-          const uint32_t hb = bf16x2_rn(z0, z1);
-          const float r0 = z0 - bf16_lo(hb), r1 = z1 - bf16_hi(hb);
-          const uint32_t mb = bf16x2_rn(r0, r1);
-          const uint32_t lb = bf16x2_rn(r0 - bf16_lo(mb), r1 - bf16_hi(mb));
-          hv[i / 2] = hb;
-          mv[i / 2] = mb;
-          lv[i / 2] = lb;
-        }
-        kahan_add(ss[t], sc[t], part);
-        const int row = lane + 32 * t;
-        const size_t off = (size_t)row * 128 + (size_t)((warp ^ (row & 7)) * 16);
-        *reinterpret_cast<uint4*>(tiles + off) = make_uint4(hv[0], hv[1], hv[2], hv[3]);
-        *reinterpret_cast<uint4*>(tiles + tb + off) = make_uint4(mv[0], mv[1], mv[2], mv[3]);
-        *reinterpret_cast<uint4*>(tiles + 2 * tb + off) = make_uint4(lv[0], lv[1], lv[2], lv[3]);
-      }
-      fence_proxy_async();
-      __syncwarp();
-      if (lane == 0) {
-        mbar_arrive(&S.fempty[f]);
-        mbar_arrive(&S.bfull);
-      }
-    }
     double* out = p.sums + ((size_t)blockIdx.x * kGcConv + warp) * 2 * p.Dp;
 #pragma unroll
     for (int t = 0; t < 8; ++t) {
       const int d = dim0 + lane + 32 * t;
+      if (t < T) bad |= !isfinite(ss[t]) || !isfinite(sc[t]);
       if (t < T && d < p.Dp) {
         const double v = type0 ? (double)ss[t] - (double)sc[t] : 0.0;
         out[(setA ? 0 : p.Dp) + d] = v;
@@ -243,25 +283,28 @@ __global__ void __maxnreg__(128)
       const int pb[6] = {0, 1, 0, 2, 0, 1};
       uint32_t ab = 0, aph = 0;
       int in_acc = 0;
+      const uint32_t t0 = smem_u32(tiles);
       for (int c = 0; c < nchunks; ++c) {
         if (in_acc == 0) {
           if (!mbar_wait_bounded(&S.acc_empty[ab], aph ^ 1, abort, p.timeout_ns)) break;
           tc_fence_after();
         }
-        if (!mbar_wait_bounded(&S.bfull, (uint32_t)c & 1u, abort, p.timeout_ns)) break;
-        tc_fence_after();
         const uint32_t d_tmem = tmem + ab * 256;
-        const uint32_t t0 = smem_u32(tiles);
+        bool ok = true;
 #pragma unroll
-        for (int q = 0; q < 6; ++q) {
-          const uint32_t a_addr = t0 + (uint32_t)(pa[q] * tb);
-          const uint32_t b_addr = t0 + (uint32_t)(pb[q] * tb);
+        for (int k = 0; k < kGcSlices; ++k) {
+          if (!mbar_wait_bounded(&S.sfull[k], (uint32_t)c & 1u, abort, p.timeout_ns)) {
+            ok = false;
+            break;
+          }
+          tc_fence_after();
 #pragma unroll
-          for (int k = 0; k < kGcPts / 16; ++k)
-            tc_mma_f16(d_tmem, smem_desc_sw128(a_addr + k * 32), smem_desc_sw128(b_addr + k * 32), idesc,
-                       (in_acc | q | k) != 0);
+          for (int q = 0; q < 6; ++q)
+            tc_mma_f16(d_tmem, smem_desc_sw128(t0 + (uint32_t)(pa[q] * tb) + k * 32),
+                       smem_desc_sw128(t0 + (uint32_t)(pb[q] * tb) + k * 32), idesc, (in_acc | q | k) != 0);
+          tc_commit(&S.sempty[k]);  // slice k may be overwritten once these MMAs complete
         }
-        tc_commit(&S.bempty);
+        if (!ok) break;
         if (++in_acc == kGcFlush || c == nchunks - 1) {
           tc_commit(&S.acc_full[ab]);
           in_acc = 0;
@@ -270,8 +313,8 @@ __global__ void __maxnreg__(128)
         }
       }
       tc_commit(&S.drain);
-      const uint64_t t0 = global_timer_ns();
-      while (!mbar_try_wait(&S.drain, 0) && global_timer_ns() - t0 < 1000000000ull) {
+      const uint64_t t0d = global_timer_ns();
+      while (!mbar_try_wait(&S.drain, 0) && global_timer_ns() - t0d < 1000000000ull) {
       }
     }
   } else {
@@ -383,8 +426,6 @@ cudaError_t gram_tc_run(prohd_ctx* ctx, const float* A, int64_t nA, const float*
   p.rows0 = std::max(128, p.Dp);
   p.N1 = p.Dp > 128 ? p.Dp - 128 : 0;
   p.rows1 = 128;
-  p.bw0 = (int)std::min<int64_t>(256, round_up(D, 32));
-  p.bw1 = p.N1 > 0 ? (int)round_up(D - 128, 32) : 32;
   const int grid = nsm;
   if (p.N1 > 0) {
     // CTA counts in proportion to work per point (output columns)
@@ -405,20 +446,20 @@ cudaError_t gram_tc_run(prohd_ctx* ctx, const float* A, int64_t nA, const float*
   p.timeout_ns = (uint64_t)timeout_ns;
   CUtensorMap tA0, tB0, tA1, tB1;
   const uint64_t rowb = (uint64_t)D * 4;
-  if (!encode_2d(ctx, &tA0, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, A, (uint64_t)D, (uint64_t)nA, rowb, p.bw0, kGcPts,
+  if (!encode_2d(ctx, &tA0, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, A, (uint64_t)D, (uint64_t)nA, rowb, p.rows0, kGcPts,
                  CU_TENSOR_MAP_SWIZZLE_NONE) ||
-      !encode_2d(ctx, &tB0, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, B, (uint64_t)D, (uint64_t)nB, rowb, p.bw0, kGcPts,
+      !encode_2d(ctx, &tB0, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, B, (uint64_t)D, (uint64_t)nB, rowb, p.rows0, kGcPts,
                  CU_TENSOR_MAP_SWIZZLE_NONE))
     return cudaErrorInvalidValue;
   tA1 = tA0;
   tB1 = tB0;
   if (p.N1 > 0 &&
-      (!encode_2d(ctx, &tA1, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, A, (uint64_t)D, (uint64_t)nA, rowb, p.bw1, kGcPts,
+      (!encode_2d(ctx, &tA1, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, A, (uint64_t)D, (uint64_t)nA, rowb, p.rows1, kGcPts,
                   CU_TENSOR_MAP_SWIZZLE_NONE) ||
-       !encode_2d(ctx, &tB1, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, B, (uint64_t)D, (uint64_t)nB, rowb, p.bw1, kGcPts,
+       !encode_2d(ctx, &tB1, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, B, (uint64_t)D, (uint64_t)nB, rowb, p.rows1, kGcPts,
                   CU_TENSOR_MAP_SWIZZLE_NONE)))
     return cudaErrorInvalidValue;
-  const size_t smem = std::max(gc_smem_bytes(p.rows0, p.bw0), gc_smem_bytes(p.rows1, p.bw1));
+  const size_t smem = std::max(gc_smem_bytes(p.rows0), gc_smem_bytes(p.rows1));
   cudaError_t e = cudaFuncSetAttribute(gram_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e) return e;
   {

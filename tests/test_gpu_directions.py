@@ -45,10 +45,16 @@ def _gpu_dirs(A, B, m, seed=0):
     return d.cpu().numpy(), e.cpu().numpy()
 
 
-@pytest.mark.parametrize("D,m", [(8, 2), (32, 4), (64, 8), (256, 8), (100, 5), (13, 3), (300, 4)])
-def test_directions_anisotropic(D, m):
+@pytest.mark.parametrize(
+    "D,m,nA,nB",
+    [(8, 2, 6000, 5000), (32, 4, 6000, 5000), (64, 8, 6000, 5000), (256, 8, 6000, 5000), (100, 5, 6000, 5000),
+     (13, 3, 6000, 5000), (300, 4, 6000, 5000), (124, 3, 6000, 5000), (160, 4, 6000, 5000), (192, 6, 6000, 5000),
+     # many 64-point chunks per CTA, ragged tails, both CTA types
+     (256, 4, 120_000, 90_001), (192, 3, 70_001, 99_999)],
+)
+def test_directions_anisotropic(D, m, nA, nB):
     # anisotropic Gaussian with eigenvalues 1/i: well separated top components
-    A, B = W.anisotropic_pair(6000, 5000, D, seed=D)
+    A, B = W.anisotropic_pair(nA, nB, D, seed=D)
     g, ge = _gpu_dirs(A, B, m)
     o, oe, _ = oracle.directions(A, B, m=m, seed=0)
     assert np.linalg.norm(g[0] - o[0]) <= _axis_bound(A, B)

@@ -68,3 +68,23 @@ def test_estimate_host_entry_matches_device():
     h = prohd.decode_result(res)
     d = prohd.prohd_estimate_sync(dev(A), dev(B), m=2, alpha_c=0.02)
     assert h["H"] == d["H"] and h["nsel_a"] == d["nsel_a"] and h["nsel_b"] == d["nsel_b"]
+
+
+@pytest.mark.parametrize("D", [64, 256, 13])
+@pytest.mark.parametrize("where", ["A_first", "A_middle", "A_last", "B_last_inf"])
+def test_estimate_nonfinite_input_is_reported(D, where):
+    # The covariance pass reads every point, so a non-finite coordinate
+    # anywhere (first chunk, middle, the ragged last chunk of a set) must
+    # surface as ENONFINITE; D = 13 takes the CUDA-core covariance kernel.
+    torch_cuda()
+    A, B = W.anisotropic_pair(30_001, 20_003, D, seed=3)
+    if where == "A_first":
+        A[0, D - 1] = np.nan
+    elif where == "A_middle":
+        A[17_777, D // 2] = np.nan
+    elif where == "A_last":
+        A[-1, 0] = np.nan
+    else:
+        B[-1, D - 1] = np.inf
+    r = prohd.prohd_estimate_sync(dev(A), dev(B), m=2, alpha_c=0.01)
+    assert r["status"] == "ENONFINITE", r["status"]
