@@ -113,6 +113,16 @@ PROHD_DEV bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
   return ok != 0;
 }
 
+// The dynamic shared-memory base rounded up to `align` bytes by pointer
+// arithmetic on the __shared__ array itself, so that the compiler still
+// knows every derived pointer addresses shared memory (a round trip through
+// an integer type would turn all accesses into generic loads and stores).
+template <uint32_t align>
+PROHD_DEV uint8_t* smem_align(uint8_t* smem) {
+  const uint32_t off = (align - (smem_u32(smem) & (align - 1))) & (align - 1);
+  return smem + off;
+}
+
 // try_wait that may suspend the thread until the phase completes or about
 // `hint_ns` have passed, so a waiting warp does not spin on issue slots.
 PROHD_DEV bool mbar_try_wait_suspend(uint64_t* bar, uint32_t parity, uint32_t hint_ns) {

@@ -174,7 +174,7 @@ __global__ void __maxnreg__(128)
     gram_tc_kernel(const GcParams p, const __grid_constant__ CUtensorMap tmA0, const __grid_constant__ CUtensorMap tmB0,
                    const __grid_constant__ CUtensorMap tmA1, const __grid_constant__ CUtensorMap tmB1) {
   extern __shared__ uint8_t smem_raw[];
-  uint8_t* base = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  uint8_t* base = smem_align<1024>(smem_raw);
   const bool type0 = (int)blockIdx.x < p.nc0;
   const int rows = type0 ? p.rows0 : p.rows1;  // tile rows (dims loaded, zero padded) = FP32 box width
   const int N = type0 ? p.N0 : p.N1;

@@ -348,7 +348,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
                  const int64_t* __restrict__ nB_dev, int KB, float* __restrict__ rowmin,
                  unsigned* __restrict__ colmin, int* __restrict__ status, uint64_t timeout_ns) {
   extern __shared__ uint8_t smem_raw[];
-  uint8_t* base = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  uint8_t* base = smem_align<1024>(smem_raw);
   uint8_t* sA = base;
   uint8_t* sB = base + (size_t)KB * kTcAKBytes;
   TcSmem& S = *reinterpret_cast<TcSmem*>(sB + (size_t)kTcStages * kTcBStage);
