@@ -260,4 +260,42 @@ __host__ __device__ constexpr uint32_t idesc_f16(int bf16, int M, int N) {
          ((uint32_t)(M >> 4) << 24);
 }
 
+// ---- SplitMix64 (Steele, Lea, Flood 2014) start vectors in the oracle's
+// counter layout, and thread-block cluster helpers
+
+PROHD_DEV uint64_t splitmix64_mix(uint64_t z) {
+  z = (z ^ (z >> 30)) * 0xbf58476d1ce4e5b9ULL;
+  z = (z ^ (z >> 27)) * 0x94d049bb133111ebULL;
+  return z ^ (z >> 31);
+}
+PROHD_DEV double splitmix64_unit(uint64_t seed, uint64_t l, uint64_t j) {
+  const uint64_t c = (l << 32) + j;
+  const uint64_t z = splitmix64_mix(seed + (c + 1ULL) * 0x9e3779b97f4a7c15ULL);
+  return (double)(z >> 11) * (1.0 / 9007199254740992.0) * 2.0 - 1.0;
+}
+
+PROHD_DEV uint32_t cluster_rank() {
+  uint32_t r;
+  asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+  return r;
+}
+PROHD_DEV void cluster_sync() {
+  asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+PROHD_DEV uint32_t map_to_cta(const void* p, uint32_t rank) {
+  uint32_t r;
+  asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(smem_u32(p)), "r"(rank));
+  return r;
+}
+PROHD_DEV void st_cluster_f32(uint32_t addr, float v) {
+  asm volatile("st.shared::cluster.f32 [%0], %1;" ::"r"(addr), "f"(v) : "memory");
+}
+PROHD_DEV void st_cluster_s32(uint32_t addr, int v) {
+  asm volatile("st.shared::cluster.s32 [%0], %1;" ::"r"(addr), "r"(v) : "memory");
+}
+PROHD_DEV void st_cluster_f64(uint32_t addr, double v) {
+  asm volatile("st.shared::cluster.f64 [%0], %1;" ::"r"(addr), "d"(v) : "memory");
+}
+
+
 }  // namespace prohd

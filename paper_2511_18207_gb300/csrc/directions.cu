@@ -266,40 +266,6 @@ constexpr int kPiThreads = 256;
 constexpr int kPiMaxD = 1024;
 constexpr int kPiMaxM = 64;
 
-PROHD_DEV uint64_t splitmix64_mix(uint64_t z) {
-  z = (z ^ (z >> 30)) * 0xbf58476d1ce4e5b9ULL;
-  z = (z ^ (z >> 27)) * 0x94d049bb133111ebULL;
-  return z ^ (z >> 31);
-}
-PROHD_DEV double splitmix64_unit(uint64_t seed, uint64_t l, uint64_t j) {
-  const uint64_t c = (l << 32) + j;
-  const uint64_t z = splitmix64_mix(seed + (c + 1ULL) * 0x9e3779b97f4a7c15ULL);
-  return (double)(z >> 11) * (1.0 / 9007199254740992.0) * 2.0 - 1.0;
-}
-
-PROHD_DEV uint32_t cluster_rank() {
-  uint32_t r;
-  asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
-  return r;
-}
-PROHD_DEV void cluster_sync() {
-  asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
-}
-PROHD_DEV uint32_t map_to_cta(const void* p, uint32_t rank) {
-  uint32_t r;
-  asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(smem_u32(p)), "r"(rank));
-  return r;
-}
-PROHD_DEV void st_cluster_f32(uint32_t addr, float v) {
-  asm volatile("st.shared::cluster.f32 [%0], %1;" ::"r"(addr), "f"(v) : "memory");
-}
-PROHD_DEV void st_cluster_s32(uint32_t addr, int v) {
-  asm volatile("st.shared::cluster.s32 [%0], %1;" ::"r"(addr), "r"(v) : "memory");
-}
-PROHD_DEV void st_cluster_f64(uint32_t addr, double v) {
-  asm volatile("st.shared::cluster.f64 [%0], %1;" ::"r"(addr), "d"(v) : "memory");
-}
-
 // Batched block sums of K values per thread (K <= KMAX), deterministic order.
 template <int KMAX>
 __device__ void block_sums(double (&v)[KMAX], int K, double* sh /*[8][KMAX]*/, double* out /*[KMAX]*/) {
@@ -587,7 +553,7 @@ __global__ void __cluster_dims__(kPiCTAs, 1, 1) __launch_bounds__(kPiThreads, 1)
       for (int j = tid; j < D; j += kPiThreads)
         if ((unsigned long long)__double_as_longlong(fabs(S.v64[j])) == s_best[0]) atomicMin(&s_idx, j);
       __syncthreads();
-      const double sgn = S.v64[s_idx] < 0.0 ? -1.0 : 1.0;
+      const double sgn = S.v64[min(s_idx, D - 1)] < 0.0 ? -1.0 : 1.0;
       for (int j = tid; j < D; j += kPiThreads) {
         const double x = sgn * S.v64[j];
         S.v64[j] = x;
@@ -633,6 +599,7 @@ struct DirBufs {
   float* C32 = nullptr;
   double* U64 = nullptr;
   float* U32 = nullptr;
+  double* si_scratch = nullptr;  // block-iteration outputs
 };
 
 static void dir_layout(Arena& ws, int D, int m, DirBufs& b) {
@@ -649,6 +616,7 @@ static void dir_layout(Arena& ws, int D, int m, DirBufs& b) {
   b.C32 = ws.take<float>((size_t)D * D);
   b.U64 = ws.take<double>((size_t)kPiCTAs * std::max(m, 1) * D);
   b.U32 = ws.take<float>((size_t)kPiCTAs * std::max(m, 1) * D);
+  b.si_scratch = ws.take<double>(subspace_scratch_doubles(D, m));
 }
 
 void directions_layout(Arena& ws, int64_t nA, int64_t nB, int D, int m) {
@@ -696,7 +664,10 @@ cudaError_t directions_run(prohd_ctx* ctx, const float* A, int64_t nA, const flo
   count_launch();
   cov_finalize_kernel<<<nsm, 256, 0, st>>>(b.G, b.sumA, b.sumB, nA, nB, D, b.C64, b.C32);
   if ((e = cudaGetLastError())) return e;
-  if (m > 0) {
+  if (m > 0 && subspace_supported(D, m)) {
+    PhaseTimer pt_pow(ctx, PROHD_PH_POWER, st);
+    if ((e = subspace_run(ctx, b.C32, b.C64, D, m, max_iters, tol, seed, dirs, eig, b.si_scratch, st))) return e;
+  } else if (m > 0) {
     const int rows_per = (D + kPiCTAs - 1) / kPiCTAs;
     size_t cbytes = (size_t)rows_per * D * sizeof(float);
     int c_in_smem = sizeof(PiSmem) + cbytes <= (size_t)160 * 1024 ? 1 : 0;

@@ -428,8 +428,12 @@ cudaError_t gram_tc_run(prohd_ctx* ctx, const float* A, int64_t nA, const float*
   p.rows1 = 128;
   const int grid = nsm;
   if (p.N1 > 0) {
-    // CTA counts in proportion to work per point (output columns)
-    p.nc0 = (int)std::lround((double)nsm * p.N0 / (double)(p.N0 + p.N1));
+    // CTA counts in proportion to each type's time per point: a fixed part
+    // (handshakes, flushes) plus parts proportional to the output columns
+    // (MMA operand reads) and to the tile rows (copy, conversion), with
+    // weights fitted to measured per-chunk times at D = 256.
+    const double w0 = 20.0 + 0.07 * (p.N0 + p.rows0), w1 = 20.0 + 0.07 * (p.N1 + p.rows1);
+    p.nc0 = (int)std::lround((double)nsm * w0 / (w0 + w1));
     p.nc0 = std::min(std::max(p.nc0, 2), nsm - 2);
   } else {
     p.nc0 = nsm;

@@ -106,6 +106,11 @@ cudaError_t directions_run(prohd_ctx* ctx, const float* A, int64_t nA, const flo
 
 // ---- tensor-core Gram (gram_tc.cu) ----
 constexpr int kMaxSms = 192;  // upper bound used to size per-CTA scratch
+// Top-m eigenvectors by block iteration with Rayleigh-Ritz (subspace.cu).
+bool subspace_supported(int D, int m);
+size_t subspace_scratch_doubles(int D, int m);
+cudaError_t subspace_run(prohd_ctx* ctx, const float* C32, const double* C64, int D, int m, int max_iters, double tol,
+                         uint64_t seed, double* dirs, double* eig, double* scratch, cudaStream_t st);
 bool gram_tc_supported(int D);
 size_t gram_tc_scratch_doubles(int D, int num_sms);
 cudaError_t gram_tc_run(prohd_ctx* ctx, const float* A, int64_t nA, const float* B, int64_t nB, int D,
