@@ -16,9 +16,10 @@
 // Gram over (theta + sigma)^2, so at most 1 + b 10^4), which keeps the FP32
 // Cholesky-QR well conditioned; it slows the convergence factor only from
 // lambda_{b+1}/lambda_m to (lambda_{b+1} + sigma)/(lambda_m + sigma).
-// A residual bound eps = max(sqrt(2 tol), 1e-6) certifies each returned
+// A residual bound eps = max(sqrt(2 tol), 2e-6) certifies each returned
 // vector to within eps lambda_1 / gap_l in angle (the residual bound of the
-// symmetric eigenproblem), FP32 arithmetic cannot certify much below 1e-6.
+// symmetric eigenproblem); FP32 arithmetic (Jacobi stopping at 4 units of
+// rounding, C V to a few units) cannot certify much below 1e-6.
 //
 // One cluster of 8 CTAs runs the iteration: CTA r owns rows [r0, r1) of C
 // (FP32, in shared memory) and of every D x b block, and holds a full copy of
@@ -39,17 +40,19 @@
 namespace prohd {
 
 constexpr int kSiCTAs = 8;
-constexpr int kSiThreads = 256;
+constexpr int kSiThreads = 512;
+constexpr int kSiFinThreads = 256;
 constexpr int kSiMaxD = 256;
 constexpr int kSiMaxB = 32;
 constexpr int kSiMaxM = 24;
 constexpr int kSiMaxRows = kSiMaxD / kSiCTAs;      // 32
 constexpr int kSiLd = kSiMaxB + 1;                 // row stride of the small matrices
 constexpr int kSiX = kSiMaxB * kSiMaxB + kSiMaxB;  // one exchange slot: b x b matrix + b values
+constexpr int kSiVld = kSiMaxD + 4;                // row stride of V^T (floats): 128-bit aligned, staggered banks
 
 struct SiSmem {
-  float V[kSiMaxD * kSiMaxB];        // basis, all rows, row stride b
-  float Cl[kSiMaxRows * kSiMaxD];    // this CTA's rows of C, row stride D
+  float Vt[kSiMaxB * kSiVld];        // basis, transposed: column j of V at Vt[j * kSiVld], zero padded
+  float Cl[kSiMaxRows * kSiMaxD];    // this CTA's rows of C, row stride Dq (D rounded up to 4), zero padded
   float W[kSiMaxRows * kSiMaxB];     // C V, local rows
   float Vr[kSiMaxRows * kSiMaxB];    // Ritz vectors V Y, local rows
   float Wr[kSiMaxRows * kSiMaxB];    // W Y -> scaled block -> Q1 -> Q
@@ -57,7 +60,9 @@ struct SiSmem {
   float X[2][kSiCTAs][kSiX];         // exchange slots, double-buffered
   float M[kSiMaxB * kSiLd];          // summed small matrix
   float Y[kSiMaxB * kSiLd];          // Jacobi eigenvectors (columns)
-  float L[kSiMaxB * kSiLd];          // Cholesky factor (lower)
+  float L[kSiMaxB * kSiLd];          // inverse Cholesky factor L^{-1} (lower)
+  float Lf[kSiMaxB * kSiLd];         // Cholesky factor L (lower)
+  float red[2 * kSiThreads / 32];    // block reductions
   float theta[kSiMaxB];              // Ritz values by rank (descending)
   float res[kSiMaxB];                // summed squared residuals
   float cs[kSiMaxB / 2][2];
@@ -91,154 +96,219 @@ PROHD_DEV float si_sum(const SiSmem& S, int buf, int idx) {
   return s;
 }
 
-// Cyclic Jacobi on the symmetric b x b matrix A (row stride kSiLd), one warp:
-// A <- Y^T A Y diagonal, Y orthogonal. Disjoint rotations of one round of a
-// round-robin tournament are applied together (rows, then columns).
-PROHD_DEV void si_jacobi(SiSmem& S, int b, int lane) {
+// Pair k of round `round` of a round-robin tournament of n (even) players.
+PROHD_DEV void si_pair(int n, int round, int k, int& p, int& q) {
+  if (k == 0) {
+    p = n - 1;
+    q = round;
+  } else {
+    p = (round + k) % (n - 1);
+    q = (round - k + n - 1) % (n - 1);
+  }
+  if (p > q) {
+    const int t = p;
+    p = q;
+    q = t;
+  }
+}
+
+// Block-wide maxima of two non-negative values (every thread gets them).
+PROHD_DEV void si_block_max2(float& a, float& b, float* red /*[2][kSiThreads/32]*/) {
+  a = warp_max(a);
+  b = warp_max(b);
+  const int w = threadIdx.x >> 5;
+  if ((threadIdx.x & 31) == 0) {
+    red[w] = a;
+    red[kSiThreads / 32 + w] = b;
+  }
+  __syncthreads();
+  a = 0.f;
+  b = 0.f;
+#pragma unroll
+  for (int i = 0; i < kSiThreads / 32; ++i) {
+    a = fmaxf(a, red[i]);
+    b = fmaxf(b, red[kSiThreads / 32 + i]);
+  }
+  __syncthreads();
+}
+
+// Cyclic Jacobi on the symmetric b x b matrix S.M, all threads: S.M <- Y^T M Y
+// diagonal, Y orthogonal. The disjoint rotations J_k of one round of a
+// round-robin tournament act on M as independent 2 x 2 block transforms
+// B_{k1,k2} <- J_{k1}^T B_{k1,k2} J_{k2} (one thread per block) and on Y as
+// column pairs, so a round is two barrier-separated steps. Sweeps stop once
+// every off-diagonal entry is within 4 units of FP32 rounding of the largest
+// diagonal entry (rotations below that only move noise); then each Ritz
+// vector's own residual in H is at most sqrt(b) 2.4e-7 theta_1.
+PROHD_DEV void si_jacobi(SiSmem& S, int b) {
+  const int tid = threadIdx.x;
   float* A = S.M;
   float* Y = S.Y;
-  for (int e = lane; e < b * b; e += 32) {
-    const int r = e / b, c = e - r * b;
-    Y[r * kSiLd + c] = r == c ? 1.f : 0.f;
+  for (int e = tid; e < kSiMaxB * kSiMaxB; e += kSiThreads) {
+    const int r = e >> 5, c = e & 31;
+    if (r < b && c < b) Y[r * kSiLd + c] = r == c ? 1.f : 0.f;
   }
-  __syncwarp();
   const int n = b + (b & 1);  // players; index b is a dummy when b is odd
   const int np = n / 2;
   for (int sweep = 0; sweep < 20; ++sweep) {
     float off = 0.f, dia = 0.f;
-    for (int e = lane; e < b * b; e += 32) {
-      const int r = e / b, c = e - r * b;
-      const float v = A[r * kSiLd + c];
-      if (r != c) off = fmaf(v, v, off);
-      else dia = fmaf(v, v, dia);
+    for (int e = tid; e < kSiMaxB * kSiMaxB; e += kSiThreads) {
+      const int r = e >> 5, c = e & 31;
+      if (r < b && c < b) {
+        const float v = fabsf(A[r * kSiLd + c]);
+        if (r != c) off = fmaxf(off, v);
+        else dia = fmaxf(dia, v);
+      }
     }
-    off = __shfl_sync(0xffffffffu, warp_sum(off), 0);
-    dia = __shfl_sync(0xffffffffu, warp_sum(dia), 0);
-    if (!(off > 1e-14f * dia)) break;
+    si_block_max2(off, dia, S.red);  // also orders the Y initialisation before use
+    if (!(off > 2.4e-7f * dia)) break;
+    const float skip = 6e-8f * dia;
     for (int round = 0; round < n - 1; ++round) {
-      if (lane < np) {
+      if (tid < np) {
         int p, q;
-        if (lane == 0) {
-          p = n - 1;
-          q = round;
-        } else {
-          p = (round + lane) % (n - 1);
-          q = (round - lane + n - 1) % (n - 1);
-        }
-        if (p > q) {
-          const int t = p;
-          p = q;
-          q = t;
-        }
+        si_pair(n, round, tid, p, q);
         float c = 1.f, s = 0.f;
         if (q < b) {
           const float apq = A[p * kSiLd + q];
-          if (apq != 0.f) {
+          if (fabsf(apq) > skip) {
             const float tau = (A[q * kSiLd + q] - A[p * kSiLd + p]) / (2.f * apq);
             const float t = copysignf(1.f, tau) / (fabsf(tau) + sqrtf(fmaf(tau, tau, 1.f)));
             c = 1.f / sqrtf(fmaf(t, t, 1.f));
             s = t * c;
           }
         }
-        S.cs[lane][0] = c;
-        S.cs[lane][1] = s;
-        S.pq[lane][0] = p;
-        S.pq[lane][1] = q;
+        S.cs[tid][0] = c;
+        S.cs[tid][1] = s;
+        S.pq[tid][0] = p;
+        S.pq[tid][1] = q;
       }
-      __syncwarp();
-      for (int e = lane; e < np * b; e += 32) {  // rows p, q
-        const int k = e / b, col = e - k * b;
-        const int p = S.pq[k][0], q = S.pq[k][1];
-        if (q >= b) continue;
-        const float c = S.cs[k][0], s = S.cs[k][1];
-        const float ap = A[p * kSiLd + col], aq = A[q * kSiLd + col];
-        A[p * kSiLd + col] = c * ap - s * aq;
-        A[q * kSiLd + col] = s * ap + c * aq;
+      __syncthreads();
+      // work items: 2 x 2 blocks (k1, k2) of M, then the column pairs of Y
+      const int nblk = np * np;
+      for (int w = tid; w < nblk + b * np; w += kSiThreads) {
+        if (w < nblk) {
+          const int k1 = w / np, k2 = w - k1 * np;
+          const int p1 = S.pq[k1][0], q1 = S.pq[k1][1], p2 = S.pq[k2][0], q2 = S.pq[k2][1];
+          const float c1 = S.cs[k1][0], s1 = S.cs[k1][1], c2 = S.cs[k2][0], s2 = S.cs[k2][1];
+          const bool v1 = q1 < b, v2 = q2 < b;  // a pair with the dummy is the identity on p
+          const float app = A[p1 * kSiLd + p2];
+          const float apq = v2 ? A[p1 * kSiLd + q2] : 0.f;
+          const float aqp = v1 ? A[q1 * kSiLd + p2] : 0.f;
+          const float aqq = v1 && v2 ? A[q1 * kSiLd + q2] : 0.f;
+          // rows: J1^T B
+          const float rpp = c1 * app - s1 * aqp, rpq = c1 * apq - s1 * aqq;
+          const float rqp = s1 * app + c1 * aqp, rqq = s1 * apq + c1 * aqq;
+          // columns: (J1^T B) J2
+          A[p1 * kSiLd + p2] = c2 * rpp - s2 * rpq;
+          if (v2) A[p1 * kSiLd + q2] = s2 * rpp + c2 * rpq;
+          if (v1) A[q1 * kSiLd + p2] = c2 * rqp - s2 * rqq;
+          if (v1 && v2) A[q1 * kSiLd + q2] = s2 * rqp + c2 * rqq;
+        } else {
+          const int e = w - nblk, k = e / b, row = e - k * b;
+          const int p = S.pq[k][0], q = S.pq[k][1];
+          if (q < b) {
+            const float c = S.cs[k][0], s = S.cs[k][1];
+            const float yp = Y[row * kSiLd + p], yq = Y[row * kSiLd + q];
+            Y[row * kSiLd + p] = c * yp - s * yq;
+            Y[row * kSiLd + q] = s * yp + c * yq;
+          }
+        }
       }
-      __syncwarp();
-      for (int e = lane; e < np * b; e += 32) {  // columns p, q of A and of Y
-        const int k = e / b, row = e - k * b;
-        const int p = S.pq[k][0], q = S.pq[k][1];
-        if (q >= b) continue;
-        const float c = S.cs[k][0], s = S.cs[k][1];
-        const float ap = A[row * kSiLd + p], aq = A[row * kSiLd + q];
-        A[row * kSiLd + p] = c * ap - s * aq;
-        A[row * kSiLd + q] = s * ap + c * aq;
-        const float yp = Y[row * kSiLd + p], yq = Y[row * kSiLd + q];
-        Y[row * kSiLd + p] = c * yp - s * yq;
-        Y[row * kSiLd + q] = s * yp + c * yq;
-      }
-      __syncwarp();
+      __syncthreads();
     }
   }
   // Ritz values by rank: descending, lower column first on ties. Every key
   // is computed once into shared memory and all comparisons read those
   // integers, so the ranks are a permutation whatever the values (NaN too).
-  if (lane < b) S.key[lane] = f32_key(A[lane * kSiLd + lane]);
-  __syncwarp();
-  if (lane < b) {
-    const uint32_t kj = S.key[lane];
+  if (tid < b) S.key[tid] = f32_key(A[tid * kSiLd + tid]);
+  __syncthreads();
+  if (tid < b) {
+    const uint32_t kj = S.key[tid];
     int rank = 0;
-    for (int k = 0; k < b; ++k) {
-      const uint32_t kk = S.key[k];
-      rank += (kk > kj) || (kk == kj && k < lane);
+    for (int kk = 0; kk < b; ++kk) {
+      const uint32_t v = S.key[kk];
+      rank += (v > kj) || (v == kj && kk < tid);
     }
-    S.perm[rank] = lane;
-    S.theta[rank] = A[lane * kSiLd + lane];
+    S.perm[rank] = tid;
+    S.theta[rank] = A[tid * kSiLd + tid];
+  }
+  __syncthreads();
+}
+
+// Cholesky S.M = L L^T (warp 0, lane i computes row i of L into S.Lf), then
+// S.L = L^{-1} (lane j forms column j by forward substitution). Rolled loops
+// over shared memory keep the code small. A pivot that rounding drove to or
+// below zero is replaced by a tiny positive one: the column is then noise,
+// which a second pass normalises.
+PROHD_DEV void si_chol_inv(SiSmem& S, int b, int lane) {
+  const float floor_piv = 1e-30f + 1e-12f * fabsf(S.M[0]);
+  float* Lf = S.Lf;
+  for (int j = 0; j < b; ++j) {
+    if (lane >= j && lane < b) {
+      float acc = S.M[lane * kSiLd + j];
+#pragma unroll 4
+      for (int k = 0; k < j; ++k) acc = fmaf(-Lf[lane * kSiLd + k], Lf[j * kSiLd + k], acc);
+      if (lane == j) Lf[j * kSiLd + j] = sqrtf(fmaxf(acc, floor_piv));
+      __syncwarp(0xffffffffu >> (31 - (b - 1)) & ~((1u << j) - 1u));
+      if (lane > j) Lf[lane * kSiLd + j] = acc / Lf[j * kSiLd + j];
+    }
+    __syncwarp();
+  }
+  // column `lane` of L^{-1}: x_i = (delta_{i,lane} - sum_{k<i} L[i][k] x_k) / L[i][i]
+  if (lane < b) {
+    for (int i = 0; i < b; ++i) {
+      float x = 0.f;
+      if (i >= lane) {
+        float acc = i == lane ? 1.f : 0.f;
+#pragma unroll 4
+        for (int k = lane; k < i; ++k) acc = fmaf(-Lf[i * kSiLd + k], S.L[k * kSiLd + lane], acc);
+        x = acc / Lf[i * kSiLd + i];
+      }
+      S.L[i * kSiLd + lane] = x;
+    }
   }
   __syncwarp();
 }
 
-// Cholesky M = L L^T of the summed Gram matrix in S.M (one warp, lane = row).
-// A pivot that rounding drove to or below zero is replaced by a tiny positive
-// one: the corresponding column is then noise, which the second pass
-// normalises.
-PROHD_DEV void si_cholesky(SiSmem& S, int b, int lane) {
-  const float floor_piv = 1e-30f + 1e-12f * fabsf(S.M[0]);
-  for (int j = 0; j < b; ++j) {
-    if (lane == j) {
-      float d = S.M[j * kSiLd + j];
-      for (int k = 0; k < j; ++k) d = fmaf(-S.L[j * kSiLd + k], S.L[j * kSiLd + k], d);
-      S.L[j * kSiLd + j] = sqrtf(fmaxf(d, floor_piv));
-    }
-    __syncwarp();
-    if (lane > j && lane < b) {
-      float v = S.M[lane * kSiLd + j];
-      for (int k = 0; k < j; ++k) v = fmaf(-S.L[lane * kSiLd + k], S.L[j * kSiLd + k], v);
-      S.L[lane * kSiLd + j] = v / S.L[j * kSiLd + j];
-    }
-    __syncwarp();
-  }
-}
-
-// Rows of Wr (local) <- rows of Wr L^{-T}: forward substitution per row.
-PROHD_DEV void si_apply_rinv(SiSmem& S, int nr, int b) {
-  const int i = threadIdx.x;
-  if (i < nr) {
-    float q[kSiMaxB];
-#pragma unroll
-    for (int j = 0; j < kSiMaxB; ++j) {
-      if (j >= b) break;
-      float v = S.Wr[i * b + j];
-      for (int k = 0; k < j; ++k) v = fmaf(-S.L[j * kSiLd + k], q[k], v);
-      q[j] = v / S.L[j * kSiLd + j];
-    }
-#pragma unroll
-    for (int j = 0; j < kSiMaxB; ++j) {
-      if (j >= b) break;
-      S.Wr[i * b + j] = q[j];
+// dst (local rows) = src L^{-T}: dst[i][j] = sum_{k <= j} src[i][k] Linv[j][k].
+PROHD_DEV void si_apply_linv(SiSmem& S, const float* src, float* dst, int nr, int b) {
+  for (int o = threadIdx.x; o < kSiMaxRows * kSiMaxB; o += kSiThreads) {
+    const int i = o >> 5, j = o & 31;
+    if (i < nr && j < b) {
+      float v = 0.f;
+      for (int kk = 0; kk <= j; ++kk) v = fmaf(src[i * b + kk], S.L[j * kSiLd + kk], v);
+      dst[i * b + j] = v;
     }
   }
 }
 
-// part[j*b + k] = sum_i Wr[i][j] Wr[i][k] over local rows.
-PROHD_DEV void si_local_gram(SiSmem& S, int nr, int b) {
-  for (int e = threadIdx.x; e < b * b; e += blockDim.x) {
-    const int j = e / b, k = e - j * b;
-    float s = 0.f;
-    for (int i = 0; i < nr; ++i) s = fmaf(S.Wr[i * b + j], S.Wr[i * b + k], s);
-    S.part[e] = s;
+// part[j*b + k] = sum_i src[i][j] src[i][k] over local rows.
+PROHD_DEV void si_local_gram(SiSmem& S, const float* src, int nr, int b) {
+  for (int e = threadIdx.x; e < kSiMaxB * kSiMaxB; e += kSiThreads) {
+    const int j = e >> 5, k = e & 31;
+    if (j < b && k < b) {
+      float s = 0.f;
+      for (int i = 0; i < nr; ++i) s = fmaf(src[i * b + j], src[i * b + k], s);
+      S.part[j * b + k] = s;
+    }
   }
+}
+
+// The exchange half of a Cholesky-QR pass over the local rows in `src`:
+// local Gram, exchange (n_extra further values of part ride along), summed
+// Gram into S.M and the extra values into S.res.
+PROHD_DEV void si_cholqr_pass(SiSmem& S, const float* src, int nr, int b, uint32_t rank, int& xb, int n_extra) {
+  si_local_gram(S, src, nr, b);
+  __syncthreads();
+  si_broadcast(S, xb, rank, b * b + n_extra);
+  cluster_sync();
+  for (int e = threadIdx.x; e < kSiMaxB * kSiMaxB; e += kSiThreads) {
+    const int j = e >> 5, k = e & 31;
+    if (j < b && k < b) S.M[j * kSiLd + k] = si_sum(S, xb, j * b + k);
+  }
+  for (int j = threadIdx.x; j < n_extra; j += kSiThreads) S.res[j] = si_sum(S, xb, b * b + j);
+  xb ^= 1;
+  __syncthreads();
 }
 
 __global__ void __cluster_dims__(kSiCTAs, 1, 1) __launch_bounds__(kSiThreads, 1)
@@ -252,11 +322,15 @@ __global__ void __cluster_dims__(kSiCTAs, 1, 1) __launch_bounds__(kSiThreads, 1)
   const int nr = r1 - r0;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
 
-  for (int e = tid; e < nr * D; e += kSiThreads) S.Cl[e] = C32[(size_t)r0 * D + e];
+  const int Dq = (D + 3) & ~3;  // C rows and V columns padded with zeros to a multiple of 4
+  for (int e = tid; e < nr * Dq; e += kSiThreads) {
+    const int i = e / Dq, k = e - i * Dq;
+    S.Cl[e] = k < D ? C32[(size_t)(r0 + i) * D + k] : 0.f;
+  }
   // start block: column j is the oracle's start vector of component j + 1
-  for (int e = tid; e < D * b; e += kSiThreads) {
-    const int i = e / b, j = e - i * b;
-    S.V[e] = (float)splitmix64_unit(seed, (uint64_t)(j + 1), (uint64_t)i);
+  for (int e = tid; e < b * Dq; e += kSiThreads) {
+    const int j = e / Dq, i = e - j * Dq;
+    S.Vt[j * kSiVld + i] = i < D ? (float)splitmix64_unit(seed, (uint64_t)(j + 1), (uint64_t)i) : 0.f;
   }
   __syncthreads();
   cluster_sync();
@@ -264,63 +338,94 @@ __global__ void __cluster_dims__(kSiCTAs, 1, 1) __launch_bounds__(kSiThreads, 1)
   int xb = 0;  // exchange buffer
   int t = 0;
   for (;; ++t) {
-    float sigma = 0.f;
     if (t == 0) {
       // first pass only orthonormalises the start block
-      for (int e = tid; e < nr * b; e += kSiThreads) S.Wr[e] = S.V[r0 * b + e];
-      for (int j = tid; j < b; j += kSiThreads) S.part[b * b + j] = 0.f;
+      for (int e = tid; e < nr * b; e += kSiThreads) {
+        const int i = e / b, j = e - i * b;
+        S.Wr[e] = S.Vt[j * kSiVld + r0 + i];
+      }
       __syncthreads();
+      si_cholqr_pass(S, S.Wr, nr, b, rank, xb, 0);
     } else {
-      // ---- W = C V for the local rows: 8-term FFMA blocks, TwoSum across blocks
+      // ---- W = C V for the local rows: 8-term FFMA blocks in two independent
+      // chains (128-bit loads of a row of C and of a column of V), TwoSum
+      // across blocks
       for (int o = tid; o < nr * b; o += kSiThreads) {
         const int i = o / b, j = o - i * b;
-        const float* crow = S.Cl + i * D;
-        float s = 0.f, c = 0.f;
-        int k = 0;
-        for (; k + 8 <= D; k += 8) {
-          float blk = 0.f;
-#pragma unroll
-          for (int u = 0; u < 8; ++u) blk = fmaf(crow[k + u], S.V[(k + u) * b + j], blk);
-          two_sum_acc(s, c, blk);
+        const float4* crow = reinterpret_cast<const float4*>(S.Cl + i * Dq);
+        const float4* vcol = reinterpret_cast<const float4*>(S.Vt + j * kSiVld);
+        float s0 = 0.f, c0 = 0.f, s1 = 0.f, c1 = 0.f;
+        int k4 = 0;
+        const int n4 = Dq >> 2;
+        for (; k4 + 4 <= n4; k4 += 4) {
+          const float4 a0 = crow[k4], a1 = crow[k4 + 1], a2 = crow[k4 + 2], a3 = crow[k4 + 3];
+          const float4 v0 = vcol[k4], v1 = vcol[k4 + 1], v2 = vcol[k4 + 2], v3 = vcol[k4 + 3];
+          float b0 = a0.x * v0.x, b1 = a2.x * v2.x;
+          b0 = fmaf(a0.y, v0.y, b0);
+          b1 = fmaf(a2.y, v2.y, b1);
+          b0 = fmaf(a0.z, v0.z, b0);
+          b1 = fmaf(a2.z, v2.z, b1);
+          b0 = fmaf(a0.w, v0.w, b0);
+          b1 = fmaf(a2.w, v2.w, b1);
+          b0 = fmaf(a1.x, v1.x, b0);
+          b1 = fmaf(a3.x, v3.x, b1);
+          b0 = fmaf(a1.y, v1.y, b0);
+          b1 = fmaf(a3.y, v3.y, b1);
+          b0 = fmaf(a1.z, v1.z, b0);
+          b1 = fmaf(a3.z, v3.z, b1);
+          b0 = fmaf(a1.w, v1.w, b0);
+          b1 = fmaf(a3.w, v3.w, b1);
+          two_sum_acc(s0, c0, b0);
+          two_sum_acc(s1, c1, b1);
         }
-        float blk = 0.f;
-        for (; k < D; ++k) blk = fmaf(crow[k], S.V[k * b + j], blk);
-        two_sum_acc(s, c, blk);
-        S.W[o] = s + c;
+        float bt = 0.f;
+        for (; k4 < n4; ++k4) {
+          const float4 a = crow[k4], v = vcol[k4];
+          bt = fmaf(a.x, v.x, bt);
+          bt = fmaf(a.y, v.y, bt);
+          bt = fmaf(a.z, v.z, bt);
+          bt = fmaf(a.w, v.w, bt);
+        }
+        two_sum_acc(s0, c0, bt);
+        two_sum_acc(s0, c0, s1);
+        S.W[o] = s0 + (c0 + c1);
       }
       __syncthreads();
       // ---- H = V^T W (local rows), exchanged
-      for (int e = tid; e < b * b; e += kSiThreads) {
-        const int j = e / b, k = e - j * b;
-        float s = 0.f;
-        for (int i = 0; i < nr; ++i) s = fmaf(S.V[(r0 + i) * b + j], S.W[i * b + k], s);
-        S.part[e] = s;
+      for (int e = tid; e < kSiMaxB * kSiMaxB; e += kSiThreads) {
+        const int j = e >> 5, k = e & 31;
+        if (j < b && k < b) {
+          float s = 0.f;
+          for (int i = 0; i < nr; ++i) s = fmaf(S.Vt[j * kSiVld + r0 + i], S.W[i * b + k], s);
+          S.part[j * b + k] = s;
+        }
       }
       __syncthreads();
       si_broadcast(S, xb, rank, b * b);
       cluster_sync();
-      for (int e = tid; e < b * b; e += kSiThreads) {
-        const int j = e / b, k = e - j * b;
-        S.M[j * kSiLd + k] = 0.5f * (si_sum(S, xb, j * b + k) + si_sum(S, xb, k * b + j));
+      for (int e = tid; e < kSiMaxB * kSiMaxB; e += kSiThreads) {
+        const int j = e >> 5, k = e & 31;
+        if (j < b && k < b) S.M[j * kSiLd + k] = 0.5f * (si_sum(S, xb, j * b + k) + si_sum(S, xb, k * b + j));
       }
       xb ^= 1;
       __syncthreads();
       // ---- Rayleigh-Ritz
-      if (warp == 0) si_jacobi(S, b, lane);
-      __syncthreads();
+      si_jacobi(S, b);
       const float th0 = fmaxf(S.theta[0], 0.f);
-      sigma = sigma_rel * th0;
-      for (int o = tid; o < nr * b; o += kSiThreads) {
-        const int i = o / b, j = o - i * b;
-        const int col = min(max(S.perm[j], 0), b - 1);
-        float v = 0.f, w = 0.f;
-        for (int k = 0; k < b; ++k) {
-          const float y = S.Y[k * kSiLd + col];
-          v = fmaf(S.V[(r0 + i) * b + k], y, v);
-          w = fmaf(S.W[i * b + k], y, w);
+      const float sigma = sigma_rel * th0;
+      for (int o = tid; o < kSiMaxRows * kSiMaxB; o += kSiThreads) {
+        const int i = o >> 5, j = o & 31;
+        if (i < nr && j < b) {
+          const int col = min(max(S.perm[j], 0), b - 1);
+          float v = 0.f, w = 0.f;
+          for (int kk = 0; kk < b; ++kk) {
+            const float y = S.Y[kk * kSiLd + col];
+            v = fmaf(S.Vt[kk * kSiVld + r0 + i], y, v);
+            w = fmaf(S.W[i * b + kk], y, w);
+          }
+          S.Vr[i * b + j] = v;
+          S.Wr[i * b + j] = w;
         }
-        S.Vr[o] = v;
-        S.Wr[o] = w;
       }
       __syncthreads();
       // residual partials of the m leading pairs, then the scaled block
@@ -334,27 +439,18 @@ __global__ void __cluster_dims__(kSiCTAs, 1, 1) __launch_bounds__(kSiThreads, 1)
           }
         S.part[b * b + j] = s;
       }
-      __syncthreads();
-      for (int o = tid; o < nr * b; o += kSiThreads) {
-        const int j = o % b;
-        const float den = fmaxf(S.theta[j], 0.f) + sigma;
-        S.Wr[o] = den > 1e-30f ? (S.Wr[o] + sigma * S.Vr[o]) / den : S.Vr[o];
+      __syncthreads();  // the residuals read Wr before it is scaled in place
+      for (int o = tid; o < kSiMaxRows * kSiMaxB; o += kSiThreads) {
+        const int i = o >> 5, j = o & 31;
+        if (i < nr && j < b) {
+          const float den = fmaxf(S.theta[j], 0.f) + sigma;
+          const float w = S.Wr[i * b + j], v = S.Vr[i * b + j];
+          S.Wr[i * b + j] = den > 1e-30f ? (w + sigma * v) / den : v;
+        }
       }
       __syncthreads();
-    }
-    // ---- Cholesky-QR, first pass (its exchange also carries the residuals)
-    si_local_gram(S, nr, b);
-    __syncthreads();
-    si_broadcast(S, xb, rank, b * b + b);
-    cluster_sync();
-    for (int e = tid; e < b * b; e += kSiThreads) {
-      const int j = e / b, k = e - j * b;
-      S.M[j * kSiLd + k] = si_sum(S, xb, e);
-    }
-    for (int j = tid; j < b; j += kSiThreads) S.res[j] = si_sum(S, xb, b * b + j);
-    xb ^= 1;
-    __syncthreads();
-    if (t > 0) {
+      // ---- first Cholesky-QR exchange, carrying the residuals
+      si_cholqr_pass(S, S.Wr, nr, b, rank, xb, b);
       bool done = t >= maxit;
       const float lim = eps * fmaxf(S.theta[0], 0.f);
       bool conv = true, bad = !(lim == lim);
@@ -362,8 +458,7 @@ __global__ void __cluster_dims__(kSiCTAs, 1, 1) __launch_bounds__(kSiThreads, 1)
         conv = conv && (sqrtf(S.res[j]) <= lim);
         bad = bad || !(S.res[j] == S.res[j]);
       }
-      done = done || conv || bad;  // NaN input: stop (the Gram pass flags it)
-      if (done) {
+      if (done || conv || bad) {  // NaN input: stop (the Gram pass flags it)
         for (int e = tid; e < nr * m; e += kSiThreads) {
           const int i = e / m, j = e - i * m;
           Uout[(size_t)j * D + r0 + i] = (double)S.Vr[i * b + j];
@@ -372,29 +467,40 @@ __global__ void __cluster_dims__(kSiCTAs, 1, 1) __launch_bounds__(kSiThreads, 1)
         break;
       }
     }
-    if (warp == 0) si_cholesky(S, b, lane);
-    __syncthreads();
-    si_apply_rinv(S, nr, b);
-    __syncthreads();
-    // ---- second pass
-    si_local_gram(S, nr, b);
-    __syncthreads();
-    si_broadcast(S, xb, rank, b * b);
-    cluster_sync();
-    for (int e = tid; e < b * b; e += kSiThreads) {
-      const int j = e / b, k = e - j * b;
-      S.M[j * kSiLd + k] = si_sum(S, xb, e);
+    // ---- finish the first pass (Wr -> W). A second pass (W -> Wr) restores
+    // orthogonality to FP32 rounding when the first one was not well
+    // conditioned: the loss after one pass is about u kappa^2, and the
+    // normalised Gram matrix I + E has kappa <= (1 + (b-1) e) / (1 - (b-1) e)
+    // for off-diagonal correlations |E_jk| <= e, so e <= 1e-2 / b keeps it
+    // within a few units of rounding.
+    float corr = 0.f, dummy = 0.f;
+    for (int e = tid; e < kSiMaxB * kSiMaxB; e += kSiThreads) {
+      const int j = e >> 5, k = e & 31;
+      if (j < b && k < b && j != k) {
+        const float den = sqrtf(S.M[j * kSiLd + j] * S.M[k * kSiLd + k]);
+        corr = fmaxf(corr, den > 0.f ? fabsf(S.M[j * kSiLd + k]) / den : 1.f);
+      }
     }
-    xb ^= 1;
+    si_block_max2(corr, dummy, S.red);
+    const bool second = !(corr <= 1e-2f / (float)b);
+    if (warp == 0) si_chol_inv(S, b, lane);
     __syncthreads();
-    if (warp == 0) si_cholesky(S, b, lane);
+    si_apply_linv(S, S.Wr, S.W, nr, b);
     __syncthreads();
-    si_apply_rinv(S, nr, b);
-    __syncthreads();
+    const float* Q = S.W;
+    if (second) {
+      si_cholqr_pass(S, S.W, nr, b, rank, xb, 0);
+      if (warp == 0) si_chol_inv(S, b, lane);
+      __syncthreads();
+      si_apply_linv(S, S.W, S.Wr, nr, b);
+      __syncthreads();
+      Q = S.Wr;
+    }
     // ---- new rows of V to every CTA
     for (int e = tid; e < nr * b * kSiCTAs; e += kSiThreads) {
       const int c = e / (nr * b), o = e - c * (nr * b);
-      st_cluster_f32(map_to_cta(&S.V[r0 * b + o], (uint32_t)c), S.Wr[o]);
+      const int i = o / b, j = o - i * b;
+      st_cluster_f32(map_to_cta(&S.Vt[j * kSiVld + r0 + i], (uint32_t)c), Q[o]);
     }
     cluster_sync();
   }
@@ -407,8 +513,8 @@ __global__ void __cluster_dims__(kSiCTAs, 1, 1) __launch_bounds__(kSiThreads, 1)
 // normalisation, sign (largest |entry| positive, lowest index on ties).
 __global__ void subspace_finalize_kernel(const double* __restrict__ Uin, int D, int m, double* __restrict__ dirs) {
   __shared__ double u[kSiMaxD];
-  __shared__ double red[kSiThreads / 32];
-  __shared__ unsigned long long s_best[kSiThreads / 32];
+  __shared__ double red[kSiFinThreads / 32];
+  __shared__ unsigned long long s_best[kSiFinThreads / 32];
   __shared__ int s_idx;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   auto block_dot = [&](const double* a, const double* bvec) -> double {
@@ -496,7 +602,7 @@ cudaError_t subspace_run(prohd_ctx* ctx, const float* C32, const double* C64, in
                          uint64_t seed, double* dirs, double* eig, double* scratch, cudaStream_t st) {
   (void)ctx;
   const int b = std::min(D, std::min(kSiMaxB, std::max(2 * m, m + 8)));
-  const float eps = (float)std::max(std::sqrt(2.0 * std::max(tol, 0.0)), 1e-6);
+  const float eps = (float)std::max(std::sqrt(2.0 * std::max(tol, 0.0)), 2e-6);
   double* Uout = scratch;
   double* part = scratch + (size_t)m * D;
   const size_t smem = sizeof(SiSmem);
@@ -507,7 +613,7 @@ cudaError_t subspace_run(prohd_ctx* ctx, const float* C32, const double* C64, in
                                                      nullptr);
   if ((e = cudaGetLastError())) return e;
   count_launch();
-  subspace_finalize_kernel<<<1, kSiThreads, 0, st>>>(Uout, D, m, dirs);
+  subspace_finalize_kernel<<<1, kSiFinThreads, 0, st>>>(Uout, D, m, dirs);
   if (eig) {
     count_launch();
     rayleigh_rows_kernel<<<(D + 7) / 8, 256, 0, st>>>(C64, dirs, D, m, part);

@@ -4,9 +4,12 @@ Centroid axis: the GPU sums FP32-centred values z - s in FP32 partials of at
 most 16 terms before FP64, so each component of a set's mean is within
 16 * 2^-24 * mean|z - s| of the FP64 mean; the axis error is then at most
 2 ||err(ybar - xbar)|| / ||ybar - xbar||, the bound asserted below.
-Principal components are compared by angle: both sides stop when
-1 - |cos| between steps falls below tol, leaving about sqrt(2 tol)/(1 - ratio)
-each (ratio = lambda_{l+1}/lambda_l). The GPU's covariance is accumulated on
+Principal components are compared by angle. The oracle's power iteration
+stops when 1 - |cos| between steps falls below tol, leaving about
+sqrt(2 tol)/(1 - ratio) (ratio = lambda_{l+1}/lambda_l). The GPU's block
+iteration stops when every returned Ritz pair has residual
+||C x - theta x|| <= 2e-6 lambda_1, which bounds its angle to the exact
+eigenvector by 2e-6 lambda_1 / gap_l. The GPU's covariance is accumulated on
 tensor cores from an exact three-way BF16 split of every centred value (six
 products, each within ~2^-24 of z_i z_j), summed in FP32 over 512 points
 (3072 exact products; random-walk error ~sqrt(3072) 2^-24 = 3.3e-6 relative)
@@ -64,7 +67,7 @@ def test_directions_anisotropic(D, m, nA, nB):
     for l in range(1, m + 1):
         ratio = lam[l] / lam[l - 1]
         gap = min(lam[l - 1] - lam[l], lam[l - 2] - lam[l - 1] if l >= 2 else np.inf)
-        tolang = 2 * (2 * np.sqrt(2e-13) / (1 - ratio)) + 1e-5 * lam[0] / gap + 1e-6 / (1 - ratio)
+        tolang = 2 * np.sqrt(2e-13) / (1 - ratio) + (1e-5 + 2e-6) * lam[0] / gap + 1e-6 / (1 - ratio)
         assert _angle(g[l], o[l]) <= tolang, (l, _angle(g[l], o[l]), tolang)
         # same sign convention
         assert float(np.dot(g[l], o[l])) > 0
