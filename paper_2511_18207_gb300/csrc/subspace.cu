@@ -63,6 +63,7 @@ struct SiSmem {
   float L[kSiMaxB * kSiLd];          // inverse Cholesky factor L^{-1} (lower)
   float Lf[kSiMaxB * kSiLd];         // Cholesky factor L (lower)
   float red[2 * kSiThreads / 32];    // block reductions
+  float dinv[kSiMaxB];               // reciprocal Cholesky pivots
   float theta[kSiMaxB];              // Ritz values by rank (descending)
   float res[kSiMaxB];                // summed squared residuals
   float cs[kSiMaxB / 2][2];
@@ -70,6 +71,14 @@ struct SiSmem {
   int perm[kSiMaxB];                 // perm[rank] = column of Y
   uint32_t key[kSiMaxB];             // order keys of the Ritz values
 };
+
+// 1/sqrt(x) for x > 0: the hardware estimate refined by one Newton step
+// (relative error well below FP32 rounding, without the division and square
+// root sequences of IEEE-exact arithmetic on the small matrices' critical paths).
+PROHD_DEV float rsqrt_nr(float x) {
+  const float r = rsqrtf(x);
+  return r * fmaf(-0.5f * x * r, r, 1.5f);
+}
 
 // Error-free s + x accumulated into (s, c).
 PROHD_DEV void two_sum_acc(float& s, float& c, float x) {
@@ -171,9 +180,14 @@ PROHD_DEV void si_jacobi(SiSmem& S, int b) {
         if (q < b) {
           const float apq = A[p * kSiLd + q];
           if (fabsf(apq) > skip) {
-            const float tau = (A[q * kSiLd + q] - A[p * kSiLd + p]) / (2.f * apq);
-            const float t = copysignf(1.f, tau) / (fabsf(tau) + sqrtf(fmaf(tau, tau, 1.f)));
-            c = 1.f / sqrtf(fmaf(t, t, 1.f));
+            // tan of the rotation angle; t only steers the rotation (any
+            // nearby angle still annihilates A[p][q] to rounding), while
+            // c = 1/sqrt(1 + t^2), s = t c keep c^2 + s^2 = 1 to rounding
+            const float tau = __fdividef(A[q * kSiLd + q] - A[p * kSiLd + p], 2.f * apq);
+            const float h = fmaf(tau, tau, 1.f);
+            const float t = fabsf(tau) < 1e18f ? __fdividef(copysignf(1.f, tau), fabsf(tau) + h * rsqrt_nr(h))
+                                               : __fdividef(0.5f, tau);
+            c = rsqrt_nr(fmaf(t, t, 1.f));
             s = t * c;
           }
         }
@@ -243,14 +257,20 @@ PROHD_DEV void si_jacobi(SiSmem& S, int b) {
 PROHD_DEV void si_chol_inv(SiSmem& S, int b, int lane) {
   const float floor_piv = 1e-30f + 1e-12f * fabsf(S.M[0]);
   float* Lf = S.Lf;
+  float* dinv = S.dinv;  // 1 / L[j][j]
   for (int j = 0; j < b; ++j) {
     if (lane >= j && lane < b) {
       float acc = S.M[lane * kSiLd + j];
 #pragma unroll 4
       for (int k = 0; k < j; ++k) acc = fmaf(-Lf[lane * kSiLd + k], Lf[j * kSiLd + k], acc);
-      if (lane == j) Lf[j * kSiLd + j] = sqrtf(fmaxf(acc, floor_piv));
+      if (lane == j) {
+        const float piv = fmaxf(acc, floor_piv);
+        const float r = rsqrt_nr(piv);
+        Lf[j * kSiLd + j] = piv * r;
+        dinv[j] = r;
+      }
       __syncwarp(0xffffffffu >> (31 - (b - 1)) & ~((1u << j) - 1u));
-      if (lane > j) Lf[lane * kSiLd + j] = acc / Lf[j * kSiLd + j];
+      if (lane > j) Lf[lane * kSiLd + j] = acc * dinv[j];
     }
     __syncwarp();
   }
@@ -262,7 +282,7 @@ PROHD_DEV void si_chol_inv(SiSmem& S, int b, int lane) {
         float acc = i == lane ? 1.f : 0.f;
 #pragma unroll 4
         for (int k = lane; k < i; ++k) acc = fmaf(-Lf[i * kSiLd + k], S.L[k * kSiLd + lane], acc);
-        x = acc / Lf[i * kSiLd + i];
+        x = acc * dinv[i];
       }
       S.L[i * kSiLd + lane] = x;
     }
