@@ -30,6 +30,9 @@ namespace prohd {
 // =====================================================================
 
 constexpr int kSimtBM = 128, kSimtBN = 128, kSimtBK = 16;
+// Candidate lists up to this length are rescored by rescore_few_kernel; the
+// tiled kernel takes longer lists (it would spend whole 128-row tiles on them).
+constexpr int kFewRows = 64;
 
 // Persistent tile loop over rows of X (optionally a list of row ids) against
 // all rows of Y. WANT_ROW: rowbest[out_row] = min (d^2, j); WANT_COL:
@@ -45,6 +48,7 @@ __global__ void __launch_bounds__(256, 1)
   __shared__ unsigned long long s_col[WANT_COL ? 16 : 1][WANT_COL ? kSimtBN : 1];
 
   const int64_t nrows = *nrows_dev, ncols = *ncols_dev;
+  if (ROW_LIST && nrows <= kFewRows) return;
   const int64_t nct = (ncols + kSimtBN - 1) / kSimtBN;
   const int64_t ntiles = ((nrows + kSimtBM - 1) / kSimtBM) * nct;
   const int tid = threadIdx.x, ty = tid >> 4, tx = tid & 15;
@@ -147,6 +151,65 @@ __global__ void __launch_bounds__(256, 1)
       }
       __syncthreads();
     }
+  }
+}
+
+// Rescoring of a short candidate list (at most kFewRows rows of X, given by
+// rowlist) against every row of Y, D <= 256: the candidates sit in shared
+// memory, each warp streams rows of Y (lane = dimension, coalesced) and forms
+// the FP32 direct-difference squared distance to every candidate, keeping
+// per candidate the minimum packed (d^2, j). rowbest is indexed by position
+// in the list, as in the tiled kernel.
+__global__ void __launch_bounds__(256)
+    rescore_few_kernel(const float* __restrict__ X, const int32_t* __restrict__ rowlist,
+                       const int64_t* __restrict__ nrows_dev, const float* __restrict__ Y,
+                       const int64_t* __restrict__ ncols_dev, int D, unsigned long long* __restrict__ rowbest) {
+  extern __shared__ __align__(16) float few_sm[];
+  const int64_t nrows = *nrows_dev, ncols = *ncols_dev;
+  if (nrows <= 0 || nrows > kFewRows) return;
+  const int nr = (int)nrows;
+  const int Dp = (D + 31) & ~31;
+  float* xs = few_sm;                                                           // [nr][Dp]
+  unsigned long long* best = reinterpret_cast<unsigned long long*>(xs + (size_t)kFewRows * 256);  // [8][kFewRows]
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int e = threadIdx.x; e < nr * Dp; e += blockDim.x) {
+    const int r = e / Dp, k = e - r * Dp;
+    xs[e] = k < D ? X[(int64_t)rowlist[r] * D + k] : 0.f;
+  }
+  for (int e = threadIdx.x; e < 8 * kFewRows; e += blockDim.x) best[e] = ~0ull;
+  __syncthreads();
+  const int T = Dp >> 5;  // dimensions per lane
+  const int64_t nw = (int64_t)gridDim.x * (blockDim.x >> 5);
+  for (int64_t j = (int64_t)blockIdx.x * (blockDim.x >> 5) + warp; j < ncols; j += nw) {
+    float y[8];
+#pragma unroll
+    for (int t = 0; t < 8; ++t) {
+      const int k = lane + 32 * t;
+      y[t] = (t < T && k < D) ? Y[j * D + k] : 0.f;
+    }
+    for (int r = 0; r < nr; ++r) {
+      const float* xr = xs + r * Dp + lane;
+      float acc = 0.f;
+#pragma unroll
+      for (int t = 0; t < 8; ++t) {
+        if (t < T) {
+          const float d = xr[32 * t] - y[t];
+          acc = fmaf(d, d, acc);
+        }
+      }
+      acc = warp_sum(acc);
+      if (lane == 0) {
+        const unsigned long long pk = pack_min(acc, (uint32_t)j);
+        if (pk < best[warp * kFewRows + r]) best[warp * kFewRows + r] = pk;
+      }
+    }
+  }
+  __syncthreads();
+  for (int r = threadIdx.x; r < nr; r += blockDim.x) {
+    unsigned long long b = ~0ull;
+#pragma unroll
+    for (int w = 0; w < 8; ++w) b = best[w * kFewRows + r] < b ? best[w * kFewRows + r] : b;
+    if (b != ~0ull) atomicMin(rowbest + r, b);
   }
 }
 
@@ -938,7 +1001,17 @@ cudaError_t hd_core(prohd_ctx* ctx, const float* A, const int64_t* nA_dev, int64
   count_launch();
   fill_u64_kernel<<<nsm * 4, 256, 0, st>>>(b.bestB, nB_max, ~0ull);
   if ((e = cudaGetLastError())) return e;
-  // rescore candidate rows of A against all of B, candidate rows of B against all of A
+  // rescore candidate rows of A against all of B, candidate rows of B against all of A:
+  // short lists by rescore_few_kernel, longer ones by the tiled kernel (each
+  // kernel leaves the other's case alone, the list length being on the device)
+  {
+    const size_t fsm = (size_t)kFewRows * 256 * sizeof(float) + (size_t)8 * kFewRows * sizeof(unsigned long long);
+    cudaFuncSetAttribute(rescore_few_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fsm);
+    count_launch();
+    rescore_few_kernel<<<nsm * 2, 256, fsm, st>>>(A, b.candA, &b.sc->ncandA, B, nB_dev, D, b.bestA);
+    count_launch();
+    rescore_few_kernel<<<nsm * 2, 256, fsm, st>>>(B, b.candB, &b.sc->ncandB, A, nA_dev, D, b.bestB);
+  }
   if ((e = launch_simt(true, true, false, A, b.candA, &b.sc->ncandA, B, nB_dev, D, b.bestA, nullptr, nsm, st))) return e;
   if ((e = launch_simt(true, true, false, B, b.candB, &b.sc->ncandB, A, nA_dev, D, b.bestB, nullptr, nsm, st))) return e;
   count_launch();
