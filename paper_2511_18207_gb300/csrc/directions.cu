@@ -25,22 +25,37 @@ namespace prohd {
 
 // ---------------------------------------------------------------- pilot shift
 
-__global__ void pilot_shift_kernel(const float* __restrict__ A, int64_t nA, int D, float* __restrict__ s32) {
-  const int64_t n = nA < 4096 ? nA : 4096;
-  // blockDim = 256; 8 row-groups x 32 column lanes per block, grid over column tiles
-  __shared__ double part[8][33];
+// Column sums of rows [256 y, 256 y + 256) of the first min(n, cap) rows of
+// X, FP64, into part[y][c]; grid (ceil(D/32), ceil(cap/256)). The sums are
+// deterministic (fixed order) and spread over enough blocks to keep the read
+// of a few MB off the critical path.
+__global__ void colsum_part_kernel(const float* __restrict__ X, int64_t n, int cap, int D, double* __restrict__ part) {
+  __shared__ double sh[8][33];
   const int cl = threadIdx.x & 31, rg = threadIdx.x >> 5;
   const int c = blockIdx.x * 32 + cl;
+  const int64_t rows = n < cap ? n : cap;
+  const int64_t r0 = (int64_t)blockIdx.y * 256;
   double s = 0.0;
   if (c < D)
-    for (int64_t i = rg; i < n; i += 8) s += (double)A[i * D + c];
-  part[rg][cl] = s;
+    for (int64_t i = r0 + rg; i < r0 + 256 && i < rows; i += 8) s += (double)X[i * D + c];
+  sh[rg][cl] = s;
   __syncthreads();
   if (rg == 0 && c < D) {
     double t = 0.0;
-    for (int g = 0; g < 8; ++g) t += part[g][cl];
-    s32[c] = (float)(t / (double)n);
+    for (int g = 0; g < 8; ++g) t += sh[g][cl];
+    part[(size_t)blockIdx.y * D + c] = t;
   }
+}
+
+// s32[c] = (sum over slices, in order) / min(n, cap).
+__global__ void pilot_shift_kernel(const double* __restrict__ part, int nslices, int64_t n, int cap, int D,
+                                   float* __restrict__ s32) {
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= D) return;
+  const int64_t rows = n < cap ? n : cap;
+  double t = 0.0;
+  for (int y = 0; y < nslices; ++y) t += part[(size_t)y * D + c];
+  s32[c] = (float)(t / (double)rows);
 }
 
 // ---------------------------------------------------------------- Gram
@@ -593,6 +608,7 @@ constexpr int kMaxSplit = 64;
 
 struct DirBufs {
   float* s32 = nullptr;
+  double* cpart = nullptr;  // pilot column sums per 256-row slice
   double *Gpart = nullptr, *sumApart = nullptr, *sumBpart = nullptr;
   double *G = nullptr, *sumA = nullptr, *sumB = nullptr, *C64 = nullptr;
   double* gc_scratch = nullptr;  // tensor-core Gram partials
@@ -604,6 +620,7 @@ struct DirBufs {
 
 static void dir_layout(Arena& ws, int D, int m, DirBufs& b) {
   b.s32 = ws.take<float>((size_t)D);
+  b.cpart = ws.take<double>((size_t)16 * D);
   if (gram_tc_supported(D)) b.gc_scratch = ws.take<double>(gram_tc_scratch_doubles(D, kMaxSms));
   // CUDA-core Gram (D > 256, D % 4 != 0 or unaligned inputs)
   b.Gpart = ws.take<double>((size_t)kMaxSplit * D * D);
@@ -635,8 +652,14 @@ cudaError_t directions_run(prohd_ctx* ctx, const float* A, int64_t nA, const flo
   if (D > kPiMaxD || m > kPiMaxM) return cudaErrorInvalidValue;
   cudaError_t e;
   const int nsm = ctx->num_sms;
-  count_launch();
-  pilot_shift_kernel<<<(D + 31) / 32, 256, 0, st>>>(A, nA, D, b.s32);
+  {
+    // shift s = mean of the first <= 4096 rows of A (16 slices of 256 rows)
+    const int nsl = (int)std::min<int64_t>(16, ceil_div(std::min<int64_t>(nA, 4096), 256));
+    count_launch();
+    colsum_part_kernel<<<dim3((D + 31) / 32, nsl), 256, 0, st>>>(A, nA, 4096, D, b.cpart);
+    count_launch();
+    pilot_shift_kernel<<<(D + 255) / 256, 256, 0, st>>>(b.cpart, nsl, nA, 4096, D, b.s32);
+  }
   const bool aligned = ((reinterpret_cast<uintptr_t>(A) | reinterpret_cast<uintptr_t>(B)) & 15) == 0;
   if (gram_tc_supported(D) && aligned && ctx->num_sms <= kMaxSms && ctx->encode_tiled) {
     if ((e = gram_tc_run(ctx, A, nA, B, nB, D, b.s32, b.gc_scratch, b.G, b.sumA, b.sumB, status_dev,

@@ -379,7 +379,9 @@ __global__ void gram_tc_reduce_kernel(const GcParams p, int ncta, double* __rest
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < DD + 2 * D;
        e += (int64_t)gridDim.x * blockDim.x) {
     if (e < DD) {
-      const int i = (int)(e / D), j = (int)(e % D);
+      // consecutive threads take consecutive rows i of one column j, so the
+      // partials (stored column-major per CTA) are read coalesced
+      const int j = (int)(e / D), i = (int)(e % D);
       if (j < i) continue;
       int c0, c1, row, col;
       if (i < 128) {
@@ -392,7 +394,7 @@ __global__ void gram_tc_reduce_kernel(const GcParams p, int ncta, double* __rest
         const float2 v = p.gacc[(size_t)c * (256 * 128) + (size_t)col * 128 + row];
         s += (double)v.x - (double)v.y;
       }
-      G[e] = s;
+      G[(int64_t)i * D + j] = s;
     } else {
       const int64_t k = e - DD;
       const int set = k < D ? 0 : 1;

@@ -228,29 +228,41 @@ __global__ void fill_u32_kernel(unsigned* p, int64_t n, unsigned v) {
 
 // Shift s = mean of the first <= 2048 rows of A and of B (FP64 sums), a
 // common origin that keeps ||a - s|| small; distances do not depend on it.
-// One block per 32 columns, 8 row groups.
-__global__ void hd_shift_kernel(const float* __restrict__ A, const int64_t* nA_dev, const float* __restrict__ B,
-                                const int64_t* nB_dev, int D, float* __restrict__ shift) {
-  const int64_t na = *nA_dev < 2048 ? *nA_dev : 2048, nb = *nB_dev < 2048 ? *nB_dev : 2048;
-  __shared__ double part[2][8][33];
+// Stage 1: column sums of 256-row slices, grid (ceil(D/32), 8, 2 sets);
+// stage 2 sums the slices in order. Row counts are read on the device.
+__global__ void hd_colsum_kernel(const float* __restrict__ A, const int64_t* nA_dev, const float* __restrict__ B,
+                                 const int64_t* nB_dev, int D, double* __restrict__ part /*[2][8][D]*/) {
+  __shared__ double sh[8][33];
+  const int set = blockIdx.z;
+  const float* X = set ? B : A;
+  const int64_t n = set ? *nB_dev : *nA_dev;
+  const int64_t rows = n < 2048 ? n : 2048;
   const int cl = threadIdx.x & 31, rg = threadIdx.x >> 5;
   const int c = blockIdx.x * 32 + cl;
-  double sa = 0.0, sb = 0.0;
-  if (c < D) {
-    for (int64_t i = rg; i < na; i += 8) sa += (double)A[i * D + c];
-    for (int64_t i = rg; i < nb; i += 8) sb += (double)B[i * D + c];
-  }
-  part[0][rg][cl] = sa;
-  part[1][rg][cl] = sb;
+  const int64_t r0 = (int64_t)blockIdx.y * 256;
+  double s = 0.0;
+  if (c < D)
+    for (int64_t i = r0 + rg; i < r0 + 256 && i < rows; i += 8) s += (double)X[i * D + c];
+  sh[rg][cl] = s;
   __syncthreads();
   if (rg == 0 && c < D) {
-    double ta = 0.0, tb = 0.0;
-    for (int g = 0; g < 8; ++g) {
-      ta += part[0][g][cl];
-      tb += part[1][g][cl];
-    }
-    shift[c] = (float)(0.5 * (ta / (double)na + tb / (double)nb));
+    double t = 0.0;
+    for (int g = 0; g < 8; ++g) t += sh[g][cl];
+    part[((size_t)set * 8 + blockIdx.y) * D + c] = t;
   }
+}
+
+__global__ void hd_shift_kernel(const double* __restrict__ part, const int64_t* nA_dev, const int64_t* nB_dev, int D,
+                                float* __restrict__ shift) {
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= D) return;
+  const int64_t na = *nA_dev < 2048 ? *nA_dev : 2048, nb = *nB_dev < 2048 ? *nB_dev : 2048;
+  double ta = 0.0, tb = 0.0;
+  for (int y = 0; y < 8; ++y) {
+    ta += part[(size_t)y * D + c];
+    tb += part[(size_t)(8 + y) * D + c];
+  }
+  shift[c] = (float)(0.5 * (ta / (double)na + tb / (double)nb));
 }
 
 // max |x - s| over both sets (in FP32, the same values the copies use), and
@@ -851,6 +863,7 @@ struct HdBufs {
   void* At = nullptr;
   void* Bt = nullptr;
   float *nA2 = nullptr, *nB2 = nullptr, *epsA = nullptr, *epsB = nullptr, *shift = nullptr;
+  double* spart = nullptr;  // shift column sums [2][8][D]
   float* rowmin = nullptr;
   unsigned* colmin = nullptr;
   int32_t *candA = nullptr, *candB = nullptr;
@@ -877,6 +890,7 @@ static void layout(Arena& ws, int64_t nA_max, int64_t nB_max, int D, int precisi
     b.candA = ws.take<int32_t>((size_t)nA_max);
     b.candB = ws.take<int32_t>((size_t)nB_max);
     b.shift = ws.take<float>((size_t)D);
+    b.spart = ws.take<double>((size_t)16 * D);
     b.sc = ws.take<HdScalars>(1);
   }
 }
@@ -940,7 +954,9 @@ cudaError_t hd_core(prohd_ctx* ctx, const float* A, const int64_t* nA_dev, int64
   PhaseTimer pt_prep(ctx, PROHD_PH_HD_PREP, st);
   cudaMemsetAsync(b.sc, 0, sizeof(HdScalars), st);
   count_launch();
-  hd_shift_kernel<<<(D + 31) / 32, 256, 0, st>>>(A, nA_dev, B, nB_dev, D, b.shift);
+  hd_colsum_kernel<<<dim3((D + 31) / 32, 8, 2), 256, 0, st>>>(A, nA_dev, B, nB_dev, D, b.spart);
+  count_launch();
+  hd_shift_kernel<<<(D + 255) / 256, 256, 0, st>>>(b.spart, nA_dev, nB_dev, D, b.shift);
   count_launch();
   hd_maxabs_kernel<<<nsm * 4, 256, 0, st>>>(A, nA_dev, D, b.shift, &b.sc->maxabs, status_dev);
   count_launch();

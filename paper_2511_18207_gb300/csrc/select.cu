@@ -265,6 +265,22 @@ __global__ void radix_pick_kernel(SelProb* __restrict__ P, int nprob, int pass, 
 
 // ---------------------------------------------------------------- band pass
 
+// Float thresholds equivalent to comparing the double of a float with x:
+// for every float v, (double)v < x <=> v < f32_up(x), (double)v <= x <=>
+// v <= f32_down(x), and likewise for > and >= (NaN stays NaN, so every
+// comparison with it stays false). FP64 comparisons per point would cost
+// more than the whole pass on this GPU.
+__device__ __forceinline__ float f32_up(double x) {
+  float f = (float)x;
+  if ((double)f < x) f = nextafterf(f, __int_as_float(0x7f800000));
+  return f;
+}
+__device__ __forceinline__ float f32_down(double x) {
+  float f = (float)x;
+  if ((double)f > x) f = nextafterf(f, __int_as_float(0xff800000));
+  return f;
+}
+
 // Marks certain members, counts them, and lists band members per side.
 // band lists: [2*nd][2][cap] int32
 __global__ void band_kernel(const float* __restrict__ qA, int64_t nA, const float* __restrict__ qB, int64_t nB,
@@ -277,7 +293,9 @@ __global__ void band_kernel(const float* __restrict__ qA, int64_t nA, const floa
   uint8_t* mask = set ? maskB : maskA;
   const double E2 = 2.0 * P[p].E;
   const double Tlo = (double)key_f32(P[p].prefix[0]), Thi = (double)key_f32(P[p].prefix[1]);
-  const double lo_in = Tlo - E2, lo_band = Tlo + E2, hi_in = Thi + E2, hi_band = Thi - E2;
+  // q < lo_in, q <= lo_band, q > hi_in, q >= hi_band in double, as float comparisons
+  const float f_lo_in = f32_up(Tlo - E2), f_lo_band = f32_down(Tlo + E2);
+  const float f_hi_in = f32_down(Thi + E2), f_hi_band = f32_up(Thi - E2);
   int32_t* b0 = band + ((size_t)p * 2 + 0) * cap;
   int32_t* b1 = band + ((size_t)p * 2 + 1) * cap;
   const int lane = threadIdx.x & 31;
@@ -287,11 +305,11 @@ __global__ void band_kernel(const float* __restrict__ qA, int64_t nA, const floa
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < end; i += stride) {
     bool in0 = false, bd0 = false, in1 = false, bd1 = false;
     if (i < n) {
-      const double v = (double)q[i];
-      in0 = v < lo_in;
-      bd0 = !in0 && v <= lo_band;
-      in1 = v > hi_in;
-      bd1 = !in1 && v >= hi_band;
+      const float v = q[i];
+      in0 = v < f_lo_in;
+      bd0 = !in0 && v <= f_lo_band;
+      in1 = v > f_hi_in;
+      bd1 = !in1 && v >= f_hi_band;
       if (in0 || in1) mask[i] = 1;
     }
     c0 += in0;
