@@ -252,6 +252,49 @@ PROHD_DEV uint64_t smem_desc_sw128(uint32_t saddr) {
   return d;
 }
 
+// Same for a K-major tile of 32-byte rows (eight TF32 values) in the
+// 32-byte swizzle: 8-row atoms of 256 bytes.
+PROHD_DEV uint64_t smem_desc_sw32(uint32_t saddr) {
+  uint64_t d = 0;
+  d |= (uint64_t)((saddr & 0x3FFFFu) >> 4);
+  d |= (uint64_t)1 << 16;
+  d |= (uint64_t)(256u >> 4) << 32;
+  d |= (uint64_t)1 << 46;
+  d |= (uint64_t)6 << 61;
+  return d;
+}
+
+// Instruction descriptor, kind::tf32, dense, FP32 accumulator, both operands
+// K-major (format 2 = TF32 in bits 7-9 and 10-12).
+__host__ __device__ constexpr uint32_t idesc_tf32(int M, int N) {
+  return (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+PROHD_DEV void tc_mma_tf32(uint32_t d_tmem, uint64_t a_desc, uint64_t b_desc, uint32_t idesc, uint32_t accumulate) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "setp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
+      "l"(a_desc), "l"(b_desc), "r"(idesc), "r"(accumulate)
+      : "memory");
+}
+
+// 32 lanes x 32 consecutive 32-bit columns, as tc_ld_32x32b_x32, and the
+// minimum of each thread's 32 values.
+PROHD_DEV void tc_ld_red_min_32x32b_x32(uint32_t taddr, float (&v)[32], float& vmin) {
+  asm volatile(
+      "tcgen05.ld.red.sync.aligned.32x32b.x32.min.f32 "
+      "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, "
+      "%16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, %32, [%33];"
+      : "=f"(v[0]), "=f"(v[1]), "=f"(v[2]), "=f"(v[3]), "=f"(v[4]), "=f"(v[5]), "=f"(v[6]), "=f"(v[7]),
+        "=f"(v[8]), "=f"(v[9]), "=f"(v[10]), "=f"(v[11]), "=f"(v[12]), "=f"(v[13]), "=f"(v[14]), "=f"(v[15]),
+        "=f"(v[16]), "=f"(v[17]), "=f"(v[18]), "=f"(v[19]), "=f"(v[20]), "=f"(v[21]), "=f"(v[22]), "=f"(v[23]),
+        "=f"(v[24]), "=f"(v[25]), "=f"(v[26]), "=f"(v[27]), "=f"(v[28]), "=f"(v[29]), "=f"(v[30]), "=f"(v[31]),
+        "=f"(vmin)
+      : "r"(taddr)
+      : "memory");
+}
+
 // Instruction descriptor, kind::f16, dense, FP32 accumulator, both operands
 // K-major: c_format (bits 4-5) = 1 (F32); a/b format (bits 7-9, 10-12) = 0 F16
 // or 1 BF16; N >> 3 in bits 17-22; M >> 4 in bits 24-28.

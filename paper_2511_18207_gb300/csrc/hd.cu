@@ -312,6 +312,23 @@ struct TileT<1> {
   static __device__ __forceinline__ float to(T h) { return __bfloat162float(h); }
 };
 
+// Entry `lane` (0..7) of a row's TF32 norm operand: the squared norm split
+// exactly into three TF32 parts (truncation to 10 explicit mantissa bits
+// leaves 11 + 11 + 2 bits: exact) next to three ones, [h, m, l, 1, 1, 1, 0, 0]
+// for A and [1, 1, 1, h, m, l, 0, 0] for B, so that one TF32 MMA of the two
+// tiles writes ||h_a||^2 + ||h_b||^2 into every accumulator entry.
+__device__ __forceinline__ float tf32_trunc(float v) { return __uint_as_float(__float_as_uint(v) & 0xffffe000u); }
+__device__ __forceinline__ float norm_part(float n2, int side, int lane) {
+  const float h = tf32_trunc(n2);
+  const float r = n2 - h;
+  const float m = tf32_trunc(r);
+  const float l = tf32_trunc(r - m);
+  const int k = side ? lane - 3 : lane;
+  const float part = k == 0 ? h : (k == 1 ? m : l);
+  if (lane >= 6) return 0.f;
+  return (k >= 0 && k < 3) ? part : 1.f;
+}
+
 // One warp per row. Writes the rounded copy h = round((x - s) 2^sigma)
 // (times `mult`: -2 for A, 1 for B) into Xt [n_pad, Dp], ||h||^2 (FP32) into
 // norm2, and eps >= ||(x - s) - h 2^-sigma|| + rounding of x - s (original
@@ -320,7 +337,8 @@ template <int BF16>
 __global__ void hd_prep_kernel(const float* __restrict__ X, const int64_t* n_dev, int64_t n_pad, int D, int Dp,
                                const float* __restrict__ shift, const float* __restrict__ maxabs, float mult,
                                typename TileT<BF16>::T* __restrict__ Xt, float* __restrict__ norm2,
-                               float* __restrict__ eps, float* __restrict__ maxnorm, float* __restrict__ maxeps) {
+                               float* __restrict__ eps, float* __restrict__ maxnorm, float* __restrict__ maxeps,
+                               float* __restrict__ nparts, int side) {
   using TT = TileT<BF16>;
   using T = typename TT::T;
   const int64_t n = *n_dev;
@@ -348,9 +366,10 @@ __global__ void hd_prep_kernel(const float* __restrict__ X, const int64_t* n_dev
         }
         out[c] = TT::from(hv * mult);
       }
-      sn = warp_sum(sn);
+      sn = __shfl_sync(0xffffffffu, warp_sum(sn), 0);
       se = warp_sum(se);
       st = warp_sum(st);
+      if (lane < 8) nparts[r * 8 + lane] = norm_part(sn, side, lane);
       if (lane == 0) {
         // ||(x-s)_exact - h/scale|| <= ||t - h/scale|| + 2^-24 ||t||; the FP32
         // sums of squares are inflated for their own rounding.
@@ -366,6 +385,7 @@ __global__ void hd_prep_kernel(const float* __restrict__ X, const int64_t* n_dev
         norm2[r] = 1e30f;  // padding: far from everything, finite in TMEM
         eps[r] = 0.f;
       }
+      if (lane < 8) nparts[r * 8 + lane] = norm_part(1e30f, side, lane);
     }
   }
   if (lane == 0) {
@@ -384,48 +404,59 @@ __global__ void hd_prep_kernel(const float* __restrict__ X, const int64_t* n_dev
 // through a 4-stage TMA ring in 128B-swizzled 256x64 tiles. Accumulators are
 // double-buffered in TMEM (2 x 256 columns) so the epilogue of tile t
 // overlaps the MMAs of tile t+1.
-// Warps: 0 = TMA producer, 1 = MMA issuer (and TMEM owner), 2..9 = epilogue
-// (warp w reads TMEM lanes 32*(w%4) .. +31 and half (w-2)/4 of the columns).
-// Before a tile's MMAs the epilogue preloads its accumulator with
-// ||h_a||^2 + ||h_b||^2 (tcgen05.st), and the MMAs add (-2 h_a) . h_b, so
-// the accumulator holds the squared distance d2 of every pair. Epilogue per
-// element: row min (registers) and the warp min over 32 rows
-// (redux.sync.min.f32), combined over the four lane quarters in shared
-// memory, then one global atomicMin per column per tile (clamped at 0 so
-// unsigned order = float order).
+// Warps: 0 = TMA producer, 1 = MMA issuer (and TMEM owner), 2..17 = epilogue
+// (warp w reads TMEM lanes 32*(w%4) .. +31 and column quarter (w-2)/4; four
+// warps per lane quarter hide the latency of the per-element work).
+// Each tile starts with one TF32 MMA (K = 8) of two small operands holding
+// exact TF32 splits of the squared norms, which writes ||h_a||^2 + ||h_b||^2
+// into every accumulator entry; the FP16/BF16 MMAs then add (-2 h_a) . h_b,
+// so the accumulator holds the squared distance d2 of every pair. Epilogue per
+// element: the row minimum comes with the TMEM load (tcgen05.ld.red.min), the
+// column minimum over 32 rows is redux.sync.min.f32; both are combined over
+// the CTA in shared memory, then one global atomicMin per column per tile
+// (clamped at 0 so unsigned order = float order). A TMEM buffer goes back to
+// the MMA as soon as it has been read.
 
 constexpr int kTcBM = 128, kTcBN = 256, kTcBK = 64, kTcStages = 4;
 constexpr int kTcAKBytes = kTcBM * kTcBK * 2;   // 16 KB per A K-block
 constexpr int kTcBStage = kTcBN * kTcBK * 2;    // 32 KB per B stage
-constexpr int kTcEpiWarps = 8;
+constexpr int kTcNBBytes = kTcBN * 32;          // 8 KB: B norm operand of one tile (256 rows x 8 TF32)
+constexpr int kTcNABytes = kTcBM * 32;          // 4 KB: A norm operand of one row block
+constexpr int kTcEpiWarps = 16;  // four per TMEM lane quarter, 64 columns each
 constexpr int kTcThreads = (2 + kTcEpiWarps) * 32;
 
 struct TcSmem {
   uint64_t b_full[kTcStages], b_empty[kTcStages];
+  uint64_t nb_full[2], nb_empty[2];
   uint64_t a_full, a_empty;
   uint64_t acc_full[2], acc_empty[2];
   uint64_t drain;
   uint32_t tmem_base;
   int abort;
-  float nb[2][kTcBN];
   float col[2][4][kTcBN];  // [tile parity][lane quarter][column]
-  float rowx[kTcBM];        // second half's row minima at the end of a row block
+  float rowx[3][kTcBM];     // other column groups' row minima at the end of a row block
 };
 
+// [B norm ring 2 x 8 KB][A norm 4 KB][A: KB x 16 KB][B ring][TcSmem]; the small
+// 32-byte-swizzled norm tiles sit first, on 256-byte boundaries.
 __host__ __device__ constexpr size_t tc_smem_bytes(int KB) {
-  return 1024 /*alignment slack*/ + (size_t)KB * kTcAKBytes + (size_t)kTcStages * kTcBStage + sizeof(TcSmem);
+  return 1024 /*alignment slack*/ + 2 * kTcNBBytes + kTcNABytes + (size_t)KB * kTcAKBytes +
+         (size_t)kTcStages * kTcBStage + sizeof(TcSmem);
 }
 
 template <int BF16>
 __global__ void __launch_bounds__(kTcThreads, 1)
     hd_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
-                 const float* __restrict__ nA2, const int64_t* __restrict__ nA_dev, const float* __restrict__ nB2,
-                 const int64_t* __restrict__ nB_dev, int KB, float* __restrict__ rowmin,
-                 unsigned* __restrict__ colmin, int* __restrict__ status, uint64_t timeout_ns) {
+                 const __grid_constant__ CUtensorMap tmNA, const __grid_constant__ CUtensorMap tmNB,
+                 const int64_t* __restrict__ nA_dev, const int64_t* __restrict__ nB_dev, int KB,
+                 float* __restrict__ rowmin, unsigned* __restrict__ colmin, int* __restrict__ status,
+                 uint64_t timeout_ns) {
   extern __shared__ uint8_t smem_raw[];
   uint8_t* base = smem_align<1024>(smem_raw);
-  uint8_t* sA = base;
-  uint8_t* sB = base + (size_t)KB * kTcAKBytes;
+  uint8_t* sNB = base;                        // [2][8 KB]
+  uint8_t* sNA = base + 2 * kTcNBBytes;       // 4 KB
+  uint8_t* sA = sNA + kTcNABytes;             // 1024-aligned (20 KB from base)
+  uint8_t* sB = sA + (size_t)KB * kTcAKBytes;
   TcSmem& S = *reinterpret_cast<TcSmem*>(sB + (size_t)kTcStages * kTcBStage);
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -438,12 +469,14 @@ __global__ void __launch_bounds__(kTcThreads, 1)
       mbar_init(&S.b_full[s], 1);
       mbar_init(&S.b_empty[s], 1);
     }
-    mbar_init(&S.a_full, 1);
-    mbar_init(&S.a_empty, 1);
     for (int b = 0; b < 2; ++b) {
+      mbar_init(&S.nb_full[b], 1);
+      mbar_init(&S.nb_empty[b], 1);
       mbar_init(&S.acc_full[b], 1);
       mbar_init(&S.acc_empty[b], kTcEpiWarps);
     }
+    mbar_init(&S.a_full, 1);
+    mbar_init(&S.a_empty, 1);
     mbar_init(&S.drain, 1);
     S.abort = 0;
     fence_mbar_init();
@@ -455,6 +488,8 @@ __global__ void __launch_bounds__(kTcThreads, 1)
   if (warp == 0 && lane == 0) {
     tma_prefetch_desc(&tmA);
     tma_prefetch_desc(&tmB);
+    tma_prefetch_desc(&tmNA);
+    tma_prefetch_desc(&tmNB);
   }
   tc_fence_before();
   __syncthreads();
@@ -465,14 +500,22 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     // ---------------- TMA producer ----------------
     if (lane == 0) {
       uint32_t st = 0, ph = 0, aph = 0;
-      uint32_t armed = 0, armed_ph = 0;  // stages with a load in flight, and its phase parity
+      uint32_t armed = 0, armed_ph = 0;  // B stages with a load in flight, and its phase parity
+      uint32_t tile = 0;                 // running tile count (B norm ring slot and parity)
+      uint32_t nb_issued = 0;            // B norm loads issued
       bool ok = true;
       for (int rb = blockIdx.x; rb < RB && ok; rb += gridDim.x) {
         if (!mbar_wait_bounded(&S.a_empty, aph ^ 1, abort, timeout_ns)) { ok = false; break; }
         aph ^= 1;
-        mbar_arrive_expect_tx(&S.a_full, (uint32_t)(KB * kTcAKBytes));
+        mbar_arrive_expect_tx(&S.a_full, (uint32_t)(KB * kTcAKBytes + kTcNABytes));
+        tma_load_2d(sNA, &tmNA, 0, rb * kTcBM, &S.a_full);
         for (int kb = 0; kb < KB; ++kb) tma_load_2d(sA + kb * kTcAKBytes, &tmA, kb * kTcBK, rb * kTcBM, &S.a_full);
-        for (int cb = 0; cb < CB && ok; ++cb) {
+        for (int cb = 0; cb < CB && ok; ++cb, ++tile) {
+          const uint32_t ns = tile & 1u, nph = (tile >> 1) & 1u;
+          if (!mbar_wait_bounded(&S.nb_empty[ns], nph ^ 1, abort, timeout_ns)) { ok = false; break; }
+          mbar_arrive_expect_tx(&S.nb_full[ns], (uint32_t)kTcNBBytes);
+          tma_load_2d(sNB + ns * kTcNBBytes, &tmNB, 0, cb * kTcBN, &S.nb_full[ns]);
+          ++nb_issued;
           for (int kb = 0; kb < KB; ++kb) {
             if (!mbar_wait_bounded(&S.b_empty[st], ph ^ 1, abort, timeout_ns)) { ok = false; break; }
             mbar_arrive_expect_tx(&S.b_full[st], (uint32_t)kTcBStage);
@@ -491,6 +534,11 @@ __global__ void __launch_bounds__(kTcThreads, 1)
           while (!mbar_try_wait(&S.b_full[s2], (armed_ph >> s2) & 1u) && global_timer_ns() - t0 < 2000000ull) {
           }
         }
+        for (uint32_t t2 = nb_issued >= 2 ? nb_issued - 2 : 0; t2 < nb_issued; ++t2) {
+          const uint64_t t0 = global_timer_ns();
+          while (!mbar_try_wait(&S.nb_full[t2 & 1u], (t2 >> 1) & 1u) && global_timer_ns() - t0 < 2000000ull) {
+          }
+        }
         const uint64_t t0 = global_timer_ns();
         while (!mbar_try_wait(&S.a_full, aph ^ 1) && global_timer_ns() - t0 < 2000000ull) {
         }
@@ -500,16 +548,24 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     // ---------------- MMA issuer ----------------
     if (lane == 0) {
       constexpr uint32_t idesc = idesc_f16(BF16, kTcBM, kTcBN);
-      uint32_t st = 0, ph = 0, aph = 0, ab = 0, aph2 = 0;
+      constexpr uint32_t idesc_n = idesc_tf32(kTcBM, kTcBN);
+      uint32_t st = 0, ph = 0, aph = 0;
+      uint32_t tile = 0;
       bool ok = true;
       for (int rb = blockIdx.x; rb < RB && ok; rb += gridDim.x) {
         if (!mbar_wait_bounded(&S.a_full, aph, abort, timeout_ns)) { ok = false; break; }
         aph ^= 1;
         tc_fence_after();
-        for (int cb = 0; cb < CB && ok; ++cb) {
-          if (!mbar_wait_bounded(&S.acc_empty[ab], aph2, abort, timeout_ns)) { ok = false; break; }
+        for (int cb = 0; cb < CB && ok; ++cb, ++tile) {
+          const uint32_t ab = tile & 1u, use = tile >> 1;
+          if (!mbar_wait_bounded(&S.acc_empty[ab], (use & 1u) ^ 1u, abort, timeout_ns)) { ok = false; break; }
+          if (!mbar_wait_bounded(&S.nb_full[ab], use & 1u, abort, timeout_ns)) { ok = false; break; }
           tc_fence_after();
-          const uint32_t d_tmem = tmem + (uint32_t)(ab * kTcBN);
+          const uint32_t d_tmem = tmem + ab * (uint32_t)kTcBN;
+          // accumulator = ||h_a||^2 + ||h_b||^2
+          tc_mma_tf32(d_tmem, smem_desc_sw32(smem_u32(sNA)), smem_desc_sw32(smem_u32(sNB + ab * kTcNBBytes)), idesc_n,
+                      0u);
+          tc_commit(&S.nb_empty[ab]);
           for (int kb = 0; kb < KB; ++kb) {
             if (!mbar_wait_bounded(&S.b_full[st], ph, abort, timeout_ns)) { ok = false; break; }
             tc_fence_after();
@@ -523,8 +579,6 @@ __global__ void __launch_bounds__(kTcThreads, 1)
           }
           if (!ok) break;
           tc_commit(&S.acc_full[ab]);
-          ab ^= 1;
-          if (ab == 0) aph2 ^= 1;
         }
         tc_commit(&S.a_empty);
       }
@@ -535,41 +589,18 @@ __global__ void __launch_bounds__(kTcThreads, 1)
       }
     }
   } else {
-    // ---------------- epilogue (warps 2..9) ----------------
+    // ---------------- epilogue (warps 2..17) ----------------
     // Every epilogue warp runs the same tile loop and reaches every named
     // barrier even after an abort (then it only skips the work), so the
     // barriers cannot wait on a warp that left early.
-    const int ew = warp - 2;           // 0..7
-    const int q = warp & 3;            // TMEM lane quarter this warp may access
-    const int hcol = (ew >> 2) * (kTcBN / 2);  // first column of this warp's half
-    const int et = threadIdx.x - 64;   // 0..255
+    const int ew = warp - 2;             // 0..15
+    const int q = warp & 3;              // TMEM lane quarter this warp may access
+    const int grp = ew >> 2;             // column group: four per lane quarter
+    const int hcol = grp * (kTcBN / 4);  // first column of this warp's group
+    const int et = threadIdx.x - 64;     // 0..511 (the first 256 also combine columns)
     const int nrb = (int)blockIdx.x < RB ? (RB - (int)blockIdx.x + (int)gridDim.x - 1) / (int)gridDim.x : 0;
     const int ntile = nrb * CB;
     bool ok = true;
-    // accumulator preload for tile i into buffer buf: ||h_a||^2 + ||h_b||^2
-    auto preload = [&](int i, int buf) {
-      const int prb = (int)blockIdx.x + (i / CB) * (int)gridDim.x, pcb = i % CB;
-      S.nb[buf][et] = nB2[(int64_t)pcb * kTcBN + et];
-      named_bar_sync(1, 32 * kTcEpiWarps);
-      if (!ok) return;
-      const float na_p = nA2[(int64_t)prb * kTcBM + q * 32 + lane];
-      const uint32_t taddr = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(buf * kTcBN + hcol);
-#pragma unroll 1
-      for (int ch = 0; ch < kTcBN / 2 / 32; ++ch) {
-        float v[32];
-#pragma unroll
-        for (int c = 0; c < 32; ++c) v[c] = na_p + S.nb[buf][hcol + ch * 32 + c];
-        __syncwarp();
-        tc_st_32x32b_x32(taddr + ch * 32, v);
-      }
-      tc_wait_st();
-    };
-    for (int i = 0; i < 2 && i < ntile; ++i) {
-      preload(i, i);
-      tc_fence_before();
-      __syncwarp();
-      if (lane == 0) mbar_arrive(&S.acc_empty[i]);
-    }
     float rmin = __int_as_float(0x7f800000);
     for (int i = 0; i < ntile; ++i) {
       const int ab = i & 1;
@@ -584,16 +615,15 @@ __global__ void __launch_bounds__(kTcThreads, 1)
         const uint32_t taddr = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(ab * kTcBN + hcol);
         float v[32];
 #pragma unroll 1
-        for (int ch = 0; ch < kTcBN / 2 / 32; ++ch) {
+        for (int ch = 0; ch < kTcBN / 4 / 32; ++ch) {
           __syncwarp();
-          tc_ld_32x32b_x32(taddr + ch * 32, v);
+          float vmin;
+          tc_ld_red_min_32x32b_x32(taddr + ch * 32, v, vmin);
           tc_wait_ld();
+          rmin = fminf(rmin, vmin);
           float cm[32];
 #pragma unroll
-          for (int c = 0; c < 32; ++c) {
-            rmin = fminf(rmin, v[c]);
-            cm[c] = redux_min_f32(v[c]);
-          }
+          for (int c = 0; c < 32; ++c) cm[c] = redux_min_f32(v[c]);
           if (lane == 0) {
             float4* dst = reinterpret_cast<float4*>(&S.col[ab][q][hcol + ch * 32]);
 #pragma unroll
@@ -601,27 +631,25 @@ __global__ void __launch_bounds__(kTcThreads, 1)
               dst[c] = make_float4(cm[4 * c], cm[4 * c + 1], cm[4 * c + 2], cm[4 * c + 3]);
           }
         }
-      }
-      // refill this buffer for tile i + 2 (the MMA waits for it)
-      if (i + 2 < ntile) preload(i + 2, ab);
-      else named_bar_sync(1, 32 * kTcEpiWarps);
-      if (ok) {
+        // this buffer's TMEM is read: hand it back to the MMA
         tc_fence_before();
         __syncwarp();
         if (lane == 0) mbar_arrive(&S.acc_empty[ab]);
       }
       named_bar_sync(1, 32 * kTcEpiWarps);
-      if (ok) {
+      if (ok && et < kTcBN) {
         const int c = et;
         float m = fminf(fminf(S.col[ab][0][c], S.col[ab][1][c]), fminf(S.col[ab][2][c], S.col[ab][3][c]));
         m = fmaxf(m, 0.f);
         atomicMin(colmin + (int64_t)cb * kTcBN + c, __float_as_uint(m));
       }
       if (cb == CB - 1) {
-        // the two warps of a lane quarter saw one half of the columns each
-        if (ew >= 4) S.rowx[q * 32 + lane] = rmin;
+        // the four warps of a lane quarter saw a quarter of the columns each
+        if (grp > 0) S.rowx[grp - 1][q * 32 + lane] = rmin;
         named_bar_sync(1, 32 * kTcEpiWarps);
-        if (ok && ew < 4) rowmin[(int64_t)rb * kTcBM + q * 32 + lane] = fminf(rmin, S.rowx[q * 32 + lane]);
+        if (ok && grp == 0)
+          rowmin[(int64_t)rb * kTcBM + q * 32 + lane] =
+              fminf(fminf(rmin, S.rowx[0][q * 32 + lane]), fminf(S.rowx[1][q * 32 + lane], S.rowx[2][q * 32 + lane]));
         rmin = __int_as_float(0x7f800000);
       }
     }
@@ -864,6 +892,7 @@ struct HdBufs {
   void* Bt = nullptr;
   float *nA2 = nullptr, *nB2 = nullptr, *epsA = nullptr, *epsB = nullptr, *shift = nullptr;
   double* spart = nullptr;  // shift column sums [2][8][D]
+  float *nA8 = nullptr, *nB8 = nullptr;  // TF32 norm operands [n_pad][8]
   float* rowmin = nullptr;
   unsigned* colmin = nullptr;
   int32_t *candA = nullptr, *candB = nullptr;
@@ -891,6 +920,8 @@ static void layout(Arena& ws, int64_t nA_max, int64_t nB_max, int D, int precisi
     b.candB = ws.take<int32_t>((size_t)nB_max);
     b.shift = ws.take<float>((size_t)D);
     b.spart = ws.take<double>((size_t)16 * D);
+    b.nA8 = ws.take<float>((size_t)b.nA_pad * 8, 1024);
+    b.nB8 = ws.take<float>((size_t)b.nB_pad * 8, 1024);
     b.sc = ws.take<HdScalars>(1);
   }
 }
@@ -964,17 +995,21 @@ cudaError_t hd_core(prohd_ctx* ctx, const float* A, const int64_t* nA_dev, int64
   if (bf16) {
     count_launch();
     hd_prep_kernel<1><<<nsm * 4, 256, 0, st>>>(A, nA_dev, b.nA_pad, D, b.Dp, b.shift, &b.sc->maxabs, -2.f,
-                                              (__nv_bfloat16*)b.At, b.nA2, b.epsA, &b.sc->maxnormA, &b.sc->maxepsA);
+                                              (__nv_bfloat16*)b.At, b.nA2, b.epsA, &b.sc->maxnormA, &b.sc->maxepsA,
+                                              b.nA8, 0);
     count_launch();
     hd_prep_kernel<1><<<nsm * 4, 256, 0, st>>>(B, nB_dev, b.nB_pad, D, b.Dp, b.shift, &b.sc->maxabs, 1.f,
-                                              (__nv_bfloat16*)b.Bt, b.nB2, b.epsB, &b.sc->maxnormB, &b.sc->maxepsB);
+                                              (__nv_bfloat16*)b.Bt, b.nB2, b.epsB, &b.sc->maxnormB, &b.sc->maxepsB,
+                                              b.nB8, 1);
   } else {
     count_launch();
     hd_prep_kernel<0><<<nsm * 4, 256, 0, st>>>(A, nA_dev, b.nA_pad, D, b.Dp, b.shift, &b.sc->maxabs, -2.f,
-                                              (__half*)b.At, b.nA2, b.epsA, &b.sc->maxnormA, &b.sc->maxepsA);
+                                              (__half*)b.At, b.nA2, b.epsA, &b.sc->maxnormA, &b.sc->maxepsA,
+                                              b.nA8, 0);
     count_launch();
     hd_prep_kernel<0><<<nsm * 4, 256, 0, st>>>(B, nB_dev, b.nB_pad, D, b.Dp, b.shift, &b.sc->maxabs, 1.f,
-                                              (__half*)b.Bt, b.nB2, b.epsB, &b.sc->maxnormB, &b.sc->maxepsB);
+                                              (__half*)b.Bt, b.nB2, b.epsB, &b.sc->maxnormB, &b.sc->maxepsB,
+                                              b.nB8, 1);
   }
   count_launch();
   fill_u32_kernel<<<nsm * 2, 256, 0, st>>>(b.colmin, b.nB_pad, 0x7f800000u);
@@ -982,10 +1017,15 @@ cudaError_t hd_core(prohd_ctx* ctx, const float* A, const int64_t* nA_dev, int64
 
   CUtensorMap tmA, tmB;
   const CUtensorMapDataType dt = bf16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT16;
+  CUtensorMap tmNA, tmNB;  // TF32 norm operands: rows of 8 values (32 bytes), 32-byte swizzle
   if (!encode_2d(ctx, &tmA, dt, b.At, (uint64_t)b.Dp, (uint64_t)b.nA_pad, (uint64_t)b.Dp * 2, kTcBK, kTcBM,
                  CU_TENSOR_MAP_SWIZZLE_128B) ||
       !encode_2d(ctx, &tmB, dt, b.Bt, (uint64_t)b.Dp, (uint64_t)b.nB_pad, (uint64_t)b.Dp * 2, kTcBK, kTcBN,
-                 CU_TENSOR_MAP_SWIZZLE_128B))
+                 CU_TENSOR_MAP_SWIZZLE_128B) ||
+      !encode_2d(ctx, &tmNA, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, b.nA8, 8, (uint64_t)b.nA_pad, 32, 8, kTcBM,
+                 CU_TENSOR_MAP_SWIZZLE_32B) ||
+      !encode_2d(ctx, &tmNB, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, b.nB8, 8, (uint64_t)b.nB_pad, 32, 8, kTcBN,
+                 CU_TENSOR_MAP_SWIZZLE_32B))
     return cudaErrorInvalidValue;
   pt_prep.stop();
   const size_t smem = tc_smem_bytes(KB);
@@ -994,19 +1034,21 @@ cudaError_t hd_core(prohd_ctx* ctx, const float* A, const int64_t* nA_dev, int64
   if (bf16) {
     cudaFuncSetAttribute(hd_tc_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     count_launch();
-    hd_tc_kernel<1><<<grid, kTcThreads, smem, st>>>(tmA, tmB, b.nA2, nA_dev, b.nB2, nB_dev, KB, b.rowmin, b.colmin,
+    hd_tc_kernel<1><<<grid, kTcThreads, smem, st>>>(tmA, tmB, tmNA, tmNB, nA_dev, nB_dev, KB, b.rowmin, b.colmin,
                                                     status_dev, (uint64_t)timeout_ns);
   } else {
     cudaFuncSetAttribute(hd_tc_kernel<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     count_launch();
-    hd_tc_kernel<0><<<grid, kTcThreads, smem, st>>>(tmA, tmB, b.nA2, nA_dev, b.nB2, nB_dev, KB, b.rowmin, b.colmin,
+    hd_tc_kernel<0><<<grid, kTcThreads, smem, st>>>(tmA, tmB, tmNA, tmNB, nA_dev, nB_dev, KB, b.rowmin, b.colmin,
                                                     status_dev, (uint64_t)timeout_ns);
   }
   if ((e = cudaGetLastError())) return e;
 
   pt_tc.stop();
   PhaseTimer pt_rs(ctx, PROHD_PH_HD_RESCORE, st);
-  const double c1 = (2.0 * b.Dp + 2.0 * D + 16.0) * 5.9604644775390625e-8;
+  // the norms enter the accumulator through a TF32 MMA of six positive
+  // exact parts (up to eight roundings of |d2|), hence 32 rather than 16
+  const double c1 = (2.0 * b.Dp + 2.0 * D + 32.0) * 5.9604644775390625e-8;
   count_launch();
   hd_bounds_kernel<<<nsm * 2, 256, 0, st>>>(b.rowmin, b.nA2, b.epsA, nA_dev, b.colmin, b.nB2, b.epsB, nB_dev, c1, b.sc);
   count_launch();
