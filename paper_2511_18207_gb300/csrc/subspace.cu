@@ -42,6 +42,7 @@ namespace prohd {
 constexpr int kSiCTAs = 8;
 constexpr int kSiThreads = 512;
 constexpr int kSiFinThreads = 256;
+constexpr int kSiJacThreads = 256;  // the Jacobi rounds run on 8 warps (fewer warps per barrier)
 constexpr int kSiMaxD = 256;
 constexpr int kSiMaxB = 32;
 constexpr int kSiMaxM = 24;
@@ -149,11 +150,32 @@ PROHD_DEV void si_block_max2(float& a, float& b, float* red /*[2][kSiThreads/32]
 // every off-diagonal entry is within 4 units of FP32 rounding of the largest
 // diagonal entry (rotations below that only move noise); then each Ritz
 // vector's own residual in H is at most sqrt(b) 2.4e-7 theta_1.
+// Maxima of two non-negative values over the Jacobi threads (all get them).
+PROHD_DEV void si_jac_max2(float& a, float& b, float* red /*[2][kSiJacThreads/32]*/) {
+  a = warp_max(a);
+  b = warp_max(b);
+  const int w = threadIdx.x >> 5;
+  if ((threadIdx.x & 31) == 0) {
+    red[w] = a;
+    red[kSiJacThreads / 32 + w] = b;
+  }
+  named_bar_sync(1, kSiJacThreads);
+  a = 0.f;
+  b = 0.f;
+#pragma unroll
+  for (int i = 0; i < kSiJacThreads / 32; ++i) {
+    a = fmaxf(a, red[i]);
+    b = fmaxf(b, red[kSiJacThreads / 32 + i]);
+  }
+  named_bar_sync(1, kSiJacThreads);
+}
+
 PROHD_DEV void si_jacobi(SiSmem& S, int b) {
+  // run by the first kSiJacThreads threads, synchronised by named barrier 1
   const int tid = threadIdx.x;
   float* A = S.M;
   float* Y = S.Y;
-  for (int e = tid; e < kSiMaxB * kSiMaxB; e += kSiThreads) {
+  for (int e = tid; e < kSiMaxB * kSiMaxB; e += kSiJacThreads) {
     const int r = e >> 5, c = e & 31;
     if (r < b && c < b) Y[r * kSiLd + c] = r == c ? 1.f : 0.f;
   }
@@ -161,7 +183,7 @@ PROHD_DEV void si_jacobi(SiSmem& S, int b) {
   const int np = n / 2;
   for (int sweep = 0; sweep < 20; ++sweep) {
     float off = 0.f, dia = 0.f;
-    for (int e = tid; e < kSiMaxB * kSiMaxB; e += kSiThreads) {
+    for (int e = tid; e < kSiMaxB * kSiMaxB; e += kSiJacThreads) {
       const int r = e >> 5, c = e & 31;
       if (r < b && c < b) {
         const float v = fabsf(A[r * kSiLd + c]);
@@ -169,7 +191,7 @@ PROHD_DEV void si_jacobi(SiSmem& S, int b) {
         else dia = fmaxf(dia, v);
       }
     }
-    si_block_max2(off, dia, S.red);  // also orders the Y initialisation before use
+    si_jac_max2(off, dia, S.red);  // also orders the Y initialisation before use
     if (!(off > 2.4e-7f * dia)) break;
     const float skip = 6e-8f * dia;
     for (int round = 0; round < n - 1; ++round) {
@@ -196,10 +218,10 @@ PROHD_DEV void si_jacobi(SiSmem& S, int b) {
         S.pq[tid][0] = p;
         S.pq[tid][1] = q;
       }
-      __syncthreads();
+      named_bar_sync(1, kSiJacThreads);
       // work items: 2 x 2 blocks (k1, k2) of M, then the column pairs of Y
       const int nblk = np * np;
-      for (int w = tid; w < nblk + b * np; w += kSiThreads) {
+      for (int w = tid; w < nblk + b * np; w += kSiJacThreads) {
         if (w < nblk) {
           const int k1 = w / np, k2 = w - k1 * np;
           const int p1 = S.pq[k1][0], q1 = S.pq[k1][1], p2 = S.pq[k2][0], q2 = S.pq[k2][1];
@@ -228,14 +250,14 @@ PROHD_DEV void si_jacobi(SiSmem& S, int b) {
           }
         }
       }
-      __syncthreads();
+      named_bar_sync(1, kSiJacThreads);
     }
   }
   // Ritz values by rank: descending, lower column first on ties. Every key
   // is computed once into shared memory and all comparisons read those
   // integers, so the ranks are a permutation whatever the values (NaN too).
   if (tid < b) S.key[tid] = f32_key(A[tid * kSiLd + tid]);
-  __syncthreads();
+  named_bar_sync(1, kSiJacThreads);
   if (tid < b) {
     const uint32_t kj = S.key[tid];
     int rank = 0;
@@ -246,7 +268,7 @@ PROHD_DEV void si_jacobi(SiSmem& S, int b) {
     S.perm[rank] = tid;
     S.theta[rank] = A[tid * kSiLd + tid];
   }
-  __syncthreads();
+  named_bar_sync(1, kSiJacThreads);
 }
 
 // Cholesky S.M = L L^T (warp 0, lane i computes row i of L into S.Lf), then
@@ -258,36 +280,33 @@ PROHD_DEV void si_chol_inv(SiSmem& S, int b, int lane) {
   const float floor_piv = 1e-30f + 1e-12f * fabsf(S.M[0]);
   float* Lf = S.Lf;
   float* dinv = S.dinv;  // 1 / L[j][j]
+  const int row = lane < b ? lane : b - 1;  // lanes past b shadow the last row, their stores are masked
+  // every lane runs the same instructions (stores are predicated), so the
+  // warp never splits
   for (int j = 0; j < b; ++j) {
-    if (lane >= j && lane < b) {
-      float acc = S.M[lane * kSiLd + j];
+    float acc = S.M[row * kSiLd + j];
 #pragma unroll 4
-      for (int k = 0; k < j; ++k) acc = fmaf(-Lf[lane * kSiLd + k], Lf[j * kSiLd + k], acc);
-      if (lane == j) {
-        const float piv = fmaxf(acc, floor_piv);
-        const float r = rsqrt_nr(piv);
-        Lf[j * kSiLd + j] = piv * r;
-        dinv[j] = r;
-      }
-      __syncwarp(0xffffffffu >> (31 - (b - 1)) & ~((1u << j) - 1u));
-      if (lane > j) Lf[lane * kSiLd + j] = acc * dinv[j];
+    for (int k = 0; k < j; ++k) acc = fmaf(-Lf[row * kSiLd + k], Lf[j * kSiLd + k], acc);
+    const float piv = fmaxf(__shfl_sync(0xffffffffu, acc, j), floor_piv);
+    const float r = rsqrt_nr(piv);
+    if (lane == j) {
+      Lf[j * kSiLd + j] = piv * r;
+      dinv[j] = r;
     }
+    if (lane > j && lane < b) Lf[lane * kSiLd + j] = acc * r;
     __syncwarp();
   }
-  // column `lane` of L^{-1}: x_i = (delta_{i,lane} - sum_{k<i} L[i][k] x_k) / L[i][i]
-  if (lane < b) {
-    for (int i = 0; i < b; ++i) {
-      float x = 0.f;
-      if (i >= lane) {
-        float acc = i == lane ? 1.f : 0.f;
+  // column `lane` of L^{-1}: x_i = (delta_{i,lane} - sum_{k<i} L[i][k] x_k) / L[i][i];
+  // x_k = 0 for k < lane, so the sums can start at 0 for every lane
+  const int col = lane < b ? lane : b - 1;
+  for (int i = 0; i < b; ++i) {
+    float acc = i == col ? 1.f : 0.f;
 #pragma unroll 4
-        for (int k = lane; k < i; ++k) acc = fmaf(-Lf[i * kSiLd + k], S.L[k * kSiLd + lane], acc);
-        x = acc * dinv[i];
-      }
-      S.L[i * kSiLd + lane] = x;
-    }
+    for (int k = 0; k < i; ++k) acc = fmaf(-Lf[i * kSiLd + k], S.L[k * kSiLd + col], acc);
+    const float x = i >= col ? acc * dinv[i] : 0.f;
+    if (lane < b) S.L[i * kSiLd + lane] = x;
+    __syncwarp();
   }
-  __syncwarp();
 }
 
 // dst (local rows) = src L^{-T}: dst[i][j] = sum_{k <= j} src[i][k] Linv[j][k].
@@ -430,7 +449,8 @@ __global__ void __cluster_dims__(kSiCTAs, 1, 1) __launch_bounds__(kSiThreads, 1)
       xb ^= 1;
       __syncthreads();
       // ---- Rayleigh-Ritz
-      si_jacobi(S, b);
+      if (tid < kSiJacThreads) si_jacobi(S, b);
+      __syncthreads();
       const float th0 = fmaxf(S.theta[0], 0.f);
       const float sigma = sigma_rel * th0;
       for (int o = tid; o < kSiMaxRows * kSiMaxB; o += kSiThreads) {
