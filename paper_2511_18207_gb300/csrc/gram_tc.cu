@@ -389,19 +389,35 @@ __global__ void gram_tc_reduce_kernel(const GcParams p, int ncta, double* __rest
       } else {
         c0 = p.nc0; c1 = ncta; row = i - 128; col = j - 128;
       }
-      double s = 0.0;
-      for (int c = c0; c < c1; ++c) {
-        const float2 v = p.gacc[(size_t)c * (256 * 128) + (size_t)col * 128 + row];
-        s += (double)v.x - (double)v.y;
+      // four interleaved partial sums (loads in flight), combined in a fixed order
+      double s4[4] = {0.0, 0.0, 0.0, 0.0};
+      int c = c0;
+      for (; c + 4 <= c1; c += 4) {
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          const float2 v = p.gacc[(size_t)(c + u) * (256 * 128) + (size_t)col * 128 + row];
+          s4[u] += (double)v.x - (double)v.y;
+        }
       }
-      G[(int64_t)i * D + j] = s;
+      for (; c < c1; ++c) {
+        const float2 v = p.gacc[(size_t)c * (256 * 128) + (size_t)col * 128 + row];
+        s4[0] += (double)v.x - (double)v.y;
+      }
+      G[(int64_t)i * D + j] = (s4[0] + s4[1]) + (s4[2] + s4[3]);
     } else {
       const int64_t k = e - DD;
       const int set = k < D ? 0 : 1;
       const int d = (int)(set ? k - D : k);
-      double s = 0.0;
+      // one partial sum per converter warp slot (independent loads), combined in order
+      double sw[kGcConv];
+#pragma unroll
+      for (int w = 0; w < kGcConv; ++w) sw[w] = 0.0;
       for (int c = 0; c < p.nc0; ++c)
-        for (int w = 0; w < kGcConv; ++w) s += p.sums[((size_t)c * kGcConv + w) * 2 * p.Dp + (size_t)set * p.Dp + d];
+#pragma unroll
+        for (int w = 0; w < kGcConv; ++w) sw[w] += p.sums[((size_t)c * kGcConv + w) * 2 * p.Dp + (size_t)set * p.Dp + d];
+      double s = 0.0;
+#pragma unroll
+      for (int w = 0; w < kGcConv; ++w) s += sw[w];
       (set ? sumB : sumA)[d] = s;
     }
   }

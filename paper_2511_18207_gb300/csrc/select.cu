@@ -333,10 +333,42 @@ __global__ void band_kernel(const float* __restrict__ qA, int64_t nA, const floa
 }
 
 // FP64 projection exactly as the sequential definition.
-__device__ __forceinline__ double proj64(const float* __restrict__ x, const double* __restrict__ u, int D) {
-  double s = 0.0;
-  for (int k = 0; k < D; ++k) s = __dadd_rn(s, __dmul_rn((double)x[k], u[k]));
-  return s;
+// FP64 keys of every band member, spread over many blocks (FP64 arithmetic is
+// scarce on this GPU: one block per band would serialise a large band's
+// sequential sums on one SM). grid (chunks, 4 * nd): y = problem * 2 + side.
+__global__ void band_keys_kernel(const float* __restrict__ A, const float* __restrict__ B, int D,
+                                 const double* __restrict__ dirs, int nd, const SelProb* __restrict__ P,
+                                 const int32_t* __restrict__ band, uint64_t* __restrict__ bandkey, int64_t cap) {
+  const int p = blockIdx.y >> 1, side = blockIdx.y & 1;
+  const int set = p / nd, d = p % nd;
+  const float* X = set ? B : A;
+  const int64_t b = P[p].nband[side];
+  const int64_t r = P[p].k - P[p].cin[side];
+  if (b == 0 || r <= 0) return;
+  __shared__ double us[1024];
+  const double* u = dirs + (size_t)d * D;
+  const bool u_sm = D <= 1024;
+  if (u_sm)
+    for (int k = threadIdx.x; k < D; k += blockDim.x) us[k] = u[k];
+  __syncthreads();
+  const double* uu = u_sm ? us : u;
+  const int32_t* lst = band + ((size_t)p * 2 + side) * cap;
+  uint64_t* keys = bandkey + ((size_t)p * 2 + side) * cap;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < b; i += (int64_t)gridDim.x * blockDim.x) {
+    double s = 0.0;
+    const float* x = X + (int64_t)lst[i] * D;
+    int k = 0;
+    for (; k + 8 <= D; k += 8) {
+      float xv[8];
+#pragma unroll
+      for (int j = 0; j < 8; ++j) xv[j] = __ldg(x + k + j);
+#pragma unroll
+      for (int j = 0; j < 8; ++j) s = __dadd_rn(s, __dmul_rn((double)xv[j], uu[k + j]));
+    }
+    for (; k < D; ++k) s = __dadd_rn(s, __dmul_rn((double)__ldg(x + k), uu[k]));
+    const uint64_t kk = f64_key(s);
+    keys[i] = side ? ~kk : kk;
+  }
 }
 
 constexpr int kBandSmem = 2048;
@@ -364,16 +396,10 @@ __global__ void __launch_bounds__(512)
   if (b == 0 || r <= 0) return;
   const int32_t* lst = band + ((size_t)p * 2 + side) * cap;
   uint64_t* keys = bandkey + ((size_t)p * 2 + side) * cap;
-
-  auto key_of = [&](int32_t idx) -> uint64_t {
-    uint64_t k = f64_key(proj64(X + (int64_t)idx * D, u, D));
-    return side ? ~k : k;
-  };
-
   if (b <= kBandSmem) {
     for (int64_t i = threadIdx.x; i < b; i += blockDim.x) {
       si[i] = lst[i];
-      sk[i] = key_of(lst[i]);
+      sk[i] = keys[i];
     }
     __syncthreads();
     for (int64_t i = threadIdx.x; i < b; i += blockDim.x) {
@@ -386,9 +412,7 @@ __global__ void __launch_bounds__(512)
     return;
   }
 
-  // large band: keys to global, then radix select of the r-th smallest (key, idx)
-  for (int64_t i = threadIdx.x; i < b; i += blockDim.x) keys[i] = key_of(lst[i]);
-  __syncthreads();
+  // large band: radix select of the r-th smallest (key, idx) over the global keys
   if (threadIdx.x == 0) {
     s_rank = r - 1;
     s_prefix = 0;
@@ -677,6 +701,8 @@ cudaError_t select_run(prohd_ctx* ctx, const float* A, int64_t nA, const float* 
   }
   count_launch();
   band_kernel<<<g, 256, 0, st>>>(b.qA, nA, b.qB, nB, nd, b.P, b.maskA, b.maskB, b.band, b.cap);
+  count_launch();
+  band_keys_kernel<<<dim3(16, 4 * nd), 256, 0, st>>>(A, B, D, dirs, nd, b.P, b.band, b.bandkey, b.cap);
   count_launch();
   band_resolve_kernel<<<4 * nd, 512, 0, st>>>(A, nA, B, nB, D, dirs, nd, b.P, b.band, b.bandkey, b.cap, b.maskA,
                                               b.maskB);
