@@ -319,11 +319,22 @@ def gpu_arm(args):
     if dom == "gram":
         t = cand["gram"][0] / 1e3
         if DIM <= 256 and DIM % 4 == 0:
-            # tensor-core Gram: one read of both sets bounds it (its FLOPs at the
-            # BF16 peak would take less time than the read)
+            # tensor-core Gram: six BF16 split products per point over rows 0-127 x all
+            # columns and rows 128-255 x columns 128-255 (three quarters of the square).
+            # Their time at the sustained BF16 peak exceeds one read of both sets at the
+            # copy bandwidth, so the tensor pipe is the bound; the HBM view is reported too.
+            dp = ((DIM + 63) // 64) * 64
+            per_point = 2.0 * 6 * 128 * (dp + max(dp - 128, 0))
+            fl = per_point * 2 * n
             by = 2.0 * n * DIM * 4
-            roof = {"kernel": "gram_tc_kernel", "bound": "hbm", "achieved": by / t / 1e9, "peak": peaks["hbm_gbs"],
-                    "unit": "GB/s", "traffic": None, "peak_source": f"{peak_src} copy bandwidth"}
+            pk = peaks.get("bf16_tflops_sustained", peaks["bf16_tflops"])
+            # DRAM bytes per launch: ncu capture at 400k + 400k points (profiles/
+            # gram_tc_kernel_400kx256.md), scaled by the number of points
+            traffic = (1.400323e9 + 0.299289e9) * (2.0 * n) / 8.0e5 if DIM == 256 else None
+            roof = {"kernel": "gram_tc_kernel", "bound": "tensor", "achieved": fl / t / 1e12, "peak": pk,
+                    "unit": "TFLOP/s", "traffic": traffic, "peak_source": f"{peak_src} sustained BF16 (cuBLAS)",
+                    "hbm_view": {"achieved_gbs": by / t / 1e9, "peak_gbs": peaks["hbm_gbs"],
+                                 "frac": by / t / 1e9 / peaks["hbm_gbs"]}}
         else:
             fl = 2.0 * (2 * n) * DIM * DIM
             roof = {"kernel": "gram_kernel", "bound": "alu", "achieved": fl / t / 1e12, "peak": fp32_peak,
