@@ -256,6 +256,63 @@ prohd_status prohd_profile_read(prohd_ctx* ctx, double* ms, int64_t* count, int 
 /* Number of kernels this library has launched in this process. */
 uint64_t prohd_launch_count(void);
 
+/* ---------------------------------------------------------------- batched pairs
+ *
+ * ProHD for many independent pairs (Algorithm 3 applied to each pair; the
+ * paper runs its class pairs one at a time). A plan lays the batch out in one
+ * workspace and writes the device tables every stage reads; each stage then
+ * runs as one launch over all pairs, and the whole sequence is captured into
+ * a CUDA graph on first use and replayed.
+ *
+ * Pairs: A, B device pointers, FP32 row-major, 16-byte aligned bases;
+ * 1 <= nA, nB < 2^31; 4 <= D <= 256 with D % 4 == 0; 1 <= m <= min(24, D)
+ * after resolving m < 0 to floor(sqrt(D)). The subset HD of a batch runs the
+ * FP32 direct-difference path (params.precision is not used).
+ */
+typedef struct {
+  const float* A;
+  int64_t nA;
+  const float* B;
+  int64_t nB;
+  int32_t D;
+  int32_t reserved;
+} prohd_pair_desc;
+
+typedef struct prohd_batch prohd_batch;
+
+/* Bytes of workspace a plan of these pairs needs (0 if the pairs are invalid). */
+size_t prohd_batch_workspace_size(const prohd_pair_desc* pairs, int npairs, const prohd_params* p);
+
+/* Plans the batch: copies the pair list (host array of device pointers),
+ * validates it, lays it out in `ws` (device, 256-byte aligned, at least the
+ * size above; owned by the caller and bound to the plan until it is
+ * destroyed), encodes the tensor maps and uploads the tables. Planning
+ * synchronises the device (synchronous copies); running does not. */
+prohd_status prohd_batch_plan(prohd_ctx* ctx, const prohd_pair_desc* pairs, int npairs, const prohd_params* p,
+                              void* ws, size_t ws_bytes, prohd_batch** out);
+void prohd_batch_destroy(prohd_batch* b);
+
+/* Runs the batch on `stream`: out is a device array of npairs results (pair
+ * i's H_hat, witnesses mapped to indices into its own A and B, |I^A|, |I^B|,
+ * status). With graphs on (the default), the first call for a given `out`
+ * captures the sequence on the plan's private stream; every call launches
+ * the graph on `stream`. Asynchronous. */
+prohd_status prohd_estimate_batched(prohd_ctx* ctx, prohd_batch* b, prohd_result* out, void* stream);
+prohd_status prohd_batch_use_graph(prohd_batch* b, int on);
+
+/* Autotuner: times the batch for candidate item sizes (Gram points per work
+ * item, projection rows per item, selection keys per block), one knob at a
+ * time, with CUDA events on `stream`; keeps the fastest in the plan and as
+ * the context's defaults for later plans. Synchronises. best_ms may be NULL. */
+prohd_status prohd_batch_autotune(prohd_ctx* ctx, prohd_batch* b, prohd_result* out, void* stream, double* best_ms);
+prohd_status prohd_batch_get_tunables(const prohd_batch* b, int32_t* gram_pts, int32_t* proj_rows, int32_t* sel_chunk);
+prohd_status prohd_batch_set_tunables(prohd_batch* b, int32_t gram_pts, int32_t proj_rows, int32_t sel_chunk);
+
+/* Device pointers (inside the plan's workspace) of pair `pair`'s directions
+ * [1+m][D] (FP64) and candidate indices (int32, the first nsel_a / nsel_b
+ * entries are valid after a run). */
+prohd_status prohd_batch_pair_outputs(const prohd_batch* b, int pair, double** dirs, int32_t** idxA, int32_t** idxB);
+
 #ifdef __cplusplus
 }
 #endif

@@ -1,0 +1,756 @@
+// Batched ProHD (Algorithm 3 for many independent pairs of uneven sizes).
+//
+// A plan, built once on the host, lays the whole batch out in one workspace
+// and writes the device tables every stage reads: a descriptor per pair, the
+// tensor-core Gram work items with their tensor maps, the projection items,
+// the selection problems, and per-D-class pair lists. Each stage then runs as
+// ONE launch over all pairs:
+//   pilot shift -> Gram (persistent, atomic ticket over items, largest first)
+//   -> Gram reduction -> covariance + centroid axis -> block iteration (one
+//   CTA per pair, one launch per D class) -> FP64 clean-up + Rayleigh
+//   quotients -> projection (one block per item) -> radix select + band
+//   resolution (every (pair, set, direction) problem) -> compaction + gather
+//   -> subset HD (persistent, atomic ticket over 128 x 128 tiles) -> finalize.
+// The sequence is captured once into a CUDA graph and replayed. Item sizes
+// (Gram points per item, projection rows per item, selection keys per
+// block) come from an autotuner that times candidates on the batch itself.
+#include <math.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <algorithm>
+#include <new>
+#include <numeric>
+
+#include "common.cuh"
+#include "internal.h"
+
+using namespace prohd;
+
+namespace {
+
+constexpr int kBatchMaxPairs = 1 << 16;
+constexpr int kTuneGramPts[] = {4096, 8192, 16384, 32768};
+constexpr int kTuneProjRows[] = {4096, 8192, 32768};
+constexpr int kTuneSelChunk[] = {4096, 16384, 131072};
+constexpr int kMinGramPts = 4096;
+constexpr int kMinProjRows = 4096;
+constexpr int kCompactItemsB = 4096;  // mask bytes per compaction block (select.cu)
+
+int resolve_m_b(const prohd_params* p, int D) { return p->m < 0 ? (int)floor(sqrt((double)D)) : p->m; }
+double resolve_ap_b(const prohd_params* p, int m) {
+  return p->alpha_p < 0 ? p->alpha_c / (double)std::max(m, 1) : p->alpha_p;
+}
+
+struct PairPlan {
+  int D, Dp, m, nd;
+  int64_t nA, nB, boundA, boundB;
+};
+
+// Host-side layout of the batch workspace. With a null base it only measures.
+struct BatchLayout {
+  // tables
+  BPair* P;
+  GcItem* items;
+  int* ids;
+  CUtensorMap* maps;
+  ProjItem* pitems;
+  void* probs;
+  double* alpha_of;
+  unsigned* hist;
+  int* order;
+  int* cls;  // [npairs] pair ids grouped by D class
+  int64_t* prefix;
+  // cleared every run
+  char* zero_base;
+  size_t zero_bytes;
+  char* ones_base;
+  size_t ones_bytes;
+  int* gticket;
+  unsigned long long* hticket;
+  int* bstatus;
+  // Gram partial slots
+  char* slots;
+  size_t slot_bytes;
+  // per-pair regions (filled into the BPair table)
+  std::vector<BPair> hp;
+  size_t end;
+};
+
+size_t item_slot_bytes(int N, int Dp) {
+  return round_up((size_t)N * 128 * sizeof(float2), 256) + round_up((size_t)8 * 2 * Dp * sizeof(double), 256);
+}
+
+int64_t items_for(int64_t n, int pts) { return ceil_div(n, pts); }
+
+// Upper bounds of the tables that depend on the tunables.
+void table_caps(const std::vector<PairPlan>& pp, int64_t& max_items, int64_t& max_pitems, size_t& slot_cap,
+                int& nmaps) {
+  max_items = 0;
+  max_pitems = 0;
+  slot_cap = 0;
+  nmaps = 0;
+  for (const auto& q : pp) {
+    const int types = q.Dp > 128 ? 2 : 1;
+    for (int t = 0; t < types; ++t) {
+      const int N = t == 0 ? q.Dp : q.Dp - 128;
+      const int64_t ni = items_for(q.nA, kMinGramPts) + items_for(q.nB, kMinGramPts);
+      max_items += ni;
+      slot_cap += (size_t)ni * item_slot_bytes(N, q.Dp);
+      nmaps += 2;
+    }
+    max_pitems += items_for(q.nA, kMinProjRows) + items_for(q.nB, kMinProjRows);
+  }
+}
+
+void batch_layout(Arena& a, const std::vector<PairPlan>& pp, const prohd_pair_desc* pairs, BatchLayout& L) {
+  const int np = (int)pp.size();
+  int64_t max_items, max_pitems;
+  size_t slot_cap;
+  int nmaps;
+  table_caps(pp, max_items, max_pitems, slot_cap, nmaps);
+  int64_t nprob = 0;
+  for (const auto& q : pp) nprob += 2 * q.nd;
+
+  L.P = a.take<BPair>((size_t)np);
+  L.items = a.take<GcItem>((size_t)max_items);
+  L.ids = a.take<int>((size_t)max_items);
+  L.maps = a.take<CUtensorMap>((size_t)std::max(nmaps, 1));
+  L.pitems = a.take<ProjItem>((size_t)max_pitems);
+  L.probs = a.take<char>((size_t)nprob * sel_prob_bytes());
+  L.alpha_of = a.take<double>((size_t)nprob);
+  L.hist = a.take<unsigned>((size_t)nprob * 512);
+  L.order = a.take<int>((size_t)np);
+  L.cls = a.take<int>((size_t)np);
+  L.prefix = a.take<int64_t>((size_t)np + 1);
+  L.slots = a.take<char>(slot_cap);
+  L.slot_bytes = slot_cap;
+
+  L.hp.assign((size_t)np, BPair{});
+  // per-pair arrays that the stages overwrite completely
+  for (int i = 0; i < np; ++i) {
+    const PairPlan& q = pp[i];
+    BPair& b = L.hp[i];
+    b.A = pairs ? pairs[i].A : nullptr;
+    b.B = pairs ? pairs[i].B : nullptr;
+    b.nA = q.nA;
+    b.nB = q.nB;
+    b.D = q.D;
+    b.Dp = q.Dp;
+    b.m = q.m;
+    b.nd = q.nd;
+    const size_t DD = (size_t)q.D * q.D, mD = (size_t)std::max(q.m, 1) * q.D;
+    b.s32 = a.take<float>((size_t)q.D);
+    b.G = a.take<double>(DD);
+    b.sumA = a.take<double>((size_t)q.D);
+    b.sumB = a.take<double>((size_t)q.D);
+    b.C64 = a.take<double>(DD);
+    b.C32 = a.take<float>(DD);
+    b.U = a.take<double>(mD);
+    b.rpart = a.take<double>(mD);
+    b.dirs = a.take<double>((size_t)q.nd * q.D);
+    b.eig = a.take<double>((size_t)std::max(q.m, 1));
+    b.qA = a.take<float>((size_t)q.nd * q.nA);
+    b.qB = a.take<float>((size_t)q.nd * q.nB);
+    b.idxA = a.take<int32_t>((size_t)q.nA);
+    b.idxB = a.take<int32_t>((size_t)q.nB);
+    b.nsel = a.take<int64_t>(2);
+    b.nblkA = (int)ceil_div(q.nA, kCompactItemsB);
+    b.nblkB = (int)ceil_div(q.nB, kCompactItemsB);
+    b.counts = a.take<unsigned>((size_t)b.nblkA + b.nblkB);
+    b.offsets = a.take<int64_t>((size_t)b.nblkA + b.nblkB);
+    b.As = a.take<float>((size_t)q.boundA * q.D);
+    b.Bs = a.take<float>((size_t)q.boundB * q.D);
+  }
+  // band lists (any size up to the set's)
+  L.end = 0;
+  // regions cleared to zero every run: statuses, maxnorms, masks, tickets
+  a.off = round_up(a.off, 256);
+  L.zero_base = a.base ? a.base + a.off : nullptr;
+  const size_t z0 = a.off;
+  L.gticket = a.take<int>(1, 16);
+  L.hticket = a.take<unsigned long long>(1, 16);
+  L.bstatus = a.take<int>(1, 16);
+  for (int i = 0; i < np; ++i) {
+    BPair& b = L.hp[i];
+    b.status = a.take<int>(1, 16);
+    b.maxnorm = a.take<float>(2, 16);
+  }
+  for (int i = 0; i < np; ++i) {
+    BPair& b = L.hp[i];
+    b.maskA = a.take<uint8_t>((size_t)pp[i].nA, 16);
+    b.maskB = a.take<uint8_t>((size_t)pp[i].nB, 16);
+  }
+  a.off = round_up(a.off, 256);
+  L.zero_bytes = a.off - z0;
+  // region filled with all-ones bytes every run: packed (d^2, index) minima
+  L.ones_base = a.base ? a.base + a.off : nullptr;
+  const size_t o0 = a.off;
+  for (int i = 0; i < np; ++i) {
+    BPair& b = L.hp[i];
+    b.bestA = a.take<unsigned long long>((size_t)pp[i].boundA, 16);
+    b.bestB = a.take<unsigned long long>((size_t)pp[i].boundB, 16);
+  }
+  a.off = round_up(a.off, 256);
+  L.ones_bytes = a.off - o0;
+}
+
+// Band lists per selection problem and side, n entries each (a band can hold
+// the whole set when keys tie).
+void band_layout(Arena& a, const std::vector<PairPlan>& pp, std::vector<int32_t*>& band,
+                 std::vector<uint64_t*>& bkey) {
+  band.clear();
+  bkey.clear();
+  for (const auto& q : pp)
+    for (int set = 0; set < 2; ++set)
+      for (int d = 0; d < q.nd; ++d)
+        for (int side = 0; side < 2; ++side) {
+          const int64_t n = set ? q.nB : q.nA;
+          band.push_back(a.take<int32_t>((size_t)n));
+          bkey.push_back(a.take<uint64_t>((size_t)n));
+        }
+}
+
+prohd_status bfail(prohd_ctx* ctx, prohd_status s, const char* msg) {
+  if (ctx) ctx->err = msg;
+  return s;
+}
+
+prohd_status check_batch(prohd_ctx* ctx, const prohd_pair_desc* pairs, int npairs, const prohd_params* p,
+                         std::vector<PairPlan>& pp) {
+  if (!pairs || npairs < 1 || npairs > kBatchMaxPairs) return bfail(ctx, PROHD_EINVAL, "npairs must be in [1, 65536]");
+  if (!p) return bfail(ctx, PROHD_EINVAL, "null params");
+  if (!(p->alpha_c > 0.0 && p->alpha_c < 1.0)) return bfail(ctx, PROHD_EINVAL, "alpha_c must be in (0, 1)");
+  if (p->alpha_p >= 0.0 && !(p->alpha_p > 0.0 && p->alpha_p < 1.0))
+    return bfail(ctx, PROHD_EINVAL, "alpha_p must be in (0, 1) or negative for alpha_c / m");
+  if (p->power_max_iters < 1) return bfail(ctx, PROHD_EINVAL, "power_max_iters must be >= 1");
+  pp.resize((size_t)npairs);
+  int64_t nprob = 0;
+  for (int i = 0; i < npairs; ++i) {
+    const prohd_pair_desc& d = pairs[i];
+    if (!d.A || !d.B) return bfail(ctx, PROHD_EINVAL, "null point-set pointer in a pair");
+    if (d.nA < 1 || d.nB < 1 || d.nA >= ((int64_t)1 << 31) || d.nB >= ((int64_t)1 << 31))
+      return bfail(ctx, PROHD_EINVAL, "set sizes must be in [1, 2^31)");
+    if (d.D < 4 || d.D > 256 || d.D % 4 != 0)
+      return bfail(ctx, PROHD_ENOTSUP, "batched pairs need D % 4 == 0 and 4 <= D <= 256");
+    if (((reinterpret_cast<uintptr_t>(d.A) | reinterpret_cast<uintptr_t>(d.B)) & 15) != 0)
+      return bfail(ctx, PROHD_EINVAL, "batched point sets need 16-byte aligned bases");
+    PairPlan& q = pp[i];
+    q.D = d.D;
+    q.Dp = (int)round_up(d.D, 64);
+    q.m = resolve_m_b(p, d.D);
+    if (q.m < 1 || q.m > 24 || q.m > d.D) return bfail(ctx, PROHD_ENOTSUP, "batched pairs need 1 <= m <= min(24, D)");
+    q.nd = 1 + q.m;
+    q.nA = d.nA;
+    q.nB = d.nB;
+    const double ap = resolve_ap_b(p, q.m);
+    int64_t sa = 0, sb = 0;
+    for (int k = 0; k < q.nd; ++k) {
+      const double al = k == 0 ? p->alpha_c : ap;
+      sa += 2 * std::min(prohd_k_of(al, q.nA), q.nA);
+      sb += 2 * std::min(prohd_k_of(al, q.nB), q.nB);
+    }
+    q.boundA = std::min(q.nA, sa);
+    q.boundB = std::min(q.nB, sb);
+    nprob += 2 * q.nd;
+  }
+  if (nprob > 32767) return bfail(ctx, PROHD_ENOTSUP, "too many selection problems in one batch (2 x sum of 1 + m)");
+  return PROHD_OK;
+}
+
+__global__ void finish_batched_kernel(const BPair* __restrict__ P, int npairs, const int* __restrict__ bstatus) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= npairs) return;
+  const BPair& q = P[i];
+  q.out->nsel_a = q.nsel[0];
+  q.out->nsel_b = q.nsel[1];
+  const int bs = *bstatus;
+  if (bs > q.out->hd.status) q.out->hd.status = bs;
+}
+
+__global__ void set_out_kernel(BPair* __restrict__ P, int npairs, prohd_result* out) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < npairs) P[i].out = out + i;
+}
+
+}  // namespace
+
+struct prohd_batch {
+  prohd_ctx* ctx = nullptr;
+  int npairs = 0;
+  prohd_params p{};
+  std::vector<prohd_pair_desc> pairs;
+  std::vector<PairPlan> pp;
+  char* ws = nullptr;
+  size_t ws_bytes = 0;
+  BatchLayout L;
+  // tunables
+  int gram_pts = 16384, proj_rows = 8192, sel_chunk = 16384;
+  // table extents for the current tunables
+  int nitems = 0, npitems = 0, nprob = 0;
+  int ncls[3] = {0, 0, 0};
+  int cls_off[3] = {0, 0, 0};
+  int Dmax = 0, ndmax = 0, mmax = 0, nblk_max = 0;
+  int64_t nmax = 0;
+  int grid_gram = 0;
+  // graph
+  bool use_graph = true;
+  cudaStream_t cap_stream = nullptr;
+  cudaGraphExec_t gexec = nullptr;
+  prohd_result* gout = nullptr;
+  uint64_t graph_launches = 0;
+};
+
+namespace {
+
+// Writes the tunable-dependent tables (Gram items, projection items) and the
+// fixed ones (pairs, problems, class lists, orders) into the workspace.
+prohd_status write_tables(prohd_batch* b) {
+  prohd_ctx* ctx = b->ctx;
+  BatchLayout& L = b->L;
+  const int np = b->npairs;
+  const auto& pp = b->pp;
+  // ---- tensor maps: per (pair, set, type)
+  std::vector<CUtensorMap> maps;
+  std::vector<int> map_of((size_t)np * 4, -1);
+  for (int i = 0; i < np; ++i) {
+    const PairPlan& q = pp[i];
+    const int types = q.Dp > 128 ? 2 : 1;
+    for (int t = 0; t < types; ++t)
+      for (int set = 0; set < 2; ++set) {
+        CUtensorMap m;
+        const float* X = set ? b->pairs[i].B : b->pairs[i].A;
+        const int64_t n = set ? q.nB : q.nA;
+        const uint32_t rows = t == 0 ? (uint32_t)std::max(128, q.Dp) : 128u;
+        if (!encode_2d(ctx, &m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, X, (uint64_t)q.D, (uint64_t)n, (uint64_t)q.D * 4,
+                       rows, 64, CU_TENSOR_MAP_SWIZZLE_NONE))
+          return bfail(ctx, PROHD_ECUDA, "tensor-map encoding failed for a batched pair");
+        map_of[(size_t)i * 4 + t * 2 + set] = (int)maps.size();
+        maps.push_back(m);
+      }
+  }
+  // ---- Gram items, largest first; the id list groups each pair's items by type
+  struct HItem {
+    GcItem it;
+    double cost;
+  };
+  std::vector<HItem> hitems;
+  std::vector<int> item_pair, item_type;
+  size_t slot_off = 0;
+  for (int i = 0; i < np; ++i) {
+    const PairPlan& q = pp[i];
+    const int types = q.Dp > 128 ? 2 : 1;
+    for (int t = 0; t < types; ++t) {
+      const int N = t == 0 ? q.Dp : q.Dp - 128;
+      const int rows = t == 0 ? std::max(128, q.Dp) : 128;
+      for (int set = 0; set < 2; ++set) {
+        const int64_t n = set ? q.nB : q.nA;
+        const int64_t ni = items_for(n, b->gram_pts);
+        for (int64_t k = 0; k < ni; ++k) {
+          HItem h;
+          h.it.tm = L.maps + map_of[(size_t)i * 4 + t * 2 + set];
+          h.it.s32 = L.hp[i].s32;
+          h.it.gacc = reinterpret_cast<float2*>(L.slots + slot_off);
+          h.it.sums = reinterpret_cast<double*>(L.slots + slot_off + round_up((size_t)N * 128 * sizeof(float2), 256));
+          slot_off += item_slot_bytes(N, q.Dp);
+          h.it.status = L.hp[i].status;
+          h.it.p0 = n * k / ni;
+          h.it.p1 = n * (k + 1) / ni;
+          h.it.D = q.D;
+          h.it.Dp = q.Dp;
+          h.it.type = t;
+          h.it.setA = set ? 0 : 1;
+          // per-chunk cost model of the kernel (fixed part + output columns + tile rows)
+          h.cost = (double)(h.it.p1 - h.it.p0) * (20.0 + 0.07 * (N + rows));
+          hitems.push_back(h);
+          item_pair.push_back(i);
+          item_type.push_back(t);
+        }
+      }
+    }
+  }
+  if (slot_off > L.slot_bytes) return bfail(ctx, PROHD_ENOMEM, "batch Gram slots exceed the workspace");
+  // execution order: decreasing cost (ticket order)
+  std::vector<int> perm(hitems.size());
+  std::iota(perm.begin(), perm.end(), 0);
+  std::stable_sort(perm.begin(), perm.end(), [&](int x, int y) { return hitems[x].cost > hitems[y].cost; });
+  std::vector<GcItem> items(hitems.size());
+  std::vector<int> pos(hitems.size());
+  for (size_t r = 0; r < perm.size(); ++r) {
+    items[r] = hitems[perm[r]].it;
+    pos[perm[r]] = (int)r;
+  }
+  // id list: per pair, type 0 items (in creation order) then type 1
+  std::vector<int> ids;
+  ids.reserve(hitems.size());
+  for (int i = 0; i < np; ++i) {
+    BPair& bp = L.hp[i];
+    for (int t = 0; t < 2; ++t) {
+      const int start = (int)ids.size();
+      for (size_t h = 0; h < hitems.size(); ++h)
+        if (item_pair[h] == i && item_type[h] == t) ids.push_back(pos[h]);
+      if (t == 0) {
+        bp.gi0 = start;
+        bp.gn0 = (int)ids.size() - start;
+      } else {
+        bp.gi1 = start;
+        bp.gn1 = (int)ids.size() - start;
+      }
+    }
+  }
+  b->nitems = (int)items.size();
+  // ---- projection items, largest first
+  std::vector<ProjItem> pitems;
+  for (int i = 0; i < np; ++i)
+    for (int set = 0; set < 2; ++set) {
+      const int64_t n = set ? pp[i].nB : pp[i].nA;
+      const int64_t ni = items_for(n, b->proj_rows);
+      for (int64_t k = 0; k < ni; ++k) {
+        ProjItem it;
+        it.pair = i;
+        it.set = set;
+        // row ranges start on 256-row tile boundaries
+        it.r0 = std::min(n, round_up(n * k / ni, 256));
+        it.r1 = std::min(n, round_up(n * (k + 1) / ni, 256));
+        if (k == ni - 1) it.r1 = n;
+        if (it.r1 > it.r0) pitems.push_back(it);
+      }
+    }
+  std::stable_sort(pitems.begin(), pitems.end(), [&](const ProjItem& x, const ProjItem& y) {
+    return (x.r1 - x.r0) * (int64_t)pp[x.pair].D > (y.r1 - y.r0) * (int64_t)pp[y.pair].D;
+  });
+  b->npitems = (int)pitems.size();
+  // ---- selection problems
+  Arena ba;
+  ba.base = b->ws;
+  ba.off = L.end;
+  ba.cap = b->ws_bytes;
+  std::vector<int32_t*> band;
+  std::vector<uint64_t*> bkey;
+  band_layout(ba, pp, band, bkey);
+  if (ba.overflow()) return bfail(ctx, PROHD_ENOMEM, "workspace too small for the batch");
+  const size_t pb = sel_prob_bytes();
+  std::vector<char> probs;
+  std::vector<double> alpha_of;
+  int prob = 0;
+  for (int i = 0; i < np; ++i) {
+    const PairPlan& q = pp[i];
+    BPair& bp = L.hp[i];
+    bp.prob0 = prob;
+    const double ap = resolve_ap_b(&b->p, q.m);
+    for (int set = 0; set < 2; ++set)
+      for (int d = 0; d < q.nd; ++d) {
+        const int64_t n = set ? q.nB : q.nA;
+        probs.resize(probs.size() + pb);
+        const size_t bi = (size_t)prob * 2;
+        sel_prob_fill(probs.data() + (size_t)prob * pb, (set ? bp.qB : bp.qA) + (size_t)d * n, n,
+                      set ? bp.B : bp.A, bp.dirs + (size_t)d * q.D, set ? bp.maskB : bp.maskA, bp.maxnorm + set,
+                      q.D, band[bi], band[bi + 1], bkey[bi], bkey[bi + 1]);
+        alpha_of.push_back(d == 0 ? b->p.alpha_c : ap);
+        ++prob;
+      }
+  }
+  b->nprob = prob;
+  // ---- D classes and the subset-HD order
+  std::vector<int> cls;
+  for (int c = 0; c < 3; ++c) {
+    b->cls_off[c] = (int)cls.size();
+    const int lo = c == 0 ? 0 : (c == 1 ? 64 : 128), hi = c == 0 ? 64 : (c == 1 ? 128 : 256);
+    for (int i = 0; i < np; ++i)
+      if (pp[i].D > lo && pp[i].D <= hi) cls.push_back(i);
+    b->ncls[c] = (int)cls.size() - b->cls_off[c];
+  }
+  std::vector<int> order((size_t)np);
+  std::iota(order.begin(), order.end(), 0);
+  std::stable_sort(order.begin(), order.end(), [&](int x, int y) {
+    return pp[x].boundA * pp[x].boundB * pp[x].D > pp[y].boundA * pp[y].boundB * pp[y].D;
+  });
+  for (int i = 0; i < np; ++i) {
+    L.hp[i].iters = b->p.power_max_iters;
+    L.hp[i].out = nullptr;
+  }
+  // ---- upload (planning is allowed to synchronise)
+  cudaError_t e = cudaSuccess;
+  auto up = [&](void* dst, const void* src, size_t bytes) {
+    if (e == cudaSuccess && bytes) e = cudaMemcpy(dst, src, bytes, cudaMemcpyHostToDevice);
+  };
+  up(L.P, L.hp.data(), sizeof(BPair) * np);
+  up(L.items, items.data(), sizeof(GcItem) * items.size());
+  up(L.ids, ids.data(), sizeof(int) * ids.size());
+  up(L.maps, maps.data(), sizeof(CUtensorMap) * maps.size());
+  up(L.pitems, pitems.data(), sizeof(ProjItem) * pitems.size());
+  up(L.probs, probs.data(), probs.size());
+  up(L.alpha_of, alpha_of.data(), sizeof(double) * alpha_of.size());
+  up(L.order, order.data(), sizeof(int) * order.size());
+  up(L.cls, cls.data(), sizeof(int) * cls.size());
+  if (e) {
+    ctx->err = std::string("CUDA error while planning the batch: ") + cudaGetErrorString(e);
+    return PROHD_ECUDA;
+  }
+  // any graph built on the old tables is stale
+  if (b->gexec) {
+    cudaGraphExecDestroy(b->gexec);
+    b->gexec = nullptr;
+    b->gout = nullptr;
+  }
+  return PROHD_OK;
+}
+
+cudaError_t enqueue(prohd_batch* b, prohd_result* out, cudaStream_t st) {
+  BatchLayout& L = b->L;
+  prohd_ctx* ctx = b->ctx;
+  const int np = b->npairs;
+  cudaError_t e;
+  count_launch();
+  set_out_kernel<<<(np + 255) / 256, 256, 0, st>>>(L.P, np, out);
+  if ((e = cudaMemsetAsync(L.zero_base, 0, L.zero_bytes, st))) return e;
+  if ((e = cudaMemsetAsync(L.ones_base, 0xff, L.ones_bytes, st))) return e;
+  {
+    PhaseTimer pt(ctx, PROHD_PH_GRAM, st);
+    if ((e = pilot_batched(L.P, np, st))) return e;
+    if ((e = gram_tc_batched(L.items, b->nitems, L.gticket, L.bstatus, b->grid_gram, b->p.wait_timeout_ns, st)))
+      return e;
+    if ((e = gram_reduce_batched(L.P, np, L.items, L.ids, b->Dmax, st))) return e;
+  }
+  {
+    PhaseTimer pt(ctx, PROHD_PH_POWER, st);
+    if ((e = covariance_batched(L.P, np, b->Dmax, st))) return e;
+    const int* lists[3] = {L.cls + b->cls_off[0], L.cls + b->cls_off[1], L.cls + b->cls_off[2]};
+    if ((e = subspace_batched(L.P, lists, b->ncls, np, b->Dmax, b->mmax, b->p.power_tol, b->p.seed, st))) return e;
+  }
+  {
+    PhaseTimer pt(ctx, PROHD_PH_PROJECT, st);
+    if ((e = proj_batched(L.P, L.pitems, b->npitems, b->ndmax, L.bstatus, st))) return e;
+  }
+  {
+    PhaseTimer pt(ctx, PROHD_PH_SELECT, st);
+    if ((e = select_batched(reinterpret_cast<SelProb*>(L.probs), b->nprob, L.alpha_of, L.hist, b->nmax, b->sel_chunk,
+                            st)))
+      return e;
+  }
+  {
+    PhaseTimer pt(ctx, PROHD_PH_GATHER, st);
+    if ((e = compact_gather_batched(L.P, np, b->nblk_max, b->nmax, st))) return e;
+  }
+  {
+    PhaseTimer pt(ctx, PROHD_PH_HD_CONTRACT, st);
+    if ((e = hd_simt_batched(L.P, L.order, np, L.prefix, L.hticket, ctx->num_sms, st))) return e;
+  }
+  count_launch();
+  finish_batched_kernel<<<(np + 255) / 256, 256, 0, st>>>(L.P, np, L.bstatus);
+  return cudaGetLastError();
+}
+
+size_t batch_bytes(const std::vector<PairPlan>& pp) {
+  Arena a;
+  BatchLayout L;
+  batch_layout(a, pp, nullptr, L);
+  std::vector<int32_t*> band;
+  std::vector<uint64_t*> bkey;
+  band_layout(a, pp, band, bkey);
+  return a.off + 256;
+}
+
+}  // namespace
+
+extern "C" {
+
+size_t prohd_batch_workspace_size(const prohd_pair_desc* pairs, int npairs, const prohd_params* p) {
+  std::vector<PairPlan> pp;
+  if (check_batch(nullptr, pairs, npairs, p, pp) != PROHD_OK) return 0;
+  return batch_bytes(pp);
+}
+
+prohd_status prohd_batch_plan(prohd_ctx* ctx, const prohd_pair_desc* pairs, int npairs, const prohd_params* p,
+                              void* ws, size_t ws_bytes, prohd_batch** out) {
+  if (!ctx || !out) return PROHD_EINVAL;
+  *out = nullptr;
+  std::vector<PairPlan> pp;
+  prohd_status s = check_batch(ctx, pairs, npairs, p, pp);
+  if (s != PROHD_OK) return s;
+  if (!ctx->encode_tiled) return bfail(ctx, PROHD_ENOTSUP, "driver has no tensor-map encoder");
+  if (ctx->num_sms > kMaxSms) return bfail(ctx, PROHD_ENOTSUP, "more SMs than this build sizes for");
+  if (!ws || (reinterpret_cast<uintptr_t>(ws) & 255)) return bfail(ctx, PROHD_EINVAL, "workspace must be 256-byte aligned");
+  if (ws_bytes < batch_bytes(pp)) return bfail(ctx, PROHD_ENOMEM, "workspace too small for the batch");
+  prohd_batch* b = new (std::nothrow) prohd_batch();
+  if (!b) return PROHD_ENOMEM;
+  b->ctx = ctx;
+  b->npairs = npairs;
+  b->p = *p;
+  if (b->p.wait_timeout_ns <= 0) b->p.wait_timeout_ns = kDefaultTimeoutNs;
+  b->pairs.assign(pairs, pairs + npairs);
+  b->pp = pp;
+  b->ws = static_cast<char*>(ws);
+  b->ws_bytes = ws_bytes;
+  Arena a;
+  a.base = b->ws;
+  a.cap = ws_bytes;
+  batch_layout(a, pp, pairs, b->L);
+  b->L.end = a.off;
+  for (const auto& q : pp) {
+    b->Dmax = std::max(b->Dmax, q.D);
+    b->ndmax = std::max(b->ndmax, q.nd);
+    b->mmax = std::max(b->mmax, q.m);
+    b->nmax = std::max(b->nmax, std::max(q.nA, q.nB));
+    b->nblk_max = std::max(b->nblk_max, (int)ceil_div(std::max(q.nA, q.nB), kCompactItemsB));
+  }
+  b->grid_gram = ctx->num_sms;
+  if (ctx->batch_tuned) {
+    b->gram_pts = ctx->batch_gram_pts;
+    b->proj_rows = ctx->batch_proj_rows;
+    b->sel_chunk = ctx->batch_sel_chunk;
+  }
+  if (cudaStreamCreateWithFlags(&b->cap_stream, cudaStreamNonBlocking) != cudaSuccess) {
+    delete b;
+    return bfail(ctx, PROHD_ECUDA, "could not create the capture stream");
+  }
+  s = write_tables(b);
+  if (s != PROHD_OK) {
+    cudaStreamDestroy(b->cap_stream);
+    delete b;
+    return s;
+  }
+  *out = b;
+  return PROHD_OK;
+}
+
+void prohd_batch_destroy(prohd_batch* b) {
+  if (!b) return;
+  if (b->gexec) cudaGraphExecDestroy(b->gexec);
+  if (b->cap_stream) cudaStreamDestroy(b->cap_stream);
+  delete b;
+}
+
+prohd_status prohd_batch_use_graph(prohd_batch* b, int on) {
+  if (!b) return PROHD_EINVAL;
+  b->use_graph = on != 0;
+  return PROHD_OK;
+}
+
+prohd_status prohd_estimate_batched(prohd_ctx* ctx, prohd_batch* b, prohd_result* out, void* stream) {
+  if (!ctx || !b || !out || b->ctx != ctx) return bfail(ctx, PROHD_EINVAL, "bad batch arguments");
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  cudaError_t e;
+  if (!b->use_graph || ctx->profiling) {
+    if ((e = enqueue(b, out, st))) {
+      ctx->err = std::string("CUDA error: ") + cudaGetErrorString(e);
+      return PROHD_ECUDA;
+    }
+    return PROHD_OK;
+  }
+  if (!b->gexec || b->gout != out) {
+    // capture the whole batch once on the plan's own stream; replays go to `stream`
+    if (b->gexec) {
+      cudaGraphExecDestroy(b->gexec);
+      b->gexec = nullptr;
+    }
+    const uint64_t l0 = g_launches.load();
+    cudaGraph_t g = nullptr;
+    e = cudaStreamBeginCapture(b->cap_stream, cudaStreamCaptureModeThreadLocal);
+    if (!e) {
+      cudaError_t e2 = enqueue(b, out, b->cap_stream);
+      e = cudaStreamEndCapture(b->cap_stream, &g);
+      if (!e) e = e2;
+    }
+    if (!e) e = cudaGraphInstantiate(&b->gexec, g, 0);
+    if (g) cudaGraphDestroy(g);
+    // kernels enqueued during capture run only when the graph is launched
+    const uint64_t in_graph = g_launches.load() - l0;
+    g_launches.fetch_sub(in_graph);
+    if (e) {
+      b->gexec = nullptr;
+      ctx->err = std::string("CUDA error while capturing the batch: ") + cudaGetErrorString(e);
+      return PROHD_ECUDA;
+    }
+    b->graph_launches = in_graph;
+    b->gout = out;
+  }
+  if ((e = cudaGraphLaunch(b->gexec, st))) {
+    ctx->err = std::string("CUDA error: ") + cudaGetErrorString(e);
+    return PROHD_ECUDA;
+  }
+  count_launch((int)b->graph_launches);
+  return PROHD_OK;
+}
+
+// Coordinate search over the three tunables, timing the whole batch with
+// CUDA events on `stream` (synchronises). The best values are kept in the
+// plan and as the context's defaults for later plans.
+prohd_status prohd_batch_autotune(prohd_ctx* ctx, prohd_batch* b, prohd_result* out, void* stream, double* best_ms) {
+  if (!ctx || !b || !out) return bfail(ctx, PROHD_EINVAL, "bad batch arguments");
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  auto time_once = [&](float& ms) -> prohd_status {
+    prohd_status s = write_tables(b);
+    if (s != PROHD_OK) return s;
+    for (int rep = 0; rep < 3; ++rep) {
+      if (rep == 1) cudaEventRecord(e0, st);
+      if (enqueue(b, out, st)) return bfail(ctx, PROHD_ECUDA, "launch failed while tuning");
+    }
+    cudaEventRecord(e1, st);
+    if (cudaEventSynchronize(e1) != cudaSuccess) return bfail(ctx, PROHD_ECUDA, "tuning run failed");
+    cudaEventElapsedTime(&ms, e0, e1);
+    ms *= 0.5f;
+    return PROHD_OK;
+  };
+  float best = 1e30f;
+  prohd_status s = PROHD_OK;
+  for (int round = 0; round < 3 && s == PROHD_OK; ++round) {
+    const int* cand = round == 0 ? kTuneGramPts : (round == 1 ? kTuneProjRows : kTuneSelChunk);
+    const int nc = round == 0 ? 4 : 3;
+    int* knob = round == 0 ? &b->gram_pts : (round == 1 ? &b->proj_rows : &b->sel_chunk);
+    int keep = *knob;
+    for (int c = 0; c < nc && s == PROHD_OK; ++c) {
+      *knob = cand[c];
+      float ms = 0.f;
+      s = time_once(ms);
+      if (s == PROHD_OK && ms < best) {
+        best = ms;
+        keep = cand[c];
+      }
+    }
+    *knob = keep;
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (s != PROHD_OK) return s;
+  s = write_tables(b);
+  if (s != PROHD_OK) return s;
+  ctx->batch_tuned = true;
+  ctx->batch_gram_pts = b->gram_pts;
+  ctx->batch_proj_rows = b->proj_rows;
+  ctx->batch_sel_chunk = b->sel_chunk;
+  if (best_ms) *best_ms = best;
+  return PROHD_OK;
+}
+
+prohd_status prohd_batch_get_tunables(const prohd_batch* b, int32_t* gram_pts, int32_t* proj_rows, int32_t* sel_chunk) {
+  if (!b) return PROHD_EINVAL;
+  if (gram_pts) *gram_pts = b->gram_pts;
+  if (proj_rows) *proj_rows = b->proj_rows;
+  if (sel_chunk) *sel_chunk = b->sel_chunk;
+  return PROHD_OK;
+}
+
+prohd_status prohd_batch_set_tunables(prohd_batch* b, int32_t gram_pts, int32_t proj_rows, int32_t sel_chunk) {
+  if (!b) return PROHD_EINVAL;
+  if (gram_pts < kMinGramPts || proj_rows < kMinProjRows || sel_chunk < 256)
+    return bfail(b->ctx, PROHD_EINVAL, "tunables below their minimum");
+  b->gram_pts = gram_pts;
+  b->proj_rows = proj_rows;
+  b->sel_chunk = sel_chunk;
+  return write_tables(b);
+}
+
+prohd_status prohd_batch_pair_outputs(const prohd_batch* b, int pair, double** dirs, int32_t** idxA, int32_t** idxB) {
+  if (!b || pair < 0 || pair >= b->npairs) return PROHD_EINVAL;
+  const BPair& q = b->L.hp[(size_t)pair];
+  if (dirs) *dirs = q.dirs;
+  if (idxA) *idxA = q.idxA;
+  if (idxB) *idxB = q.idxB;
+  return PROHD_OK;
+}
+
+}  // extern "C"

@@ -244,8 +244,8 @@ __global__ void reduce_parts_kernel(const double* __restrict__ Gpart, const doub
 }
 
 // dirs[0] = centroid axis; C64 = G/N - dmu dmu^T (full symmetric); C32 copy.
-__global__ void centroid_axis_kernel(const double* __restrict__ sumA, const double* __restrict__ sumB, int64_t nA,
-                                     int64_t nB, int D, double* __restrict__ dirs) {
+__device__ __forceinline__ void centroid_axis_body(const double* __restrict__ sumA, const double* __restrict__ sumB,
+                                                   int64_t nA, int64_t nB, int D, double* __restrict__ dirs) {
   __shared__ double sh[33];
   double part = 0.0;
   for (int c = threadIdx.x; c < D; c += blockDim.x) {
@@ -259,9 +259,14 @@ __global__ void centroid_axis_kernel(const double* __restrict__ sumA, const doub
   }
 }
 
-__global__ void cov_finalize_kernel(const double* __restrict__ G, const double* __restrict__ sumA,
-                                    const double* __restrict__ sumB, int64_t nA, int64_t nB, int D,
-                                    double* __restrict__ C64, float* __restrict__ C32) {
+__global__ void centroid_axis_kernel(const double* __restrict__ sumA, const double* __restrict__ sumB, int64_t nA,
+                                     int64_t nB, int D, double* __restrict__ dirs) {
+  centroid_axis_body(sumA, sumB, nA, nB, D, dirs);
+}
+
+__device__ __forceinline__ void cov_finalize_body(const double* __restrict__ G, const double* __restrict__ sumA,
+                                                  const double* __restrict__ sumB, int64_t nA, int64_t nB, int D,
+                                                  double* __restrict__ C64, float* __restrict__ C32) {
   const double N = (double)(nA + nB);
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < (int64_t)D * D;
        e += (int64_t)gridDim.x * blockDim.x) {
@@ -272,6 +277,70 @@ __global__ void cov_finalize_kernel(const double* __restrict__ G, const double* 
     C64[e] = c;
     C32[e] = (float)c;
   }
+}
+
+__global__ void cov_finalize_kernel(const double* __restrict__ G, const double* __restrict__ sumA,
+                                    const double* __restrict__ sumB, int64_t nA, int64_t nB, int D,
+                                    double* __restrict__ C64, float* __restrict__ C32) {
+  cov_finalize_body(G, sumA, sumB, nA, nB, D, C64, C32);
+}
+
+// ---------------------------------------------------------------- batched pairs
+
+// Pilot shift of every pair: s = mean of the first <= 4096 rows of A. Any
+// shift gives the same C in exact arithmetic; a nearby one keeps the
+// centred values small, so FP32 column sums (combined in FP64) suffice.
+// One block per pair, thread (d, g) sums rows g, g + G, ... of column d.
+__global__ void pilot_batched_kernel(const BPair* __restrict__ P) {
+  __shared__ double sh[256];
+  const BPair& q = P[blockIdx.x];
+  const int D = q.D;
+  const int64_t rows = q.nA < 4096 ? q.nA : 4096;
+  const int G = D < 256 ? 256 / D : 1;
+  const int d = threadIdx.x % D, g = threadIdx.x / D;
+  float s0 = 0.f, s1 = 0.f, s2 = 0.f, s3 = 0.f;
+  if (g < G && threadIdx.x < G * D) {
+    int64_t r = g;
+    for (; r + 3 * G < rows; r += 4 * G) {
+      s0 += q.A[r * D + d];
+      s1 += q.A[(r + G) * D + d];
+      s2 += q.A[(r + 2 * G) * D + d];
+      s3 += q.A[(r + 3 * G) * D + d];
+    }
+    for (; r < rows; r += G) s0 += q.A[r * D + d];
+  }
+  sh[threadIdx.x] = ((double)s0 + (double)s1) + ((double)s2 + (double)s3);
+  __syncthreads();
+  if ((int)threadIdx.x < D) {
+    double t = 0.0;
+    for (int gg = 0; gg < G; ++gg) t += sh[gg * D + threadIdx.x];
+    q.s32[threadIdx.x] = (float)(t / (double)rows);
+  }
+}
+
+__global__ void centroid_axis_batched_kernel(const BPair* __restrict__ P) {
+  const BPair& q = P[blockIdx.x];
+  centroid_axis_body(q.sumA, q.sumB, q.nA, q.nB, q.D, q.dirs);
+}
+
+__global__ void cov_finalize_batched_kernel(const BPair* __restrict__ P) {
+  const BPair& q = P[blockIdx.y];
+  cov_finalize_body(q.G, q.sumA, q.sumB, q.nA, q.nB, q.D, q.C64, q.C32);
+}
+
+cudaError_t pilot_batched(const BPair* P, int npairs, cudaStream_t st) {
+  count_launch();
+  pilot_batched_kernel<<<npairs, 256, 0, st>>>(P);
+  return cudaGetLastError();
+}
+
+cudaError_t covariance_batched(const BPair* P, int npairs, int Dmax, cudaStream_t st) {
+  count_launch();
+  centroid_axis_batched_kernel<<<npairs, 256, 0, st>>>(P);
+  const unsigned gx = (unsigned)std::max<int64_t>(1, std::min<int64_t>(32, ceil_div((int64_t)Dmax * Dmax, 1024)));
+  count_launch();
+  cov_finalize_batched_kernel<<<dim3(gx, npairs), 256, 0, st>>>(P);
+  return cudaGetLastError();
 }
 
 // ---------------------------------------------------------------- power iteration

@@ -30,6 +30,8 @@ namespace prohd {
 // =====================================================================
 
 constexpr int kSimtBM = 128, kSimtBN = 128, kSimtBK = 16;
+
+__device__ __forceinline__ int64_t ceil_div_dev(int64_t x, int64_t m) { return (x + m - 1) / m; }
 // Candidate lists up to this length are rescored by rescore_few_kernel; the
 // tiled kernel takes longer lists (it would spend whole 128-row tiles on them).
 constexpr int kFewRows = 64;
@@ -37,25 +39,26 @@ constexpr int kFewRows = 64;
 // Persistent tile loop over rows of X (optionally a list of row ids) against
 // all rows of Y. WANT_ROW: rowbest[out_row] = min (d^2, j); WANT_COL:
 // colbest[j] = min (d^2, row id). Packed values are (float bits << 32 | idx).
-template <bool ROW_LIST, bool WANT_ROW, bool WANT_COL>
-__global__ void __launch_bounds__(256, 1)
-    simt_dist_kernel(const float* __restrict__ X, const int32_t* __restrict__ rowlist,
-                     const int64_t* __restrict__ nrows_dev, const float* __restrict__ Y,
-                     const int64_t* __restrict__ ncols_dev, int D, unsigned long long* __restrict__ rowbest,
-                     unsigned long long* __restrict__ colbest) {
-  __shared__ __align__(16) float As[kSimtBK][kSimtBM + 4];
-  __shared__ __align__(16) float Bs[kSimtBK][kSimtBN + 4];
-  __shared__ unsigned long long s_col[WANT_COL ? 16 : 1][WANT_COL ? kSimtBN : 1];
+template <bool WANT_COL>
+struct SimtSmem {
+  __align__(16) float As[kSimtBK][kSimtBM + 4];
+  __align__(16) float Bs[kSimtBK][kSimtBN + 4];
+  unsigned long long s_col[WANT_COL ? 16 : 1][WANT_COL ? kSimtBN : 1];
+};
 
-  const int64_t nrows = *nrows_dev, ncols = *ncols_dev;
-  if (ROW_LIST && nrows <= kFewRows) return;
-  const int64_t nct = (ncols + kSimtBN - 1) / kSimtBN;
-  const int64_t ntiles = ((nrows + kSimtBM - 1) / kSimtBM) * nct;
+// One 128 x 128 tile (row block rt, column block ct).
+template <bool ROW_LIST, bool WANT_ROW, bool WANT_COL>
+__device__ __forceinline__ void simt_tile(SimtSmem<WANT_COL>& sm, const float* __restrict__ X,
+                                          const int32_t* __restrict__ rowlist, int64_t nrows,
+                                          const float* __restrict__ Y, int64_t ncols, int D,
+                                          unsigned long long* __restrict__ rowbest,
+                                          unsigned long long* __restrict__ colbest, int64_t rt, int64_t ct) {
+  auto& As = sm.As;
+  auto& Bs = sm.Bs;
+  auto& s_col = sm.s_col;
   const int tid = threadIdx.x, ty = tid >> 4, tx = tid & 15;
   const int lr = tid >> 1, koff = (tid & 1) * 8;
-
-  for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
-    const int64_t rt = tile / nct, ct = tile % nct;
+  {
     const int64_t xr = rt * kSimtBM + lr, yr = ct * kSimtBN + lr;
     const bool vx = xr < nrows, vy = yr < ncols;
     const int64_t srcx = vx ? (ROW_LIST ? (int64_t)rowlist[xr] : xr) : 0;
@@ -152,6 +155,31 @@ __global__ void __launch_bounds__(256, 1)
       __syncthreads();
     }
   }
+}
+
+template <bool ROW_LIST, bool WANT_ROW, bool WANT_COL>
+__device__ __forceinline__ void simt_dist_body(const float* __restrict__ X, const int32_t* __restrict__ rowlist,
+                                               const int64_t* __restrict__ nrows_dev, const float* __restrict__ Y,
+                                               const int64_t* __restrict__ ncols_dev, int D,
+                                               unsigned long long* __restrict__ rowbest,
+                                               unsigned long long* __restrict__ colbest) {
+  __shared__ SimtSmem<WANT_COL> sm;
+  const int64_t nrows = *nrows_dev, ncols = *ncols_dev;
+  if (ROW_LIST && nrows <= kFewRows) return;
+  const int64_t nct = (ncols + kSimtBN - 1) / kSimtBN;
+  const int64_t ntiles = ((nrows + kSimtBM - 1) / kSimtBM) * nct;
+  for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x)
+    simt_tile<ROW_LIST, WANT_ROW, WANT_COL>(sm, X, rowlist, nrows, Y, ncols, D, rowbest, colbest, tile / nct,
+                                            tile % nct);
+}
+
+template <bool ROW_LIST, bool WANT_ROW, bool WANT_COL>
+__global__ void __launch_bounds__(256, 1)
+    simt_dist_kernel(const float* __restrict__ X, const int32_t* __restrict__ rowlist,
+                     const int64_t* __restrict__ nrows_dev, const float* __restrict__ Y,
+                     const int64_t* __restrict__ ncols_dev, int D, unsigned long long* __restrict__ rowbest,
+                     unsigned long long* __restrict__ colbest) {
+  simt_dist_body<ROW_LIST, WANT_ROW, WANT_COL>(X, rowlist, nrows_dev, Y, ncols_dev, D, rowbest, colbest);
 }
 
 // Rescoring of a short candidate list (at most kFewRows rows of X, given by
@@ -802,13 +830,12 @@ __device__ double dist64(const float* a, const float* b, int D) {
 // identity) give the row number of each entry. Every index is validated
 // before use: with non-finite input the candidate lists can be empty, and the
 // result is then NaN with the device status set.
-__global__ void hd_finalize_kernel(const float* __restrict__ A, const int64_t* nA_dev, const float* __restrict__ B,
-                                   const int64_t* nB_dev, int D, const unsigned long long* __restrict__ bestA,
-                                   const int32_t* __restrict__ idsA, const int64_t* cntA_dev,
-                                   const unsigned long long* __restrict__ bestB, const int32_t* __restrict__ idsB,
-                                   const int64_t* cntB_dev, const int32_t* __restrict__ mapA,
-                                   const int32_t* __restrict__ mapB, const HdScalars* sc, int* status,
-                                   prohd_hd_result* out) {
+__device__ __forceinline__ void hd_finalize_body(
+    const float* __restrict__ A, const int64_t* nA_dev, const float* __restrict__ B, const int64_t* nB_dev, int D,
+    const unsigned long long* __restrict__ bestA, const int32_t* __restrict__ idsA, const int64_t* cntA_dev,
+    const unsigned long long* __restrict__ bestB, const int32_t* __restrict__ idsB, const int64_t* cntB_dev,
+    const int32_t* __restrict__ mapA, const int32_t* __restrict__ mapB, const HdScalars* sc, int* status,
+    prohd_hd_result* out) {
   __shared__ unsigned long long sh[32];
   __shared__ int64_t s_nn[2];
   __shared__ double s_d[2];
@@ -875,6 +902,95 @@ __global__ void hd_finalize_kernel(const float* __restrict__ A, const int64_t* n
     }
     *out = r;
   }
+}
+
+__global__ void hd_finalize_kernel(const float* __restrict__ A, const int64_t* nA_dev, const float* __restrict__ B,
+                                   const int64_t* nB_dev, int D, const unsigned long long* __restrict__ bestA,
+                                   const int32_t* __restrict__ idsA, const int64_t* cntA_dev,
+                                   const unsigned long long* __restrict__ bestB, const int32_t* __restrict__ idsB,
+                                   const int64_t* cntB_dev, const int32_t* __restrict__ mapA,
+                                   const int32_t* __restrict__ mapB, const HdScalars* sc, int* status,
+                                   prohd_hd_result* out) {
+  hd_finalize_body(A, nA_dev, B, nB_dev, D, bestA, idsA, cntA_dev, bestB, idsB, cntB_dev, mapA, mapB, sc, status, out);
+}
+
+// ---------------------------------------------------------------- batched pairs
+
+// Exact FP32 HD of every pair's candidate subsets (direct differences, the
+// FP32 path) as one persistent launch over a work queue of 128 x 128 tiles:
+// tile t belongs to the pair whose range [prefix[i], prefix[i+1]) holds it
+// (pairs in the batch's order, largest first), and blocks take tiles from an
+// atomic ticket. Then one finalize block per pair maps the witnesses to
+// caller indices and recomputes their distances in FP64.
+__global__ void hd_tile_scan_kernel(const BPair* __restrict__ P, const int* __restrict__ order, int npairs,
+                                    int64_t* __restrict__ prefix) {
+  __shared__ int64_t wsum[32];
+  __shared__ int64_t carry;
+  if (threadIdx.x == 0) carry = 0;
+  __syncthreads();
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  for (int base = 0; base < npairs; base += blockDim.x) {
+    const int i = base + threadIdx.x;
+    int64_t v = 0;
+    if (i < npairs) {
+      const BPair& q = P[order[i]];
+      v = ceil_div_dev(q.nsel[0], kSimtBM) * ceil_div_dev(q.nsel[1], kSimtBN);
+    }
+    int64_t incl = v;
+    for (int o = 1; o < 32; o <<= 1) {
+      const int64_t t = __shfl_up_sync(0xffffffffu, incl, o);
+      if (lane >= o) incl += t;
+    }
+    if (lane == 31) wsum[w] = incl;
+    __syncthreads();
+    if (w == 0) {
+      const int64_t x = lane < nw ? wsum[lane] : 0;
+      int64_t xi = x;
+      for (int o = 1; o < 32; o <<= 1) {
+        const int64_t t = __shfl_up_sync(0xffffffffu, xi, o);
+        if (lane >= o) xi += t;
+      }
+      if (lane < nw) wsum[lane] = xi - x;
+    }
+    __syncthreads();
+    if (i < npairs) prefix[i] = carry + wsum[w] + incl - v;
+    __syncthreads();
+    if (threadIdx.x == blockDim.x - 1) carry += wsum[w] + incl;
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) prefix[npairs] = carry;
+}
+
+__global__ void __launch_bounds__(256, 1)
+    simt_dist_queue_kernel(const BPair* __restrict__ P, const int* __restrict__ order, int npairs,
+                           const int64_t* __restrict__ prefix, unsigned long long* __restrict__ ticket) {
+  __shared__ SimtSmem<true> sm;
+  __shared__ int64_t s_t;
+  const int64_t total = prefix[npairs];
+  for (;;) {
+    if (threadIdx.x == 0) s_t = (int64_t)atomicAdd(ticket, 1ull);
+    __syncthreads();
+    const int64_t t = s_t;
+    __syncthreads();
+    if (t >= total) break;
+    int lo = 0, hi = npairs;  // prefix[lo] <= t < prefix[hi]
+    while (hi - lo > 1) {
+      const int mid = (lo + hi) >> 1;
+      if (prefix[mid] <= t) lo = mid;
+      else hi = mid;
+    }
+    const BPair& q = P[order[lo]];
+    const int64_t nrows = q.nsel[0], ncols = q.nsel[1];
+    const int64_t nct = ceil_div_dev(ncols, kSimtBN), local = t - prefix[lo];
+    simt_tile<false, true, true>(sm, q.As, nullptr, nrows, q.Bs, ncols, q.D, q.bestA, q.bestB, local / nct,
+                                 local % nct);
+  }
+}
+
+__global__ void hd_finalize_batched_kernel(const BPair* __restrict__ P) {
+  const BPair& q = P[blockIdx.x];
+  hd_finalize_body(q.As, q.nsel + 0, q.Bs, q.nsel + 1, q.D, q.bestA, nullptr, q.nsel + 0, q.bestB, nullptr,
+                   q.nsel + 1, q.idxA, q.idxB, nullptr, q.status, &q.out->hd);
 }
 
 // =====================================================================
@@ -1075,6 +1191,18 @@ cudaError_t hd_core(prohd_ctx* ctx, const float* A, const int64_t* nA_dev, int64
   count_launch();
   hd_finalize_kernel<<<1, 1024, 0, st>>>(A, nA_dev, B, nB_dev, D, b.bestA, b.candA, &b.sc->ncandA, b.bestB, b.candB,
                                          &b.sc->ncandB, mapA, mapB, b.sc, status_dev, out);
+  return cudaGetLastError();
+}
+
+cudaError_t hd_simt_batched(const BPair* P, const int* order, int npairs, int64_t* prefix, unsigned long long* ticket,
+                            int num_sms, cudaStream_t st) {
+  count_launch();
+  hd_tile_scan_kernel<<<1, 1024, 0, st>>>(P, order, npairs, prefix);
+  cudaMemsetAsync(ticket, 0, sizeof(unsigned long long), st);
+  count_launch();
+  simt_dist_queue_kernel<<<num_sms * 2, 256, 0, st>>>(P, order, npairs, prefix, ticket);
+  count_launch();
+  hd_finalize_batched_kernel<<<npairs, 1024, 0, st>>>(P);
   return cudaGetLastError();
 }
 

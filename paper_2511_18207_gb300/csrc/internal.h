@@ -28,6 +28,9 @@ struct prohd_ctx {
   std::vector<Pending> pending;
   double ph_ms[PROHD_PH_COUNT] = {};
   int64_t ph_count[PROHD_PH_COUNT] = {};
+  // batched-pair tunables found by prohd_batch_autotune (defaults for new plans)
+  bool batch_tuned = false;
+  int batch_gram_pts = 16384, batch_proj_rows = 8192, batch_sel_chunk = 16384;
 };
 
 namespace prohd {
@@ -116,6 +119,85 @@ size_t gram_tc_scratch_doubles(int D, int num_sms);
 cudaError_t gram_tc_run(prohd_ctx* ctx, const float* A, int64_t nA, const float* B, int64_t nB, int D,
                         const float* s32, double* scratch, double* G, double* sumA, double* sumB, int* status,
                         int64_t timeout_ns, cudaStream_t st);
+
+// ---- batched pairs (batch.cu drives these; each stage is one launch for all pairs) ----
+
+// One unit of tensor-core Gram work: a point range of one set against one
+// output block (type 0: rows 0..127 x all Dp columns; type 1: rows 128..Dp-1
+// x columns 128..Dp-1). The tensor map lives in device memory.
+struct GcItem {
+  const CUtensorMap* tm;  // FP32 tiles of the set: box (type 0: max(128, Dp); type 1: 128) dims x 64 points
+  const float* s32;       // pilot shift of the pair [D]
+  float2* gacc;           // [N][128] compensated partial sums (sum, compensation)
+  double* sums;           // [8][2][Dp] per-converter-warp set sums
+  int* status;            // the pair's status
+  int64_t p0, p1;         // point range [p0, p1) of the set
+  int D, Dp, type, setA;
+};
+
+// Device-side descriptor of one pair of a batch: its inputs, parameters and
+// the slices of the batch workspace that each stage reads and writes.
+struct BPair {
+  const float* A;
+  const float* B;
+  int64_t nA, nB;
+  int D, Dp, m, nd;
+  // directions
+  float* s32;
+  double *G, *sumA, *sumB, *C64;
+  float* C32;
+  double* U;      // [m][D] Ritz vectors before the FP64 clean-up
+  double* rpart;  // [m][D] Rayleigh-quotient partials
+  double* dirs;   // [nd][D]
+  double* eig;    // [max(m,1)]
+  int iters;      // block-iteration cap
+  // selection
+  float *qA, *qB;  // [nd][n] FP32 projections
+  float* maxnorm;  // [2]
+  uint8_t *maskA, *maskB;
+  int32_t *idxA, *idxB;
+  int64_t* nsel;       // [2]
+  unsigned* counts;    // [2][nblk] compaction block counts
+  int64_t* offsets;    // [2][nblk]
+  int nblkA, nblkB;
+  // subset distance
+  float *As, *Bs;
+  unsigned long long *bestA, *bestB;
+  int* status;
+  prohd_result* out;
+  // Gram items of this pair, as positions in the batch's item-id list
+  int gi0, gn0, gi1, gn1;
+  int prob0;  // first selection problem of this pair (set-major: set * nd + d)
+};
+
+// One unit of projection work: rows [r0, r1) of one set of one pair.
+struct ProjItem {
+  int pair, set;
+  int64_t r0, r1;
+};
+
+size_t gram_tc_smem_batched();
+cudaError_t gram_tc_batched(const GcItem* items, int nitems, int* ticket, int* batch_status, int grid,
+                            int64_t timeout_ns, cudaStream_t st);
+cudaError_t gram_reduce_batched(const BPair* P, int npairs, const GcItem* items, const int* ids, int Dmax,
+                                cudaStream_t st);
+cudaError_t pilot_batched(const BPair* P, int npairs, cudaStream_t st);
+cudaError_t covariance_batched(const BPair* P, int npairs, int Dmax, cudaStream_t st);
+// Block iteration with one CTA per pair, one launch per D class (D <= 64, 128, 256).
+cudaError_t subspace_batched(const BPair* P, const int* const cls_pairs[3], const int ncls[3], int npairs, int Dmax,
+                             int mmax, double tol, uint64_t seed, cudaStream_t st);
+cudaError_t proj_batched(const BPair* P, const ProjItem* items, int nitems, int ndmax, int* batch_status,
+                         cudaStream_t st);
+struct SelProb;
+size_t sel_prob_bytes();
+cudaError_t select_batched(SelProb* probs, int nprob, const double* alpha_of, unsigned* hist, int64_t nmax, int chunk,
+                           cudaStream_t st);
+// Fills the data fields of one selection problem (host side, at planning).
+void sel_prob_fill(void* dst, const float* q, int64_t n, const float* X, const double* u, uint8_t* mask,
+                   const float* maxnorm, int D, int32_t* band0, int32_t* band1, uint64_t* key0, uint64_t* key1);
+cudaError_t compact_gather_batched(const BPair* P, int npairs, int nblk_max, int64_t nmax, cudaStream_t st);
+cudaError_t hd_simt_batched(const BPair* P, const int* order, int npairs, int64_t* prefix, unsigned long long* ticket,
+                            int num_sms, cudaStream_t st);
 
 // ---- small utilities (api.cu) ----
 cudaError_t set_i64(int64_t* p, int64_t v, cudaStream_t st);

@@ -15,6 +15,8 @@
 //     the band in between is ranked by FP64 projections recomputed exactly as
 //     the sequential definition (__dmul_rn / __dadd_rn), ties by index.
 //  The largest side is the same on reversed keys.
+#include <string.h>
+
 #include <algorithm>
 
 #include "common.cuh"
@@ -31,10 +33,12 @@ constexpr int kProjStride = 36;  // padded row stride (floats): conflict-free 16
 
 // q[d*n + i] = fl32(x_i . u_d); rownorm max into *maxnorm; non-finite check.
 // Requires D % 4 == 0 and a 16-byte aligned base (cp.async 16 B).
+// Tiles t0, t0 + tstride, ... below t1 of the set.
 template <int ND>
-__global__ void __launch_bounds__(kProjThreads)
-    proj_kernel(const float* __restrict__ X, int64_t n, int D, const double* __restrict__ dirs, int nd,
-                float* __restrict__ q, float* __restrict__ maxnorm, int* __restrict__ status) {
+__device__ __forceinline__ void proj_body(const float* __restrict__ X, int64_t n, int D,
+                                          const double* __restrict__ dirs, int nd, float* __restrict__ q,
+                                          float* __restrict__ maxnorm, int* __restrict__ status, int64_t t0,
+                                          int64_t t1, int64_t tstride) {
   extern __shared__ __align__(16) float psm[];
   const int Dq = (D + kProjK - 1) / kProjK * kProjK;
   float* us = psm;                               // [ND][Dq]
@@ -44,7 +48,6 @@ __global__ void __launch_bounds__(kProjThreads)
     us[i] = (d < nd && k < D) ? (float)dirs[(size_t)d * D + k] : 0.f;
   }
   const int t = threadIdx.x;
-  const int64_t ntiles = (n + kProjRows - 1) / kProjRows;
   const int nchunks = Dq / kProjK;
   float wmax = 0.f;
   bool bad = false;
@@ -72,7 +75,7 @@ __global__ void __launch_bounds__(kProjThreads)
   };
 
   __syncthreads();
-  for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+  for (int64_t tile = t0; tile < t1; tile += tstride) {
     float acc0[ND], acc1[ND];
 #pragma unroll
     for (int d = 0; d < ND; ++d) acc0[d] = acc1[d] = 0.f;
@@ -126,6 +129,24 @@ __global__ void __launch_bounds__(kProjThreads)
   if (__any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0) atomicMax(status, (int)PROHD_ENONFINITE);
 }
 
+template <int ND>
+__global__ void __launch_bounds__(kProjThreads)
+    proj_kernel(const float* __restrict__ X, int64_t n, int D, const double* __restrict__ dirs, int nd,
+                float* __restrict__ q, float* __restrict__ maxnorm, int* __restrict__ status) {
+  proj_body<ND>(X, n, D, dirs, nd, q, maxnorm, status, blockIdx.x, (n + kProjRows - 1) / kProjRows, gridDim.x);
+}
+
+// Batched: one item (a row range of one set of one pair) per block.
+template <int ND>
+__global__ void __launch_bounds__(kProjThreads)
+    proj_items_kernel(const BPair* __restrict__ P, const ProjItem* __restrict__ items) {
+  const ProjItem it = items[blockIdx.x];
+  const BPair& q = P[it.pair];
+  const int64_t n = it.set ? q.nB : q.nA;
+  proj_body<ND>(it.set ? q.B : q.A, n, q.D, q.dirs, q.nd, it.set ? q.qB : q.qA, q.maxnorm + it.set, q.status,
+                it.r0 / kProjRows, (it.r1 + kProjRows - 1) / kProjRows, 1);
+}
+
 // Fallback for D % 4 != 0 or unaligned bases: warp per row, lanes over dims.
 __global__ void proj_simple_kernel(const float* __restrict__ X, int64_t n, int D, const double* __restrict__ dirs,
                                    int nd, float* __restrict__ q, float* __restrict__ maxnorm, int* __restrict__ status) {
@@ -163,6 +184,17 @@ struct SelProb {
   double E;             // |q - p64| bound for this (set, direction)
   int64_t cin[2];       // points certainly selected on each side
   int64_t nband[2];     // band sizes
+  // the problem's data: FP32 keys q[0..n), points X [n][D], direction u,
+  // selection mask, band lists and their FP64 keys (one per side)
+  const float* q;
+  int64_t n;
+  const float* X;
+  const double* u;
+  uint8_t* mask;
+  const float* maxnorm;  // max ||x|| of the set
+  int D;
+  int32_t* band[2];
+  uint64_t* bkey[2];
 };
 
 constexpr int kMaxDirs = 64;
@@ -170,36 +202,65 @@ struct KList {
   int64_t k[2 * kMaxDirs];  // k of (set, direction) p = set * nd + d, passed by value
 };
 
-__global__ void sel_init_kernel(SelProb* __restrict__ P, int nd, const KList kl, int64_t nA, int64_t nB, int D,
-                                const double* __restrict__ dirs, const float* __restrict__ maxnorm) {
-  const int p = blockIdx.x * blockDim.x + threadIdx.x;
-  if (p >= 2 * nd) return;
-  const int set = p / nd, d = p % nd;
-  const int64_t n = set ? nB : nA;
-  int64_t k = kl.k[p];
+// Starting state of a problem whose data fields are set: ranks of the k-th
+// smallest and largest keys, and the bound E.
+__device__ __forceinline__ void sel_reset(SelProb& s, int64_t k) {
+  const int64_t n = s.n;
   k = k < 1 ? 1 : (k > n ? n : k);
   double un = 0.0;
-  for (int j = 0; j < D; ++j) un += dirs[(size_t)d * D + j] * dirs[(size_t)d * D + j];
+  for (int j = 0; j < s.D; ++j) un += s.u[j] * s.u[j];
   un = sqrt(un);
-  SelProb s;
   s.prefix[0] = s.prefix[1] = 0;
   s.rank[0] = k - 1;
   s.rank[1] = n - k;
   s.k = k;
-  s.E = ((double)D + 8.0) * 5.9604644775390625e-8 * 1.0201 * (double)maxnorm[set] * un + 1e-300;
+  s.E = ((double)s.D + 8.0) * 5.9604644775390625e-8 * 1.0201 * (double)(*s.maxnorm) * un + 1e-300;
   s.cin[0] = s.cin[1] = 0;
   s.nband[0] = s.nband[1] = 0;
+}
+
+__global__ void sel_init_kernel(SelProb* __restrict__ P, int nd, const KList kl, const float* __restrict__ A,
+                                const float* __restrict__ qA, int64_t nA, uint8_t* __restrict__ maskA,
+                                const float* __restrict__ B, const float* __restrict__ qB, int64_t nB,
+                                uint8_t* __restrict__ maskB, int D, const double* __restrict__ dirs,
+                                const float* __restrict__ maxnorm, int32_t* __restrict__ band,
+                                uint64_t* __restrict__ bandkey, int64_t cap) {
+  const int p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= 2 * nd) return;
+  const int set = p / nd, d = p % nd;
+  SelProb s;
+  s.n = set ? nB : nA;
+  s.q = (set ? qB : qA) + (size_t)d * s.n;
+  s.X = set ? B : A;
+  s.u = dirs + (size_t)d * D;
+  s.mask = set ? maskB : maskA;
+  s.maxnorm = maxnorm + set;
+  s.D = D;
+  for (int side = 0; side < 2; ++side) {
+    s.band[side] = band + ((size_t)p * 2 + side) * cap;
+    s.bkey[side] = bandkey + ((size_t)p * 2 + side) * cap;
+  }
+  sel_reset(s, kl.k[p]);
   P[p] = s;
 }
 
+// Batched: the data fields were written when the batch was planned; k comes
+// from the problem's alpha (alpha_c on the centroid axis, alpha_p on the
+// components) and the set size.
+__global__ void sel_reset_batched_kernel(SelProb* __restrict__ P, int nprob, const double* __restrict__ alpha_of) {
+  const int p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= nprob) return;
+  SelProb& s = P[p];
+  const double kk = floor(alpha_of[p] * (double)s.n);
+  sel_reset(s, kk < 1.0 ? 1 : (int64_t)kk);
+}
+
 // grid (chunks, 2*nd). hist: [2*nd][2][256]
-__global__ void radix_hist_kernel(const float* __restrict__ qA, int64_t nA, const float* __restrict__ qB, int64_t nB,
-                                  int nd, const SelProb* __restrict__ P, int pass, unsigned* __restrict__ hist) {
+__global__ void radix_hist_kernel(const SelProb* __restrict__ P, int pass, unsigned* __restrict__ hist) {
   __shared__ unsigned h[2][256];
   const int p = blockIdx.y;
-  const int set = p / nd, d = p % nd;
-  const int64_t n = set ? nB : nA;
-  const float* q = (set ? qB : qA) + (size_t)d * n;
+  const int64_t n = P[p].n;
+  const float* q = P[p].q;
   for (int i = threadIdx.x; i < 512; i += blockDim.x) (&h[0][0])[i] = 0;
   __syncthreads();
   const int shift = 24 - 8 * pass;
@@ -283,21 +344,18 @@ __device__ __forceinline__ float f32_down(double x) {
 
 // Marks certain members, counts them, and lists band members per side.
 // band lists: [2*nd][2][cap] int32
-__global__ void band_kernel(const float* __restrict__ qA, int64_t nA, const float* __restrict__ qB, int64_t nB,
-                            int nd, SelProb* __restrict__ P, uint8_t* __restrict__ maskA, uint8_t* __restrict__ maskB,
-                            int32_t* __restrict__ band, int64_t cap) {
+__global__ void band_kernel(SelProb* __restrict__ P) {
   const int p = blockIdx.y;
-  const int set = p / nd, d = p % nd;
-  const int64_t n = set ? nB : nA;
-  const float* q = (set ? qB : qA) + (size_t)d * n;
-  uint8_t* mask = set ? maskB : maskA;
+  const int64_t n = P[p].n;
+  const float* q = P[p].q;
+  uint8_t* mask = P[p].mask;
   const double E2 = 2.0 * P[p].E;
   const double Tlo = (double)key_f32(P[p].prefix[0]), Thi = (double)key_f32(P[p].prefix[1]);
   // q < lo_in, q <= lo_band, q > hi_in, q >= hi_band in double, as float comparisons
   const float f_lo_in = f32_up(Tlo - E2), f_lo_band = f32_down(Tlo + E2);
   const float f_hi_in = f32_down(Thi + E2), f_hi_band = f32_up(Thi - E2);
-  int32_t* b0 = band + ((size_t)p * 2 + 0) * cap;
-  int32_t* b1 = band + ((size_t)p * 2 + 1) * cap;
+  int32_t* b0 = P[p].band[0];
+  int32_t* b1 = P[p].band[1];
   const int lane = threadIdx.x & 31;
   unsigned long long c0 = 0, c1 = 0;
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
@@ -336,24 +394,22 @@ __global__ void band_kernel(const float* __restrict__ qA, int64_t nA, const floa
 // FP64 keys of every band member, spread over many blocks (FP64 arithmetic is
 // scarce on this GPU: one block per band would serialise a large band's
 // sequential sums on one SM). grid (chunks, 4 * nd): y = problem * 2 + side.
-__global__ void band_keys_kernel(const float* __restrict__ A, const float* __restrict__ B, int D,
-                                 const double* __restrict__ dirs, int nd, const SelProb* __restrict__ P,
-                                 const int32_t* __restrict__ band, uint64_t* __restrict__ bandkey, int64_t cap) {
+__global__ void band_keys_kernel(const SelProb* __restrict__ P) {
   const int p = blockIdx.y >> 1, side = blockIdx.y & 1;
-  const int set = p / nd, d = p % nd;
-  const float* X = set ? B : A;
+  const float* X = P[p].X;
+  const int D = P[p].D;
   const int64_t b = P[p].nband[side];
   const int64_t r = P[p].k - P[p].cin[side];
   if (b == 0 || r <= 0) return;
   __shared__ double us[1024];
-  const double* u = dirs + (size_t)d * D;
+  const double* u = P[p].u;
   const bool u_sm = D <= 1024;
   if (u_sm)
     for (int k = threadIdx.x; k < D; k += blockDim.x) us[k] = u[k];
   __syncthreads();
   const double* uu = u_sm ? us : u;
-  const int32_t* lst = band + ((size_t)p * 2 + side) * cap;
-  uint64_t* keys = bandkey + ((size_t)p * 2 + side) * cap;
+  const int32_t* lst = P[p].band[side];
+  uint64_t* keys = P[p].bkey[side];
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < b; i += (int64_t)gridDim.x * blockDim.x) {
     double s = 0.0;
     const float* x = X + (int64_t)lst[i] * D;
@@ -377,25 +433,19 @@ constexpr int kBandSmem = 2048;
 // mark the r = k - cin smallest. Small bands are ranked in shared memory by
 // counting; large bands use a radix select over the 96-bit (key, index).
 __global__ void __launch_bounds__(512)
-    band_resolve_kernel(const float* __restrict__ A, int64_t nA, const float* __restrict__ B, int64_t nB, int D,
-                        const double* __restrict__ dirs, int nd, const SelProb* __restrict__ P,
-                        const int32_t* __restrict__ band, uint64_t* __restrict__ bandkey, int64_t cap,
-                        uint8_t* __restrict__ maskA, uint8_t* __restrict__ maskB) {
+    band_resolve_kernel(const SelProb* __restrict__ P) {
   __shared__ uint64_t sk[kBandSmem];
   __shared__ int32_t si[kBandSmem];
   __shared__ unsigned hist[256];
   __shared__ int64_t s_rank;
   __shared__ uint64_t s_prefix;
   const int p = blockIdx.x >> 1, side = blockIdx.x & 1;
-  const int set = p / nd, d = p % nd;
-  const float* X = set ? B : A;
-  uint8_t* mask = set ? maskB : maskA;
-  const double* u = dirs + (size_t)d * D;
+  uint8_t* mask = P[p].mask;
   const int64_t b = P[p].nband[side];
   const int64_t r = P[p].k - P[p].cin[side];
   if (b == 0 || r <= 0) return;
-  const int32_t* lst = band + ((size_t)p * 2 + side) * cap;
-  uint64_t* keys = bandkey + ((size_t)p * 2 + side) * cap;
+  const int32_t* lst = P[p].band[side];
+  const uint64_t* keys = P[p].bkey[side];
   if (b <= kBandSmem) {
     for (int64_t i = threadIdx.x; i < b; i += blockDim.x) {
       si[i] = lst[i];
@@ -483,7 +533,8 @@ __global__ void __launch_bounds__(512)
 
 constexpr int kCompactItems = 4096;  // mask bytes per block
 
-__global__ void compact_count_kernel(const uint8_t* __restrict__ mask, int64_t n, unsigned* __restrict__ counts) {
+__device__ __forceinline__ void compact_count_body(const uint8_t* __restrict__ mask, int64_t n,
+                                                   unsigned* __restrict__ counts) {
   const int64_t base = (int64_t)blockIdx.x * kCompactItems;
   unsigned c = 0;
   for (int i = threadIdx.x; i < kCompactItems; i += blockDim.x) {
@@ -501,9 +552,13 @@ __global__ void compact_count_kernel(const uint8_t* __restrict__ mask, int64_t n
   }
 }
 
+__global__ void compact_count_kernel(const uint8_t* __restrict__ mask, int64_t n, unsigned* __restrict__ counts) {
+  compact_count_body(mask, n, counts);
+}
+
 // single block: exclusive scan of counts -> offsets; total -> *nsel
-__global__ void compact_scan_kernel(const unsigned* __restrict__ counts, int64_t nblocks, int64_t* __restrict__ offsets,
-                                    int64_t* __restrict__ nsel) {
+__device__ __forceinline__ void compact_scan_body(const unsigned* __restrict__ counts, int64_t nblocks,
+                                                  int64_t* __restrict__ offsets, int64_t* __restrict__ nsel) {
   __shared__ int64_t carry;
   __shared__ int64_t wsum[32];
   if (threadIdx.x == 0) carry = 0;
@@ -537,8 +592,13 @@ __global__ void compact_scan_kernel(const unsigned* __restrict__ counts, int64_t
   if (threadIdx.x == 0) *nsel = carry;
 }
 
-__global__ void compact_write_kernel(const uint8_t* __restrict__ mask, int64_t n, const int64_t* __restrict__ offsets,
-                                     int32_t* __restrict__ idx) {
+__global__ void compact_scan_kernel(const unsigned* __restrict__ counts, int64_t nblocks, int64_t* __restrict__ offsets,
+                                    int64_t* __restrict__ nsel) {
+  compact_scan_body(counts, nblocks, offsets, nsel);
+}
+
+__device__ __forceinline__ void compact_write_body(const uint8_t* __restrict__ mask, int64_t n,
+                                                   const int64_t* __restrict__ offsets, int32_t* __restrict__ idx) {
   // blockDim = 1024; each thread handles 4 consecutive bytes
   __shared__ unsigned wsum[32];
   const int64_t base = (int64_t)blockIdx.x * kCompactItems + threadIdx.x * 4;
@@ -572,8 +632,13 @@ __global__ void compact_write_kernel(const uint8_t* __restrict__ mask, int64_t n
     if (f[j]) idx[pos++] = (int32_t)(base + j);
 }
 
-__global__ void gather_rows_kernel(const float* __restrict__ X, int D, const int32_t* __restrict__ idx,
-                                   const int64_t* __restrict__ n_dev, float* __restrict__ out) {
+__global__ void compact_write_kernel(const uint8_t* __restrict__ mask, int64_t n, const int64_t* __restrict__ offsets,
+                                     int32_t* __restrict__ idx) {
+  compact_write_body(mask, n, offsets, idx);
+}
+
+__device__ __forceinline__ void gather_rows_body(const float* __restrict__ X, int D, const int32_t* __restrict__ idx,
+                                                 const int64_t* __restrict__ n_dev, float* __restrict__ out) {
   const int64_t n = *n_dev;
   const int lane = threadIdx.x & 31;
   const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
@@ -583,6 +648,54 @@ __global__ void gather_rows_kernel(const float* __restrict__ X, int D, const int
     float* dst = out + r * D;
     for (int k = lane; k < D; k += 32) dst[k] = src[k];
   }
+}
+
+__global__ void gather_rows_kernel(const float* __restrict__ X, int D, const int32_t* __restrict__ idx,
+                                   const int64_t* __restrict__ n_dev, float* __restrict__ out) {
+  gather_rows_body(X, D, idx, n_dev, out);
+}
+
+// Batched compaction and gather: segment blockIdx.y = 2 * pair + set.
+struct SegView {
+  const uint8_t* mask;
+  int64_t n;
+  unsigned* counts;
+  int64_t* offsets;
+  int nblk;
+  int32_t* idx;
+  int64_t* nsel;
+  const float* X;
+  float* sub;
+};
+__device__ __forceinline__ SegView seg_view(const BPair& q, int set) {
+  SegView v;
+  v.mask = set ? q.maskB : q.maskA;
+  v.n = set ? q.nB : q.nA;
+  v.counts = q.counts + (set ? q.nblkA : 0);
+  v.offsets = q.offsets + (set ? q.nblkA : 0);
+  v.nblk = set ? q.nblkB : q.nblkA;
+  v.idx = set ? q.idxB : q.idxA;
+  v.nsel = q.nsel + set;
+  v.X = set ? q.B : q.A;
+  v.sub = set ? q.Bs : q.As;
+  return v;
+}
+__global__ void compact_count_batched_kernel(const BPair* __restrict__ P) {
+  const SegView v = seg_view(P[blockIdx.y >> 1], blockIdx.y & 1);
+  if ((int)blockIdx.x < v.nblk) compact_count_body(v.mask, v.n, v.counts);
+}
+__global__ void compact_scan_batched_kernel(const BPair* __restrict__ P) {
+  const SegView v = seg_view(P[blockIdx.x >> 1], blockIdx.x & 1);
+  compact_scan_body(v.counts, v.nblk, v.offsets, v.nsel);
+}
+__global__ void compact_write_batched_kernel(const BPair* __restrict__ P) {
+  const SegView v = seg_view(P[blockIdx.y >> 1], blockIdx.y & 1);
+  if ((int)blockIdx.x < v.nblk) compact_write_body(v.mask, v.n, v.offsets, v.idx);
+}
+__global__ void gather_batched_kernel(const BPair* __restrict__ P) {
+  const BPair& q = P[blockIdx.y >> 1];
+  const SegView v = seg_view(q, blockIdx.y & 1);
+  gather_rows_body(v.X, q.D, v.idx, v.nsel, v.sub);
 }
 
 // ---------------------------------------------------------------- host side
@@ -689,23 +802,23 @@ cudaError_t select_run(prohd_ctx* ctx, const float* A, int64_t nA, const float* 
   }
   PhaseTimer pt_sel(ctx, PROHD_PH_SELECT, st);
   count_launch();
-  sel_init_kernel<<<1, 128, 0, st>>>(b.P, nd, kl, nA, nB, D, dirs, b.maxnorm);
+  sel_init_kernel<<<1, 128, 0, st>>>(b.P, nd, kl, A, b.qA, nA, b.maskA, B, b.qB, nB, b.maskB, D, dirs, b.maxnorm,
+                                     b.band, b.bandkey, b.cap);
   const int64_t nmax = std::max(nA, nB);
   const unsigned chunks = (unsigned)std::max<int64_t>(1, std::min<int64_t>(ceil_div(nmax, 256 * 16), (nsm * 8 + 2 * nd - 1) / (2 * nd)));
   dim3 g(chunks, 2 * nd);
   for (int pass = 0; pass < 4; ++pass) {
     count_launch();
-    radix_hist_kernel<<<g, 256, 0, st>>>(b.qA, nA, b.qB, nB, nd, b.P, pass, b.hist);
+    radix_hist_kernel<<<g, 256, 0, st>>>(b.P, pass, b.hist);
     count_launch();
     radix_pick_kernel<<<(4 * nd * 32 + 127) / 128, 128, 0, st>>>(b.P, 2 * nd, pass, b.hist);
   }
   count_launch();
-  band_kernel<<<g, 256, 0, st>>>(b.qA, nA, b.qB, nB, nd, b.P, b.maskA, b.maskB, b.band, b.cap);
+  band_kernel<<<g, 256, 0, st>>>(b.P);
   count_launch();
-  band_keys_kernel<<<dim3(16, 4 * nd), 256, 0, st>>>(A, B, D, dirs, nd, b.P, b.band, b.bandkey, b.cap);
+  band_keys_kernel<<<dim3(16, 4 * nd), 256, 0, st>>>(b.P);
   count_launch();
-  band_resolve_kernel<<<4 * nd, 512, 0, st>>>(A, nA, B, nB, D, dirs, nd, b.P, b.band, b.bandkey, b.cap, b.maskA,
-                                              b.maskB);
+  band_resolve_kernel<<<4 * nd, 512, 0, st>>>(b.P);
   if ((e = cudaGetLastError())) return e;
   if ((e = mark_to_indices(b.maskA, nA, idxA, nselA, b.counts, b.offsets, st))) return e;
   if ((e = mark_to_indices(b.maskB, nB, idxB, nselB, b.counts, b.offsets, st))) return e;
@@ -717,6 +830,89 @@ cudaError_t gather_rows(const float* X, int D, const int32_t* idx, const int64_t
   (void)n_max;
   count_launch();
   gather_rows_kernel<<<num_sms * 8, 256, 0, st>>>(X, D, idx, n_dev, out);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------- batched pairs
+
+size_t sel_prob_bytes() { return sizeof(SelProb); }
+
+void sel_prob_fill(void* dst, const float* q, int64_t n, const float* X, const double* u, uint8_t* mask,
+                   const float* maxnorm, int D, int32_t* band0, int32_t* band1, uint64_t* key0, uint64_t* key1) {
+  SelProb s;
+  memset(&s, 0, sizeof s);
+  s.q = q;
+  s.n = n;
+  s.X = X;
+  s.u = u;
+  s.mask = mask;
+  s.maxnorm = maxnorm;
+  s.D = D;
+  s.band[0] = band0;
+  s.band[1] = band1;
+  s.bkey[0] = key0;
+  s.bkey[1] = key1;
+  memcpy(dst, &s, sizeof s);
+}
+
+cudaError_t proj_batched(const BPair* P, const ProjItem* items, int nitems, int ndmax, int* batch_status,
+                         cudaStream_t st) {
+  (void)batch_status;
+  if (nitems == 0) return cudaSuccess;
+  const int Dq = 256;  // smem sized for the largest D of a batch (D <= 256)
+  auto go = [&](auto kern, int ND) -> cudaError_t {
+    const size_t smem = (size_t)ND * Dq * 4 + (size_t)2 * kProjRows * kProjStride * 4;
+    cudaError_t r = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (r) return r;
+    count_launch();
+    kern<<<nitems, kProjThreads, smem, st>>>(P, items);
+    return cudaGetLastError();
+  };
+  if (ndmax <= 3) return go(proj_items_kernel<3>, 3);
+  if (ndmax <= 5) return go(proj_items_kernel<5>, 5);
+  if (ndmax <= 9) return go(proj_items_kernel<9>, 9);
+  if (ndmax <= 13) return go(proj_items_kernel<13>, 13);
+  if (ndmax <= 17) return go(proj_items_kernel<17>, 17);
+  if (ndmax <= 24) return go(proj_items_kernel<24>, 24);
+  return go(proj_items_kernel<32>, 32);
+}
+
+// Radix select and band resolution of every (pair, set, direction) problem
+// of the batch at once. `chunk` keys per block of the histogram and band
+// passes (the grid's x extent covers the largest set).
+cudaError_t select_batched(SelProb* probs, int nprob, const double* alpha_of, unsigned* hist, int64_t nmax, int chunk,
+                           cudaStream_t st) {
+  if (nprob > 32767) return cudaErrorInvalidValue;
+  cudaMemsetAsync(hist, 0, sizeof(unsigned) * (size_t)nprob * 512, st);
+  count_launch();
+  sel_reset_batched_kernel<<<(nprob + 127) / 128, 128, 0, st>>>(probs, nprob, alpha_of);
+  const unsigned chunks = (unsigned)std::max<int64_t>(1, ceil_div(nmax, std::max(chunk, 256)));
+  dim3 g(chunks, nprob);
+  for (int pass = 0; pass < 4; ++pass) {
+    count_launch();
+    radix_hist_kernel<<<g, 256, 0, st>>>(probs, pass, hist);
+    count_launch();
+    radix_pick_kernel<<<(2 * nprob * 32 + 127) / 128, 128, 0, st>>>(probs, nprob, pass, hist);
+  }
+  count_launch();
+  band_kernel<<<g, 256, 0, st>>>(probs);
+  count_launch();
+  band_keys_kernel<<<dim3(1, 2 * nprob), 256, 0, st>>>(probs);
+  count_launch();
+  band_resolve_kernel<<<2 * nprob, 512, 0, st>>>(probs);
+  return cudaGetLastError();
+}
+
+cudaError_t compact_gather_batched(const BPair* P, int npairs, int nblk_max, int64_t nmax, cudaStream_t st) {
+  (void)nmax;
+  count_launch();
+  compact_count_batched_kernel<<<dim3(nblk_max, 2 * npairs), 256, 0, st>>>(P);
+  count_launch();
+  compact_scan_batched_kernel<<<2 * npairs, 1024, 0, st>>>(P);
+  count_launch();
+  compact_write_batched_kernel<<<dim3(nblk_max, 2 * npairs), 1024, 0, st>>>(P);
+  count_launch();
+  gather_batched_kernel<<<dim3(16, 2 * npairs), 256, 0, st>>>(P);
   return cudaGetLastError();
 }
 

@@ -51,14 +51,18 @@ constexpr int kSiLd = kSiMaxB + 1;                 // row stride of the small ma
 constexpr int kSiX = kSiMaxB * kSiMaxB + kSiMaxB;  // one exchange slot: b x b matrix + b values
 constexpr int kSiVld = kSiMaxD + 4;                // row stride of V^T (floats): 128-bit aligned, staggered banks
 
-struct SiSmem {
-  float Vt[kSiMaxB * kSiVld];        // basis, transposed: column j of V at Vt[j * kSiVld], zero padded
-  float Cl[kSiMaxRows * kSiMaxD];    // this CTA's rows of C, row stride Dq (D rounded up to 4), zero padded
-  float W[kSiMaxRows * kSiMaxB];     // C V, local rows
-  float Vr[kSiMaxRows * kSiMaxB];    // Ritz vectors V Y, local rows
-  float Wr[kSiMaxRows * kSiMaxB];    // W Y -> scaled block -> Q1 -> Q
+// NC CTAs (a cluster when NC > 1) share the iteration; each holds ROWS rows
+// of every D x b block (and, in a cluster, its rows of C), V^T with row
+// stride VLD floats.
+template <int NC, int ROWS, int VLD>
+struct SiSmemT {
+  float Vt[kSiMaxB * VLD];                 // basis, transposed: column j of V at Vt[j * VLD], zero padded
+  float Cl[NC > 1 ? ROWS * kSiMaxD : 4];   // this CTA's rows of C (cluster only), row stride Dq, zero padded
+  float W[ROWS * kSiMaxB];           // C V, local rows
+  float Vr[ROWS * kSiMaxB];          // Ritz vectors V Y, local rows
+  float Wr[ROWS * kSiMaxB];          // W Y -> scaled block -> Q1 -> Q
   float part[kSiX];                  // this CTA's partial before an exchange
-  float X[2][kSiCTAs][kSiX];         // exchange slots, double-buffered
+  float X[2][NC][kSiX];              // exchange slots, double-buffered
   float M[kSiMaxB * kSiLd];          // summed small matrix
   float Y[kSiMaxB * kSiLd];          // Jacobi eigenvectors (columns)
   float L[kSiMaxB * kSiLd];          // inverse Cholesky factor L^{-1} (lower)
@@ -72,6 +76,7 @@ struct SiSmem {
   int perm[kSiMaxB];                 // perm[rank] = column of Y
   uint32_t key[kSiMaxB];             // order keys of the Ritz values
 };
+using SiSmem = SiSmemT<kSiCTAs, kSiMaxRows, kSiVld>;
 
 // 1/sqrt(x) for x > 0: the hardware estimate refined by one Newton step
 // (relative error well below FP32 rounding, without the division and square
@@ -89,20 +94,34 @@ PROHD_DEV void two_sum_acc(float& s, float& c, float x) {
   s = t;
 }
 
+// Barrier over the CTAs that share the iteration.
+template <int NC>
+PROHD_DEV void si_sync() {
+  if constexpr (NC > 1)
+    cluster_sync();
+  else
+    __syncthreads();
+}
+
 // Sends this CTA's part[0..n) into slot X[buf][rank] of every CTA of the cluster.
-PROHD_DEV void si_broadcast(SiSmem& S, int buf, uint32_t rank, int n) {
+template <int NC, class SM>
+PROHD_DEV void si_broadcast(SM& S, int buf, uint32_t rank, int n) {
   float* dst = &S.X[buf][rank][0];
-  for (int e = threadIdx.x; e < n * kSiCTAs; e += blockDim.x) {
+  for (int e = threadIdx.x; e < n * NC; e += blockDim.x) {
     const int c = e / n, i = e - c * n;
-    st_cluster_f32(map_to_cta(dst + i, (uint32_t)c), S.part[i]);
+    if constexpr (NC > 1)
+      st_cluster_f32(map_to_cta(dst + i, (uint32_t)c), S.part[i]);
+    else
+      dst[i] = S.part[i];
   }
 }
 
 // out[i] = sum over CTAs (fixed order) of X[buf][*][off + i], i < n.
-PROHD_DEV float si_sum(const SiSmem& S, int buf, int idx) {
+template <int NC, class SM>
+PROHD_DEV float si_sum(const SM& S, int buf, int idx) {
   float s = 0.f;
 #pragma unroll
-  for (int r = 0; r < kSiCTAs; ++r) s += S.X[buf][r][idx];
+  for (int r = 0; r < NC; ++r) s += S.X[buf][r][idx];
   return s;
 }
 
@@ -170,7 +189,8 @@ PROHD_DEV void si_jac_max2(float& a, float& b, float* red /*[2][kSiJacThreads/32
   named_bar_sync(1, kSiJacThreads);
 }
 
-PROHD_DEV void si_jacobi(SiSmem& S, int b) {
+template <class SM>
+PROHD_DEV void si_jacobi(SM& S, int b) {
   // run by the first kSiJacThreads threads, synchronised by named barrier 1
   const int tid = threadIdx.x;
   float* A = S.M;
@@ -276,7 +296,8 @@ PROHD_DEV void si_jacobi(SiSmem& S, int b) {
 // over shared memory keep the code small. A pivot that rounding drove to or
 // below zero is replaced by a tiny positive one: the column is then noise,
 // which a second pass normalises.
-PROHD_DEV void si_chol_inv(SiSmem& S, int b, int lane) {
+template <class SM>
+PROHD_DEV void si_chol_inv(SM& S, int b, int lane) {
   const float floor_piv = 1e-30f + 1e-12f * fabsf(S.M[0]);
   float* Lf = S.Lf;
   float* dinv = S.dinv;  // 1 / L[j][j]
@@ -310,8 +331,9 @@ PROHD_DEV void si_chol_inv(SiSmem& S, int b, int lane) {
 }
 
 // dst (local rows) = src L^{-T}: dst[i][j] = sum_{k <= j} src[i][k] Linv[j][k].
-PROHD_DEV void si_apply_linv(SiSmem& S, const float* src, float* dst, int nr, int b) {
-  for (int o = threadIdx.x; o < kSiMaxRows * kSiMaxB; o += kSiThreads) {
+template <int ROWS, class SM>
+PROHD_DEV void si_apply_linv(SM& S, const float* src, float* dst, int nr, int b) {
+  for (int o = threadIdx.x; o < ROWS * kSiMaxB; o += kSiThreads) {
     const int i = o >> 5, j = o & 31;
     if (i < nr && j < b) {
       float v = 0.f;
@@ -322,7 +344,8 @@ PROHD_DEV void si_apply_linv(SiSmem& S, const float* src, float* dst, int nr, in
 }
 
 // part[j*b + k] = sum_i src[i][j] src[i][k] over local rows.
-PROHD_DEV void si_local_gram(SiSmem& S, const float* src, int nr, int b) {
+template <class SM>
+PROHD_DEV void si_local_gram(SM& S, const float* src, int nr, int b) {
   for (int e = threadIdx.x; e < kSiMaxB * kSiMaxB; e += kSiThreads) {
     const int j = e >> 5, k = e & 31;
     if (j < b && k < b) {
@@ -336,43 +359,47 @@ PROHD_DEV void si_local_gram(SiSmem& S, const float* src, int nr, int b) {
 // The exchange half of a Cholesky-QR pass over the local rows in `src`:
 // local Gram, exchange (n_extra further values of part ride along), summed
 // Gram into S.M and the extra values into S.res.
-PROHD_DEV void si_cholqr_pass(SiSmem& S, const float* src, int nr, int b, uint32_t rank, int& xb, int n_extra) {
+template <int NC, class SM>
+PROHD_DEV void si_cholqr_pass(SM& S, const float* src, int nr, int b, uint32_t rank, int& xb, int n_extra) {
   si_local_gram(S, src, nr, b);
   __syncthreads();
-  si_broadcast(S, xb, rank, b * b + n_extra);
-  cluster_sync();
+  si_broadcast<NC>(S, xb, rank, b * b + n_extra);
+  si_sync<NC>();
   for (int e = threadIdx.x; e < kSiMaxB * kSiMaxB; e += kSiThreads) {
     const int j = e >> 5, k = e & 31;
-    if (j < b && k < b) S.M[j * kSiLd + k] = si_sum(S, xb, j * b + k);
+    if (j < b && k < b) S.M[j * kSiLd + k] = si_sum<NC>(S, xb, j * b + k);
   }
-  for (int j = threadIdx.x; j < n_extra; j += kSiThreads) S.res[j] = si_sum(S, xb, b * b + j);
+  for (int j = threadIdx.x; j < n_extra; j += kSiThreads) S.res[j] = si_sum<NC>(S, xb, b * b + j);
   xb ^= 1;
   __syncthreads();
 }
 
-__global__ void __cluster_dims__(kSiCTAs, 1, 1) __launch_bounds__(kSiThreads, 1)
-    subspace_kernel(const float* __restrict__ C32, int D, int m, int b, int maxit, float eps, float sigma_rel,
-                    uint64_t seed, double* __restrict__ Uout, int* __restrict__ iters_out) {
-  extern __shared__ __align__(16) uint8_t sism[];
-  SiSmem& S = *reinterpret_cast<SiSmem*>(sism);
-  const uint32_t rank = cluster_rank();
-  const int rows_per = (D + kSiCTAs - 1) / kSiCTAs;
+// The iteration, run by NC CTAs (a cluster of 8 for one pair, or one CTA per
+// pair of a batch, which reads C from global memory and needs D % 4 == 0).
+template <int NC, int ROWS, int VLD>
+PROHD_DEV void subspace_body(SiSmemT<NC, ROWS, VLD>& S, const float* __restrict__ C32, int D, int m, int b,
+                             int maxit, float eps, float sigma_rel, uint64_t seed, double* __restrict__ Uout,
+                             int* __restrict__ iters_out) {
+  uint32_t rank = 0;
+  if constexpr (NC > 1) rank = cluster_rank();
+  const int rows_per = (D + NC - 1) / NC;
   const int r0 = min(D, (int)rank * rows_per), r1 = min(D, r0 + rows_per);
   const int nr = r1 - r0;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
 
   const int Dq = (D + 3) & ~3;  // C rows and V columns padded with zeros to a multiple of 4
-  for (int e = tid; e < nr * Dq; e += kSiThreads) {
-    const int i = e / Dq, k = e - i * Dq;
-    S.Cl[e] = k < D ? C32[(size_t)(r0 + i) * D + k] : 0.f;
-  }
+  if constexpr (NC > 1)
+    for (int e = tid; e < nr * Dq; e += kSiThreads) {
+      const int i = e / Dq, k = e - i * Dq;
+      S.Cl[e] = k < D ? C32[(size_t)(r0 + i) * D + k] : 0.f;
+    }
   // start block: column j is the oracle's start vector of component j + 1
   for (int e = tid; e < b * Dq; e += kSiThreads) {
     const int j = e / Dq, i = e - j * Dq;
-    S.Vt[j * kSiVld + i] = i < D ? (float)splitmix64_unit(seed, (uint64_t)(j + 1), (uint64_t)i) : 0.f;
+    S.Vt[j * VLD + i] = i < D ? (float)splitmix64_unit(seed, (uint64_t)(j + 1), (uint64_t)i) : 0.f;
   }
   __syncthreads();
-  cluster_sync();
+  si_sync<NC>();
 
   int xb = 0;  // exchange buffer
   int t = 0;
@@ -381,18 +408,19 @@ __global__ void __cluster_dims__(kSiCTAs, 1, 1) __launch_bounds__(kSiThreads, 1)
       // first pass only orthonormalises the start block
       for (int e = tid; e < nr * b; e += kSiThreads) {
         const int i = e / b, j = e - i * b;
-        S.Wr[e] = S.Vt[j * kSiVld + r0 + i];
+        S.Wr[e] = S.Vt[j * VLD + r0 + i];
       }
       __syncthreads();
-      si_cholqr_pass(S, S.Wr, nr, b, rank, xb, 0);
+      si_cholqr_pass<NC>(S, S.Wr, nr, b, rank, xb, 0);
     } else {
       // ---- W = C V for the local rows: 8-term FFMA blocks in two independent
       // chains (128-bit loads of a row of C and of a column of V), TwoSum
       // across blocks
       for (int o = tid; o < nr * b; o += kSiThreads) {
         const int i = o / b, j = o - i * b;
-        const float4* crow = reinterpret_cast<const float4*>(S.Cl + i * Dq);
-        const float4* vcol = reinterpret_cast<const float4*>(S.Vt + j * kSiVld);
+        const float4* crow = NC > 1 ? reinterpret_cast<const float4*>(S.Cl + i * Dq)
+                                    : reinterpret_cast<const float4*>(C32 + (size_t)(r0 + i) * D);
+        const float4* vcol = reinterpret_cast<const float4*>(S.Vt + j * VLD);
         float s0 = 0.f, c0 = 0.f, s1 = 0.f, c1 = 0.f;
         int k4 = 0;
         const int n4 = Dq >> 2;
@@ -435,16 +463,16 @@ __global__ void __cluster_dims__(kSiCTAs, 1, 1) __launch_bounds__(kSiThreads, 1)
         const int j = e >> 5, k = e & 31;
         if (j < b && k < b) {
           float s = 0.f;
-          for (int i = 0; i < nr; ++i) s = fmaf(S.Vt[j * kSiVld + r0 + i], S.W[i * b + k], s);
+          for (int i = 0; i < nr; ++i) s = fmaf(S.Vt[j * VLD + r0 + i], S.W[i * b + k], s);
           S.part[j * b + k] = s;
         }
       }
       __syncthreads();
-      si_broadcast(S, xb, rank, b * b);
-      cluster_sync();
+      si_broadcast<NC>(S, xb, rank, b * b);
+      si_sync<NC>();
       for (int e = tid; e < kSiMaxB * kSiMaxB; e += kSiThreads) {
         const int j = e >> 5, k = e & 31;
-        if (j < b && k < b) S.M[j * kSiLd + k] = 0.5f * (si_sum(S, xb, j * b + k) + si_sum(S, xb, k * b + j));
+        if (j < b && k < b) S.M[j * kSiLd + k] = 0.5f * (si_sum<NC>(S, xb, j * b + k) + si_sum<NC>(S, xb, k * b + j));
       }
       xb ^= 1;
       __syncthreads();
@@ -453,14 +481,14 @@ __global__ void __cluster_dims__(kSiCTAs, 1, 1) __launch_bounds__(kSiThreads, 1)
       __syncthreads();
       const float th0 = fmaxf(S.theta[0], 0.f);
       const float sigma = sigma_rel * th0;
-      for (int o = tid; o < kSiMaxRows * kSiMaxB; o += kSiThreads) {
+      for (int o = tid; o < ROWS * kSiMaxB; o += kSiThreads) {
         const int i = o >> 5, j = o & 31;
         if (i < nr && j < b) {
           const int col = min(max(S.perm[j], 0), b - 1);
           float v = 0.f, w = 0.f;
           for (int kk = 0; kk < b; ++kk) {
             const float y = S.Y[kk * kSiLd + col];
-            v = fmaf(S.Vt[kk * kSiVld + r0 + i], y, v);
+            v = fmaf(S.Vt[kk * VLD + r0 + i], y, v);
             w = fmaf(S.W[i * b + kk], y, w);
           }
           S.Vr[i * b + j] = v;
@@ -480,7 +508,7 @@ __global__ void __cluster_dims__(kSiCTAs, 1, 1) __launch_bounds__(kSiThreads, 1)
         S.part[b * b + j] = s;
       }
       __syncthreads();  // the residuals read Wr before it is scaled in place
-      for (int o = tid; o < kSiMaxRows * kSiMaxB; o += kSiThreads) {
+      for (int o = tid; o < ROWS * kSiMaxB; o += kSiThreads) {
         const int i = o >> 5, j = o & 31;
         if (i < nr && j < b) {
           const float den = fmaxf(S.theta[j], 0.f) + sigma;
@@ -490,7 +518,7 @@ __global__ void __cluster_dims__(kSiCTAs, 1, 1) __launch_bounds__(kSiThreads, 1)
       }
       __syncthreads();
       // ---- first Cholesky-QR exchange, carrying the residuals
-      si_cholqr_pass(S, S.Wr, nr, b, rank, xb, b);
+      si_cholqr_pass<NC>(S, S.Wr, nr, b, rank, xb, b);
       bool done = t >= maxit;
       const float lim = eps * fmaxf(S.theta[0], 0.f);
       bool conv = true, bad = !(lim == lim);
@@ -525,33 +553,57 @@ __global__ void __cluster_dims__(kSiCTAs, 1, 1) __launch_bounds__(kSiThreads, 1)
     const bool second = !(corr <= 1e-2f / (float)b);
     if (warp == 0) si_chol_inv(S, b, lane);
     __syncthreads();
-    si_apply_linv(S, S.Wr, S.W, nr, b);
+    si_apply_linv<ROWS>(S, S.Wr, S.W, nr, b);
     __syncthreads();
     const float* Q = S.W;
     if (second) {
-      si_cholqr_pass(S, S.W, nr, b, rank, xb, 0);
+      si_cholqr_pass<NC>(S, S.W, nr, b, rank, xb, 0);
       if (warp == 0) si_chol_inv(S, b, lane);
       __syncthreads();
-      si_apply_linv(S, S.W, S.Wr, nr, b);
+      si_apply_linv<ROWS>(S, S.W, S.Wr, nr, b);
       __syncthreads();
       Q = S.Wr;
     }
     // ---- new rows of V to every CTA
-    for (int e = tid; e < nr * b * kSiCTAs; e += kSiThreads) {
+    for (int e = tid; e < nr * b * NC; e += kSiThreads) {
       const int c = e / (nr * b), o = e - c * (nr * b);
       const int i = o / b, j = o - i * b;
-      st_cluster_f32(map_to_cta(&S.Vt[j * kSiVld + r0 + i], (uint32_t)c), Q[o]);
+      if constexpr (NC > 1)
+        st_cluster_f32(map_to_cta(&S.Vt[j * VLD + r0 + i], (uint32_t)c), Q[o]);
+      else
+        S.Vt[j * VLD + r0 + i] = Q[o];
     }
-    cluster_sync();
+    si_sync<NC>();
   }
   // every CTA leaves the loop in the same iteration; keep the cluster alive
   // until all remote accesses are done
-  cluster_sync();
+  si_sync<NC>();
+}
+
+__global__ void __cluster_dims__(kSiCTAs, 1, 1) __launch_bounds__(kSiThreads, 1)
+    subspace_kernel(const float* __restrict__ C32, int D, int m, int b, int maxit, float eps, float sigma_rel,
+                    uint64_t seed, double* __restrict__ Uout, int* __restrict__ iters_out) {
+  extern __shared__ __align__(16) uint8_t sism[];
+  subspace_body<kSiCTAs, kSiMaxRows, kSiVld>(*reinterpret_cast<SiSmem*>(sism), C32, D, m, b, maxit, eps, sigma_rel,
+                                             seed, Uout, iters_out);
+}
+
+// One CTA per pair of a batch; pairs of this launch's D class come from `list`.
+template <int ROWS>
+__global__ void __launch_bounds__(kSiThreads, 1)
+    subspace1_batched_kernel(const BPair* __restrict__ P, const int* __restrict__ list, float eps, float sigma_rel,
+                             uint64_t seed) {
+  extern __shared__ __align__(16) uint8_t sism[];
+  const BPair& q = P[list[blockIdx.x]];
+  if (q.m < 1) return;
+  const int b = min(q.D, min(kSiMaxB, max(2 * q.m, q.m + 8)));
+  subspace_body<1, ROWS, ROWS + 4>(*reinterpret_cast<SiSmemT<1, ROWS, ROWS + 4>*>(sism), q.C32, q.D, q.m, b,
+                                   max(q.iters, 1), eps, sigma_rel, seed, q.U, nullptr);
 }
 
 // FP64 clean-up of the m Ritz vectors (one CTA): modified Gram-Schmidt twice,
 // normalisation, sign (largest |entry| positive, lowest index on ties).
-__global__ void subspace_finalize_kernel(const double* __restrict__ Uin, int D, int m, double* __restrict__ dirs) {
+PROHD_DEV void subspace_finalize_body(const double* __restrict__ Uin, int D, int m, double* __restrict__ dirs) {
   __shared__ double u[kSiMaxD];
   __shared__ double red[kSiFinThreads / 32];
   __shared__ unsigned long long s_best[kSiFinThreads / 32];
@@ -610,8 +662,8 @@ __global__ void subspace_finalize_kernel(const double* __restrict__ Uin, int D, 
 
 // Rayleigh quotients lambda_l = u_l^T C u_l with the FP64 covariance: one warp
 // per row i writes u_l[i] (C u_l)[i]; a second kernel sums the rows in order.
-__global__ void rayleigh_rows_kernel(const double* __restrict__ C64, const double* __restrict__ dirs, int D, int m,
-                                     double* __restrict__ part) {
+PROHD_DEV void rayleigh_rows_body(const double* __restrict__ C64, const double* __restrict__ dirs, int D, int m,
+                                  double* __restrict__ part) {
   const int lane = threadIdx.x & 31;
   const int i = (int)((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5);
   if (i >= D) return;
@@ -624,7 +676,7 @@ __global__ void rayleigh_rows_kernel(const double* __restrict__ C64, const doubl
   }
 }
 
-__global__ void rayleigh_sum_kernel(const double* __restrict__ part, int D, int m, double* __restrict__ eig) {
+PROHD_DEV void rayleigh_sum_body(const double* __restrict__ part, int D, int m, double* __restrict__ eig) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   for (int l = warp; l < m; l += blockDim.x >> 5) {
     double s = 0.0;
@@ -632,6 +684,31 @@ __global__ void rayleigh_sum_kernel(const double* __restrict__ part, int D, int 
     s = warp_sum(s);
     if (lane == 0) eig[l] = s;
   }
+}
+
+__global__ void subspace_finalize_kernel(const double* __restrict__ Uin, int D, int m, double* __restrict__ dirs) {
+  subspace_finalize_body(Uin, D, m, dirs);
+}
+__global__ void rayleigh_rows_kernel(const double* __restrict__ C64, const double* __restrict__ dirs, int D, int m,
+                                     double* __restrict__ part) {
+  rayleigh_rows_body(C64, dirs, D, m, part);
+}
+__global__ void rayleigh_sum_kernel(const double* __restrict__ part, int D, int m, double* __restrict__ eig) {
+  rayleigh_sum_body(part, D, m, eig);
+}
+
+// Batched forms: one block (finalize, sums) or one grid row (row partials) per pair.
+__global__ void subspace_finalize_batched_kernel(const BPair* __restrict__ P) {
+  const BPair& q = P[blockIdx.x];
+  if (q.m >= 1) subspace_finalize_body(q.U, q.D, q.m, q.dirs);
+}
+__global__ void rayleigh_rows_batched_kernel(const BPair* __restrict__ P) {
+  const BPair& q = P[blockIdx.y];
+  if (q.m >= 1) rayleigh_rows_body(q.C64, q.dirs, q.D, q.m, q.rpart);
+}
+__global__ void rayleigh_sum_batched_kernel(const BPair* __restrict__ P) {
+  const BPair& q = P[blockIdx.x];
+  if (q.m >= 1) rayleigh_sum_body(q.rpart, q.D, q.m, q.eig);
 }
 
 bool subspace_supported(int D, int m) { return D >= 1 && D <= kSiMaxD && m >= 1 && m <= kSiMaxM; }
@@ -660,6 +737,32 @@ cudaError_t subspace_run(prohd_ctx* ctx, const float* C32, const double* C64, in
     count_launch();
     rayleigh_sum_kernel<<<1, 256, 0, st>>>(part, D, m, eig);
   }
+  return cudaGetLastError();
+}
+
+cudaError_t subspace_batched(const BPair* P, const int* const cls_pairs[3], const int ncls[3], int npairs, int Dmax,
+                             int mmax, double tol, uint64_t seed, cudaStream_t st) {
+  if (mmax < 1) return cudaSuccess;
+  if (mmax > kSiMaxM || Dmax > kSiMaxD) return cudaErrorInvalidValue;
+  const float eps = (float)std::max(std::sqrt(2.0 * std::max(tol, 0.0)), 2e-6);
+  cudaError_t e;
+  auto go = [&](auto kern, size_t smem, const int* list, int n) -> cudaError_t {
+    if (n == 0) return cudaSuccess;
+    cudaError_t r = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (r) return r;
+    count_launch();
+    kern<<<n, kSiThreads, smem, st>>>(P, list, eps, 0.01f, seed);
+    return cudaGetLastError();
+  };
+  if ((e = go(subspace1_batched_kernel<64>, sizeof(SiSmemT<1, 64, 68>), cls_pairs[0], ncls[0]))) return e;
+  if ((e = go(subspace1_batched_kernel<128>, sizeof(SiSmemT<1, 128, 132>), cls_pairs[1], ncls[1]))) return e;
+  if ((e = go(subspace1_batched_kernel<256>, sizeof(SiSmemT<1, 256, 260>), cls_pairs[2], ncls[2]))) return e;
+  count_launch();
+  subspace_finalize_batched_kernel<<<npairs, kSiFinThreads, 0, st>>>(P);
+  count_launch();
+  rayleigh_rows_batched_kernel<<<dim3((Dmax + 7) / 8, npairs), 256, 0, st>>>(P);
+  count_launch();
+  rayleigh_sum_batched_kernel<<<npairs, 256, 0, st>>>(P);
   return cudaGetLastError();
 }
 

@@ -33,6 +33,9 @@ EXPORTS = [
     "prohd_estimate_workspace_size", "prohd_estimate_host_workspace_size",
     "hausdorff_exact", "prohd_directions", "prohd_select", "prohd_estimate", "prohd_estimate_host",
     "prohd_profile_enable", "prohd_profile_read", "prohd_launch_count", "hausdorff_exact_noalloc",
+    "prohd_batch_workspace_size", "prohd_batch_plan", "prohd_batch_destroy", "prohd_estimate_batched",
+    "prohd_batch_use_graph", "prohd_batch_autotune", "prohd_batch_get_tunables", "prohd_batch_set_tunables",
+    "prohd_batch_pair_outputs",
 ]
 
 #: prohd_phase names, in enum order
@@ -56,6 +59,11 @@ class HdResult(ctypes.Structure):
 
 class Result(ctypes.Structure):
     _fields_ = [("hd", HdResult), ("nsel_a", ctypes.c_int64), ("nsel_b", ctypes.c_int64)]
+
+
+class PairDesc(ctypes.Structure):
+    _fields_ = [("A", ctypes.c_void_p), ("nA", ctypes.c_int64), ("B", ctypes.c_void_p), ("nB", ctypes.c_int64),
+                ("D", ctypes.c_int32), ("reserved", ctypes.c_int32)]
 
 
 _lib = None
@@ -112,6 +120,26 @@ def load_library(path: str = LIB_PATH):
         lib.prohd_launch_count.restype = ctypes.c_uint64
         lib.hausdorff_exact_noalloc.argtypes = [vp, vp, i64, vp, i64, i32, vp, vp]
         lib.hausdorff_exact_noalloc.restype = i32
+        pd = ctypes.POINTER(PairDesc)
+        pi32 = ctypes.POINTER(ctypes.c_int32)
+        lib.prohd_batch_workspace_size.argtypes = [pd, i32, pp]
+        lib.prohd_batch_workspace_size.restype = sz
+        lib.prohd_batch_plan.argtypes = [vp, pd, i32, pp, vp, sz, ctypes.POINTER(vp)]
+        lib.prohd_batch_plan.restype = i32
+        lib.prohd_batch_destroy.argtypes = [vp]
+        lib.prohd_batch_destroy.restype = None
+        lib.prohd_estimate_batched.argtypes = [vp, vp, vp, vp]
+        lib.prohd_estimate_batched.restype = i32
+        lib.prohd_batch_use_graph.argtypes = [vp, i32]
+        lib.prohd_batch_use_graph.restype = i32
+        lib.prohd_batch_autotune.argtypes = [vp, vp, vp, vp, ctypes.POINTER(ctypes.c_double)]
+        lib.prohd_batch_autotune.restype = i32
+        lib.prohd_batch_get_tunables.argtypes = [vp, pi32, pi32, pi32]
+        lib.prohd_batch_get_tunables.restype = i32
+        lib.prohd_batch_set_tunables.argtypes = [vp, i32, i32, i32]
+        lib.prohd_batch_set_tunables.restype = i32
+        lib.prohd_batch_pair_outputs.argtypes = [vp, i32, ctypes.POINTER(vp), ctypes.POINTER(vp), ctypes.POINTER(vp)]
+        lib.prohd_batch_pair_outputs.restype = i32
         _lib = lib
         return lib
 
@@ -316,6 +344,103 @@ class Context:
                                           self._stream(stream))
         self._raise(rc, "prohd_estimate_host")
         return out_host
+
+
+class Batch:
+    """A planned batch of independent pairs (prohd_batch_plan). Keeps the
+    pair tensors and the workspace alive for the plan's lifetime."""
+
+    def __init__(self, ctx: Context, pairs, params: Params | None = None, **kw):
+        torch = _torch()
+        self.ctx = ctx
+        self.params = params if params is not None else default_params(**kw)
+        self.pairs = []
+        for A, B in pairs:
+            _check_points(A, "A")
+            _check_points(B, "B")
+            if A.shape[1] != B.shape[1]:
+                raise ValueError("A and B of a pair must have the same D")
+            self.pairs.append((A, B))
+        n = len(self.pairs)
+        self._desc = (PairDesc * n)()
+        for i, (A, B) in enumerate(self.pairs):
+            self._desc[i] = PairDesc(A.data_ptr(), A.shape[0], B.data_ptr(), B.shape[0], A.shape[1], 0)
+        need = ctx.lib.prohd_batch_workspace_size(self._desc, n, ctypes.byref(self.params))
+        if need == 0:
+            # let the planner report why
+            need = 256
+        dev = self.pairs[0][0].device
+        self.ws = torch.empty(int(need), dtype=torch.uint8, device=dev)
+        self.out = torch.empty(n * ctypes.sizeof(Result), dtype=torch.uint8, device=dev)
+        h = ctypes.c_void_p()
+        rc = ctx.lib.prohd_batch_plan(ctx.h, self._desc, n, ctypes.byref(self.params), _ptr(self.ws), self.ws.numel(),
+                                      ctypes.byref(h))
+        ctx._raise(rc, "prohd_batch_plan")
+        self.h = h
+        self.n = n
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.ctx.lib.prohd_batch_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def use_graph(self, on: bool):
+        self.ctx._raise(self.ctx.lib.prohd_batch_use_graph(self.h, 1 if on else 0), "prohd_batch_use_graph")
+
+    def run(self, stream=None):
+        """Enqueues the whole batch; returns the device result buffer."""
+        rc = self.ctx.lib.prohd_estimate_batched(self.ctx.h, self.h, _ptr(self.out), self.ctx._stream(stream))
+        self.ctx._raise(rc, "prohd_estimate_batched")
+        return self.out
+
+    def autotune(self, stream=None) -> float:
+        ms = ctypes.c_double()
+        rc = self.ctx.lib.prohd_batch_autotune(self.ctx.h, self.h, _ptr(self.out), self.ctx._stream(stream),
+                                               ctypes.byref(ms))
+        self.ctx._raise(rc, "prohd_batch_autotune")
+        return ms.value
+
+    def tunables(self) -> dict:
+        g, p, s = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32()
+        self.ctx._raise(self.ctx.lib.prohd_batch_get_tunables(self.h, ctypes.byref(g), ctypes.byref(p),
+                                                              ctypes.byref(s)), "prohd_batch_get_tunables")
+        return dict(gram_pts=g.value, proj_rows=p.value, sel_chunk=s.value)
+
+    def set_tunables(self, gram_pts: int, proj_rows: int, sel_chunk: int):
+        self.ctx._raise(self.ctx.lib.prohd_batch_set_tunables(self.h, gram_pts, proj_rows, sel_chunk),
+                        "prohd_batch_set_tunables")
+
+    def results(self) -> list:
+        """Decodes the result buffer (call after the stream is synchronised)."""
+        host = bytes(self.out.cpu().numpy().tobytes())
+        sz = ctypes.sizeof(Result)
+        return [decode_result(Result.from_buffer_copy(host[i * sz:(i + 1) * sz])) for i in range(self.n)]
+
+    def pair_outputs(self, i: int, nsel_a: int, nsel_b: int):
+        """(dirs [1+m, D] float64, idxA [nsel_a], idxB [nsel_b]) of pair i as numpy arrays."""
+        torch = _torch()
+        d, a, b = ctypes.c_void_p(), ctypes.c_void_p(), ctypes.c_void_p()
+        self.ctx._raise(self.ctx.lib.prohd_batch_pair_outputs(self.h, i, ctypes.byref(d), ctypes.byref(a),
+                                                              ctypes.byref(b)), "prohd_batch_pair_outputs")
+        A, _ = self.pairs[i]
+        D = A.shape[1]
+        m = self.params.m if self.params.m >= 0 else int(math.isqrt(D))
+        base = self.ws.data_ptr()
+
+        def view(ptr, count, dtype, itemsize):
+            off = ptr - base
+            return self.ws[off:off + count * itemsize].view(dtype)
+
+        dirs = view(d.value, (1 + m) * D, torch.float64, 8).reshape(1 + m, D).cpu().numpy()
+        ia = view(a.value, nsel_a, torch.int32, 4).cpu().numpy().astype(np.int64)
+        ib = view(b.value, nsel_b, torch.int32, 4).cpu().numpy().astype(np.int64)
+        return dirs, ia, ib
 
 
 # ----------------------------------------------------------------- decoding

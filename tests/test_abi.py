@@ -33,3 +33,20 @@ def test_host_only_helpers():
     assert prohd.k_of(0.5, 1) == 1
     p = prohd.default_params()
     assert p.m == -1 and p.precision == 1 and p.alpha_c == 0.01 and p.power_max_iters == 1000
+
+
+def test_batch_workspace_size_is_host_only():
+    # planning checks run on the host: valid pairs get a size, invalid ones 0
+    lib = prohd.load_library()
+    p = prohd.default_params(m=8)
+    ok = (prohd.PairDesc * 2)(prohd.PairDesc(256, 1000, 512, 2000, 64, 0),
+                              prohd.PairDesc(1024, 5000, 2048, 300, 256, 0))
+    n = lib.prohd_batch_workspace_size(ok, 2, ctypes.byref(p))
+    assert n > 0
+    big = (prohd.PairDesc * 1)(prohd.PairDesc(256, 100_000, 512, 100_000, 256, 0))
+    assert lib.prohd_batch_workspace_size(big, 1, ctypes.byref(p)) > n
+    for D, a in ((13, 256), (512, 256), (64, 4)):
+        bad = (prohd.PairDesc * 1)(prohd.PairDesc(a, 1000, 512, 2000, D, 0))
+        assert lib.prohd_batch_workspace_size(bad, 1, ctypes.byref(p)) == 0, (D, a)
+    p30 = prohd.default_params(m=30)
+    assert lib.prohd_batch_workspace_size(ok, 2, ctypes.byref(p30)) == 0
