@@ -309,9 +309,11 @@ prohd_status prohd_batch_get_tunables(const prohd_batch* b, int32_t* gram_pts, i
 prohd_status prohd_batch_set_tunables(prohd_batch* b, int32_t gram_pts, int32_t proj_rows, int32_t sel_chunk);
 
 /* Device pointers (inside the plan's workspace) of pair `pair`'s directions
- * [1+m][D] (FP64) and candidate indices (int32, the first nsel_a / nsel_b
- * entries are valid after a run). */
-prohd_status prohd_batch_pair_outputs(const prohd_batch* b, int pair, double** dirs, int32_t** idxA, int32_t** idxB);
+ * [1+m][D] (FP64), candidate indices (int32, the first nsel_a / nsel_b
+ * entries are valid after a run) and block-iteration step count (one int32).
+ * Any output pointer may be NULL. */
+prohd_status prohd_batch_pair_outputs(const prohd_batch* b, int pair, double** dirs, int32_t** idxA, int32_t** idxB,
+                                      int32_t** iters);
 
 #ifdef __cplusplus
 }

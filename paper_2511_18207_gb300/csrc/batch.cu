@@ -174,6 +174,7 @@ void batch_layout(Arena& a, const std::vector<PairPlan>& pp, const prohd_pair_de
   for (int i = 0; i < np; ++i) {
     BPair& b = L.hp[i];
     b.status = a.take<int>(1, 16);
+    b.iters_out = a.take<int>(1, 16);
     b.maxnorm = a.take<float>(2, 16);
   }
   for (int i = 0; i < np; ++i) {
@@ -293,6 +294,9 @@ struct prohd_batch {
   int Dmax = 0, ndmax = 0, mmax = 0, nblk_max = 0;
   int64_t nmax = 0;
   int grid_gram = 0;
+  // side streams and events of the fork-join around the block iteration
+  cudaStream_t side[2] = {nullptr, nullptr};
+  cudaEvent_t ev_fork = nullptr, ev_join[2] = {nullptr, nullptr};
   // graph
   bool use_graph = true;
   cudaStream_t cap_stream = nullptr;
@@ -516,7 +520,17 @@ cudaError_t enqueue(prohd_batch* b, prohd_result* out, cudaStream_t st) {
     PhaseTimer pt(ctx, PROHD_PH_POWER, st);
     if ((e = covariance_batched(L.P, np, b->Dmax, st))) return e;
     const int* lists[3] = {L.cls + b->cls_off[0], L.cls + b->cls_off[1], L.cls + b->cls_off[2]};
-    if ((e = subspace_batched(L.P, lists, b->ncls, np, b->Dmax, b->mmax, b->p.power_tol, b->p.seed, st))) return e;
+    // the three D classes run side by side: fork two streams off `st`, join them back
+    const cudaStream_t cs[3] = {st, b->side[0], b->side[1]};
+    if ((e = cudaEventRecord(b->ev_fork, st))) return e;
+    for (int k = 0; k < 2; ++k)
+      if ((e = cudaStreamWaitEvent(b->side[k], b->ev_fork, 0))) return e;
+    if ((e = subspace_batched(L.P, lists, b->ncls, np, b->Dmax, b->mmax, b->p.power_tol, b->p.seed, cs))) return e;
+    for (int k = 0; k < 2; ++k) {
+      if ((e = cudaEventRecord(b->ev_join[k], b->side[k]))) return e;
+      if ((e = cudaStreamWaitEvent(st, b->ev_join[k], 0))) return e;
+    }
+    if ((e = subspace_batched_finish(L.P, np, b->Dmax, b->mmax, st))) return e;
   }
   {
     PhaseTimer pt(ctx, PROHD_PH_PROJECT, st);
@@ -600,14 +614,19 @@ prohd_status prohd_batch_plan(prohd_ctx* ctx, const prohd_pair_desc* pairs, int 
     b->proj_rows = ctx->batch_proj_rows;
     b->sel_chunk = ctx->batch_sel_chunk;
   }
-  if (cudaStreamCreateWithFlags(&b->cap_stream, cudaStreamNonBlocking) != cudaSuccess) {
-    delete b;
-    return bfail(ctx, PROHD_ECUDA, "could not create the capture stream");
+  bool ok = cudaStreamCreateWithFlags(&b->cap_stream, cudaStreamNonBlocking) == cudaSuccess;
+  for (int k = 0; k < 2 && ok; ++k) {
+    ok = cudaStreamCreateWithFlags(&b->side[k], cudaStreamNonBlocking) == cudaSuccess &&
+         cudaEventCreateWithFlags(&b->ev_join[k], cudaEventDisableTiming) == cudaSuccess;
+  }
+  ok = ok && cudaEventCreateWithFlags(&b->ev_fork, cudaEventDisableTiming) == cudaSuccess;
+  if (!ok) {
+    prohd_batch_destroy(b);
+    return bfail(ctx, PROHD_ECUDA, "could not create the batch's streams and events");
   }
   s = write_tables(b);
   if (s != PROHD_OK) {
-    cudaStreamDestroy(b->cap_stream);
-    delete b;
+    prohd_batch_destroy(b);
     return s;
   }
   *out = b;
@@ -618,6 +637,11 @@ void prohd_batch_destroy(prohd_batch* b) {
   if (!b) return;
   if (b->gexec) cudaGraphExecDestroy(b->gexec);
   if (b->cap_stream) cudaStreamDestroy(b->cap_stream);
+  for (int k = 0; k < 2; ++k) {
+    if (b->side[k]) cudaStreamDestroy(b->side[k]);
+    if (b->ev_join[k]) cudaEventDestroy(b->ev_join[k]);
+  }
+  if (b->ev_fork) cudaEventDestroy(b->ev_fork);
   delete b;
 }
 
@@ -744,12 +768,14 @@ prohd_status prohd_batch_set_tunables(prohd_batch* b, int32_t gram_pts, int32_t 
   return write_tables(b);
 }
 
-prohd_status prohd_batch_pair_outputs(const prohd_batch* b, int pair, double** dirs, int32_t** idxA, int32_t** idxB) {
+prohd_status prohd_batch_pair_outputs(const prohd_batch* b, int pair, double** dirs, int32_t** idxA, int32_t** idxB,
+                                      int32_t** iters) {
   if (!b || pair < 0 || pair >= b->npairs) return PROHD_EINVAL;
   const BPair& q = b->L.hp[(size_t)pair];
   if (dirs) *dirs = q.dirs;
   if (idxA) *idxA = q.idxA;
   if (idxB) *idxB = q.idxB;
+  if (iters) *iters = q.iters_out;
   return PROHD_OK;
 }
 

@@ -267,13 +267,15 @@ __global__ void centroid_axis_kernel(const double* __restrict__ sumA, const doub
 __device__ __forceinline__ void cov_finalize_body(const double* __restrict__ G, const double* __restrict__ sumA,
                                                   const double* __restrict__ sumB, int64_t nA, int64_t nB, int D,
                                                   double* __restrict__ C64, float* __restrict__ C32) {
-  const double N = (double)(nA + nB);
+  // one FP64 reciprocal, then products (FP64 division is slow on this GPU);
+  // each product is within one rounding of the quotient
+  const double invN = 1.0 / (double)(nA + nB);
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < (int64_t)D * D;
        e += (int64_t)gridDim.x * blockDim.x) {
     const int i = (int)(e / D), j = (int)(e % D);
     const int a = i < j ? i : j, b = i < j ? j : i;
-    const double di = (sumA[i] + sumB[i]) / N, dj = (sumA[j] + sumB[j]) / N;
-    const double c = G[(size_t)a * D + b] / N - di * dj;
+    const double di = (__ldg(sumA + i) + __ldg(sumB + i)) * invN, dj = (__ldg(sumA + j) + __ldg(sumB + j)) * invN;
+    const double c = __ldg(G + (size_t)a * D + b) * invN - di * dj;
     C64[e] = c;
     C32[e] = (float)c;
   }
@@ -302,12 +304,12 @@ __global__ void pilot_batched_kernel(const BPair* __restrict__ P) {
   if (g < G && threadIdx.x < G * D) {
     int64_t r = g;
     for (; r + 3 * G < rows; r += 4 * G) {
-      s0 += q.A[r * D + d];
-      s1 += q.A[(r + G) * D + d];
-      s2 += q.A[(r + 2 * G) * D + d];
-      s3 += q.A[(r + 3 * G) * D + d];
+      s0 += __ldg(q.A + r * D + d);
+      s1 += __ldg(q.A + (r + G) * D + d);
+      s2 += __ldg(q.A + (r + 2 * G) * D + d);
+      s3 += __ldg(q.A + (r + 3 * G) * D + d);
     }
-    for (; r < rows; r += G) s0 += q.A[r * D + d];
+    for (; r < rows; r += G) s0 += __ldg(q.A + r * D + d);
   }
   sh[threadIdx.x] = ((double)s0 + (double)s1) + ((double)s2 + (double)s3);
   __syncthreads();

@@ -574,12 +574,12 @@ __global__ void gram_tc_reduce_batched_kernel(const BPair* __restrict__ P, const
       for (; l + 4 <= l1; l += 4) {
 #pragma unroll
         for (int u = 0; u < 4; ++u) {
-          const float2 v = items[ids[l + u]].gacc[(size_t)col * 128 + row];
+          const float2 v = __ldg(items[ids[l + u]].gacc + (size_t)col * 128 + row);
           s4[u] += (double)v.x - (double)v.y;
         }
       }
       for (; l < l1; ++l) {
-        const float2 v = items[ids[l]].gacc[(size_t)col * 128 + row];
+        const float2 v = __ldg(items[ids[l]].gacc + (size_t)col * 128 + row);
         s4[0] += (double)v.x - (double)v.y;
       }
       q.G[(int64_t)i * D + j] = (s4[0] + s4[1]) + (s4[2] + s4[3]);
@@ -593,7 +593,7 @@ __global__ void gram_tc_reduce_batched_kernel(const BPair* __restrict__ P, const
       for (int l = q.gi0; l < q.gi0 + q.gn0; ++l) {
         const double* sm = items[ids[l]].sums;
 #pragma unroll
-        for (int w = 0; w < kGcConv; ++w) sw[w] += sm[(size_t)w * 2 * Dp + (size_t)set * Dp + d];
+        for (int w = 0; w < kGcConv; ++w) sw[w] += __ldg(sm + (size_t)w * 2 * Dp + (size_t)set * Dp + d);
       }
       double s = 0.0;
 #pragma unroll

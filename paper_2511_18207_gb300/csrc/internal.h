@@ -151,6 +151,7 @@ struct BPair {
   double* dirs;   // [nd][D]
   double* eig;    // [max(m,1)]
   int iters;      // block-iteration cap
+  int* iters_out; // block-iteration steps taken
   // selection
   float *qA, *qB;  // [nd][n] FP32 projections
   float* maxnorm;  // [2]
@@ -183,9 +184,11 @@ cudaError_t gram_reduce_batched(const BPair* P, int npairs, const GcItem* items,
                                 cudaStream_t st);
 cudaError_t pilot_batched(const BPair* P, int npairs, cudaStream_t st);
 cudaError_t covariance_batched(const BPair* P, int npairs, int Dmax, cudaStream_t st);
-// Block iteration with one CTA per pair, one launch per D class (D <= 64, 128, 256).
+// Block iteration with one CTA per pair, one launch per D class (D <= 64, 128, 256),
+// each on its own stream; then the FP64 clean-up and Rayleigh quotients.
 cudaError_t subspace_batched(const BPair* P, const int* const cls_pairs[3], const int ncls[3], int npairs, int Dmax,
-                             int mmax, double tol, uint64_t seed, cudaStream_t st);
+                             int mmax, double tol, uint64_t seed, const cudaStream_t cls_st[3]);
+cudaError_t subspace_batched_finish(const BPair* P, int npairs, int Dmax, int mmax, cudaStream_t st);
 cudaError_t proj_batched(const BPair* P, const ProjItem* items, int nitems, int ndmax, int* batch_status,
                          cudaStream_t st);
 struct SelProb;

@@ -267,7 +267,7 @@ __global__ void radix_hist_kernel(const SelProb* __restrict__ P, int pass, unsig
   const uint32_t himask = pass == 0 ? 0u : (0xffffffffu << (32 - 8 * pass));
   const uint32_t p0 = P[p].prefix[0], p1 = P[p].prefix[1];
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-    uint32_t key = f32_key(q[i]);
+    uint32_t key = f32_key(__ldg(q + i));
     uint32_t bin = (key >> shift) & 255u;
     if (((key ^ p0) & himask) == 0) atomicAdd(&h[0][bin], 1u);
     if (((key ^ p1) & himask) == 0) atomicAdd(&h[1][bin], 1u);
@@ -363,7 +363,7 @@ __global__ void band_kernel(SelProb* __restrict__ P) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < end; i += stride) {
     bool in0 = false, bd0 = false, in1 = false, bd1 = false;
     if (i < n) {
-      const float v = q[i];
+      const float v = __ldg(q + i);
       in0 = v < f_lo_in;
       bd0 = !in0 && v <= f_lo_band;
       in1 = v > f_hi_in;
@@ -412,7 +412,7 @@ __global__ void band_keys_kernel(const SelProb* __restrict__ P) {
   uint64_t* keys = P[p].bkey[side];
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < b; i += (int64_t)gridDim.x * blockDim.x) {
     double s = 0.0;
-    const float* x = X + (int64_t)lst[i] * D;
+    const float* x = X + (int64_t)__ldg(lst + i) * D;
     int k = 0;
     for (; k + 8 <= D; k += 8) {
       float xv[8];
@@ -448,8 +448,8 @@ __global__ void __launch_bounds__(512)
   const uint64_t* keys = P[p].bkey[side];
   if (b <= kBandSmem) {
     for (int64_t i = threadIdx.x; i < b; i += blockDim.x) {
-      si[i] = lst[i];
-      sk[i] = keys[i];
+      si[i] = __ldg(lst + i);
+      sk[i] = __ldg(keys + i);
     }
     __syncthreads();
     for (int64_t i = threadIdx.x; i < b; i += blockDim.x) {
@@ -476,7 +476,7 @@ __global__ void __launch_bounds__(512)
     __syncthreads();
     const uint64_t pre = s_prefix;
     for (int64_t i = threadIdx.x; i < b; i += blockDim.x) {
-      uint64_t k = keys[i];
+      uint64_t k = __ldg(keys + i);
       if (((k ^ pre) & him) == 0) atomicAdd(&hist[(k >> shift) & 255], 1u);
     }
     __syncthreads();
@@ -504,8 +504,8 @@ __global__ void __launch_bounds__(512)
     __syncthreads();
     const uint32_t pre = s_ipre;
     for (int64_t i = threadIdx.x; i < b; i += blockDim.x) {
-      if (keys[i] != kstar) continue;
-      uint32_t id = (uint32_t)lst[i];
+      if (__ldg(keys + i) != kstar) continue;
+      uint32_t id = (uint32_t)__ldg(lst + i);
       if (((id ^ pre) & him) == 0) atomicAdd(&hist[(id >> shift) & 255], 1u);
     }
     __syncthreads();
@@ -523,8 +523,8 @@ __global__ void __launch_bounds__(512)
   }
   const uint32_t istar = s_ipre;
   for (int64_t i = threadIdx.x; i < b; i += blockDim.x) {
-    const uint64_t k = keys[i];
-    const uint32_t id = (uint32_t)lst[i];
+    const uint64_t k = __ldg(keys + i);
+    const uint32_t id = (uint32_t)__ldg(lst + i);
     if (k < kstar || (k == kstar && id <= istar)) mask[id] = 1;
   }
 }
@@ -539,7 +539,7 @@ __device__ __forceinline__ void compact_count_body(const uint8_t* __restrict__ m
   unsigned c = 0;
   for (int i = threadIdx.x; i < kCompactItems; i += blockDim.x) {
     int64_t g = base + i;
-    c += (g < n && mask[g]) ? 1u : 0u;
+    c += (g < n && __ldg(mask + g)) ? 1u : 0u;
   }
   c = warp_sum(c);
   __shared__ unsigned s[32];
@@ -606,7 +606,7 @@ __device__ __forceinline__ void compact_write_body(const uint8_t* __restrict__ m
 #pragma unroll
   for (int j = 0; j < 4; ++j) {
     int64_t g = base + j;
-    f[j] = (g < n && mask[g]) ? 1u : 0u;
+    f[j] = (g < n && __ldg(mask + g)) ? 1u : 0u;
     c += f[j];
   }
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
@@ -644,9 +644,9 @@ __device__ __forceinline__ void gather_rows_body(const float* __restrict__ X, in
   const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
   const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
   for (int64_t r = warp; r < n; r += nw) {
-    const float* src = X + (int64_t)idx[r] * D;
+    const float* src = X + (int64_t)__ldg(idx + r) * D;
     float* dst = out + r * D;
-    for (int k = lane; k < D; k += 32) dst[k] = src[k];
+    for (int k = lane; k < D; k += 32) dst[k] = __ldg(src + k);
   }
 }
 

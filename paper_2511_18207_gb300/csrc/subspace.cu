@@ -42,7 +42,7 @@ namespace prohd {
 constexpr int kSiCTAs = 8;
 constexpr int kSiThreads = 512;
 constexpr int kSiFinThreads = 256;
-constexpr int kSiJacThreads = 256;  // the Jacobi rounds run on 8 warps (fewer warps per barrier)
+constexpr int kSiJacThreads = 256;  // the Jacobi rounds run on 8 warps (one warp alone is slower: the rounds are latency-bound)
 constexpr int kSiMaxD = 256;
 constexpr int kSiMaxB = 32;
 constexpr int kSiMaxM = 24;
@@ -58,6 +58,7 @@ template <int NC, int ROWS, int VLD>
 struct SiSmemT {
   float Vt[kSiMaxB * VLD];                 // basis, transposed: column j of V at Vt[j * VLD], zero padded
   float Cl[NC > 1 ? ROWS * kSiMaxD : 4];   // this CTA's rows of C (cluster only), row stride Dq, zero padded
+  float Cst[NC > 1 ? 4 : 2 * 32 * ROWS];   // one CTA: C streamed in 32-row chunks, double-buffered
   float W[ROWS * kSiMaxB];           // C V, local rows
   float Vr[ROWS * kSiMaxB];          // Ritz vectors V Y, local rows
   float Wr[ROWS * kSiMaxB];          // W Y -> scaled block -> Q1 -> Q
@@ -170,28 +171,38 @@ PROHD_DEV void si_block_max2(float& a, float& b, float* red /*[2][kSiThreads/32]
 // diagonal entry (rotations below that only move noise); then each Ritz
 // vector's own residual in H is at most sqrt(b) 2.4e-7 theta_1.
 // Maxima of two non-negative values over the Jacobi threads (all get them).
+// Barrier of the Jacobi threads: the warp itself, or named barrier 1.
+PROHD_DEV void si_jac_sync() {
+  if constexpr (kSiJacThreads == 32)
+    __syncwarp();
+  else
+    named_bar_sync(1, kSiJacThreads);
+}
+
 PROHD_DEV void si_jac_max2(float& a, float& b, float* red /*[2][kSiJacThreads/32]*/) {
   a = warp_max(a);
   b = warp_max(b);
-  const int w = threadIdx.x >> 5;
-  if ((threadIdx.x & 31) == 0) {
-    red[w] = a;
-    red[kSiJacThreads / 32 + w] = b;
-  }
-  named_bar_sync(1, kSiJacThreads);
-  a = 0.f;
-  b = 0.f;
+  if constexpr (kSiJacThreads > 32) {
+    const int w = threadIdx.x >> 5;
+    if ((threadIdx.x & 31) == 0) {
+      red[w] = a;
+      red[kSiJacThreads / 32 + w] = b;
+    }
+    si_jac_sync();
+    a = 0.f;
+    b = 0.f;
 #pragma unroll
-  for (int i = 0; i < kSiJacThreads / 32; ++i) {
-    a = fmaxf(a, red[i]);
-    b = fmaxf(b, red[kSiJacThreads / 32 + i]);
+    for (int i = 0; i < kSiJacThreads / 32; ++i) {
+      a = fmaxf(a, red[i]);
+      b = fmaxf(b, red[kSiJacThreads / 32 + i]);
+    }
   }
-  named_bar_sync(1, kSiJacThreads);
+  si_jac_sync();
 }
 
 template <class SM>
 PROHD_DEV void si_jacobi(SM& S, int b) {
-  // run by the first kSiJacThreads threads, synchronised by named barrier 1
+  // run by the first kSiJacThreads threads, synchronised by si_jac_sync
   const int tid = threadIdx.x;
   float* A = S.M;
   float* Y = S.Y;
@@ -238,7 +249,7 @@ PROHD_DEV void si_jacobi(SM& S, int b) {
         S.pq[tid][0] = p;
         S.pq[tid][1] = q;
       }
-      named_bar_sync(1, kSiJacThreads);
+      si_jac_sync();
       // work items: 2 x 2 blocks (k1, k2) of M, then the column pairs of Y
       const int nblk = np * np;
       for (int w = tid; w < nblk + b * np; w += kSiJacThreads) {
@@ -270,14 +281,14 @@ PROHD_DEV void si_jacobi(SM& S, int b) {
           }
         }
       }
-      named_bar_sync(1, kSiJacThreads);
+      si_jac_sync();
     }
   }
   // Ritz values by rank: descending, lower column first on ties. Every key
   // is computed once into shared memory and all comparisons read those
   // integers, so the ranks are a permutation whatever the values (NaN too).
   if (tid < b) S.key[tid] = f32_key(A[tid * kSiLd + tid]);
-  named_bar_sync(1, kSiJacThreads);
+  si_jac_sync();
   if (tid < b) {
     const uint32_t kj = S.key[tid];
     int rank = 0;
@@ -288,7 +299,7 @@ PROHD_DEV void si_jacobi(SM& S, int b) {
     S.perm[rank] = tid;
     S.theta[rank] = A[tid * kSiLd + tid];
   }
-  named_bar_sync(1, kSiJacThreads);
+  si_jac_sync();
 }
 
 // Cholesky S.M = L L^T (warp 0, lane i computes row i of L into S.Lf), then
@@ -416,10 +427,8 @@ PROHD_DEV void subspace_body(SiSmemT<NC, ROWS, VLD>& S, const float* __restrict_
       // ---- W = C V for the local rows: 8-term FFMA blocks in two independent
       // chains (128-bit loads of a row of C and of a column of V), TwoSum
       // across blocks
-      for (int o = tid; o < nr * b; o += kSiThreads) {
-        const int i = o / b, j = o - i * b;
-        const float4* crow = NC > 1 ? reinterpret_cast<const float4*>(S.Cl + i * Dq)
-                                    : reinterpret_cast<const float4*>(C32 + (size_t)(r0 + i) * D);
+      auto cv_row = [&](const float* __restrict__ crow_f, int j) -> float {
+        const float4* crow = reinterpret_cast<const float4*>(crow_f);
         const float4* vcol = reinterpret_cast<const float4*>(S.Vt + j * VLD);
         float s0 = 0.f, c0 = 0.f, s1 = 0.f, c1 = 0.f;
         int k4 = 0;
@@ -455,7 +464,46 @@ PROHD_DEV void subspace_body(SiSmemT<NC, ROWS, VLD>& S, const float* __restrict_
         }
         two_sum_acc(s0, c0, bt);
         two_sum_acc(s0, c0, s1);
-        S.W[o] = s0 + (c0 + c1);
+        return s0 + (c0 + c1);
+      };
+      if constexpr (NC > 1) {
+        for (int o = tid; o < nr * b; o += kSiThreads) {
+          const int i = o / b, j = o - i * b;
+          S.W[o] = cv_row(S.Cl + i * Dq, j);
+        }
+      } else {
+        // C streams from global memory (L2) through two 32-row shared
+        // buffers by cp.async, the next chunk in flight while this one is used
+        const int n4 = Dq >> 2;
+        const int nchunk = (D + 31) >> 5;
+        auto issue = [&](int c) {
+          float* dst = S.Cst + (c & 1) * 32 * ROWS;
+          const int rows = min(32, D - c * 32);
+          for (int e = tid; e < rows * n4; e += kSiThreads) {
+            const int i = e / n4, k4 = e - i * n4;
+            const uint32_t sa = smem_u32(dst + i * Dq + 4 * k4);
+            const float* gp = C32 + (size_t)(c * 32 + i) * D + 4 * k4;
+            asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(sa), "l"(gp) : "memory");
+          }
+          asm volatile("cp.async.commit_group;" ::: "memory");
+        };
+        issue(0);
+        for (int c = 0; c < nchunk; ++c) {
+          if (c + 1 < nchunk) {
+            issue(c + 1);
+            asm volatile("cp.async.wait_group 1;" ::: "memory");
+          } else {
+            asm volatile("cp.async.wait_group 0;" ::: "memory");
+          }
+          __syncthreads();
+          const float* cb = S.Cst + (c & 1) * 32 * ROWS;
+          const int rows = min(32, D - c * 32);
+          for (int o = tid; o < rows * b; o += kSiThreads) {
+            const int i = o / b, j = o - i * b;
+            S.W[(c * 32 + i) * b + j] = cv_row(cb + i * Dq, j);
+          }
+          __syncthreads();  // the buffer is refilled two chunks later
+        }
       }
       __syncthreads();
       // ---- H = V^T W (local rows), exchanged
@@ -598,7 +646,7 @@ __global__ void __launch_bounds__(kSiThreads, 1)
   if (q.m < 1) return;
   const int b = min(q.D, min(kSiMaxB, max(2 * q.m, q.m + 8)));
   subspace_body<1, ROWS, ROWS + 4>(*reinterpret_cast<SiSmemT<1, ROWS, ROWS + 4>*>(sism), q.C32, q.D, q.m, b,
-                                   max(q.iters, 1), eps, sigma_rel, seed, q.U, nullptr);
+                                   max(q.iters, 1), eps, sigma_rel, seed, q.U, q.iters_out);
 }
 
 // FP64 clean-up of the m Ritz vectors (one CTA): modified Gram-Schmidt twice,
@@ -741,22 +789,30 @@ cudaError_t subspace_run(prohd_ctx* ctx, const float* C32, const double* C64, in
 }
 
 cudaError_t subspace_batched(const BPair* P, const int* const cls_pairs[3], const int ncls[3], int npairs, int Dmax,
-                             int mmax, double tol, uint64_t seed, cudaStream_t st) {
+                             int mmax, double tol, uint64_t seed, const cudaStream_t cls_st[3]) {
+  (void)npairs;
+  (void)Dmax;
   if (mmax < 1) return cudaSuccess;
   if (mmax > kSiMaxM || Dmax > kSiMaxD) return cudaErrorInvalidValue;
   const float eps = (float)std::max(std::sqrt(2.0 * std::max(tol, 0.0)), 2e-6);
   cudaError_t e;
-  auto go = [&](auto kern, size_t smem, const int* list, int n) -> cudaError_t {
+  auto go = [&](auto kern, size_t smem, const int* list, int n, cudaStream_t s) -> cudaError_t {
     if (n == 0) return cudaSuccess;
     cudaError_t r = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (r) return r;
     count_launch();
-    kern<<<n, kSiThreads, smem, st>>>(P, list, eps, 0.01f, seed);
+    kern<<<n, kSiThreads, smem, s>>>(P, list, eps, 0.01f, seed);
     return cudaGetLastError();
   };
-  if ((e = go(subspace1_batched_kernel<64>, sizeof(SiSmemT<1, 64, 68>), cls_pairs[0], ncls[0]))) return e;
-  if ((e = go(subspace1_batched_kernel<128>, sizeof(SiSmemT<1, 128, 132>), cls_pairs[1], ncls[1]))) return e;
-  if ((e = go(subspace1_batched_kernel<256>, sizeof(SiSmemT<1, 256, 260>), cls_pairs[2], ncls[2]))) return e;
+  // largest class first: its CTAs are the longest
+  if ((e = go(subspace1_batched_kernel<256>, sizeof(SiSmemT<1, 256, 260>), cls_pairs[2], ncls[2], cls_st[2]))) return e;
+  if ((e = go(subspace1_batched_kernel<128>, sizeof(SiSmemT<1, 128, 132>), cls_pairs[1], ncls[1], cls_st[1]))) return e;
+  if ((e = go(subspace1_batched_kernel<64>, sizeof(SiSmemT<1, 64, 68>), cls_pairs[0], ncls[0], cls_st[0]))) return e;
+  return cudaSuccess;
+}
+
+cudaError_t subspace_batched_finish(const BPair* P, int npairs, int Dmax, int mmax, cudaStream_t st) {
+  if (mmax < 1) return cudaSuccess;
   count_launch();
   subspace_finalize_batched_kernel<<<npairs, kSiFinThreads, 0, st>>>(P);
   count_launch();

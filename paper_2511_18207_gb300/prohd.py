@@ -138,7 +138,8 @@ def load_library(path: str = LIB_PATH):
         lib.prohd_batch_get_tunables.restype = i32
         lib.prohd_batch_set_tunables.argtypes = [vp, i32, i32, i32]
         lib.prohd_batch_set_tunables.restype = i32
-        lib.prohd_batch_pair_outputs.argtypes = [vp, i32, ctypes.POINTER(vp), ctypes.POINTER(vp), ctypes.POINTER(vp)]
+        lib.prohd_batch_pair_outputs.argtypes = [vp, i32, ctypes.POINTER(vp), ctypes.POINTER(vp), ctypes.POINTER(vp),
+                                                 ctypes.POINTER(vp)]
         lib.prohd_batch_pair_outputs.restype = i32
         _lib = lib
         return lib
@@ -422,12 +423,25 @@ class Batch:
         sz = ctypes.sizeof(Result)
         return [decode_result(Result.from_buffer_copy(host[i * sz:(i + 1) * sz])) for i in range(self.n)]
 
+    def iterations(self) -> np.ndarray:
+        """Block-iteration steps of every pair in the last run (after a synchronise)."""
+        torch = _torch()
+        out = np.zeros(self.n, dtype=np.int64)
+        base = self.ws.data_ptr()
+        for i in range(self.n):
+            it = ctypes.c_void_p()
+            self.ctx._raise(self.ctx.lib.prohd_batch_pair_outputs(self.h, i, None, None, None, ctypes.byref(it)),
+                            "prohd_batch_pair_outputs")
+            off = it.value - base
+            out[i] = int(self.ws[off:off + 4].view(torch.int32).item())
+        return out
+
     def pair_outputs(self, i: int, nsel_a: int, nsel_b: int):
         """(dirs [1+m, D] float64, idxA [nsel_a], idxB [nsel_b]) of pair i as numpy arrays."""
         torch = _torch()
         d, a, b = ctypes.c_void_p(), ctypes.c_void_p(), ctypes.c_void_p()
         self.ctx._raise(self.ctx.lib.prohd_batch_pair_outputs(self.h, i, ctypes.byref(d), ctypes.byref(a),
-                                                              ctypes.byref(b)), "prohd_batch_pair_outputs")
+                                                              ctypes.byref(b), None), "prohd_batch_pair_outputs")
         A, _ = self.pairs[i]
         D = A.shape[1]
         m = self.params.m if self.params.m >= 0 else int(math.isqrt(D))
