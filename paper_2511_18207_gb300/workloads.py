@@ -144,6 +144,37 @@ def batched_pairs(npairs: int = 512, n_lo: int = 1000, n_hi: int = 100_000,
     return pairs
 
 
+def batched_pairs_device(npairs: int = 512, n_lo: int = 1000, n_hi: int = 100_000, dims=(64, 128, 256),
+                         k_lo: int = 4, k_hi: int = 32, seed: int = 0, device: str = "cuda"):
+    """The law of ``batched_pairs`` drawn with torch generators on the device
+    (the benchmark's 512-pair batch holds about 13 GB; drawing it on the host
+    would dominate the run). Sizes, D and K come from a seeded CPU generator,
+    the points from a seeded device generator: list of (A, B) float32 CUDA
+    tensors."""
+    import torch
+
+    g = torch.Generator(device="cpu")
+    g.manual_seed(int(seed))
+    gd = torch.Generator(device=device)
+    gd.manual_seed(int(seed) + 1)
+    lo, hi = math.log(n_lo), math.log(n_hi)
+    pairs = []
+    for _ in range(npairs):
+        u = torch.rand(2, generator=g, dtype=torch.float64)
+        sizes = [int(round(math.exp(lo + float(x) * (hi - lo)))) for x in u]
+        D = int(dims[int(torch.randint(0, len(dims), (1,), generator=g))])
+        K = int(torch.randint(k_lo, k_hi + 1, (1,), generator=g))
+        sets = []
+        for n in sizes:
+            means = torch.randn(K, D, generator=gd, device=device) * 2.0
+            sd = torch.sqrt(torch.empty(K, D, device=device).uniform_(0.2, 2.0, generator=gd))
+            comp = torch.randint(0, K, (n,), generator=gd, device=device)
+            X = torch.randn(n, D, generator=gd, device=device) * sd[comp] + means[comp]
+            sets.append(X.contiguous())
+        pairs.append((sets[0], sets[1]))
+    return pairs
+
+
 def student_t_mixture(n: int, D: int = 128, K: int = 8, nu: float = 3.0, seed: int = 0) -> np.ndarray:
     """K-component mixture of anisotropic multivariate Student-t (nu) laws:
     component c has mean ~ N(0, 4I) and scale Q_c diag(1/i) Q_c^T."""
