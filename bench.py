@@ -360,6 +360,9 @@ def gpu_arm(args):
     batched = None
     if not args.no_batched:
         batched = batched_arm(args, peaks, peak_src, dist, dev)
+    learned_res = None
+    if not args.no_learned and rank == 0:
+        learned_res = learned_arm(args, peaks, dev)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
@@ -394,6 +397,7 @@ def gpu_arm(args):
         "cpu_baseline": cpu,
         "clocks": clk,
         "batched": batched,
+        "learned": learned_res,
     }
     if rank == 0:
         print(json.dumps(line))
@@ -509,6 +513,56 @@ def batched_arm(args, peaks, peak_src, dist, dev):
     }
 
 
+# ---------------------------------------------------------------- learned directions
+
+LEARNED_WORKLOAD = ("learned directions: network 10D -> 256 -> 256 -> 4D (D = 128, BF16 tensor-core GEMMs, FP32 "
+                    "accumulate, Adam), trained on generated anisotropic Student-t (nu = 3) mixture pairs "
+                    "(n ~ U[5k, 20k]) labelled by exact-HD witnesses; held-out pairs of n = 100,000 against plain "
+                    "ProHD at an equal candidate budget")
+
+
+def learned_arm(args, peaks, dev):
+    """Training throughput of the network and its held-out gain."""
+    import torch
+    from paper_2511_18207_gb300 import learned, prohd
+
+    ctx = prohd.context()
+    t0 = time.time()
+    X, Y = learned.make_dataset(ctx, args.learned_pairs, D=128, seed=args.seed + 11)
+    t_data = time.time() - t0
+    net = prohd.Mlp(ctx, 128, seed=1)
+    B = 256
+    # warm-up, then the timed steps (CUDA events on the launching stream)
+    learned.train(net, X, Y, steps=args.warmup, batch=B, lr=1e-3, seed=1)
+    st = torch.cuda.current_stream()
+    l0 = ctx.launch_count()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(st)
+    losses, _ = learned.train(net, X, Y, steps=args.learned_steps, batch=B, lr=1e-3, seed=2)
+    e1.record(st)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / args.learned_steps
+    launches = (ctx.launch_count() - l0) // args.learned_steps
+    s = net.nparam
+    n_in, h, n_out = 1280, 256, 512
+    fwd = 2.0 * B * (n_in * h + h * h + h * n_out)
+    bwd = 2.0 * B * (n_in * h + 2 * h * h + 2 * h * n_out)  # weight gradients, and input gradients of layers 2-3
+    fl = fwd + bwd
+    ev = learned.evaluate(ctx, net, args.learned_eval, n=100_000, D=128, seed=args.seed + 12345)
+    ev.pop("rows")
+    return {
+        "workload": LEARNED_WORKLOAD, "params": s, "train_pairs": args.learned_pairs, "data_prep_s": t_data,
+        "batch": B, "steps": args.learned_steps, "ms_per_step": ms, "samples_per_s": 1000.0 * B / ms,
+        "gpu_launches_per_step": launches, "loss_first20": float(losses[:20].mean()),
+        "loss_last20": float(losses[-20:].mean()),
+        "roofline": {"kernel": "mlp_gemm_bf16_kernel (whole train step)", "bound": "latency",
+                     "achieved": fl / (ms / 1e3) / 1e12, "unit": "TFLOP/s",
+                     "peak": peaks["bf16_tflops"], "frac": fl / (ms / 1e3) / 1e12 / peaks["bf16_tflops"],
+                     "note": "GEMMs of 256 x <=1280 x <=512: the step is launch- and latency-bound, not tensor-bound"},
+        "held_out": ev,
+    }
+
+
 # ---------------------------------------------------------------- reference arm
 
 def reference_arm(args):
@@ -553,6 +607,10 @@ def main():
     ap.add_argument("--no-exact", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-batched", action="store_true", help="skip the 512-pair batch measurement")
+    ap.add_argument("--no-learned", action="store_true", help="skip the learned-direction measurement")
+    ap.add_argument("--learned-pairs", type=int, default=1024)
+    ap.add_argument("--learned-steps", type=int, default=1000)
+    ap.add_argument("--learned-eval", type=int, default=8)
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

@@ -315,6 +315,73 @@ prohd_status prohd_batch_set_tunables(prohd_batch* b, int32_t gram_pts, int32_t 
 prohd_status prohd_batch_pair_outputs(const prohd_batch* b, int pair, double** dirs, int32_t** idxA, int32_t** idxB,
                                       int32_t** iters);
 
+/* ---------------------------------------------------------------- given directions
+ *
+ * Algorithm 3 from the selection on: the caller's directions dirs [nd][D]
+ * (device, FP64, unit rows; row 0 conventionally the centroid axis) with
+ * per-direction k lists kA, kB (HOST arrays of nd values >= 1; a direction
+ * keeps its kA[d] smallest and kA[d] largest projections of A). Selection,
+ * union, gather and the subset HD run as in prohd_estimate (params.precision
+ * picks the tiles; m, alpha are not used). idxA / idxB may be NULL. */
+size_t prohd_estimate_dirs_workspace_size(int64_t nA, int64_t nB, int D, int nd, const int64_t* kA, const int64_t* kB,
+                                          int precision);
+prohd_status prohd_estimate_dirs(prohd_ctx* ctx, const float* A, int64_t nA, const float* B, int64_t nB, int D,
+                                 const prohd_params* p, const double* dirs, int nd, const int64_t* kA,
+                                 const int64_t* kB, prohd_result* out, int32_t* idxA, int32_t* idxB, void* ws,
+                                 size_t ws_bytes, void* stream);
+
+/* ---------------------------------------------------------------- learned directions
+ *
+ * A small network proposes 4 extra unit directions per pair from cheap set
+ * statistics (the learned direction dictionary of Sec. V, future work in the
+ * paper). It only adds directions, so plain ProHD is its fallback.
+ *
+ * Features (prohd_features), x [10 D] FP32: the centroid difference
+ * ybar - xbar, the 8 leading components scaled by sqrt(lambda), and the
+ * per-dimension union variances, divided by s = sqrt(trace(C)/D) (the
+ * variances by s^2). The call also returns the directions [9][D] (centroid
+ * axis + 8 components, as prohd_directions with m = 8) and eig [8].
+ *
+ * Network: h1 = relu(x W1 + b1), h2 = relu(h1 W2 + b2), z = h2 W3 + b3 with
+ * W1 [10D x 256], W2 [256 x 256], W3 [256 x 4D]; the 4 vectors of z are
+ * normalised. Loss against a unit label w (the witness direction
+ * (a* - b*)/||a* - b*|| of the exact HD): 1 - (1/10) log sum_j exp(10 (u_j . w)^2),
+ * averaged over the batch.
+ *
+ * State: params | Adam m | Adam v, FP32, prohd_mlp_state_bytes(D) bytes of
+ * device memory owned by the caller (prohd_mlp_param_count(D) floats per
+ * block; layout W1, b1, W2, b2, W3, b3, each row-major and 64-float aligned).
+ * precision: PROHD_FP32 (CUDA-core FP32 GEMMs) or PROHD_BF16 (operands
+ * rounded to BF16, tensor-core products, FP32 accumulation). Every call
+ * needs a scratch buffer of prohd_mlp_scratch_bytes(D, batch) (256-byte
+ * aligned). feat [batch][10 D], label [batch][D], outputs [batch][4][D].
+ */
+size_t prohd_features_workspace_size(int64_t nA, int64_t nB, int D);
+prohd_status prohd_features(prohd_ctx* ctx, const float* A, int64_t nA, const float* B, int64_t nB, int D,
+                            const prohd_params* p, float* feat, double* dirs, double* eig, void* ws, size_t ws_bytes,
+                            void* stream);
+size_t prohd_mlp_param_count(int D);
+size_t prohd_mlp_state_bytes(int D);
+size_t prohd_mlp_scratch_bytes(int D, int batch);
+/* Weights uniform on +-sqrt(6 / fan_in) from SplitMix64 (seed, layer 101..103,
+ * element index); biases and Adam moments zero. */
+prohd_status prohd_mlp_init(prohd_ctx* ctx, int D, uint64_t seed, void* state, void* stream);
+/* Unit directions of a batch: FP32 [batch][4][D] and/or FP64 (renormalised) [batch][4][D]; either may be NULL. */
+prohd_status prohd_mlp_forward(prohd_ctx* ctx, int D, const void* state, const float* feat, int batch, int precision,
+                               float* dirs32, double* dirs64, void* scratch, size_t scratch_bytes, void* stream);
+/* Mean loss (device float) and, if grad != NULL, its gradient [param_count] (no update). */
+prohd_status prohd_mlp_loss_grad(prohd_ctx* ctx, int D, const void* state, const float* feat, const float* label,
+                                 int batch, int precision, float* loss, float* grad, void* scratch,
+                                 size_t scratch_bytes, void* stream);
+/* One Adam step (beta 0.9 / 0.999, eps 1e-8, bias-corrected with `step`,
+ * counting from 1) on the mean loss of the batch; loss may be NULL. */
+prohd_status prohd_mlp_train_step(prohd_ctx* ctx, int D, void* state, const float* feat, const float* label, int batch,
+                                  int precision, float lr, int64_t step, float* loss, void* scratch,
+                                  size_t scratch_bytes, void* stream);
+/* The Adam update alone, with a caller gradient [param_count] (device FP32). */
+prohd_status prohd_mlp_adam_step(prohd_ctx* ctx, int D, void* state, const float* grad, float lr, int64_t step,
+                                 void* stream);
+
 #ifdef __cplusplus
 }
 #endif

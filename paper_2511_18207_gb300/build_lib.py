@@ -17,7 +17,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 OUT_DIR = os.path.join(HERE, "_lib")
 LIB = os.path.join(OUT_DIR, "libprohd.so")
-SOURCES = ["api.cu", "hd.cu", "select.cu", "directions.cu", "gram_tc.cu", "subspace.cu", "noalloc.cu", "batch.cu"]
+SOURCES = ["api.cu", "hd.cu", "select.cu", "directions.cu", "gram_tc.cu", "subspace.cu", "noalloc.cu", "batch.cu", "mlp.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-fvisibility=default",
               "--expt-relaxed-constexpr"]

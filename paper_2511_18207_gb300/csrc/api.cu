@@ -147,37 +147,52 @@ struct EstLayout {
   size_t mark_dir, mark_sel, mark_hd;  // arena offsets where each phase's scratch starts
 };
 
-void est_layout(Arena& a, int64_t nA, int64_t nB, int D, const prohd_params* p, EstLayout& L) {
-  const int m = resolve_m(p, D);
-  L.nd = 1 + m;
-  const double ap = resolve_alpha_p(p, m);
-  k_list(nA, L.nd, p->alpha_c, ap, L.kA);
-  k_list(nB, L.nd, p->alpha_c, ap, L.kB);
+// Layout of an estimate with nd directions and the given k lists; m_dirs >= 0
+// reserves the directions phase's scratch (m_dirs components), -1 skips it.
+void est_layout_k(Arena& a, int64_t nA, int64_t nB, int D, int nd, const int64_t* kA, const int64_t* kB,
+                  int precision, int m_dirs, EstLayout& L) {
+  L.nd = nd;
+  for (int d = 0; d < nd; ++d) {
+    L.kA[d] = kA[d];
+    L.kB[d] = kB[d];
+  }
   L.boundA = subset_bound(nA, L.nd, L.kA);
   L.boundB = subset_bound(nB, L.nd, L.kB);
   L.status = a.take<int>(8);
   L.dirs = a.take<double>((size_t)L.nd * D);
-  L.eig = a.take<double>((size_t)std::max(m, 1));
+  L.eig = a.take<double>((size_t)std::max(m_dirs, 1));
   L.idxA = a.take<int32_t>((size_t)nA);
   L.idxB = a.take<int32_t>((size_t)nB);
   L.nselA = a.take<int64_t>(1);
   L.nselB = a.take<int64_t>(1);
   L.As = a.take<float>((size_t)L.boundA * D);
   L.Bs = a.take<float>((size_t)L.boundB * D);
-  // the three phases run one after another and share the rest of the arena
+  // the phases run one after another and share the rest of the arena
   const size_t start = a.off;
   size_t end = start;
   L.mark_dir = L.mark_sel = L.mark_hd = (start + 255) / 256 * 256;
   Arena t = a;
-  directions_layout(t, nA, nB, D, m);
-  end = std::max(end, t.off);
+  if (m_dirs >= 0) {
+    directions_layout(t, nA, nB, D, m_dirs);
+    end = std::max(end, t.off);
+  }
   t = a;
   select_layout(t, nA, nB, D, L.nd);
   end = std::max(end, t.off);
   t = a;
-  hd_core_layout(t, L.boundA, L.boundB, D, p->precision);
+  hd_core_layout(t, L.boundA, L.boundB, D, precision);
   end = std::max(end, t.off);
   a.off = end;
+}
+
+void est_layout(Arena& a, int64_t nA, int64_t nB, int D, const prohd_params* p, EstLayout& L) {
+  const int m = resolve_m(p, D);
+  const int nd = 1 + m;
+  const double ap = resolve_alpha_p(p, m);
+  int64_t kA[64], kB[64];
+  k_list(nA, nd, p->alpha_c, ap, kA);
+  k_list(nB, nd, p->alpha_c, ap, kB);
+  est_layout_k(a, nA, nB, D, nd, kA, kB, p->precision, m, L);
 }
 
 }  // namespace
@@ -361,15 +376,11 @@ prohd_status prohd_select(prohd_ctx* ctx, const float* A, int64_t nA, const floa
   return e ? cuda_fail(ctx, e) : PROHD_OK;
 }
 
-static prohd_status estimate_impl(prohd_ctx* ctx, const float* A, int64_t nA, const float* B, int64_t nB, int D,
-                                  const prohd_params* p, prohd_result* out, int32_t* idxA, int32_t* idxB,
-                                  double* dirs, char* wsb, size_t ws_bytes, cudaStream_t st) {
-  Arena a;
-  a.base = wsb;
-  a.cap = ws_bytes;
-  EstLayout L;
-  est_layout(a, nA, nB, D, p, L);
-  if (a.overflow()) return fail(ctx, PROHD_ENOMEM, "workspace too small%s");
+// given_dirs: the caller's directions (nd = L.nd) replace the directions phase.
+static prohd_status estimate_run(prohd_ctx* ctx, const float* A, int64_t nA, const float* B, int64_t nB, int D,
+                                 const prohd_params* p, EstLayout& L, prohd_result* out, int32_t* idxA,
+                                 int32_t* idxB, double* dirs, const double* given_dirs, char* wsb, size_t ws_bytes,
+                                 cudaStream_t st) {
   if (idxA) L.idxA = idxA;
   if (idxB) L.idxB = idxB;
   if (dirs) L.dirs = dirs;
@@ -382,13 +393,15 @@ static prohd_status estimate_impl(prohd_ctx* ctx, const float* A, int64_t nA, co
     return t;
   };
   cudaError_t e = zero_i32(L.status, 8, st);
-  if (!e) {
+  const double* use_dirs = given_dirs ? given_dirs : L.dirs;
+  if (!e && !given_dirs) {
     Arena t = phase(L.mark_dir);
     e = directions_run(ctx, A, nA, B, nB, D, m, p->power_max_iters, p->power_tol, p->seed, L.dirs, L.eig, L.status, t, st);
   }
   if (!e) {
     Arena t = phase(L.mark_sel);
-    e = select_run(ctx, A, nA, B, nB, D, L.dirs, L.nd, L.kA, L.kB, L.idxA, L.nselA, L.idxB, L.nselB, L.status, t, st);
+    e = select_run(ctx, A, nA, B, nB, D, use_dirs, L.nd, L.kA, L.kB, L.idxA, L.nselA, L.idxB, L.nselB, L.status, t,
+                   st);
   }
   {
     PhaseTimer pt(ctx, PROHD_PH_GATHER, st);
@@ -407,6 +420,18 @@ static prohd_status estimate_impl(prohd_ctx* ctx, const float* A, int64_t nA, co
     e = cudaGetLastError();
   }
   return e ? cuda_fail(ctx, e) : PROHD_OK;
+}
+
+static prohd_status estimate_impl(prohd_ctx* ctx, const float* A, int64_t nA, const float* B, int64_t nB, int D,
+                                  const prohd_params* p, prohd_result* out, int32_t* idxA, int32_t* idxB,
+                                  double* dirs, char* wsb, size_t ws_bytes, cudaStream_t st) {
+  Arena a;
+  a.base = wsb;
+  a.cap = ws_bytes;
+  EstLayout L;
+  est_layout(a, nA, nB, D, p, L);
+  if (a.overflow()) return fail(ctx, PROHD_ENOMEM, "workspace too small%s");
+  return estimate_run(ctx, A, nA, B, nB, D, p, L, out, idxA, idxB, dirs, nullptr, wsb, ws_bytes, st);
 }
 
 prohd_status prohd_estimate(prohd_ctx* ctx, const float* A, int64_t nA, const float* B, int64_t nB, int D,
@@ -474,6 +499,167 @@ prohd_status prohd_profile_read(prohd_ctx* ctx, double* ms, int64_t* count, int 
     }
   }
   return PROHD_OK;
+}
+
+// ---------------------------------------------------------------- estimate with given directions
+
+static prohd_status check_klist(prohd_ctx* ctx, int nd, const int64_t* kA, const int64_t* kB) {
+  if (nd < 1 || nd > 64) return fail(ctx, PROHD_EINVAL, "need 1..64 directions%s");
+  if (!kA || !kB) return fail(ctx, PROHD_EINVAL, "null k lists%s");
+  for (int d = 0; d < nd; ++d)
+    if (kA[d] < 1 || kB[d] < 1) return fail(ctx, PROHD_EINVAL, "k must be >= 1%s");
+  return PROHD_OK;
+}
+
+size_t prohd_estimate_dirs_workspace_size(int64_t nA, int64_t nB, int D, int nd, const int64_t* kA, const int64_t* kB,
+                                          int precision) {
+  if (nd < 1 || nd > 64 || !kA || !kB) return 0;
+  Arena a;
+  EstLayout L;
+  est_layout_k(a, nA, nB, D, nd, kA, kB, precision, -1, L);
+  return a.off + 256;
+}
+
+prohd_status prohd_estimate_dirs(prohd_ctx* ctx, const float* A, int64_t nA, const float* B, int64_t nB, int D,
+                                 const prohd_params* p, const double* dirs, int nd, const int64_t* kA,
+                                 const int64_t* kB, prohd_result* out, int32_t* idxA, int32_t* idxB, void* ws,
+                                 size_t ws_bytes, void* stream) {
+  prohd_status s = check_sets(ctx, A, nA, B, nB, D);
+  if (s) return s;
+  if ((s = check_params(ctx, p, D))) return s;
+  if (!dirs) return fail(ctx, PROHD_EINVAL, "null dirs%s");
+  if ((s = check_klist(ctx, nd, kA, kB))) return s;
+  if (!out) return fail(ctx, PROHD_EINVAL, "null output%s");
+  if ((s = check_ws(ctx, ws, ws_bytes, prohd_estimate_dirs_workspace_size(nA, nB, D, nd, kA, kB, p->precision))))
+    return s;
+  Arena a;
+  a.base = static_cast<char*>(ws);
+  a.cap = ws_bytes;
+  EstLayout L;
+  est_layout_k(a, nA, nB, D, nd, kA, kB, p->precision, -1, L);
+  return estimate_run(ctx, A, nA, B, nB, D, p, L, out, idxA, idxB, nullptr, dirs, static_cast<char*>(ws), ws_bytes,
+                      reinterpret_cast<cudaStream_t>(stream));
+}
+
+// ---------------------------------------------------------------- learned directions
+
+size_t prohd_features_workspace_size(int64_t nA, int64_t nB, int D) {
+  Arena a;
+  a.take<int>(8);
+  directions_layout(a, nA, nB, D, 8);
+  return a.off + 256;
+}
+
+prohd_status prohd_features(prohd_ctx* ctx, const float* A, int64_t nA, const float* B, int64_t nB, int D,
+                            const prohd_params* p, float* feat, double* dirs, double* eig, void* ws, size_t ws_bytes,
+                            void* stream) {
+  prohd_status s = check_sets(ctx, A, nA, B, nB, D);
+  if (s) return s;
+  if (!p || !feat || !dirs || !eig) return fail(ctx, PROHD_EINVAL, "null argument%s");
+  if (D < 8) return fail(ctx, PROHD_EINVAL, "features need D >= 8 (8 components)%s");
+  if (p->power_max_iters < 1) return fail(ctx, PROHD_EINVAL, "power_max_iters must be >= 1%s");
+  if ((s = check_ws(ctx, ws, ws_bytes, prohd_features_workspace_size(nA, nB, D)))) return s;
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  Arena a;
+  a.base = static_cast<char*>(ws);
+  a.cap = ws_bytes;
+  int* status = a.take<int>(8);
+  cudaError_t e = zero_i32(status, 8, st);
+  if (!e) e = directions_features(ctx, A, nA, B, nB, D, p->power_max_iters, p->power_tol, p->seed, dirs, eig, feat,
+                                  status, a, st);
+  return e ? cuda_fail(ctx, e) : PROHD_OK;
+}
+
+size_t prohd_mlp_param_count(int D) { return D >= 1 ? mlp_shape(D).nparam : 0; }
+size_t prohd_mlp_state_bytes(int D) { return D >= 1 ? 3 * mlp_shape(D).nparam * sizeof(float) : 0; }
+size_t prohd_mlp_scratch_bytes(int D, int batch) {
+  return (D >= 1 && batch >= 1) ? mlp_scratch_floats(D, batch) * sizeof(float) + 256 : 0;
+}
+
+static prohd_status check_mlp(prohd_ctx* ctx, int D, int batch, int precision, const void* state, void* scratch,
+                              size_t scratch_bytes) {
+  if (!ctx) return PROHD_EINVAL;
+  if (D < 8 || D > 1024) return fail(ctx, PROHD_EINVAL, "the network needs 8 <= D <= 1024%s");
+  if (batch < 1 || batch > 65535) return fail(ctx, PROHD_EINVAL, "batch must be in [1, 65535]%s");
+  if (precision != PROHD_FP32 && precision != PROHD_BF16)
+    return fail(ctx, PROHD_EINVAL, "network precision is PROHD_FP32 or PROHD_BF16%s");
+  if (!state) return fail(ctx, PROHD_EINVAL, "null state%s");
+  if (scratch && ((reinterpret_cast<uintptr_t>(scratch) & 255) || scratch_bytes < prohd_mlp_scratch_bytes(D, batch)))
+    return fail(ctx, PROHD_ENOMEM, "scratch too small or misaligned%s");
+  if (!scratch) return fail(ctx, PROHD_EINVAL, "null scratch%s");
+  return PROHD_OK;
+}
+
+prohd_status prohd_mlp_init(prohd_ctx* ctx, int D, uint64_t seed, void* state, void* stream) {
+  if (!ctx) return PROHD_EINVAL;
+  if (D < 8 || D > 1024 || !state) return fail(ctx, PROHD_EINVAL, "bad network arguments%s");
+  cudaError_t e = mlp_init(mlp_shape(D), static_cast<float*>(state), seed, reinterpret_cast<cudaStream_t>(stream));
+  return e ? cuda_fail(ctx, e) : PROHD_OK;
+}
+
+prohd_status prohd_mlp_forward(prohd_ctx* ctx, int D, const void* state, const float* feat, int batch, int precision,
+                               float* dirs32, double* dirs64, void* scratch, size_t scratch_bytes, void* stream) {
+  prohd_status s = check_mlp(ctx, D, batch, precision, state, scratch, scratch_bytes);
+  if (s) return s;
+  if (!feat) return fail(ctx, PROHD_EINVAL, "null features%s");
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  const MlpShape sh = mlp_shape(D);
+  float* sc = static_cast<float*>(scratch);
+  cudaError_t e = mlp_forward(sh, static_cast<const float*>(state), feat, batch, precision, sc, nullptr, st);
+  const MlpActsView v = mlp_acts_view(D, batch, sc);
+  if (!e && dirs32)
+    e = cudaMemcpyAsync(dirs32, v.u, sizeof(float) * (size_t)batch * sh.n_out, cudaMemcpyDeviceToDevice, st);
+  if (!e && dirs64) e = mlp_dirs64(v.u, batch * 4, D, dirs64, st);
+  return e ? cuda_fail(ctx, e) : PROHD_OK;
+}
+
+prohd_status prohd_mlp_loss_grad(prohd_ctx* ctx, int D, const void* state, const float* feat, const float* label,
+                                 int batch, int precision, float* loss, float* grad, void* scratch,
+                                 size_t scratch_bytes, void* stream) {
+  prohd_status s = check_mlp(ctx, D, batch, precision, state, scratch, scratch_bytes);
+  if (s) return s;
+  if (!feat || !label) return fail(ctx, PROHD_EINVAL, "null features or labels%s");
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  const MlpShape sh = mlp_shape(D);
+  float* sc = static_cast<float*>(scratch);
+  const float* P = static_cast<const float*>(state);
+  cudaError_t e = mlp_forward(sh, P, feat, batch, precision, sc, label, st);
+  if (!e && grad) e = mlp_backward(sh, P, feat, batch, precision, sc, st);
+  const MlpActsView v = mlp_acts_view(D, batch, sc);
+  if (!e && loss) e = cudaMemcpyAsync(loss, v.lmean, sizeof(float), cudaMemcpyDeviceToDevice, st);
+  if (!e && grad) e = cudaMemcpyAsync(grad, v.grad, sizeof(float) * sh.nparam, cudaMemcpyDeviceToDevice, st);
+  return e ? cuda_fail(ctx, e) : PROHD_OK;
+}
+
+prohd_status prohd_mlp_train_step(prohd_ctx* ctx, int D, void* state, const float* feat, const float* label, int batch,
+                                  int precision, float lr, int64_t step, float* loss, void* scratch,
+                                  size_t scratch_bytes, void* stream) {
+  prohd_status s = check_mlp(ctx, D, batch, precision, state, scratch, scratch_bytes);
+  if (s) return s;
+  if (!feat || !label) return fail(ctx, PROHD_EINVAL, "null features or labels%s");
+  if (step < 1) return fail(ctx, PROHD_EINVAL, "step counts from 1%s");
+  if (!(lr > 0.f)) return fail(ctx, PROHD_EINVAL, "learning rate must be positive%s");
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  const MlpShape sh = mlp_shape(D);
+  float* sc = static_cast<float*>(scratch);
+  float* P = static_cast<float*>(state);
+  cudaError_t e = mlp_forward(sh, P, feat, batch, precision, sc, label, st);
+  if (!e) e = mlp_backward(sh, P, feat, batch, precision, sc, st);
+  const MlpActsView v = mlp_acts_view(D, batch, sc);
+  if (!e) e = mlp_adam(sh, P, v.grad, lr, step, st);
+  if (!e && loss) e = cudaMemcpyAsync(loss, v.lmean, sizeof(float), cudaMemcpyDeviceToDevice, st);
+  return e ? cuda_fail(ctx, e) : PROHD_OK;
+}
+
+prohd_status prohd_mlp_adam_step(prohd_ctx* ctx, int D, void* state, const float* grad, float lr, int64_t step,
+                                 void* stream) {
+  if (!ctx) return PROHD_EINVAL;
+  if (D < 8 || D > 1024 || !state || !grad) return fail(ctx, PROHD_EINVAL, "bad network arguments%s");
+  if (step < 1) return fail(ctx, PROHD_EINVAL, "step counts from 1%s");
+  if (!(lr > 0.f)) return fail(ctx, PROHD_EINVAL, "learning rate must be positive%s");
+  cudaError_t e = mlp_adam(mlp_shape(D), static_cast<float*>(state), grad, lr, step,
+                           reinterpret_cast<cudaStream_t>(stream));
+  return e ? cuda_fail(ctx, e) : PROHD_OK;
 }
 
 uint64_t prohd_launch_count(void) { return g_launches.load(); }

@@ -778,4 +778,15 @@ cudaError_t directions_run(prohd_ctx* ctx, const float* A, int64_t nA, const flo
   return cudaSuccess;
 }
 
+cudaError_t directions_features(prohd_ctx* ctx, const float* A, int64_t nA, const float* B, int64_t nB, int D,
+                                int max_iters, double tol, uint64_t seed, double* dirs, double* eig, float* feat,
+                                int* status, Arena& ws, cudaStream_t st) {
+  Arena run = ws;
+  cudaError_t e = directions_run(ctx, A, nA, B, nB, D, 8, max_iters, tol, seed, dirs, eig, status, run, st);
+  if (e) return e;
+  DirBufs b;
+  dir_layout(ws, D, 8, b);  // the buffers directions_run just filled
+  return mlp_features(b.sumA, b.sumB, nA, nB, b.C64, dirs, eig, D, feat, st);
+}
+
 }  // namespace prohd

@@ -202,6 +202,36 @@ cudaError_t compact_gather_batched(const BPair* P, int npairs, int nblk_max, int
 cudaError_t hd_simt_batched(const BPair* P, const int* order, int npairs, int64_t* prefix, unsigned long long* ticket,
                             int num_sms, cudaStream_t st);
 
+// ---- learned directions (mlp.cu) ----
+// Parameter layout (FP32, offsets in floats, each block 64-aligned):
+// W1 [10D x 256], b1, W2 [256 x 256], b2, W3 [256 x 4D], b3. The training
+// state is params | Adam m | Adam v (3 * nparam floats).
+struct MlpShape {
+  int D, n_in, h, n_out;
+  size_t w1, b1, w2, b2, w3, b3, nparam;
+};
+MlpShape mlp_shape(int D);
+size_t mlp_scratch_floats(int D, int B);
+struct MlpActsView {
+  float *u, *loss, *lmean, *grad;
+};
+MlpActsView mlp_acts_view(int D, int B, float* scratch);
+cudaError_t mlp_init(const MlpShape& s, float* state, uint64_t seed, cudaStream_t st);
+// Forward pass of B samples; with labels W it also forms the loss and the
+// gradient of the head (kept in the scratch for mlp_backward).
+cudaError_t mlp_forward(const MlpShape& s, const float* P, const float* X, int B, int prec, float* scratch,
+                        const float* W, cudaStream_t st);
+cudaError_t mlp_backward(const MlpShape& s, const float* P, const float* X, int B, int prec, float* scratch,
+                         cudaStream_t st);
+cudaError_t mlp_adam(const MlpShape& s, float* state, const float* grad, float lr, int64_t step, cudaStream_t st);
+cudaError_t mlp_features(const double* sumA, const double* sumB, int64_t nA, int64_t nB, const double* C64,
+                         const double* dirs, const double* eig, int D, float* feat, cudaStream_t st);
+cudaError_t mlp_dirs64(const float* U, int count, int D, double* out, cudaStream_t st);
+// Directions (m = 8) and the network's input features of one pair.
+cudaError_t directions_features(prohd_ctx* ctx, const float* A, int64_t nA, const float* B, int64_t nB, int D,
+                                int max_iters, double tol, uint64_t seed, double* dirs, double* eig, float* feat,
+                                int* status, Arena& ws, cudaStream_t st);
+
 // ---- small utilities (api.cu) ----
 cudaError_t set_i64(int64_t* p, int64_t v, cudaStream_t st);
 cudaError_t zero_i32(int* p, int n, cudaStream_t st);

@@ -36,6 +36,9 @@ EXPORTS = [
     "prohd_batch_workspace_size", "prohd_batch_plan", "prohd_batch_destroy", "prohd_estimate_batched",
     "prohd_batch_use_graph", "prohd_batch_autotune", "prohd_batch_get_tunables", "prohd_batch_set_tunables",
     "prohd_batch_pair_outputs",
+    "prohd_estimate_dirs_workspace_size", "prohd_estimate_dirs", "prohd_features_workspace_size", "prohd_features",
+    "prohd_mlp_param_count", "prohd_mlp_state_bytes", "prohd_mlp_scratch_bytes", "prohd_mlp_init", "prohd_mlp_forward",
+    "prohd_mlp_loss_grad", "prohd_mlp_train_step", "prohd_mlp_adam_step",
 ]
 
 #: prohd_phase names, in enum order
@@ -141,6 +144,30 @@ def load_library(path: str = LIB_PATH):
         lib.prohd_batch_pair_outputs.argtypes = [vp, i32, ctypes.POINTER(vp), ctypes.POINTER(vp), ctypes.POINTER(vp),
                                                  ctypes.POINTER(vp)]
         lib.prohd_batch_pair_outputs.restype = i32
+        pi64 = ctypes.POINTER(ctypes.c_int64)
+        lib.prohd_estimate_dirs_workspace_size.argtypes = [i64, i64, i32, i32, pi64, pi64, i32]
+        lib.prohd_estimate_dirs_workspace_size.restype = sz
+        lib.prohd_estimate_dirs.argtypes = [vp, vp, i64, vp, i64, i32, pp, vp, i32, pi64, pi64, vp, vp, vp, vp, sz, vp]
+        lib.prohd_estimate_dirs.restype = i32
+        lib.prohd_features_workspace_size.argtypes = [i64, i64, i32]
+        lib.prohd_features_workspace_size.restype = sz
+        lib.prohd_features.argtypes = [vp, vp, i64, vp, i64, i32, pp, vp, vp, vp, vp, sz, vp]
+        lib.prohd_features.restype = i32
+        for f in ("prohd_mlp_param_count", "prohd_mlp_state_bytes"):
+            getattr(lib, f).argtypes = [i32]
+            getattr(lib, f).restype = sz
+        lib.prohd_mlp_scratch_bytes.argtypes = [i32, i32]
+        lib.prohd_mlp_scratch_bytes.restype = sz
+        lib.prohd_mlp_init.argtypes = [vp, i32, ctypes.c_uint64, vp, vp]
+        lib.prohd_mlp_init.restype = i32
+        lib.prohd_mlp_forward.argtypes = [vp, i32, vp, vp, i32, i32, vp, vp, vp, sz, vp]
+        lib.prohd_mlp_forward.restype = i32
+        lib.prohd_mlp_loss_grad.argtypes = [vp, i32, vp, vp, vp, i32, i32, vp, vp, vp, sz, vp]
+        lib.prohd_mlp_loss_grad.restype = i32
+        lib.prohd_mlp_train_step.argtypes = [vp, i32, vp, vp, vp, i32, i32, ctypes.c_float, i64, vp, vp, sz, vp]
+        lib.prohd_mlp_train_step.restype = i32
+        lib.prohd_mlp_adam_step.argtypes = [vp, i32, vp, vp, ctypes.c_float, i64, vp]
+        lib.prohd_mlp_adam_step.restype = i32
         _lib = lib
         return lib
 
@@ -327,6 +354,46 @@ class Context:
         self._raise(rc, "prohd_estimate")
         return out
 
+    def prohd_estimate_dirs(self, A, B, dirs, kA, kB, params: Params | None = None, out=None, idxA=None, idxB=None,
+                            stream=None, **kw):
+        """Enqueues prohd_estimate_dirs (selection onwards with the given
+        directions dirs [nd, D] FP64 and k lists); returns the result buffer."""
+        torch = _torch()
+        _check_points(A, "A")
+        _check_points(B, "B")
+        p = params if params is not None else default_params(**kw)
+        D = A.shape[1]
+        dirs = dirs.to(device=A.device, dtype=torch.float64).contiguous()
+        nd = dirs.shape[0]
+        ka = (ctypes.c_int64 * nd)(*[int(k) for k in kA])
+        kb = (ctypes.c_int64 * nd)(*[int(k) for k in kB])
+        need = self.lib.prohd_estimate_dirs_workspace_size(A.shape[0], B.shape[0], D, nd, ka, kb, p.precision)
+        ws = self.workspace(need)
+        out = torch.empty(ctypes.sizeof(Result), dtype=torch.uint8, device=A.device) if out is None else out
+        rc = self.lib.prohd_estimate_dirs(self.h, _ptr(A), A.shape[0], _ptr(B), B.shape[0], D, ctypes.byref(p),
+                                          _ptr(dirs), nd, ka, kb, _ptr(out),
+                                          _ptr(idxA) if idxA is not None else None,
+                                          _ptr(idxB) if idxB is not None else None, _ptr(ws), ws.numel(),
+                                          self._stream(stream))
+        self._raise(rc, "prohd_estimate_dirs")
+        return out
+
+    def prohd_features(self, A, B, feat=None, dirs=None, eig=None, seed=0, stream=None):
+        """Network input features [10 D] (FP32), directions [9, D] and eig [8] of a pair."""
+        torch = _torch()
+        _check_points(A, "A")
+        _check_points(B, "B")
+        D = A.shape[1]
+        p = default_params(m=8, seed=seed)
+        feat = torch.empty(10 * D, dtype=torch.float32, device=A.device) if feat is None else feat
+        dirs = torch.empty((9, D), dtype=torch.float64, device=A.device) if dirs is None else dirs
+        eig = torch.empty(8, dtype=torch.float64, device=A.device) if eig is None else eig
+        ws = self.workspace(self.lib.prohd_features_workspace_size(A.shape[0], B.shape[0], D))
+        rc = self.lib.prohd_features(self.h, _ptr(A), A.shape[0], _ptr(B), B.shape[0], D, ctypes.byref(p), _ptr(feat),
+                                     _ptr(dirs), _ptr(eig), _ptr(ws), ws.numel(), self._stream(stream))
+        self._raise(rc, "prohd_features")
+        return feat, dirs, eig
+
     def prohd_estimate_host(self, A_host, B_host, params: Params | None = None, out_host=None, ws=None,
                             stream=None, **kw):
         """A_host, B_host: CPU float32 tensors (pinned for async copies). Returns
@@ -455,6 +522,124 @@ class Batch:
         ia = view(a.value, nsel_a, torch.int32, 4).cpu().numpy().astype(np.int64)
         ib = view(b.value, nsel_b, torch.int32, 4).cpu().numpy().astype(np.int64)
         return dirs, ia, ib
+
+
+class Mlp:
+    """The learned-direction network: FP32 state (params | Adam m | Adam v)
+    and a scratch buffer on the device; every computation runs in the
+    library's kernels."""
+
+    MAGIC = b"PHDMLP01"
+
+    def __init__(self, ctx: Context, D: int, seed: int = 0, device=None, init: bool = True):
+        torch = _torch()
+        self.ctx, self.D = ctx, int(D)
+        dev = device if device is not None else f"cuda:{ctx.device}"
+        self.nparam = int(ctx.lib.prohd_mlp_param_count(self.D))
+        self.state = torch.zeros(3 * self.nparam, dtype=torch.float32, device=dev)
+        self.step = 0
+        self._scratch = None
+        self._batch = 0
+        if init:
+            self.init(seed)
+
+    def init(self, seed: int, stream=None):
+        rc = self.ctx.lib.prohd_mlp_init(self.ctx.h, self.D, int(seed), _ptr(self.state), self.ctx._stream(stream))
+        self.ctx._raise(rc, "prohd_mlp_init")
+        self.step = 0
+
+    def scratch(self, batch: int):
+        torch = _torch()
+        need = int(self.ctx.lib.prohd_mlp_scratch_bytes(self.D, batch))
+        if self._scratch is None or self._scratch.numel() < need:
+            self._scratch = torch.empty(need, dtype=torch.uint8, device=self.state.device)
+        return self._scratch
+
+    @property
+    def params(self):
+        return self.state[: self.nparam]
+
+    def forward(self, feat, precision="bf16", want64=False, stream=None):
+        """Unit directions [B, 4, D] (FP32), and FP64 [B, 4, D] when want64."""
+        torch = _torch()
+        feat = feat.reshape(-1, 10 * self.D).contiguous()
+        B = feat.shape[0]
+        prec = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
+        u = torch.empty((B, 4, self.D), dtype=torch.float32, device=feat.device)
+        u64 = torch.empty((B, 4, self.D), dtype=torch.float64, device=feat.device) if want64 else None
+        sc = self.scratch(B)
+        rc = self.ctx.lib.prohd_mlp_forward(self.ctx.h, self.D, _ptr(self.state), _ptr(feat), B, prec, _ptr(u),
+                                            _ptr(u64) if want64 else None, _ptr(sc), sc.numel(),
+                                            self.ctx._stream(stream))
+        self.ctx._raise(rc, "prohd_mlp_forward")
+        return (u, u64) if want64 else u
+
+    def loss_grad(self, feat, label, precision="fp32", want_grad=True, stream=None):
+        torch = _torch()
+        feat = feat.reshape(-1, 10 * self.D).contiguous()
+        label = label.reshape(-1, self.D).contiguous()
+        B = feat.shape[0]
+        prec = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
+        loss = torch.empty(1, dtype=torch.float32, device=feat.device)
+        grad = torch.empty(self.nparam, dtype=torch.float32, device=feat.device) if want_grad else None
+        sc = self.scratch(B)
+        rc = self.ctx.lib.prohd_mlp_loss_grad(self.ctx.h, self.D, _ptr(self.state), _ptr(feat), _ptr(label), B, prec,
+                                              _ptr(loss), _ptr(grad) if want_grad else None, _ptr(sc), sc.numel(),
+                                              self.ctx._stream(stream))
+        self.ctx._raise(rc, "prohd_mlp_loss_grad")
+        return loss, grad
+
+    def train_step(self, feat, label, lr=1e-3, precision="bf16", loss=None, stream=None):
+        """One Adam step; returns the device loss (mean over the batch, before the step)."""
+        torch = _torch()
+        B = feat.shape[0]
+        prec = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
+        loss = torch.empty(1, dtype=torch.float32, device=feat.device) if loss is None else loss
+        sc = self.scratch(B)
+        self.step += 1
+        rc = self.ctx.lib.prohd_mlp_train_step(self.ctx.h, self.D, _ptr(self.state), _ptr(feat), _ptr(label), B, prec,
+                                               ctypes.c_float(lr), self.step, _ptr(loss), _ptr(sc), sc.numel(),
+                                               self.ctx._stream(stream))
+        self.ctx._raise(rc, "prohd_mlp_train_step")
+        return loss
+
+    def adam(self, grad, lr=1e-3, stream=None):
+        """One Adam step with a given gradient [param_count] (device FP32)."""
+        self.step += 1
+        rc = self.ctx.lib.prohd_mlp_adam_step(self.ctx.h, self.D, _ptr(self.state), _ptr(grad.contiguous()),
+                                              ctypes.c_float(lr), self.step, self.ctx._stream(stream))
+        self.ctx._raise(rc, "prohd_mlp_adam_step")
+
+    # ------------------------------------------------------------- checkpoints
+
+    def save(self, path: str, rng_state: bytes = b""):
+        """Versioned checkpoint: magic, D, step, parameter count, the host
+        RNG state of the training sampler, then params, Adam m, Adam v."""
+        import struct
+        body = self.state.detach().cpu().numpy().tobytes()
+        with open(path, "wb") as f:
+            f.write(self.MAGIC)
+            f.write(struct.pack("<iqqq", self.D, self.step, self.nparam, len(rng_state)))
+            f.write(rng_state)
+            f.write(body)
+
+    @classmethod
+    def load(cls, ctx: Context, path: str, device=None):
+        """Returns (network, rng_state)."""
+        import struct
+        torch = _torch()
+        with open(path, "rb") as f:
+            if f.read(8) != cls.MAGIC:
+                raise ValueError(f"{path}: not a network checkpoint of this version")
+            D, step, nparam, nrng = struct.unpack("<iqqq", f.read(28))
+            rng = f.read(nrng)
+            body = np.frombuffer(f.read(), dtype=np.float32)
+        net = cls(ctx, D, init=False, device=device)
+        if nparam != net.nparam or body.size != 3 * nparam:
+            raise ValueError(f"{path}: parameter count {nparam} does not match D = {D}")
+        net.state.copy_(torch.from_numpy(body.copy()))
+        net.step = step
+        return net, rng
 
 
 # ----------------------------------------------------------------- decoding

@@ -195,6 +195,43 @@ def student_t_mixture(n: int, D: int = 128, K: int = 8, nu: float = 3.0, seed: i
     return out
 
 
+def student_t_mixture_device(n: int, D: int = 128, K: int = 8, nu: float = 3.0, seed: int = 0,
+                             device: str = "cuda"):
+    """The law of ``student_t_mixture`` drawn with torch on the device
+    (component rotations from QR of Gaussian matrices, signs fixed by R's
+    diagonal): a float32 CUDA tensor [n, D]."""
+    import torch
+
+    g = torch.Generator(device=device)
+    g.manual_seed(int(seed))
+    lam = 1.0 / torch.arange(1, D + 1, dtype=torch.float64, device=device)
+    G = torch.randn(K, D, D, generator=g, device=device, dtype=torch.float64)
+    Q, R = torch.linalg.qr(G)
+    Q = Q * torch.sign(torch.diagonal(R, dim1=1, dim2=2))[:, None, :]
+    M = torch.sqrt(lam)[None, :, None] * Q.transpose(1, 2)          # [K, D, D]: x = z @ M_c
+    means = torch.randn(K, D, generator=g, device=device, dtype=torch.float64) * 2.0
+    comp = torch.randint(0, K, (n,), generator=g, device=device)
+    z = torch.randn(n, D, generator=g, device=device, dtype=torch.float64)
+    w = _chi2_torch(n, nu, g, device) / nu
+    x = torch.empty(n, D, dtype=torch.float64, device=device)
+    for c in range(K):
+        rows = torch.nonzero(comp == c, as_tuple=True)[0]
+        x[rows] = z[rows] @ M[c]
+    x = x / torch.sqrt(w)[:, None] + means[comp]
+    return x.to(torch.float32).contiguous()
+
+
+def _chi2_torch(n: int, nu: float, g, device):
+    """Chi-squared(nu) draws as the sum of nu squared normals (integer nu) or
+    a Gamma(nu/2, 2) draw otherwise."""
+    import torch
+
+    if float(nu).is_integer():
+        z = torch.randn(n, int(nu), generator=g, device=device, dtype=torch.float64)
+        return (z * z).sum(1)
+    return torch._standard_gamma(torch.full((n,), nu / 2.0, device=device, dtype=torch.float64)) * 2.0
+
+
 def subsample(X: np.ndarray, n: int, seed: int = 0) -> np.ndarray:
     """Seeded row subsample (without replacement), rows kept in index order."""
     if n >= X.shape[0]:
