@@ -87,9 +87,14 @@ def test_bf16_gradient_matches_oracle(D, B):
     G = omlp.backward(P, f)
     assert np.linalg.norm(u.cpu().numpy() - f["U"]) <= 2e-3 * np.linalg.norm(f["U"])
     assert abs(float(loss) - f["loss_mean"]) <= 1e-4
+    # Gradients: a flipped operand upstream can move a near-zero
+    # pre-activation across 0, and a flipped ReLU mask adds or removes a whole
+    # term of a B-term weight-gradient sum (about 1/sqrt(B) of its column);
+    # measured 3.8% normwise on W2 at B = 64. A wrong fragment layout or
+    # stride would be O(1).
     Gg = omlp.unflatten(grad.double().cpu().numpy(), D)
     for k in G:
-        assert np.linalg.norm(Gg[k] - G[k]) <= 1e-2 * np.linalg.norm(G[k]) + 1e-12, k
+        assert np.linalg.norm(Gg[k] - G[k]) <= 5e-2 * np.linalg.norm(G[k]) + 1e-12, k
     # and the BF16 path stays near the FP64 network (operand rounding only)
     f64 = omlp.forward(P, X.astype(np.float64), Wl.astype(np.float64))
     assert np.linalg.norm(u.cpu().numpy() - f64["U"]) <= 3e-2 * np.linalg.norm(f64["U"])
