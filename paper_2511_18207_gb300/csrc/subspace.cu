@@ -58,7 +58,8 @@ template <int NC, int ROWS, int VLD>
 struct SiSmemT {
   float Vt[kSiMaxB * VLD];                 // basis, transposed: column j of V at Vt[j * VLD], zero padded
   float Cl[NC > 1 ? ROWS * kSiMaxD : 4];   // this CTA's rows of C (cluster only), row stride Dq, zero padded
-  float Cst[NC > 1 ? 4 : 2 * 32 * ROWS];   // one CTA: C streamed in 32-row chunks, double-buffered
+  float Cst[NC > 1 ? 4 : 2 * 16 * ROWS];   // one CTA: C streamed in 16-row chunks, double-buffered
+  float Vn[NC > 1 ? 4 : ROWS * kSiMaxB];   // one CTA: V row-major [k][j], columns past b zero
   float W[ROWS * kSiMaxB];           // C V, local rows
   float Vr[ROWS * kSiMaxB];          // Ritz vectors V Y, local rows
   float Wr[ROWS * kSiMaxB];          // W Y -> scaled block -> Q1 -> Q
@@ -344,19 +345,34 @@ PROHD_DEV void si_chol_inv(SM& S, int b, int lane) {
 // dst (local rows) = src L^{-T}: dst[i][j] = sum_{k <= j} src[i][k] Linv[j][k].
 template <int ROWS, class SM>
 PROHD_DEV void si_apply_linv(SM& S, const float* src, float* dst, int nr, int b) {
-  for (int o = threadIdx.x; o < ROWS * kSiMaxB; o += kSiThreads) {
-    const int i = o >> 5, j = o & 31;
-    if (i < nr && j < b) {
-      float v = 0.f;
-      for (int kk = 0; kk <= j; ++kk) v = fmaf(src[i * b + kk], S.L[j * kSiLd + kk], v);
-      dst[i * b + j] = v;
-    }
+  (void)ROWS;
+  for (int o = threadIdx.x; o < nr * b; o += kSiThreads) {
+    const int i = o / b, j = o - i * b;
+    float v = 0.f;
+    for (int kk = 0; kk <= j; ++kk) v = fmaf(src[i * b + kk], S.L[j * kSiLd + kk], v);
+    dst[i * b + j] = v;
   }
 }
 
 // part[j*b + k] = sum_i src[i][j] src[i][k] over local rows.
+// With many local rows (one CTA holding all D rows) and b <= 16 the rows are
+// split in four quarters summed by separate threads into `scratch`
+// ([4][b * b]) and combined in a fixed order.
 template <class SM>
-PROHD_DEV void si_local_gram(SM& S, const float* src, int nr, int b) {
+PROHD_DEV void si_local_gram(SM& S, const float* src, int nr, int b, float* scratch) {
+  if (scratch && b <= 16 && nr > 64) {
+    const int bb = b * b, q4 = (nr + 3) >> 2;
+    for (int t = threadIdx.x; t < 4 * bb; t += kSiThreads) {
+      const int q = t / bb, e = t - q * bb, j = e / b, k = e - j * b;
+      float s = 0.f;
+      for (int i = q * q4; i < min(nr, (q + 1) * q4); ++i) s = fmaf(src[i * b + j], src[i * b + k], s);
+      scratch[t] = s;
+    }
+    __syncthreads();
+    for (int e = threadIdx.x; e < bb; e += kSiThreads)
+      S.part[e] = (scratch[e] + scratch[bb + e]) + (scratch[2 * bb + e] + scratch[3 * bb + e]);
+    return;
+  }
   for (int e = threadIdx.x; e < kSiMaxB * kSiMaxB; e += kSiThreads) {
     const int j = e >> 5, k = e & 31;
     if (j < b && k < b) {
@@ -372,7 +388,8 @@ PROHD_DEV void si_local_gram(SM& S, const float* src, int nr, int b) {
 // Gram into S.M and the extra values into S.res.
 template <int NC, class SM>
 PROHD_DEV void si_cholqr_pass(SM& S, const float* src, int nr, int b, uint32_t rank, int& xb, int n_extra) {
-  si_local_gram(S, src, nr, b);
+  // one CTA: the idle exchange buffer is scratch (no other CTA writes it)
+  si_local_gram(S, src, nr, b, NC == 1 ? &S.X[xb ^ 1][0][0] : nullptr);
   __syncthreads();
   si_broadcast<NC>(S, xb, rank, b * b + n_extra);
   si_sync<NC>();
@@ -409,6 +426,8 @@ PROHD_DEV void subspace_body(SiSmemT<NC, ROWS, VLD>& S, const float* __restrict_
     const int j = e / Dq, i = e - j * Dq;
     S.Vt[j * VLD + i] = i < D ? (float)splitmix64_unit(seed, (uint64_t)(j + 1), (uint64_t)i) : 0.f;
   }
+  if constexpr (NC == 1)
+    for (int e = tid; e < ROWS * kSiMaxB; e += kSiThreads) S.Vn[e] = 0.f;
   __syncthreads();
   si_sync<NC>();
 
@@ -471,22 +490,41 @@ PROHD_DEV void subspace_body(SiSmemT<NC, ROWS, VLD>& S, const float* __restrict_
           const int i = o / b, j = o - i * b;
           S.W[o] = cv_row(S.Cl + i * Dq, j);
         }
+      } else if (b > 16) {
+        // (b > 16, m > 8): one output per thread and step, C rows from L2
+        for (int o = tid; o < nr * b; o += kSiThreads) {
+          const int i = o / b, j = o - i * b;
+          S.W[o] = cv_row(C32 + (size_t)i * D, j);
+        }
       } else {
-        // C streams from global memory (L2) through two 32-row shared
-        // buffers by cp.async, the next chunk in flight while this one is used
+        // C streams from global memory (L2) through two 16-row shared
+        // buffers by cp.async, the next chunk in flight while this one is
+        // used. C is symmetric, so chunk c (rows 16c..16c+15) holds the k
+        // terms 16c..16c+15 of every output W[i][j] = sum_k C[k][i] V[k][j].
+        // A thread owns a 2 x 4 block (rows i0, i0 + 1; columns 4g..4g+3)
+        // and per k loads one float2 of C and one float4 of V: eight FMAs
+        // per 24 bytes of shared memory instead of one per 8. Each 8-term
+        // FMA block is added to the output by TwoSum.
         const int n4 = Dq >> 2;
-        const int nchunk = (D + 31) >> 5;
+        const int nchunk = (D + 15) >> 4;
         auto issue = [&](int c) {
-          float* dst = S.Cst + (c & 1) * 32 * ROWS;
-          const int rows = min(32, D - c * 32);
+          float* dst = S.Cst + (c & 1) * 16 * ROWS;
+          const int rows = min(16, D - c * 16);
           for (int e = tid; e < rows * n4; e += kSiThreads) {
             const int i = e / n4, k4 = e - i * n4;
             const uint32_t sa = smem_u32(dst + i * Dq + 4 * k4);
-            const float* gp = C32 + (size_t)(c * 32 + i) * D + 4 * k4;
+            const float* gp = C32 + (size_t)(c * 16 + i) * D + 4 * k4;
             asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(sa), "l"(gp) : "memory");
           }
           asm volatile("cp.async.commit_group;" ::: "memory");
         };
+        const int gj = (b + 3) >> 2;
+        const int ntask = (D >> 1) * gj;
+        const bool act = tid < ntask;
+        const int i0 = act ? 2 * (tid / gj) : 0, g = act ? tid % gj : 0;
+        float sa[8], sc[8];
+#pragma unroll
+        for (int o = 0; o < 8; ++o) sa[o] = sc[o] = 0.f;
         issue(0);
         for (int c = 0; c < nchunk; ++c) {
           if (c + 1 < nchunk) {
@@ -496,23 +534,67 @@ PROHD_DEV void subspace_body(SiSmemT<NC, ROWS, VLD>& S, const float* __restrict_
             asm volatile("cp.async.wait_group 0;" ::: "memory");
           }
           __syncthreads();
-          const float* cb = S.Cst + (c & 1) * 32 * ROWS;
-          const int rows = min(32, D - c * 32);
-          for (int o = tid; o < rows * b; o += kSiThreads) {
-            const int i = o / b, j = o - i * b;
-            S.W[(c * 32 + i) * b + j] = cv_row(cb + i * Dq, j);
+          const float* cb = S.Cst + (c & 1) * 16 * ROWS;
+          const int kn = min(16, D - c * 16);
+          if (act) {
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+              float pb[8];
+#pragma unroll
+              for (int o = 0; o < 8; ++o) pb[o] = 0.f;
+              if (h * 8 < kn) {
+#pragma unroll
+                for (int kk = 0; kk < 8; ++kk) {
+                  const int k = h * 8 + kk;
+                  if (k >= kn) break;  // the last chunk may hold 4, 8 or 12 rows
+                  const float2 cv = *reinterpret_cast<const float2*>(cb + k * Dq + i0);
+                  const float4 v = *reinterpret_cast<const float4*>(S.Vn + (c * 16 + k) * kSiMaxB + 4 * g);
+                  pb[0] = fmaf(cv.x, v.x, pb[0]);
+                  pb[1] = fmaf(cv.x, v.y, pb[1]);
+                  pb[2] = fmaf(cv.x, v.z, pb[2]);
+                  pb[3] = fmaf(cv.x, v.w, pb[3]);
+                  pb[4] = fmaf(cv.y, v.x, pb[4]);
+                  pb[5] = fmaf(cv.y, v.y, pb[5]);
+                  pb[6] = fmaf(cv.y, v.z, pb[6]);
+                  pb[7] = fmaf(cv.y, v.w, pb[7]);
+                }
+#pragma unroll
+                for (int o = 0; o < 8; ++o) two_sum_acc(sa[o], sc[o], pb[o]);
+              }
+            }
           }
           __syncthreads();  // the buffer is refilled two chunks later
+        }
+        if (act) {
+#pragma unroll
+          for (int o = 0; o < 8; ++o) {
+            const int i = i0 + (o >> 2), j = 4 * g + (o & 3);
+            if (j < b) S.W[i * b + j] = sa[o] + sc[o];
+          }
         }
       }
       __syncthreads();
       // ---- H = V^T W (local rows), exchanged
-      for (int e = tid; e < kSiMaxB * kSiMaxB; e += kSiThreads) {
-        const int j = e >> 5, k = e & 31;
-        if (j < b && k < b) {
+      if (NC == 1 && b <= 16 && nr > 64) {
+        // rows split in quarters (see si_local_gram), the idle exchange buffer as scratch
+        float* scr = &S.X[xb ^ 1][0][0];
+        const int bb = b * b, q4 = (nr + 3) >> 2;
+        for (int t2 = tid; t2 < 4 * bb; t2 += kSiThreads) {
+          const int q = t2 / bb, e = t2 - q * bb, j = e / b, k = e - j * b;
           float s = 0.f;
-          for (int i = 0; i < nr; ++i) s = fmaf(S.Vt[j * VLD + r0 + i], S.W[i * b + k], s);
-          S.part[j * b + k] = s;
+          for (int i = q * q4; i < min(nr, (q + 1) * q4); ++i) s = fmaf(S.Vt[j * VLD + r0 + i], S.W[i * b + k], s);
+          scr[t2] = s;
+        }
+        __syncthreads();
+        for (int e = tid; e < bb; e += kSiThreads) S.part[e] = (scr[e] + scr[bb + e]) + (scr[2 * bb + e] + scr[3 * bb + e]);
+      } else {
+        for (int e = tid; e < kSiMaxB * kSiMaxB; e += kSiThreads) {
+          const int j = e >> 5, k = e & 31;
+          if (j < b && k < b) {
+            float s = 0.f;
+            for (int i = 0; i < nr; ++i) s = fmaf(S.Vt[j * VLD + r0 + i], S.W[i * b + k], s);
+            S.part[j * b + k] = s;
+          }
         }
       }
       __syncthreads();
@@ -529,40 +611,50 @@ PROHD_DEV void subspace_body(SiSmemT<NC, ROWS, VLD>& S, const float* __restrict_
       __syncthreads();
       const float th0 = fmaxf(S.theta[0], 0.f);
       const float sigma = sigma_rel * th0;
-      for (int o = tid; o < ROWS * kSiMaxB; o += kSiThreads) {
-        const int i = o >> 5, j = o & 31;
-        if (i < nr && j < b) {
-          const int col = min(max(S.perm[j], 0), b - 1);
-          float v = 0.f, w = 0.f;
-          for (int kk = 0; kk < b; ++kk) {
-            const float y = S.Y[kk * kSiLd + col];
-            v = fmaf(S.Vt[kk * VLD + r0 + i], y, v);
-            w = fmaf(S.W[i * b + kk], y, w);
-          }
-          S.Vr[i * b + j] = v;
-          S.Wr[i * b + j] = w;
+      for (int o = tid; o < nr * b; o += kSiThreads) {
+        const int i = o / b, j = o - i * b;
+        const int col = min(max(S.perm[j], 0), b - 1);
+        float v = 0.f, w = 0.f;
+        for (int kk = 0; kk < b; ++kk) {
+          const float y = S.Y[kk * kSiLd + col];
+          v = fmaf(S.Vt[kk * VLD + r0 + i], y, v);
+          w = fmaf(S.W[i * b + kk], y, w);
         }
+        S.Vr[i * b + j] = v;
+        S.Wr[i * b + j] = w;
       }
       __syncthreads();
       // residual partials of the m leading pairs, then the scaled block
       // (C x_j + sigma x_j) / (theta_j + sigma)
-      for (int j = tid; j < b; j += kSiThreads) {
-        float s = 0.f;
-        if (j < m)
-          for (int i = 0; i < nr; ++i) {
-            const float r = fmaf(-S.theta[j], S.Vr[i * b + j], S.Wr[i * b + j]);
-            s = fmaf(r, r, s);
-          }
-        S.part[b * b + j] = s;
+      if (NC == 1) {
+        // one warp per component, lanes over rows
+        for (int j = warp; j < b; j += kSiThreads / 32) {
+          float s = 0.f;
+          if (j < m)
+            for (int i = lane; i < nr; i += 32) {
+              const float r = fmaf(-S.theta[j], S.Vr[i * b + j], S.Wr[i * b + j]);
+              s = fmaf(r, r, s);
+            }
+          s = warp_sum(s);
+          if (lane == 0) S.part[b * b + j] = s;
+        }
+      } else {
+        for (int j = tid; j < b; j += kSiThreads) {
+          float s = 0.f;
+          if (j < m)
+            for (int i = 0; i < nr; ++i) {
+              const float r = fmaf(-S.theta[j], S.Vr[i * b + j], S.Wr[i * b + j]);
+              s = fmaf(r, r, s);
+            }
+          S.part[b * b + j] = s;
+        }
       }
       __syncthreads();  // the residuals read Wr before it is scaled in place
-      for (int o = tid; o < ROWS * kSiMaxB; o += kSiThreads) {
-        const int i = o >> 5, j = o & 31;
-        if (i < nr && j < b) {
-          const float den = fmaxf(S.theta[j], 0.f) + sigma;
-          const float w = S.Wr[i * b + j], v = S.Vr[i * b + j];
-          S.Wr[i * b + j] = den > 1e-30f ? (w + sigma * v) / den : v;
-        }
+      for (int o = tid; o < nr * b; o += kSiThreads) {
+        const int i = o / b, j = o - i * b;
+        const float den = fmaxf(S.theta[j], 0.f) + sigma;
+        const float w = S.Wr[i * b + j], v = S.Vr[i * b + j];
+        S.Wr[i * b + j] = den > 1e-30f ? (w + sigma * v) / den : v;
       }
       __syncthreads();
       // ---- first Cholesky-QR exchange, carrying the residuals
@@ -618,8 +710,10 @@ PROHD_DEV void subspace_body(SiSmemT<NC, ROWS, VLD>& S, const float* __restrict_
       const int i = o / b, j = o - i * b;
       if constexpr (NC > 1)
         st_cluster_f32(map_to_cta(&S.Vt[j * VLD + r0 + i], (uint32_t)c), Q[o]);
-      else
+      else {
         S.Vt[j * VLD + r0 + i] = Q[o];
+        S.Vn[(r0 + i) * kSiMaxB + j] = Q[o];
+      }
     }
     si_sync<NC>();
   }
