@@ -202,6 +202,35 @@ def oracle_sample(A, B, rows_cov: int = 200_000, rows_hd: int = 256) -> dict:
 
 # ---------------------------------------------------------------- GPU arm
 
+def part_arm(args):
+    """One of the secondary measurements alone (--workload batched|learned):
+    a JSON line of its own, the sub-object's figures under the line's keys."""
+    import torch
+
+    rank, world, local = dist_info()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    dist = dist_init(world, True)
+    peaks, peak_src = load_peaks()
+    if args.workload == "batched":
+        r = batched_arm(args, peaks, peak_src, dist, dev)
+        line = {"metric": "batched ProHD set-pairs/s (512 uneven pairs)", "value": world * r["value"],
+                "unit": "set-pairs/s", "n_gpus": world, "steps": r["steps"], "warmup": args.warmup,
+                "ms_per_step": r["ms_per_batch"], "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+                "dtype": "f32", "data": "synthetic", "config": {"workload": r["workload"]}, "batched": r}
+    else:
+        r = learned_arm(args, peaks, dev) if rank == 0 else None
+        line = None if r is None else {
+            "metric": "learned-direction training samples/s (batch 256, D = 128)", "value": r["samples_per_s"],
+            "unit": "samples/s", "n_gpus": world, "steps": r["steps"], "warmup": args.warmup,
+            "ms_per_step": r["ms_per_step"], "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "bf16", "data": "synthetic", "config": {"workload": r["workload"]}, "learned": r}
+    if rank == 0 and line is not None:
+        print(json.dumps(line))
+    if dist is not None:
+        dist.destroy_process_group()
+
+
 def gpu_arm(args):
     import numpy as np
     import torch
@@ -611,11 +640,16 @@ def main():
     ap.add_argument("--learned-pairs", type=int, default=1024)
     ap.add_argument("--learned-steps", type=int, default=1000)
     ap.add_argument("--learned-eval", type=int, default=8)
+    ap.add_argument("--workload", choices=["pair", "batched", "learned"], default="pair",
+                    help="pair: the 2M x 2M headline line (with the batch and learned objects); "
+                         "batched / learned: only that measurement, on a line of its own")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
     if args.impl == "reference":
         reference_arm(args)
+    elif args.workload != "pair":
+        part_arm(args)
     else:
         gpu_arm(args)
 

@@ -39,10 +39,14 @@ constexpr int kFewRows = 64;
 // Persistent tile loop over rows of X (optionally a list of row ids) against
 // all rows of Y. WANT_ROW: rowbest[out_row] = min (d^2, j); WANT_COL:
 // colbest[j] = min (d^2, row id). Packed values are (float bits << 32 | idx).
+// Two k-stages of the operand tiles; the column-minimum scratch reuses them
+// after the k-loop (a barrier separates the last reads from its writes).
 template <bool WANT_COL>
-struct SimtSmem {
-  __align__(16) float As[kSimtBK][kSimtBM + 4];
-  __align__(16) float Bs[kSimtBK][kSimtBN + 4];
+union SimtSmem {
+  struct {
+    __align__(16) float As[2][kSimtBK][kSimtBM + 4];
+    __align__(16) float Bs[2][kSimtBK][kSimtBN + 4];
+  } t;
   unsigned long long s_col[WANT_COL ? 16 : 1][WANT_COL ? kSimtBN : 1];
 };
 
@@ -53,8 +57,8 @@ __device__ __forceinline__ void simt_tile(SimtSmem<WANT_COL>& sm, const float* _
                                           const float* __restrict__ Y, int64_t ncols, int D,
                                           unsigned long long* __restrict__ rowbest,
                                           unsigned long long* __restrict__ colbest, int64_t rt, int64_t ct) {
-  auto& As = sm.As;
-  auto& Bs = sm.Bs;
+  auto& As = sm.t.As;
+  auto& Bs = sm.t.Bs;
   auto& s_col = sm.s_col;
   const int tid = threadIdx.x, ty = tid >> 4, tx = tid & 15;
   const int lr = tid >> 1, koff = (tid & 1) * 8;
@@ -71,27 +75,37 @@ __device__ __forceinline__ void simt_tile(SimtSmem<WANT_COL>& sm, const float* _
 #pragma unroll
       for (int j = 0; j < 8; ++j) acc[i][j] = 0.f;
 
-    for (int k0 = 0; k0 < D; k0 += kSimtBK) {
-      float xa[8], yb[8];
+    // double-buffered k-steps: the next step's global loads are in flight
+    // (in registers) while this step's tiles are used; one barrier per step
+    float xa[8], yb[8];
+    auto load = [&](int k0) {
 #pragma unroll
       for (int e = 0; e < 8; ++e) {
-        int k = k0 + koff + e;
+        const int k = k0 + koff + e;
         xa[e] = (vx && k < D) ? __ldg(xrow + k) : 0.f;
         yb[e] = (vy && k < D) ? __ldg(yrow + k) : 0.f;
       }
-      __syncthreads();
+    };
+    auto store = [&](int stg) {
 #pragma unroll
       for (int e = 0; e < 8; ++e) {
-        As[koff + e][lr] = xa[e];
-        Bs[koff + e][lr] = yb[e];
+        As[stg][koff + e][lr] = xa[e];
+        Bs[stg][koff + e][lr] = yb[e];
       }
-      __syncthreads();
+    };
+    load(0);
+    __syncthreads();  // the previous tile's readers of stage 0 (and of the column scratch) are done
+    store(0);
+    __syncthreads();
+    for (int k0 = 0, stg = 0; k0 < D; k0 += kSimtBK, stg ^= 1) {
+      const bool more = k0 + kSimtBK < D;
+      if (more) load(k0 + kSimtBK);
 #pragma unroll
       for (int kk = 0; kk < kSimtBK; ++kk) {
-        float4 a0 = *reinterpret_cast<const float4*>(&As[kk][ty * 4]);
-        float4 a1 = *reinterpret_cast<const float4*>(&As[kk][64 + ty * 4]);
-        float4 b0 = *reinterpret_cast<const float4*>(&Bs[kk][tx * 4]);
-        float4 b1 = *reinterpret_cast<const float4*>(&Bs[kk][64 + tx * 4]);
+        float4 a0 = *reinterpret_cast<const float4*>(&As[stg][kk][ty * 4]);
+        float4 a1 = *reinterpret_cast<const float4*>(&As[stg][kk][64 + ty * 4]);
+        float4 b0 = *reinterpret_cast<const float4*>(&Bs[stg][kk][tx * 4]);
+        float4 b1 = *reinterpret_cast<const float4*>(&Bs[stg][kk][64 + tx * 4]);
         float a[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
         float b[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
 #pragma unroll
@@ -102,6 +116,8 @@ __device__ __forceinline__ void simt_tile(SimtSmem<WANT_COL>& sm, const float* _
             acc[i][j] = fmaf(d, d, acc[i][j]);
           }
       }
+      if (more) store(stg ^ 1);
+      __syncthreads();
     }
 
     if (WANT_ROW) {
