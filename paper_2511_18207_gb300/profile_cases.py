@@ -1,0 +1,47 @@
+"""Small, fixed workloads for kernel profiling (``ncu``) of single kernels.
+
+    python -m paper_2511_18207_gb300.profile_cases directions   # Gram + block iteration, 400k + 400k x 256
+    python -m paper_2511_18207_gb300.profile_cases exact        # distance contraction, 100k x 100k x 256, FP16
+
+Each case runs its call twice (the second launch is the one to capture, e.g.
+``ncu -k regex:gram_tc_kernel -s 1 -c 1``), keeps the device footprint to a
+few hundred MB (inputs larger than L2), and prints a one-line result.
+"""
+from __future__ import annotations
+
+import sys
+
+
+def directions():
+    import torch
+
+    from . import prohd, workloads as W
+
+    A, B = W.anisotropic_pair(400_000, 400_000, 256, seed=1)
+    At, Bt = torch.from_numpy(A).cuda(), torch.from_numpy(B).cuda()
+    c = prohd.context()
+    for _ in range(2):
+        d, e = c.prohd_directions(At, Bt, m=8)
+    torch.cuda.synchronize()
+    print("eigenvalues", e.cpu().numpy()[:4])
+
+
+def exact():
+    import torch
+
+    from . import prohd, workloads as W
+
+    A, B = W.mixture_pair(100_000, 256, 16, seed=3)
+    At, Bt = torch.from_numpy(A).cuda(), torch.from_numpy(B).cuda()
+    r = None
+    for _ in range(2):
+        r = prohd.hausdorff_exact_sync(At, Bt, "fp16")
+    print("H", r["H"], r["status"])
+
+
+CASES = {"directions": directions, "exact": exact}
+
+if __name__ == "__main__":
+    if len(sys.argv) != 2 or sys.argv[1] not in CASES:
+        sys.exit(f"usage: python -m paper_2511_18207_gb300.profile_cases {{{'|'.join(CASES)}}}")
+    CASES[sys.argv[1]]()
