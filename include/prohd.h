@@ -266,8 +266,9 @@ uint64_t prohd_launch_count(void);
  *
  * Pairs: A, B device pointers, FP32 row-major, 16-byte aligned bases;
  * 1 <= nA, nB < 2^31; 4 <= D <= 256 with D % 4 == 0; 1 <= m <= min(24, D)
- * after resolving m < 0 to floor(sqrt(D)). The subset HD of a batch runs the
- * FP32 direct-difference path (params.precision is not used).
+ * after resolving m < 0 to floor(sqrt(D)). params.precision picks the subset
+ * HD as in prohd_estimate: PROHD_FP16 / PROHD_BF16 tensor-core tiles with the
+ * rigorous margin and FP32 rescoring, or PROHD_FP32 direct differences.
  */
 typedef struct {
   const float* A;

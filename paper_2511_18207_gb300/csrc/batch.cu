@@ -10,7 +10,10 @@
 //   CTA per pair, one launch per D class) -> FP64 clean-up + Rayleigh
 //   quotients -> projection (one block per item) -> radix select + band
 //   resolution (every (pair, set, direction) problem) -> compaction + gather
-//   -> subset HD (persistent, atomic ticket over 128 x 128 tiles) -> finalize.
+//   -> subset HD -> finalize. The subset HD runs either on the tensor cores
+//   (FP16/BF16 tiles over (pair, row block) items, margins, FP32 rescoring of
+//   the candidates) or as FP32 direct differences (persistent, atomic ticket
+//   over 128 x 128 tiles), as params.precision asks.
 // The sequence is captured once into a CUDA graph and replayed. Item sizes
 // (Gram points per item, projection rows per item, selection keys per
 // block) come from an autotuner that times candidates on the batch itself.
@@ -66,6 +69,8 @@ struct BatchLayout {
   size_t zero_bytes;
   char* ones_base;
   size_t ones_bytes;
+  unsigned* colmin_base;
+  int64_t colmin_count;
   int* gticket;
   unsigned long long* hticket;
   int* bstatus;
@@ -84,8 +89,8 @@ size_t item_slot_bytes(int N, int Dp) {
 int64_t items_for(int64_t n, int pts) { return ceil_div(n, pts); }
 
 // Upper bounds of the tables that depend on the tunables.
-void table_caps(const std::vector<PairPlan>& pp, int64_t& max_items, int64_t& max_pitems, size_t& slot_cap,
-                int& nmaps) {
+void table_caps(const std::vector<PairPlan>& pp, bool tensor, int64_t& max_items, int64_t& max_pitems,
+                size_t& slot_cap, int& nmaps) {
   max_items = 0;
   max_pitems = 0;
   slot_cap = 0;
@@ -100,15 +105,16 @@ void table_caps(const std::vector<PairPlan>& pp, int64_t& max_items, int64_t& ma
       nmaps += 2;
     }
     max_pitems += items_for(q.nA, kMinProjRows) + items_for(q.nB, kMinProjRows);
+    if (tensor) nmaps += 4;  // subset distance: A, B and their norm operands
   }
 }
 
-void batch_layout(Arena& a, const std::vector<PairPlan>& pp, const prohd_pair_desc* pairs, BatchLayout& L) {
+void batch_layout(Arena& a, const std::vector<PairPlan>& pp, const prohd_pair_desc* pairs, bool tensor, BatchLayout& L) {
   const int np = (int)pp.size();
   int64_t max_items, max_pitems;
   size_t slot_cap;
   int nmaps;
-  table_caps(pp, max_items, max_pitems, slot_cap, nmaps);
+  table_caps(pp, tensor, max_items, max_pitems, slot_cap, nmaps);
   int64_t nprob = 0;
   for (const auto& q : pp) nprob += 2 * q.nd;
 
@@ -161,6 +167,24 @@ void batch_layout(Arena& a, const std::vector<PairPlan>& pp, const prohd_pair_de
     b.offsets = a.take<int64_t>((size_t)b.nblkA + b.nblkB);
     b.As = a.take<float>((size_t)q.boundA * q.D);
     b.Bs = a.take<float>((size_t)q.boundB * q.D);
+    if (tensor) {
+      // tensor-core subset distance: 16-bit copies padded to whole tiles
+      b.hd_nA_pad = round_up(q.boundA, 128);
+      b.hd_nB_pad = round_up(q.boundB, 256);
+      b.hd_At = a.take<uint16_t>((size_t)b.hd_nA_pad * q.Dp, 1024);
+      b.hd_Bt = a.take<uint16_t>((size_t)b.hd_nB_pad * q.Dp, 1024);
+      b.hd_nA8 = a.take<float>((size_t)b.hd_nA_pad * 8, 1024);
+      b.hd_nB8 = a.take<float>((size_t)b.hd_nB_pad * 8, 1024);
+      b.hd_nA2 = a.take<float>((size_t)b.hd_nA_pad);
+      b.hd_nB2 = a.take<float>((size_t)b.hd_nB_pad);
+      b.hd_epsA = a.take<float>((size_t)b.hd_nA_pad);
+      b.hd_epsB = a.take<float>((size_t)b.hd_nB_pad);
+      b.hd_rowmin = a.take<float>((size_t)b.hd_nA_pad);
+      b.hd_candA = a.take<int32_t>((size_t)q.boundA);
+      b.hd_candB = a.take<int32_t>((size_t)q.boundB);
+      b.hd_shift = a.take<float>((size_t)q.D);
+      b.hd_spart = a.take<double>((size_t)16 * q.D);
+    }
   }
   // band lists (any size up to the set's)
   L.end = 0;
@@ -176,6 +200,7 @@ void batch_layout(Arena& a, const std::vector<PairPlan>& pp, const prohd_pair_de
     b.status = a.take<int>(1, 16);
     b.iters_out = a.take<int>(1, 16);
     b.maxnorm = a.take<float>(2, 16);
+    if (tensor) b.hd_sc = a.take<char>(hd_scalars_bytes(), 16);
   }
   for (int i = 0; i < np; ++i) {
     BPair& b = L.hp[i];
@@ -194,6 +219,12 @@ void batch_layout(Arena& a, const std::vector<PairPlan>& pp, const prohd_pair_de
   }
   a.off = round_up(a.off, 256);
   L.ones_bytes = a.off - o0;
+  // column minima of the contraction, +inf (as bits) every run
+  L.colmin_base = a.base ? reinterpret_cast<unsigned*>(a.base + a.off) : nullptr;
+  const size_t c0 = a.off;
+  if (tensor)
+    for (int i = 0; i < np; ++i) L.hp[i].hd_colmin = a.take<unsigned>((size_t)L.hp[i].hd_nB_pad, 4);
+  L.colmin_count = (int64_t)((a.off - c0) / sizeof(unsigned));
 }
 
 // Band lists per selection problem and side, n entries each (a band can hold
@@ -225,6 +256,8 @@ prohd_status check_batch(prohd_ctx* ctx, const prohd_pair_desc* pairs, int npair
   if (p->alpha_p >= 0.0 && !(p->alpha_p > 0.0 && p->alpha_p < 1.0))
     return bfail(ctx, PROHD_EINVAL, "alpha_p must be in (0, 1) or negative for alpha_c / m");
   if (p->power_max_iters < 1) return bfail(ctx, PROHD_EINVAL, "power_max_iters must be >= 1");
+  if (p->precision != PROHD_FP32 && p->precision != PROHD_FP16 && p->precision != PROHD_BF16)
+    return bfail(ctx, PROHD_EINVAL, "unknown precision");
   pp.resize((size_t)npairs);
   int64_t nprob = 0;
   for (int i = 0; i < npairs; ++i) {
@@ -294,6 +327,7 @@ struct prohd_batch {
   int Dmax = 0, ndmax = 0, mmax = 0, nblk_max = 0;
   int64_t nmax = 0;
   int grid_gram = 0;
+  bool tensor = false;  // subset HD on the tensor-core path (FP16 / BF16)
   // side streams and events of the fork-join around the block iteration
   cudaStream_t side[2] = {nullptr, nullptr};
   cudaEvent_t ev_fork = nullptr, ev_join[2] = {nullptr, nullptr};
@@ -332,6 +366,25 @@ prohd_status write_tables(prohd_batch* b) {
         map_of[(size_t)i * 4 + t * 2 + set] = (int)maps.size();
         maps.push_back(m);
       }
+  }
+  // ---- subset-distance maps (tensor path): A, B tiles and their norm operands
+  if (b->tensor) {
+    const CUtensorMapDataType dt =
+        b->p.precision == PROHD_BF16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT16;
+    for (int i = 0; i < np; ++i) {
+      BPair& q = L.hp[i];
+      CUtensorMap m[4];
+      const uint64_t Dp = (uint64_t)q.Dp;
+      if (!encode_2d(ctx, &m[0], dt, q.hd_At, Dp, (uint64_t)q.hd_nA_pad, Dp * 2, 64, 128, CU_TENSOR_MAP_SWIZZLE_128B) ||
+          !encode_2d(ctx, &m[1], dt, q.hd_Bt, Dp, (uint64_t)q.hd_nB_pad, Dp * 2, 64, 256, CU_TENSOR_MAP_SWIZZLE_128B) ||
+          !encode_2d(ctx, &m[2], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, q.hd_nA8, 8, (uint64_t)q.hd_nA_pad, 32, 8, 128,
+                     CU_TENSOR_MAP_SWIZZLE_32B) ||
+          !encode_2d(ctx, &m[3], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, q.hd_nB8, 8, (uint64_t)q.hd_nB_pad, 32, 8, 256,
+                     CU_TENSOR_MAP_SWIZZLE_32B))
+        return bfail(ctx, PROHD_ECUDA, "tensor-map encoding failed for a batched subset");
+      q.hd_map = (int)maps.size();
+      for (int k = 0; k < 4; ++k) maps.push_back(m[k]);
+    }
   }
   // ---- Gram items, largest first; the id list groups each pair's items by type
   struct HItem {
@@ -548,17 +601,24 @@ cudaError_t enqueue(prohd_batch* b, prohd_result* out, cudaStream_t st) {
   }
   {
     PhaseTimer pt(ctx, PROHD_PH_HD_CONTRACT, st);
-    if ((e = hd_simt_batched(L.P, L.order, np, L.prefix, L.hticket, ctx->num_sms, st))) return e;
+    if (b->tensor) {
+      if ((e = fill_u32_region(L.colmin_base, L.colmin_count, 0x7f800000u, ctx->num_sms, st))) return e;
+      if ((e = hd_tc_batched(L.P, L.order, np, L.prefix, L.maps, b->Dmax, b->p.precision == PROHD_BF16 ? 1 : 0,
+                             L.bstatus, ctx->num_sms, b->p.wait_timeout_ns, st)))
+        return e;
+    } else if ((e = hd_simt_batched(L.P, L.order, np, L.prefix, L.hticket, ctx->num_sms, st))) {
+      return e;
+    }
   }
   count_launch();
   finish_batched_kernel<<<(np + 255) / 256, 256, 0, st>>>(L.P, np, L.bstatus);
   return cudaGetLastError();
 }
 
-size_t batch_bytes(const std::vector<PairPlan>& pp) {
+size_t batch_bytes(const std::vector<PairPlan>& pp, bool tensor) {
   Arena a;
   BatchLayout L;
-  batch_layout(a, pp, nullptr, L);
+  batch_layout(a, pp, nullptr, tensor, L);
   std::vector<int32_t*> band;
   std::vector<uint64_t*> bkey;
   band_layout(a, pp, band, bkey);
@@ -572,7 +632,7 @@ extern "C" {
 size_t prohd_batch_workspace_size(const prohd_pair_desc* pairs, int npairs, const prohd_params* p) {
   std::vector<PairPlan> pp;
   if (check_batch(nullptr, pairs, npairs, p, pp) != PROHD_OK) return 0;
-  return batch_bytes(pp);
+  return batch_bytes(pp, p->precision != PROHD_FP32);
 }
 
 prohd_status prohd_batch_plan(prohd_ctx* ctx, const prohd_pair_desc* pairs, int npairs, const prohd_params* p,
@@ -585,7 +645,8 @@ prohd_status prohd_batch_plan(prohd_ctx* ctx, const prohd_pair_desc* pairs, int 
   if (!ctx->encode_tiled) return bfail(ctx, PROHD_ENOTSUP, "driver has no tensor-map encoder");
   if (ctx->num_sms > kMaxSms) return bfail(ctx, PROHD_ENOTSUP, "more SMs than this build sizes for");
   if (!ws || (reinterpret_cast<uintptr_t>(ws) & 255)) return bfail(ctx, PROHD_EINVAL, "workspace must be 256-byte aligned");
-  if (ws_bytes < batch_bytes(pp)) return bfail(ctx, PROHD_ENOMEM, "workspace too small for the batch");
+  const bool tensor = p->precision != PROHD_FP32;
+  if (ws_bytes < batch_bytes(pp, tensor)) return bfail(ctx, PROHD_ENOMEM, "workspace too small for the batch");
   prohd_batch* b = new (std::nothrow) prohd_batch();
   if (!b) return PROHD_ENOMEM;
   b->ctx = ctx;
@@ -599,7 +660,8 @@ prohd_status prohd_batch_plan(prohd_ctx* ctx, const prohd_pair_desc* pairs, int 
   Arena a;
   a.base = b->ws;
   a.cap = ws_bytes;
-  batch_layout(a, pp, pairs, b->L);
+  b->tensor = tensor;
+  batch_layout(a, pp, pairs, tensor, b->L);
   b->L.end = a.off;
   for (const auto& q : pp) {
     b->Dmax = std::max(b->Dmax, q.D);

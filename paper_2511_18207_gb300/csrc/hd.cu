@@ -204,10 +204,10 @@ __global__ void __launch_bounds__(256, 1)
 // the FP32 direct-difference squared distance to every candidate, keeping
 // per candidate the minimum packed (d^2, j). rowbest is indexed by position
 // in the list, as in the tiled kernel.
-__global__ void __launch_bounds__(256)
-    rescore_few_kernel(const float* __restrict__ X, const int32_t* __restrict__ rowlist,
-                       const int64_t* __restrict__ nrows_dev, const float* __restrict__ Y,
-                       const int64_t* __restrict__ ncols_dev, int D, unsigned long long* __restrict__ rowbest) {
+__device__ __forceinline__ void rescore_few_body(const float* __restrict__ X, const int32_t* __restrict__ rowlist,
+                                                 const int64_t* __restrict__ nrows_dev, const float* __restrict__ Y,
+                                                 const int64_t* __restrict__ ncols_dev, int D,
+                                                 unsigned long long* __restrict__ rowbest) {
   extern __shared__ __align__(16) float few_sm[];
   const int64_t nrows = *nrows_dev, ncols = *ncols_dev;
   if (nrows <= 0 || nrows > kFewRows) return;
@@ -257,6 +257,13 @@ __global__ void __launch_bounds__(256)
   }
 }
 
+__global__ void __launch_bounds__(256)
+    rescore_few_kernel(const float* __restrict__ X, const int32_t* __restrict__ rowlist,
+                       const int64_t* __restrict__ nrows_dev, const float* __restrict__ Y,
+                       const int64_t* __restrict__ ncols_dev, int D, unsigned long long* __restrict__ rowbest) {
+  rescore_few_body(X, rowlist, nrows_dev, Y, ncols_dev, D, rowbest);
+}
+
 __global__ void fill_u64_kernel(unsigned long long* p, int64_t n, unsigned long long v) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
     p[i] = v;
@@ -274,10 +281,10 @@ __global__ void fill_u32_kernel(unsigned* p, int64_t n, unsigned v) {
 // common origin that keeps ||a - s|| small; distances do not depend on it.
 // Stage 1: column sums of 256-row slices, grid (ceil(D/32), 8, 2 sets);
 // stage 2 sums the slices in order. Row counts are read on the device.
-__global__ void hd_colsum_kernel(const float* __restrict__ A, const int64_t* nA_dev, const float* __restrict__ B,
-                                 const int64_t* nB_dev, int D, double* __restrict__ part /*[2][8][D]*/) {
+__device__ __forceinline__ void hd_colsum_body(const float* __restrict__ A, const int64_t* nA_dev,
+                                               const float* __restrict__ B, const int64_t* nB_dev, int D,
+                                               double* __restrict__ part /*[2][8][D]*/, int set) {
   __shared__ double sh[8][33];
-  const int set = blockIdx.z;
   const float* X = set ? B : A;
   const int64_t n = set ? *nB_dev : *nA_dev;
   const int64_t rows = n < 2048 ? n : 2048;
@@ -296,8 +303,13 @@ __global__ void hd_colsum_kernel(const float* __restrict__ A, const int64_t* nA_
   }
 }
 
-__global__ void hd_shift_kernel(const double* __restrict__ part, const int64_t* nA_dev, const int64_t* nB_dev, int D,
-                                float* __restrict__ shift) {
+__global__ void hd_colsum_kernel(const float* __restrict__ A, const int64_t* nA_dev, const float* __restrict__ B,
+                                 const int64_t* nB_dev, int D, double* __restrict__ part /*[2][8][D]*/) {
+  hd_colsum_body(A, nA_dev, B, nB_dev, D, part, blockIdx.z);
+}
+
+__device__ __forceinline__ void hd_shift_body(const double* __restrict__ part, const int64_t* nA_dev,
+                                              const int64_t* nB_dev, int D, float* __restrict__ shift) {
   const int c = blockIdx.x * blockDim.x + threadIdx.x;
   if (c >= D) return;
   const int64_t na = *nA_dev < 2048 ? *nA_dev : 2048, nb = *nB_dev < 2048 ? *nB_dev : 2048;
@@ -309,10 +321,16 @@ __global__ void hd_shift_kernel(const double* __restrict__ part, const int64_t* 
   shift[c] = (float)(0.5 * (ta / (double)na + tb / (double)nb));
 }
 
+__global__ void hd_shift_kernel(const double* __restrict__ part, const int64_t* nA_dev, const int64_t* nB_dev, int D,
+                                float* __restrict__ shift) {
+  hd_shift_body(part, nA_dev, nB_dev, D, shift);
+}
+
 // max |x - s| over both sets (in FP32, the same values the copies use), and
 // the non-finite input check.
-__global__ void hd_maxabs_kernel(const float* __restrict__ X, const int64_t* n_dev, int D,
-                                 const float* __restrict__ shift, float* __restrict__ maxabs, int* status) {
+__device__ __forceinline__ void hd_maxabs_body(const float* __restrict__ X, const int64_t* n_dev, int D,
+                                               const float* __restrict__ shift, float* __restrict__ maxabs,
+                                               int* status) {
   const int64_t n = *n_dev;
   const int lane = threadIdx.x & 31;
   const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
@@ -330,6 +348,11 @@ __global__ void hd_maxabs_kernel(const float* __restrict__ X, const int64_t* n_d
   m = warp_max(m);
   if (__any_sync(0xffffffffu, bad) && lane == 0) atomicMax(status, (int)PROHD_ENONFINITE);
   if (lane == 0) atomic_max_nonneg(maxabs, m);
+}
+
+__global__ void hd_maxabs_kernel(const float* __restrict__ X, const int64_t* n_dev, int D,
+                                 const float* __restrict__ shift, float* __restrict__ maxabs, int* status) {
+  hd_maxabs_body(X, n_dev, D, shift, maxabs, status);
 }
 
 // Scale exponent: max|x - s| * 2^sigma lies in [2^12, 2^13), so the rounded
@@ -378,11 +401,12 @@ __device__ __forceinline__ float norm_part(float n2, int side, int lane) {
 // norm2, and eps >= ||(x - s) - h 2^-sigma|| + rounding of x - s (original
 // units) into eps. Padding rows: zeros, norm2 = 1e30, eps = 0.
 template <int BF16>
-__global__ void hd_prep_kernel(const float* __restrict__ X, const int64_t* n_dev, int64_t n_pad, int D, int Dp,
-                               const float* __restrict__ shift, const float* __restrict__ maxabs, float mult,
-                               typename TileT<BF16>::T* __restrict__ Xt, float* __restrict__ norm2,
-                               float* __restrict__ eps, float* __restrict__ maxnorm, float* __restrict__ maxeps,
-                               float* __restrict__ nparts, int side) {
+__device__ __forceinline__ void hd_prep_body(const float* __restrict__ X, const int64_t* n_dev, int64_t n_pad, int D,
+                                             int Dp, const float* __restrict__ shift, const float* __restrict__ maxabs,
+                                             float mult, typename TileT<BF16>::T* __restrict__ Xt,
+                                             float* __restrict__ norm2, float* __restrict__ eps,
+                                             float* __restrict__ maxnorm, float* __restrict__ maxeps,
+                                             float* __restrict__ nparts, int side) {
   using TT = TileT<BF16>;
   using T = typename TT::T;
   const int64_t n = *n_dev;
@@ -438,6 +462,15 @@ __global__ void hd_prep_kernel(const float* __restrict__ X, const int64_t* n_dev
   }
 }
 
+template <int BF16>
+__global__ void hd_prep_kernel(const float* __restrict__ X, const int64_t* n_dev, int64_t n_pad, int D, int Dp,
+                               const float* __restrict__ shift, const float* __restrict__ maxabs, float mult,
+                               typename TileT<BF16>::T* __restrict__ Xt, float* __restrict__ norm2,
+                               float* __restrict__ eps, float* __restrict__ maxnorm, float* __restrict__ maxeps,
+                               float* __restrict__ nparts, int side) {
+  hd_prep_body<BF16>(X, n_dev, n_pad, D, Dp, shift, maxabs, mult, Xt, norm2, eps, maxnorm, maxeps, nparts, side);
+}
+
 // =====================================================================
 // tcgen05 contraction with fused row-min / column-min epilogue
 // =====================================================================
@@ -488,24 +521,72 @@ __host__ __device__ constexpr size_t tc_smem_bytes(int KB) {
          (size_t)kTcStages * kTcBStage + sizeof(TcSmem);
 }
 
-template <int BF16>
-__global__ void __launch_bounds__(kTcThreads, 1)
-    hd_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
-                 const __grid_constant__ CUtensorMap tmNA, const __grid_constant__ CUtensorMap tmNB,
-                 const int64_t* __restrict__ nA_dev, const int64_t* __restrict__ nB_dev, int KB,
-                 float* __restrict__ rowmin, unsigned* __restrict__ colmin, int* __restrict__ status,
-                 uint64_t timeout_ns) {
+// One unit of contraction work: row block rb of A against the CB column
+// tiles of B, with the pair's operand maps, depth KB and minima.
+struct TcItem {
+  const CUtensorMap *tmA, *tmB, *tmNA, *tmNB;
+  int KB, CB, rb;
+  float* rowmin;
+  unsigned* colmin;
+};
+
+// The items of one pair: row blocks blockIdx.x, blockIdx.x + gridDim.x, ...
+struct TcItemsOne {
+  const CUtensorMap *tmA, *tmB, *tmNA, *tmNB;
+  int KB, RB, CB;
+  float* rowmin;
+  unsigned* colmin;
+  __device__ bool get(int k, TcItem& it) const {
+    const int rb = (int)blockIdx.x + k * (int)gridDim.x;
+    if (rb >= RB) return false;
+    it.tmA = tmA; it.tmB = tmB; it.tmNA = tmNA; it.tmNB = tmNB;
+    it.KB = KB; it.CB = CB; it.rb = rb; it.rowmin = rowmin; it.colmin = colmin;
+    return true;
+  }
+};
+
+// The items of a batch: item i is row block i - prefix[p] of pair order[p]
+// (prefix over pairs of their row-block counts), CTAs taking items
+// blockIdx.x, blockIdx.x + gridDim.x, ... in every role alike.
+struct TcItemsBatch {
+  const BPair* P;
+  const int* order;
+  const int64_t* prefix;
+  const CUtensorMap* maps;
+  int npairs;
+  __device__ bool get(int k, TcItem& it) const {
+    const int64_t i = (int64_t)blockIdx.x + (int64_t)k * gridDim.x;
+    if (i >= prefix[npairs]) return false;
+    int lo = 0, hi = npairs;  // prefix[lo] <= i < prefix[hi]
+    while (hi - lo > 1) {
+      const int mid = (lo + hi) >> 1;
+      if (prefix[mid] <= i) lo = mid;
+      else hi = mid;
+    }
+    const BPair& q = P[order[lo]];
+    const CUtensorMap* m = maps + q.hd_map;
+    it.tmA = m; it.tmB = m + 1; it.tmNA = m + 2; it.tmNB = m + 3;
+    it.KB = q.Dp / kTcBK;
+    it.CB = (int)((q.nsel[1] + kTcBN - 1) / kTcBN);
+    it.rb = (int)(i - prefix[lo]);
+    it.rowmin = q.hd_rowmin;
+    it.colmin = q.hd_colmin;
+    return true;
+  }
+};
+
+template <int BF16, class Items>
+__device__ __forceinline__ void hd_tc_body(const Items& items, int KBmax, int* __restrict__ status,
+                                           uint64_t timeout_ns, const CUtensorMap* const* prefetch) {
   extern __shared__ uint8_t smem_raw[];
   uint8_t* base = smem_align<1024>(smem_raw);
   uint8_t* sNB = base;                        // [2][8 KB]
   uint8_t* sNA = base + 2 * kTcNBBytes;       // 4 KB
   uint8_t* sA = sNA + kTcNABytes;             // 1024-aligned (20 KB from base)
-  uint8_t* sB = sA + (size_t)KB * kTcAKBytes;
+  uint8_t* sB = sA + (size_t)KBmax * kTcAKBytes;
   TcSmem& S = *reinterpret_cast<TcSmem*>(sB + (size_t)kTcStages * kTcBStage);
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int64_t nA = *nA_dev, nB = *nB_dev;
-  const int RB = (int)((nA + kTcBM - 1) / kTcBM), CB = (int)((nB + kTcBN - 1) / kTcBN);
   volatile int* abort = &S.abort;
 
   if (threadIdx.x == 0) {
@@ -529,12 +610,8 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     tc_alloc(&S.tmem_base, 512);
     tc_relinquish();
   }
-  if (warp == 0 && lane == 0) {
-    tma_prefetch_desc(&tmA);
-    tma_prefetch_desc(&tmB);
-    tma_prefetch_desc(&tmNA);
-    tma_prefetch_desc(&tmNB);
-  }
+  if (warp == 0 && lane == 0 && prefetch)
+    for (int i = 0; i < 4; ++i) tma_prefetch_desc(prefetch[i]);
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
@@ -548,22 +625,24 @@ __global__ void __launch_bounds__(kTcThreads, 1)
       uint32_t tile = 0;                 // running tile count (B norm ring slot and parity)
       uint32_t nb_issued = 0;            // B norm loads issued
       bool ok = true;
-      for (int rb = blockIdx.x; rb < RB && ok; rb += gridDim.x) {
+      TcItem it;
+      for (int k = 0; ok && items.get(k, it); ++k) {
+        const int rb = it.rb, KB = it.KB, CB = it.CB;
         if (!mbar_wait_bounded(&S.a_empty, aph ^ 1, abort, timeout_ns)) { ok = false; break; }
         aph ^= 1;
         mbar_arrive_expect_tx(&S.a_full, (uint32_t)(KB * kTcAKBytes + kTcNABytes));
-        tma_load_2d(sNA, &tmNA, 0, rb * kTcBM, &S.a_full);
-        for (int kb = 0; kb < KB; ++kb) tma_load_2d(sA + kb * kTcAKBytes, &tmA, kb * kTcBK, rb * kTcBM, &S.a_full);
+        tma_load_2d(sNA, it.tmNA, 0, rb * kTcBM, &S.a_full);
+        for (int kb = 0; kb < KB; ++kb) tma_load_2d(sA + kb * kTcAKBytes, it.tmA, kb * kTcBK, rb * kTcBM, &S.a_full);
         for (int cb = 0; cb < CB && ok; ++cb, ++tile) {
           const uint32_t ns = tile & 1u, nph = (tile >> 1) & 1u;
           if (!mbar_wait_bounded(&S.nb_empty[ns], nph ^ 1, abort, timeout_ns)) { ok = false; break; }
           mbar_arrive_expect_tx(&S.nb_full[ns], (uint32_t)kTcNBBytes);
-          tma_load_2d(sNB + ns * kTcNBBytes, &tmNB, 0, cb * kTcBN, &S.nb_full[ns]);
+          tma_load_2d(sNB + ns * kTcNBBytes, it.tmNB, 0, cb * kTcBN, &S.nb_full[ns]);
           ++nb_issued;
           for (int kb = 0; kb < KB; ++kb) {
             if (!mbar_wait_bounded(&S.b_empty[st], ph ^ 1, abort, timeout_ns)) { ok = false; break; }
             mbar_arrive_expect_tx(&S.b_full[st], (uint32_t)kTcBStage);
-            tma_load_2d(sB + st * kTcBStage, &tmB, kb * kTcBK, cb * kTcBN, &S.b_full[st]);
+            tma_load_2d(sB + st * kTcBStage, it.tmB, kb * kTcBK, cb * kTcBN, &S.b_full[st]);
             armed |= 1u << st;
             armed_ph = (armed_ph & ~(1u << st)) | (ph << st);
             if (++st == kTcStages) { st = 0; ph ^= 1; }
@@ -596,7 +675,9 @@ __global__ void __launch_bounds__(kTcThreads, 1)
       uint32_t st = 0, ph = 0, aph = 0;
       uint32_t tile = 0;
       bool ok = true;
-      for (int rb = blockIdx.x; rb < RB && ok; rb += gridDim.x) {
+      TcItem it;
+      for (int k = 0; ok && items.get(k, it); ++k) {
+        const int KB = it.KB, CB = it.CB;
         if (!mbar_wait_bounded(&S.a_full, aph, abort, timeout_ns)) { ok = false; break; }
         aph ^= 1;
         tc_fence_after();
@@ -642,14 +723,17 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     const int grp = ew >> 2;             // column group: four per lane quarter
     const int hcol = grp * (kTcBN / 4);  // first column of this warp's group
     const int et = threadIdx.x - 64;     // 0..511 (the first 256 also combine columns)
-    const int nrb = (int)blockIdx.x < RB ? (RB - (int)blockIdx.x + (int)gridDim.x - 1) / (int)gridDim.x : 0;
-    const int ntile = nrb * CB;
     bool ok = true;
     float rmin = __int_as_float(0x7f800000);
-    for (int i = 0; i < ntile; ++i) {
+    TcItem it;
+    int i = 0;  // running tile count: TMEM buffer and phase
+    for (int k = 0; items.get(k, it); ++k)
+    for (int cb = 0; cb < it.CB; ++cb, ++i) {
+      const int CB = it.CB, rb = it.rb;
+      float* rowmin = it.rowmin;
+      unsigned* colmin = it.colmin;
       const int ab = i & 1;
       const uint32_t par = (uint32_t)(i >> 1) & 1u;
-      const int rb = (int)blockIdx.x + (i / CB) * (int)gridDim.x, cb = i % CB;
       int got = 0;
       if (ok && lane == 0) got = mbar_wait_bounded(&S.acc_full[ab], par, abort, timeout_ns) ? 1 : 0;
       got = __shfl_sync(0xffffffffu, got, 0);
@@ -708,6 +792,41 @@ __global__ void __launch_bounds__(kTcThreads, 1)
   }
 }
 
+template <int BF16>
+__global__ void __launch_bounds__(kTcThreads, 1)
+    hd_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
+                 const __grid_constant__ CUtensorMap tmNA, const __grid_constant__ CUtensorMap tmNB,
+                 const int64_t* __restrict__ nA_dev, const int64_t* __restrict__ nB_dev, int KB,
+                 float* __restrict__ rowmin, unsigned* __restrict__ colmin, int* __restrict__ status,
+                 uint64_t timeout_ns) {
+  const int64_t nA = *nA_dev, nB = *nB_dev;
+  TcItemsOne items;
+  items.tmA = &tmA; items.tmB = &tmB; items.tmNA = &tmNA; items.tmNB = &tmNB;
+  items.KB = KB;
+  items.RB = (int)((nA + kTcBM - 1) / kTcBM);
+  items.CB = (int)((nB + kTcBN - 1) / kTcBN);
+  items.rowmin = rowmin;
+  items.colmin = colmin;
+  const CUtensorMap* pf[4] = {&tmA, &tmB, &tmNA, &tmNB};
+  hd_tc_body<BF16>(items, KB, status, timeout_ns, pf);
+}
+
+// Batched: every pair's row blocks against its own column tiles, the maps in
+// device memory; the smem layout holds the deepest pair (KBmax).
+template <int BF16>
+__global__ void __launch_bounds__(kTcThreads, 1)
+    hd_tc_batched_kernel(const BPair* __restrict__ P, const int* __restrict__ order, const int64_t* __restrict__ prefix,
+                         const CUtensorMap* __restrict__ maps, int npairs, int KBmax, int* __restrict__ status,
+                         uint64_t timeout_ns) {
+  TcItemsBatch items;
+  items.P = P;
+  items.order = order;
+  items.prefix = prefix;
+  items.maps = maps;
+  items.npairs = npairs;
+  hd_tc_body<BF16>(items, KBmax, status, timeout_ns, nullptr);
+}
+
 // =====================================================================
 // Margins, candidates, finalisation
 // =====================================================================
@@ -737,11 +856,11 @@ __device__ __forceinline__ void row_interval(float r2, float norm2_self, float m
   lo = (inv * sqrt(fmax(r - dd, 0.0)) - e) * (1.0 - 1e-6);
 }
 
-__global__ void hd_bounds_kernel(const float* __restrict__ rowmin, const float* __restrict__ nA2,
-                                 const float* __restrict__ epsA, const int64_t* nA_dev,
-                                 const unsigned* __restrict__ colmin, const float* __restrict__ nB2,
-                                 const float* __restrict__ epsB, const int64_t* nB_dev, double c1,
-                                 HdScalars* __restrict__ sc) {
+__device__ __forceinline__ void hd_bounds_body(const float* __restrict__ rowmin, const float* __restrict__ nA2,
+                                               const float* __restrict__ epsA, const int64_t* nA_dev,
+                                               const unsigned* __restrict__ colmin, const float* __restrict__ nB2,
+                                               const float* __restrict__ epsB, const int64_t* nB_dev, double c1,
+                                               HdScalars* __restrict__ sc) {
   const int64_t nA = *nA_dev, nB = *nB_dev;
   const double inv = ldexp(1.0, -scale_exponent(sc->maxabs));
   double lbA = 0.0, lbB = 0.0;
@@ -772,14 +891,23 @@ __global__ void hd_bounds_kernel(const float* __restrict__ rowmin, const float* 
   }
 }
 
+__global__ void hd_bounds_kernel(const float* __restrict__ rowmin, const float* __restrict__ nA2,
+                                 const float* __restrict__ epsA, const int64_t* nA_dev,
+                                 const unsigned* __restrict__ colmin, const float* __restrict__ nB2,
+                                 const float* __restrict__ epsB, const int64_t* nB_dev, double c1,
+                                 HdScalars* __restrict__ sc) {
+  hd_bounds_body(rowmin, nA2, epsA, nA_dev, colmin, nB2, epsB, nB_dev, c1, sc);
+}
+
 // Appends every row (column) whose upper bound reaches the largest lower
 // bound to the candidate list.
-__global__ void hd_flag_kernel(const float* __restrict__ rowmin, const float* __restrict__ nA2,
-                               const float* __restrict__ epsA, const int64_t* nA_dev,
-                               const unsigned* __restrict__ colmin, const float* __restrict__ nB2,
-                               const float* __restrict__ epsB, const int64_t* nB_dev, double c1,
-                               HdScalars* __restrict__ sc, int32_t* __restrict__ candA, int32_t* __restrict__ candB,
-                               int64_t* __restrict__ ncandA, int64_t* __restrict__ ncandB) {
+__device__ __forceinline__ void hd_flag_body(const float* __restrict__ rowmin, const float* __restrict__ nA2,
+                                             const float* __restrict__ epsA, const int64_t* nA_dev,
+                                             const unsigned* __restrict__ colmin, const float* __restrict__ nB2,
+                                             const float* __restrict__ epsB, const int64_t* nB_dev, double c1,
+                                             HdScalars* __restrict__ sc, int32_t* __restrict__ candA,
+                                             int32_t* __restrict__ candB, int64_t* __restrict__ ncandA,
+                                             int64_t* __restrict__ ncandB) {
   const int64_t nA = *nA_dev, nB = *nB_dev;
   const double inv = ldexp(1.0, -scale_exponent(sc->maxabs));
   const double LBa = sc->LB[0], LBb = sc->LB[1];
@@ -813,6 +941,15 @@ __global__ void hd_flag_kernel(const float* __restrict__ rowmin, const float* __
     base = __shfl_sync(0xffffffffu, base, 0);
     if (f) candB[base + __popc(m & ((1u << lane) - 1))] = (int32_t)j;
   }
+}
+
+__global__ void hd_flag_kernel(const float* __restrict__ rowmin, const float* __restrict__ nA2,
+                               const float* __restrict__ epsA, const int64_t* nA_dev,
+                               const unsigned* __restrict__ colmin, const float* __restrict__ nB2,
+                               const float* __restrict__ epsB, const int64_t* nB_dev, double c1,
+                               HdScalars* __restrict__ sc, int32_t* __restrict__ candA, int32_t* __restrict__ candB,
+                               int64_t* __restrict__ ncandA, int64_t* __restrict__ ncandB) {
+  hd_flag_body(rowmin, nA2, epsA, nA_dev, colmin, nB2, epsB, nB_dev, c1, sc, candA, candB, ncandA, ncandB);
 }
 
 // Block-wide argmax over (value, lowest id): key = float bits << 32 | ~id.
@@ -938,8 +1075,9 @@ __global__ void hd_finalize_kernel(const float* __restrict__ A, const int64_t* n
 // (pairs in the batch's order, largest first), and blocks take tiles from an
 // atomic ticket. Then one finalize block per pair maps the witnesses to
 // caller indices and recomputes their distances in FP64.
+// mode 0: 128 x 128 tiles of the subset product; mode 1: 128-row blocks of A.
 __global__ void hd_tile_scan_kernel(const BPair* __restrict__ P, const int* __restrict__ order, int npairs,
-                                    int64_t* __restrict__ prefix) {
+                                    int64_t* __restrict__ prefix, int mode) {
   __shared__ int64_t wsum[32];
   __shared__ int64_t carry;
   if (threadIdx.x == 0) carry = 0;
@@ -950,7 +1088,8 @@ __global__ void hd_tile_scan_kernel(const BPair* __restrict__ P, const int* __re
     int64_t v = 0;
     if (i < npairs) {
       const BPair& q = P[order[i]];
-      v = ceil_div_dev(q.nsel[0], kSimtBM) * ceil_div_dev(q.nsel[1], kSimtBN);
+      v = mode == 0 ? ceil_div_dev(q.nsel[0], kSimtBM) * ceil_div_dev(q.nsel[1], kSimtBN)
+                    : ceil_div_dev(q.nsel[0], 128);
     }
     int64_t incl = v;
     for (int o = 1; o < 32; o <<= 1) {
@@ -1213,12 +1352,132 @@ cudaError_t hd_core(prohd_ctx* ctx, const float* A, const int64_t* nA_dev, int64
 cudaError_t hd_simt_batched(const BPair* P, const int* order, int npairs, int64_t* prefix, unsigned long long* ticket,
                             int num_sms, cudaStream_t st) {
   count_launch();
-  hd_tile_scan_kernel<<<1, 1024, 0, st>>>(P, order, npairs, prefix);
+  hd_tile_scan_kernel<<<1, 1024, 0, st>>>(P, order, npairs, prefix, 0);
   cudaMemsetAsync(ticket, 0, sizeof(unsigned long long), st);
   count_launch();
   simt_dist_queue_kernel<<<num_sms * 2, 256, 0, st>>>(P, order, npairs, prefix, ticket);
   count_launch();
   hd_finalize_batched_kernel<<<npairs, 1024, 0, st>>>(P);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------- batched tensor-core subset distance
+
+size_t hd_scalars_bytes() { return sizeof(HdScalars); }
+size_t hd_tc_row_block() { return kTcBM; }
+
+// The single-pair kernels of the tensor path, one grid row (y or z) per
+// (pair, set) or per pair, the pair's buffers from its descriptor.
+__global__ void hd_colsum_batched_kernel(const BPair* __restrict__ P) {
+  const BPair& q = P[blockIdx.z >> 1];
+  if ((int)blockIdx.x * 32 >= q.D) return;
+  hd_colsum_body(q.As, q.nsel + 0, q.Bs, q.nsel + 1, q.D, q.hd_spart, blockIdx.z & 1);
+}
+__global__ void hd_shift_batched_kernel(const BPair* __restrict__ P) {
+  const BPair& q = P[blockIdx.y];
+  hd_shift_body(q.hd_spart, q.nsel + 0, q.nsel + 1, q.D, q.hd_shift);
+}
+__global__ void hd_maxabs_batched_kernel(const BPair* __restrict__ P) {
+  const BPair& q = P[blockIdx.y >> 1];
+  const int set = blockIdx.y & 1;
+  HdScalars* sc = static_cast<HdScalars*>(q.hd_sc);
+  hd_maxabs_body(set ? q.Bs : q.As, q.nsel + set, q.D, q.hd_shift, &sc->maxabs, q.status);
+}
+template <int BF16>
+__global__ void hd_prep_batched_kernel(const BPair* __restrict__ P) {
+  using T = typename TileT<BF16>::T;
+  const BPair& q = P[blockIdx.y >> 1];
+  const int set = blockIdx.y & 1;
+  HdScalars* sc = static_cast<HdScalars*>(q.hd_sc);
+  if (set == 0)
+    hd_prep_body<BF16>(q.As, q.nsel + 0, q.hd_nA_pad, q.D, q.Dp, q.hd_shift, &sc->maxabs, -2.f,
+                       static_cast<T*>(q.hd_At), q.hd_nA2, q.hd_epsA, &sc->maxnormA, &sc->maxepsA, q.hd_nA8, 0);
+  else
+    hd_prep_body<BF16>(q.Bs, q.nsel + 1, q.hd_nB_pad, q.D, q.Dp, q.hd_shift, &sc->maxabs, 1.f,
+                       static_cast<T*>(q.hd_Bt), q.hd_nB2, q.hd_epsB, &sc->maxnormB, &sc->maxepsB, q.hd_nB8, 1);
+}
+__device__ __forceinline__ double hd_c1(const BPair& q) {
+  return (2.0 * q.Dp + 2.0 * q.D + 32.0) * 5.9604644775390625e-8;
+}
+__global__ void hd_bounds_batched_kernel(const BPair* __restrict__ P) {
+  const BPair& q = P[blockIdx.y];
+  hd_bounds_body(q.hd_rowmin, q.hd_nA2, q.hd_epsA, q.nsel + 0, q.hd_colmin, q.hd_nB2, q.hd_epsB, q.nsel + 1, hd_c1(q),
+                 static_cast<HdScalars*>(q.hd_sc));
+}
+__global__ void hd_flag_batched_kernel(const BPair* __restrict__ P) {
+  const BPair& q = P[blockIdx.y];
+  HdScalars* sc = static_cast<HdScalars*>(q.hd_sc);
+  hd_flag_body(q.hd_rowmin, q.hd_nA2, q.hd_epsA, q.nsel + 0, q.hd_colmin, q.hd_nB2, q.hd_epsB, q.nsel + 1, hd_c1(q),
+               sc, q.hd_candA, q.hd_candB, &sc->ncandA, &sc->ncandB);
+}
+// Candidate rows of A against all of B (set 0) and of B against all of A (set 1).
+__global__ void __launch_bounds__(256) rescore_few_batched_kernel(const BPair* __restrict__ P) {
+  const BPair& q = P[blockIdx.y >> 1];
+  const int set = blockIdx.y & 1;
+  HdScalars* sc = static_cast<HdScalars*>(q.hd_sc);
+  if (set == 0)
+    rescore_few_body(q.As, q.hd_candA, &sc->ncandA, q.Bs, q.nsel + 1, q.D, q.bestA);
+  else
+    rescore_few_body(q.Bs, q.hd_candB, &sc->ncandB, q.As, q.nsel + 0, q.D, q.bestB);
+}
+__global__ void __launch_bounds__(256, 1) rescore_list_batched_kernel(const BPair* __restrict__ P) {
+  const BPair& q = P[blockIdx.y >> 1];
+  const int set = blockIdx.y & 1;
+  HdScalars* sc = static_cast<HdScalars*>(q.hd_sc);
+  if (set == 0)
+    simt_dist_body<true, true, false>(q.As, q.hd_candA, &sc->ncandA, q.Bs, q.nsel + 1, q.D, q.bestA, nullptr);
+  else
+    simt_dist_body<true, true, false>(q.Bs, q.hd_candB, &sc->ncandB, q.As, q.nsel + 0, q.D, q.bestB, nullptr);
+}
+__global__ void hd_finalize_tc_batched_kernel(const BPair* __restrict__ P) {
+  const BPair& q = P[blockIdx.x];
+  HdScalars* sc = static_cast<HdScalars*>(q.hd_sc);
+  hd_finalize_body(q.As, q.nsel + 0, q.Bs, q.nsel + 1, q.D, q.bestA, q.hd_candA, &sc->ncandA, q.bestB, q.hd_candB,
+                   &sc->ncandB, q.idxA, q.idxB, sc, q.status, &q.out->hd);
+}
+
+cudaError_t hd_tc_batched(const BPair* P, const int* order, int npairs, int64_t* prefix, const CUtensorMap* maps,
+                          int Dmax, int bf16, int* batch_status, int num_sms, int64_t timeout_ns, cudaStream_t st) {
+  const int Dp_max = (int)round_up(Dmax, kTcBK), KBmax = Dp_max / kTcBK;
+  cudaError_t e;
+  count_launch(5);
+  hd_colsum_batched_kernel<<<dim3((Dmax + 31) / 32, 8, 2 * npairs), 256, 0, st>>>(P);
+  hd_shift_batched_kernel<<<dim3((Dmax + 255) / 256, npairs), 256, 0, st>>>(P);
+  hd_maxabs_batched_kernel<<<dim3(4, 2 * npairs), 256, 0, st>>>(P);
+  if (bf16)
+    hd_prep_batched_kernel<1><<<dim3(4, 2 * npairs), 256, 0, st>>>(P);
+  else
+    hd_prep_batched_kernel<0><<<dim3(4, 2 * npairs), 256, 0, st>>>(P);
+  hd_tile_scan_kernel<<<1, 1024, 0, st>>>(P, order, npairs, prefix, 1);
+  if ((e = cudaGetLastError())) return e;
+  const size_t smem = tc_smem_bytes(KBmax);
+  if (bf16) {
+    cudaFuncSetAttribute(hd_tc_batched_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    count_launch();
+    hd_tc_batched_kernel<1><<<num_sms, kTcThreads, smem, st>>>(P, order, prefix, maps, npairs, KBmax, batch_status,
+                                                               (uint64_t)timeout_ns);
+  } else {
+    cudaFuncSetAttribute(hd_tc_batched_kernel<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    count_launch();
+    hd_tc_batched_kernel<0><<<num_sms, kTcThreads, smem, st>>>(P, order, prefix, maps, npairs, KBmax, batch_status,
+                                                               (uint64_t)timeout_ns);
+  }
+  if ((e = cudaGetLastError())) return e;
+  const size_t fsm = (size_t)kFewRows * 256 * sizeof(float) + (size_t)8 * kFewRows * sizeof(unsigned long long);
+  cudaFuncSetAttribute(rescore_few_batched_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fsm);
+  count_launch(5);
+  hd_bounds_batched_kernel<<<dim3(4, npairs), 256, 0, st>>>(P);
+  hd_flag_batched_kernel<<<dim3(4, npairs), 256, 0, st>>>(P);
+  rescore_few_batched_kernel<<<dim3(8, 2 * npairs), 256, fsm, st>>>(P);
+  rescore_list_batched_kernel<<<dim3(8, 2 * npairs), 256, 0, st>>>(P);
+  hd_finalize_tc_batched_kernel<<<npairs, 1024, 0, st>>>(P);
+  return cudaGetLastError();
+}
+
+cudaError_t fill_u32_region(unsigned* p, int64_t n, unsigned v, int num_sms, cudaStream_t st) {
+  if (n <= 0) return cudaSuccess;
+  count_launch();
+  fill_u32_kernel<<<num_sms * 2, 256, 0, st>>>(p, n, v);
   return cudaGetLastError();
 }
 

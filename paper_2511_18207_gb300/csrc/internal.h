@@ -166,6 +166,16 @@ struct BPair {
   unsigned long long *bestA, *bestB;
   int* status;
   prohd_result* out;
+  // tensor-core subset distance (FP16 / BF16 batches): rounded copies, norms,
+  // margins, minima, candidate lists, shift, scalars; four tensor maps from hd_map
+  void *hd_At, *hd_Bt;
+  float *hd_nA2, *hd_nB2, *hd_epsA, *hd_epsB, *hd_rowmin, *hd_shift, *hd_nA8, *hd_nB8;
+  unsigned* hd_colmin;
+  int32_t *hd_candA, *hd_candB;
+  double* hd_spart;
+  void* hd_sc;
+  int64_t hd_nA_pad, hd_nB_pad;
+  int hd_map;
   // Gram items of this pair, as positions in the batch's item-id list
   int gi0, gn0, gi1, gn1;
   int prob0;  // first selection problem of this pair (set-major: set * nd + d)
@@ -199,6 +209,13 @@ cudaError_t select_batched(SelProb* probs, int nprob, const double* alpha_of, un
 void sel_prob_fill(void* dst, const float* q, int64_t n, const float* X, const double* u, uint8_t* mask,
                    const float* maxnorm, int D, int32_t* band0, int32_t* band1, uint64_t* key0, uint64_t* key1);
 cudaError_t compact_gather_batched(const BPair* P, int npairs, int nblk_max, int64_t nmax, cudaStream_t st);
+size_t hd_scalars_bytes();
+size_t hd_tc_row_block();   // rows of A per contraction item (128)
+// Tensor-core subset HD of every pair: prep, contraction over (pair, row block)
+// items, margins, FP32 rescoring of candidates, FP64 witnesses.
+cudaError_t hd_tc_batched(const BPair* P, const int* order, int npairs, int64_t* prefix, const CUtensorMap* maps,
+                          int Dmax, int bf16, int* batch_status, int num_sms, int64_t timeout_ns, cudaStream_t st);
+cudaError_t fill_u32_region(unsigned* p, int64_t n, unsigned v, int num_sms, cudaStream_t st);
 cudaError_t hd_simt_batched(const BPair* P, const int* order, int npairs, int64_t* prefix, unsigned long long* ticket,
                             int num_sms, cudaStream_t st);
 

@@ -44,10 +44,10 @@ def _angle(u, v):
     return float(np.arccos(min(c, 1.0)))
 
 
-def _run(pairs, m=8, alpha=0.01, graph=True, tune=None):
+def _run(pairs, m=8, alpha=0.01, graph=True, tune=None, precision="fp16"):
     torch = torch_cuda()
     dpairs = [(dev(A), dev(B)) for A, B in pairs]
-    b = prohd.Batch(ctx(), dpairs, m=m, alpha_c=alpha)
+    b = prohd.Batch(ctx(), dpairs, m=m, alpha_c=alpha, precision=precision)
     b.use_graph(graph)
     if tune is not None:
         b.set_tunables(*tune)
@@ -100,11 +100,14 @@ def _check_pair(b, i, A, B, r, m, alpha, check_dirs=True):
         j = int(np.argmax(np.abs(U[l - 1])))
         assert U[l - 1, j] > 0
 
-def test_batch_matches_oracle_per_pair():
+@pytest.mark.parametrize("precision", ["fp16", "bf16", "fp32"])
+def test_batch_matches_oracle_per_pair(precision):
+    # fp16 / bf16: tensor-core subset HD with margins and FP32 rescoring;
+    # fp32: direct differences; the same H within FP32 rounding either way
     pairs = _pairs(SPEC)
-    b, res = _run(pairs)
+    b, res = _run(pairs, precision=precision)
     for i, ((A, B), r) in enumerate(zip(pairs, res)):
-        _check_pair(b, i, A, B, r, 8, 0.01, check_dirs=A.shape[0] * A.shape[1] < 3e6)
+        _check_pair(b, i, A, B, r, 8, 0.01, check_dirs=precision == "fp16" and A.shape[0] * A.shape[1] < 3e6)
 
 
 def test_batch_graph_replay_is_deterministic():
@@ -164,6 +167,9 @@ def test_batch_small_alpha_and_m():
     # k = 1 everywhere (alpha n < 1) and m = 2
     pairs = _pairs([(500, 700, 64), (90, 80, 128), (3000, 10, 256)], seed=21)
     b, res = _run(pairs, m=2, alpha=0.0005)
+    for i, ((A, B), r) in enumerate(zip(pairs, res)):
+        _check_pair(b, i, A, B, r, 2, 0.0005, check_dirs=False)
+    b, res = _run(pairs, m=2, alpha=0.0005, precision="fp32")
     for i, ((A, B), r) in enumerate(zip(pairs, res)):
         _check_pair(b, i, A, B, r, 2, 0.0005, check_dirs=False)
 
