@@ -271,21 +271,52 @@ def gpu_arm(args):
     run_steps(p16, args.warmup)
     torch.cuda.synchronize()
 
-    # timed region: K steps, profiling phases with CUDA events on the same stream
+    # phases: K eager steps with CUDA events around each phase on the same stream
     ctx.profile_read(reset=True)
     ctx.profile_enable(True)
     l0 = ctx.launch_count()
-    barrier(dist)
     torch.cuda.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(st)
     run_steps(p16, args.steps)
     e1.record(st)
     torch.cuda.synchronize()
-    barrier(dist)
-    launches = ctx.launch_count() - l0
+    per_call = (ctx.launch_count() - l0) // args.steps
     ctx.profile_enable(False)
     phases = ctx.profile_read(reset=True)
+    ms_eager = e0.elapsed_time(e1) / args.steps
+
+    # timed region: the estimate captured once in a CUDA graph (every entry point
+    # is capturable: no allocation, no synchronisation), K replays
+    graph = None
+    try:
+        gs = torch.cuda.Stream()
+        gs.wait_stream(st)
+        with torch.cuda.stream(gs):
+            run_steps(p16, 1)
+        st.wait_stream(gs)
+        torch.cuda.synchronize()
+        graph = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(graph):
+            ctx.prohd_estimate(At, Bt, params=p16, out=out, ws=ws)
+        for _ in range(args.warmup):
+            graph.replay()
+        torch.cuda.synchronize()
+    except Exception as ex:  # eager steps keep the measurement going
+        print(f"graph capture unavailable ({ex}); timing eager steps", file=sys.stderr)
+        graph = None
+    barrier(dist)
+    torch.cuda.synchronize()
+    e0.record(st)
+    if graph is not None:
+        for _ in range(args.steps):
+            graph.replay()
+    else:
+        run_steps(p16, args.steps)
+    e1.record(st)
+    torch.cuda.synchronize()
+    barrier(dist)
+    launches = per_call * args.steps
     t_ms = max_over_ranks(dist, e0.elapsed_time(e1), dev)
     ms_step = t_ms / args.steps
     res16 = prohd.decode_result(out)
@@ -419,6 +450,8 @@ def gpu_arm(args):
                  "rel_err_lowp_before_rescoring": (abs(resbf["H_lowp"] - resbf["H"]) / resbf["H"])},
         "fp16_rel_err_lowp_before_rescoring": abs(res16["H_lowp"] - res16["H"]) / res16["H"],
         "phases_ms_per_step": {k: round(v[0] * v[1] / args.steps, 4) for k, v in cand.items()},
+        "timing": ("CUDA-graph replays of one prohd_estimate" if graph is not None else "eager calls"),
+        "eager_ms_per_step": ms_eager,
         "e2e": {"value": world * 1000.0 / e2e_ms, "unit": UNIT, "ms_per_step": e2e_ms,
                 "h2d_bytes_per_step": 2 * n * DIM * 4, "d2h_bytes_per_step": ctypes.sizeof(prohd.Result)},
         "gpu_launches": launches,

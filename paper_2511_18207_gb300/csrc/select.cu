@@ -256,9 +256,9 @@ __global__ void sel_reset_batched_kernel(SelProb* __restrict__ P, int nprob, con
 }
 
 // grid (chunks, 2*nd). hist: [2*nd][2][256]
-__global__ void radix_hist_kernel(const SelProb* __restrict__ P, int pass, unsigned* __restrict__ hist) {
+__global__ void radix_hist_kernel(const SelProb* __restrict__ P, int pass, unsigned* __restrict__ hist, int pbase) {
   __shared__ unsigned h[2][256];
-  const int p = blockIdx.y;
+  const int p = pbase + blockIdx.y;
   const int64_t n = P[p].n;
   const float* q = P[p].q;
   for (int i = threadIdx.x; i < 512; i += blockDim.x) (&h[0][0])[i] = 0;
@@ -281,10 +281,11 @@ __global__ void radix_hist_kernel(const SelProb* __restrict__ P, int pass, unsig
 }
 
 // One warp per (problem, side): pick the bin holding the target rank.
-__global__ void radix_pick_kernel(SelProb* __restrict__ P, int nprob, int pass, unsigned* __restrict__ hist) {
+__global__ void radix_pick_kernel(SelProb* __restrict__ P, int nprob, int pass, unsigned* __restrict__ hist,
+                                  int pbase) {
   const int w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
   if (w >= nprob * 2) return;
-  const int p = w >> 1, side = w & 1;
+  const int p = pbase + (w >> 1), side = w & 1;
   unsigned* h = hist + (size_t)p * 512 + side * 256;
   int64_t r = P[p].rank[side];
   // each lane owns 8 consecutive bins
@@ -344,8 +345,8 @@ __device__ __forceinline__ float f32_down(double x) {
 
 // Marks certain members, counts them, and lists band members per side.
 // band lists: [2*nd][2][cap] int32
-__global__ void band_kernel(SelProb* __restrict__ P) {
-  const int p = blockIdx.y;
+__global__ void band_kernel(SelProb* __restrict__ P, int pbase) {
+  const int p = pbase + blockIdx.y;
   const int64_t n = P[p].n;
   const float* q = P[p].q;
   uint8_t* mask = P[p].mask;
@@ -804,17 +805,22 @@ cudaError_t select_run(prohd_ctx* ctx, const float* A, int64_t nA, const float* 
   count_launch();
   sel_init_kernel<<<1, 128, 0, st>>>(b.P, nd, kl, A, b.qA, nA, b.maskA, B, b.qB, nB, b.maskB, D, dirs, b.maxnorm,
                                      b.band, b.bandkey, b.cap);
-  const int64_t nmax = std::max(nA, nB);
-  const unsigned chunks = (unsigned)std::max<int64_t>(1, std::min<int64_t>(ceil_div(nmax, 256 * 16), (nsm * 8 + 2 * nd - 1) / (2 * nd)));
-  dim3 g(chunks, 2 * nd);
-  for (int pass = 0; pass < 4; ++pass) {
+  // one set at a time: a set's keys (nd n 4 bytes) stay in L2 across its
+  // four histogram passes and the band pass
+  for (int set = 0; set < 2; ++set) {
+    const int64_t n = set ? nB : nA;
+    const unsigned chunks =
+        (unsigned)std::max<int64_t>(1, std::min<int64_t>(ceil_div(n, 256 * 16), (nsm * 8 + nd - 1) / nd));
+    dim3 g(chunks, nd);
+    for (int pass = 0; pass < 4; ++pass) {
+      count_launch();
+      radix_hist_kernel<<<g, 256, 0, st>>>(b.P, pass, b.hist, set * nd);
+      count_launch();
+      radix_pick_kernel<<<(2 * nd * 32 + 127) / 128, 128, 0, st>>>(b.P, nd, pass, b.hist, set * nd);
+    }
     count_launch();
-    radix_hist_kernel<<<g, 256, 0, st>>>(b.P, pass, b.hist);
-    count_launch();
-    radix_pick_kernel<<<(4 * nd * 32 + 127) / 128, 128, 0, st>>>(b.P, 2 * nd, pass, b.hist);
+    band_kernel<<<g, 256, 0, st>>>(b.P, set * nd);
   }
-  count_launch();
-  band_kernel<<<g, 256, 0, st>>>(b.P);
   count_launch();
   band_keys_kernel<<<dim3(16, 4 * nd), 256, 0, st>>>(b.P);
   count_launch();
@@ -890,12 +896,12 @@ cudaError_t select_batched(SelProb* probs, int nprob, const double* alpha_of, un
   dim3 g(chunks, nprob);
   for (int pass = 0; pass < 4; ++pass) {
     count_launch();
-    radix_hist_kernel<<<g, 256, 0, st>>>(probs, pass, hist);
+    radix_hist_kernel<<<g, 256, 0, st>>>(probs, pass, hist, 0);
     count_launch();
-    radix_pick_kernel<<<(2 * nprob * 32 + 127) / 128, 128, 0, st>>>(probs, nprob, pass, hist);
+    radix_pick_kernel<<<(2 * nprob * 32 + 127) / 128, 128, 0, st>>>(probs, nprob, pass, hist, 0);
   }
   count_launch();
-  band_kernel<<<g, 256, 0, st>>>(probs);
+  band_kernel<<<g, 256, 0, st>>>(probs, 0);
   count_launch();
   band_keys_kernel<<<dim3(1, 2 * nprob), 256, 0, st>>>(probs);
   count_launch();
