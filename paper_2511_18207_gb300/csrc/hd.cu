@@ -224,13 +224,19 @@ __device__ __forceinline__ void rescore_few_body(const float* __restrict__ X, co
   __syncthreads();
   const int T = Dp >> 5;  // dimensions per lane
   const int64_t nw = (int64_t)gridDim.x * (blockDim.x >> 5);
-  for (int64_t j = (int64_t)blockIdx.x * (blockDim.x >> 5) + warp; j < ncols; j += nw) {
-    float y[8];
+  // the next row's values are loaded while this row is scored
+  float y[8], yn[8];
+  auto load_row = [&](float (&dst)[8], int64_t jj) {
 #pragma unroll
     for (int t = 0; t < 8; ++t) {
       const int k = lane + 32 * t;
-      y[t] = (t < T && k < D) ? Y[j * D + k] : 0.f;
+      dst[t] = (jj < ncols && t < T && k < D) ? __ldg(Y + jj * D + k) : 0.f;
     }
+  };
+  int64_t j = (int64_t)blockIdx.x * (blockDim.x >> 5) + warp;
+  load_row(y, j);
+  for (; j < ncols; j += nw) {
+    load_row(yn, j + nw);
     for (int r = 0; r < nr; ++r) {
       const float* xr = xs + r * Dp + lane;
       float acc = 0.f;
@@ -247,6 +253,8 @@ __device__ __forceinline__ void rescore_few_body(const float* __restrict__ X, co
         if (pk < best[warp * kFewRows + r]) best[warp * kFewRows + r] = pk;
       }
     }
+#pragma unroll
+    for (int t = 0; t < 8; ++t) y[t] = yn[t];
   }
   __syncthreads();
   for (int r = threadIdx.x; r < nr; r += blockDim.x) {
