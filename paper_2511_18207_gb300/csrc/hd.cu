@@ -341,16 +341,26 @@ __device__ __forceinline__ void hd_maxabs_body(const float* __restrict__ X, cons
                                                int* status) {
   const int64_t n = *n_dev;
   const int lane = threadIdx.x & 31;
-  const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
-  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  const int64_t total = n * D;
+  const int64_t tid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x, nth = (int64_t)gridDim.x * blockDim.x;
   float m = 0.f;
   bool bad = false;
-  for (int64_t r = warp; r < n; r += nwarps) {
-    const float* x = X + r * D;
-    for (int c = lane; c < D; c += 32) {
-      float v = x[c];
+  if ((D & 3) == 0 && (reinterpret_cast<uintptr_t>(X) & 15) == 0) {
+    // element stream in 128-bit loads, independent of the row structure
+    const float4* X4 = reinterpret_cast<const float4*>(X);
+    const int D4 = D >> 2;
+    for (int64_t e = tid; e < (total >> 2); e += nth) {
+      const float4 v = __ldg(X4 + e);
+      const int c = (int)(e % D4) * 4;
+      bad |= !isfinite(v.x) || !isfinite(v.y) || !isfinite(v.z) || !isfinite(v.w);
+      m = fmaxf(m, fmaxf(fmaxf(fabsf(v.x - shift[c]), fabsf(v.y - shift[c + 1])),
+                         fmaxf(fabsf(v.z - shift[c + 2]), fabsf(v.w - shift[c + 3]))));
+    }
+  } else {
+    for (int64_t e = tid; e < total; e += nth) {
+      const float v = X[e];
       bad |= !isfinite(v);
-      m = fmaxf(m, fabsf(v - shift[c]));
+      m = fmaxf(m, fabsf(v - shift[e % D]));
     }
   }
   m = warp_max(m);
@@ -424,15 +434,29 @@ __device__ __forceinline__ void hd_prep_body(const float* __restrict__ X, const 
   const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
   const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
   float wmaxn = 0.f, wmaxe = 0.f;
+  // a lane's values of the next row are loaded while this row is converted
+  // (Dp <= 256: at most 8 values per lane)
+  float xv[8], xn[8];
+  auto load_row = [&](float (&dst)[8], int64_t rr) {
+#pragma unroll
+    for (int t = 0; t < 8; ++t) {
+      const int c = lane + 32 * t;
+      dst[t] = (rr < n && c < D) ? __ldg(X + rr * D + c) : 0.f;
+    }
+  };
+  load_row(xv, warp);
   for (int64_t r = warp; r < n_pad; r += nwarps) {
+    load_row(xn, r + nwarps);
     T* out = Xt + r * Dp;
     if (r < n) {
-      const float* x = X + r * D;
       float sn = 0.f, se = 0.f, st = 0.f;
-      for (int c = lane; c < Dp; c += 32) {
+#pragma unroll
+      for (int tt = 0; tt < 8; ++tt) {
+        const int c = lane + 32 * tt;
+        if (c >= Dp) break;
         float hv = 0.f;
         if (c < D) {
-          float t = x[c] - shift[c];
+          float t = xv[tt] - shift[c];
           T h = TT::from(t * scale);
           hv = TT::to(h);
           float rr = t - hv * inv;  // exact: t and hv*inv agree to the tile precision
@@ -463,6 +487,8 @@ __device__ __forceinline__ void hd_prep_body(const float* __restrict__ X, const 
       }
       if (lane < 8) nparts[r * 8 + lane] = norm_part(1e30f, side, lane);
     }
+#pragma unroll
+    for (int t = 0; t < 8; ++t) xv[t] = xn[t];
   }
   if (lane == 0) {
     atomic_max_nonneg(maxnorm, wmaxn);
