@@ -296,6 +296,23 @@ def prohd(A, B, alpha: float = 0.01, m: int | None = None, alpha_p: float | None
                 idxA=idxA, idxB=idxB, dirs=dirs, lam=lam)
 
 
+def refined(A, B, idxA, idxB):
+    """One-sided refinement of a ProHD estimate (reading of Sec. III-E's
+    underestimation claim): max(h(A_sel, B), h(B_sel, A)), each selected
+    point's nearest neighbour searched in the whole other set. Every term is
+    a true nearest-neighbour distance of a point of A (or B), so the result
+    never exceeds H(A, B) (Eq. 1). Returns a dict with H1, h_ab, h_ba, dir and
+    the witness of H1 in the original index space."""
+    A, B = _f32(A), _f32(B)
+    idxA = np.asarray(idxA, dtype=np.int64)
+    idxB = np.asarray(idxB, dtype=np.int64)
+    h_ab, ia, jb = directed_hd(A[idxA], B)
+    h_ba, jb2, ia2 = directed_hd(B[idxB], A)
+    if h_ab >= h_ba:
+        return dict(H1=h_ab, h_ab=h_ab, h_ba=h_ba, dir=0, wit_a=int(idxA[ia]), wit_b=int(jb))
+    return dict(H1=h_ba, h_ab=h_ab, h_ba=h_ba, dir=1, wit_a=int(ia2), wit_b=int(idxB[jb2]))
+
+
 # --------------------------------------------------------------------------
 # Sec. III-E quantities
 # --------------------------------------------------------------------------

@@ -125,3 +125,67 @@ def test_delta_closed_form():
     assert oracle.delta(A, A, np.array([1.0, 0.0])) == 0.0
     assert oracle.delta(A, B, np.array([1.0, 0.0])) == 3.0
     assert oracle.delta(A, B, np.array([0.0, 1.0])) == 5.0
+
+
+def _brute_one_sided(X, Y, idx):
+    best, wi, wj = -1.0, -1, -1
+    for i in idx:
+        dmin, jmin = None, -1
+        for j in range(Y.shape[0]):
+            d = float(np.sqrt(sum((float(X[i, c]) - float(Y[j, c])) ** 2 for c in range(X.shape[1]))))
+            if dmin is None or d < dmin:
+                dmin, jmin = d, j
+        if dmin > best:
+            best, wi, wj = dmin, int(i), jmin
+    return best, wi, wj
+
+
+@pytest.mark.parametrize("seed", range(4))
+def test_refined_against_brute_force(seed):
+    rng = np.random.default_rng(40 + seed)
+    A = rng.standard_normal((13, 3)).astype(np.float32)
+    B = (rng.standard_normal((11, 3)) + 0.7).astype(np.float32)
+    ia = np.array(sorted(rng.choice(13, 5, replace=False)))
+    ib = np.array(sorted(rng.choice(11, 4, replace=False)))
+    r = oracle.refined(A, B, ia, ib)
+    h_ab, a1, b1 = _brute_one_sided(A, B, ia)
+    h_ba, b2, a2 = _brute_one_sided(B, A, ib)
+    assert r["h_ab"] == pytest.approx(h_ab, rel=1e-12)
+    assert r["h_ba"] == pytest.approx(h_ba, rel=1e-12)
+    assert r["H1"] == max(r["h_ab"], r["h_ba"])
+    # the witness is a pair of the original sets at distance H1
+    wa, wb = (a1, b1) if h_ab >= h_ba else (a2, b2)
+    assert (r["wit_a"], r["wit_b"]) == (wa, wb)
+
+
+def test_refined_one_dimensional_closed_form():
+    # A = {0, 5, 10}, B = {0, 10}: H = 5 (the middle point of A); the
+    # extremes alone see no gap, the middle point brings H back
+    A = np.array([[0.0], [5.0], [10.0]], dtype=np.float32)
+    B = np.array([[0.0], [10.0]], dtype=np.float32)
+    assert oracle.hausdorff(A, B)["H"] == 5.0
+    assert oracle.refined(A, B, [0, 2], [0, 1])["H1"] == 0.0
+    r = oracle.refined(A, B, [1], [0])
+    assert r["H1"] == 5.0 and r["wit_a"] == 1 and r["dir"] == 0
+
+
+def test_refined_never_exceeds_h_and_grows_with_the_subsets():
+    # on the tiny trials where Algorithm 3's subset HD overshoots H, the
+    # one-sided form stays below H; enlarging either subset cannot lower it;
+    # keeping every point gives H exactly
+    rng = np.random.default_rng(0)
+    over = 0
+    for _ in range(300):
+        A = rng.standard_normal((8, 2)).astype(np.float32)
+        B = rng.standard_normal((8, 2)).astype(np.float32)
+        H = oracle.hausdorff(A, B)["H"]
+        p = oracle.prohd(A, B, alpha=0.13, m=1)
+        over += p["H_hat"] > H + 1e-9
+        r = oracle.refined(A, B, p["idxA"], p["idxB"])
+        assert r["H1"] <= H + 1e-12
+        big = oracle.refined(A, B, np.union1d(p["idxA"], [3]), p["idxB"])
+        assert big["H1"] >= r["H1"]
+    assert over > 0
+    A = rng.standard_normal((9, 4)).astype(np.float32)
+    B = rng.standard_normal((6, 4)).astype(np.float32)
+    assert oracle.refined(A, B, np.arange(9), np.arange(6))["H1"] == oracle.hausdorff(A, B)["H"]
