@@ -74,6 +74,12 @@ typedef struct prohd_ctx prohd_ctx;
  *                after power_max_iters steps (defaults 1000 and 1e-13)
  *   seed         seed of the SplitMix64 start vectors of the power iteration
  *   precision    PROHD_FP32 / PROHD_FP16 / PROHD_BF16 for the subset HD
+ *   refine       0: H_hat = H(A_sel, B_sel) as Algorithm 3 states (default);
+ *                1: one-sided refinement H_hat = max(h(A_sel, B), h(B_sel, A)),
+ *                   each selected point against the whole other set. It never
+ *                   exceeds H(A, B) (the selected points are points of A and B),
+ *                   at the cost of two subset-vs-set contractions
+ *                   (prohd_estimate / prohd_estimate_dirs / prohd_estimate_host)
  *   wait_timeout_ns  limit of every bounded device wait (default 4e9 ns)
  */
 typedef struct {
@@ -82,7 +88,7 @@ typedef struct {
   double alpha_c;
   double alpha_p;
   int32_t power_max_iters;
-  int32_t reserved0;
+  int32_t refine;
   double power_tol;
   uint64_t seed;
   int64_t wait_timeout_ns;
@@ -288,7 +294,8 @@ size_t prohd_batch_workspace_size(const prohd_pair_desc* pairs, int npairs, cons
  * validates it, lays it out in `ws` (device, 256-byte aligned, at least the
  * size above; owned by the caller and bound to the plan until it is
  * destroyed), encodes the tensor maps and uploads the tables. Planning
- * synchronises the device (synchronous copies); running does not. */
+ * synchronises the device (synchronous copies); running does not.
+ * params.refine must be 0 (PROHD_ENOTSUP otherwise). */
 prohd_status prohd_batch_plan(prohd_ctx* ctx, const prohd_pair_desc* pairs, int npairs, const prohd_params* p,
                               void* ws, size_t ws_bytes, prohd_batch** out);
 void prohd_batch_destroy(prohd_batch* b);
@@ -323,9 +330,10 @@ prohd_status prohd_batch_pair_outputs(const prohd_batch* b, int pair, double** d
  * per-direction k lists kA, kB (HOST arrays of nd values >= 1; a direction
  * keeps its kA[d] smallest and kA[d] largest projections of A). Selection,
  * union, gather and the subset HD run as in prohd_estimate (params.precision
- * picks the tiles; m, alpha are not used). idxA / idxB may be NULL. */
+ * picks the tiles and params.refine the one-sided refinement; m, alpha are
+ * not used). idxA / idxB may be NULL. */
 size_t prohd_estimate_dirs_workspace_size(int64_t nA, int64_t nB, int D, int nd, const int64_t* kA, const int64_t* kB,
-                                          int precision);
+                                          const prohd_params* p);
 prohd_status prohd_estimate_dirs(prohd_ctx* ctx, const float* A, int64_t nA, const float* B, int64_t nB, int D,
                                  const prohd_params* p, const double* dirs, int nd, const int64_t* kA,
                                  const int64_t* kB, prohd_result* out, int32_t* idxA, int32_t* idxB, void* ws,

@@ -23,6 +23,31 @@ __global__ void finish_estimate_kernel(prohd_result* out, const int64_t* nselA, 
   out->nsel_b = *nselB;
 }
 
+// One-sided refinement (max of the two directed distances of each selected
+// set against the whole other set): r1 holds h(A_sel, B) in its h_ab, with
+// witness (ab_a mapped to A, ab_b in B); r2 holds h(B_sel, A) likewise with
+// the roles of the sets swapped.
+__global__ void refine_combine_kernel(const prohd_hd_result* r1, const prohd_hd_result* r2, prohd_result* out) {
+  prohd_hd_result r;
+  const prohd_hd_result a = *r1, b = *r2;
+  r.h_ab = a.h_ab;
+  r.h_ba = b.h_ab;
+  r.ab_a = a.ab_a;
+  r.ab_b = a.ab_b;
+  r.ba_b = b.ab_a;
+  r.ba_a = b.ab_b;
+  r.dir = r.h_ab >= r.h_ba ? 0 : 1;
+  r.H = r.dir == 0 ? r.h_ab : r.h_ba;
+  r.wit_a = r.dir == 0 ? r.ab_a : r.ba_a;
+  r.wit_b = r.dir == 0 ? r.ab_b : r.ba_b;
+  r.status = a.status > b.status ? a.status : b.status;
+  if (out->hd.status > r.status) r.status = out->hd.status;
+  r.H_lowp = fmax(a.H_lowp, b.H_lowp);
+  r.n_rescored_a = a.n_rescored_a;
+  r.n_rescored_b = b.n_rescored_a;
+  out->hd = r;
+}
+
 cudaError_t set_i64(int64_t* p, int64_t v, cudaStream_t st) {
   count_launch();
   set_i64_kernel<<<1, 1, 0, st>>>(p, v);
@@ -99,6 +124,7 @@ static prohd_status check_params(prohd_ctx* ctx, const prohd_params* p, int D) {
   if (p->precision != PROHD_FP32 && !tc_supported_dim(D))
     return fail(ctx, PROHD_ENOTSUP, "tensor-core precisions need D <= 256 (use PROHD_FP32)%s");
   if (p->power_max_iters < 1) return fail(ctx, PROHD_EINVAL, "power_max_iters must be >= 1%s");
+  if (p->refine != 0 && p->refine != 1) return fail(ctx, PROHD_EINVAL, "refine must be 0 or 1%s");
   return PROHD_OK;
 }
 
@@ -145,12 +171,17 @@ struct EstLayout {
   int nd;
   int64_t kA[64], kB[64];
   size_t mark_dir, mark_sel, mark_hd;  // arena offsets where each phase's scratch starts
+  // one-sided refinement: full-set sizes on the device and the two directed results
+  bool refine = false;
+  int64_t *nA_full = nullptr, *nB_full = nullptr;
+  prohd_hd_result *r1 = nullptr, *r2 = nullptr;
+  size_t mark_ref2 = 0;  // second contraction's scratch (after the first's)
 };
 
 // Layout of an estimate with nd directions and the given k lists; m_dirs >= 0
 // reserves the directions phase's scratch (m_dirs components), -1 skips it.
 void est_layout_k(Arena& a, int64_t nA, int64_t nB, int D, int nd, const int64_t* kA, const int64_t* kB,
-                  int precision, int m_dirs, EstLayout& L) {
+                  int precision, int m_dirs, EstLayout& L, bool refine = false) {
   L.nd = nd;
   for (int d = 0; d < nd; ++d) {
     L.kA[d] = kA[d];
@@ -167,6 +198,13 @@ void est_layout_k(Arena& a, int64_t nA, int64_t nB, int D, int nd, const int64_t
   L.nselB = a.take<int64_t>(1);
   L.As = a.take<float>((size_t)L.boundA * D);
   L.Bs = a.take<float>((size_t)L.boundB * D);
+  L.refine = refine;
+  if (refine) {
+    L.nA_full = a.take<int64_t>(1);
+    L.nB_full = a.take<int64_t>(1);
+    L.r1 = a.take<prohd_hd_result>(1);
+    L.r2 = a.take<prohd_hd_result>(1);
+  }
   // the phases run one after another and share the rest of the arena
   const size_t start = a.off;
   size_t end = start;
@@ -182,6 +220,15 @@ void est_layout_k(Arena& a, int64_t nA, int64_t nB, int D, int nd, const int64_t
   t = a;
   hd_core_layout(t, L.boundA, L.boundB, D, precision);
   end = std::max(end, t.off);
+  if (refine) {
+    // h(A_sel, B) then h(B_sel, A): one after the other in the same region
+    t = a;
+    hd_core_layout(t, L.boundA, nB, D, precision);
+    end = std::max(end, t.off);
+    t = a;
+    hd_core_layout(t, L.boundB, nA, D, precision);
+    end = std::max(end, t.off);
+  }
   a.off = end;
 }
 
@@ -192,7 +239,7 @@ void est_layout(Arena& a, int64_t nA, int64_t nB, int D, const prohd_params* p, 
   int64_t kA[64], kB[64];
   k_list(nA, nd, p->alpha_c, ap, kA);
   k_list(nB, nd, p->alpha_c, ap, kB);
-  est_layout_k(a, nA, nB, D, nd, kA, kB, p->precision, m, L);
+  est_layout_k(a, nA, nB, D, nd, kA, kB, p->precision, m, L, p->refine != 0);
 }
 
 }  // namespace
@@ -414,6 +461,27 @@ static prohd_status estimate_run(prohd_ctx* ctx, const float* A, int64_t nA, con
     e = hd_core(ctx, L.As, L.nselA, L.boundA, L.Bs, L.nselB, L.boundB, D, p->precision, L.idxA, L.idxB, &out->hd,
                 L.status, t, to, st);
   }
+  if (!e && L.refine) {
+    // h(A_sel, B) and h(B_sel, A) on the original sets, then their maximum
+    const int64_t to = p->wait_timeout_ns > 0 ? p->wait_timeout_ns : kDefaultTimeoutNs;
+    e = set_i64(L.nA_full, nA, st);
+    if (!e) e = set_i64(L.nB_full, nB, st);
+    if (!e) {
+      Arena t = phase(L.mark_hd);
+      e = hd_core(ctx, L.As, L.nselA, L.boundA, B, L.nB_full, nB, D, p->precision, L.idxA, nullptr, L.r1, L.status, t,
+                  to, st);
+    }
+    if (!e) {
+      Arena t = phase(L.mark_hd);
+      e = hd_core(ctx, L.Bs, L.nselB, L.boundB, A, L.nA_full, nA, D, p->precision, L.idxB, nullptr, L.r2, L.status, t,
+                  to, st);
+    }
+    if (!e) {
+      count_launch();
+      refine_combine_kernel<<<1, 1, 0, st>>>(L.r1, L.r2, out);
+      e = cudaGetLastError();
+    }
+  }
   if (!e) {
     count_launch();
     finish_estimate_kernel<<<1, 1, 0, st>>>(out, L.nselA, L.nselB);
@@ -512,11 +580,11 @@ static prohd_status check_klist(prohd_ctx* ctx, int nd, const int64_t* kA, const
 }
 
 size_t prohd_estimate_dirs_workspace_size(int64_t nA, int64_t nB, int D, int nd, const int64_t* kA, const int64_t* kB,
-                                          int precision) {
-  if (nd < 1 || nd > 64 || !kA || !kB) return 0;
+                                          const prohd_params* p) {
+  if (nd < 1 || nd > 64 || !kA || !kB || !p) return 0;
   Arena a;
   EstLayout L;
-  est_layout_k(a, nA, nB, D, nd, kA, kB, precision, -1, L);
+  est_layout_k(a, nA, nB, D, nd, kA, kB, p->precision, -1, L, p->refine != 0);
   return a.off + 256;
 }
 
@@ -530,13 +598,12 @@ prohd_status prohd_estimate_dirs(prohd_ctx* ctx, const float* A, int64_t nA, con
   if (!dirs) return fail(ctx, PROHD_EINVAL, "null dirs%s");
   if ((s = check_klist(ctx, nd, kA, kB))) return s;
   if (!out) return fail(ctx, PROHD_EINVAL, "null output%s");
-  if ((s = check_ws(ctx, ws, ws_bytes, prohd_estimate_dirs_workspace_size(nA, nB, D, nd, kA, kB, p->precision))))
-    return s;
+  if ((s = check_ws(ctx, ws, ws_bytes, prohd_estimate_dirs_workspace_size(nA, nB, D, nd, kA, kB, p)))) return s;
   Arena a;
   a.base = static_cast<char*>(ws);
   a.cap = ws_bytes;
   EstLayout L;
-  est_layout_k(a, nA, nB, D, nd, kA, kB, p->precision, -1, L);
+  est_layout_k(a, nA, nB, D, nd, kA, kB, p->precision, -1, L, p->refine != 0);
   return estimate_run(ctx, A, nA, B, nB, D, p, L, out, idxA, idxB, nullptr, dirs, static_cast<char*>(ws), ws_bytes,
                       reinterpret_cast<cudaStream_t>(stream));
 }

@@ -258,6 +258,7 @@ prohd_status check_batch(prohd_ctx* ctx, const prohd_pair_desc* pairs, int npair
   if (p->power_max_iters < 1) return bfail(ctx, PROHD_EINVAL, "power_max_iters must be >= 1");
   if (p->precision != PROHD_FP32 && p->precision != PROHD_FP16 && p->precision != PROHD_BF16)
     return bfail(ctx, PROHD_EINVAL, "unknown precision");
+  if (p->refine != 0) return bfail(ctx, PROHD_ENOTSUP, "the one-sided refinement is not batched; use prohd_estimate");
   pp.resize((size_t)npairs);
   int64_t nprob = 0;
   for (int i = 0; i < npairs; ++i) {

@@ -47,7 +47,7 @@ PHASES = ["gram", "power", "project", "select", "gather", "hd_prep", "hd_contrac
 
 class Params(ctypes.Structure):
     _fields_ = [("m", ctypes.c_int32), ("precision", ctypes.c_int32), ("alpha_c", ctypes.c_double),
-                ("alpha_p", ctypes.c_double), ("power_max_iters", ctypes.c_int32), ("reserved0", ctypes.c_int32),
+                ("alpha_p", ctypes.c_double), ("power_max_iters", ctypes.c_int32), ("refine", ctypes.c_int32),
                 ("power_tol", ctypes.c_double), ("seed", ctypes.c_uint64), ("wait_timeout_ns", ctypes.c_int64),
                 ("reserved", ctypes.c_int64 * 4)]
 
@@ -145,7 +145,7 @@ def load_library(path: str = LIB_PATH):
                                                  ctypes.POINTER(vp)]
         lib.prohd_batch_pair_outputs.restype = i32
         pi64 = ctypes.POINTER(ctypes.c_int64)
-        lib.prohd_estimate_dirs_workspace_size.argtypes = [i64, i64, i32, i32, pi64, pi64, i32]
+        lib.prohd_estimate_dirs_workspace_size.argtypes = [i64, i64, i32, i32, pi64, pi64, pp]
         lib.prohd_estimate_dirs_workspace_size.restype = sz
         lib.prohd_estimate_dirs.argtypes = [vp, vp, i64, vp, i64, i32, pp, vp, i32, pi64, pi64, vp, vp, vp, vp, sz, vp]
         lib.prohd_estimate_dirs.restype = i32
@@ -367,7 +367,7 @@ class Context:
         nd = dirs.shape[0]
         ka = (ctypes.c_int64 * nd)(*[int(k) for k in kA])
         kb = (ctypes.c_int64 * nd)(*[int(k) for k in kB])
-        need = self.lib.prohd_estimate_dirs_workspace_size(A.shape[0], B.shape[0], D, nd, ka, kb, p.precision)
+        need = self.lib.prohd_estimate_dirs_workspace_size(A.shape[0], B.shape[0], D, nd, ka, kb, ctypes.byref(p))
         ws = self.workspace(need)
         out = torch.empty(ctypes.sizeof(Result), dtype=torch.uint8, device=A.device) if out is None else out
         rc = self.lib.prohd_estimate_dirs(self.h, _ptr(A), A.shape[0], _ptr(B), B.shape[0], D, ctypes.byref(p),

@@ -182,4 +182,6 @@ def test_batch_rejects_bad_pairs():
     A = dev(np.zeros((10, 16), np.float32))
     with pytest.raises(prohd.ProHDError, match="ENOTSUP"):
         prohd.Batch(ctx(), [(A, A)], m=30, alpha_c=0.1)
+    with pytest.raises(prohd.ProHDError, match="ENOTSUP"):
+        prohd.Batch(ctx(), [(A, A)], m=2, alpha_c=0.1, refine=1)
     torch.cuda.synchronize()

@@ -88,3 +88,63 @@ def test_estimate_nonfinite_input_is_reported(D, where):
         B[-1, D - 1] = np.inf
     r = prohd.prohd_estimate_sync(dev(A), dev(B), m=2, alpha_c=0.01)
     assert r["status"] == "ENONFINITE", r["status"]
+
+
+@pytest.mark.parametrize("prec", ["fp16", "bf16", "fp32"])
+@pytest.mark.parametrize("shape", [(6_001, 5_003, 16, 2, 0.02), (20_000, 17_771, 256, 8, 0.01)])
+def test_estimate_refined_matches_oracle(prec, shape):
+    # params.refine = 1: max(h(A_sel, B), h(B_sel, A)) with each selected
+    # point's nearest neighbour searched in the whole other set; never above H
+    torch_cuda()
+    nA, nB, D, m, alpha = shape
+    if D == 16:
+        A, B = W.gaussian_outliers(nA, nB, D, seed=5)
+    else:
+        A, _ = W.mixture_pair(nA, D, 16, seed=6)
+        _, B = W.mixture_pair(nB, D, 16, seed=7)
+    r0 = prohd.prohd_estimate_sync(dev(A), dev(B), want_indices=True, m=m, alpha_c=alpha, precision=prec)
+    r = prohd.prohd_estimate_sync(dev(A), dev(B), want_indices=True, m=m, alpha_c=alpha, precision=prec, refine=1)
+    assert r["status"] == "OK", r
+    # same candidate sets as the plain estimate
+    np.testing.assert_array_equal(r["idxA"], r0["idxA"])
+    np.testing.assert_array_equal(r["idxB"], r0["idxB"])
+    o = oracle.refined(A, B, r["idxA"], r["idxB"])
+    assert rel(r["h_ab"], o["h_ab"]) <= 1e-5, (r["h_ab"], o["h_ab"])
+    assert rel(r["h_ba"], o["h_ba"]) <= 1e-5, (r["h_ba"], o["h_ba"])
+    assert rel(r["H"], o["H1"]) <= 1e-5
+    assert r["dir"] == (0 if r["h_ab"] >= r["h_ba"] else 1)
+    # the witness is a selected point and its nearest neighbour in the full set
+    sel = r["idxA"] if r["dir"] == 0 else r["idxB"]
+    assert (r["wit_a"] if r["dir"] == 0 else r["wit_b"]) in set(sel.tolist())
+    d = np.sqrt(((A[r["wit_a"]].astype(np.float64) - B[r["wit_b"]]) ** 2).sum())
+    assert d == pytest.approx(r["H"], rel=1e-12)
+    if D == 16:
+        assert r["H"] <= oracle.hausdorff(A, B)["H"] * (1 + 1e-7)
+
+
+def test_estimate_refined_with_given_directions():
+    torch = torch_cuda()
+    A, B = W.mixture_pair(12_000, 64, 8, seed=8)
+    rng = np.random.default_rng(9)
+    dirs = rng.standard_normal((5, 64))
+    dirs /= np.linalg.norm(dirs, axis=1, keepdims=True)
+    kA, kB = [90] + [20] * 4, [70] + [15] * 4
+    c = prohd.context()
+    idxA = torch.empty(A.shape[0], dtype=torch.int32, device="cuda")
+    idxB = torch.empty(B.shape[0], dtype=torch.int32, device="cuda")
+    out = c.prohd_estimate_dirs(dev(A), dev(B), torch.from_numpy(dirs).cuda(), kA, kB, precision="fp16",
+                                idxA=idxA, idxB=idxB, refine=1)
+    torch.cuda.synchronize()
+    r = prohd.decode_result(out)
+    assert r["status"] == "OK"
+    ia, ib = oracle.select(A, dirs, kA), oracle.select(B, dirs, kB)
+    np.testing.assert_array_equal(idxA[: r["nsel_a"]].cpu().numpy(), ia)
+    o = oracle.refined(A, B, ia, ib)
+    assert rel(r["H"], o["H1"]) <= 1e-5
+
+
+def test_refine_must_be_zero_or_one():
+    torch_cuda()
+    A, B = W.random_clouds(500, 400, 8, seed=1)
+    with pytest.raises(prohd.ProHDError):
+        prohd.prohd_estimate_sync(dev(A), dev(B), refine=2)
