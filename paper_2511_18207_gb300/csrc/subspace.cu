@@ -3,8 +3,10 @@
 //
 // The top-m eigenvectors of C are a plain definition; the oracle reaches them
 // by deflated power iteration, one vector at a time, and this path reaches
-// the same vectors with a block of b = min(D, max(2m, m + 8), 32) vectors
-// iterated together:
+// the same vectors with a block of b vectors iterated together: b = D when
+// D <= 32 (the block spans the space, so the first Rayleigh-Ritz step is
+// already the full eigendecomposition whatever the eigengaps), else
+// b = min(max(2m, m + 8), 32):
 //   V orthonormal (D x b); W = C V; H = V^T W; H = Y diag(theta) Y^T (Jacobi);
 //   Ritz vectors X = V Y, residuals r_j = W y_j - theta_j x_j;
 //   stop when ||r_j|| <= eps theta_1 for the m leading pairs, else
@@ -45,6 +47,12 @@ constexpr int kSiFinThreads = 256;
 constexpr int kSiJacThreads = 256;  // the Jacobi rounds run on 8 warps (one warp alone is slower: the rounds are latency-bound)
 constexpr int kSiMaxD = 256;
 constexpr int kSiMaxB = 32;
+
+// block size for D dimensions and m components (D <= 256, m <= 24)
+__host__ __device__ inline int si_block(int D, int m) {
+  const int want = 2 * m > m + 8 ? 2 * m : m + 8;
+  return D <= kSiMaxB ? D : (want < kSiMaxB ? want : kSiMaxB);
+}
 constexpr int kSiMaxM = 24;
 constexpr int kSiMaxRows = kSiMaxD / kSiCTAs;      // 32
 constexpr int kSiLd = kSiMaxB + 1;                 // row stride of the small matrices
@@ -738,7 +746,7 @@ __global__ void __launch_bounds__(kSiThreads, 1)
   extern __shared__ __align__(16) uint8_t sism[];
   const BPair& q = P[list[blockIdx.x]];
   if (q.m < 1) return;
-  const int b = min(q.D, min(kSiMaxB, max(2 * q.m, q.m + 8)));
+  const int b = si_block(q.D, q.m);
   subspace_body<1, ROWS, ROWS + 4>(*reinterpret_cast<SiSmemT<1, ROWS, ROWS + 4>*>(sism), q.C32, q.D, q.m, b,
                                    max(q.iters, 1), eps, sigma_rel, seed, q.U, q.iters_out);
 }
@@ -860,7 +868,7 @@ size_t subspace_scratch_doubles(int D, int m) { return (size_t)2 * std::max(m, 1
 cudaError_t subspace_run(prohd_ctx* ctx, const float* C32, const double* C64, int D, int m, int max_iters, double tol,
                          uint64_t seed, double* dirs, double* eig, double* scratch, cudaStream_t st) {
   (void)ctx;
-  const int b = std::min(D, std::min(kSiMaxB, std::max(2 * m, m + 8)));
+  const int b = si_block(D, m);
   const float eps = (float)std::max(std::sqrt(2.0 * std::max(tol, 0.0)), 2e-6);
   double* Uout = scratch;
   double* part = scratch + (size_t)m * D;
