@@ -313,6 +313,59 @@ def refined(A, B, idxA, idxB):
     return dict(H1=h_ba, h_ab=h_ab, h_ba=h_ba, dir=1, wit_a=int(ia2), wit_b=int(idxB[jb2]))
 
 
+ADAPTIVE_MAX_STEPS = 32
+
+
+def adaptive(A, B, alpha: float, alpha_max: float, rel_tol: float, m: int | None = None,
+             alpha_p: float | None = None, seed: int = 0, dirs=None, max_steps: int = ADAPTIVE_MAX_STEPS):
+    """Adaptive alpha schedule (the future direction of Sec. VI: alpha grown
+    until the estimate meets an error budget), read as a doubling schedule on
+    the one-sided refined estimate.
+
+    Directions are taken once (or given). Step t keeps alpha_t = alpha 2^t on
+    the centroid axis and alpha_p 2^t on each component (alpha_p defaults to
+    alpha / m), selects as Algorithm 3 does, and takes the refined estimate
+    H_t = max(h(A_sel, B), h(B_sel, A)). Candidate sets grow with t, so H_t
+    never decreases and never exceeds H. The schedule stops, checked in this
+    order, when every point is selected on both sides (H_t = H), when t >= 1
+    and H_t - H_{t-1} <= rel_tol H_t, when alpha 2^(t+1) > alpha_max, or after
+    ``max_steps`` steps. Returns H1 (the last H_t), the per-step H and subset
+    sizes, the number of steps, the stop reason and the last alpha values."""
+    A, B = _f32(A), _f32(B)
+    D = A.shape[1]
+    if dirs is None:
+        if m is None:
+            m = default_m(D)
+        dirs, _, _ = directions(A, B, m=m, seed=seed)
+    dirs = np.atleast_2d(np.asarray(dirs, dtype=np.float64))
+    nd = dirs.shape[0]
+    if alpha_p is None:
+        alpha_p = alpha / max(nd - 1, 1)
+    Hs, na, nb = [], [], []
+    t = 0
+    while True:
+        a_t, ap_t = alpha * 2.0**t, alpha_p * 2.0**t
+        ia = select(A, dirs, k_list(A.shape[0], nd, a_t, ap_t))
+        ib = select(B, dirs, k_list(B.shape[0], nd, a_t, ap_t))
+        r = refined(A, B, ia, ib)
+        Hs.append(r["H1"])
+        na.append(int(ia.size))
+        nb.append(int(ib.size))
+        if ia.size == A.shape[0] and ib.size == B.shape[0]:
+            reason = "all"
+        elif t >= 1 and Hs[-1] - Hs[-2] <= rel_tol * Hs[-1]:
+            reason = "stable"
+        elif alpha * 2.0 ** (t + 1) > alpha_max:
+            reason = "budget"
+        elif t + 1 >= max_steps:
+            reason = "steps"
+        else:
+            t += 1
+            continue
+        return dict(H1=Hs[-1], H=Hs, nsel_a=na, nsel_b=nb, steps=t + 1, reason=reason, alpha=a_t, alpha_p=ap_t,
+                    idxA=ia, idxB=ib, refined=r, dirs=dirs)
+
+
 # --------------------------------------------------------------------------
 # Sec. III-E quantities
 # --------------------------------------------------------------------------

@@ -189,3 +189,64 @@ def test_refined_never_exceeds_h_and_grows_with_the_subsets():
     A = rng.standard_normal((9, 4)).astype(np.float32)
     B = rng.standard_normal((6, 4)).astype(np.float32)
     assert oracle.refined(A, B, np.arange(9), np.arange(6))["H1"] == oracle.hausdorff(A, B)["H"]
+
+
+def test_adaptive_alpha_hand_derived(golden):
+    g = golden("adaptive_alpha_1d.json")
+    A = np.array(g["A"], dtype=np.float32)
+    B = np.array(g["B"], dtype=np.float32)
+    assert oracle.hausdorff(A, B)["H"] == 4.0
+    for c in g["cases"]:
+        r = oracle.adaptive(A, B, g["alpha"], c["alpha_max"], c["rel_tol"], dirs=g["dirs"])
+        assert r["H"] == c["H"], c
+        assert r["nsel_a"] == c["nsel_a"] and all(n == 2 for n in r["nsel_b"])
+        assert r["reason"] == c["reason"] and r["steps"] == len(c["H"])
+        assert r["alpha"] == pytest.approx(c["alpha"], rel=1e-15)
+
+
+def _brute_adaptive(A, B, dirs, alpha, alpha_max, rel_tol):
+    # selection by full sorts, refined estimate by nested loops
+    Hs = []
+    t = 0
+    while True:
+        a_t = alpha * 2.0**t
+        ks = [max(1, min(int(np.floor(a_t * A.shape[0])), A.shape[0]))] * len(dirs)
+        kb = [max(1, min(int(np.floor(a_t * B.shape[0])), B.shape[0]))] * len(dirs)
+        ia, ib = _brute_select(A, dirs, ks), _brute_select(B, dirs, kb)
+        h = max(_brute_one_sided(A, B, ia)[0], _brute_one_sided(B, A, ib)[0])
+        Hs.append(h)
+        if ia.size == A.shape[0] and ib.size == B.shape[0]:
+            return Hs, "all"
+        if t >= 1 and Hs[-1] - Hs[-2] <= rel_tol * Hs[-1]:
+            return Hs, "stable"
+        if alpha * 2.0 ** (t + 1) > alpha_max:
+            return Hs, "budget"
+        t += 1
+
+
+@pytest.mark.parametrize("seed", range(4))
+def test_adaptive_alpha_against_brute_force(seed):
+    rng = np.random.default_rng(70 + seed)
+    A = rng.standard_normal((23, 3)).astype(np.float32)
+    B = (rng.standard_normal((17, 3)) * 1.3 + 0.5).astype(np.float32)
+    dirs = rng.standard_normal((2, 3))
+    dirs /= np.linalg.norm(dirs, axis=1, keepdims=True)
+    for alpha_max, tol in [(0.99, 0.0), (0.3, 0.0), (0.99, 0.05)]:
+        # alpha_p = alpha on the second direction, as the brute force takes it
+        r = oracle.adaptive(A, B, 0.05, alpha_max, tol, dirs=dirs, alpha_p=0.05)
+        Hs, why = _brute_adaptive(A, B, dirs, 0.05, alpha_max, tol)
+        assert r["reason"] == why and r["steps"] == len(Hs)
+        np.testing.assert_allclose(r["H"], Hs, rtol=1e-12)
+
+
+def test_adaptive_alpha_invariants():
+    # non-decreasing, never above H, and equal to H once every point is kept
+    A, B = W.random_clouds(300, 200, 3, seed=4)
+    H = oracle.hausdorff(A, B)["H"]
+    r = oracle.adaptive(A, B, 0.005, 0.99, 0.0, m=1)
+    assert all(b >= a for a, b in zip(r["H"], r["H"][1:]))
+    assert max(r["H"]) <= H + 1e-12
+    assert r["reason"] in ("all", "stable")
+    if r["reason"] == "all":
+        assert r["H1"] == H
+    assert all(b >= a for a, b in zip(r["nsel_a"], r["nsel_a"][1:]))
