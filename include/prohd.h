@@ -339,6 +339,45 @@ prohd_status prohd_estimate_dirs(prohd_ctx* ctx, const float* A, int64_t nA, con
                                  const int64_t* kB, prohd_result* out, int32_t* idxA, int32_t* idxB, void* ws,
                                  size_t ws_bytes, void* stream);
 
+/* ---------------------------------------------------------------- adaptive alpha
+ *
+ * The adaptive alpha schedule Sec. VI proposes for strict error budgets, read
+ * as doubling alpha on the one-sided refined estimate: the directions are
+ * computed once (as prohd_estimate computes them); step t = 0, 1, ... keeps
+ * alpha_t = alpha_c 2^t per side on the centroid axis and alpha_p 2^t on each
+ * component (alpha_p < 0: alpha_c / m), selects as Algorithm 3, and takes
+ * H_t = max(h(A_sel, B), h(B_sel, A)) (params.refine = 1 semantics). The
+ * candidate sets grow with t, so H_t never decreases and never exceeds H.
+ * The schedule stops, checked in this order, when every point of both sets is
+ * selected (H_t = H: PROHD_ADAPT_ALL), when t >= 1 and H_t - H_{t-1} <=
+ * rel_tol H_t (PROHD_ADAPT_STABLE), when alpha_c 2^(t+1) > alpha_max
+ * (PROHD_ADAPT_BUDGET), or after PROHD_ADAPT_MAX_STEPS steps.
+ *
+ * params.refine is ignored (always the refined estimate); alpha_max must be
+ * in [alpha_c, 1), rel_tol >= 0. out (device) holds the last step's result,
+ * dirs (device, [1+m][D] FP64) the directions, idxA / idxB (device) the last
+ * step's candidate indices; each may be NULL but out. info (HOST) receives
+ * the schedule. The stop decision is taken on the host: the call
+ * synchronises `stream` once per step, so it cannot be captured in a CUDA
+ * graph. The workspace holds the largest step's subsets. */
+#define PROHD_ADAPT_MAX_STEPS 32
+enum { PROHD_ADAPT_ALL = 0, PROHD_ADAPT_STABLE = 1, PROHD_ADAPT_BUDGET = 2, PROHD_ADAPT_STEPS = 3 };
+typedef struct prohd_adaptive_info {
+  int32_t steps;                          /* steps run (>= 1) */
+  int32_t reason;                         /* PROHD_ADAPT_* */
+  double alpha_c, alpha_p;                /* the last step's fractions */
+  double H[PROHD_ADAPT_MAX_STEPS];        /* H_t per step */
+  int64_t nsel_a[PROHD_ADAPT_MAX_STEPS];  /* |A_sel| per step */
+  int64_t nsel_b[PROHD_ADAPT_MAX_STEPS];  /* |B_sel| per step */
+} prohd_adaptive_info;
+
+size_t prohd_estimate_adaptive_workspace_size(int64_t nA, int64_t nB, int D, const prohd_params* p,
+                                              double alpha_max);
+prohd_status prohd_estimate_adaptive(prohd_ctx* ctx, const float* A, int64_t nA, const float* B, int64_t nB, int D,
+                                     const prohd_params* p, double alpha_max, double rel_tol, prohd_result* out,
+                                     prohd_adaptive_info* info, int32_t* idxA, int32_t* idxB, double* dirs,
+                                     void* ws, size_t ws_bytes, void* stream);
+
 /* ---------------------------------------------------------------- learned directions
  *
  * A small network proposes 4 extra unit directions per pair from cheap set

@@ -423,6 +423,34 @@ prohd_status prohd_select(prohd_ctx* ctx, const float* A, int64_t nA, const floa
   return e ? cuda_fail(ctx, e) : PROHD_OK;
 }
 
+// One-sided refinement after the selection and gather: h(A_sel, B) and
+// h(B_sel, A) on the original sets, then their maximum into out->hd (whose
+// status field must hold the earlier stages' status, or 0).
+static cudaError_t refine_run(prohd_ctx* ctx, const float* A, int64_t nA, const float* B, int64_t nB, int D,
+                              const prohd_params* p, EstLayout& L, prohd_result* out, char* wsb, size_t ws_bytes,
+                              cudaStream_t st) {
+  Arena t;
+  t.base = wsb;
+  t.cap = ws_bytes;
+  t.off = L.mark_hd;
+  const int64_t to = p->wait_timeout_ns > 0 ? p->wait_timeout_ns : kDefaultTimeoutNs;
+  cudaError_t e = set_i64(L.nA_full, nA, st);
+  if (!e) e = set_i64(L.nB_full, nB, st);
+  if (!e)
+    e = hd_core(ctx, L.As, L.nselA, L.boundA, B, L.nB_full, nB, D, p->precision, L.idxA, nullptr, L.r1, L.status, t,
+                to, st);
+  t.off = L.mark_hd;
+  if (!e)
+    e = hd_core(ctx, L.Bs, L.nselB, L.boundB, A, L.nA_full, nA, D, p->precision, L.idxB, nullptr, L.r2, L.status, t,
+                to, st);
+  if (!e) {
+    count_launch();
+    refine_combine_kernel<<<1, 1, 0, st>>>(L.r1, L.r2, out);
+    e = cudaGetLastError();
+  }
+  return e;
+}
+
 // given_dirs: the caller's directions (nd = L.nd) replace the directions phase.
 static prohd_status estimate_run(prohd_ctx* ctx, const float* A, int64_t nA, const float* B, int64_t nB, int D,
                                  const prohd_params* p, EstLayout& L, prohd_result* out, int32_t* idxA,
@@ -461,27 +489,7 @@ static prohd_status estimate_run(prohd_ctx* ctx, const float* A, int64_t nA, con
     e = hd_core(ctx, L.As, L.nselA, L.boundA, L.Bs, L.nselB, L.boundB, D, p->precision, L.idxA, L.idxB, &out->hd,
                 L.status, t, to, st);
   }
-  if (!e && L.refine) {
-    // h(A_sel, B) and h(B_sel, A) on the original sets, then their maximum
-    const int64_t to = p->wait_timeout_ns > 0 ? p->wait_timeout_ns : kDefaultTimeoutNs;
-    e = set_i64(L.nA_full, nA, st);
-    if (!e) e = set_i64(L.nB_full, nB, st);
-    if (!e) {
-      Arena t = phase(L.mark_hd);
-      e = hd_core(ctx, L.As, L.nselA, L.boundA, B, L.nB_full, nB, D, p->precision, L.idxA, nullptr, L.r1, L.status, t,
-                  to, st);
-    }
-    if (!e) {
-      Arena t = phase(L.mark_hd);
-      e = hd_core(ctx, L.Bs, L.nselB, L.boundB, A, L.nA_full, nA, D, p->precision, L.idxB, nullptr, L.r2, L.status, t,
-                  to, st);
-    }
-    if (!e) {
-      count_launch();
-      refine_combine_kernel<<<1, 1, 0, st>>>(L.r1, L.r2, out);
-      e = cudaGetLastError();
-    }
-  }
+  if (!e && L.refine) e = refine_run(ctx, A, nA, B, nB, D, p, L, out, wsb, ws_bytes, st);
   if (!e) {
     count_launch();
     finish_estimate_kernel<<<1, 1, 0, st>>>(out, L.nselA, L.nselB);
@@ -606,6 +614,130 @@ prohd_status prohd_estimate_dirs(prohd_ctx* ctx, const float* A, int64_t nA, con
   est_layout_k(a, nA, nB, D, nd, kA, kB, p->precision, -1, L, p->refine != 0);
   return estimate_run(ctx, A, nA, B, nB, D, p, L, out, idxA, idxB, nullptr, dirs, static_cast<char*>(ws), ws_bytes,
                       reinterpret_cast<cudaStream_t>(stream));
+}
+
+// ---------------------------------------------------------------- adaptive alpha
+
+// number of doublings the schedule can take: the largest t with alpha_c 2^t <= alpha_max
+static int adaptive_last_step(double alpha_c, double alpha_max) {
+  int t = 0;
+  while (t + 1 < PROHD_ADAPT_MAX_STEPS && alpha_c * ldexp(1.0, t + 1) <= alpha_max) ++t;
+  return t;
+}
+
+static bool adaptive_layout(Arena& a, int64_t nA, int64_t nB, int D, const prohd_params* p, double alpha_max,
+                            EstLayout& L) {
+  const int m = resolve_m(p, D);
+  const int nd = 1 + m;
+  const double ap = resolve_alpha_p(p, m);
+  const double sc = ldexp(1.0, adaptive_last_step(p->alpha_c, alpha_max));
+  int64_t kA[64], kB[64];
+  k_list(nA, nd, p->alpha_c * sc, ap * sc, kA);
+  k_list(nB, nd, p->alpha_c * sc, ap * sc, kB);
+  est_layout_k(a, nA, nB, D, nd, kA, kB, p->precision, m, L, true);
+  return true;
+}
+
+size_t prohd_estimate_adaptive_workspace_size(int64_t nA, int64_t nB, int D, const prohd_params* p,
+                                              double alpha_max) {
+  if (!p || !(p->alpha_c > 0.0) || !(alpha_max >= p->alpha_c)) return 0;
+  Arena a;
+  EstLayout L;
+  adaptive_layout(a, nA, nB, D, p, alpha_max, L);
+  return a.off + 256;
+}
+
+prohd_status prohd_estimate_adaptive(prohd_ctx* ctx, const float* A, int64_t nA, const float* B, int64_t nB, int D,
+                                     const prohd_params* p, double alpha_max, double rel_tol, prohd_result* out,
+                                     prohd_adaptive_info* info, int32_t* idxA, int32_t* idxB, double* dirs,
+                                     void* ws, size_t ws_bytes, void* stream) {
+  prohd_status s = check_sets(ctx, A, nA, B, nB, D);
+  if (s) return s;
+  if ((s = check_params(ctx, p, D))) return s;
+  if (!(alpha_max >= p->alpha_c && alpha_max < 1.0))
+    return fail(ctx, PROHD_EINVAL, "alpha_max must be in [alpha_c, 1)%s");
+  if (!(rel_tol >= 0.0)) return fail(ctx, PROHD_EINVAL, "rel_tol must be >= 0%s");
+  if (!out || !info) return fail(ctx, PROHD_EINVAL, "null output%s");
+  if ((s = check_ws(ctx, ws, ws_bytes, prohd_estimate_adaptive_workspace_size(nA, nB, D, p, alpha_max)))) return s;
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  char* wsb = static_cast<char*>(ws);
+  Arena a;
+  a.base = wsb;
+  a.cap = ws_bytes;
+  EstLayout L;
+  adaptive_layout(a, nA, nB, D, p, alpha_max, L);
+  if (a.overflow()) return fail(ctx, PROHD_ENOMEM, "workspace too small%s");
+  if (idxA) L.idxA = idxA;
+  if (idxB) L.idxB = idxB;
+  if (dirs) L.dirs = dirs;
+  const int m = L.nd - 1;
+  const double ap = resolve_alpha_p(p, m);
+  *info = prohd_adaptive_info{};
+  auto phase = [&](size_t mark) {
+    Arena t;
+    t.base = wsb;
+    t.cap = ws_bytes;
+    t.off = mark;
+    return t;
+  };
+  cudaError_t e = zero_i32(L.status, 8, st);
+  if (!e) {
+    Arena t = phase(L.mark_dir);
+    e = directions_run(ctx, A, nA, B, nB, D, m, p->power_max_iters, p->power_tol, p->seed, L.dirs, L.eig, L.status, t,
+                       st);
+  }
+  prohd_result h{};
+  for (int step = 0; !e; ++step) {
+    const double sc = ldexp(1.0, step);
+    const double a_t = p->alpha_c * sc, ap_t = ap * sc;
+    k_list(nA, L.nd, a_t, ap_t, L.kA);
+    k_list(nB, L.nd, a_t, ap_t, L.kB);
+    e = cudaMemsetAsync(out, 0, sizeof(prohd_result), st);
+    if (!e) {
+      Arena t = phase(L.mark_sel);
+      e = select_run(ctx, A, nA, B, nB, D, L.dirs, L.nd, L.kA, L.kB, L.idxA, L.nselA, L.idxB, L.nselB, L.status, t,
+                     st);
+    }
+    {
+      PhaseTimer pt(ctx, PROHD_PH_GATHER, st);
+      if (!e) e = gather_rows(A, D, L.idxA, L.nselA, L.boundA, L.As, ctx->num_sms, st);
+      if (!e) e = gather_rows(B, D, L.idxB, L.nselB, L.boundB, L.Bs, ctx->num_sms, st);
+    }
+    if (!e) e = refine_run(ctx, A, nA, B, nB, D, p, L, out, wsb, ws_bytes, st);
+    if (!e) {
+      count_launch();
+      finish_estimate_kernel<<<1, 1, 0, st>>>(out, L.nselA, L.nselB);
+      e = cudaGetLastError();
+    }
+    // the stop decision needs this step's result on the host
+    if (!e) e = cudaMemcpyAsync(&h, out, sizeof(prohd_result), cudaMemcpyDeviceToHost, st);
+    if (!e) e = cudaStreamSynchronize(st);
+    if (e) break;
+    info->steps = step + 1;
+    info->alpha_c = a_t;
+    info->alpha_p = ap_t;
+    info->H[step] = h.hd.H;
+    info->nsel_a[step] = h.nsel_a;
+    info->nsel_b[step] = h.nsel_b;
+    if (h.hd.status != PROHD_OK) break;  // reported through out
+    if (h.nsel_a == nA && h.nsel_b == nB) {
+      info->reason = PROHD_ADAPT_ALL;
+      break;
+    }
+    if (step >= 1 && info->H[step] - info->H[step - 1] <= rel_tol * info->H[step]) {
+      info->reason = PROHD_ADAPT_STABLE;
+      break;
+    }
+    if (p->alpha_c * ldexp(1.0, step + 1) > alpha_max) {
+      info->reason = PROHD_ADAPT_BUDGET;
+      break;
+    }
+    if (step + 1 >= PROHD_ADAPT_MAX_STEPS) {
+      info->reason = PROHD_ADAPT_STEPS;
+      break;
+    }
+  }
+  return e ? cuda_fail(ctx, e) : PROHD_OK;
 }
 
 // ---------------------------------------------------------------- learned directions

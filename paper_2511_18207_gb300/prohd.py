@@ -39,6 +39,7 @@ EXPORTS = [
     "prohd_estimate_dirs_workspace_size", "prohd_estimate_dirs", "prohd_features_workspace_size", "prohd_features",
     "prohd_mlp_param_count", "prohd_mlp_state_bytes", "prohd_mlp_scratch_bytes", "prohd_mlp_init", "prohd_mlp_forward",
     "prohd_mlp_loss_grad", "prohd_mlp_train_step", "prohd_mlp_adam_step",
+    "prohd_estimate_adaptive_workspace_size", "prohd_estimate_adaptive",
 ]
 
 #: prohd_phase names, in enum order
@@ -62,6 +63,16 @@ class HdResult(ctypes.Structure):
 
 class Result(ctypes.Structure):
     _fields_ = [("hd", HdResult), ("nsel_a", ctypes.c_int64), ("nsel_b", ctypes.c_int64)]
+
+
+ADAPT_MAX_STEPS = 32
+ADAPT_REASONS = {0: "all", 1: "stable", 2: "budget", 3: "steps"}
+
+
+class AdaptiveInfo(ctypes.Structure):
+    _fields_ = [("steps", ctypes.c_int32), ("reason", ctypes.c_int32), ("alpha_c", ctypes.c_double),
+                ("alpha_p", ctypes.c_double), ("H", ctypes.c_double * ADAPT_MAX_STEPS),
+                ("nsel_a", ctypes.c_int64 * ADAPT_MAX_STEPS), ("nsel_b", ctypes.c_int64 * ADAPT_MAX_STEPS)]
 
 
 class PairDesc(ctypes.Structure):
@@ -149,6 +160,11 @@ def load_library(path: str = LIB_PATH):
         lib.prohd_estimate_dirs_workspace_size.restype = sz
         lib.prohd_estimate_dirs.argtypes = [vp, vp, i64, vp, i64, i32, pp, vp, i32, pi64, pi64, vp, vp, vp, vp, sz, vp]
         lib.prohd_estimate_dirs.restype = i32
+        lib.prohd_estimate_adaptive_workspace_size.argtypes = [i64, i64, i32, pp, ctypes.c_double]
+        lib.prohd_estimate_adaptive_workspace_size.restype = sz
+        lib.prohd_estimate_adaptive.argtypes = [vp, vp, i64, vp, i64, i32, pp, ctypes.c_double, ctypes.c_double, vp,
+                                                ctypes.POINTER(AdaptiveInfo), vp, vp, vp, vp, sz, vp]
+        lib.prohd_estimate_adaptive.restype = i32
         lib.prohd_features_workspace_size.argtypes = [i64, i64, i32]
         lib.prohd_features_workspace_size.restype = sz
         lib.prohd_features.argtypes = [vp, vp, i64, vp, i64, i32, pp, vp, vp, vp, vp, sz, vp]
@@ -377,6 +393,33 @@ class Context:
                                           self._stream(stream))
         self._raise(rc, "prohd_estimate_dirs")
         return out
+
+    def prohd_estimate_adaptive(self, A, B, alpha_max, rel_tol, params: Params | None = None, out=None, idxA=None,
+                                idxB=None, dirs=None, stream=None, **kw):
+        """Runs the adaptive alpha schedule (synchronises the stream once per
+        step); returns (device result buffer, decoded schedule dict)."""
+        torch = _torch()
+        _check_points(A, "A")
+        _check_points(B, "B")
+        p = params if params is not None else default_params(**kw)
+        D = A.shape[1]
+        need = self.lib.prohd_estimate_adaptive_workspace_size(A.shape[0], B.shape[0], D, ctypes.byref(p),
+                                                              float(alpha_max))
+        ws = self.workspace(need)
+        out = torch.empty(ctypes.sizeof(Result), dtype=torch.uint8, device=A.device) if out is None else out
+        info = AdaptiveInfo()
+        rc = self.lib.prohd_estimate_adaptive(self.h, _ptr(A), A.shape[0], _ptr(B), B.shape[0], D, ctypes.byref(p),
+                                              float(alpha_max), float(rel_tol), _ptr(out), ctypes.byref(info),
+                                              _ptr(idxA) if idxA is not None else None,
+                                              _ptr(idxB) if idxB is not None else None,
+                                              _ptr(dirs) if dirs is not None else None, _ptr(ws), ws.numel(),
+                                              self._stream(stream))
+        self._raise(rc, "prohd_estimate_adaptive")
+        n = info.steps
+        sched = dict(steps=n, reason=ADAPT_REASONS.get(info.reason, info.reason), alpha_c=info.alpha_c,
+                     alpha_p=info.alpha_p, H=list(info.H[:n]), nsel_a=list(info.nsel_a[:n]),
+                     nsel_b=list(info.nsel_b[:n]))
+        return out, sched
 
     def prohd_features(self, A, B, feat=None, dirs=None, eig=None, seed=0, stream=None):
         """Network input features [10 D] (FP32), directions [9, D] and eig [8] of a pair."""

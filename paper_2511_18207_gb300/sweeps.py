@@ -5,7 +5,9 @@ scalability studies (Sec. IV-D, IV-E):
 * ``alpha``: the selection fraction (Fig. 2's sweep, here on random clouds);
 * ``dim``: D in {2, ..., 256} at 100k + 100k points (Fig. 3);
 * ``ratio``: n_B / n_A in {0.125, 0.25, 0.5, 1} with n_A = 100k, D = 4 (Fig. 4);
-* ``size``: n_A = n_B from 100k to 1M, D = 4 (Fig. 5).
+* ``size``: n_A = n_B from 100k to 1M, D = 4 (Fig. 5);
+* ``adaptive``: the adaptive alpha schedule of Sec. VI (doubling alpha on the
+  refined estimate until it stabilises) at D = 4, 64, 256.
 
 Every point runs through the library: the estimate of Algorithm 3
 (``prohd_estimate``), its one-sided refinement (``refine = 1``) and the exact
@@ -35,6 +37,10 @@ SWEEPS = {
     "dim": [dict(n_a=100_000, n_b=100_000, D=d, alpha=0.01) for d in (2, 4, 8, 16, 32, 64, 128, 256)],
     "ratio": [dict(n_a=100_000, n_b=int(100_000 * r), D=4, alpha=0.01) for r in (0.125, 0.25, 0.5, 1.0)],
     "size": [dict(n_a=n, n_b=n, D=4, alpha=0.01) for n in (100_000, 250_000, 500_000, 1_000_000)],
+    # adaptive alpha (prohd_estimate_adaptive): alpha doubled from 0.25% up to
+    # 16% until the refined estimate grows by at most rel_tol
+    "adaptive": [dict(n_a=100_000, n_b=100_000, D=d, alpha=0.0025, alpha_max=0.16, rel_tol=t)
+                 for d in (4, 64, 256) for t in (1e-3, 1e-2)],
 }
 
 
@@ -84,6 +90,32 @@ def run_point(pt: dict, seeds: int, torch, power_max_iters: int | None = None) -
                 exact_ms=float(np.median(a["ms_exact"])), subset_frac=float(a["frac"].mean()))
 
 
+def run_adaptive_point(pt: dict, seeds: int, torch, power_max_iters: int | None = None) -> dict:
+    """One adaptive-alpha point averaged over ``seeds`` random-cloud pairs."""
+    ctx = prohd.context()
+    D = pt["D"]
+    m = max(1, int(math.isqrt(D)))
+    rows = []
+    for s in range(seeds):
+        A, B = W.random_clouds(pt["n_a"], pt["n_b"], D, seed=1000 * s + D)
+        At, Bt = torch.from_numpy(A).cuda(), torch.from_numpy(B).cuda()
+        p = prohd.default_params(m=m, alpha_c=pt["alpha"], precision="fp16", power_max_iters=power_max_iters)
+        (o, sched), t = _timed(lambda: ctx.prohd_estimate_adaptive(At, Bt, pt["alpha_max"], pt["rel_tol"],
+                                                                   params=p), torch)
+        r = prohd.decode_result(o)
+        ex = prohd.decode_hd(ctx.hausdorff_exact(At, Bt, "fp16"))
+        if r["status"] != "OK" or ex["status"] != "OK":
+            raise RuntimeError(f"status {r['status']} / {ex['status']} at {pt}, seed {s}")
+        rows.append(dict(err=(ex["H"] - r["H"]) / ex["H"], ms=t, steps=sched["steps"], alpha=sched["alpha_c"],
+                         frac=(r["nsel_a"] + r["nsel_b"]) / (pt["n_a"] + pt["n_b"]), reason=sched["reason"]))
+        del At, Bt
+    a = {k: np.array([r[k] for r in rows]) for k in rows[0] if k != "reason"}
+    return dict(pt, m=m, seeds=seeds, rel_err_mean=float(a["err"].mean()), rel_err_max=float(a["err"].max()),
+                ms=float(np.median(a["ms"])), steps_mean=float(a["steps"].mean()),
+                alpha_final_mean=float(a["alpha"].mean()), subset_frac=float(a["frac"].mean()),
+                reasons=sorted({r["reason"] for r in rows}))
+
+
 def run(which, seeds: int = 5, log=None, power_max_iters: int | None = None) -> dict:
     import torch
 
@@ -93,7 +125,8 @@ def run(which, seeds: int = 5, log=None, power_max_iters: int | None = None) -> 
     for name in which:
         res = []
         for pt in SWEEPS[name]:
-            r = run_point(pt, seeds, torch, power_max_iters)
+            point = run_adaptive_point if name == "adaptive" else run_point
+            r = point(pt, seeds, torch, power_max_iters)
             res.append(r)
             if log is not None:
                 print(json.dumps(dict(sweep=name, **r)), file=log, flush=True)
@@ -105,6 +138,17 @@ def markdown(out: dict) -> str:
     lines = []
     for name, res in out.items():
         lines.append(f"### {name}\n")
+        if name == "adaptive":
+            lines.append("| n_A | n_B | D | alpha_0 | alpha_max | rel_tol | steps | final alpha | subset "
+                         "| err (mean / max) | ms | stop |")
+            lines.append("|---:|---:|---:|---:|---:|---:|---:|---:|---:|---:|---:|---|")
+            for r in res:
+                lines.append(f"| {r['n_a']:,} | {r['n_b']:,} | {r['D']} | {r['alpha']} | {r['alpha_max']} "
+                             f"| {r['rel_tol']} | {r['steps_mean']:.1f} | {r['alpha_final_mean']:.4f} "
+                             f"| {100 * r['subset_frac']:.2f}% | {100 * r['rel_err_mean']:.2f}% / "
+                             f"{100 * r['rel_err_max']:.2f}% | {r['ms']:.2f} | {', '.join(r['reasons'])} |")
+            lines.append("")
+            continue
         lines.append("| n_A | n_B | D | alpha | subset | |err| Alg. 3 | above H | err refined (mean / max) "
                      "| ms Alg. 3 | ms refined | ms exact |")
         lines.append("|---:|---:|---:|---:|---:|---:|---:|---:|---:|---:|---:|")
@@ -119,7 +163,7 @@ def markdown(out: dict) -> str:
 
 def main(argv=None):
     ap = argparse.ArgumentParser(description=__doc__.split("\n\n")[0])
-    ap.add_argument("--which", default="alpha,dim,ratio,size")
+    ap.add_argument("--which", default="alpha,dim,ratio,size,adaptive")
     ap.add_argument("--seeds", type=int, default=5)
     ap.add_argument("--json", default=None, help="write the results here as one JSON object")
     ap.add_argument("--power-max-iters", type=int, default=None, help="cap of the direction stage's iterations")

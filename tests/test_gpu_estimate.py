@@ -148,3 +148,66 @@ def test_refine_must_be_zero_or_one():
     A, B = W.random_clouds(500, 400, 8, seed=1)
     with pytest.raises(prohd.ProHDError):
         prohd.prohd_estimate_sync(dev(A), dev(B), refine=2)
+
+
+def _adaptive(A, B, alpha, alpha_max, tol, m, prec):
+    torch = torch_cuda()
+    D = A.shape[1]
+    dirs = torch.empty((1 + m, D), dtype=torch.float64, device="cuda")
+    idxA = torch.empty(A.shape[0], dtype=torch.int32, device="cuda")
+    idxB = torch.empty(B.shape[0], dtype=torch.int32, device="cuda")
+    out, sched = prohd.context().prohd_estimate_adaptive(dev(A), dev(B), alpha_max, tol, m=m, alpha_c=alpha,
+                                                         precision=prec, idxA=idxA, idxB=idxB, dirs=dirs)
+    torch.cuda.synchronize()
+    r = prohd.decode_result(out)
+    assert r["status"] == "OK", r
+    d = dirs.cpu().numpy()
+    o = oracle.adaptive(A, B, alpha, alpha_max, tol, dirs=d)
+    assert sched["steps"] == o["steps"] and sched["reason"] == o["reason"], (sched, o["H"], o["reason"])
+    assert sched["nsel_a"] == o["nsel_a"] and sched["nsel_b"] == o["nsel_b"]
+    np.testing.assert_allclose(sched["H"], o["H"], rtol=1e-5)
+    assert sched["alpha_c"] == o["alpha"] and sched["alpha_p"] == pytest.approx(o["alpha_p"], rel=1e-15)
+    np.testing.assert_array_equal(idxA[: r["nsel_a"]].cpu().numpy(), o["idxA"])
+    np.testing.assert_array_equal(idxB[: r["nsel_b"]].cpu().numpy(), o["idxB"])
+    assert r["H"] == sched["H"][-1]
+    # never decreasing along the schedule
+    assert all(b >= a for a, b in zip(sched["H"], sched["H"][1:]))
+    return r, sched, o
+
+
+@pytest.mark.parametrize("prec", ["fp16", "fp32"])
+def test_adaptive_alpha_matches_oracle(prec):
+    # N(0,I16) vs N(0.5,I16) with outliers; doubling 0.5% -> at most 32%
+    A, B = W.gaussian_outliers(6_001, 5_003, 16, seed=11)
+    _adaptive(A, B, 0.005, 0.3, 0.0, 2, prec)
+
+
+def test_adaptive_alpha_stable_stop_d64():
+    A, _ = W.mixture_pair(20_000, 64, 8, seed=12)
+    _, B = W.mixture_pair(17_771, 64, 8, seed=13)
+    r, sched, _ = _adaptive(A, B, 0.0025, 0.05, 0.01, 4, "bf16")
+    assert sched["reason"] in ("stable", "budget")
+
+
+def test_adaptive_alpha_reaches_the_exact_hd():
+    # alpha 1% doubled up to 64% keeps every point (k >= n/2 per side): H
+    A, B = W.random_clouds(4_000, 3_001, 8, seed=14)
+    r, sched, _ = _adaptive(A, B, 0.01, 0.99, 0.0, 2, "fp16")
+    if sched["reason"] == "all":
+        assert rel(r["H"], oracle.hausdorff(A, B)["H"]) <= 1e-5
+    assert r["H"] <= oracle.hausdorff(A, B)["H"] * (1 + 1e-7)
+
+
+def test_adaptive_alpha_single_step_and_bad_arguments():
+    torch = torch_cuda()
+    A, B = W.random_clouds(2_000, 1_500, 4, seed=15)
+    out, sched = prohd.context().prohd_estimate_adaptive(dev(A), dev(B), 0.02, 0.0, m=1, alpha_c=0.02)
+    torch.cuda.synchronize()
+    assert sched["steps"] == 1 and sched["reason"] == "budget"
+    r = prohd.decode_result(out)
+    r1 = prohd.prohd_estimate_sync(dev(A), dev(B), m=1, alpha_c=0.02, refine=1)
+    assert r["H"] == r1["H"] and r["nsel_a"] == r1["nsel_a"]
+    with pytest.raises(prohd.ProHDError):
+        prohd.context().prohd_estimate_adaptive(dev(A), dev(B), 0.01, 0.0, m=1, alpha_c=0.02)
+    with pytest.raises(prohd.ProHDError):
+        prohd.context().prohd_estimate_adaptive(dev(A), dev(B), 0.5, -1.0, m=1, alpha_c=0.02)

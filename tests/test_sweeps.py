@@ -10,6 +10,7 @@ def test_sweep_grid_matches_the_studies():
     assert [p["n_b"] / p["n_a"] for p in sweeps.SWEEPS["ratio"]] == [0.125, 0.25, 0.5, 1.0]
     assert [p["n_a"] + p["n_b"] for p in sweeps.SWEEPS["size"]] == [200_000, 500_000, 1_000_000, 2_000_000]
     assert all(p["alpha"] == 0.01 for k in ("dim", "ratio", "size") for p in sweeps.SWEEPS[k])
+    assert all(p["alpha_max"] >= p["alpha"] for p in sweeps.SWEEPS["adaptive"])
 
 
 def test_markdown_table():
@@ -29,3 +30,7 @@ def test_one_small_point_on_the_gpu():
     # the refinement never exceeds the exact HD
     assert r["refined_rel_err_max"] < 1.0 and r["refined_rel_err_mean"] >= -1e-6
     assert 0 < r["subset_frac"] < 1 and r["exact_ms"] > 0
+    a = sweeps.run_adaptive_point(dict(n_a=3000, n_b=1500, D=4, alpha=0.005, alpha_max=0.16, rel_tol=1e-3), seeds=2,
+                                  torch=torch)
+    assert a["rel_err_mean"] >= -1e-6 and a["steps_mean"] >= 1
+    assert "adaptive" in sweeps.markdown({"adaptive": [a]})
