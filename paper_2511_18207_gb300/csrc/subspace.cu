@@ -10,7 +10,9 @@
 //   V orthonormal (D x b); W = C V; H = V^T W; H = Y diag(theta) Y^T (Jacobi);
 //   Ritz vectors X = V Y, residuals r_j = W y_j - theta_j x_j;
 //   stop when ||r_j|| <= eps theta_1 for the m leading pairs, else
-//   V = orth((W Y + sigma X) diag(1 / (theta + sigma))) by Cholesky-QR, twice.
+//   V = orth((W Y + sigma X) diag(1 / (theta + sigma))) by Cholesky-QR, twice;
+//   also stop (at the cap, or earlier once the observed rate shows the cap
+//   cannot be met: the stall test below) with the current Ritz vectors.
 // The error of the leading m Ritz vectors falls like ((lambda_{b+1} + sigma) /
 // (lambda_m + sigma))^t, against lambda_{l+1}/lambda_l per step for each
 // vector of the power iteration. The shift sigma = theta_1 / 100 bounds the
@@ -47,6 +49,8 @@ constexpr int kSiFinThreads = 256;
 constexpr int kSiJacThreads = 256;  // the Jacobi rounds run on 8 warps (one warp alone is slower: the rounds are latency-bound)
 constexpr int kSiMaxD = 256;
 constexpr int kSiMaxB = 32;
+constexpr int kSiStallWin = 16;    // steps per window of the stall test
+constexpr int kSiStallStart = 48;  // no stall test before this step
 
 // block size for D dimensions and m components (D <= 256, m <= 24)
 __host__ __device__ inline int si_block(int D, int m) {
@@ -441,6 +445,10 @@ PROHD_DEV void subspace_body(SiSmemT<NC, ROWS, VLD>& S, const float* __restrict_
 
   int xb = 0;  // exchange buffer
   int t = 0;
+  // largest relative residual max_j ||r_j|| / theta_1 at the last two window
+  // boundaries (every thread holds the same values: they come from the
+  // summed shared-memory residuals)
+  float r_prev = 0.f, r_cur = 0.f;
   for (;; ++t) {
     if (t == 0) {
       // first pass only orthonormalises the start block
@@ -670,9 +678,31 @@ PROHD_DEV void subspace_body(SiSmemT<NC, ROWS, VLD>& S, const float* __restrict_
       bool done = t >= maxit;
       const float lim = eps * fmaxf(S.theta[0], 0.f);
       bool conv = true, bad = !(lim == lim);
+      float rmax = 0.f;
       for (int j = 0; j < m; ++j) {
         conv = conv && (sqrtf(S.res[j]) <= lim);
         bad = bad || !(S.res[j] == S.res[j]);
+        rmax = fmaxf(rmax, sqrtf(S.res[j]));
+      }
+      // Stall: once past kSiStallStart steps, at every window boundary the
+      // observed contraction of the largest residual over the last window
+      // predicts the steps still needed to reach eps; when that does not fit
+      // in the cap (or the residual no longer falls: the FP32 floor), stop
+      // now with the current Ritz vectors rather than at the cap. Nearly
+      // degenerate spectra (isotropic clouds, D > 32) converge at rates of
+      // 0.99 per step or slower and would otherwise run to the cap.
+      if (!conv && t % kSiStallWin == 0) {
+        r_prev = r_cur;
+        r_cur = S.theta[0] > 0.f ? rmax / S.theta[0] : 0.f;
+        if (t >= kSiStallStart && r_prev > 0.f) {
+          const float rate = r_cur / r_prev;
+          if (!(rate < 1.f)) {
+            done = true;
+          } else {
+            const float need = (float)kSiStallWin * logf(eps / r_cur) / logf(rate);
+            done = done || (float)t + need > (float)maxit;
+          }
+        }
       }
       if (done || conv || bad) {  // NaN input: stop (the Gram pass flags it)
         for (int e = tid; e < nr * m; e += kSiThreads) {
