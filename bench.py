@@ -375,6 +375,20 @@ def gpu_arm(args):
         torch.cuda.synchronize()
         exact = prohd.decode_hd(hout)
         exact["ms"] = e0.elapsed_time(e1)
+        # the same exact distance with row pruning (a sampled lower bound, a
+        # prefix contraction that drops rows certainly below it, the exact
+        # path on the rest)
+        pws = ctx.workspace(ctx.lib.hausdorff_exact_pruned_workspace_size(n, n, DIM, 1))
+        pout = torch.empty(ctypes.sizeof(prohd.HdResult), dtype=torch.uint8, device=dev)
+        e0.record(st)
+        ctx.hausdorff_exact_pruned(At, Bt, "fp16", out=pout, ws=pws)
+        e1.record(st)
+        torch.cuda.synchronize()
+        pr = prohd.decode_hd(pout)
+        _, kept = ctx.hausdorff_exact_pruned(At, Bt, "fp16", out=pout, ws=pws, want_kept=True)
+        exact["pruned"] = {"ms": e0.elapsed_time(e1), "H": pr["H"], "status": pr["status"], "rows_kept": kept,
+                           "equals_dense": pr["H"] == exact["H"]}
+        del pws
         ws = ctx.workspace(ws_need)
     clk = clocks.stop()
 
@@ -472,6 +486,7 @@ def gpu_arm(args):
         "H_hat": res16["H"], "H_exact": H, "rel_err_vs_exact": (abs(res16["H"] - H) / H) if H else None,
         "signed_err": ((res16["H"] - H) / H) if H else None,
         "exact_ms": exact["ms"] if exact else None,
+        "exact_pruned": exact.get("pruned") if exact else None,
         "speedup_vs_gpu_exact": (exact["ms"] / ms_step) if exact else None,
         "nsel": [nsa, nsb], "status": res16["status"], "exact_status": exact["status"] if exact else None,
         "rescored": [res16["n_rescored_a"], res16["n_rescored_b"]],

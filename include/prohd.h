@@ -167,6 +167,27 @@ prohd_status hausdorff_exact(prohd_ctx* ctx, const float* A, int64_t nA, const f
                              void* stream);
 
 /*
+ * The same exact distance with row pruning (the early-break idea of exact
+ * Hausdorff algorithms, Sec. II, as whole-set passes): for each direction
+ * h(X, Y), an exact pass over 1,024 evenly spread rows of X gives a lower
+ * bound LB1 of h(X, Y); one tensor-core contraction of every row of X
+ * against the first max(8192, n_Y / 64) rows of Y gives each row a certified
+ * upper bound of its NN distance; an exact pass over 1,024 evenly spread rows
+ * of those whose bound reaches LB1 gives LB2; the exact path of
+ * hausdorff_exact runs on the rows whose bound reaches max(LB1, LB2)
+ * (lowered by 1e-4 relative). The row attaining
+ * h(X, Y) always stays, so out equals hausdorff_exact's result up to the
+ * FP32 argmin of rows within 1e-4 of the maximum. FP16/BF16 and
+ * nA, nB >= 32768 only; otherwise (and for PROHD_FP32) this is
+ * hausdorff_exact. kept (HOST, may be NULL) receives the rows left in each
+ * direction ({-1, -1} without pruning); passing it synchronises `stream`.
+ */
+size_t hausdorff_exact_pruned_workspace_size(int64_t nA, int64_t nB, int D, int precision);
+prohd_status hausdorff_exact_pruned(prohd_ctx* ctx, const float* A, int64_t nA, const float* B, int64_t nB, int D,
+                                    int precision, prohd_hd_result* out, int64_t* kept, void* ws, size_t ws_bytes,
+                                    void* stream);
+
+/*
  * Projection directions (Algorithm 1 step 2 and Algorithm 2 step 2):
  *   dirs[0]      centroid axis u = (ybar - xbar)/||ybar - xbar||, or e_1 when
  *                ||ybar - xbar|| < 1e-9

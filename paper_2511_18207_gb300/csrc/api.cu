@@ -48,6 +48,52 @@ __global__ void refine_combine_kernel(const prohd_hd_result* r1, const prohd_hd_
   out->hd = r;
 }
 
+// idx[i] = floor(i n / S): S rows spread evenly over n
+__global__ void strided_idx_kernel(int32_t* idx, int64_t S, int64_t n) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < S; i += (int64_t)gridDim.x * blockDim.x)
+    idx[i] = (int32_t)((i * n) / S);
+}
+
+// mask[i] = hi[i] >= scale * max(*lb1, *lb2) (lb2 may be null)
+__global__ void keep_mask_kernel(const float* __restrict__ hi, int64_t n, const double* lb1, const double* lb2,
+                                 double scale, uint8_t* __restrict__ mask) {
+  const double L = scale * (lb2 ? fmax(*lb1, *lb2) : *lb1);
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    mask[i] = (double)hi[i] >= L ? 1 : 0;
+}
+
+// S = min(Smax, *nlist) entries of list spread evenly: idx[i] = list[floor(i nlist / S)]
+__global__ void strided_sub_kernel(int32_t* __restrict__ idx, int64_t* __restrict__ nS, int64_t Smax,
+                                   const int32_t* __restrict__ list, const int64_t* __restrict__ nlist) {
+  const int64_t n = *nlist;
+  const int64_t S = n < Smax ? n : Smax;
+  for (int64_t i = threadIdx.x; i < S; i += blockDim.x) idx[i] = list[(i * n) / S];
+  if (threadIdx.x == 0) *nS = S;
+}
+
+// The two directed results of the pruned exact distance: r1 = h(A, B) in its
+// h_ab (witness ab_a in A, ab_b in B), r2 = h(B, A) in its h_ab with the sets'
+// roles swapped.
+__global__ void directed_combine_kernel(const prohd_hd_result* r1, const prohd_hd_result* r2, prohd_hd_result* out) {
+  prohd_hd_result r;
+  const prohd_hd_result a = *r1, b = *r2;
+  r.h_ab = a.h_ab;
+  r.h_ba = b.h_ab;
+  r.ab_a = a.ab_a;
+  r.ab_b = a.ab_b;
+  r.ba_b = b.ab_a;
+  r.ba_a = b.ab_b;
+  r.dir = r.h_ab >= r.h_ba ? 0 : 1;
+  r.H = r.dir == 0 ? r.h_ab : r.h_ba;
+  r.wit_a = r.dir == 0 ? r.ab_a : r.ba_a;
+  r.wit_b = r.dir == 0 ? r.ab_b : r.ba_b;
+  r.status = a.status > b.status ? a.status : b.status;
+  r.H_lowp = fmax(a.H_lowp, b.H_lowp);
+  r.n_rescored_a = a.n_rescored_a;
+  r.n_rescored_b = b.n_rescored_a;
+  *out = r;
+}
+
 cudaError_t set_i64(int64_t* p, int64_t v, cudaStream_t st) {
   count_launch();
   set_i64_kernel<<<1, 1, 0, st>>>(p, v);
@@ -614,6 +660,194 @@ prohd_status prohd_estimate_dirs(prohd_ctx* ctx, const float* A, int64_t nA, con
   est_layout_k(a, nA, nB, D, nd, kA, kB, p->precision, -1, L, p->refine != 0);
   return estimate_run(ctx, A, nA, B, nB, D, p, L, out, idxA, idxB, nullptr, dirs, static_cast<char*>(ws), ws_bytes,
                       reinterpret_cast<cudaStream_t>(stream));
+}
+
+// ---------------------------------------------------------------- exact distance with row pruning
+
+constexpr int64_t kPruneSample = 1024;   // rows of the lower-bound sample
+constexpr int64_t kPruneMinRows = 32768; // smaller sets take the plain contraction
+// The sample's distance is the FP64 length of the FP32 nearest neighbour of
+// its row, which can exceed the row's true NN distance by the FP32 rounding
+// of D-term squared sums (under 2^-24 D relative); the pruning threshold is
+// lowered by 1e-4 relative to stay below the true distance.
+constexpr double kPruneScale = 1.0 - 1e-4;
+
+// columns of Y the pruning contraction scans: n_Y / 64, at least 8192, whole tiles
+static int64_t prune_prefix(int64_t nY) {
+  const int64_t p = std::max<int64_t>(8192, nY / 64);
+  return std::min(nY, (p + 255) / 256 * 256);
+}
+static bool prune_applies(int64_t nA, int64_t nB, int precision) {
+  return precision != PROHD_FP32 && nA >= kPruneMinRows && nB >= kPruneMinRows;
+}
+
+namespace {
+struct PruneLayout {
+  int* status;
+  int64_t *nA, *nB, *nS, *nAp, *nBp, *nkeep;
+  int32_t* sidx;
+  float* Xs;
+  prohd_hd_result *rs, *rk;  // rs [4]: the two samples' results per direction; rk [2]: kept rows' results
+  float* hi;                 // certified upper bounds of the rows' NN distances
+  uint8_t* mask;
+  unsigned* counts;
+  int64_t* offsets;
+  int32_t* kidx;
+  float* Xk;
+  size_t mark;
+};
+void prune_layout(Arena& a, int64_t nA, int64_t nB, int D, int precision, PruneLayout& L) {
+  const int64_t nmax = std::max(nA, nB);
+  const int64_t S = std::min(kPruneSample, std::min(nA, nB));
+  L.status = a.take<int>(8);
+  L.nA = a.take<int64_t>(1);
+  L.nB = a.take<int64_t>(1);
+  L.nS = a.take<int64_t>(1);
+  L.nAp = a.take<int64_t>(1);
+  L.nBp = a.take<int64_t>(1);
+  L.nkeep = a.take<int64_t>(1);
+  L.sidx = a.take<int32_t>((size_t)S);
+  L.Xs = a.take<float>((size_t)S * D);
+  L.rs = a.take<prohd_hd_result>(4);
+  L.rk = a.take<prohd_hd_result>(2);
+  L.hi = a.take<float>((size_t)nmax);
+  L.mask = a.take<uint8_t>((size_t)nmax);
+  L.counts = a.take<unsigned>((size_t)compact_blocks(nmax));
+  L.offsets = a.take<int64_t>((size_t)compact_blocks(nmax));
+  L.kidx = a.take<int32_t>((size_t)nmax);
+  L.Xk = a.take<float>((size_t)nmax * D);
+  // the passes run one after another in the rest of the arena
+  L.mark = (a.off + 255) / 256 * 256;
+  size_t end = a.off;
+  for (int dir = 0; dir < 2; ++dir) {
+    const int64_t nX = dir == 0 ? nA : nB, nY = dir == 0 ? nB : nA;
+    Arena t = a;
+    hd_core_layout(t, S, nY, D, precision);
+    end = std::max(end, t.off);
+    t = a;
+    hd_prefix_layout(t, nX, prune_prefix(nY), D, precision);
+    end = std::max(end, t.off);
+    t = a;
+    hd_core_layout(t, nX, nY, D, precision);
+    end = std::max(end, t.off);
+  }
+  a.off = end;
+}
+}  // namespace
+
+// h(X, Y) with row pruning. h over an evenly spread sample of rows of X is a
+// lower bound LB1 of h(X, Y); one contraction of every row against the first
+// prune_prefix(n_Y) rows of Y gives each row a certified upper bound of its
+// NN distance; the rows whose bound reaches LB1 are the hard ones, and h over
+// an evenly spread sample of those is a second, larger lower bound LB2. The
+// exact path then runs on the rows whose bound reaches max(LB1, LB2). Every
+// lower bound is a row's own distance, so the row attaining h(X, Y) always
+// stays and the result equals the plain one.
+static cudaError_t pruned_directed(prohd_ctx* ctx, const float* X, int64_t nX, const float* Y, int64_t nY, int D,
+                                   int precision, PruneLayout& L, int dir, char* wsb, size_t ws_bytes,
+                                   cudaStream_t st) {
+  const int64_t S = std::min(kPruneSample, nX);
+  const int64_t nYp = prune_prefix(nY);
+  int64_t* nXd = dir == 0 ? L.nA : L.nB;
+  int64_t* nYd = dir == 0 ? L.nB : L.nA;
+  int64_t* nYpd = dir == 0 ? L.nBp : L.nAp;
+  const int nsm = ctx->num_sms;
+  auto phase = [&]() {
+    Arena t;
+    t.base = wsb;
+    t.cap = ws_bytes;
+    t.off = L.mark;
+    return t;
+  };
+  // the kept rows are few (a small share of n_max): the contraction cuts
+  // the columns into segments so that every SM works
+  auto exact_rows = [&](const int32_t* idx, const int64_t* n_dev, int64_t n_max, float* rows, prohd_hd_result* r) {
+    cudaError_t e2 = gather_rows(X, D, idx, n_dev, n_max, rows, nsm, st);
+    if (e2) return e2;
+    Arena t = phase();
+    return hd_core(ctx, rows, n_dev, n_max, Y, nYd, nY, D, precision, idx, nullptr, r, L.status, t, kDefaultTimeoutNs,
+                   st, true);
+  };
+  auto keep = [&](const double* lb2) {
+    count_launch();
+    keep_mask_kernel<<<nsm * 2, 256, 0, st>>>(L.hi, nX, &L.rs[dir].h_ab, lb2, kPruneScale, L.mask);
+    cudaError_t e2 = cudaGetLastError();
+    return e2 ? e2 : mask_to_indices(L.mask, nX, L.kidx, L.nkeep, L.counts, L.offsets, st);
+  };
+  cudaError_t e = set_i64(L.nS, S, st);
+  if (!e) e = set_i64(nYpd, nYp, st);
+  if (!e) {
+    count_launch();
+    strided_idx_kernel<<<8, 128, 0, st>>>(L.sidx, S, nX);
+    e = cudaGetLastError();
+  }
+  if (!e) e = exact_rows(L.sidx, L.nS, S, L.Xs, L.rs + dir);  // LB1
+  if (!e) {
+    Arena t = phase();
+    e = hd_prefix_upper(ctx, X, nXd, nX, Y, nYpd, nYp, D, precision, L.hi, L.status, t, kDefaultTimeoutNs, st);
+  }
+  if (!e) e = keep(nullptr);
+  if (!e) {
+    count_launch();
+    strided_sub_kernel<<<1, 1024, 0, st>>>(L.sidx, L.nS, S, L.kidx, L.nkeep);
+    e = cudaGetLastError();
+  }
+  if (!e) e = exact_rows(L.sidx, L.nS, S, L.Xs, L.rs + 2 + dir);  // LB2
+  if (!e) e = keep(&L.rs[2 + dir].h_ab);
+  if (!e) e = exact_rows(L.kidx, L.nkeep, nX, L.Xk, L.rk + dir);
+  return e;
+}
+
+size_t hausdorff_exact_pruned_workspace_size(int64_t nA, int64_t nB, int D, int precision) {
+  if (bad_n(nA) || bad_n(nB) || D < 1) return 0;
+  if (!prune_applies(nA, nB, precision)) return hausdorff_exact_workspace_size(nA, nB, D, precision);
+  Arena a;
+  PruneLayout L;
+  prune_layout(a, nA, nB, D, precision, L);
+  return a.off + 256;
+}
+
+prohd_status hausdorff_exact_pruned(prohd_ctx* ctx, const float* A, int64_t nA, const float* B, int64_t nB, int D,
+                                    int precision, prohd_hd_result* out, int64_t* kept, void* ws, size_t ws_bytes,
+                                    void* stream) {
+  if (!prune_applies(nA, nB, precision)) {
+    if (kept) kept[0] = kept[1] = -1;
+    return hausdorff_exact(ctx, A, nA, B, nB, D, precision, out, ws, ws_bytes, stream);
+  }
+  prohd_status s = check_sets(ctx, A, nA, B, nB, D);
+  if (s) return s;
+  if (!out) return fail(ctx, PROHD_EINVAL, "null output%s");
+  if (precision != PROHD_FP16 && precision != PROHD_BF16) return fail(ctx, PROHD_EINVAL, "unknown precision%s");
+  if (!tc_supported_dim(D)) return fail(ctx, PROHD_ENOTSUP, "tensor-core precisions need D <= 256 (use PROHD_FP32)%s");
+  if ((s = check_ws(ctx, ws, ws_bytes, hausdorff_exact_pruned_workspace_size(nA, nB, D, precision)))) return s;
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  char* wsb = static_cast<char*>(ws);
+  Arena a;
+  a.base = wsb;
+  a.cap = ws_bytes;
+  PruneLayout L;
+  prune_layout(a, nA, nB, D, precision, L);
+  if (a.overflow()) return fail(ctx, PROHD_ENOMEM, "workspace too small%s");
+  cudaError_t e = zero_i32(L.status, 8, st);
+  if (!e) e = set_i64(L.nA, nA, st);
+  if (!e) e = set_i64(L.nB, nB, st);
+  int64_t keep_host[2] = {-1, -1};
+  for (int dir = 0; dir < 2 && !e; ++dir) {
+    e = dir == 0 ? pruned_directed(ctx, A, nA, B, nB, D, precision, L, 0, wsb, ws_bytes, st)
+                 : pruned_directed(ctx, B, nB, A, nA, D, precision, L, 1, wsb, ws_bytes, st);
+    if (!e && kept) e = cudaMemcpyAsync(&keep_host[dir], L.nkeep, sizeof(int64_t), cudaMemcpyDeviceToHost, st);
+    if (!e && kept) e = cudaStreamSynchronize(st);
+  }
+  if (!e) {
+    count_launch();
+    directed_combine_kernel<<<1, 1, 0, st>>>(L.rk, L.rk + 1, out);
+    e = cudaGetLastError();
+  }
+  if (kept) {
+    kept[0] = keep_host[0];
+    kept[1] = keep_host[1];
+  }
+  return e ? cuda_fail(ctx, e) : PROHD_OK;
 }
 
 // ---------------------------------------------------------------- adaptive alpha

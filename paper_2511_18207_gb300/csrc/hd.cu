@@ -556,10 +556,14 @@ __host__ __device__ constexpr size_t tc_smem_bytes(int KB) {
 }
 
 // One unit of contraction work: row block rb of A against the CB column
-// tiles of B, with the pair's operand maps, depth KB and minima.
+// tiles of B starting at tile cb0, with the pair's operand maps, depth KB and
+// minima. seg: the row block's columns are split over several items, so its
+// row minima are combined with atomicMin (the buffer starts at +inf) rather
+// than stored.
 struct TcItem {
   const CUtensorMap *tmA, *tmB, *tmNA, *tmNB;
-  int KB, CB, rb;
+  int KB, CB, cb0, rb;
+  bool seg;
   float* rowmin;
   unsigned* colmin;
 };
@@ -574,8 +578,30 @@ struct TcItemsOne {
     const int rb = (int)blockIdx.x + k * (int)gridDim.x;
     if (rb >= RB) return false;
     it.tmA = tmA; it.tmB = tmB; it.tmNA = tmNA; it.tmNB = tmNB;
-    it.KB = KB; it.CB = CB; it.rb = rb; it.rowmin = rowmin; it.colmin = colmin;
+    it.KB = KB; it.CB = CB; it.cb0 = 0; it.seg = false; it.rb = rb; it.rowmin = rowmin; it.colmin = colmin;
     return true;
+  }
+};
+
+// The items of one pair with the columns cut into segments (a few rows
+// against many columns): item g = blockIdx.x + k gridDim.x is segment g % NS
+// of row block g / NS, the CBall column tiles cut into NS non-empty segments
+// of at most CS tiles, so that every CTA gets about two items.
+struct TcItemsSeg {
+  const CUtensorMap *tmA, *tmB, *tmNA, *tmNB;
+  int KB, RB, CBall, NS, CS;
+  float* rowmin;
+  unsigned* colmin;
+  __device__ bool get(int k, TcItem& it) const {
+    const int64_t g = (int64_t)blockIdx.x + (int64_t)k * gridDim.x;
+    if (g >= (int64_t)RB * NS) return false;
+    const int rb = (int)(g / NS), sg = (int)(g - (int64_t)rb * NS);
+    it.tmA = tmA; it.tmB = tmB; it.tmNA = tmNA; it.tmNB = tmNB;
+    it.KB = KB; it.rb = rb; it.rowmin = rowmin; it.colmin = colmin;
+    it.cb0 = sg * CS;
+    it.CB = min(CS, CBall - it.cb0);
+    it.seg = NS > 1;
+    return it.CB > 0;
   }
 };
 
@@ -602,6 +628,8 @@ struct TcItemsBatch {
     it.tmA = m; it.tmB = m + 1; it.tmNA = m + 2; it.tmNB = m + 3;
     it.KB = q.Dp / kTcBK;
     it.CB = (int)((q.nsel[1] + kTcBN - 1) / kTcBN);
+    it.cb0 = 0;
+    it.seg = false;
     it.rb = (int)(i - prefix[lo]);
     it.rowmin = q.hd_rowmin;
     it.colmin = q.hd_colmin;
@@ -671,12 +699,12 @@ __device__ __forceinline__ void hd_tc_body(const Items& items, int KBmax, int* _
           const uint32_t ns = tile & 1u, nph = (tile >> 1) & 1u;
           if (!mbar_wait_bounded(&S.nb_empty[ns], nph ^ 1, abort, timeout_ns)) { ok = false; break; }
           mbar_arrive_expect_tx(&S.nb_full[ns], (uint32_t)kTcNBBytes);
-          tma_load_2d(sNB + ns * kTcNBBytes, it.tmNB, 0, cb * kTcBN, &S.nb_full[ns]);
+          tma_load_2d(sNB + ns * kTcNBBytes, it.tmNB, 0, (it.cb0 + cb) * kTcBN, &S.nb_full[ns]);
           ++nb_issued;
           for (int kb = 0; kb < KB; ++kb) {
             if (!mbar_wait_bounded(&S.b_empty[st], ph ^ 1, abort, timeout_ns)) { ok = false; break; }
             mbar_arrive_expect_tx(&S.b_full[st], (uint32_t)kTcBStage);
-            tma_load_2d(sB + st * kTcBStage, it.tmB, kb * kTcBK, cb * kTcBN, &S.b_full[st]);
+            tma_load_2d(sB + st * kTcBStage, it.tmB, kb * kTcBK, (it.cb0 + cb) * kTcBN, &S.b_full[st]);
             armed |= 1u << st;
             armed_ph = (armed_ph & ~(1u << st)) | (ph << st);
             if (++st == kTcStages) { st = 0; ph ^= 1; }
@@ -803,15 +831,21 @@ __device__ __forceinline__ void hd_tc_body(const Items& items, int KBmax, int* _
         const int c = et;
         float m = fminf(fminf(S.col[ab][0][c], S.col[ab][1][c]), fminf(S.col[ab][2][c], S.col[ab][3][c]));
         m = fmaxf(m, 0.f);
-        atomicMin(colmin + (int64_t)cb * kTcBN + c, __float_as_uint(m));
+        atomicMin(colmin + (int64_t)(it.cb0 + cb) * kTcBN + c, __float_as_uint(m));
       }
       if (cb == CB - 1) {
         // the four warps of a lane quarter saw a quarter of the columns each
         if (grp > 0) S.rowx[grp - 1][q * 32 + lane] = rmin;
         named_bar_sync(1, 32 * kTcEpiWarps);
-        if (ok && grp == 0)
-          rowmin[(int64_t)rb * kTcBM + q * 32 + lane] =
+        if (ok && grp == 0) {
+          const float r =
               fminf(fminf(rmin, S.rowx[0][q * 32 + lane]), fminf(S.rowx[1][q * 32 + lane], S.rowx[2][q * 32 + lane]));
+          float* dst = rowmin + (int64_t)rb * kTcBM + q * 32 + lane;
+          // clamped at 0 so unsigned order = float order (the margins treat
+          // a negative low-precision d2 as 0 anyway)
+          if (it.seg) atomicMin(reinterpret_cast<unsigned*>(dst), __float_as_uint(fmaxf(r, 0.f)));
+          else *dst = r;
+        }
         rmin = __int_as_float(0x7f800000);
       }
     }
@@ -826,7 +860,7 @@ __device__ __forceinline__ void hd_tc_body(const Items& items, int KBmax, int* _
   }
 }
 
-template <int BF16>
+template <int BF16, bool SEG>
 __global__ void __launch_bounds__(kTcThreads, 1)
     hd_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
                  const __grid_constant__ CUtensorMap tmNA, const __grid_constant__ CUtensorMap tmNB,
@@ -834,15 +868,34 @@ __global__ void __launch_bounds__(kTcThreads, 1)
                  float* __restrict__ rowmin, unsigned* __restrict__ colmin, int* __restrict__ status,
                  uint64_t timeout_ns) {
   const int64_t nA = *nA_dev, nB = *nB_dev;
-  TcItemsOne items;
-  items.tmA = &tmA; items.tmB = &tmB; items.tmNA = &tmNA; items.tmNB = &tmNB;
-  items.KB = KB;
-  items.RB = (int)((nA + kTcBM - 1) / kTcBM);
-  items.CB = (int)((nB + kTcBN - 1) / kTcBN);
-  items.rowmin = rowmin;
-  items.colmin = colmin;
   const CUtensorMap* pf[4] = {&tmA, &tmB, &tmNA, &tmNB};
-  hd_tc_body<BF16>(items, KB, status, timeout_ns, pf);
+  if constexpr (!SEG) {
+    TcItemsOne items;
+    items.tmA = &tmA; items.tmB = &tmB; items.tmNA = &tmNA; items.tmNB = &tmNB;
+    items.KB = KB;
+    items.RB = (int)((nA + kTcBM - 1) / kTcBM);
+    items.CB = (int)((nB + kTcBN - 1) / kTcBN);
+    items.rowmin = rowmin;
+    items.colmin = colmin;
+    hd_tc_body<BF16>(items, KB, status, timeout_ns, pf);
+  } else {
+    TcItemsSeg items;
+    items.tmA = &tmA; items.tmB = &tmB; items.tmNA = &tmNA; items.tmNB = &tmNB;
+    items.KB = KB;
+    items.RB = (int)((nA + kTcBM - 1) / kTcBM);
+    items.CBall = (int)((nB + kTcBN - 1) / kTcBN);
+    // fewer than two row blocks per CTA: cut the columns into segments so
+    // that every CTA gets about two items (the row minima buffer starts at +inf)
+    const int want = 2 * (int)gridDim.x;
+    items.NS = items.RB >= want ? 1 : min(items.CBall, (want + items.RB - 1) / items.RB);
+    items.NS = max(items.NS, 1);
+    items.CS = (items.CBall + items.NS - 1) / items.NS;
+    // no empty segment: an item list must not end before its last item
+    items.NS = max(1, (items.CBall + items.CS - 1) / items.CS);
+    items.rowmin = rowmin;
+    items.colmin = colmin;
+    hd_tc_body<BF16>(items, KB, status, timeout_ns, pf);
+  }
 }
 
 // Batched: every pair's row blocks against its own column tiles, the maps in
@@ -1257,33 +1310,15 @@ static cudaError_t launch_simt(bool row_list, bool want_row, bool want_col, cons
   return cudaGetLastError();
 }
 
-cudaError_t hd_core(prohd_ctx* ctx, const float* A, const int64_t* nA_dev, int64_t nA_max, const float* B,
-                    const int64_t* nB_dev, int64_t nB_max, int D, int precision, const int32_t* mapA,
-                    const int32_t* mapB, prohd_hd_result* out, int* status_dev, Arena& ws, int64_t timeout_ns,
-                    cudaStream_t st) {
-  HdBufs b;
-  layout(ws, nA_max, nB_max, D, precision, b);
-  if (ws.overflow()) return cudaErrorMemoryAllocation;
+// Rounded copies, norms and margins of A and B, then the tensor-core
+// contraction into b.rowmin / b.colmin (squared low-precision minima, scaled
+// units). c1 receives the margin constant of row_interval.
+static cudaError_t tc_prep_contract(prohd_ctx* ctx, const float* A, const int64_t* nA_dev, const float* B,
+                                    const int64_t* nB_dev, int D, int precision, HdBufs& b, int* status_dev,
+                                    int64_t timeout_ns, cudaStream_t st, double& c1, bool few_rows = false) {
+  if (!tc_supported_dim(D)) return cudaErrorInvalidValue;
   const int nsm = ctx->num_sms;
   cudaError_t e;
-
-  if (precision == PROHD_FP32) {
-    count_launch();
-    fill_u64_kernel<<<nsm * 4, 256, 0, st>>>(b.bestA, nA_max, ~0ull);
-    count_launch();
-    fill_u64_kernel<<<nsm * 4, 256, 0, st>>>(b.bestB, nB_max, ~0ull);
-    {
-      PhaseTimer pt(ctx, PROHD_PH_HD_CONTRACT, st);
-      if ((e = launch_simt(false, true, true, A, nullptr, nA_dev, B, nB_dev, D, b.bestA, b.bestB, nsm, st))) return e;
-    }
-    PhaseTimer pt2(ctx, PROHD_PH_HD_RESCORE, st);
-    count_launch();
-    hd_finalize_kernel<<<1, 1024, 0, st>>>(A, nA_dev, B, nB_dev, D, b.bestA, nullptr, nA_dev, b.bestB, nullptr,
-                                           nB_dev, mapA, mapB, nullptr, status_dev, out);
-    return cudaGetLastError();
-  }
-
-  if (!tc_supported_dim(D)) return cudaErrorInvalidValue;
   const int bf16 = precision == PROHD_BF16 ? 1 : 0;
   const int KB = b.Dp / kTcBK;
 
@@ -1318,6 +1353,8 @@ cudaError_t hd_core(prohd_ctx* ctx, const float* A, const int64_t* nA_dev, int64
   }
   count_launch();
   fill_u32_kernel<<<nsm * 2, 256, 0, st>>>(b.colmin, b.nB_pad, 0x7f800000u);
+  count_launch();
+  fill_u32_kernel<<<nsm, 256, 0, st>>>(reinterpret_cast<unsigned*>(b.rowmin), b.nA_pad, 0x7f800000u);
   if ((e = cudaGetLastError())) return e;
 
   CUtensorMap tmA, tmB;
@@ -1334,26 +1371,63 @@ cudaError_t hd_core(prohd_ctx* ctx, const float* A, const int64_t* nA_dev, int64
     return cudaErrorInvalidValue;
   pt_prep.stop();
   const size_t smem = tc_smem_bytes(KB);
-  const int grid = (int)std::min<int64_t>(nsm, b.nA_pad / kTcBM);
+  // few row blocks (by the bound, or as the caller expects from a device
+  // count): one CTA per SM with the columns cut into segments
+  const bool seg = few_rows || b.nA_pad / kTcBM < 2 * (int64_t)nsm;
+  const int grid = seg ? nsm : (int)std::min<int64_t>(nsm, b.nA_pad / kTcBM);
   PhaseTimer pt_tc(ctx, PROHD_PH_HD_CONTRACT, st);
+  auto go = [&](auto kern) {
+    cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    count_launch();
+    kern<<<grid, kTcThreads, smem, st>>>(tmA, tmB, tmNA, tmNB, nA_dev, nB_dev, KB, b.rowmin, b.colmin, status_dev,
+                                         (uint64_t)timeout_ns);
+  };
   if (bf16) {
-    cudaFuncSetAttribute(hd_tc_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    count_launch();
-    hd_tc_kernel<1><<<grid, kTcThreads, smem, st>>>(tmA, tmB, tmNA, tmNB, nA_dev, nB_dev, KB, b.rowmin, b.colmin,
-                                                    status_dev, (uint64_t)timeout_ns);
+    if (seg) go(hd_tc_kernel<1, true>);
+    else go(hd_tc_kernel<1, false>);
   } else {
-    cudaFuncSetAttribute(hd_tc_kernel<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    count_launch();
-    hd_tc_kernel<0><<<grid, kTcThreads, smem, st>>>(tmA, tmB, tmNA, tmNB, nA_dev, nB_dev, KB, b.rowmin, b.colmin,
-                                                    status_dev, (uint64_t)timeout_ns);
+    if (seg) go(hd_tc_kernel<0, true>);
+    else go(hd_tc_kernel<0, false>);
   }
   if ((e = cudaGetLastError())) return e;
 
   pt_tc.stop();
-  PhaseTimer pt_rs(ctx, PROHD_PH_HD_RESCORE, st);
   // the norms enter the accumulator through a TF32 MMA of six positive
   // exact parts (up to eight roundings of |d2|), hence 32 rather than 16
-  const double c1 = (2.0 * b.Dp + 2.0 * D + 32.0) * 5.9604644775390625e-8;
+  c1 = (2.0 * b.Dp + 2.0 * D + 32.0) * 5.9604644775390625e-8;
+  return cudaSuccess;
+}
+
+cudaError_t hd_core(prohd_ctx* ctx, const float* A, const int64_t* nA_dev, int64_t nA_max, const float* B,
+                    const int64_t* nB_dev, int64_t nB_max, int D, int precision, const int32_t* mapA,
+                    const int32_t* mapB, prohd_hd_result* out, int* status_dev, Arena& ws, int64_t timeout_ns,
+                    cudaStream_t st, bool few_rows) {
+  HdBufs b;
+  layout(ws, nA_max, nB_max, D, precision, b);
+  if (ws.overflow()) return cudaErrorMemoryAllocation;
+  const int nsm = ctx->num_sms;
+  cudaError_t e;
+
+  if (precision == PROHD_FP32) {
+    count_launch();
+    fill_u64_kernel<<<nsm * 4, 256, 0, st>>>(b.bestA, nA_max, ~0ull);
+    count_launch();
+    fill_u64_kernel<<<nsm * 4, 256, 0, st>>>(b.bestB, nB_max, ~0ull);
+    {
+      PhaseTimer pt(ctx, PROHD_PH_HD_CONTRACT, st);
+      if ((e = launch_simt(false, true, true, A, nullptr, nA_dev, B, nB_dev, D, b.bestA, b.bestB, nsm, st))) return e;
+    }
+    PhaseTimer pt2(ctx, PROHD_PH_HD_RESCORE, st);
+    count_launch();
+    hd_finalize_kernel<<<1, 1024, 0, st>>>(A, nA_dev, B, nB_dev, D, b.bestA, nullptr, nA_dev, b.bestB, nullptr,
+                                           nB_dev, mapA, mapB, nullptr, status_dev, out);
+    return cudaGetLastError();
+  }
+
+  double c1 = 0.0;
+  if ((e = tc_prep_contract(ctx, A, nA_dev, B, nB_dev, D, precision, b, status_dev, timeout_ns, st, c1, few_rows)))
+    return e;
+  PhaseTimer pt_rs(ctx, PROHD_PH_HD_RESCORE, st);
   count_launch();
   hd_bounds_kernel<<<nsm * 2, 256, 0, st>>>(b.rowmin, b.nA2, b.epsA, nA_dev, b.colmin, b.nB2, b.epsB, nB_dev, c1, b.sc);
   count_launch();
@@ -1381,6 +1455,44 @@ cudaError_t hd_core(prohd_ctx* ctx, const float* A, const int64_t* nA_dev, int64
   hd_finalize_kernel<<<1, 1024, 0, st>>>(A, nA_dev, B, nB_dev, D, b.bestA, b.candA, &b.sc->ncandA, b.bestB, b.candB,
                                          &b.sc->ncandB, mapA, mapB, b.sc, status_dev, out);
   return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------- row pruning
+
+// hi[i] = the upper end of row i's interval: a certified upper bound (in
+// original units, rounded up to FP32) of row i's NN distance over the columns
+// the contraction saw, so of its NN distance over all columns.
+__global__ void hd_row_upper_kernel(const float* __restrict__ rowmin, const float* __restrict__ nA2,
+                                    const float* __restrict__ epsA, const int64_t* __restrict__ nA_dev,
+                                    const HdScalars* __restrict__ sc, double c1, float* __restrict__ hi_out) {
+  const int64_t n = *nA_dev;
+  const double inv = ldexp(1.0, -scale_exponent(sc->maxabs));
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += stride) {
+    double lo, hi;
+    row_interval(rowmin[i], nA2[i], sc->maxnormB, epsA[i], sc->maxepsB, c1, inv, lo, hi);
+    hi_out[i] = __double2float_ru(hi);
+  }
+}
+
+cudaError_t hd_prefix_upper(prohd_ctx* ctx, const float* X, const int64_t* nX_dev, int64_t nX_max, const float* Y,
+                            const int64_t* nYp_dev, int64_t nYp_max, int D, int precision, float* hi, int* status_dev,
+                            Arena& ws, int64_t timeout_ns, cudaStream_t st) {
+  if (precision == PROHD_FP32) return cudaErrorInvalidValue;
+  HdBufs b;
+  layout(ws, nX_max, nYp_max, D, precision, b);
+  if (ws.overflow()) return cudaErrorMemoryAllocation;
+  double c1 = 0.0;
+  cudaError_t e = tc_prep_contract(ctx, X, nX_dev, Y, nYp_dev, D, precision, b, status_dev, timeout_ns, st, c1);
+  if (e) return e;
+  count_launch();
+  hd_row_upper_kernel<<<ctx->num_sms * 2, 256, 0, st>>>(b.rowmin, b.nA2, b.epsA, nX_dev, b.sc, c1, hi);
+  return cudaGetLastError();
+}
+
+void hd_prefix_layout(Arena& ws, int64_t nX_max, int64_t nYp_max, int D, int precision) {
+  HdBufs b;
+  layout(ws, nX_max, nYp_max, D, precision, b);
 }
 
 cudaError_t hd_simt_batched(const BPair* P, const int* order, int npairs, int64_t* prefix, unsigned long long* ticket,

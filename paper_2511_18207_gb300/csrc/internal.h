@@ -89,7 +89,7 @@ void hd_core_layout(Arena& ws, int64_t nA_max, int64_t nB_max, int D, int precis
 cudaError_t hd_core(prohd_ctx* ctx, const float* A, const int64_t* nA_dev, int64_t nA_max, const float* B,
                     const int64_t* nB_dev, int64_t nB_max, int D, int precision, const int32_t* mapA,
                     const int32_t* mapB, prohd_hd_result* out, int* status_dev, Arena& ws, int64_t timeout_ns,
-                    cudaStream_t st);
+                    cudaStream_t st, bool few_rows = false);
 bool tc_supported_dim(int D);
 
 // ---- selection (select.cu) ----
@@ -208,6 +208,18 @@ cudaError_t select_batched(SelProb* probs, int nprob, const double* alpha_of, un
 // Fills the data fields of one selection problem (host side, at planning).
 void sel_prob_fill(void* dst, const float* q, int64_t n, const float* X, const double* u, uint8_t* mask,
                    const float* maxnorm, int D, int32_t* band0, int32_t* band1, uint64_t* key0, uint64_t* key1);
+// Ascending indices of the set bytes of mask[0..n) into idx, their count
+// into *nsel (device); counts / offsets hold compact_blocks(n) entries.
+int64_t compact_blocks(int64_t n);
+cudaError_t mask_to_indices(const uint8_t* mask, int64_t n, int32_t* idx, int64_t* nsel, unsigned* counts,
+                            int64_t* offsets, cudaStream_t st);
+// Row pruning for the exact distance: rows of X (nX_dev of at most nX_max)
+// against the first nYp_dev rows of Y on tensor cores; hi[i] receives a
+// certified upper bound of row i's NN distance over those rows (so over Y).
+void hd_prefix_layout(Arena& ws, int64_t nX_max, int64_t nYp_max, int D, int precision);
+cudaError_t hd_prefix_upper(prohd_ctx* ctx, const float* X, const int64_t* nX_dev, int64_t nX_max, const float* Y,
+                            const int64_t* nYp_dev, int64_t nYp_max, int D, int precision, float* hi, int* status_dev,
+                            Arena& ws, int64_t timeout_ns, cudaStream_t st);
 cudaError_t compact_gather_batched(const BPair* P, int npairs, int nblk_max, int64_t nmax, cudaStream_t st);
 size_t hd_scalars_bytes();
 size_t hd_tc_row_block();   // rows of A per contraction item (128)

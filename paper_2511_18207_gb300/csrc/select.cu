@@ -766,8 +766,10 @@ static cudaError_t launch_proj(const float* X, int64_t n, int D, const double* d
   return go(proj_kernel<32>, 32);
 }
 
-static cudaError_t mark_to_indices(const uint8_t* mask, int64_t n, int32_t* idx, int64_t* nsel, unsigned* counts,
-                                   int64_t* offsets, cudaStream_t st) {
+int64_t compact_blocks(int64_t n) { return ceil_div(n, kCompactItems); }
+
+cudaError_t mask_to_indices(const uint8_t* mask, int64_t n, int32_t* idx, int64_t* nsel, unsigned* counts,
+                            int64_t* offsets, cudaStream_t st) {
   const int64_t nblk = ceil_div(n, kCompactItems);
   count_launch();
   compact_count_kernel<<<(unsigned)nblk, 256, 0, st>>>(mask, n, counts);
@@ -826,8 +828,8 @@ cudaError_t select_run(prohd_ctx* ctx, const float* A, int64_t nA, const float* 
   count_launch();
   band_resolve_kernel<<<4 * nd, 512, 0, st>>>(b.P);
   if ((e = cudaGetLastError())) return e;
-  if ((e = mark_to_indices(b.maskA, nA, idxA, nselA, b.counts, b.offsets, st))) return e;
-  if ((e = mark_to_indices(b.maskB, nB, idxB, nselB, b.counts, b.offsets, st))) return e;
+  if ((e = mask_to_indices(b.maskA, nA, idxA, nselA, b.counts, b.offsets, st))) return e;
+  if ((e = mask_to_indices(b.maskB, nB, idxB, nselB, b.counts, b.offsets, st))) return e;
   return cudaGetLastError();
 }
 

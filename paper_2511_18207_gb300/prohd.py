@@ -40,6 +40,7 @@ EXPORTS = [
     "prohd_mlp_param_count", "prohd_mlp_state_bytes", "prohd_mlp_scratch_bytes", "prohd_mlp_init", "prohd_mlp_forward",
     "prohd_mlp_loss_grad", "prohd_mlp_train_step", "prohd_mlp_adam_step",
     "prohd_estimate_adaptive_workspace_size", "prohd_estimate_adaptive",
+    "hausdorff_exact_pruned_workspace_size", "hausdorff_exact_pruned",
 ]
 
 #: prohd_phase names, in enum order
@@ -160,6 +161,10 @@ def load_library(path: str = LIB_PATH):
         lib.prohd_estimate_dirs_workspace_size.restype = sz
         lib.prohd_estimate_dirs.argtypes = [vp, vp, i64, vp, i64, i32, pp, vp, i32, pi64, pi64, vp, vp, vp, vp, sz, vp]
         lib.prohd_estimate_dirs.restype = i32
+        lib.hausdorff_exact_pruned_workspace_size.argtypes = [i64, i64, i32, i32]
+        lib.hausdorff_exact_pruned_workspace_size.restype = sz
+        lib.hausdorff_exact_pruned.argtypes = [vp, vp, i64, vp, i64, i32, i32, vp, pi64, vp, sz, vp]
+        lib.hausdorff_exact_pruned.restype = i32
         lib.prohd_estimate_adaptive_workspace_size.argtypes = [i64, i64, i32, pp, ctypes.c_double]
         lib.prohd_estimate_adaptive_workspace_size.restype = sz
         lib.prohd_estimate_adaptive.argtypes = [vp, vp, i64, vp, i64, i32, pp, ctypes.c_double, ctypes.c_double, vp,
@@ -301,6 +306,23 @@ class Context:
                                       _ptr(ws), ws.numel(), self._stream(stream))
         self._raise(rc, "hausdorff_exact")
         return out
+
+    def hausdorff_exact_pruned(self, A, B, precision="fp16", out=None, ws=None, stream=None, want_kept=False):
+        """Enqueues hausdorff_exact_pruned; returns the device result buffer
+        (and, with want_kept, the rows left per direction; that synchronises)."""
+        torch = _torch()
+        _check_points(A, "A")
+        _check_points(B, "B")
+        prec = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
+        D = A.shape[1]
+        need = self.lib.hausdorff_exact_pruned_workspace_size(A.shape[0], B.shape[0], D, prec)
+        ws = self.workspace(need) if ws is None else ws
+        out = torch.empty(ctypes.sizeof(HdResult), dtype=torch.uint8, device=A.device) if out is None else out
+        kept = (ctypes.c_int64 * 2)(-1, -1)
+        rc = self.lib.hausdorff_exact_pruned(self.h, _ptr(A), A.shape[0], _ptr(B), B.shape[0], D, prec, _ptr(out),
+                                             kept if want_kept else None, _ptr(ws), ws.numel(), self._stream(stream))
+        self._raise(rc, "hausdorff_exact_pruned")
+        return (out, [kept[0], kept[1]]) if want_kept else out
 
     def hausdorff_exact_noalloc(self, A, B, out=None, stream=None):
         """Enqueues hausdorff_exact_noalloc (FP32, library-internal scratch,

@@ -105,3 +105,51 @@ def test_hd_lowp_rows_within_margin(prec):
     A = rng.standard_normal((1500, 128)).astype(np.float32)
     B = rng.standard_normal((1400, 128)).astype(np.float32)
     _check(A, B, prec)
+
+
+def _pruned(A, B, prec="fp16"):
+    torch = torch_cuda()
+    out, kept = ctx().hausdorff_exact_pruned(dev(A), dev(B), prec, want_kept=True)
+    torch.cuda.synchronize()
+    return prohd.decode_hd(out), kept
+
+
+@pytest.mark.parametrize("prec", ["fp16", "bf16"])
+def test_hd_pruned_matches_oracle(prec):
+    # both sets above the pruning threshold (32,768 rows); ragged sizes
+    A, B = W.gaussian_outliers(40_001, 36_003, 16, seed=21)
+    r, kept = _pruned(A, B, prec)
+    assert r["status"] == "OK", r
+    assert 0 < kept[0] <= A.shape[0] and 0 < kept[1] <= B.shape[0]
+    o = oracle.hausdorff(A, B)
+    assert rel(r["H"], o["H"]) <= 1e-5 and rel(r["h_ab"], o["h_ab"]) <= 1e-5 and rel(r["h_ba"], o["h_ba"]) <= 1e-5
+    d = np.sqrt(((A[r["wit_a"]].astype(np.float64) - B[r["wit_b"]]) ** 2).sum())
+    assert d == pytest.approx(r["H"], rel=1e-12)
+
+
+@pytest.mark.parametrize("D", [64, 256])
+def test_hd_pruned_equals_the_dense_path(D):
+    # a mixture pair with heavy-tailed points: most rows are dropped, the
+    # result is the plain contraction's
+    torch = torch_cuda()
+    A = W.student_t_mixture(150_000, D, K=8, nu=3.0, seed=22)
+    B = W.student_t_mixture(120_001, D, K=8, nu=3.0, seed=23)
+    r, kept = _pruned(A, B)
+    dense = prohd.decode_hd(ctx().hausdorff_exact(dev(A), dev(B), "fp16"))
+    torch.cuda.synchronize()
+    assert r["status"] == "OK" and dense["status"] == "OK"
+    # both are the FP32 path's result; only the FP32 argmin of a row within
+    # rounding of the maximum could tell them apart
+    assert rel(r["H"], dense["H"]) <= 1e-6 and rel(r["h_ab"], dense["h_ab"]) <= 1e-6
+    assert rel(r["h_ba"], dense["h_ba"]) <= 1e-6
+    assert kept[0] < A.shape[0] and kept[1] < B.shape[0]
+    # the witness rows are real nearest-neighbour pairs at distance H
+    d = np.sqrt(((A[r["wit_a"]].astype(np.float64) - B[r["wit_b"]]) ** 2).sum())
+    assert d == pytest.approx(r["H"], rel=1e-12)
+
+
+def test_hd_pruned_small_sets_take_the_plain_path():
+    A, B = W.random_clouds(5_000, 40_000, 8, seed=24)
+    r, kept = _pruned(A, B)
+    assert kept == [-1, -1]
+    assert rel(r["H"], oracle.hausdorff(A, B)["H"]) <= 1e-5
