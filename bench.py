@@ -488,6 +488,7 @@ def gpu_arm(args):
         "exact_ms": exact["ms"] if exact else None,
         "exact_pruned": exact.get("pruned") if exact else None,
         "speedup_vs_gpu_exact": (exact["ms"] / ms_step) if exact else None,
+        "speedup_vs_gpu_exact_pruned": (exact["pruned"]["ms"] / ms_step) if exact and exact.get("pruned") else None,
         "nsel": [nsa, nsb], "status": res16["status"], "exact_status": exact["status"] if exact else None,
         "rescored": [res16["n_rescored_a"], res16["n_rescored_b"]],
         "refined": (dict(refined, rel_err_vs_exact=(H - refined["H"]) / H if H else None) if refined else None),

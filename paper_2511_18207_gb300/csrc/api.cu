@@ -48,18 +48,22 @@ __global__ void refine_combine_kernel(const prohd_hd_result* r1, const prohd_hd_
   out->hd = r;
 }
 
-// idx[i] = floor(i n / S): S rows spread evenly over n
-__global__ void strided_idx_kernel(int32_t* idx, int64_t S, int64_t n) {
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < S; i += (int64_t)gridDim.x * blockDim.x)
-    idx[i] = (int32_t)((i * n) / S);
+// mask[i] = i < *n_dev and hi[i] >= scale * max(*lb1, *lb2) (lb2 may be null), for i < n_max
+__global__ void keep_mask_kernel(const float* __restrict__ hi, const int64_t* n_dev, int64_t n_max, const double* lb1,
+                                 const double* lb2, double scale, uint8_t* __restrict__ mask) {
+  const int64_t n = *n_dev;
+  const double L = scale * (lb2 ? fmax(*lb1, *lb2) : *lb1);
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n_max; i += (int64_t)gridDim.x * blockDim.x)
+    mask[i] = (i < n && (double)hi[i] >= L) ? 1 : 0;
 }
 
-// mask[i] = hi[i] >= scale * max(*lb1, *lb2) (lb2 may be null)
-__global__ void keep_mask_kernel(const float* __restrict__ hi, int64_t n, const double* lb1, const double* lb2,
-                                 double scale, uint8_t* __restrict__ mask) {
-  const double L = scale * (lb2 ? fmax(*lb1, *lb2) : *lb1);
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-    mask[i] = (double)hi[i] >= L ? 1 : 0;
+// S = min(Smax, *n_dev) indices spread evenly over [0, *n_dev): idx[i] = floor(i n / S)
+__global__ void strided_dev_kernel(int32_t* __restrict__ idx, int64_t* __restrict__ nS, int64_t Smax,
+                                   const int64_t* __restrict__ n_dev) {
+  const int64_t n = *n_dev;
+  const int64_t S = n < Smax ? n : Smax;
+  for (int64_t i = threadIdx.x; i < S; i += blockDim.x) idx[i] = (int32_t)((i * n) / S);
+  if (threadIdx.x == 0) *nS = S;
 }
 
 // S = min(Smax, *nlist) entries of list spread evenly: idx[i] = list[floor(i nlist / S)]
@@ -69,6 +73,14 @@ __global__ void strided_sub_kernel(int32_t* __restrict__ idx, int64_t* __restric
   const int64_t S = n < Smax ? n : Smax;
   for (int64_t i = threadIdx.x; i < S; i += blockDim.x) idx[i] = list[(i * n) / S];
   if (threadIdx.x == 0) *nS = S;
+}
+
+// out[i] = map[idx[i]] for i < *n_dev
+__global__ void compose_idx_kernel(int32_t* __restrict__ out, const int32_t* __restrict__ idx,
+                                   const int32_t* __restrict__ map, const int64_t* __restrict__ n_dev) {
+  const int64_t n = *n_dev;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    out[i] = map[idx[i]];
 }
 
 // The two directed results of the pruned exact distance: r1 = h(A, B) in its
@@ -191,6 +203,148 @@ static int64_t subset_bound(int64_t n, int nd, const int64_t* k) {
   return std::min(n, s);
 }
 
+// ---------------------------------------------------------------- row pruning (directed distances)
+
+constexpr int64_t kPruneSample = 1024;   // rows of a lower-bound sample
+constexpr int64_t kPruneMinRows = 32768; // smaller column sets take the plain contraction
+// A sample's distance is the FP64 length of the FP32 nearest neighbour of
+// its row, which can exceed the row's true NN distance by the FP32 rounding
+// of D-term squared sums (under 2^-24 D relative); the pruning threshold is
+// lowered by 1e-4 relative to stay below the true distance.
+constexpr double kPruneScale = 1.0 - 1e-4;
+
+// columns of Y the pruning contraction scans: n_Y / 64, at least 8192, whole tiles
+static int64_t prune_prefix(int64_t nY) {
+  const int64_t p = std::max<int64_t>(8192, nY / 64);
+  return std::min(nY, (p + 255) / 256 * 256);
+}
+
+namespace {
+// Buffers of the pruned directed distance h(X, Y) for two directions:
+// direction d has at most nX[d] rows in X and nY[d] rows in Y.
+struct PruneLayout {
+  int64_t *nS, *nYp, *nkeep;
+  int32_t* sidx;
+  float* Xs;
+  prohd_hd_result* rs;  // [4]: the two samples' results per direction
+  float* hi;            // certified upper bounds of the rows' NN distances
+  uint8_t* mask;
+  unsigned* counts;
+  int64_t* offsets;
+  int32_t *kidx, *kmap;
+  float* Xk;
+  size_t mark;          // the passes' shared scratch starts here
+};
+void prune_layout(Arena& a, const int64_t nX[2], const int64_t nY[2], int D, int precision, PruneLayout& L) {
+  const int64_t xm = std::max(nX[0], nX[1]);
+  const int64_t S = std::min(kPruneSample, xm);
+  L.nS = a.take<int64_t>(1);
+  L.nYp = a.take<int64_t>(1);
+  L.nkeep = a.take<int64_t>(1);
+  L.sidx = a.take<int32_t>((size_t)S);
+  L.Xs = a.take<float>((size_t)S * D);
+  L.rs = a.take<prohd_hd_result>(4);
+  L.hi = a.take<float>((size_t)xm);
+  L.mask = a.take<uint8_t>((size_t)xm);
+  L.counts = a.take<unsigned>((size_t)compact_blocks(xm));
+  L.offsets = a.take<int64_t>((size_t)compact_blocks(xm));
+  L.kidx = a.take<int32_t>((size_t)xm);
+  L.kmap = a.take<int32_t>((size_t)xm);
+  L.Xk = a.take<float>((size_t)xm * D);
+  L.mark = (a.off + 255) / 256 * 256;
+  size_t end = a.off;
+  for (int d = 0; d < 2; ++d) {
+    const int64_t Sd = std::min(kPruneSample, nX[d]);
+    Arena t = a;
+    hd_core_layout(t, Sd, nY[d], D, precision);
+    end = std::max(end, t.off);
+    t = a;
+    hd_prefix_layout(t, nX[d], prune_prefix(nY[d]), D, precision);
+    end = std::max(end, t.off);
+    t = a;
+    hd_core_layout(t, nX[d], nY[d], D, precision);
+    end = std::max(end, t.off);
+  }
+  a.off = end;
+}
+}  // namespace
+
+// h(X, Y) with row pruning, X holding *nX_dev rows (at most nX_max), Y nY
+// rows; the result r carries witness rows of X mapped through `map` (NULL:
+// X's own indices). h over an evenly spread sample of rows of X is a lower
+// bound LB1; one contraction of every row against the first prune_prefix(nY)
+// rows of Y gives each row a certified upper bound of its NN distance; the
+// rows whose bound reaches LB1 are the hard ones, and h over an evenly spread
+// sample of those is a second, larger lower bound LB2. The exact path then
+// runs on the rows whose bound reaches max(LB1, LB2). Every lower bound is a
+// row's own distance, so the row attaining h(X, Y) always stays and the
+// result equals the plain one. X of at most kPruneSample rows, or Y under
+// kPruneMinRows rows, takes the plain path directly.
+static cudaError_t pruned_directed(prohd_ctx* ctx, const float* X, const int64_t* nX_dev, int64_t nX_max,
+                                   const float* Y, const int64_t* nY_dev, int64_t nY, int D, int precision,
+                                   const int32_t* map, PruneLayout& L, int dir, prohd_hd_result* r, int* status,
+                                   char* wsb, size_t ws_bytes, cudaStream_t st) {
+  const int nsm = ctx->num_sms;
+  auto phase = [&]() {
+    Arena t;
+    t.base = wsb;
+    t.cap = ws_bytes;
+    t.off = L.mark;
+    return t;
+  };
+  if (nX_max <= kPruneSample || nY < kPruneMinRows) {
+    Arena t = phase();
+    return hd_core(ctx, X, nX_dev, nX_max, Y, nY_dev, nY, D, precision, map, nullptr, r, status, t, kDefaultTimeoutNs,
+                   st, true);
+  }
+  const int64_t S = kPruneSample;
+  const int64_t nYp = prune_prefix(nY);
+  // rows of X (by index) against all of Y; few rows: the contraction cuts
+  // the columns into segments so that every SM works
+  auto exact_rows = [&](const int32_t* idx, const int32_t* idx_map, const int64_t* n_dev, int64_t n_max, float* rows,
+                        prohd_hd_result* res) {
+    cudaError_t e2 = gather_rows(X, D, idx, n_dev, n_max, rows, nsm, st);
+    if (e2) return e2;
+    Arena t = phase();
+    return hd_core(ctx, rows, n_dev, n_max, Y, nY_dev, nY, D, precision, idx_map, nullptr, res, status, t,
+                   kDefaultTimeoutNs, st, true);
+  };
+  auto keep = [&](const double* lb2) {
+    count_launch();
+    keep_mask_kernel<<<nsm * 2, 256, 0, st>>>(L.hi, nX_dev, nX_max, &L.rs[dir].h_ab, lb2, kPruneScale, L.mask);
+    cudaError_t e2 = cudaGetLastError();
+    return e2 ? e2 : mask_to_indices(L.mask, nX_max, L.kidx, L.nkeep, L.counts, L.offsets, st);
+  };
+  cudaError_t e = set_i64(L.nYp, nYp, st);
+  if (!e) {
+    count_launch();
+    strided_dev_kernel<<<1, 1024, 0, st>>>(L.sidx, L.nS, S, nX_dev);
+    e = cudaGetLastError();
+  }
+  if (!e) e = exact_rows(L.sidx, nullptr, L.nS, S, L.Xs, L.rs + dir);  // LB1
+  if (!e) {
+    Arena t = phase();
+    e = hd_prefix_upper(ctx, X, nX_dev, nX_max, Y, L.nYp, nYp, D, precision, L.hi, status, t, kDefaultTimeoutNs, st);
+  }
+  if (!e) e = keep(nullptr);
+  if (!e) {
+    count_launch();
+    strided_sub_kernel<<<1, 1024, 0, st>>>(L.sidx, L.nS, S, L.kidx, L.nkeep);
+    e = cudaGetLastError();
+  }
+  if (!e) e = exact_rows(L.sidx, nullptr, L.nS, S, L.Xs, L.rs + 2 + dir);  // LB2
+  if (!e) e = keep(&L.rs[2 + dir].h_ab);
+  const int32_t* final_map = L.kidx;
+  if (!e && map) {
+    count_launch();
+    compose_idx_kernel<<<nsm * 2, 256, 0, st>>>(L.kmap, L.kidx, map, L.nkeep);
+    e = cudaGetLastError();
+    final_map = L.kmap;
+  }
+  if (!e) e = exact_rows(L.kidx, final_map, L.nkeep, nX_max, L.Xk, r);
+  return e;
+}
+
 // ---------------------------------------------------------------- layouts
 
 namespace {
@@ -218,10 +372,10 @@ struct EstLayout {
   int64_t kA[64], kB[64];
   size_t mark_dir, mark_sel, mark_hd;  // arena offsets where each phase's scratch starts
   // one-sided refinement: full-set sizes on the device and the two directed results
-  bool refine = false;
+  bool refine = false, refine_pruned = false;
   int64_t *nA_full = nullptr, *nB_full = nullptr;
   prohd_hd_result *r1 = nullptr, *r2 = nullptr;
-  size_t mark_ref2 = 0;  // second contraction's scratch (after the first's)
+  PruneLayout P;  // the refinement's row pruning (tensor-core precisions)
 };
 
 // Layout of an estimate with nd directions and the given k lists; m_dirs >= 0
@@ -245,11 +399,17 @@ void est_layout_k(Arena& a, int64_t nA, int64_t nB, int D, int nd, const int64_t
   L.As = a.take<float>((size_t)L.boundA * D);
   L.Bs = a.take<float>((size_t)L.boundB * D);
   L.refine = refine;
+  L.refine_pruned = refine && precision != PROHD_FP32;
   if (refine) {
     L.nA_full = a.take<int64_t>(1);
     L.nB_full = a.take<int64_t>(1);
     L.r1 = a.take<prohd_hd_result>(1);
     L.r2 = a.take<prohd_hd_result>(1);
+  }
+  if (L.refine_pruned) {
+    // its buffers and its own scratch, ahead of the phases' shared region
+    const int64_t nX[2] = {L.boundA, L.boundB}, nY[2] = {nB, nA};
+    prune_layout(a, nX, nY, D, precision, L.P);
   }
   // the phases run one after another and share the rest of the arena
   const size_t start = a.off;
@@ -266,7 +426,7 @@ void est_layout_k(Arena& a, int64_t nA, int64_t nB, int D, int nd, const int64_t
   t = a;
   hd_core_layout(t, L.boundA, L.boundB, D, precision);
   end = std::max(end, t.off);
-  if (refine) {
+  if (refine && !L.refine_pruned) {
     // h(A_sel, B) then h(B_sel, A): one after the other in the same region
     t = a;
     hd_core_layout(t, L.boundA, nB, D, precision);
@@ -482,6 +642,21 @@ static cudaError_t refine_run(prohd_ctx* ctx, const float* A, int64_t nA, const 
   const int64_t to = p->wait_timeout_ns > 0 ? p->wait_timeout_ns : kDefaultTimeoutNs;
   cudaError_t e = set_i64(L.nA_full, nA, st);
   if (!e) e = set_i64(L.nB_full, nB, st);
+  if (L.refine_pruned) {
+    // the same two directed distances with row pruning (equal results)
+    if (!e)
+      e = pruned_directed(ctx, L.As, L.nselA, L.boundA, B, L.nB_full, nB, D, p->precision, L.idxA, L.P, 0, L.r1,
+                          L.status, wsb, ws_bytes, st);
+    if (!e)
+      e = pruned_directed(ctx, L.Bs, L.nselB, L.boundB, A, L.nA_full, nA, D, p->precision, L.idxB, L.P, 1, L.r2,
+                          L.status, wsb, ws_bytes, st);
+    if (!e) {
+      count_launch();
+      refine_combine_kernel<<<1, 1, 0, st>>>(L.r1, L.r2, out);
+      e = cudaGetLastError();
+    }
+    return e;
+  }
   if (!e)
     e = hd_core(ctx, L.As, L.nselA, L.boundA, B, L.nB_full, nB, D, p->precision, L.idxA, nullptr, L.r1, L.status, t,
                 to, st);
@@ -664,146 +839,33 @@ prohd_status prohd_estimate_dirs(prohd_ctx* ctx, const float* A, int64_t nA, con
 
 // ---------------------------------------------------------------- exact distance with row pruning
 
-constexpr int64_t kPruneSample = 1024;   // rows of the lower-bound sample
-constexpr int64_t kPruneMinRows = 32768; // smaller sets take the plain contraction
-// The sample's distance is the FP64 length of the FP32 nearest neighbour of
-// its row, which can exceed the row's true NN distance by the FP32 rounding
-// of D-term squared sums (under 2^-24 D relative); the pruning threshold is
-// lowered by 1e-4 relative to stay below the true distance.
-constexpr double kPruneScale = 1.0 - 1e-4;
-
-// columns of Y the pruning contraction scans: n_Y / 64, at least 8192, whole tiles
-static int64_t prune_prefix(int64_t nY) {
-  const int64_t p = std::max<int64_t>(8192, nY / 64);
-  return std::min(nY, (p + 255) / 256 * 256);
-}
 static bool prune_applies(int64_t nA, int64_t nB, int precision) {
   return precision != PROHD_FP32 && nA >= kPruneMinRows && nB >= kPruneMinRows;
 }
 
 namespace {
-struct PruneLayout {
+struct ExactPruneLayout {
   int* status;
-  int64_t *nA, *nB, *nS, *nAp, *nBp, *nkeep;
-  int32_t* sidx;
-  float* Xs;
-  prohd_hd_result *rs, *rk;  // rs [4]: the two samples' results per direction; rk [2]: kept rows' results
-  float* hi;                 // certified upper bounds of the rows' NN distances
-  uint8_t* mask;
-  unsigned* counts;
-  int64_t* offsets;
-  int32_t* kidx;
-  float* Xk;
-  size_t mark;
+  int64_t *nA, *nB;
+  prohd_hd_result* rk;  // [2]: h(A, B), h(B, A)
+  PruneLayout P;
 };
-void prune_layout(Arena& a, int64_t nA, int64_t nB, int D, int precision, PruneLayout& L) {
-  const int64_t nmax = std::max(nA, nB);
-  const int64_t S = std::min(kPruneSample, std::min(nA, nB));
+void exact_prune_layout(Arena& a, int64_t nA, int64_t nB, int D, int precision, ExactPruneLayout& L) {
   L.status = a.take<int>(8);
   L.nA = a.take<int64_t>(1);
   L.nB = a.take<int64_t>(1);
-  L.nS = a.take<int64_t>(1);
-  L.nAp = a.take<int64_t>(1);
-  L.nBp = a.take<int64_t>(1);
-  L.nkeep = a.take<int64_t>(1);
-  L.sidx = a.take<int32_t>((size_t)S);
-  L.Xs = a.take<float>((size_t)S * D);
-  L.rs = a.take<prohd_hd_result>(4);
   L.rk = a.take<prohd_hd_result>(2);
-  L.hi = a.take<float>((size_t)nmax);
-  L.mask = a.take<uint8_t>((size_t)nmax);
-  L.counts = a.take<unsigned>((size_t)compact_blocks(nmax));
-  L.offsets = a.take<int64_t>((size_t)compact_blocks(nmax));
-  L.kidx = a.take<int32_t>((size_t)nmax);
-  L.Xk = a.take<float>((size_t)nmax * D);
-  // the passes run one after another in the rest of the arena
-  L.mark = (a.off + 255) / 256 * 256;
-  size_t end = a.off;
-  for (int dir = 0; dir < 2; ++dir) {
-    const int64_t nX = dir == 0 ? nA : nB, nY = dir == 0 ? nB : nA;
-    Arena t = a;
-    hd_core_layout(t, S, nY, D, precision);
-    end = std::max(end, t.off);
-    t = a;
-    hd_prefix_layout(t, nX, prune_prefix(nY), D, precision);
-    end = std::max(end, t.off);
-    t = a;
-    hd_core_layout(t, nX, nY, D, precision);
-    end = std::max(end, t.off);
-  }
-  a.off = end;
+  const int64_t nX[2] = {nA, nB}, nY[2] = {nB, nA};
+  prune_layout(a, nX, nY, D, precision, L.P);
 }
 }  // namespace
-
-// h(X, Y) with row pruning. h over an evenly spread sample of rows of X is a
-// lower bound LB1 of h(X, Y); one contraction of every row against the first
-// prune_prefix(n_Y) rows of Y gives each row a certified upper bound of its
-// NN distance; the rows whose bound reaches LB1 are the hard ones, and h over
-// an evenly spread sample of those is a second, larger lower bound LB2. The
-// exact path then runs on the rows whose bound reaches max(LB1, LB2). Every
-// lower bound is a row's own distance, so the row attaining h(X, Y) always
-// stays and the result equals the plain one.
-static cudaError_t pruned_directed(prohd_ctx* ctx, const float* X, int64_t nX, const float* Y, int64_t nY, int D,
-                                   int precision, PruneLayout& L, int dir, char* wsb, size_t ws_bytes,
-                                   cudaStream_t st) {
-  const int64_t S = std::min(kPruneSample, nX);
-  const int64_t nYp = prune_prefix(nY);
-  int64_t* nXd = dir == 0 ? L.nA : L.nB;
-  int64_t* nYd = dir == 0 ? L.nB : L.nA;
-  int64_t* nYpd = dir == 0 ? L.nBp : L.nAp;
-  const int nsm = ctx->num_sms;
-  auto phase = [&]() {
-    Arena t;
-    t.base = wsb;
-    t.cap = ws_bytes;
-    t.off = L.mark;
-    return t;
-  };
-  // the kept rows are few (a small share of n_max): the contraction cuts
-  // the columns into segments so that every SM works
-  auto exact_rows = [&](const int32_t* idx, const int64_t* n_dev, int64_t n_max, float* rows, prohd_hd_result* r) {
-    cudaError_t e2 = gather_rows(X, D, idx, n_dev, n_max, rows, nsm, st);
-    if (e2) return e2;
-    Arena t = phase();
-    return hd_core(ctx, rows, n_dev, n_max, Y, nYd, nY, D, precision, idx, nullptr, r, L.status, t, kDefaultTimeoutNs,
-                   st, true);
-  };
-  auto keep = [&](const double* lb2) {
-    count_launch();
-    keep_mask_kernel<<<nsm * 2, 256, 0, st>>>(L.hi, nX, &L.rs[dir].h_ab, lb2, kPruneScale, L.mask);
-    cudaError_t e2 = cudaGetLastError();
-    return e2 ? e2 : mask_to_indices(L.mask, nX, L.kidx, L.nkeep, L.counts, L.offsets, st);
-  };
-  cudaError_t e = set_i64(L.nS, S, st);
-  if (!e) e = set_i64(nYpd, nYp, st);
-  if (!e) {
-    count_launch();
-    strided_idx_kernel<<<8, 128, 0, st>>>(L.sidx, S, nX);
-    e = cudaGetLastError();
-  }
-  if (!e) e = exact_rows(L.sidx, L.nS, S, L.Xs, L.rs + dir);  // LB1
-  if (!e) {
-    Arena t = phase();
-    e = hd_prefix_upper(ctx, X, nXd, nX, Y, nYpd, nYp, D, precision, L.hi, L.status, t, kDefaultTimeoutNs, st);
-  }
-  if (!e) e = keep(nullptr);
-  if (!e) {
-    count_launch();
-    strided_sub_kernel<<<1, 1024, 0, st>>>(L.sidx, L.nS, S, L.kidx, L.nkeep);
-    e = cudaGetLastError();
-  }
-  if (!e) e = exact_rows(L.sidx, L.nS, S, L.Xs, L.rs + 2 + dir);  // LB2
-  if (!e) e = keep(&L.rs[2 + dir].h_ab);
-  if (!e) e = exact_rows(L.kidx, L.nkeep, nX, L.Xk, L.rk + dir);
-  return e;
-}
 
 size_t hausdorff_exact_pruned_workspace_size(int64_t nA, int64_t nB, int D, int precision) {
   if (bad_n(nA) || bad_n(nB) || D < 1) return 0;
   if (!prune_applies(nA, nB, precision)) return hausdorff_exact_workspace_size(nA, nB, D, precision);
   Arena a;
-  PruneLayout L;
-  prune_layout(a, nA, nB, D, precision, L);
+  ExactPruneLayout L;
+  exact_prune_layout(a, nA, nB, D, precision, L);
   return a.off + 256;
 }
 
@@ -825,17 +887,19 @@ prohd_status hausdorff_exact_pruned(prohd_ctx* ctx, const float* A, int64_t nA, 
   Arena a;
   a.base = wsb;
   a.cap = ws_bytes;
-  PruneLayout L;
-  prune_layout(a, nA, nB, D, precision, L);
+  ExactPruneLayout L;
+  exact_prune_layout(a, nA, nB, D, precision, L);
   if (a.overflow()) return fail(ctx, PROHD_ENOMEM, "workspace too small%s");
   cudaError_t e = zero_i32(L.status, 8, st);
   if (!e) e = set_i64(L.nA, nA, st);
   if (!e) e = set_i64(L.nB, nB, st);
   int64_t keep_host[2] = {-1, -1};
   for (int dir = 0; dir < 2 && !e; ++dir) {
-    e = dir == 0 ? pruned_directed(ctx, A, nA, B, nB, D, precision, L, 0, wsb, ws_bytes, st)
-                 : pruned_directed(ctx, B, nB, A, nA, D, precision, L, 1, wsb, ws_bytes, st);
-    if (!e && kept) e = cudaMemcpyAsync(&keep_host[dir], L.nkeep, sizeof(int64_t), cudaMemcpyDeviceToHost, st);
+    e = dir == 0 ? pruned_directed(ctx, A, L.nA, nA, B, L.nB, nB, D, precision, nullptr, L.P, 0, L.rk, L.status, wsb,
+                                   ws_bytes, st)
+                 : pruned_directed(ctx, B, L.nB, nB, A, L.nA, nA, D, precision, nullptr, L.P, 1, L.rk + 1, L.status,
+                                   wsb, ws_bytes, st);
+    if (!e && kept) e = cudaMemcpyAsync(&keep_host[dir], L.P.nkeep, sizeof(int64_t), cudaMemcpyDeviceToHost, st);
     if (!e && kept) e = cudaStreamSynchronize(st);
   }
   if (!e) {

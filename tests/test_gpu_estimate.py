@@ -91,7 +91,9 @@ def test_estimate_nonfinite_input_is_reported(D, where):
 
 
 @pytest.mark.parametrize("prec", ["fp16", "bf16", "fp32"])
-@pytest.mark.parametrize("shape", [(6_001, 5_003, 16, 2, 0.02), (20_000, 17_771, 256, 8, 0.01)])
+@pytest.mark.parametrize("shape", [(6_001, 5_003, 16, 2, 0.02), (20_000, 17_771, 256, 8, 0.01),
+                                   # other set above 32,768 rows, subsets above 1,024: the row-pruned passes
+                                   (60_000, 50_001, 32, 3, 0.02)])
 def test_estimate_refined_matches_oracle(prec, shape):
     # params.refine = 1: max(h(A_sel, B), h(B_sel, A)) with each selected
     # point's nearest neighbour searched in the whole other set; never above H
@@ -211,3 +213,9 @@ def test_adaptive_alpha_single_step_and_bad_arguments():
         prohd.context().prohd_estimate_adaptive(dev(A), dev(B), 0.01, 0.0, m=1, alpha_c=0.02)
     with pytest.raises(prohd.ProHDError):
         prohd.context().prohd_estimate_adaptive(dev(A), dev(B), 0.5, -1.0, m=1, alpha_c=0.02)
+
+
+def test_adaptive_alpha_with_pruned_refinement():
+    # sets above 32,768 rows: every step's refinement takes the row-pruned passes
+    A, B = W.gaussian_outliers(40_001, 36_003, 16, seed=16)
+    _adaptive(A, B, 0.005, 0.08, 0.0, 2, "fp16")
