@@ -353,11 +353,10 @@ def gpu_arm(args):
         resr = prohd.decode_result(out)
         refined = {"ms_per_step": e0.elapsed_time(e1) / kr, "steps": kr, "H": resr["H"], "status": resr["status"],
                    "phases_ms_per_step": {k: round(v[0] / kr, 4) for k, v in rph.items() if v[1]}}
-        if "hd_contract" in rph:
-            # the subset-vs-subset contraction plus the two subset-vs-full-set ones
-            fl = 2.0 * DIM * (resr["nsel_a"] * resr["nsel_b"] + (resr["nsel_a"] + resr["nsel_b"]) * n)
-            t = rph["hd_contract"][0] / kr / 1e3
-            refined["hd_contract_tflops"] = fl / t / 1e12
+        # the two subset-vs-full-set distances take the row-pruned passes
+        # (sampled lower bounds, a prefix contraction, the exact path on the
+        # rows left), so there is no dense flop count to rate them by
+        refined["note"] = "h(A_sel, B) and h(B_sel, A) through the row-pruned passes of hausdorff_exact_pruned"
         del rws
         ws = ctx.workspace(ws_need)
 
