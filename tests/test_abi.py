@@ -50,3 +50,23 @@ def test_batch_workspace_size_is_host_only():
         assert lib.prohd_batch_workspace_size(bad, 1, ctypes.byref(p)) == 0, (D, a)
     p30 = prohd.default_params(m=30)
     assert lib.prohd_batch_workspace_size(ok, 2, ctypes.byref(p30)) == 0
+
+
+def test_new_entry_points_size_their_workspaces_on_the_host():
+    lib = prohd.load_library()
+    # pruned exact distance: the plain size below 32,768 rows or with FP32
+    for nA, nB, prec in ((1000, 2000, 1), (100_000, 90_000, 0)):
+        assert lib.hausdorff_exact_pruned_workspace_size(nA, nB, 64, prec) == \
+            lib.hausdorff_exact_workspace_size(nA, nB, 64, prec)
+    assert lib.hausdorff_exact_pruned_workspace_size(100_000, 90_000, 64, 1) > 0
+    # the refinement needs more room than the plain estimate
+    p0 = prohd.default_params(m=4)
+    p1 = prohd.default_params(m=4, refine=1)
+    assert lib.prohd_estimate_workspace_size(50_000, 40_000, 64, ctypes.byref(p1)) > \
+        lib.prohd_estimate_workspace_size(50_000, 40_000, 64, ctypes.byref(p0))
+    # adaptive alpha: sized for the largest step the budget allows; 0 when
+    # the budget is below the first step
+    small = lib.prohd_estimate_adaptive_workspace_size(50_000, 40_000, 64, ctypes.byref(p0), 0.01)
+    large = lib.prohd_estimate_adaptive_workspace_size(50_000, 40_000, 64, ctypes.byref(p0), 0.3)
+    assert 0 < small < large
+    assert lib.prohd_estimate_adaptive_workspace_size(50_000, 40_000, 64, ctypes.byref(p0), 0.005) == 0
