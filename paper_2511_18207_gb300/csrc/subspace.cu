@@ -51,6 +51,7 @@ constexpr int kSiMaxD = 256;
 constexpr int kSiMaxB = 32;
 constexpr int kSiStallWin = 16;    // steps per window of the stall test
 constexpr int kSiStallStart = 48;  // no stall test before this step
+constexpr int kSiRRWarm = 4;       // steps with a Rayleigh-Ritz step every time
 
 // block size for D dimensions and m components (D <= 256, m <= 24)
 __host__ __device__ inline int si_block(int D, int m) {
@@ -590,6 +591,24 @@ PROHD_DEV void subspace_body(SiSmemT<NC, ROWS, VLD>& S, const float* __restrict_
         }
       }
       __syncthreads();
+      // Plain steps: after kSiRRWarm steps, every other step skips the
+      // Rayleigh-Ritz part (H, Jacobi, Ritz vectors, residuals). The block
+      // spans C^t V_0 either way, so the subspace converges at the same rate
+      // per multiplication; the basis from the last Rayleigh-Ritz step keeps
+      // its column order and Ritz values for the scaling, and the last step
+      // before the cap, like every stop test, is a Rayleigh-Ritz step.
+      const bool plain = t > kSiRRWarm && (t & 1) && t < maxit;
+      if (plain) {
+        const float sigma_p = sigma_rel * fmaxf(S.theta[0], 0.f);
+        for (int o = tid; o < nr * b; o += kSiThreads) {
+          const int i = o / b, j = o - i * b;
+          const float den = fmaxf(S.theta[j], 0.f) + sigma_p;
+          const float w = S.W[i * b + j], v = S.Vt[j * VLD + r0 + i];
+          S.Wr[i * b + j] = den > 1e-30f ? (w + sigma_p * v) / den : v;
+        }
+        __syncthreads();
+        si_cholqr_pass<NC>(S, S.Wr, nr, b, rank, xb, 0);
+      } else {
       // ---- H = V^T W (local rows), exchanged
       if (NC == 1 && b <= 16 && nr > 64) {
         // rows split in quarters (see si_local_gram), the idle exchange buffer as scratch
@@ -712,6 +731,7 @@ PROHD_DEV void subspace_body(SiSmemT<NC, ROWS, VLD>& S, const float* __restrict_
         if (rank == 0 && tid == 0 && iters_out) *iters_out = t;
         break;
       }
+      }  // Rayleigh-Ritz step
     }
     // ---- finish the first pass (Wr -> W). A second pass (W -> Wr) restores
     // orthogonality to FP32 rounding when the first one was not well
