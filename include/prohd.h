@@ -177,12 +177,19 @@ prohd_status hausdorff_exact(prohd_ctx* ctx, const float* A, int64_t nA, const f
  * hausdorff_exact runs on the rows whose bound reaches max(LB1, LB2)
  * (lowered by 1e-4 relative). The row attaining
  * h(X, Y) always stays, so out equals hausdorff_exact's result up to the
- * FP32 argmin of rows within 1e-4 of the maximum. FP16/BF16 and
- * nA, nB >= 32768 only; otherwise (and for PROHD_FP32) this is
- * hausdorff_exact. kept (HOST, may be NULL) receives the rows left in each
+ * FP32 argmin of rows within 1e-4 of the maximum. FP16/BF16,
+ * nA, nB >= 32768 and nA * nB at least the context's pair threshold
+ * (prohd_set_prune_min_pairs, default 4e9) only; otherwise (and for
+ * PROHD_FP32) this is hausdorff_exact. The one-sided refinement
+ * (params.refine) prunes its two directed distances by the same rule, rows
+ * being the subset and columns the other full set. kept (HOST, may be NULL) receives the rows left in each
  * direction ({-1, -1} without pruning); passing it synchronises `stream`.
  */
 size_t hausdorff_exact_pruned_workspace_size(int64_t nA, int64_t nB, int D, int precision);
+/* Pair threshold of the row pruning (>= 0; 0 prunes whenever the row counts
+ * allow). Smaller contractions take the plain path, whose fixed costs are
+ * lower: at 1.9e9 pairs the plain path is faster, at 7.5e9 the pruned one. */
+prohd_status prohd_set_prune_min_pairs(prohd_ctx* ctx, double min_pairs);
 prohd_status hausdorff_exact_pruned(prohd_ctx* ctx, const float* A, int64_t nA, const float* B, int64_t nB, int D,
                                     int precision, prohd_hd_result* out, int64_t* kept, void* ws, size_t ws_bytes,
                                     void* stream);

@@ -207,6 +207,9 @@ static int64_t subset_bound(int64_t n, int nd, const int64_t* k) {
 
 constexpr int64_t kPruneSample = 1024;   // rows of a lower-bound sample
 constexpr int64_t kPruneMinRows = 32768; // smaller column sets take the plain contraction
+// Smaller contractions (rows x columns) than ctx->prune_min_pairs (default
+// 4e9) take the plain path: at 1.9e9 pairs the passes' fixed costs exceed
+// the saving, at 7.5e9 pairs the pruning wins.
 // A sample's distance is the FP64 length of the FP32 nearest neighbour of
 // its row, which can exceed the row's true NN distance by the FP32 rounding
 // of D-term squared sums (under 2^-24 D relative); the pruning threshold is
@@ -292,7 +295,10 @@ static cudaError_t pruned_directed(prohd_ctx* ctx, const float* X, const int64_t
     t.off = L.mark;
     return t;
   };
-  if (nX_max <= kPruneSample || nY < kPruneMinRows) {
+  if (nX_max <= kPruneSample || nY < kPruneMinRows || (double)nX_max * (double)nY < ctx->prune_min_pairs) {
+    // every row is kept
+    cudaError_t e0 = cudaMemcpyAsync(L.nkeep, nX_dev, sizeof(int64_t), cudaMemcpyDeviceToDevice, st);
+    if (e0) return e0;
     Arena t = phase();
     return hd_core(ctx, X, nX_dev, nX_max, Y, nY_dev, nY, D, precision, map, nullptr, r, status, t, kDefaultTimeoutNs,
                    st, true);
@@ -839,6 +845,8 @@ prohd_status prohd_estimate_dirs(prohd_ctx* ctx, const float* A, int64_t nA, con
 
 // ---------------------------------------------------------------- exact distance with row pruning
 
+// the pruned layout (workspace) applies by the row counts alone; whether a
+// call prunes also depends on the context's pair threshold
 static bool prune_applies(int64_t nA, int64_t nB, int precision) {
   return precision != PROHD_FP32 && nA >= kPruneMinRows && nB >= kPruneMinRows;
 }
@@ -872,7 +880,7 @@ size_t hausdorff_exact_pruned_workspace_size(int64_t nA, int64_t nB, int D, int 
 prohd_status hausdorff_exact_pruned(prohd_ctx* ctx, const float* A, int64_t nA, const float* B, int64_t nB, int D,
                                     int precision, prohd_hd_result* out, int64_t* kept, void* ws, size_t ws_bytes,
                                     void* stream) {
-  if (!prune_applies(nA, nB, precision)) {
+  if (!prune_applies(nA, nB, precision) || (ctx && (double)nA * (double)nB < ctx->prune_min_pairs)) {
     if (kept) kept[0] = kept[1] = -1;
     return hausdorff_exact(ctx, A, nA, B, nB, D, precision, out, ws, ws_bytes, stream);
   }
@@ -912,6 +920,13 @@ prohd_status hausdorff_exact_pruned(prohd_ctx* ctx, const float* A, int64_t nA, 
     kept[1] = keep_host[1];
   }
   return e ? cuda_fail(ctx, e) : PROHD_OK;
+}
+
+prohd_status prohd_set_prune_min_pairs(prohd_ctx* ctx, double min_pairs) {
+  if (!ctx) return PROHD_EINVAL;
+  if (!(min_pairs >= 0.0)) return fail(ctx, PROHD_EINVAL, "min_pairs must be >= 0%s");
+  ctx->prune_min_pairs = min_pairs;
+  return PROHD_OK;
 }
 
 // ---------------------------------------------------------------- adaptive alpha

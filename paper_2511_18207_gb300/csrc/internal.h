@@ -31,6 +31,9 @@ struct prohd_ctx {
   // batched-pair tunables found by prohd_batch_autotune (defaults for new plans)
   bool batch_tuned = false;
   int batch_gram_pts = 16384, batch_proj_rows = 8192, batch_sel_chunk = 16384;
+  // row pruning of directed distances only for contractions of at least this
+  // many (row, column) pairs (prohd_set_prune_min_pairs)
+  double prune_min_pairs = 4e9;
 };
 
 namespace prohd {

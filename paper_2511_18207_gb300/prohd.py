@@ -40,7 +40,7 @@ EXPORTS = [
     "prohd_mlp_param_count", "prohd_mlp_state_bytes", "prohd_mlp_scratch_bytes", "prohd_mlp_init", "prohd_mlp_forward",
     "prohd_mlp_loss_grad", "prohd_mlp_train_step", "prohd_mlp_adam_step",
     "prohd_estimate_adaptive_workspace_size", "prohd_estimate_adaptive",
-    "hausdorff_exact_pruned_workspace_size", "hausdorff_exact_pruned",
+    "hausdorff_exact_pruned_workspace_size", "hausdorff_exact_pruned", "prohd_set_prune_min_pairs",
 ]
 
 #: prohd_phase names, in enum order
@@ -165,6 +165,8 @@ def load_library(path: str = LIB_PATH):
         lib.hausdorff_exact_pruned_workspace_size.restype = sz
         lib.hausdorff_exact_pruned.argtypes = [vp, vp, i64, vp, i64, i32, i32, vp, pi64, vp, sz, vp]
         lib.hausdorff_exact_pruned.restype = i32
+        lib.prohd_set_prune_min_pairs.argtypes = [vp, ctypes.c_double]
+        lib.prohd_set_prune_min_pairs.restype = i32
         lib.prohd_estimate_adaptive_workspace_size.argtypes = [i64, i64, i32, pp, ctypes.c_double]
         lib.prohd_estimate_adaptive_workspace_size.restype = sz
         lib.prohd_estimate_adaptive.argtypes = [vp, vp, i64, vp, i64, i32, pp, ctypes.c_double, ctypes.c_double, vp,
@@ -323,6 +325,11 @@ class Context:
                                              kept if want_kept else None, _ptr(ws), ws.numel(), self._stream(stream))
         self._raise(rc, "hausdorff_exact_pruned")
         return (out, [kept[0], kept[1]]) if want_kept else out
+
+    def set_prune_min_pairs(self, min_pairs: float):
+        """Pair threshold of the row pruning (pruned exact distance and the
+        refinement); 0 prunes whenever the row counts allow."""
+        self._raise(self.lib.prohd_set_prune_min_pairs(self.h, float(min_pairs)), "prohd_set_prune_min_pairs")
 
     def hausdorff_exact_noalloc(self, A, B, out=None, stream=None):
         """Enqueues hausdorff_exact_noalloc (FP32, library-internal scratch,

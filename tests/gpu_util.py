@@ -23,3 +23,13 @@ def dev(x):
 
 def rel(a, b):
     return abs(a - b) / max(abs(b), 1e-300)
+
+
+@pytest.fixture
+def prune_always():
+    """Row pruning at any contraction size (the default threshold, 4e9
+    row-column pairs, would leave oracle-sized cases on the plain path)."""
+    c = ctx()
+    c.set_prune_min_pairs(0.0)
+    yield c
+    c.set_prune_min_pairs(4e9)

@@ -10,7 +10,7 @@ import oracle
 from paper_2511_18207_gb300 import prohd
 from paper_2511_18207_gb300 import workloads as W
 
-from .gpu_util import dev, rel, torch_cuda
+from .gpu_util import dev, prune_always, rel, torch_cuda  # noqa: F401 (fixture)
 
 pytestmark = pytest.mark.gpu
 
@@ -94,7 +94,7 @@ def test_estimate_nonfinite_input_is_reported(D, where):
 @pytest.mark.parametrize("shape", [(6_001, 5_003, 16, 2, 0.02), (20_000, 17_771, 256, 8, 0.01),
                                    # other set above 32,768 rows, subsets above 1,024: the row-pruned passes
                                    (60_000, 50_001, 32, 3, 0.02)])
-def test_estimate_refined_matches_oracle(prec, shape):
+def test_estimate_refined_matches_oracle(prec, shape, prune_always):
     # params.refine = 1: max(h(A_sel, B), h(B_sel, A)) with each selected
     # point's nearest neighbour searched in the whole other set; never above H
     torch_cuda()
@@ -215,7 +215,7 @@ def test_adaptive_alpha_single_step_and_bad_arguments():
         prohd.context().prohd_estimate_adaptive(dev(A), dev(B), 0.5, -1.0, m=1, alpha_c=0.02)
 
 
-def test_adaptive_alpha_with_pruned_refinement():
+def test_adaptive_alpha_with_pruned_refinement(prune_always):
     # sets above 32,768 rows: every step's refinement takes the row-pruned passes
     A, B = W.gaussian_outliers(40_001, 36_003, 16, seed=16)
     _adaptive(A, B, 0.005, 0.08, 0.0, 2, "fp16")

@@ -11,7 +11,7 @@ import oracle
 from paper_2511_18207_gb300 import prohd
 from paper_2511_18207_gb300 import workloads as W
 
-from .gpu_util import ctx, dev, rel, torch_cuda
+from .gpu_util import ctx, dev, prune_always, rel, torch_cuda  # noqa: F401 (fixture)
 
 pytestmark = pytest.mark.gpu
 
@@ -115,7 +115,7 @@ def _pruned(A, B, prec="fp16"):
 
 
 @pytest.mark.parametrize("prec", ["fp16", "bf16"])
-def test_hd_pruned_matches_oracle(prec):
+def test_hd_pruned_matches_oracle(prec, prune_always):
     # both sets above the pruning threshold (32,768 rows); ragged sizes
     A, B = W.gaussian_outliers(40_001, 36_003, 16, seed=21)
     r, kept = _pruned(A, B, prec)
@@ -128,7 +128,7 @@ def test_hd_pruned_matches_oracle(prec):
 
 
 @pytest.mark.parametrize("D", [64, 256])
-def test_hd_pruned_equals_the_dense_path(D):
+def test_hd_pruned_equals_the_dense_path(D, prune_always):
     # a mixture pair with heavy-tailed points: most rows are dropped, the
     # result is the plain contraction's
     torch = torch_cuda()
@@ -150,6 +150,14 @@ def test_hd_pruned_equals_the_dense_path(D):
 
 def test_hd_pruned_small_sets_take_the_plain_path():
     A, B = W.random_clouds(5_000, 40_000, 8, seed=24)
+    r, kept = _pruned(A, B)
+    assert kept == [-1, -1]
+    assert rel(r["H"], oracle.hausdorff(A, B)["H"]) <= 1e-5
+
+
+def test_hd_pruned_below_the_pair_threshold_takes_the_plain_path():
+    # 40,001 x 36,003 pairs are below the default threshold (4e9)
+    A, B = W.gaussian_outliers(40_001, 36_003, 16, seed=25)
     r, kept = _pruned(A, B)
     assert kept == [-1, -1]
     assert rel(r["H"], oracle.hausdorff(A, B)["H"]) <= 1e-5
