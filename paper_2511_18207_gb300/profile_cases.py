@@ -2,6 +2,7 @@
 
     python -m paper_2511_18207_gb300.profile_cases directions   # Gram + block iteration, 400k + 400k x 256
     python -m paper_2511_18207_gb300.profile_cases exact        # distance contraction, 100k x 100k x 256, FP16
+    python -m paper_2511_18207_gb300.profile_cases pruned       # row-pruned exact distance, 2M x 2M x 256 (launch list)
 
 Each case runs its call twice (the second launch is the one to capture, e.g.
 ``ncu -k regex:gram_tc_kernel -s 1 -c 1``), keeps the device footprint to a
@@ -39,7 +40,24 @@ def exact():
     print("H", r["H"], r["status"])
 
 
-CASES = {"directions": directions, "exact": exact}
+def pruned():
+    # the benchmark's anisotropic pair; for a launch list (one-pass metric)
+    # only: the inputs and workspace hold about 8 GB on the device
+    import torch
+
+    from . import prohd, workloads as W
+
+    A, B = W.anisotropic_pair(2_000_000, 2_000_000, 256, shift_sigma=0.1, t_frac=0.001, nu=3.0, seed=0)
+    At, Bt = torch.from_numpy(A).cuda(), torch.from_numpy(B).cuda()
+    c = prohd.context()
+    kept = None
+    for _ in range(2):
+        out, kept = c.hausdorff_exact_pruned(At, Bt, "fp16", want_kept=True)
+    r = prohd.decode_hd(out)
+    print("H", r["H"], r["status"], "rows kept", kept)
+
+
+CASES = {"directions": directions, "exact": exact, "pruned": pruned}
 
 if __name__ == "__main__":
     if len(sys.argv) != 2 or sys.argv[1] not in CASES:
