@@ -219,3 +219,23 @@ def test_adaptive_alpha_with_pruned_refinement(prune_always):
     # sets above 32,768 rows: every step's refinement takes the row-pruned passes
     A, B = W.gaussian_outliers(40_001, 36_003, 16, seed=16)
     _adaptive(A, B, 0.005, 0.08, 0.0, 2, "fp16")
+
+
+def test_refined_with_every_point_selected_is_the_exact_hd():
+    # 2k >= n on every direction: both subsets are the whole sets, so the
+    # refined estimate is H itself
+    A, B = W.random_clouds(700, 600, 8, seed=17)
+    r = prohd.prohd_estimate_sync(dev(A), dev(B), m=2, alpha_c=0.6, alpha_p=0.6, refine=1)
+    assert r["status"] == "OK" and r["nsel_a"] == 700 and r["nsel_b"] == 600
+    assert rel(r["H"], oracle.hausdorff(A, B)["H"]) <= 1e-5
+
+
+def test_adaptive_alpha_single_step_budget_edge():
+    # alpha_max just below the second step: one step, stop reason "budget"
+    torch = torch_cuda()
+    A, B = W.gaussian_outliers(3_000, 2_500, 16, seed=18)
+    out, sched = prohd.context().prohd_estimate_adaptive(dev(A), dev(B), 0.02 * 2 - 1e-12, 0.0, m=2, alpha_c=0.02)
+    torch.cuda.synchronize()
+    assert sched["steps"] == 1 and sched["reason"] == "budget"
+    o = oracle.adaptive(A, B, 0.02, 0.04 - 1e-12, 0.0, dirs=None, m=2)
+    assert o["steps"] == 1 and o["reason"] == "budget"

@@ -161,3 +161,23 @@ def test_hd_pruned_below_the_pair_threshold_takes_the_plain_path():
     r, kept = _pruned(A, B)
     assert kept == [-1, -1]
     assert rel(r["H"], oracle.hausdorff(A, B)["H"]) <= 1e-5
+
+
+def test_hd_pruned_identical_sets(prune_always):
+    # H = 0: the lower bounds are 0, nothing is dropped, the result is exact
+    A = W.student_t_mixture(40_000, 32, K=4, nu=3.0, seed=26)
+    r, kept = _pruned(A, A.copy())
+    assert r["status"] == "OK" and r["H"] == 0.0
+    assert kept == [A.shape[0], A.shape[0]]
+
+
+def test_hd_pruned_with_duplicated_rows(prune_always):
+    # repeated rows (ties in every minimum) in both sets
+    rng = np.random.default_rng(27)
+    base = W.student_t_mixture(20_000, 32, K=4, nu=3.0, seed=27)
+    A = np.concatenate([base, base[rng.integers(0, 20_000, 20_000)]])
+    B = np.concatenate([base[:18_000] + 0.05, base[rng.integers(0, 20_000, 18_000)]]).astype(np.float32)
+    r, kept = _pruned(A, B)
+    dense = prohd.decode_hd(ctx().hausdorff_exact(dev(A), dev(B), "fp16"))
+    assert r["status"] == "OK" and rel(r["H"], dense["H"]) <= 1e-6
+    assert rel(r["H"], oracle.hausdorff(A, B)["H"]) <= 1e-5
