@@ -236,6 +236,7 @@ struct PruneLayout {
   int64_t* offsets;
   int32_t *kidx, *kmap;
   float* Xk;
+  HdShared Ysh;         // the other set's rounded copy, made once per direction
   size_t mark;          // the passes' shared scratch starts here
 };
 void prune_layout(Arena& a, const int64_t nX[2], const int64_t nY[2], int D, int precision, PruneLayout& L) {
@@ -254,6 +255,7 @@ void prune_layout(Arena& a, const int64_t nX[2], const int64_t nY[2], int D, int
   L.kidx = a.take<int32_t>((size_t)xm);
   L.kmap = a.take<int32_t>((size_t)xm);
   L.Xk = a.take<float>((size_t)xm * D);
+  hd_shared_layout(a, std::max(nY[0], nY[1]), D, precision, L.Ysh);
   L.mark = (a.off + 255) / 256 * 256;
   size_t end = a.off;
   for (int d = 0; d < 2; ++d) {
@@ -313,7 +315,7 @@ static cudaError_t pruned_directed(prohd_ctx* ctx, const float* X, const int64_t
     if (e2) return e2;
     Arena t = phase();
     return hd_core(ctx, rows, n_dev, n_max, Y, nY_dev, nY, D, precision, idx_map, nullptr, res, status, t,
-                   kDefaultTimeoutNs, st, true);
+                   kDefaultTimeoutNs, st, true, &L.Ysh);
   };
   auto keep = [&](const double* lb2) {
     count_launch();
@@ -322,6 +324,9 @@ static cudaError_t pruned_directed(prohd_ctx* ctx, const float* X, const int64_t
     return e2 ? e2 : mask_to_indices(L.mask, nX_max, L.kidx, L.nkeep, L.counts, L.offsets, st);
   };
   cudaError_t e = set_i64(L.nYp, nYp, st);
+  // Y's rounded copy once for every pass of this direction, with a shift and
+  // scale that cover all rows of X
+  if (!e) e = hd_shared_prepare(ctx, X, nX_dev, Y, nY_dev, D, precision, L.Ysh, status, st);
   if (!e) {
     count_launch();
     strided_dev_kernel<<<1, 1024, 0, st>>>(L.sidx, L.nS, S, nX_dev);
@@ -330,7 +335,8 @@ static cudaError_t pruned_directed(prohd_ctx* ctx, const float* X, const int64_t
   if (!e) e = exact_rows(L.sidx, nullptr, L.nS, S, L.Xs, L.rs + dir);  // LB1
   if (!e) {
     Arena t = phase();
-    e = hd_prefix_upper(ctx, X, nX_dev, nX_max, Y, L.nYp, nYp, D, precision, L.hi, status, t, kDefaultTimeoutNs, st);
+    e = hd_prefix_upper(ctx, X, nX_dev, nX_max, Y, L.nYp, nYp, D, precision, L.hi, status, t, kDefaultTimeoutNs, st,
+                        &L.Ysh);
   }
   if (!e) e = keep(nullptr);
   if (!e) {

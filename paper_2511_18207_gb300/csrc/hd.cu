@@ -1310,12 +1310,59 @@ static cudaError_t launch_simt(bool row_list, bool want_row, bool want_col, cons
   return cudaGetLastError();
 }
 
+// The scalars of a shared preparation that every contraction against it uses.
+__global__ void hd_shared_scalars_kernel(const HdScalars* __restrict__ src, HdScalars* __restrict__ dst) {
+  dst->maxabs = src->maxabs;
+  dst->maxnormB = src->maxnormB;
+  dst->maxepsB = src->maxepsB;
+}
+
+void hd_shared_layout(Arena& ws, int64_t nY_max, int D, int precision, HdShared& s) {
+  s.pad = round_up(nY_max, kTcBN);
+  s.Dp = (int)round_up(D, kTcBK);
+  s.Yt = ws.take<uint16_t>((size_t)s.pad * s.Dp, 1024);
+  s.n2 = ws.take<float>((size_t)s.pad);
+  s.eps = ws.take<float>((size_t)s.pad);
+  s.n8 = ws.take<float>((size_t)s.pad * 8, 1024);
+  s.shift = ws.take<float>((size_t)D);
+  s.spart = ws.take<double>((size_t)16 * D);
+  s.sc = ws.take<HdScalars>(1);
+  (void)precision;
+}
+
+cudaError_t hd_shared_prepare(prohd_ctx* ctx, const float* X, const int64_t* nX_dev, const float* Y,
+                              const int64_t* nY_dev, int D, int precision, HdShared& s, int* status_dev,
+                              cudaStream_t st) {
+  if (precision == PROHD_FP32 || !tc_supported_dim(D)) return cudaErrorInvalidValue;
+  const int nsm = ctx->num_sms;
+  HdScalars* sc = static_cast<HdScalars*>(s.sc);
+  PhaseTimer pt(ctx, PROHD_PH_HD_PREP, st);
+  cudaMemsetAsync(sc, 0, sizeof(HdScalars), st);
+  count_launch();
+  hd_colsum_kernel<<<dim3((D + 31) / 32, 8, 2), 256, 0, st>>>(X, nX_dev, Y, nY_dev, D, s.spart);
+  count_launch();
+  hd_shift_kernel<<<(D + 255) / 256, 256, 0, st>>>(s.spart, nX_dev, nY_dev, D, s.shift);
+  count_launch();
+  hd_maxabs_kernel<<<nsm * 4, 256, 0, st>>>(X, nX_dev, D, s.shift, &sc->maxabs, status_dev);
+  count_launch();
+  hd_maxabs_kernel<<<nsm * 4, 256, 0, st>>>(Y, nY_dev, D, s.shift, &sc->maxabs, status_dev);
+  count_launch();
+  if (precision == PROHD_BF16)
+    hd_prep_kernel<1><<<nsm * 4, 256, 0, st>>>(Y, nY_dev, s.pad, D, s.Dp, s.shift, &sc->maxabs, 1.f,
+                                              (__nv_bfloat16*)s.Yt, s.n2, s.eps, &sc->maxnormB, &sc->maxepsB, s.n8, 1);
+  else
+    hd_prep_kernel<0><<<nsm * 4, 256, 0, st>>>(Y, nY_dev, s.pad, D, s.Dp, s.shift, &sc->maxabs, 1.f, (__half*)s.Yt,
+                                              s.n2, s.eps, &sc->maxnormB, &sc->maxepsB, s.n8, 1);
+  return cudaGetLastError();
+}
+
 // Rounded copies, norms and margins of A and B, then the tensor-core
 // contraction into b.rowmin / b.colmin (squared low-precision minima, scaled
 // units). c1 receives the margin constant of row_interval.
 static cudaError_t tc_prep_contract(prohd_ctx* ctx, const float* A, const int64_t* nA_dev, const float* B,
                                     const int64_t* nB_dev, int D, int precision, HdBufs& b, int* status_dev,
-                                    int64_t timeout_ns, cudaStream_t st, double& c1, bool few_rows = false) {
+                                    int64_t timeout_ns, cudaStream_t st, double& c1, bool few_rows = false,
+                                    const HdShared* shared = nullptr) {
   if (!tc_supported_dim(D)) return cudaErrorInvalidValue;
   const int nsm = ctx->num_sms;
   cudaError_t e;
@@ -1324,6 +1371,29 @@ static cudaError_t tc_prep_contract(prohd_ctx* ctx, const float* A, const int64_
 
   PhaseTimer pt_prep(ctx, PROHD_PH_HD_PREP, st);
   cudaMemsetAsync(b.sc, 0, sizeof(HdScalars), st);
+  if (shared) {
+    // B was prepared once (hd_shared_prepare) with a shift and scale that
+    // cover every row set A is drawn from: take its copy, norms, margins and
+    // scalars, and prepare A alone with the same shift and scale
+    b.shift = shared->shift;
+    b.Bt = shared->Yt;
+    b.nB2 = shared->n2;
+    b.epsB = shared->eps;
+    b.nB8 = shared->n8;
+    count_launch();
+    hd_shared_scalars_kernel<<<1, 1, 0, st>>>(static_cast<const HdScalars*>(shared->sc), b.sc);
+    if (bf16) {
+      count_launch();
+      hd_prep_kernel<1><<<nsm * 4, 256, 0, st>>>(A, nA_dev, b.nA_pad, D, b.Dp, b.shift, &b.sc->maxabs, -2.f,
+                                                (__nv_bfloat16*)b.At, b.nA2, b.epsA, &b.sc->maxnormA, &b.sc->maxepsA,
+                                                b.nA8, 0);
+    } else {
+      count_launch();
+      hd_prep_kernel<0><<<nsm * 4, 256, 0, st>>>(A, nA_dev, b.nA_pad, D, b.Dp, b.shift, &b.sc->maxabs, -2.f,
+                                                (__half*)b.At, b.nA2, b.epsA, &b.sc->maxnormA, &b.sc->maxepsA,
+                                                b.nA8, 0);
+    }
+  } else {
   count_launch();
   hd_colsum_kernel<<<dim3((D + 31) / 32, 8, 2), 256, 0, st>>>(A, nA_dev, B, nB_dev, D, b.spart);
   count_launch();
@@ -1351,6 +1421,7 @@ static cudaError_t tc_prep_contract(prohd_ctx* ctx, const float* A, const int64_
                                               (__half*)b.Bt, b.nB2, b.epsB, &b.sc->maxnormB, &b.sc->maxepsB,
                                               b.nB8, 1);
   }
+  }  // own preparation of both sets
   count_launch();
   fill_u32_kernel<<<nsm * 2, 256, 0, st>>>(b.colmin, b.nB_pad, 0x7f800000u);
   count_launch();
@@ -1401,7 +1472,7 @@ static cudaError_t tc_prep_contract(prohd_ctx* ctx, const float* A, const int64_
 cudaError_t hd_core(prohd_ctx* ctx, const float* A, const int64_t* nA_dev, int64_t nA_max, const float* B,
                     const int64_t* nB_dev, int64_t nB_max, int D, int precision, const int32_t* mapA,
                     const int32_t* mapB, prohd_hd_result* out, int* status_dev, Arena& ws, int64_t timeout_ns,
-                    cudaStream_t st, bool few_rows) {
+                    cudaStream_t st, bool few_rows, const HdShared* shared) {
   HdBufs b;
   layout(ws, nA_max, nB_max, D, precision, b);
   if (ws.overflow()) return cudaErrorMemoryAllocation;
@@ -1425,7 +1496,8 @@ cudaError_t hd_core(prohd_ctx* ctx, const float* A, const int64_t* nA_dev, int64
   }
 
   double c1 = 0.0;
-  if ((e = tc_prep_contract(ctx, A, nA_dev, B, nB_dev, D, precision, b, status_dev, timeout_ns, st, c1, few_rows)))
+  if ((e = tc_prep_contract(ctx, A, nA_dev, B, nB_dev, D, precision, b, status_dev, timeout_ns, st, c1, few_rows,
+                            shared)))
     return e;
   PhaseTimer pt_rs(ctx, PROHD_PH_HD_RESCORE, st);
   count_launch();
@@ -1477,13 +1549,14 @@ __global__ void hd_row_upper_kernel(const float* __restrict__ rowmin, const floa
 
 cudaError_t hd_prefix_upper(prohd_ctx* ctx, const float* X, const int64_t* nX_dev, int64_t nX_max, const float* Y,
                             const int64_t* nYp_dev, int64_t nYp_max, int D, int precision, float* hi, int* status_dev,
-                            Arena& ws, int64_t timeout_ns, cudaStream_t st) {
+                            Arena& ws, int64_t timeout_ns, cudaStream_t st, const HdShared* shared) {
   if (precision == PROHD_FP32) return cudaErrorInvalidValue;
   HdBufs b;
   layout(ws, nX_max, nYp_max, D, precision, b);
   if (ws.overflow()) return cudaErrorMemoryAllocation;
   double c1 = 0.0;
-  cudaError_t e = tc_prep_contract(ctx, X, nX_dev, Y, nYp_dev, D, precision, b, status_dev, timeout_ns, st, c1);
+  cudaError_t e =
+      tc_prep_contract(ctx, X, nX_dev, Y, nYp_dev, D, precision, b, status_dev, timeout_ns, st, c1, false, shared);
   if (e) return e;
   count_launch();
   hd_row_upper_kernel<<<ctx->num_sms * 2, 256, 0, st>>>(b.rowmin, b.nA2, b.epsA, nX_dev, b.sc, c1, hi);

@@ -89,10 +89,11 @@ constexpr int64_t kDefaultTimeoutNs = 4000000000LL;
 // Sizes may live on the device (n*_dev) with host upper bounds (n*_max); the
 // index maps translate row numbers to caller indices for the witnesses.
 void hd_core_layout(Arena& ws, int64_t nA_max, int64_t nB_max, int D, int precision);
+struct HdShared;
 cudaError_t hd_core(prohd_ctx* ctx, const float* A, const int64_t* nA_dev, int64_t nA_max, const float* B,
                     const int64_t* nB_dev, int64_t nB_max, int D, int precision, const int32_t* mapA,
                     const int32_t* mapB, prohd_hd_result* out, int* status_dev, Arena& ws, int64_t timeout_ns,
-                    cudaStream_t st, bool few_rows = false);
+                    cudaStream_t st, bool few_rows = false, const HdShared* shared = nullptr);
 bool tc_supported_dim(int D);
 
 // ---- selection (select.cu) ----
@@ -216,13 +217,28 @@ void sel_prob_fill(void* dst, const float* q, int64_t n, const float* X, const d
 int64_t compact_blocks(int64_t n);
 cudaError_t mask_to_indices(const uint8_t* mask, int64_t n, int32_t* idx, int64_t* nsel, unsigned* counts,
                             int64_t* offsets, cudaStream_t st);
+// One set's rounded copy (with its norms and margins) and the shift and
+// scale it was made with, prepared once for several contractions against
+// row sets drawn from one set X (hd_shared_prepare covers X and Y).
+struct HdShared {
+  void* Yt = nullptr;
+  float *n2 = nullptr, *eps = nullptr, *n8 = nullptr, *shift = nullptr;
+  double* spart = nullptr;
+  void* sc = nullptr;
+  int64_t pad = 0;
+  int Dp = 0;
+};
+void hd_shared_layout(Arena& ws, int64_t nY_max, int D, int precision, HdShared& s);
+cudaError_t hd_shared_prepare(prohd_ctx* ctx, const float* X, const int64_t* nX_dev, const float* Y,
+                              const int64_t* nY_dev, int D, int precision, HdShared& s, int* status_dev,
+                              cudaStream_t st);
 // Row pruning for the exact distance: rows of X (nX_dev of at most nX_max)
 // against the first nYp_dev rows of Y on tensor cores; hi[i] receives a
 // certified upper bound of row i's NN distance over those rows (so over Y).
 void hd_prefix_layout(Arena& ws, int64_t nX_max, int64_t nYp_max, int D, int precision);
 cudaError_t hd_prefix_upper(prohd_ctx* ctx, const float* X, const int64_t* nX_dev, int64_t nX_max, const float* Y,
                             const int64_t* nYp_dev, int64_t nYp_max, int D, int precision, float* hi, int* status_dev,
-                            Arena& ws, int64_t timeout_ns, cudaStream_t st);
+                            Arena& ws, int64_t timeout_ns, cudaStream_t st, const HdShared* shared = nullptr);
 cudaError_t compact_gather_batched(const BPair* P, int npairs, int nblk_max, int64_t nmax, cudaStream_t st);
 size_t hd_scalars_bytes();
 size_t hd_tc_row_block();   // rows of A per contraction item (128)
