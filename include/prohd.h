@@ -167,32 +167,40 @@ prohd_status hausdorff_exact(prohd_ctx* ctx, const float* A, int64_t nA, const f
                              void* stream);
 
 /*
- * The same exact distance with row pruning (the early-break idea of exact
- * Hausdorff algorithms, Sec. II, as whole-set passes): for each direction
- * h(X, Y), an exact pass over 1,024 evenly spread rows of X gives a lower
- * bound LB1 of h(X, Y); one tensor-core contraction of every row of X
- * against the first max(8192, n_Y / 64) rows of Y gives each row a certified
- * upper bound of its NN distance; an exact pass over 1,024 evenly spread rows
- * of those whose bound reaches LB1 gives LB2; the exact path of
- * hausdorff_exact runs on the rows whose bound reaches max(LB1, LB2)
- * (lowered by 1e-4 relative). The row attaining
- * h(X, Y) always stays, so out equals hausdorff_exact's result up to the
- * FP32 argmin of rows within 1e-4 of the maximum. FP16/BF16,
- * nA, nB >= 32768 and nA * nB at least the context's pair threshold
- * (prohd_set_prune_min_pairs, default 4e9) only; otherwise (and for
- * PROHD_FP32) this is hausdorff_exact. The one-sided refinement
- * (params.refine) prunes its two directed distances by the same rule, rows
- * being the subset and columns the other full set. kept (HOST, may be NULL) receives the rows left in each
- * direction ({-1, -1} without pruning); passing it synchronises `stream`.
+ * The same exact distance with row pruning: the early-break idea of the exact
+ * Hausdorff algorithms the paper compares with (Sec. II), as whole-set passes.
+ * For each direction h(X, Y):
+ *   1. an exact pass over 1,024 evenly spread rows of X gives a lower bound
+ *      LB1 of h(X, Y);
+ *   2. one tensor-core contraction of every row of X against the first
+ *      max(8192, n_Y / 64) rows of Y gives every row a certified upper bound
+ *      of its NN distance;
+ *   3. an exact pass over 1,024 evenly spread rows among those whose bound
+ *      reaches LB1 gives LB2;
+ *   4. the exact path of hausdorff_exact runs on the rows whose bound reaches
+ *      max(LB1, LB2), lowered by 1e-4 relative.
+ * The row attaining h(X, Y) always stays, so out equals hausdorff_exact's
+ * result up to the FP32 argmin of rows within 1e-4 of the maximum.
+ * Arguments as for hausdorff_exact, plus
+ *   kept    HOST int64_t[2] or NULL: the rows left in each direction
+ *           ({-1, -1} when the plain path ran); passing it synchronises
+ *           `stream`.
+ * Pruning applies with FP16/BF16 tiles, nA, nB >= 32768 and nA * nB at least
+ * the context's pair threshold; otherwise (and for PROHD_FP32) the call is
+ * hausdorff_exact. The one-sided refinement (params.refine) prunes its two
+ * directed distances by the same rule, its rows being the subset and its
+ * columns the other full set. The workspace size depends on the row counts
+ * only.
  */
 size_t hausdorff_exact_pruned_workspace_size(int64_t nA, int64_t nB, int D, int precision);
-/* Pair threshold of the row pruning (>= 0; 0 prunes whenever the row counts
- * allow). Smaller contractions take the plain path, whose fixed costs are
- * lower: at 1.9e9 pairs the plain path is faster, at 7.5e9 the pruned one. */
-prohd_status prohd_set_prune_min_pairs(prohd_ctx* ctx, double min_pairs);
 prohd_status hausdorff_exact_pruned(prohd_ctx* ctx, const float* A, int64_t nA, const float* B, int64_t nB, int D,
                                     int precision, prohd_hd_result* out, int64_t* kept, void* ws, size_t ws_bytes,
                                     void* stream);
+/* Pair threshold of the row pruning (default 4e9; >= 0, else PROHD_EINVAL;
+ * 0 prunes whenever the row counts allow). Smaller contractions take the
+ * plain path, whose fixed costs are lower: measured, the plain path is faster
+ * at 1.9e9 pairs and the pruned one at 7.5e9. */
+prohd_status prohd_set_prune_min_pairs(prohd_ctx* ctx, double min_pairs);
 
 /*
  * Projection directions (Algorithm 1 step 2 and Algorithm 2 step 2):
