@@ -708,7 +708,8 @@ def reference_arm(args):
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": 1000.0 * tot / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f64", "data": "synthetic", "impl": "reference",
-        "config": {"workload": WORKLOAD, "n_a": args.n, "n_b": args.n, "D": DIM, "m": M_PCS, "alpha": ALPHA,
+        "config": {"workload": WORKLOAD if args.n == N_POINTS else WORKLOAD.replace("2,000,000", f"{args.n:,}"),
+                   "n_a": args.n, "n_b": args.n, "D": DIM, "m": M_PCS, "alpha": ALPHA,
                    "parallelism": "host cores (OpenMP)"},
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": last["cores"], "kind": "oracle",
                          "sample": last["sample"]},

@@ -61,3 +61,27 @@ def test_reference_arm_other_ranks_exit_without_work(monkeypatch, capsys):
 
     bench.reference_arm(Args())
     assert capsys.readouterr().out == ""
+
+
+def test_reference_arm_line_on_a_small_pair(monkeypatch, capsys):
+    # rank 0 times the oracle and prints one JSON line with the contract's keys
+    import json
+
+    import bench
+
+    monkeypatch.setenv("RANK", "0")
+    monkeypatch.setenv("WORLD_SIZE", "1")
+
+    class Args:
+        seed = 0
+        n = 20_000
+        warmup = 3
+        steps = 1
+
+    bench.reference_arm(Args())
+    line = json.loads(capsys.readouterr().out.strip().splitlines()[-1])
+    assert line["impl"] == "reference" and line["value"] > 0 and line["higher_is_better"] is True
+    assert line["unit"] == bench.UNIT and line["metric"] == bench.METRIC
+    assert line["e2e"]["h2d_bytes_per_step"] == 0 and line["e2e"]["value"] == line["value"]
+    assert line["cpu_baseline"]["kind"] == "oracle" and line["cpu_baseline"]["cores"] >= 1
+    assert "20,000" in line["config"]["workload"]
