@@ -100,3 +100,26 @@ def test_one_dimensional_closed_form():
         cands = [abs(a - b[k2]) for k2 in (k - 1, k) if 0 <= k2 < b.size]
         best = max(best, min(cands))
     assert oracle.directed_hd(A, B)[0] == pytest.approx(best, rel=1e-15)
+
+
+@pytest.mark.parametrize("seed", range(3))
+def test_row_pruning_scheme_keeps_the_row_attaining_h(seed):
+    # The scheme of the pruned exact distance, in FP64 on small sets: sampled
+    # rows give lower bounds of h(X, Y); every row's NN distance over a
+    # prefix of Y bounds its NN distance from above; the rows whose bound
+    # reaches the largest lower bound keep h(X, Y) exactly.
+    rng = np.random.default_rng(90 + seed)
+    X = (rng.standard_normal((3000, 6)) * np.linspace(2, 0.3, 6)).astype(np.float32)
+    Y = (rng.standard_normal((2500, 6)) * np.linspace(2, 0.3, 6) + 0.2).astype(np.float32)
+    h, _, _, nn, _ = oracle.directed_hd(X, Y, want_rows=True)
+    nn = np.sqrt(nn)
+    sample1 = (np.arange(64) * X.shape[0]) // 64
+    lb1 = nn[sample1].max()
+    prefix = np.sqrt(((X[:, None, :].astype(np.float64) - Y[None, :256, :]) ** 2).sum(-1)).min(1)
+    assert np.all(prefix >= nn - 1e-12)
+    hard = np.flatnonzero(prefix >= lb1)
+    lb2 = nn[hard[(np.arange(min(64, hard.size)) * hard.size) // min(64, hard.size)]].max()
+    kept = np.flatnonzero(prefix >= max(lb1, lb2) * (1 - 1e-4))
+    assert kept.size < X.shape[0]
+    assert nn[kept].max() == h
+    assert oracle.directed_hd(X[kept], Y)[0] == h
