@@ -183,8 +183,9 @@ prohd_status hausdorff_exact(prohd_ctx* ctx, const float* A, int64_t nA, const f
  * result up to the FP32 argmin of rows within 1e-4 of the maximum.
  * Arguments as for hausdorff_exact, plus
  *   kept    HOST int64_t[2] or NULL: the rows left in each direction
- *           ({-1, -1} when the plain path ran); passing it synchronises
- *           `stream`.
+ *           ({-1, -1} when the plain path ran). Non-NULL synchronises
+ *           `stream` once, after all the work is enqueued, so it must be
+ *           NULL while `stream` is being captured into a CUDA graph.
  * Pruning applies with FP16/BF16 tiles, nA, nB >= 32768 and nA * nB at least
  * the context's pair threshold; otherwise (and for PROHD_FP32) the call is
  * hausdorff_exact. The one-sided refinement (params.refine) prunes its two
@@ -267,8 +268,11 @@ prohd_status prohd_estimate_host(prohd_ctx* ctx, const float* A_host, int64_t nA
  * 2 MiB __device__ array inside the library (held by every GPU that loads
  * it), so nA + nB is limited to about 262,000 points and larger inputs return
  * PROHD_EINVAL. The first call on a device looks up the array's address
- * (cudaGetSymbolAddress): make it before any stream capture. All calls share
- * the array: calls whose GPU work overlaps race; serialise them.
+ * (cudaGetSymbolAddress): make it before any stream capture. After
+ * cudaDeviceReset the next call on that device looks the address up again
+ * (the reset unloads the array), so it too must come before any capture.
+ * All calls share the array: calls whose GPU work overlaps race; serialise
+ * them.
  */
 prohd_status hausdorff_exact_noalloc(prohd_ctx* ctx, const float* A, int64_t nA, const float* B, int64_t nB,
                                      int D, prohd_hd_result* out, void* stream);

@@ -288,7 +288,7 @@ void prune_layout(Arena& a, const int64_t nX[2], const int64_t nY[2], int D, int
 static cudaError_t pruned_directed(prohd_ctx* ctx, const float* X, const int64_t* nX_dev, int64_t nX_max,
                                    const float* Y, const int64_t* nY_dev, int64_t nY, int D, int precision,
                                    const int32_t* map, PruneLayout& L, int dir, prohd_hd_result* r, int* status,
-                                   char* wsb, size_t ws_bytes, cudaStream_t st) {
+                                   char* wsb, size_t ws_bytes, int64_t timeout_ns, cudaStream_t st) {
   const int nsm = ctx->num_sms;
   auto phase = [&]() {
     Arena t;
@@ -302,8 +302,8 @@ static cudaError_t pruned_directed(prohd_ctx* ctx, const float* X, const int64_t
     cudaError_t e0 = cudaMemcpyAsync(L.nkeep, nX_dev, sizeof(int64_t), cudaMemcpyDeviceToDevice, st);
     if (e0) return e0;
     Arena t = phase();
-    return hd_core(ctx, X, nX_dev, nX_max, Y, nY_dev, nY, D, precision, map, nullptr, r, status, t, kDefaultTimeoutNs,
-                   st, true);
+    return hd_core(ctx, X, nX_dev, nX_max, Y, nY_dev, nY, D, precision, map, nullptr, r, status, t, timeout_ns, st,
+                   true);
   }
   const int64_t S = kPruneSample;
   const int64_t nYp = prune_prefix(nY);
@@ -315,7 +315,7 @@ static cudaError_t pruned_directed(prohd_ctx* ctx, const float* X, const int64_t
     if (e2) return e2;
     Arena t = phase();
     return hd_core(ctx, rows, n_dev, n_max, Y, nY_dev, nY, D, precision, idx_map, nullptr, res, status, t,
-                   kDefaultTimeoutNs, st, true, &L.Ysh);
+                   timeout_ns, st, true, &L.Ysh);
   };
   auto keep = [&](const double* lb2) {
     count_launch();
@@ -335,7 +335,7 @@ static cudaError_t pruned_directed(prohd_ctx* ctx, const float* X, const int64_t
   if (!e) e = exact_rows(L.sidx, nullptr, L.nS, S, L.Xs, L.rs + dir);  // LB1
   if (!e) {
     Arena t = phase();
-    e = hd_prefix_upper(ctx, X, nX_dev, nX_max, Y, L.nYp, nYp, D, precision, L.hi, status, t, kDefaultTimeoutNs, st,
+    e = hd_prefix_upper(ctx, X, nX_dev, nX_max, Y, L.nYp, nYp, D, precision, L.hi, status, t, timeout_ns, st,
                         &L.Ysh);
   }
   if (!e) e = keep(nullptr);
@@ -616,7 +616,9 @@ prohd_status prohd_directions(prohd_ctx* ctx, const float* A, int64_t nA, const 
   a.cap = ws_bytes;
   int* status = a.take<int>(8);
   cudaError_t e = zero_i32(status, 8, st);
-  if (!e) e = directions_run(ctx, A, nA, B, nB, D, m, p->power_max_iters, p->power_tol, p->seed, dirs, eig, status, a, st);
+  if (!e)
+    e = directions_run(ctx, A, nA, B, nB, D, m, p->power_max_iters, p->power_tol, p->seed, dirs, eig, status, a, st,
+                       p->wait_timeout_ns);
   return e ? cuda_fail(ctx, e) : PROHD_OK;
 }
 
@@ -658,10 +660,10 @@ static cudaError_t refine_run(prohd_ctx* ctx, const float* A, int64_t nA, const 
     // the same two directed distances with row pruning (equal results)
     if (!e)
       e = pruned_directed(ctx, L.As, L.nselA, L.boundA, B, L.nB_full, nB, D, p->precision, L.idxA, L.P, 0, L.r1,
-                          L.status, wsb, ws_bytes, st);
+                          L.status, wsb, ws_bytes, to, st);
     if (!e)
       e = pruned_directed(ctx, L.Bs, L.nselB, L.boundB, A, L.nA_full, nA, D, p->precision, L.idxB, L.P, 1, L.r2,
-                          L.status, wsb, ws_bytes, st);
+                          L.status, wsb, ws_bytes, to, st);
     if (!e) {
       count_launch();
       refine_combine_kernel<<<1, 1, 0, st>>>(L.r1, L.r2, out);
@@ -704,7 +706,8 @@ static prohd_status estimate_run(prohd_ctx* ctx, const float* A, int64_t nA, con
   const double* use_dirs = given_dirs ? given_dirs : L.dirs;
   if (!e && !given_dirs) {
     Arena t = phase(L.mark_dir);
-    e = directions_run(ctx, A, nA, B, nB, D, m, p->power_max_iters, p->power_tol, p->seed, L.dirs, L.eig, L.status, t, st);
+    e = directions_run(ctx, A, nA, B, nB, D, m, p->power_max_iters, p->power_tol, p->seed, L.dirs, L.eig, L.status, t, st,
+                       p->wait_timeout_ns);
   }
   if (!e) {
     Arena t = phase(L.mark_sel);
@@ -861,6 +864,7 @@ namespace {
 struct ExactPruneLayout {
   int* status;
   int64_t *nA, *nB;
+  int64_t* kept;        // [2]: rows kept per direction
   prohd_hd_result* rk;  // [2]: h(A, B), h(B, A)
   PruneLayout P;
 };
@@ -868,6 +872,7 @@ void exact_prune_layout(Arena& a, int64_t nA, int64_t nB, int D, int precision, 
   L.status = a.take<int>(8);
   L.nA = a.take<int64_t>(1);
   L.nB = a.take<int64_t>(1);
+  L.kept = a.take<int64_t>(2);
   L.rk = a.take<prohd_hd_result>(2);
   const int64_t nX[2] = {nA, nB}, nY[2] = {nB, nA};
   prune_layout(a, nX, nY, D, precision, L.P);
@@ -907,14 +912,14 @@ prohd_status hausdorff_exact_pruned(prohd_ctx* ctx, const float* A, int64_t nA, 
   cudaError_t e = zero_i32(L.status, 8, st);
   if (!e) e = set_i64(L.nA, nA, st);
   if (!e) e = set_i64(L.nB, nB, st);
-  int64_t keep_host[2] = {-1, -1};
+  // kept-row counts: each direction's count is copied (device to device)
+  // before the next direction reuses the pruning buffers, and read back once
   for (int dir = 0; dir < 2 && !e; ++dir) {
     e = dir == 0 ? pruned_directed(ctx, A, L.nA, nA, B, L.nB, nB, D, precision, nullptr, L.P, 0, L.rk, L.status, wsb,
-                                   ws_bytes, st)
+                                   ws_bytes, kDefaultTimeoutNs, st)
                  : pruned_directed(ctx, B, L.nB, nB, A, L.nA, nA, D, precision, nullptr, L.P, 1, L.rk + 1, L.status,
-                                   wsb, ws_bytes, st);
-    if (!e && kept) e = cudaMemcpyAsync(&keep_host[dir], L.P.nkeep, sizeof(int64_t), cudaMemcpyDeviceToHost, st);
-    if (!e && kept) e = cudaStreamSynchronize(st);
+                                   wsb, ws_bytes, kDefaultTimeoutNs, st);
+    if (!e && kept) e = cudaMemcpyAsync(L.kept + dir, L.P.nkeep, sizeof(int64_t), cudaMemcpyDeviceToDevice, st);
   }
   if (!e) {
     count_launch();
@@ -922,8 +927,11 @@ prohd_status hausdorff_exact_pruned(prohd_ctx* ctx, const float* A, int64_t nA, 
     e = cudaGetLastError();
   }
   if (kept) {
-    kept[0] = keep_host[0];
-    kept[1] = keep_host[1];
+    int64_t keep_host[2] = {-1, -1};
+    if (!e) e = cudaMemcpyAsync(keep_host, L.kept, 2 * sizeof(int64_t), cudaMemcpyDeviceToHost, st);
+    if (!e) e = cudaStreamSynchronize(st);
+    kept[0] = e ? -1 : keep_host[0];
+    kept[1] = e ? -1 : keep_host[1];
   }
   return e ? cuda_fail(ctx, e) : PROHD_OK;
 }
@@ -1003,7 +1011,7 @@ prohd_status prohd_estimate_adaptive(prohd_ctx* ctx, const float* A, int64_t nA,
   if (!e) {
     Arena t = phase(L.mark_dir);
     e = directions_run(ctx, A, nA, B, nB, D, m, p->power_max_iters, p->power_tol, p->seed, L.dirs, L.eig, L.status, t,
-                       st);
+                       st, p->wait_timeout_ns);
   }
   prohd_result h{};
   for (int step = 0; !e; ++step) {
@@ -1084,7 +1092,7 @@ prohd_status prohd_features(prohd_ctx* ctx, const float* A, int64_t nA, const fl
   int* status = a.take<int>(8);
   cudaError_t e = zero_i32(status, 8, st);
   if (!e) e = directions_features(ctx, A, nA, B, nB, D, p->power_max_iters, p->power_tol, p->seed, dirs, eig, feat,
-                                  status, a, st);
+                                  status, a, st, p->wait_timeout_ns);
   return e ? cuda_fail(ctx, e) : PROHD_OK;
 }
 

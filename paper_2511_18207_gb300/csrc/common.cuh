@@ -139,13 +139,15 @@ PROHD_DEV bool mbar_try_wait_suspend(uint64_t* bar, uint32_t parity, uint32_t hi
 
 // Bounded wait: returns false (and sets *abort) once `timeout_ns` of global
 // time has passed or another thread has raised *abort. After one fast check
-// the thread suspends in try_wait (woken when the phase completes), checking
-// the abort flag and the timer between suspensions.
+// the thread suspends in try_wait (woken when the phase completes) for at
+// most min(20 us, timeout_ns), checking the abort flag and the timer between
+// suspensions, so a limit below 20 us is honoured too.
 PROHD_DEV bool mbar_wait_bounded(uint64_t* bar, uint32_t parity, volatile int* abort, uint64_t timeout_ns) {
   if (mbar_try_wait(bar, parity)) return true;
   const uint64_t t0 = global_timer_ns();
+  const uint32_t hint = timeout_ns < 20000ull ? (uint32_t)(timeout_ns > 0 ? timeout_ns : 1) : 20000u;
   for (;;) {
-    if (mbar_try_wait_suspend(bar, parity, 20000u)) return true;
+    if (mbar_try_wait_suspend(bar, parity, hint)) return true;
     if (*abort) return false;
     if (global_timer_ns() - t0 > timeout_ns) {
       *abort = 1;

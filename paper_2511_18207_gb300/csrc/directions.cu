@@ -716,7 +716,7 @@ void directions_layout(Arena& ws, int64_t nA, int64_t nB, int D, int m) {
 
 cudaError_t directions_run(prohd_ctx* ctx, const float* A, int64_t nA, const float* B, int64_t nB, int D, int m,
                            int max_iters, double tol, uint64_t seed, double* dirs, double* eig, int* status_dev,
-                           Arena& ws, cudaStream_t st) {
+                           Arena& ws, cudaStream_t st, int64_t timeout_ns) {
   DirBufs b;
   dir_layout(ws, D, m, b);
   if (ws.overflow()) return cudaErrorMemoryAllocation;
@@ -734,7 +734,7 @@ cudaError_t directions_run(prohd_ctx* ctx, const float* A, int64_t nA, const flo
   const bool aligned = ((reinterpret_cast<uintptr_t>(A) | reinterpret_cast<uintptr_t>(B)) & 15) == 0;
   if (gram_tc_supported(D) && aligned && ctx->num_sms <= kMaxSms && ctx->encode_tiled) {
     if ((e = gram_tc_run(ctx, A, nA, B, nB, D, b.s32, b.gc_scratch, b.G, b.sumA, b.sumB, status_dev,
-                         kDefaultTimeoutNs, st)))
+                         timeout_ns > 0 ? timeout_ns : kDefaultTimeoutNs, st)))
       return e;
   } else {
     const int nt = (D + kGT - 1) / kGT;
@@ -780,9 +780,9 @@ cudaError_t directions_run(prohd_ctx* ctx, const float* A, int64_t nA, const flo
 
 cudaError_t directions_features(prohd_ctx* ctx, const float* A, int64_t nA, const float* B, int64_t nB, int D,
                                 int max_iters, double tol, uint64_t seed, double* dirs, double* eig, float* feat,
-                                int* status, Arena& ws, cudaStream_t st) {
+                                int* status, Arena& ws, cudaStream_t st, int64_t timeout_ns) {
   Arena run = ws;
-  cudaError_t e = directions_run(ctx, A, nA, B, nB, D, 8, max_iters, tol, seed, dirs, eig, status, run, st);
+  cudaError_t e = directions_run(ctx, A, nA, B, nB, D, 8, max_iters, tol, seed, dirs, eig, status, run, st, timeout_ns);
   if (e) return e;
   DirBufs b;
   dir_layout(ws, D, 8, b);  // the buffers directions_run just filled

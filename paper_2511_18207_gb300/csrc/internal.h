@@ -109,7 +109,7 @@ cudaError_t gather_rows(const float* X, int D, const int32_t* idx, const int64_t
 void directions_layout(Arena& ws, int64_t nA, int64_t nB, int D, int m);
 cudaError_t directions_run(prohd_ctx* ctx, const float* A, int64_t nA, const float* B, int64_t nB, int D, int m,
                            int max_iters, double tol, uint64_t seed, double* dirs, double* eig, int* status_dev,
-                           Arena& ws, cudaStream_t st);
+                           Arena& ws, cudaStream_t st, int64_t timeout_ns);
 
 // ---- tensor-core Gram (gram_tc.cu) ----
 constexpr int kMaxSms = 192;  // upper bound used to size per-CTA scratch
@@ -278,7 +278,7 @@ cudaError_t mlp_dirs64(const float* U, int count, int D, double* out, cudaStream
 // Directions (m = 8) and the network's input features of one pair.
 cudaError_t directions_features(prohd_ctx* ctx, const float* A, int64_t nA, const float* B, int64_t nB, int D,
                                 int max_iters, double tol, uint64_t seed, double* dirs, double* eig, float* feat,
-                                int* status, Arena& ws, cudaStream_t st);
+                                int* status, Arena& ws, cudaStream_t st, int64_t timeout_ns);
 
 // ---- small utilities (api.cu) ----
 cudaError_t set_i64(int64_t* p, int64_t v, cudaStream_t st);

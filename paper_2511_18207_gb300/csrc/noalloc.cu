@@ -20,7 +20,10 @@
 // Host code cannot use the array's name as a device address (on the host it
 // is only a stand-in symbol), so the first call on each device, with that
 // device current, looks the address up with cudaGetSymbolAddress and caches
-// it. Make that first call before any stream capture begins.
+// it together with the unique id of the current context. Make that first
+// call before any stream capture begins. cudaDeviceReset destroys the
+// context and the module that holds the array; the next call sees a new
+// context id and looks the address up again (again: not under capture).
 //
 // All calls share the one array, and a call leaves its contents behind; the
 // FP32 path resets everything it reads (status, sizes, per-point minima)
@@ -40,6 +43,34 @@ __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratchBytes];
 
 std::mutex g_noalloc_mu;
 void* g_noalloc_ptr[kNoAllocMaxDevices] = {};
+unsigned long long g_noalloc_ctx_id[kNoAllocMaxDevices] = {};
+
+// Unique id of the calling thread's current context (0 if none or if the
+// driver lacks the calls). Ids are never reused within a process, unlike
+// context handles, so a reset device is recognised.
+unsigned long long current_context_id() {
+  typedef CUresult (*GetCurrentFn)(CUcontext*);
+  typedef CUresult (*GetIdFn)(CUcontext, unsigned long long*);
+  static GetCurrentFn get_current = nullptr;
+  static GetIdFn get_id = nullptr;
+  static bool looked_up = false;
+  if (!looked_up) {
+    void* f = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      get_current = reinterpret_cast<GetCurrentFn>(f);
+    f = nullptr;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetId", &f, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      get_id = reinterpret_cast<GetIdFn>(f);
+    looked_up = true;
+  }
+  CUcontext c = nullptr;
+  unsigned long long id = 0;
+  if (get_current && get_id && get_current(&c) == CUDA_SUCCESS && c && get_id(c, &id) == CUDA_SUCCESS) return id;
+  return 0;
+}
 
 }  // namespace
 
@@ -65,7 +96,8 @@ extern "C" prohd_status hausdorff_exact_noalloc(prohd_ctx* ctx, const float* A, 
   void* scratch = nullptr;
   {
     std::lock_guard<std::mutex> lock(g_noalloc_mu);
-    if (!g_noalloc_ptr[dev]) {
+    const unsigned long long cid = current_context_id();
+    if (!g_noalloc_ptr[dev] || cid != g_noalloc_ctx_id[dev]) {
       void* p = nullptr;
       e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
       if (e != cudaSuccess || !p) {
@@ -73,6 +105,8 @@ extern "C" prohd_status hausdorff_exact_noalloc(prohd_ctx* ctx, const float* A, 
         return PROHD_ECUDA;
       }
       g_noalloc_ptr[dev] = p;
+      // the lookup itself makes the primary context current if none was
+      g_noalloc_ctx_id[dev] = current_context_id();
     }
     scratch = g_noalloc_ptr[dev];
   }

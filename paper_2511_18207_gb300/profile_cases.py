@@ -5,8 +5,10 @@
     python -m paper_2511_18207_gb300.profile_cases pruned       # row-pruned exact distance, 2M x 2M x 256 (launch list)
 
 Each case runs its call twice (the second launch is the one to capture, e.g.
-``ncu -k regex:gram_tc_kernel -s 1 -c 1``), keeps the device footprint to a
-few hundred MB (inputs larger than L2), and prints a one-line result.
+``ncu --clock-control none -k regex:gram_tc_kernel -s 1 -c 1``), keeps the
+device footprint to a few hundred MB (inputs larger than L2), and prints a
+one-line result. Every capture must keep ``--clock-control none``: without it
+ncu locks the GPU clocks, and a shared GPU's next user inherits the lock.
 """
 from __future__ import annotations
 
