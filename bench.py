@@ -42,6 +42,9 @@ N_POINTS = 2_000_000
 DIM = 256
 M_PCS = 8
 ALPHA = 0.01
+# DRAM bytes (read + write) per launch of gram_tc_kernel from one ncu capture
+# (None until the current kernel has been captured)
+GRAM_TRAFFIC = None
 WORKLOAD = ("anisotropic Gaussian pair, n=m=2,000,000, D=256 (eigenvalues 1/i, random rotation); "
             "B shifted 0.1 sigma along a random unit vector with 0.1% Student-t (nu=3) points; "
             "ProHD with centroid axis + top-8 PCs, alpha=0.01 per side (alpha/8 per PC), FP16 tiles")
@@ -157,12 +160,15 @@ def make_pair(seed: int, n: int):
 # ---------------------------------------------------------------- oracle sample
 
 def oracle_sample(A, B, rows_cov: int = 200_000, rows_hd: int = 256) -> dict:
-    """Times the FP64 oracle's ProHD on a bounded sample of the workload and
-    extrapolates to the full pair: the covariance is accumulated over every
-    k-th row (time x N/rows), centroids, power iteration and the full
-    selection (projection + sort of all points) run as they are, and the
-    subset HD is run for the first `rows_hd` outer rows of each direction
-    (time x subset size / rows_hd, its cost is linear in the outer rows)."""
+    """Times the FP64 oracle's ProHD on a bounded sample of the workload.
+
+    Measured: the covariance accumulated over every k-th row, centroids and
+    the power iteration, the full selection (projection and sort of every
+    point), and the subset HD for the first `rows_hd` outer rows of each
+    direction. The full-pair time is extrapolated from those measurements:
+    covariance x N / rows used, subset HD x subset rows / rows_hd (both costs
+    are linear in the rows); the other stages ran in full. Both the measured
+    and the extrapolated seconds are returned, with the factors."""
     import numpy as np
 
     import oracle
@@ -172,8 +178,9 @@ def oracle_sample(A, B, rows_cov: int = 200_000, rows_hd: int = 256) -> dict:
     sa = max(1, N // rows_cov)
     t0 = time.perf_counter()
     _, C = oracle.union_covariance(A[::sa], B[::sa])
+    t_cov = time.perf_counter() - t0
     rows_used = A[::sa].shape[0] + B[::sa].shape[0]
-    t_cov = (time.perf_counter() - t0) * N / rows_used
+    f_cov = N / rows_used
     t0 = time.perf_counter()
     u0 = oracle.centroid_axis(oracle.centroid(A), oracle.centroid(B))
     U, _, _ = oracle.power_iteration(C, M_PCS, seed=0)
@@ -188,16 +195,84 @@ def oracle_sample(A, B, rows_cov: int = 200_000, rows_hd: int = 256) -> dict:
     t0 = time.perf_counter()
     oracle.directed_hd(As, Bs, 0, ra)
     oracle.directed_hd(Bs, As, 0, rb)
-    t_hd_s = time.perf_counter() - t0
-    t_hd = t_hd_s * (As.shape[0] + Bs.shape[0]) / (ra + rb)
-    total = t_cov + t_dir + t_sel + t_hd
-    return {"seconds_per_pair": total, "value": 1.0 / total, "cores": oracle.num_threads(),
-            "stages_s": {"covariance": round(t_cov, 3), "centroids+power": round(t_dir, 3),
-                         "selection": round(t_sel, 3), "subset_hd": round(t_hd, 3)},
-            "sample": (f"covariance over every {sa}-th row ({rows_used} rows) scaled x{N / rows_used:.1f}; "
-                       f"centroids, power iteration and selection on all {N} points; subset HD outer loop on "
-                       f"{ra}+{rb} of {As.shape[0]}+{Bs.shape[0]} subset rows, scaled linearly"),
+    t_hd = time.perf_counter() - t0
+    f_hd = (As.shape[0] + Bs.shape[0]) / (ra + rb)
+    measured = {"covariance": t_cov, "centroids+power": t_dir, "selection": t_sel, "subset_hd": t_hd}
+    extrap = {"covariance": t_cov * f_cov, "centroids+power": t_dir, "selection": t_sel, "subset_hd": t_hd * f_hd}
+    total = sum(extrap.values())
+    return {"seconds_per_pair": total, "sample_seconds": sum(measured.values()), "value": 1.0 / total,
+            "cores": oracle.num_threads(), "extrapolated": True,
+            "scale_factors": {"covariance": round(f_cov, 3), "subset_hd": round(f_hd, 3)},
+            "stages_s_measured": {k: round(v, 4) for k, v in measured.items()},
+            "stages_s_extrapolated": {k: round(v, 4) for k, v in extrap.items()},
+            "sample": (f"measured: covariance over every {sa}-th row ({rows_used} of {N} rows), centroids, power "
+                       f"iteration and selection on all {N} points, subset HD outer loop on {ra}+{rb} of "
+                       f"{As.shape[0]}+{Bs.shape[0]} subset rows; the full pair's time is extrapolated with "
+                       f"covariance x{f_cov:.1f} and subset HD x{f_hd:.1f}"),
             "nsel": [int(As.shape[0]), int(Bs.shape[0])]}
+
+
+def oracle_full_runs() -> dict:
+    """The FP64 oracle's ProHD run in full (no sampling, no extrapolation) on
+    the two smaller workloads: 2,000 + 2,000 points in D = 16 (Gaussian with
+    1% scaled outliers; m = 2, alpha = 0.02) with its exact HD too, and the
+    200,000 + 200,000 point, D = 256 mixture pair (m = 8, alpha = 0.01).
+    Wall seconds on the host cores."""
+    import oracle
+    from paper_2511_18207_gb300 import workloads as W
+
+    out = {"cores": oracle.num_threads()}
+    A, B = W.gaussian_outliers(2000, 2000, 16, seed=0)
+    t0 = time.perf_counter()
+    o = oracle.prohd(A, B, alpha=0.02, m=2, alpha_p=0.02, seed=0)
+    t_p = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    h = oracle.hausdorff(A, B)
+    t_h = time.perf_counter() - t0
+    out["gaussian_2k_D16"] = {"prohd_s": t_p, "exact_hd_s": t_h, "H_hat": o["H_hat"], "H": h["H"]}
+    A, B = W.mixture_pair(200_000, 256, 16, seed=1)
+    t0 = time.perf_counter()
+    o = oracle.prohd(A, B, alpha=0.01, m=8, seed=0)
+    t_p = time.perf_counter() - t0
+    out["mixture_200k_D256"] = {"prohd_s": t_p, "H_hat": o["H_hat"], "nsel": [int(o["idxA"].size),
+                                                                              int(o["idxB"].size)],
+                                "exact_hd": "not run: about 3e13 FP64 operations, beyond a bench run's minutes"}
+    return out
+
+
+def subsample_check(ctx, A, B, dev, n_sub: int = 20_000, seed: int = 11) -> dict:
+    """GPU results against the FP64 oracle on a seeded 20,000-point subsample
+    of each set of the 2M pair: the GPU's exact HD (FP16 tiles with FP32
+    rescoring) and its ProHD estimate (plain and refined) against the
+    oracle's brute-force FP64 exact HD and the oracle's own ProHD estimate."""
+    import numpy as np
+    import torch
+
+    import oracle
+    from paper_2511_18207_gb300 import prohd
+
+    rng = np.random.default_rng(seed)
+    ia = np.sort(rng.choice(A.shape[0], n_sub, replace=False))
+    ib = np.sort(rng.choice(B.shape[0], n_sub, replace=False))
+    As, Bs = np.ascontiguousarray(A[ia]), np.ascontiguousarray(B[ib])
+    At, Bt = torch.from_numpy(As).to(dev), torch.from_numpy(Bs).to(dev)
+    g_exact = prohd.decode_hd(ctx.hausdorff_exact(At, Bt, "fp16"))
+    torch.cuda.synchronize()
+    g_est = prohd.prohd_estimate_sync(At, Bt, m=M_PCS, alpha_c=ALPHA, precision="fp16")
+    g_ref = prohd.prohd_estimate_sync(At, Bt, m=M_PCS, alpha_c=ALPHA, precision="fp16", refine=1)
+    t0 = time.perf_counter()
+    o_exact = oracle.hausdorff(As, Bs)
+    t_exact = time.perf_counter() - t0
+    o_est = oracle.prohd(As, Bs, alpha=ALPHA, m=M_PCS, seed=0)
+    H = o_exact["H"]
+    return {"n": n_sub, "H_fp64": H, "oracle_exact_hd_s": t_exact,
+            "gpu_exact_rel_err": abs(g_exact["H"] - H) / H,
+            "gpu_hhat_rel_err_vs_fp64_exact": abs(g_est["H"] - H) / H,
+            "gpu_hhat_signed_vs_fp64_exact": (g_est["H"] - H) / H,
+            "gpu_refined_rel_err_vs_fp64_exact": abs(g_ref["H"] - H) / H,
+            "gpu_hhat_rel_diff_vs_oracle_hhat": abs(g_est["H"] - o_est["H_hat"]) / o_est["H_hat"],
+            "note": "GPU directions come from tensor-core covariance partials, the oracle's from FP64 two-pass "
+                    "sums, so the candidate sets (and H_hat) can differ slightly"}
 
 
 # ---------------------------------------------------------------- GPU arm
@@ -421,25 +496,34 @@ def gpu_arm(args):
     fp32_peak = 152 * 128 * 2 * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
     if dom == "gram":
         t = cand["gram"][0] / 1e3
+        # the method's work for the covariance (Algorithm 2): one read of both
+        # sets and 2 N D^2 flops for the D x D Gram of the N = 2n points; the
+        # roofline is the larger of the two bound times
+        by = 2.0 * n * DIM * 4
+        fl = 2.0 * (2 * n) * DIM * DIM
         if DIM <= 256 and DIM % 4 == 0:
-            # tensor-core Gram: six BF16 split products per point over rows 0-127 x all
-            # columns and rows 128-255 x columns 128-255 (three quarters of the square).
-            # Their time at the sustained BF16 peak exceeds one read of both sets at the
-            # copy bandwidth, so the tensor pipe is the bound; the HBM view is reported too.
-            dp = ((DIM + 63) // 64) * 64
-            per_point = 2.0 * 6 * 128 * (dp + max(dp - 128, 0))
-            fl = per_point * 2 * n
-            by = 2.0 * n * DIM * 4
             pk = peaks.get("bf16_tflops_sustained", peaks["bf16_tflops"])
-            # DRAM bytes per launch: ncu capture at 400k + 400k points (profiles/
-            # gram_tc_kernel_400kx256.md), scaled by the number of points
-            traffic = (1.400323e9 + 0.299289e9) * (2.0 * n) / 8.0e5 if DIM == 256 else None
-            roof = {"kernel": "gram_tc_kernel", "bound": "tensor", "achieved": fl / t / 1e12, "peak": pk,
-                    "unit": "TFLOP/s", "traffic": traffic, "peak_source": f"{peak_src} sustained BF16 (cuBLAS)",
-                    "hbm_view": {"achieved_gbs": by / t / 1e9, "peak_gbs": peaks["hbm_gbs"],
-                                 "frac": by / t / 1e9 / peaks["hbm_gbs"]}}
+            t_hbm, t_tc = by / (peaks["hbm_gbs"] * 1e9), fl / (pk * 1e12)
+            # the tensor cores run two BF16 MMAs per point over the full
+            # 256 x 256 product (a two-part split, X = sum h h^T + 2 m h^T)
+            dp = 256 if DIM > 128 else 2 * ((DIM + 63) // 64) * 64
+            issued = 2.0 * 2 * 256 * dp * (2 * n) / (2 if DIM <= 128 else 1)
+            note = {"issued_tflops": issued / t / 1e12, "issued_frac_of_sustained_bf16": issued / t / 1e12 / pk,
+                    "issued_work": "2 BF16 MMAs per point over the CTA pair's 256-row product"}
+            if t_hbm >= t_tc:
+                roof = {"kernel": "gram_tc_kernel", "bound": "hbm", "achieved": by / t / 1e9,
+                        "peak": peaks["hbm_gbs"], "unit": "GB/s", "traffic": GRAM_TRAFFIC,
+                        "peak_source": f"{peak_src} copy bandwidth",
+                        "work": "one read of both sets (2 n D 4 bytes); 2 N D^2 flops take less time at the "
+                                "sustained BF16 peak", "tensor_view": {"achieved_tflops": fl / t / 1e12,
+                                                                      "peak_tflops": pk,
+                                                                      "frac": fl / t / 1e12 / pk},
+                        "split_products": note}
+            else:
+                roof = {"kernel": "gram_tc_kernel", "bound": "tensor", "achieved": fl / t / 1e12, "peak": pk,
+                        "unit": "TFLOP/s", "traffic": GRAM_TRAFFIC, "peak_source": f"{peak_src} sustained BF16",
+                        "work": "2 N D^2 flops", "split_products": note}
         else:
-            fl = 2.0 * (2 * n) * DIM * DIM
             roof = {"kernel": "gram_kernel", "bound": "alu", "achieved": fl / t / 1e12, "peak": fp32_peak,
                     "unit": "TFLOP/s", "traffic": None,
                     "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 flop x max SM clock"}
@@ -468,10 +552,14 @@ def gpu_arm(args):
         learned_res = learned_arm(args, peaks, dev)
 
     cpu = None
+    subsample = None
     if rank == 0 and world == 1 and not args.no_cpu:
         s = oracle_sample(A, B)
         cpu = {"value": s["value"], "unit": UNIT, "cores": s["cores"], "kind": "oracle", "sample": s["sample"],
-               "stages_s": s["stages_s"]}
+               "extrapolated": True, "sample_seconds": s["sample_seconds"], "scale_factors": s["scale_factors"],
+               "stages_s_measured": s["stages_s_measured"], "stages_s_extrapolated": s["stages_s_extrapolated"],
+               "full_runs": oracle_full_runs()}
+        subsample = subsample_check(ctx, A, B, dev)
 
     H = exact["H"] if exact else None
     line = {
@@ -503,6 +591,7 @@ def gpu_arm(args):
         "gpu_launches": launches,
         "roofline": roof,
         "cpu_baseline": cpu,
+        "fp64_subsample_20k": subsample,
         "clocks": clk,
         "batched": batched,
         "learned": learned_res,
@@ -688,33 +777,44 @@ def learned_arm(args, peaks, dev):
 # ---------------------------------------------------------------- reference arm
 
 def reference_arm(args):
+    """The FP64 oracle as the reference: each step is one bounded sample of
+    the 2M pair (oracle_sample); ms_per_step is that step's measured time,
+    and value is the full-pair throughput extrapolated from it by the stated
+    factors (the full pair would take minutes per step on the host cores)."""
     rank, world, _ = dist_info()
     if rank != 0:
         return
-    import oracle
-
     A, B = make_pair(seed=args.seed, n=args.n)
     for _ in range(args.warmup):
         oracle_sample(A, B, rows_cov=50_000, rows_hd=32)
     t0 = time.perf_counter()
-    tot = 0.0
+    sample_s = 0.0
+    pair_s = 0.0
     last = None
     for _ in range(args.steps):
+        t1 = time.perf_counter()
         last = oracle_sample(A, B)
-        tot += last["seconds_per_pair"]
+        sample_s += time.perf_counter() - t1
+        pair_s += last["seconds_per_pair"]
     wall = time.perf_counter() - t0
-    value = args.steps / tot
+    value = args.steps / pair_s
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
-        "ms_per_step": 1000.0 * tot / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-        "dtype": "f64", "data": "synthetic", "impl": "reference",
+        "ms_per_step": 1000.0 * sample_s / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
+        "extrapolated": True,
+        "ms_per_full_pair_extrapolated": 1000.0 * pair_s / args.steps,
+        "step_note": ("a step is one bounded sample of the pair, timed (ms_per_step); value is the full pair's "
+                      "throughput extrapolated from it by scale_factors"),
+        "scale_factors": last["scale_factors"],
         "config": {"workload": WORKLOAD if args.n == N_POINTS else WORKLOAD.replace("2,000,000", f"{args.n:,}"),
                    "n_a": args.n, "n_b": args.n, "D": DIM, "m": M_PCS, "alpha": ALPHA,
                    "parallelism": "host cores (OpenMP)"},
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": last["cores"], "kind": "oracle",
-                         "sample": last["sample"]},
+                         "sample": last["sample"], "extrapolated": True},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
-        "stages_s": last["stages_s"], "wall_s": wall,
+        "stages_s_measured": last["stages_s_measured"], "stages_s_extrapolated": last["stages_s_extrapolated"],
+        "wall_s": wall,
     }
     print(json.dumps(line))
 
@@ -732,9 +832,9 @@ def main():
     ap.add_argument("--no-batched", action="store_true", help="skip the 512-pair batch measurement")
     ap.add_argument("--no-learned", action="store_true", help="skip the learned-direction measurement")
     ap.add_argument("--no-refined", action="store_true", help="skip the one-sided refinement measurements")
-    ap.add_argument("--learned-pairs", type=int, default=1024)
-    ap.add_argument("--learned-steps", type=int, default=1000)
-    ap.add_argument("--learned-eval", type=int, default=8)
+    ap.add_argument("--learned-pairs", type=int, default=50_000)
+    ap.add_argument("--learned-steps", type=int, default=4000)
+    ap.add_argument("--learned-eval", type=int, default=32)
     ap.add_argument("--workload", choices=["pair", "batched", "learned"], default="pair",
                     help="pair: the 2M x 2M headline line (with the batch and learned objects); "
                          "batched / learned: only that measurement, on a line of its own")

@@ -220,6 +220,22 @@ prohd_status prohd_directions(prohd_ctx* ctx, const float* A, int64_t nA, const 
                               size_t ws_bytes, void* stream);
 
 /*
+ * Union covariance of the stacked set [A; B] (Algorithm 2 step 2: the
+ * principal components are eigenvectors of this matrix), the same matrix
+ * prohd_directions iterates on:
+ *   C      device FP64 [D * D], row-major: C = (1/N) sum_z (z - mu)(z - mu)^T
+ *          over the N = nA + nB points
+ *   mean   device FP64 [D] receiving mu, or NULL
+ * For D <= 256 with D % 4 == 0 and 16-byte aligned sets the products come
+ * from BF16 tensor-core tiles (a two-part split of each centred FP32 value,
+ * FP32 accumulation of 512 points, FP64 across blocks); otherwise from FP32
+ * CUDA-core tiles with FP64 accumulation.
+ */
+size_t prohd_covariance_workspace_size(int64_t nA, int64_t nB, int D);
+prohd_status prohd_covariance(prohd_ctx* ctx, const float* A, int64_t nA, const float* B, int64_t nB, int D,
+                              double* C, double* mean, void* ws, size_t ws_bytes, void* stream);
+
+/*
  * Extreme selection for given directions (Algorithms 1-2, steps "argsort",
  * "keep bottom-k and top-k", "unique"; Algorithm 3 step 4, union):
  *   dirs       device FP64 [ndirs * D] (any vectors; the projection is x^T u)
@@ -469,6 +485,22 @@ prohd_status prohd_mlp_train_step(prohd_ctx* ctx, int D, void* state, const floa
 /* The Adam update alone, with a caller gradient [param_count] (device FP32). */
 prohd_status prohd_mlp_adam_step(prohd_ctx* ctx, int D, void* state, const float* grad, float lr, int64_t step,
                                  void* stream);
+/* Checkpoint of a network's state, so training can resume exactly. File:
+ * "PHDMLP01", int32 D, int64 step, int64 parameter count, int64 extra-byte
+ * count (little-endian, unpadded), the caller's extra bytes (e.g. the state
+ * of its training-data sampler), then params | Adam m | Adam v as FP32.
+ * `state` is the device state; save copies it to the host and synchronises
+ * `stream`. PROHD_EINVAL if the file cannot be written. */
+prohd_status prohd_mlp_save(prohd_ctx* ctx, const char* path, int D, int64_t step, const void* state,
+                            const void* extra, int64_t extra_bytes, void* stream);
+/* Reads a checkpoint: D and step into *D_out / *step_out and the extra-byte
+ * count into *extra_bytes (may be NULL). state == NULL reads the header only;
+ * otherwise state (device, prohd_mlp_state_bytes(*D_out) bytes) receives
+ * params | m | v and extra (host, extra_cap bytes) the extra bytes, and the
+ * call synchronises `stream`. PROHD_EINVAL for a missing, foreign, truncated
+ * or mismatched file, or an extra buffer smaller than the file's. */
+prohd_status prohd_mlp_load(prohd_ctx* ctx, const char* path, int* D_out, int64_t* step_out, void* state,
+                            void* extra, int64_t extra_cap, int64_t* extra_bytes, void* stream);
 
 #ifdef __cplusplus
 }

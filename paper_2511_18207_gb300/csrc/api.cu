@@ -622,6 +622,30 @@ prohd_status prohd_directions(prohd_ctx* ctx, const float* A, int64_t nA, const 
   return e ? cuda_fail(ctx, e) : PROHD_OK;
 }
 
+size_t prohd_covariance_workspace_size(int64_t nA, int64_t nB, int D) {
+  if (bad_n(nA) || bad_n(nB) || D < 1) return 0;
+  Arena a;
+  a.take<int>(8);
+  covariance_layout(a, D);
+  return a.off + 256;
+}
+
+prohd_status prohd_covariance(prohd_ctx* ctx, const float* A, int64_t nA, const float* B, int64_t nB, int D,
+                              double* C, double* mean, void* ws, size_t ws_bytes, void* stream) {
+  prohd_status s = check_sets(ctx, A, nA, B, nB, D);
+  if (s) return s;
+  if (!C) return fail(ctx, PROHD_EINVAL, "null C%s");
+  if ((s = check_ws(ctx, ws, ws_bytes, prohd_covariance_workspace_size(nA, nB, D)))) return s;
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  Arena a;
+  a.base = static_cast<char*>(ws);
+  a.cap = ws_bytes;
+  int* status = a.take<int>(8);
+  cudaError_t e = zero_i32(status, 8, st);
+  if (!e) e = covariance_run(ctx, A, nA, B, nB, D, C, mean, status, a, st, kDefaultTimeoutNs);
+  return e ? cuda_fail(ctx, e) : PROHD_OK;
+}
+
 prohd_status prohd_select(prohd_ctx* ctx, const float* A, int64_t nA, const float* B, int64_t nB, int D,
                           const double* dirs, int ndirs, const int64_t* kA, const int64_t* kB, int32_t* idxA,
                           int64_t* nselA, int32_t* idxB, int64_t* nselB, void* ws, size_t ws_bytes, void* stream) {
@@ -1185,6 +1209,81 @@ prohd_status prohd_mlp_adam_step(prohd_ctx* ctx, int D, void* state, const float
   if (!(lr > 0.f)) return fail(ctx, PROHD_EINVAL, "learning rate must be positive%s");
   cudaError_t e = mlp_adam(mlp_shape(D), static_cast<float*>(state), grad, lr, step,
                            reinterpret_cast<cudaStream_t>(stream));
+  return e ? cuda_fail(ctx, e) : PROHD_OK;
+}
+
+// Checkpoint file: "PHDMLP01", int32 D, int64 step, int64 parameter count,
+// int64 extra-byte count (all little-endian, unpadded), the extra bytes,
+// then params | Adam m | Adam v as FP32.
+static const char kMlpMagic[8] = {'P', 'H', 'D', 'M', 'L', 'P', '0', '1'};
+
+prohd_status prohd_mlp_save(prohd_ctx* ctx, const char* path, int D, int64_t step, const void* state,
+                            const void* extra, int64_t extra_bytes, void* stream) {
+  if (!ctx) return PROHD_EINVAL;
+  if (!path || D < 8 || D > 1024 || !state || step < 0 || extra_bytes < 0 || (extra_bytes > 0 && !extra))
+    return fail(ctx, PROHD_EINVAL, "bad checkpoint arguments%s");
+  const int64_t np = (int64_t)mlp_shape(D).nparam;
+  std::vector<float> body((size_t)(3 * np));
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  cudaError_t e = cudaMemcpyAsync(body.data(), state, body.size() * sizeof(float), cudaMemcpyDeviceToHost, st);
+  if (!e) e = cudaStreamSynchronize(st);
+  if (e) return cuda_fail(ctx, e);
+  unsigned char head[8 + 4 + 3 * 8];
+  const int32_t d32 = D;
+  memcpy(head, kMlpMagic, 8);
+  memcpy(head + 8, &d32, 4);
+  memcpy(head + 12, &step, 8);
+  memcpy(head + 20, &np, 8);
+  memcpy(head + 28, &extra_bytes, 8);
+  FILE* f = fopen(path, "wb");
+  if (!f) return fail(ctx, PROHD_EINVAL, "cannot open the checkpoint file for writing%s");
+  bool ok = fwrite(head, 1, sizeof head, f) == sizeof head;
+  if (ok && extra_bytes > 0) ok = fwrite(extra, 1, (size_t)extra_bytes, f) == (size_t)extra_bytes;
+  if (ok) ok = fwrite(body.data(), sizeof(float), body.size(), f) == body.size();
+  ok = (fclose(f) == 0) && ok;
+  return ok ? PROHD_OK : fail(ctx, PROHD_EINVAL, "writing the checkpoint failed%s");
+}
+
+prohd_status prohd_mlp_load(prohd_ctx* ctx, const char* path, int* D_out, int64_t* step_out, void* state,
+                            void* extra, int64_t extra_cap, int64_t* extra_bytes, void* stream) {
+  if (!ctx) return PROHD_EINVAL;
+  if (!path || !D_out || !step_out || extra_cap < 0) return fail(ctx, PROHD_EINVAL, "bad checkpoint arguments%s");
+  FILE* f = fopen(path, "rb");
+  if (!f) return fail(ctx, PROHD_EINVAL, "cannot open the checkpoint file%s");
+  unsigned char head[8 + 4 + 3 * 8];
+  int32_t d32 = 0;
+  int64_t step = 0, np = 0, nx = 0;
+  bool ok = fread(head, 1, sizeof head, f) == sizeof head && memcmp(head, kMlpMagic, 8) == 0;
+  if (ok) {
+    memcpy(&d32, head + 8, 4);
+    memcpy(&step, head + 12, 8);
+    memcpy(&np, head + 20, 8);
+    memcpy(&nx, head + 28, 8);
+    ok = d32 >= 8 && d32 <= 1024 && np == (int64_t)mlp_shape(d32).nparam && nx >= 0 && step >= 0;
+  }
+  if (!ok) {
+    fclose(f);
+    return fail(ctx, PROHD_EINVAL, "not a network checkpoint of this version%s");
+  }
+  *D_out = d32;
+  *step_out = step;
+  if (extra_bytes) *extra_bytes = nx;
+  if (!state) {  // header only
+    fclose(f);
+    return PROHD_OK;
+  }
+  if (nx > extra_cap || (nx > 0 && !extra)) {
+    fclose(f);
+    return fail(ctx, PROHD_EINVAL, "the extra-byte buffer is smaller than the checkpoint's%s");
+  }
+  if (nx > 0) ok = fread(extra, 1, (size_t)nx, f) == (size_t)nx;
+  std::vector<float> body((size_t)(3 * np));
+  if (ok) ok = fread(body.data(), sizeof(float), body.size(), f) == body.size();
+  fclose(f);
+  if (!ok) return fail(ctx, PROHD_EINVAL, "the checkpoint file is truncated%s");
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  cudaError_t e = cudaMemcpyAsync(state, body.data(), body.size() * sizeof(float), cudaMemcpyHostToDevice, st);
+  if (!e) e = cudaStreamSynchronize(st);
   return e ? cuda_fail(ctx, e) : PROHD_OK;
 }
 

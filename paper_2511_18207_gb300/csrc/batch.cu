@@ -82,9 +82,6 @@ struct BatchLayout {
   size_t end;
 };
 
-size_t item_slot_bytes(int N, int Dp) {
-  return round_up((size_t)N * 128 * sizeof(float2), 256) + round_up((size_t)8 * 2 * Dp * sizeof(double), 256);
-}
 
 int64_t items_for(int64_t n, int pts) { return ceil_div(n, pts); }
 
@@ -96,14 +93,10 @@ void table_caps(const std::vector<PairPlan>& pp, bool tensor, int64_t& max_items
   slot_cap = 0;
   nmaps = 0;
   for (const auto& q : pp) {
-    const int types = q.Dp > 128 ? 2 : 1;
-    for (int t = 0; t < types; ++t) {
-      const int N = t == 0 ? q.Dp : q.Dp - 128;
-      const int64_t ni = items_for(q.nA, kMinGramPts) + items_for(q.nB, kMinGramPts);
-      max_items += ni;
-      slot_cap += (size_t)ni * item_slot_bytes(N, q.Dp);
-      nmaps += 2;
-    }
+    const int64_t ni = items_for(q.nA, kMinGramPts) + items_for(q.nB, kMinGramPts);
+    max_items += ni;
+    slot_cap += (size_t)ni * gram_tc_item_slot_bytes(q.Dp);
+    nmaps += 2;
     max_pitems += items_for(q.nA, kMinProjRows) + items_for(q.nB, kMinProjRows);
     if (tensor) nmaps += 4;  // subset distance: A, B and their norm operands
   }
@@ -150,6 +143,7 @@ void batch_layout(Arena& a, const std::vector<PairPlan>& pp, const prohd_pair_de
     b.G = a.take<double>(DD);
     b.sumA = a.take<double>((size_t)q.D);
     b.sumB = a.take<double>((size_t)q.D);
+    b.gcorr = a.take<double>((size_t)q.D);
     b.C64 = a.take<double>(DD);
     b.C32 = a.take<float>(DD);
     b.U = a.take<double>(mD);
@@ -349,24 +343,21 @@ prohd_status write_tables(prohd_batch* b) {
   BatchLayout& L = b->L;
   const int np = b->npairs;
   const auto& pp = b->pp;
-  // ---- tensor maps: per (pair, set, type)
+  // ---- tensor maps: per (pair, set), FP32 boxes of 128 dimensions x 64 points
   std::vector<CUtensorMap> maps;
-  std::vector<int> map_of((size_t)np * 4, -1);
+  std::vector<int> map_of((size_t)np * 2, -1);
   for (int i = 0; i < np; ++i) {
     const PairPlan& q = pp[i];
-    const int types = q.Dp > 128 ? 2 : 1;
-    for (int t = 0; t < types; ++t)
-      for (int set = 0; set < 2; ++set) {
-        CUtensorMap m;
-        const float* X = set ? b->pairs[i].B : b->pairs[i].A;
-        const int64_t n = set ? q.nB : q.nA;
-        const uint32_t rows = t == 0 ? (uint32_t)std::max(128, q.Dp) : 128u;
-        if (!encode_2d(ctx, &m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, X, (uint64_t)q.D, (uint64_t)n, (uint64_t)q.D * 4,
-                       rows, 64, CU_TENSOR_MAP_SWIZZLE_NONE))
-          return bfail(ctx, PROHD_ECUDA, "tensor-map encoding failed for a batched pair");
-        map_of[(size_t)i * 4 + t * 2 + set] = (int)maps.size();
-        maps.push_back(m);
-      }
+    for (int set = 0; set < 2; ++set) {
+      CUtensorMap m;
+      const float* X = set ? b->pairs[i].B : b->pairs[i].A;
+      const int64_t n = set ? q.nB : q.nA;
+      if (!encode_2d(ctx, &m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, X, (uint64_t)q.D, (uint64_t)n, (uint64_t)q.D * 4, 128,
+                     64, CU_TENSOR_MAP_SWIZZLE_NONE))
+        return bfail(ctx, PROHD_ECUDA, "tensor-map encoding failed for a batched pair");
+      map_of[(size_t)i * 2 + set] = (int)maps.size();
+      maps.push_back(m);
+    }
   }
   // ---- subset-distance maps (tensor path): A, B tiles and their norm operands
   if (b->tensor) {
@@ -387,43 +378,37 @@ prohd_status write_tables(prohd_batch* b) {
       for (int k = 0; k < 4; ++k) maps.push_back(m[k]);
     }
   }
-  // ---- Gram items, largest first; the id list groups each pair's items by type
+  // ---- Gram items (a point range of one set, run by a CTA pair), largest first
   struct HItem {
     GcItem it;
     double cost;
   };
   std::vector<HItem> hitems;
-  std::vector<int> item_pair, item_type;
+  std::vector<int> item_pair;
   size_t slot_off = 0;
   for (int i = 0; i < np; ++i) {
     const PairPlan& q = pp[i];
-    const int types = q.Dp > 128 ? 2 : 1;
-    for (int t = 0; t < types; ++t) {
-      const int N = t == 0 ? q.Dp : q.Dp - 128;
-      const int rows = t == 0 ? std::max(128, q.Dp) : 128;
-      for (int set = 0; set < 2; ++set) {
-        const int64_t n = set ? q.nB : q.nA;
-        const int64_t ni = items_for(n, b->gram_pts);
-        for (int64_t k = 0; k < ni; ++k) {
-          HItem h;
-          h.it.tm = L.maps + map_of[(size_t)i * 4 + t * 2 + set];
-          h.it.s32 = L.hp[i].s32;
-          h.it.gacc = reinterpret_cast<float2*>(L.slots + slot_off);
-          h.it.sums = reinterpret_cast<double*>(L.slots + slot_off + round_up((size_t)N * 128 * sizeof(float2), 256));
-          slot_off += item_slot_bytes(N, q.Dp);
-          h.it.status = L.hp[i].status;
-          h.it.p0 = n * k / ni;
-          h.it.p1 = n * (k + 1) / ni;
-          h.it.D = q.D;
-          h.it.Dp = q.Dp;
-          h.it.type = t;
-          h.it.setA = set ? 0 : 1;
-          // per-chunk cost model of the kernel (fixed part + output columns + tile rows)
-          h.cost = (double)(h.it.p1 - h.it.p0) * (20.0 + 0.07 * (N + rows));
-          hitems.push_back(h);
-          item_pair.push_back(i);
-          item_type.push_back(t);
-        }
+    for (int set = 0; set < 2; ++set) {
+      const int64_t n = set ? q.nB : q.nA;
+      const int64_t ni = items_for(n, b->gram_pts);
+      for (int64_t k = 0; k < ni; ++k) {
+        HItem h;
+        h.it.tm = L.maps + map_of[(size_t)i * 2 + set];
+        h.it.s32 = L.hp[i].s32;
+        h.it.out = reinterpret_cast<float*>(L.slots + slot_off);
+        h.it.sums = reinterpret_cast<double*>(L.slots + slot_off + gram_tc_item_sums_offset(q.Dp));
+        slot_off += gram_tc_item_slot_bytes(q.Dp);
+        h.it.status = L.hp[i].status;
+        h.it.p0 = n * k / ni;
+        h.it.p1 = n * (k + 1) / ni;
+        h.it.D = q.D;
+        h.it.Dp = q.Dp;
+        h.it.setA = set ? 0 : 1;
+        // steps of the pair: 64 points each for D > 128 (the CTAs split the
+        // dimensions), 128 points for D <= 128 (they split the points)
+        h.cost = (double)(h.it.p1 - h.it.p0) / (q.Dp > 128 ? 64.0 : 128.0);
+        hitems.push_back(h);
+        item_pair.push_back(i);
       }
     }
   }
@@ -438,23 +423,16 @@ prohd_status write_tables(prohd_batch* b) {
     items[r] = hitems[perm[r]].it;
     pos[perm[r]] = (int)r;
   }
-  // id list: per pair, type 0 items (in creation order) then type 1
+  // id list: per pair, its items in creation order (set A, then set B)
   std::vector<int> ids;
   ids.reserve(hitems.size());
   for (int i = 0; i < np; ++i) {
     BPair& bp = L.hp[i];
-    for (int t = 0; t < 2; ++t) {
-      const int start = (int)ids.size();
-      for (size_t h = 0; h < hitems.size(); ++h)
-        if (item_pair[h] == i && item_type[h] == t) ids.push_back(pos[h]);
-      if (t == 0) {
-        bp.gi0 = start;
-        bp.gn0 = (int)ids.size() - start;
-      } else {
-        bp.gi1 = start;
-        bp.gn1 = (int)ids.size() - start;
-      }
-    }
+    const int start = (int)ids.size();
+    for (size_t h = 0; h < hitems.size(); ++h)
+      if (item_pair[h] == i) ids.push_back(pos[h]);
+    bp.gi0 = start;
+    bp.gn0 = (int)ids.size() - start;
   }
   b->nitems = (int)items.size();
   // ---- projection items, largest first

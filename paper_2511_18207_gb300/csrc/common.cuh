@@ -342,5 +342,50 @@ PROHD_DEV void st_cluster_f64(uint32_t addr, double v) {
   asm volatile("st.shared::cluster.f64 [%0], %1;" ::"r"(addr), "d"(v) : "memory");
 }
 
+// ---- CTA pairs (cta_group::2): one thread of the even CTA of a 2-CTA
+// cluster issues MMAs that read operands from both CTAs' shared memory (at
+// the same offsets) and accumulate into both CTAs' tensor memory. Every
+// tcgen05 instruction of such a kernel uses cta_group::2, and the
+// allocation and deallocation are collective over one warp of each CTA.
+
+PROHD_DEV void tc2_alloc(uint32_t* smem_slot, uint32_t ncols) {
+  asm volatile("tcgen05.alloc.cta_group::2.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(smem_slot)),
+               "r"(ncols)
+               : "memory");
+}
+PROHD_DEV void tc2_relinquish() {
+  asm volatile("tcgen05.relinquish_alloc_permit.cta_group::2.sync.aligned;" ::: "memory");
+}
+PROHD_DEV void tc2_dealloc(uint32_t taddr, uint32_t ncols) {
+  asm volatile("tcgen05.dealloc.cta_group::2.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols) : "memory");
+}
+// D[tmem of both CTAs] (+)= A * B^T with M = 256: A rows 0..127 from this
+// CTA's tile, 128..255 from the peer's; B rows 0..N/2-1 from this CTA's
+// tile, N/2..N-1 from the peer's.
+PROHD_DEV void tc2_mma_f16(uint32_t d_tmem, uint64_t a_desc, uint64_t b_desc, uint32_t idesc, uint32_t accumulate) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "setp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::2.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
+      "l"(a_desc), "l"(b_desc), "r"(idesc), "r"(accumulate)
+      : "memory");
+}
+// Arrive once on the mbarrier at this offset in every CTA of `mask` when all
+// tcgen05 operations this thread issued before have completed.
+PROHD_DEV void tc2_commit_mc(uint64_t* bar, uint16_t mask) {
+  asm volatile(
+      "tcgen05.commit.cta_group::2.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64 [%0], %1;" ::"r"(
+          smem_u32(bar)),
+      "h"(mask)
+      : "memory");
+}
+// Arrive on an mbarrier of any CTA of the cluster (address from map_to_cta),
+// with the default release semantics of mbarrier.arrive. Data the arriving
+// thread wrote to its own CTA's shared memory for the tensor core is made
+// visible to the async proxy by fence.proxy.async before the arrive.
+PROHD_DEV void mbar_arrive_remote(uint32_t cluster_addr) {
+  asm volatile("mbarrier.arrive.shared::cluster.b64 _, [%0];" ::"r"(cluster_addr) : "memory");
+}
+
 
 }  // namespace prohd

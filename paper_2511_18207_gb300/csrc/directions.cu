@@ -778,6 +778,37 @@ cudaError_t directions_run(prohd_ctx* ctx, const float* A, int64_t nA, const flo
   return cudaSuccess;
 }
 
+// mean = s + (sum_A + sum_B) / N: the union mean from the shifted set sums.
+__global__ void union_mean_kernel(const float* __restrict__ s32, const double* __restrict__ sumA,
+                                  const double* __restrict__ sumB, int64_t N, int D, double* __restrict__ mean) {
+  for (int d = blockIdx.x * blockDim.x + threadIdx.x; d < D; d += gridDim.x * blockDim.x)
+    mean[d] = (double)s32[d] + (sumA[d] + sumB[d]) / (double)N;
+}
+
+void covariance_layout(Arena& ws, int D) {
+  DirBufs b;
+  dir_layout(ws, D, 0, b);
+  ws.take<double>((size_t)D);  // the centroid axis the directions pass writes
+}
+
+cudaError_t covariance_run(prohd_ctx* ctx, const float* A, int64_t nA, const float* B, int64_t nB, int D, double* C,
+                           double* mean, int* status, Arena& ws, cudaStream_t st, int64_t timeout_ns) {
+  Arena run = ws;
+  DirBufs b;
+  dir_layout(ws, D, 0, b);
+  double* axis = ws.take<double>((size_t)D);
+  if (ws.overflow()) return cudaErrorMemoryAllocation;
+  cudaError_t e = directions_run(ctx, A, nA, B, nB, D, 0, 1, 0.0, 0, axis, nullptr, status, run, st, timeout_ns);
+  if (e) return e;
+  if ((e = cudaMemcpyAsync(C, b.C64, sizeof(double) * (size_t)D * D, cudaMemcpyDeviceToDevice, st))) return e;
+  if (mean) {
+    count_launch();
+    union_mean_kernel<<<(D + 255) / 256, 256, 0, st>>>(b.s32, b.sumA, b.sumB, nA + nB, D, mean);
+    e = cudaGetLastError();
+  }
+  return e;
+}
+
 cudaError_t directions_features(prohd_ctx* ctx, const float* A, int64_t nA, const float* B, int64_t nB, int D,
                                 int max_iters, double tol, uint64_t seed, double* dirs, double* eig, float* feat,
                                 int* status, Arena& ws, cudaStream_t st, int64_t timeout_ns) {

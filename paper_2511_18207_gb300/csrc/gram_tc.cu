@@ -2,33 +2,47 @@
 // tensor cores (Algorithm 2 step 2: principal components of [A; B] need the
 // union covariance), for D <= 256 with D % 4 == 0.
 //
-// Each FP32 centred value z is split exactly into three BF16 parts
-// z = h + m + l (h = bf16(z), m = bf16(z - h), l = bf16(z - h - m); the
-// residual is below 2^-25 |z|), and G is accumulated from the six products
-// hh^T + hm^T + mh^T + hl^T + lh^T + mm^T, whose sum differs from zz^T by
-// about 2^-24 |z_i z_j| per point. The tensor core accumulates 512 points in
-// FP32 in TMEM; each 512-point partial is then added into a per-CTA
-// Kahan-compensated FP32 accumulator in global memory, and a final kernel
-// sums the CTAs in FP64 in a fixed order.
+// Arithmetic. Each FP32 centred value z is split into two BF16 parts,
+// z = h + m + r with h = bf16(z), m = bf16(z - h) and |r| <= 2^-16 |z|. The
+// tensor cores accumulate X = sum h h^T + 2 sum m h^T in FP32, and
+// (X + X^T) / 2 = sum (h h^T + h m^T + m h^T) is zz^T up to the terms m m^T
+// and h r^T + r h^T, each at most 2^-16 |z_i z_j| per point. The rounding
+// residuals m and r have zero mean, so these terms cancel in the sum over
+// points except on the diagonal, where m_i^2 is always positive; the
+// converters therefore add sum (z_i^2 - h_i^2 - 2 h_i m_i) to G_ii, computed
+// per point in FP32 with one rounding. The tensor core adds 512 points (64
+// MMAs) into a TMEM accumulator, which is added in FP32 into a running sum
+// kept in the other half of TMEM; each CTA writes its running sum once, and
+// two final kernels sum the CTAs in FP64 in a fixed order and symmetrise.
 //
-// Pipeline per CTA: a TMA warp streams FP32 tiles [64 points x rows dims]
-// through a two-stage ring (dims past D arrive as zeros); eight converter
-// warps read them from shared memory, centre, split and transpose them into
-// one K-major, 128B-swizzled BF16 stage [dims x 64 points] x {h, m, l} (the
-// operand layout of the distance contraction); one thread issues the MMAs
-// slice by slice (16 points per slice, two converter warps per slice), and
-// each slice is handed back to its converters as soon as its MMAs complete,
-// so the conversion of the next chunk overlaps the MMAs of this one; four
-// epilogue warps move finished 512-point partials from TMEM into the
-// compensated accumulators.
+// Work split. Two CTAs of a cluster work as a pair on one tile of 64 points
+// per step (cta_group::2, M = 256): for D > 128 each CTA stages and converts
+// its own 128 dimensions of the same points (CTA r: dimensions 128r ..
+// 128r + 127), and the pair's two MMAs per 16-point slice produce the whole
+// 256 x 256 product, rows 128r.. in CTA r's tensor memory. Every point is
+// read from HBM once, and each CTA's tensor core reads its own A half and
+// half of B. For D <= 128 the two CTAs convert different points (CTA r the
+// r-th 64-point half of a 128-point step) in the same layout; the product's
+// diagonal blocks hold each CTA's own Gram, and the off-diagonal blocks (one
+// CTA's points against the other's) are computed and ignored.
 //
-// Work split: CTAs of type 0 own output rows 0..127 against all Dp columns,
-// type 1 (when Dp > 128) rows 128..Dp-1 against columns 128..Dp-1; each type
-// covers all points, with CTA counts in proportion to their work per point,
-// and every CTA's points lie in one set (A or B).
-// Warps: 0..7 converters, 8 MMA issuer (and TMEM owner), 9..12 epilogue,
-// 13 TMA producer.
+// Pipeline per CTA: a TMA warp streams FP32 tiles [64 points x 128 dims]
+// through a four-stage ring (dimensions past D arrive as zeros); eight
+// converter warps centre, split and transpose them into K-major,
+// 128B-swizzled BF16 tile pairs {h, 2m} [128 dims x 64 points] (the operand
+// layout of the distance contraction; two pairs, used by alternate steps, so
+// conversion runs a step ahead of the MMAs) and hand each 16-point slice to the
+// even CTA's MMA thread (a cluster-scope mbarrier arrive); that thread issues
+// the slice's two MMAs and hands the slice back to both CTAs' converters when
+// they complete; four epilogue warps per CTA fold each 512-point accumulator
+// into the running sum. The odd CTA's converters and epilogue signal the even
+// CTA's barriers with remote mbarrier arrives after fence.proxy.async (a
+// release at cluster scope costs a memory barrier per arrive, which stalled
+// every step).
+// Warps: 0..7 converters, 8 MMA issuer (even CTA) and TMEM owner, 9..12
+// epilogue, 13 TMA producer.
 #include <cuda_bf16.h>
+#include <limits.h>
 #include <string.h>
 
 #include <algorithm>
@@ -38,14 +52,22 @@
 
 namespace prohd {
 
-constexpr int kGcPts = 64;          // points per chunk (one 128-byte K row of BF16)
+constexpr int kGcPts = 64;          // points per tile (one 128-byte K row of BF16)
+constexpr int kGcRows = 128;        // dimensions per CTA
 constexpr int kGcConv = 8;          // converter warps, 8 points each
 constexpr int kGcEpi = 4;
 constexpr int kGcMmaWarp = kGcConv;
 constexpr int kGcTmaWarp = kGcConv + 1 + kGcEpi;
 constexpr int kGcThreads = (kGcTmaWarp + 1) * 32;
-constexpr int kGcFlush = 8;         // chunks per FP32 accumulation in TMEM (512 points)
-constexpr int kGcMaxRows = 256;
+constexpr int kGcStages = 4;        // FP32 staging ring
+constexpr int kGcBufs = 2;          // operand tile pairs: conversion runs a step ahead of the MMAs
+constexpr int kGcFlush = 8;         // steps per TMEM accumulation (512 points per CTA row)
+constexpr int kGcSlices = kGcPts / 16;
+constexpr uint32_t kGcTileBytes = kGcRows * 128;             // one BF16 operand tile
+constexpr uint32_t kGcStageBytes = kGcPts * kGcRows * 4;     // one FP32 stage
+constexpr uint32_t kGcSumCol = 256;                          // TMEM column of the running sums
+constexpr int kGcSlotFloats = 2 * 256 * kGcRows;             // per pair: [rank][col][row] partial products
+constexpr int kGcSumsDoubles = 2 * kGcConv * 2 * kGcRows;    // per pair: [rank][warp][z | corr][dim]
 
 // Packed round-to-nearest conversion of two FP32 values to BF16x2 (a in the
 // low half, b in the high half), and the FP32 values of the halves.
@@ -65,545 +87,590 @@ __device__ __forceinline__ void kahan_add(float& s, float& c, float x) {
   s = t;
 }
 
-constexpr int kGcSlices = kGcPts / 16;  // K-steps of one chunk
-
 struct GcSmem {
-  uint64_t ffull[2], fempty[2], sfull[kGcSlices], sempty[kGcSlices], acc_full[2], acc_empty[2], drain;
+  uint64_t ffull[kGcStages], fempty[kGcStages];
+  uint64_t sfull[kGcBufs][kGcSlices];   // even CTA: slice converted by both CTAs (4 arrivals)
+  uint64_t sempty[kGcBufs][kGcSlices];  // slice's MMAs done (committed to both CTAs)
+  uint64_t acc_full;           // accumulator holds a finished interval (committed to both CTAs)
+  uint64_t acc_empty;          // even CTA: accumulator read by both CTAs' epilogues (8 arrivals)
+  uint64_t drain;
   uint32_t tmem_base;
-  int abort;
-  int next;  // work item taken by this CTA (batched launches)
+  int abort;       // set by this CTA's waits or by the peer's
+  int next;        // batched launches: the item both CTAs take next (written by the even CTA)
+  int my_abort;    // abort snapshots exchanged between items
+  int peer_abort;
 };
 
-__host__ __device__ constexpr size_t gc_tile_bytes(int rows) { return (size_t)rows * 128; }
-__host__ __device__ constexpr size_t gc_stage_bytes(int rows) { return (size_t)kGcPts * rows * 4; }
-__host__ __device__ constexpr size_t gc_smem_bytes(int rows) {
-  return 1024 + 3 * gc_tile_bytes(rows) + 2 * gc_stage_bytes(rows) + sizeof(GcSmem);
-}
+constexpr size_t kGcSmemBytes =
+    1024 + (size_t)kGcBufs * 2 * kGcTileBytes + (size_t)kGcStages * kGcStageBytes + sizeof(GcSmem);
 
 struct GcParams {
   int64_t nA, nB;
   int D, Dp;
   const float* s32;   // pilot shift [D]
-  int nc0;            // CTAs of type 0 (the rest are type 1)
-  int ncA0, ncA1;     // CTAs of each type that read set A (the rest read B)
-  int rows0, rows1;   // tile rows (dims) of each type, 128, 192 or 256; also the FP32 box width
-  int N0, N1;         // output columns of each type
-  float2* gacc;       // [gridDim][256 x 128] Kahan (sum, compensation) partials, element (col, row) at col*128 + row
-  double* sums;       // [gridDim][kGcConv][2][Dp] FP64 per-warp set sums of z - s
+  int nclu, ncA;      // clusters; clusters reading A (the rest read B)
+  float* out;         // [nclu] x kGcSlotFloats
+  double* sums;       // [nclu] x kGcSumsDoubles
   int* status;
   uint64_t timeout_ns;
-  // batched launches: CTAs take items from the table through an atomic
-  // ticket; nullptr for one pair (CTA i is item i of the static split above)
+  // batched launches: clusters take items from the table through an atomic
+  // ticket; nullptr for one pair (cluster c is item c of the static split)
   const GcItem* items;
   int nitems;
   int* ticket;
 };
 
-// Splits two FP32 values exactly enough into BF16 triples (see the file
-// comment) and returns the packed pairs (point i in the low half).
-__device__ __forceinline__ void gc_split_pair(float z0, float z1, uint32_t& h, uint32_t& m, uint32_t& l) {
-  // one packed BF16x2 conversion per split level, unpacked to FP32 by
-  // shifts (a BF16 is the top half of an FP32)
-  h = bf16x2_rn(z0, z1);
-  const float r0 = z0 - bf16_lo(h), r1 = z1 - bf16_hi(h);
-  m = bf16x2_rn(r0, r1);
-  l = bf16x2_rn(r0 - bf16_lo(m), r1 - bf16_hi(m));
-}
-
-// One converter warp's share of a chunk: 8 points x 32T dims from the FP32
-// stage (row stride 32T floats) into the three BF16 tiles. `st` points at
-// this warp's first point and this lane's dimension, `dst` at this lane's
-// 16-byte slot in row `lane` of the h tile (rows lane + 32 t sit 4096 t
-// bytes further). Only the first `nv` points are real when !FULL; the rest
-// contribute zeros. Dimensions past D were zero-filled by the copy and have
-// a zero shift.
-template <int T, bool FULL>
-__device__ __forceinline__ void gc_convert(const float* __restrict__ st, uint8_t* __restrict__ dst,
-                                           const float (&shift)[8], float (&ss)[8], float (&sc)[8], int nv) {
-  constexpr int BW = 32 * T;
-  constexpr int TB = 4096 * T;  // bytes of one BF16 tile (32T rows x 128 B)
+// Splits eight points of one dimension into the {h, 2m} operand rows (16
+// bytes each, point i in the low half of pair i/2) and accumulates the set
+// sum (Kahan) and the diagonal correction sum (z^2 - h^2 - 2hm). Only the
+// first `nv` points are real when !FULL; the rest contribute zeros.
+template <bool FULL>
+__device__ __forceinline__ void gc_convert_row(const float* __restrict__ st, uint8_t* __restrict__ dst, float shift,
+                                               float& ss, float& sc, float& cr, int nv) {
+  float z[8];
 #pragma unroll
-  for (int t = 0; t < T; ++t) {
-    float z[8];
-#pragma unroll
-    for (int i = 0; i < 8; ++i) {
-      const float x = st[i * BW + 32 * t];
-      z[i] = (FULL || i < nv) ? x - shift[t] : 0.f;
-    }
-    kahan_add(ss[t], sc[t], ((z[0] + z[1]) + (z[2] + z[3])) + ((z[4] + z[5]) + (z[6] + z[7])));
-    uint32_t h[4], m[4], l[4];
-#pragma unroll
-    for (int i = 0; i < 4; ++i) gc_split_pair(z[2 * i], z[2 * i + 1], h[i], m[i], l[i]);
-    uint8_t* o = dst + t * 4096;
-    *reinterpret_cast<uint4*>(o) = make_uint4(h[0], h[1], h[2], h[3]);
-    *reinterpret_cast<uint4*>(o + TB) = make_uint4(m[0], m[1], m[2], m[3]);
-    *reinterpret_cast<uint4*>(o + 2 * TB) = make_uint4(l[0], l[1], l[2], l[3]);
+  for (int i = 0; i < 8; ++i) {
+    const float x = st[i * kGcRows];
+    z[i] = (FULL || i < nv) ? x - shift : 0.f;
   }
-}
-
-// All chunks of one converter warp (slice `warp / 2` of every chunk).
-template <int T>
-__device__ __forceinline__ bool gc_converter(GcSmem& S, const float* stage, uint8_t* tiles, int warp, int lane,
-                                             int nchunks, uint32_t g0, int64_t p0, int64_t p1,
-                                             const float (&shift)[8], float (&ss)[8], float (&sc)[8],
-                                             uint64_t timeout_ns) {
-  constexpr int BW = 32 * T;
-  volatile int* abort = &S.abort;
-  const int s = warp >> 1;
-  const float* st0 = stage + (size_t)(warp * 8) * BW + lane;
-  uint8_t* dst = tiles + lane * 128 + ((warp ^ (lane & 7)) * 16);
-  for (int c = 0; c < nchunks; ++c) {
-    const uint32_t g = g0 + (uint32_t)c;  // ring position over all of this CTA's chunks
-    const int f = g & 1;
-    int got = 1;
-    if (lane == 0) {
-      got = mbar_wait_bounded(&S.sempty[s], (g & 1u) ^ 1u, abort, timeout_ns) &&
-            mbar_wait_bounded(&S.ffull[f], (g >> 1) & 1u, abort, timeout_ns);
-    }
-    got = __shfl_sync(0xffffffffu, got, 0);
-    if (!got) return false;
-    const float* st = st0 + (size_t)f * kGcPts * BW;
-    const int64_t left = p1 - (p0 + (int64_t)c * kGcPts + warp * 8);
-    if (left >= 8)
-      gc_convert<T, true>(st, dst, shift, ss, sc, 8);
-    else
-      gc_convert<T, false>(st, dst, shift, ss, sc, left > 0 ? (int)left : 0);
-    fence_proxy_async();
-    __syncwarp();
-    if (lane == 0) {
-      mbar_arrive(&S.fempty[f]);
-      mbar_arrive(&S.sfull[s]);
-    }
+  kahan_add(ss, sc, ((z[0] + z[1]) + (z[2] + z[3])) + ((z[4] + z[5]) + (z[6] + z[7])));
+  uint32_t h[4], m2[4];
+  float corr = 0.f;
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const float z0 = z[2 * i], z1 = z[2 * i + 1];
+    h[i] = bf16x2_rn(z0, z1);
+    const float h0 = bf16_lo(h[i]), h1 = bf16_hi(h[i]);
+    const float e0 = z0 - h0, e1 = z1 - h1;  // exact
+    m2[i] = bf16x2_rn(2.f * e0, 2.f * e1);   // 2m, exact doubling of bf16(e)
+    // z^2 - h^2 - 2hm = e (z + h) - h (2m): h (2m) is exact in FP32, the
+    // fused multiply-add rounds once
+    corr += fmaf(e0, z0 + h0, -(h0 * bf16_lo(m2[i])));
+    corr += fmaf(e1, z1 + h1, -(h1 * bf16_hi(m2[i])));
   }
-  return true;
+  cr += corr;
+  *reinterpret_cast<uint4*>(dst) = make_uint4(h[0], h[1], h[2], h[3]);
+  *reinterpret_cast<uint4*>(dst + kGcTileBytes) = make_uint4(m2[0], m2[1], m2[2], m2[3]);
 }
 
-// 14 warps: one SMSP holds 4 of them, so 16384 / (4 x 32) = 128 registers per thread at most.
-__global__ void __maxnreg__(128)
-    gram_tc_kernel(const GcParams p, const __grid_constant__ CUtensorMap tmA0, const __grid_constant__ CUtensorMap tmB0,
-                   const __grid_constant__ CUtensorMap tmA1, const __grid_constant__ CUtensorMap tmB1) {
+// Waits with the kernel's limit; on failure the peer CTA is told to stop too.
+__device__ __forceinline__ bool gc_wait(uint64_t* bar, uint32_t parity, volatile int* abort, uint32_t peer_abort,
+                                        uint64_t timeout_ns) {
+  if (mbar_wait_bounded(bar, parity, abort, timeout_ns)) return true;
+  st_cluster_s32(peer_abort, 1);
+  return false;
+}
+
+__global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kGcThreads, 1)
+    gram_tc_kernel(const GcParams p, const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB) {
   extern __shared__ uint8_t smem_raw[];
   uint8_t* base = smem_align<1024>(smem_raw);
-  const bool batched = p.items != nullptr;
-  const bool btype0 = (int)blockIdx.x < p.nc0;
-  // shared-memory layout for the largest tile this CTA can meet
-  const int lrows = batched ? kGcMaxRows : (btype0 ? p.rows0 : p.rows1);
-  const size_t ltb = gc_tile_bytes(lrows);
-  uint8_t* tiles = base;                                    // [3][rows x 128 B]
-  float* stage = reinterpret_cast<float*>(base + 3 * ltb);  // [2][64][rows]
-  GcSmem& S = *reinterpret_cast<GcSmem*>(base + 3 * ltb + 2 * gc_stage_bytes(lrows));
-  volatile int* abort = &S.abort;
+  uint8_t* tiles = base;  // [kGcBufs][h, 2m]
+  float* stage = reinterpret_cast<float*>(base + kGcBufs * 2 * kGcTileBytes);  // [kGcStages][64][128]
+  GcSmem& S =
+      *reinterpret_cast<GcSmem*>(base + kGcBufs * 2 * kGcTileBytes + (size_t)kGcStages * kGcStageBytes);
+  const uint32_t rank = cluster_rank();
+  const bool leader = rank == 0;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  volatile int* abort = &S.abort;
+  const uint32_t peer_abort = map_to_cta(&S.abort, rank ^ 1u);
+  const bool batched = p.items != nullptr;
 
   if (threadIdx.x == 0) {
-    for (int s = 0; s < 2; ++s) {
+    for (int s = 0; s < kGcStages; ++s) {
       mbar_init(&S.ffull[s], 1);
       mbar_init(&S.fempty[s], kGcConv);
-      mbar_init(&S.acc_full[s], 1);
-      mbar_init(&S.acc_empty[s], kGcEpi);
     }
-    for (int s = 0; s < kGcSlices; ++s) {
-      mbar_init(&S.sfull[s], kGcConv / kGcSlices);
-      mbar_init(&S.sempty[s], 1);
-    }
+    for (int b = 0; b < kGcBufs; ++b)
+      for (int s = 0; s < kGcSlices; ++s) {
+        mbar_init(&S.sfull[b][s], 2 * (kGcConv / kGcSlices));
+        mbar_init(&S.sempty[b][s], 1);
+      }
+    mbar_init(&S.acc_full, 1);
+    mbar_init(&S.acc_empty, 2 * kGcEpi);
     mbar_init(&S.drain, 1);
     S.abort = 0;
+    S.next = 0;
+    S.my_abort = 0;
+    S.peer_abort = 0;
     fence_mbar_init();
   }
   if (warp == kGcMmaWarp) {
-    tc_alloc(&S.tmem_base, 512);
-    tc_relinquish();
+    tc2_alloc(&S.tmem_base, 512);
+    tc2_relinquish();
   }
   tc_fence_before();
   __syncthreads();
+  cluster_sync();  // both CTAs' barriers exist before any remote arrive
   tc_fence_after();
   const uint32_t tmem = S.tmem_base;
 
-  // Ring positions run on over all items of this CTA, so every barrier's
-  // phase parity follows from one chunk counter (g0 + c) and one flush
-  // counter per consumer.
-  uint32_t g0 = 0, armed = 0;
-  uint32_t ab = 0, aph = 0;  // TMEM accumulator ring (MMA issuer and epilogue keep their own copies)
+  // Ring positions and accumulation intervals run on over all items, so
+  // every barrier's phase parity follows from two counters.
+  uint32_t g0 = 0, f0 = 0;
+  const int clu = (int)(blockIdx.x >> 1);
 
   for (int iter = 0;; ++iter) {
     GcItem w;
     if (!batched) {
       if (iter > 0) break;
-      // this CTA's set and point range in the static split of one pair
-      const int ci = btype0 ? (int)blockIdx.x : (int)blockIdx.x - p.nc0;
-      const int nct = btype0 ? p.nc0 : (int)gridDim.x - p.nc0;
-      const int ncA = btype0 ? p.ncA0 : p.ncA1;
-      const bool setA = ci < ncA;
+      const bool setA = clu < p.ncA;
       const int64_t n = setA ? p.nA : p.nB;
-      const int cj = setA ? ci : ci - ncA, ncj = setA ? ncA : nct - ncA;
-      w.tm = btype0 ? (setA ? &tmA0 : &tmB0) : (setA ? &tmA1 : &tmB1);
+      const int cj = setA ? clu : clu - p.ncA, ncj = setA ? p.ncA : p.nclu - p.ncA;
+      w.tm = setA ? &tmA : &tmB;
       w.s32 = p.s32;
-      w.gacc = p.gacc + (size_t)blockIdx.x * (256 * 128);
-      w.sums = p.sums + (size_t)blockIdx.x * kGcConv * 2 * p.Dp;
+      w.out = p.out + (size_t)clu * kGcSlotFloats;
+      w.sums = p.sums + (size_t)clu * kGcSumsDoubles;
       w.status = p.status;
       w.p0 = n * cj / ncj;
       w.p1 = n * (cj + 1) / ncj;
       w.D = p.D;
       w.Dp = p.Dp;
-      w.type = btype0 ? 0 : 1;
       w.setA = setA ? 1 : 0;
     } else {
-      if (threadIdx.x == 0) S.next = atomicAdd(p.ticket, 1);
-      __syncthreads();
+      // both CTAs take the same item and agree on stopping: each publishes
+      // its abort state, the even CTA the ticket, then a cluster barrier
+      cluster_sync();
+      if (threadIdx.x == 0) {
+        const int a = *abort;
+        S.my_abort = a;
+        st_cluster_s32(map_to_cta(&S.peer_abort, rank ^ 1u), a);
+        if (leader) {
+          const int it = atomicAdd(p.ticket, 1);
+          S.next = it;
+          st_cluster_s32(map_to_cta(&S.next, 1), it);
+        }
+      }
+      cluster_sync();
+      if (S.my_abort | S.peer_abort) break;
       const int it = S.next;
       if (it >= p.nitems) break;
       w = p.items[it];
     }
-    const bool type0 = w.type == 0;
-    const int rows = type0 ? max(128, w.Dp) : 128;  // tile rows (dims loaded, zero padded) = FP32 box width
-    const int N = type0 ? w.Dp : w.Dp - 128;
-    const int dim0 = type0 ? 0 : 128;                // first dimension loaded
-    const size_t tb = gc_tile_bytes(rows);
-    const int64_t p0 = w.p0, p1 = w.p1;
-    const int nchunks = (int)((p1 - p0 + kGcPts - 1) / kGcPts);
-    const bool setA = w.setA != 0;
+    const bool split_dims = w.Dp > kGcRows;
+    const int64_t span = split_dims ? kGcPts : 2 * kGcPts;           // points per step of the pair
+    const int64_t cta_off = split_dims ? 0 : (int64_t)rank * kGcPts;  // this CTA's first point of a step
+    const int dim0 = split_dims ? (int)rank * kGcRows : 0;
+    const int nsteps = w.p1 > w.p0 ? (int)((w.p1 - w.p0 + span - 1) / span) : 0;
+    const int nint = (nsteps + kGcFlush - 1) / kGcFlush;
+    const int N = split_dims ? 256 : 2 * w.Dp;           // MMA N
+    const int ucol0 = split_dims ? 0 : (int)rank * w.Dp;  // this CTA's useful accumulator columns
+    const int ucols = split_dims ? 256 : w.Dp;
+    const int urows = split_dims ? kGcRows : w.Dp;        // useful TMEM lanes
 
     if (warp == kGcTmaWarp) {
-      // ---------------- TMA producer: FP32 point tiles into the 2-stage ring ----------------
+      // ---------------- TMA producer ----------------
       if (lane == 0) {
         tma_prefetch_desc(w.tm);
-        const uint32_t bytes = (uint32_t)gc_stage_bytes(rows);
-        for (int c = 0; c < nchunks; ++c) {
+        uint32_t armed = g0;
+        for (int c = 0; c < nsteps; ++c) {
           const uint32_t g = g0 + (uint32_t)c;
-          const int f = g & 1;
-          if (!mbar_wait_bounded(&S.fempty[f], ((g >> 1) & 1u) ^ 1u, abort, p.timeout_ns)) break;
-          mbar_arrive_expect_tx(&S.ffull[f], bytes);
-          tma_load_2d(stage + (size_t)f * kGcPts * rows, w.tm, dim0, (int)(p0 + (int64_t)c * kGcPts), &S.ffull[f]);
+          const int f = (int)(g % kGcStages);
+          if (!gc_wait(&S.fempty[f], ((g / kGcStages) & 1u) ^ 1u, abort, peer_abort, p.timeout_ns)) break;
+          mbar_arrive_expect_tx(&S.ffull[f], kGcStageBytes);
+          const int64_t y = w.p0 + (int64_t)c * span + cta_off;
+          tma_load_2d(stage + (size_t)f * (kGcStageBytes / 4), w.tm, dim0, (int)y, &S.ffull[f]);
           armed = g + 1;
         }
         if (*abort) {
           // error path: let the copies already issued land before the CTA exits
-          for (uint32_t g = armed >= 2 ? armed - 2 : 0; g < armed; ++g) {
+          for (uint32_t g = armed >= g0 + kGcStages ? armed - kGcStages : g0; g < armed; ++g) {
             const uint64_t t0 = global_timer_ns();
-            while (!mbar_try_wait(&S.ffull[g & 1], (g >> 1) & 1u) && global_timer_ns() - t0 < 2000000ull) {
+            while (!mbar_try_wait(&S.ffull[g % kGcStages], (g / kGcStages) & 1u) &&
+                   global_timer_ns() - t0 < 2000000ull) {
             }
           }
         }
       }
     } else if (warp < kGcConv) {
       // ---------------- converters: centre, split, transpose ----------------
-      const int T = rows / 32;  // dims per lane: dim = dim0 + lane + 32 t
-      float ss[8], sc[8], shift[8];
+      const int s = warp >> 1;
+      const float* st0 = stage + (size_t)(warp * 8) * kGcRows + lane;
+      uint8_t* dst0 = tiles + lane * 128 + ((warp ^ (lane & 7)) * 16);
+      float ss[4], sc[4], cr[4], shift[4];
 #pragma unroll
-      for (int t = 0; t < 8; ++t) {
-        ss[t] = sc[t] = 0.f;
+      for (int t = 0; t < 4; ++t) {
+        ss[t] = sc[t] = cr[t] = 0.f;
         const int d = dim0 + lane + 32 * t;
-        shift[t] = (t < T && d < w.D) ? w.s32[d] : 0.f;
+        shift[t] = d < w.D ? w.s32[d] : 0.f;
       }
-      if (T == 8)
-        gc_converter<8>(S, stage, tiles, warp, lane, nchunks, g0, p0, p1, shift, ss, sc, p.timeout_ns);
-      else if (T == 6)
-        gc_converter<6>(S, stage, tiles, warp, lane, nchunks, g0, p0, p1, shift, ss, sc, p.timeout_ns);
-      else
-        gc_converter<4>(S, stage, tiles, warp, lane, nchunks, g0, p0, p1, shift, ss, sc, p.timeout_ns);
+      for (int c = 0; c < nsteps; ++c) {
+        const uint32_t g = g0 + (uint32_t)c;
+        const int f = (int)(g % kGcStages);
+        const int bf = (int)(g % kGcBufs);
+        const uint32_t use = g / kGcBufs;  // this buffer's use count: wait for the MMAs of its previous use
+        uint8_t* dst = dst0 + (size_t)bf * 2 * kGcTileBytes;
+        int got = 1;
+        if (lane == 0)
+          got = gc_wait(&S.sempty[bf][s], (use & 1u) ^ 1u, abort, peer_abort, p.timeout_ns) &&
+                gc_wait(&S.ffull[f], (g / kGcStages) & 1u, abort, peer_abort, p.timeout_ns);
+        got = __shfl_sync(0xffffffffu, got, 0);
+        if (!got) break;
+        const float* st = st0 + (size_t)f * kGcPts * kGcRows;
+        const int64_t left = w.p1 - (w.p0 + (int64_t)c * span + cta_off + warp * 8);
+        if (left >= 8) {
+#pragma unroll
+          for (int t = 0; t < 4; ++t)
+            gc_convert_row<true>(st + 32 * t, dst + t * 4096, shift[t], ss[t], sc[t], cr[t], 8);
+        } else {
+          const int nv = left > 0 ? (int)left : 0;
+#pragma unroll
+          for (int t = 0; t < 4; ++t)
+            gc_convert_row<false>(st + 32 * t, dst + t * 4096, shift[t], ss[t], sc[t], cr[t], nv);
+        }
+        fence_proxy_async();
+        __syncwarp();
+        if (lane == 0) {
+          mbar_arrive(&S.fempty[f]);
+          if (leader) mbar_arrive(&S.sfull[bf][s]);
+          else mbar_arrive_remote(map_to_cta(&S.sfull[bf][s], 0));
+        }
+      }
       // A non-finite coordinate makes its dimension's running sum non-finite
       // (so does an FP32 overflow of the sum, which would also ruin G).
       bool bad = false;
-      double* out = w.sums + (size_t)warp * 2 * w.Dp;
+      double* out = w.sums + (size_t)(rank * kGcConv + warp) * 2 * kGcRows;
 #pragma unroll
-      for (int t = 0; t < 8; ++t) {
-        const int d = dim0 + lane + 32 * t;
-        if (t < T) bad |= !isfinite(ss[t]) || !isfinite(sc[t]);
-        if (t < T && d < w.Dp) {
-          const double v = type0 ? (double)ss[t] - (double)sc[t] : 0.0;
-          out[(setA ? 0 : w.Dp) + d] = v;
-          out[(setA ? w.Dp : 0) + d] = 0.0;
-        }
+      for (int t = 0; t < 4; ++t) {
+        bad |= !isfinite(ss[t]) || !isfinite(sc[t]) || !isfinite(cr[t]);
+        out[lane + 32 * t] = (double)ss[t] - (double)sc[t];
+        out[kGcRows + lane + 32 * t] = (double)cr[t];
       }
       if (__any_sync(0xffffffffu, bad) && lane == 0) atomicMax(w.status, (int)PROHD_ENONFINITE);
     } else if (warp == kGcMmaWarp) {
-      // ---------------- MMA issuer ----------------
-      if (lane == 0) {
-        const uint32_t idesc = idesc_f16(1, 128, N);
-        // products (A part, B part): hh, hm, mh, hl, lh, mm
-        const int pa[6] = {0, 0, 1, 0, 2, 1};
-        const int pb[6] = {0, 1, 0, 2, 0, 1};
+      // ---------------- MMA issuer (even CTA) ----------------
+      if (leader && lane == 0) {
+        const uint32_t idesc = idesc_f16(1, 256, N);
         int in_acc = 0;
-        const uint32_t t0 = smem_u32(tiles);
-        for (int c = 0; c < nchunks; ++c) {
+        uint32_t fi = f0;
+        for (int c = 0; c < nsteps; ++c) {
           const uint32_t g = g0 + (uint32_t)c;
           if (in_acc == 0) {
-            if (!mbar_wait_bounded(&S.acc_empty[ab], aph ^ 1, abort, p.timeout_ns)) break;
+            if (!gc_wait(&S.acc_empty, (fi & 1u) ^ 1u, abort, peer_abort, p.timeout_ns)) break;
             tc_fence_after();
           }
-          const uint32_t d_tmem = tmem + ab * 256;
           bool ok = true;
+          const int bf = (int)(g % kGcBufs);
+          const uint32_t use = g / kGcBufs;
+          const uint32_t th = smem_u32(tiles) + (uint32_t)bf * 2 * kGcTileBytes, tm2 = th + kGcTileBytes;
 #pragma unroll
           for (int k = 0; k < kGcSlices; ++k) {
-            if (!mbar_wait_bounded(&S.sfull[k], g & 1u, abort, p.timeout_ns)) {
+            if (!gc_wait(&S.sfull[bf][k], use & 1u, abort, peer_abort, p.timeout_ns)) {
               ok = false;
               break;
             }
             tc_fence_after();
-#pragma unroll
-            for (int q = 0; q < 6; ++q)
-              tc_mma_f16(d_tmem, smem_desc_sw128(t0 + (uint32_t)(pa[q] * tb) + k * 32),
-                         smem_desc_sw128(t0 + (uint32_t)(pb[q] * tb) + k * 32), idesc, (in_acc | q | k) != 0);
-            tc_commit(&S.sempty[k]);  // slice k may be overwritten once these MMAs complete
+            const uint64_t bh = smem_desc_sw128(th + k * 32);
+            tc2_mma_f16(tmem, bh, bh, idesc, (in_acc | k) != 0);
+            tc2_mma_f16(tmem, smem_desc_sw128(tm2 + k * 32), bh, idesc, 1u);
+            tc2_commit_mc(&S.sempty[bf][k], 0x3);  // slice k of this buffer may be overwritten in both CTAs
           }
           if (!ok) break;
-          if (++in_acc == kGcFlush || c == nchunks - 1) {
-            tc_commit(&S.acc_full[ab]);
+          if (++in_acc == kGcFlush || c == nsteps - 1) {
+            tc2_commit_mc(&S.acc_full, 0x3);
             in_acc = 0;
-            ab ^= 1;
-            if (ab == 0) aph ^= 1;
+            ++fi;
           }
         }
       }
     } else {
-      // ---------------- epilogue: FP32 TMEM partials -> compensated accumulators ----------------
-      const int q = warp & 3;
-      const int row = q * 32 + lane;  // output row within this type's 128 rows
-      float2* gsl = w.gacc;
-      const int nflush = (nchunks + kGcFlush - 1) / kGcFlush;
+      // ---------------- epilogue: accumulator -> running sum -> global ----------------
+      const int q = warp & 3;  // TMEM lane quarter this warp may access
+      const int row = q * 32 + lane;
+      const bool useful = q * 32 < urows;
+      const uint32_t acc_empty_leader = map_to_cta(&S.acc_empty, 0);
+      const uint32_t lane_base = tmem + ((uint32_t)(q * 32) << 16);
       bool ok = true;
-      for (int fl = 0; fl < nflush; ++fl) {
+      for (int i = 0; i < nint; ++i) {
+        const uint32_t fi = f0 + (uint32_t)i;
         int got = 0;
-        if (ok && lane == 0) got = mbar_wait_bounded(&S.acc_full[ab], aph, abort, p.timeout_ns) ? 1 : 0;
+        if (lane == 0) got = gc_wait(&S.acc_full, fi & 1u, abort, peer_abort, p.timeout_ns) ? 1 : 0;
         got = __shfl_sync(0xffffffffu, got, 0);
-        ok = ok && got;
-        if (!ok) break;
-        tc_fence_after();
-        const uint32_t taddr = tmem + ((uint32_t)(q * 32) << 16) + ab * 256;
-        for (int cc = 0; cc < N / 32; ++cc) {
-          // running sums are Kahan-compensated FP32 pairs (sum, compensation):
-          // as accurate as FP64 accumulation of the 512-point partials, and
-          // FP64 arithmetic is scarce here. Loads are issued before any add.
-          float2 acc[32];
-          float2* col0 = gsl + (size_t)(cc * 32) * 128 + row;
-#pragma unroll
-          for (int c = 0; c < 32; ++c) acc[c] = fl == 0 ? make_float2(0.f, 0.f) : __ldcg(col0 + (size_t)c * 128);
-          float v[32];
-          __syncwarp();
-          tc_ld_32x32b_x32(taddr + cc * 32, v);
-          tc_wait_ld();
-#pragma unroll
-          for (int c = 0; c < 32; ++c) {
-            kahan_add(acc[c].x, acc[c].y, v[c]);
-            __stcg(col0 + (size_t)c * 128, acc[c]);
-          }
+        if (!got) {
+          ok = false;
+          break;
         }
+        tc_fence_after();
+        if (useful) {
+          for (int cc = 0; cc < ucols / 32; ++cc) {
+            float v[32], sum[32];
+            __syncwarp();
+            tc_ld_32x32b_x32(lane_base + (uint32_t)(ucol0 + cc * 32), v);
+            if (i > 0) tc_ld_32x32b_x32(lane_base + kGcSumCol + (uint32_t)(cc * 32), sum);
+            tc_wait_ld();
+#pragma unroll
+            for (int j = 0; j < 32; ++j) sum[j] = i > 0 ? sum[j] + v[j] : v[j];
+            tc_st_32x32b_x32(lane_base + kGcSumCol + (uint32_t)(cc * 32), sum);
+          }
+          tc_wait_st();
+        }
+        // this CTA's half of the accumulator is read: tell the MMA thread
         tc_fence_before();
         __syncwarp();
-        if (lane == 0) mbar_arrive(&S.acc_empty[ab]);
-        ab ^= 1;
-        if (ab == 0) aph ^= 1;
+        if (lane == 0) {
+          if (leader) mbar_arrive(&S.acc_empty);
+          else mbar_arrive_remote(acc_empty_leader);
+        }
       }
-      if (nflush == 0)
-        for (int col = 0; col < N; ++col) gsl[(size_t)col * 128 + row] = make_float2(0.f, 0.f);
+      if (ok) {
+        // the item's partial product: [col][row], useful columns only (zeros for an empty item)
+        float* o = w.out + (size_t)rank * ucols * kGcRows;
+        for (int cc = 0; cc < ucols / 32; ++cc) {
+          float sum[32];
+          if (useful && nint > 0) {
+            __syncwarp();
+            tc_ld_32x32b_x32(lane_base + kGcSumCol + (uint32_t)(cc * 32), sum);
+            tc_wait_ld();
+          } else {
+#pragma unroll
+            for (int j = 0; j < 32; ++j) sum[j] = 0.f;
+          }
+#pragma unroll
+          for (int j = 0; j < 32; ++j) o[(size_t)(cc * 32 + j) * kGcRows + row] = sum[j];
+        }
+        tc_fence_before();
+      }
     }
-    // the item is finished by every role: the rings are idle, so the next
-    // item may change the tile geometry
+    // the item is finished by every role of this CTA: the rings are idle
     __syncthreads();
-    g0 += (uint32_t)nchunks;
-    if (*abort) break;
+    g0 += (uint32_t)nsteps;
+    f0 += (uint32_t)nint;
+    if (!batched) break;
   }
 
+  // every MMA the pair issued has completed before either CTA moves on
   if (warp == kGcMmaWarp && lane == 0) {
-    tc_commit(&S.drain);
-    const uint64_t t0d = global_timer_ns();
-    while (!mbar_try_wait(&S.drain, 0) && global_timer_ns() - t0d < 1000000000ull) {
+    if (leader) tc2_commit_mc(&S.drain, 0x3);
+    const uint64_t t0 = global_timer_ns();
+    while (!mbar_try_wait(&S.drain, 0) && global_timer_ns() - t0 < 1000000000ull) {
     }
   }
   __syncthreads();
-  // a batched launch reports a timeout batch-wide: items this CTA never ran belong to other pairs
   if (threadIdx.x == 0 && S.abort) atomicMax(p.status, (int)PROHD_ETIMEOUT);
+  // neither CTA leaves while the other may still read its shared memory or
+  // arrive on its barriers; then the pair frees its tensor memory together
+  cluster_sync();
   if (warp == kGcMmaWarp) {
     __syncwarp();
     tc_fence_after();
-    tc_dealloc(tmem, 512);
+    tc2_dealloc(tmem, 512);
   }
 }
 
-// G (upper triangle, FP64, row-major D x D) and the set sums, summed over the
-// CTAs of each type in a fixed order.
-__global__ void gram_tc_reduce_kernel(const GcParams p, int ncta, double* __restrict__ G, double* __restrict__ sumA,
-                                      double* __restrict__ sumB) {
-  const int D = p.D;
+// ---------------------------------------------------------------- reduction
+
+// The partial product X of a list of pair slots: X[i][j] for one slot list
+// entry. Split dimensions (Dp > 128): row i lives in CTA i / 128 at lane
+// i % 128, all 256 columns. Split points: both CTAs hold rows 0..Dp-1 and
+// columns 0..Dp-1 of their own points, so X is their sum.
+__device__ __forceinline__ float gc_x(const float* __restrict__ slot, int Dp, int i, int j) {
+  if (Dp > kGcRows) return __ldg(slot + (size_t)(i >> 7) * 256 * kGcRows + (size_t)j * kGcRows + (i & 127));
+  return __ldg(slot + (size_t)j * kGcRows + i) + __ldg(slot + (size_t)(Dp + j) * kGcRows + i);
+}
+
+// Floats of one pair slot's partial products: two CTAs x useful columns x 128 rows.
+__host__ __device__ constexpr size_t gc_slot_floats(int Dp) { return (size_t)2 * (Dp > kGcRows ? 256 : Dp) * kGcRows; }
+
+// Reduction of the pair slots, each summed in FP64 in a fixed order:
+//  1. Z = sum over slots of X, stored transposed in G's memory
+//     (G[j * D + i] = Z(i, j); reads of X are contiguous in i);
+//  2. per dimension (one warp each, lane l taking slots l, l + 32, ...,
+//     then a fixed butterfly): the set sums of z - s and the diagonal
+//     correction sum of z^2 - h^2 - 2hm;
+//  3. the upper triangle of G is overwritten in place with
+//     (Z(i, j) + Z(j, i)) / 2, plus the correction for i == j. Thread (i, j)
+//     reads G[j D + i] and G[i D + j] and writes G[i D + j]; no other thread
+//     of the upper triangle reads that location, so the pass is free of races.
+template <class SlotOf>
+__device__ __forceinline__ void gc_sum_pass(const SlotOf& slot_of, int nslots, int Dp, int D, double* __restrict__ G,
+                                            int64_t e0, int64_t estride) {
   const int64_t DD = (int64_t)D * D;
-  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < DD + 2 * D;
-       e += (int64_t)gridDim.x * blockDim.x) {
-    if (e < DD) {
-      // consecutive threads take consecutive rows i of one column j, so the
-      // partials (stored column-major per CTA) are read coalesced
-      const int j = (int)(e / D), i = (int)(e % D);
-      if (j < i) continue;
-      int c0, c1, row, col;
-      if (i < 128) {
-        c0 = 0; c1 = p.nc0; row = i; col = j;
-      } else {
-        c0 = p.nc0; c1 = ncta; row = i - 128; col = j - 128;
-      }
-      // four interleaved partial sums (loads in flight), combined in a fixed order
-      double s4[4] = {0.0, 0.0, 0.0, 0.0};
-      int c = c0;
-      for (; c + 4 <= c1; c += 4) {
+  for (int64_t e = e0; e < DD; e += estride) {
+    const int j = (int)(e / D), i = (int)(e % D);
+    double s4[4] = {0.0, 0.0, 0.0, 0.0};
+    int c = 0;
+    for (; c + 4 <= nslots; c += 4) {
 #pragma unroll
-        for (int u = 0; u < 4; ++u) {
-          const float2 v = p.gacc[(size_t)(c + u) * (256 * 128) + (size_t)col * 128 + row];
-          s4[u] += (double)v.x - (double)v.y;
+      for (int u = 0; u < 4; ++u) {
+        const float* slot;
+        const double* sums;
+        bool setA;
+        slot_of(c + u, slot, sums, setA);
+        s4[u] += (double)gc_x(slot, Dp, i, j);
+      }
+    }
+    for (; c < nslots; ++c) {
+      const float* slot;
+      const double* sums;
+      bool setA;
+      slot_of(c, slot, sums, setA);
+      s4[0] += (double)gc_x(slot, Dp, i, j);
+    }
+    G[(size_t)j * D + i] = (s4[0] + s4[1]) + (s4[2] + s4[3]);
+  }
+}
+
+// Warp w0, w0 + wstride, ...: dimension d.
+template <class SlotOf>
+__device__ __forceinline__ void gc_dims_pass(const SlotOf& slot_of, int nslots, int Dp, int D,
+                                             double* __restrict__ sumA, double* __restrict__ sumB,
+                                             double* __restrict__ corr, int w0, int wstride) {
+  const int lane = threadIdx.x & 31;
+  for (int d = w0; d < D; d += wstride) {
+    const int r0 = Dp > kGcRows ? (d >> 7) : 0, r1 = Dp > kGcRows ? r0 : 1;
+    const int dl = Dp > kGcRows ? (d & 127) : d;
+    double sa = 0.0, sb = 0.0, cr = 0.0;
+    for (int c = lane; c < nslots; c += 32) {
+      const float* slot;
+      const double* sums;
+      bool setA;
+      slot_of(c, slot, sums, setA);
+      for (int r = r0; r <= r1; ++r)
+        for (int w = 0; w < kGcConv; ++w) {
+          const double* sw = sums + (size_t)(r * kGcConv + w) * 2 * kGcRows;
+          const double z = __ldg(sw + dl);
+          cr += __ldg(sw + kGcRows + dl);
+          if (setA) sa += z;
+          else sb += z;
         }
-      }
-      for (; c < c1; ++c) {
-        const float2 v = p.gacc[(size_t)c * (256 * 128) + (size_t)col * 128 + row];
-        s4[0] += (double)v.x - (double)v.y;
-      }
-      G[(int64_t)i * D + j] = (s4[0] + s4[1]) + (s4[2] + s4[3]);
-    } else {
-      const int64_t k = e - DD;
-      const int set = k < D ? 0 : 1;
-      const int d = (int)(set ? k - D : k);
-      // one partial sum per converter warp slot (independent loads), combined in order
-      double sw[kGcConv];
+    }
 #pragma unroll
-      for (int w = 0; w < kGcConv; ++w) sw[w] = 0.0;
-      for (int c = 0; c < p.nc0; ++c)
-#pragma unroll
-        for (int w = 0; w < kGcConv; ++w) sw[w] += p.sums[((size_t)c * kGcConv + w) * 2 * p.Dp + (size_t)set * p.Dp + d];
-      double s = 0.0;
-#pragma unroll
-      for (int w = 0; w < kGcConv; ++w) s += sw[w];
-      (set ? sumB : sumA)[d] = s;
+    for (int o = 16; o > 0; o >>= 1) {
+      sa += __shfl_xor_sync(0xffffffffu, sa, o);
+      sb += __shfl_xor_sync(0xffffffffu, sb, o);
+      cr += __shfl_xor_sync(0xffffffffu, cr, o);
+    }
+    if (lane == 0) {
+      sumA[d] = sa;
+      sumB[d] = sb;
+      corr[d] = cr;
     }
   }
 }
 
-bool gram_tc_supported(int D) { return D >= 4 && D <= kGcMaxRows && D % 4 == 0; }
+__device__ __forceinline__ void gc_sym_pass(int D, double* __restrict__ G, const double* __restrict__ corr,
+                                            int64_t e0, int64_t estride) {
+  const int64_t DD = (int64_t)D * D;
+  for (int64_t e = e0; e < DD; e += estride) {
+    const int i = (int)(e / D), j = (int)(e % D);
+    if (j < i) continue;
+    if (i != j) G[(size_t)i * D + j] = 0.5 * (G[(size_t)j * D + i] + G[(size_t)i * D + j]);
+    else G[(size_t)i * D + i] += corr[i];
+  }
+}
+
+// One pair: blocks [0, nsum) sum X into G, the rest take the dimensions.
+__global__ void __launch_bounds__(256) gram_tc_sum_kernel(const GcParams p, int nsum, double* __restrict__ G,
+                                                          double* __restrict__ sumA, double* __restrict__ sumB,
+                                                          double* __restrict__ corr) {
+  auto slot_of = [&](int c, const float*& slot, const double*& sums, bool& setA) {
+    slot = p.out + (size_t)c * kGcSlotFloats;
+    sums = p.sums + (size_t)c * kGcSumsDoubles;
+    setA = c < p.ncA;
+  };
+  if ((int)blockIdx.x < nsum)
+    gc_sum_pass(slot_of, p.nclu, p.Dp, p.D, G, blockIdx.x * (int64_t)blockDim.x + threadIdx.x,
+                (int64_t)nsum * blockDim.x);
+  else
+    gc_dims_pass(slot_of, p.nclu, p.Dp, p.D, sumA, sumB, corr,
+                 (int)((blockIdx.x - nsum) * (blockDim.x >> 5) + (threadIdx.x >> 5)),
+                 (int)((gridDim.x - nsum) * (blockDim.x >> 5)));
+}
+
+__global__ void __launch_bounds__(256) gram_tc_sym_kernel(int D, double* __restrict__ G,
+                                                          const double* __restrict__ corr) {
+  gc_sym_pass(D, G, corr, blockIdx.x * (int64_t)blockDim.x + threadIdx.x, (int64_t)gridDim.x * blockDim.x);
+}
+
+bool gram_tc_supported(int D) { return D >= 4 && D <= 2 * kGcRows && D % 4 == 0; }
 
 size_t gram_tc_scratch_doubles(int D, int num_sms) {
-  const int Dp = (int)round_up(D, 64);
-  return (size_t)num_sms * 256 * 128 + (size_t)num_sms * kGcConv * 2 * Dp;
+  (void)D;
+  return (size_t)(num_sms / 2) * (kGcSlotFloats / 2 + kGcSumsDoubles) + 2 * kGcRows;
 }
 
 cudaError_t gram_tc_run(prohd_ctx* ctx, const float* A, int64_t nA, const float* B, int64_t nB, int D,
                         const float* s32, double* scratch, double* G, double* sumA, double* sumB, int* status,
                         int64_t timeout_ns, cudaStream_t st) {
-  const int nsm = ctx->num_sms;
+  if (nA < 1 || nB < 1 || nA > INT_MAX || nB > INT_MAX) return cudaErrorInvalidValue;
   GcParams p;
   p.nA = nA;
   p.nB = nB;
   p.D = D;
   p.Dp = (int)round_up(D, 64);
   p.s32 = s32;
-  p.N0 = p.Dp;
-  p.rows0 = std::max(128, p.Dp);
-  p.N1 = p.Dp > 128 ? p.Dp - 128 : 0;
-  p.rows1 = 128;
-  const int grid = nsm;
-  if (p.N1 > 0) {
-    // CTA counts in proportion to each type's time per point: a fixed part
-    // (handshakes, flushes) plus parts proportional to the output columns
-    // (MMA operand reads) and to the tile rows (copy, conversion), with
-    // weights fitted to measured per-chunk times at D = 256.
-    const double w0 = 20.0 + 0.07 * (p.N0 + p.rows0), w1 = 20.0 + 0.07 * (p.N1 + p.rows1);
-    p.nc0 = (int)std::lround((double)nsm * w0 / (w0 + w1));
-    p.nc0 = std::min(std::max(p.nc0, 2), nsm - 2);
-  } else {
-    p.nc0 = nsm;
+  p.nclu = ctx->num_sms / 2;
+  {
+    // clusters in proportion to the set sizes, at least one per set
+    int a = (int)std::lround((double)p.nclu * (double)nA / (double)(nA + nB));
+    p.ncA = std::min(std::max(a, 1), p.nclu - 1);
   }
-  auto split = [&](int nct) {
-    int a = (int)std::lround((double)nct * (double)nA / (double)(nA + nB));
-    return std::min(std::max(a, 1), nct - 1);
-  };
-  p.ncA0 = split(p.nc0);
-  p.ncA1 = p.N1 > 0 ? split(grid - p.nc0) : 0;
-  p.gacc = reinterpret_cast<float2*>(scratch);
-  p.sums = scratch + (size_t)nsm * 256 * 128;
+  p.out = reinterpret_cast<float*>(scratch);
+  p.sums = scratch + (size_t)p.nclu * (kGcSlotFloats / 2);
   p.status = status;
   p.timeout_ns = (uint64_t)timeout_ns;
   p.items = nullptr;
   p.nitems = 0;
   p.ticket = nullptr;
-  CUtensorMap tA0, tB0, tA1, tB1;
+  CUtensorMap tA, tB;
   const uint64_t rowb = (uint64_t)D * 4;
-  if (!encode_2d(ctx, &tA0, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, A, (uint64_t)D, (uint64_t)nA, rowb, p.rows0, kGcPts,
+  if (!encode_2d(ctx, &tA, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, A, (uint64_t)D, (uint64_t)nA, rowb, kGcRows, kGcPts,
                  CU_TENSOR_MAP_SWIZZLE_NONE) ||
-      !encode_2d(ctx, &tB0, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, B, (uint64_t)D, (uint64_t)nB, rowb, p.rows0, kGcPts,
+      !encode_2d(ctx, &tB, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, B, (uint64_t)D, (uint64_t)nB, rowb, kGcRows, kGcPts,
                  CU_TENSOR_MAP_SWIZZLE_NONE))
     return cudaErrorInvalidValue;
-  tA1 = tA0;
-  tB1 = tB0;
-  if (p.N1 > 0 &&
-      (!encode_2d(ctx, &tA1, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, A, (uint64_t)D, (uint64_t)nA, rowb, p.rows1, kGcPts,
-                  CU_TENSOR_MAP_SWIZZLE_NONE) ||
-       !encode_2d(ctx, &tB1, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, B, (uint64_t)D, (uint64_t)nB, rowb, p.rows1, kGcPts,
-                  CU_TENSOR_MAP_SWIZZLE_NONE)))
-    return cudaErrorInvalidValue;
-  const size_t smem = std::max(gc_smem_bytes(p.rows0), gc_smem_bytes(p.rows1));
-  cudaError_t e = cudaFuncSetAttribute(gram_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  cudaError_t e =
+      cudaFuncSetAttribute(gram_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kGcSmemBytes);
   if (e) return e;
   {
     PhaseTimer pt(ctx, PROHD_PH_GRAM, st);
     count_launch();
-    gram_tc_kernel<<<grid, kGcThreads, smem, st>>>(p, tA0, tB0, tA1, tB1);
+    gram_tc_kernel<<<2 * p.nclu, kGcThreads, kGcSmemBytes, st>>>(p, tA, tB);
     if ((e = cudaGetLastError())) return e;
   }
+  double* corr = p.sums + (size_t)p.nclu * kGcSumsDoubles;
+  const int nsum = (int)std::max<int64_t>(1, std::min<int64_t>(ceil_div((int64_t)D * D, 256), (int64_t)ctx->num_sms * 4));
+  const int ndim = (int)ceil_div(D, 8);  // 8 warps per block, one dimension each
   count_launch();
-  gram_tc_reduce_kernel<<<nsm, 256, 0, st>>>(p, grid, G, sumA, sumB);
+  gram_tc_sum_kernel<<<nsum + ndim, 256, 0, st>>>(p, nsum, G, sumA, sumB, corr);
+  count_launch();
+  gram_tc_sym_kernel<<<nsum, 256, 0, st>>>(D, G, corr);
   return cudaGetLastError();
 }
 
 // ---------------------------------------------------------------- batched pairs
 
-// G and the set sums of every pair of a batch from its items' partials
-// (type-0 items for rows 0..127 and the sums, type-1 items for the rest),
-// in the fixed order of the pair's item list. grid (chunks, pairs).
-__global__ void gram_tc_reduce_batched_kernel(const BPair* __restrict__ P, const GcItem* __restrict__ items,
-                                              const int* __restrict__ ids) {
+// G and the set sums of every pair of a batch from its items' partials, in
+// the fixed order of the pair's item list. grid (chunks + dimension blocks, pairs).
+__global__ void __launch_bounds__(256) gram_tc_sum_batched_kernel(const BPair* __restrict__ P,
+                                                                  const GcItem* __restrict__ items,
+                                                                  const int* __restrict__ ids, int nsum) {
   const BPair& q = P[blockIdx.y];
-  const int D = q.D, Dp = q.Dp;
-  const int64_t DD = (int64_t)D * D;
-  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < DD + 2 * D;
-       e += (int64_t)gridDim.x * blockDim.x) {
-    if (e < DD) {
-      const int j = (int)(e / D), i = (int)(e % D);
-      if (j < i) continue;
-      int l0, l1, row, col;
-      if (i < 128) {
-        l0 = q.gi0; l1 = q.gi0 + q.gn0; row = i; col = j;
-      } else {
-        l0 = q.gi1; l1 = q.gi1 + q.gn1; row = i - 128; col = j - 128;
-      }
-      double s4[4] = {0.0, 0.0, 0.0, 0.0};
-      int l = l0;
-      for (; l + 4 <= l1; l += 4) {
-#pragma unroll
-        for (int u = 0; u < 4; ++u) {
-          const float2 v = __ldg(items[ids[l + u]].gacc + (size_t)col * 128 + row);
-          s4[u] += (double)v.x - (double)v.y;
-        }
-      }
-      for (; l < l1; ++l) {
-        const float2 v = __ldg(items[ids[l]].gacc + (size_t)col * 128 + row);
-        s4[0] += (double)v.x - (double)v.y;
-      }
-      q.G[(int64_t)i * D + j] = (s4[0] + s4[1]) + (s4[2] + s4[3]);
-    } else {
-      const int64_t k = e - DD;
-      const int set = k < D ? 0 : 1;
-      const int d = (int)(set ? k - D : k);
-      double sw[kGcConv];
-#pragma unroll
-      for (int w = 0; w < kGcConv; ++w) sw[w] = 0.0;
-      for (int l = q.gi0; l < q.gi0 + q.gn0; ++l) {
-        const double* sm = items[ids[l]].sums;
-#pragma unroll
-        for (int w = 0; w < kGcConv; ++w) sw[w] += __ldg(sm + (size_t)w * 2 * Dp + (size_t)set * Dp + d);
-      }
-      double s = 0.0;
-#pragma unroll
-      for (int w = 0; w < kGcConv; ++w) s += sw[w];
-      (set ? q.sumB : q.sumA)[d] = s;
-    }
-  }
+  auto slot_of = [&](int c, const float*& slot, const double*& sums, bool& setA) {
+    const GcItem& it = items[ids[q.gi0 + c]];
+    slot = it.out;
+    sums = it.sums;
+    setA = it.setA != 0;
+  };
+  if ((int)blockIdx.x < nsum)
+    gc_sum_pass(slot_of, q.gn0, q.Dp, q.D, q.G, blockIdx.x * (int64_t)blockDim.x + threadIdx.x,
+                (int64_t)nsum * blockDim.x);
+  else
+    gc_dims_pass(slot_of, q.gn0, q.Dp, q.D, q.sumA, q.sumB, q.gcorr,
+                 (int)((blockIdx.x - nsum) * (blockDim.x >> 5) + (threadIdx.x >> 5)),
+                 (int)((gridDim.x - nsum) * (blockDim.x >> 5)));
 }
 
-size_t gram_tc_smem_batched() { return gc_smem_bytes(kGcMaxRows); }
+__global__ void __launch_bounds__(256) gram_tc_sym_batched_kernel(const BPair* __restrict__ P) {
+  const BPair& q = P[blockIdx.y];
+  gc_sym_pass(q.D, q.G, q.gcorr, blockIdx.x * (int64_t)blockDim.x + threadIdx.x, (int64_t)gridDim.x * blockDim.x);
+}
+
+size_t gram_tc_smem_batched() { return kGcSmemBytes; }
+size_t gram_tc_item_sums_offset(int Dp) { return round_up(gc_slot_floats(Dp) * sizeof(float), 256); }
+size_t gram_tc_item_slot_bytes(int Dp) {
+  return gram_tc_item_sums_offset(Dp) + round_up((size_t)kGcSumsDoubles * sizeof(double), 256);
+}
 
 cudaError_t gram_tc_batched(const GcItem* items, int nitems, int* ticket, int* batch_status, int grid,
                             int64_t timeout_ns, cudaStream_t st) {
@@ -613,24 +680,26 @@ cudaError_t gram_tc_batched(const GcItem* items, int nitems, int* ticket, int* b
   p.ticket = ticket;
   p.status = batch_status;
   p.timeout_ns = (uint64_t)timeout_ns;
-  p.nc0 = grid;  // unused in batched launches
-  const size_t smem = gc_smem_bytes(kGcMaxRows);
-  cudaError_t e = cudaFuncSetAttribute(gram_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  p.nclu = grid / 2;
+  cudaError_t e =
+      cudaFuncSetAttribute(gram_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kGcSmemBytes);
   if (e) return e;
   // the tensor maps live in the item table; the kernel's own map parameters are unused
   CUtensorMap none;
   memset(&none, 0, sizeof none);
   count_launch();
-  gram_tc_kernel<<<grid, kGcThreads, smem, st>>>(p, none, none, none, none);
+  gram_tc_kernel<<<2 * (grid / 2), kGcThreads, kGcSmemBytes, st>>>(p, none, none);
   return cudaGetLastError();
 }
 
 cudaError_t gram_reduce_batched(const BPair* P, int npairs, const GcItem* items, const int* ids, int Dmax,
                                 cudaStream_t st) {
-  const int64_t work = (int64_t)Dmax * Dmax + 2 * Dmax;
-  const unsigned gx = (unsigned)std::max<int64_t>(1, std::min<int64_t>(16, ceil_div(work, 256 * 4)));
+  const int nsum = (int)std::max<int64_t>(1, std::min<int64_t>(16, ceil_div((int64_t)Dmax * Dmax, 256 * 4)));
+  const int ndim = (int)ceil_div(Dmax, 8);
   count_launch();
-  gram_tc_reduce_batched_kernel<<<dim3(gx, npairs), 256, 0, st>>>(P, items, ids);
+  gram_tc_sum_batched_kernel<<<dim3(nsum + ndim, npairs), 256, 0, st>>>(P, items, ids, nsum);
+  count_launch();
+  gram_tc_sym_batched_kernel<<<dim3(nsum, npairs), 256, 0, st>>>(P);
   return cudaGetLastError();
 }
 

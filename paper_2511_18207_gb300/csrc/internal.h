@@ -111,6 +111,11 @@ cudaError_t directions_run(prohd_ctx* ctx, const float* A, int64_t nA, const flo
                            int max_iters, double tol, uint64_t seed, double* dirs, double* eig, int* status_dev,
                            Arena& ws, cudaStream_t st, int64_t timeout_ns);
 
+// Union covariance C (FP64, D x D, 1/N) and mean of [A; B] (directions.cu).
+void covariance_layout(Arena& ws, int D);
+cudaError_t covariance_run(prohd_ctx* ctx, const float* A, int64_t nA, const float* B, int64_t nB, int D, double* C,
+                           double* mean, int* status, Arena& ws, cudaStream_t st, int64_t timeout_ns);
+
 // ---- tensor-core Gram (gram_tc.cu) ----
 constexpr int kMaxSms = 192;  // upper bound used to size per-CTA scratch
 // Top-m eigenvectors by block iteration with Rayleigh-Ritz (subspace.cu).
@@ -126,17 +131,16 @@ cudaError_t gram_tc_run(prohd_ctx* ctx, const float* A, int64_t nA, const float*
 
 // ---- batched pairs (batch.cu drives these; each stage is one launch for all pairs) ----
 
-// One unit of tensor-core Gram work: a point range of one set against one
-// output block (type 0: rows 0..127 x all Dp columns; type 1: rows 128..Dp-1
-// x columns 128..Dp-1). The tensor map lives in device memory.
+// One unit of tensor-core Gram work for a CTA pair: a point range of one
+// set. The tensor map (box 128 dimensions x 64 points) lives in device memory.
 struct GcItem {
-  const CUtensorMap* tm;  // FP32 tiles of the set: box (type 0: max(128, Dp); type 1: 128) dims x 64 points
+  const CUtensorMap* tm;  // FP32 tiles of the set
   const float* s32;       // pilot shift of the pair [D]
-  float2* gacc;           // [N][128] compensated partial sums (sum, compensation)
-  double* sums;           // [8][2][Dp] per-converter-warp set sums
+  float* out;             // [2 CTAs][useful columns: 256, or Dp if Dp <= 128][128 rows] partial products
+  double* sums;           // [2 CTAs][8 warps][set sum | diagonal correction][128 dims]
   int* status;            // the pair's status
   int64_t p0, p1;         // point range [p0, p1) of the set
-  int D, Dp, type, setA;
+  int D, Dp, setA;
 };
 
 // Device-side descriptor of one pair of a batch: its inputs, parameters and
@@ -149,6 +153,7 @@ struct BPair {
   // directions
   float* s32;
   double *G, *sumA, *sumB, *C64;
+  double* gcorr;  // [D] diagonal corrections of the tensor-core Gram
   float* C32;
   double* U;      // [m][D] Ritz vectors before the FP64 clean-up
   double* rpart;  // [m][D] Rayleigh-quotient partials
@@ -180,8 +185,8 @@ struct BPair {
   void* hd_sc;
   int64_t hd_nA_pad, hd_nB_pad;
   int hd_map;
-  // Gram items of this pair, as positions in the batch's item-id list
-  int gi0, gn0, gi1, gn1;
+  // Gram items of this pair (both sets), as positions in the batch's item-id list
+  int gi0, gn0;
   int prob0;  // first selection problem of this pair (set-major: set * nd + d)
 };
 
@@ -192,6 +197,8 @@ struct ProjItem {
 };
 
 size_t gram_tc_smem_batched();
+size_t gram_tc_item_slot_bytes(int Dp);   // output slot of one item (partial products, then sums)
+size_t gram_tc_item_sums_offset(int Dp);  // byte offset of the sums within a slot
 cudaError_t gram_tc_batched(const GcItem* items, int nitems, int* ticket, int* batch_status, int grid,
                             int64_t timeout_ns, cudaStream_t st);
 cudaError_t gram_reduce_batched(const BPair* P, int npairs, const GcItem* items, const int* ids, int Dmax,

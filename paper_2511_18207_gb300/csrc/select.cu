@@ -9,8 +9,15 @@
 //  1. FP32 projections q (one HBM pass over the points, cp.async-staged tiles,
 //     all directions at once) and E = (D+8) 2^-24 max||x|| ||u|| (1.01)^2, a
 //     bound on |q - p64| for every point.
-//  2. The exact k-th smallest FP32 key T (4-pass radix select over
-//     order-preserving uint32 keys, all (set, direction, side) problems at once).
+//  2. The exact k-th smallest FP32 key T over order-preserving uint32 keys.
+//     One pair: the projection pass also counts every key's top byte, one
+//     pass counts the next 11 bits of the keys inside the byte holding rank
+//     k; the 19-bit prefix found gives a value range [L, H] that contains T,
+//     so q < L - 2E is certainly selected and q > H + 2E certainly not; one
+//     pass over the keys marks the former and lists the rest of
+//     [L - 2E, H + 2E] as candidates (a few hundred points), and the last
+//     bits of T are found among the candidates alone. Batches: a 4-pass radix select over all keys of all
+//     (pair, set, direction, side) problems at once.
 //  3. q < T - 2E: certainly among the k smallest; q > T + 2E: certainly not;
 //     the band in between is ranked by FP64 projections recomputed exactly as
 //     the sequential definition (__dmul_rn / __dadd_rn), ties by index.
@@ -34,19 +41,24 @@ constexpr int kProjStride = 36;  // padded row stride (floats): conflict-free 16
 // q[d*n + i] = fl32(x_i . u_d); rownorm max into *maxnorm; non-finite check.
 // Requires D % 4 == 0 and a 16-byte aligned base (cp.async 16 B).
 // Tiles t0, t0 + tstride, ... below t1 of the set.
+// hist0 (may be null): [nd][256] counts of the top byte of f32_key(q) per
+// direction, accumulated in shared memory and added once per block.
 template <int ND>
 __device__ __forceinline__ void proj_body(const float* __restrict__ X, int64_t n, int D,
                                           const double* __restrict__ dirs, int nd, float* __restrict__ q,
                                           float* __restrict__ maxnorm, int* __restrict__ status, int64_t t0,
-                                          int64_t t1, int64_t tstride) {
+                                          int64_t t1, int64_t tstride, unsigned* __restrict__ hist0) {
   extern __shared__ __align__(16) float psm[];
   const int Dq = (D + kProjK - 1) / kProjK * kProjK;
   float* us = psm;                               // [ND][Dq]
   float* xs = psm + (size_t)ND * Dq;             // [2][kProjRows][kProjStride]
+  unsigned* hs = reinterpret_cast<unsigned*>(xs + (size_t)2 * kProjRows * kProjStride);  // [ND][256]
   for (int i = threadIdx.x; i < ND * Dq; i += blockDim.x) {
     int d = i / Dq, k = i % Dq;
     us[i] = (d < nd && k < D) ? (float)dirs[(size_t)d * D + k] : 0.f;
   }
+  if (hist0)
+    for (int i = threadIdx.x; i < ND * 256; i += blockDim.x) hs[i] = 0u;
   const int t = threadIdx.x;
   const int nchunks = Dq / kProjK;
   float wmax = 0.f;
@@ -112,17 +124,28 @@ __device__ __forceinline__ void proj_body(const float* __restrict__ X, int64_t n
     if (r0 < n) {
 #pragma unroll
       for (int d = 0; d < ND; ++d)
-        if (d < nd) q[(size_t)d * n + r0] = acc0[d];
+        if (d < nd) {
+          q[(size_t)d * n + r0] = acc0[d];
+          if (hist0) atomicAdd(&hs[d * 256 + (f32_key(acc0[d]) >> 24)], 1u);
+        }
       bad |= !isfinite(n0);
       wmax = fmaxf(wmax, sqrtf(n0));
     }
     if (r1 < n) {
 #pragma unroll
       for (int d = 0; d < ND; ++d)
-        if (d < nd) q[(size_t)d * n + r1] = acc1[d];
+        if (d < nd) {
+          q[(size_t)d * n + r1] = acc1[d];
+          if (hist0) atomicAdd(&hs[d * 256 + (f32_key(acc1[d]) >> 24)], 1u);
+        }
       bad |= !isfinite(n1);
       wmax = fmaxf(wmax, sqrtf(n1));
     }
+  }
+  if (hist0) {
+    __syncthreads();
+    for (int i = threadIdx.x; i < nd * 256; i += blockDim.x)
+      if (hs[i]) atomicAdd(hist0 + i, hs[i]);
   }
   wmax = warp_max(wmax);
   if ((threadIdx.x & 31) == 0) atomic_max_nonneg(maxnorm, wmax);
@@ -132,8 +155,10 @@ __device__ __forceinline__ void proj_body(const float* __restrict__ X, int64_t n
 template <int ND>
 __global__ void __launch_bounds__(kProjThreads)
     proj_kernel(const float* __restrict__ X, int64_t n, int D, const double* __restrict__ dirs, int nd,
-                float* __restrict__ q, float* __restrict__ maxnorm, int* __restrict__ status) {
-  proj_body<ND>(X, n, D, dirs, nd, q, maxnorm, status, blockIdx.x, (n + kProjRows - 1) / kProjRows, gridDim.x);
+                float* __restrict__ q, float* __restrict__ maxnorm, int* __restrict__ status,
+                unsigned* __restrict__ hist0) {
+  proj_body<ND>(X, n, D, dirs, nd, q, maxnorm, status, blockIdx.x, (n + kProjRows - 1) / kProjRows, gridDim.x,
+                hist0);
 }
 
 // Batched: one item (a row range of one set of one pair) per block.
@@ -144,7 +169,7 @@ __global__ void __launch_bounds__(kProjThreads)
   const BPair& q = P[it.pair];
   const int64_t n = it.set ? q.nB : q.nA;
   proj_body<ND>(it.set ? q.B : q.A, n, q.D, q.dirs, q.nd, it.set ? q.qB : q.qA, q.maxnorm + it.set, q.status,
-                it.r0 / kProjRows, (it.r1 + kProjRows - 1) / kProjRows, 1);
+                it.r0 / kProjRows, (it.r1 + kProjRows - 1) / kProjRows, 1, nullptr);
 }
 
 // Fallback for D % 4 != 0 or unaligned bases: warp per row, lanes over dims.
@@ -183,7 +208,11 @@ struct SelProb {
   int64_t k;            // k of this (set, direction)
   double E;             // |q - p64| bound for this (set, direction)
   int64_t cin[2];       // points certainly selected on each side
-  int64_t nband[2];     // band sizes
+  int64_t nband[2];     // band sizes (candidate counts between extraction and candidate selection)
+  // one-pass extraction (single pair): side 0 selects v < t_in[0] and lists
+  // the rest of v <= c_lim[0]; side 1 selects v > t_in[1] and lists the rest
+  // of v >= c_lim[1]
+  float t_in[2], c_lim[2];
   // the problem's data: FP32 keys q[0..n), points X [n][D], direction u,
   // selection mask, band lists and their FP64 keys (one per side)
   const float* q;
@@ -217,31 +246,6 @@ __device__ __forceinline__ void sel_reset(SelProb& s, int64_t k) {
   s.E = ((double)s.D + 8.0) * 5.9604644775390625e-8 * 1.0201 * (double)(*s.maxnorm) * un + 1e-300;
   s.cin[0] = s.cin[1] = 0;
   s.nband[0] = s.nband[1] = 0;
-}
-
-__global__ void sel_init_kernel(SelProb* __restrict__ P, int nd, const KList kl, const float* __restrict__ A,
-                                const float* __restrict__ qA, int64_t nA, uint8_t* __restrict__ maskA,
-                                const float* __restrict__ B, const float* __restrict__ qB, int64_t nB,
-                                uint8_t* __restrict__ maskB, int D, const double* __restrict__ dirs,
-                                const float* __restrict__ maxnorm, int32_t* __restrict__ band,
-                                uint64_t* __restrict__ bandkey, int64_t cap) {
-  const int p = blockIdx.x * blockDim.x + threadIdx.x;
-  if (p >= 2 * nd) return;
-  const int set = p / nd, d = p % nd;
-  SelProb s;
-  s.n = set ? nB : nA;
-  s.q = (set ? qB : qA) + (size_t)d * s.n;
-  s.X = set ? B : A;
-  s.u = dirs + (size_t)d * D;
-  s.mask = set ? maskB : maskA;
-  s.maxnorm = maxnorm + set;
-  s.D = D;
-  for (int side = 0; side < 2; ++side) {
-    s.band[side] = band + ((size_t)p * 2 + side) * cap;
-    s.bkey[side] = bandkey + ((size_t)p * 2 + side) * cap;
-  }
-  sel_reset(s, kl.k[p]);
-  P[p] = s;
 }
 
 // Batched: the data fields were written when the batch was planned; k comes
@@ -343,6 +347,383 @@ __device__ __forceinline__ float f32_down(double x) {
   return f;
 }
 
+// ---------------------------------------------------------------- one pair: one pass over the keys
+
+// Value of a key, with the keys that decode to NaN (bins beyond the finite
+// range) mapped to -inf / +inf so that thresholds built from them select
+// nothing as certain and list everything else as candidates.
+__device__ __forceinline__ float key_value_lo(uint32_t k) {
+  const float v = key_f32(k);
+  return v == v ? v : __int_as_float(0xff800000);
+}
+__device__ __forceinline__ float key_value_hi(uint32_t k) {
+  const float v = key_f32(k);
+  return v == v ? v : __int_as_float(0x7f800000);
+}
+
+// Index of the bin holding rank r among n bins counted in ascending order
+// (side 0) or descending order (side 1), and the rank left inside it; one
+// block of 256 threads, bins in shared memory, the scan in the fixed order of
+// thread indices. Writes *bin and *left from the thread that owns the bin.
+template <int NB>
+__device__ __forceinline__ void block_pick(const unsigned* __restrict__ h, int64_t r, int side, int* bin,
+                                           int64_t* left) {
+  constexpr int PER = NB / 256;
+  __shared__ unsigned long long s_part[256];
+  const int t = threadIdx.x;
+  // thread t owns PER consecutive bins of the side's order
+  unsigned long long own = 0;
+#pragma unroll
+  for (int j = 0; j < PER; ++j) {
+    const int o = t * PER + j;
+    own += h[side ? NB - 1 - o : o];
+  }
+  s_part[t] = own;
+  __syncthreads();
+  // inclusive scan (Hillis-Steele) over 256 partial counts
+  for (int off = 1; off < 256; off <<= 1) {
+    const unsigned long long v = t >= off ? s_part[t - off] : 0ull;
+    __syncthreads();
+    s_part[t] += v;
+    __syncthreads();
+  }
+  const unsigned long long incl = s_part[t], excl = incl - own;
+  if ((int64_t)excl <= r && r < (int64_t)incl) {
+    int64_t x = r - (int64_t)excl;
+    for (int j = 0; j < PER; ++j) {
+      const int o = t * PER + j;
+      const int b = side ? NB - 1 - o : o;
+      if (x < (int64_t)h[b]) {
+        *bin = b;
+        *left = x;
+        break;
+      }
+      x -= h[b];
+    }
+  }
+  __syncthreads();
+}
+
+// One block per (set, direction) problem: its data, k, the bound E, and
+// from the top-byte histogram of its keys the byte of each side's k-th key
+// (prefix[side] = byte << 24) and the rank left inside that byte (counted
+// from the low end for side 0, from the high end for side 1).
+__global__ void __launch_bounds__(256)
+    sel_init_pick_kernel(SelProb* __restrict__ P, int nd, const KList kl, const float* __restrict__ A,
+                         const float* __restrict__ qA, int64_t nA, uint8_t* __restrict__ maskA,
+                         const float* __restrict__ B, const float* __restrict__ qB, int64_t nB,
+                         uint8_t* __restrict__ maskB, int D, const double* __restrict__ dirs,
+                         const float* __restrict__ maxnorm, int32_t* __restrict__ band,
+                         uint64_t* __restrict__ bandkey, int64_t cap, const unsigned* __restrict__ hist0) {
+  __shared__ unsigned h[256];
+  __shared__ int s_bin[2];
+  __shared__ int64_t s_left[2];
+  const int p = blockIdx.x;
+  const int set = p / nd, d = p % nd;
+  const int64_t n = set ? nB : nA;
+  int64_t k = kl.k[p];
+  k = k < 1 ? 1 : (k > n ? n : k);
+  h[threadIdx.x] = hist0[(size_t)p * 256 + threadIdx.x];
+  if (threadIdx.x < 2) {
+    s_bin[threadIdx.x] = threadIdx.x ? 0 : 255;
+    s_left[threadIdx.x] = 0;
+  }
+  __syncthreads();
+  for (int side = 0; side < 2; ++side) block_pick<256>(h, k - 1, side, &s_bin[side], &s_left[side]);
+  if (threadIdx.x != 0) return;
+  SelProb s;
+  s.n = n;
+  s.q = (set ? qB : qA) + (size_t)d * s.n;
+  s.X = set ? B : A;
+  s.u = dirs + (size_t)d * D;
+  s.mask = set ? maskB : maskA;
+  s.maxnorm = maxnorm + set;
+  s.D = D;
+  for (int side = 0; side < 2; ++side) {
+    s.band[side] = band + ((size_t)p * 2 + side) * cap;
+    s.bkey[side] = bandkey + ((size_t)p * 2 + side) * cap;
+  }
+  sel_reset(s, k);
+  for (int side = 0; side < 2; ++side) {
+    s.prefix[side] = (uint32_t)s_bin[side] << 24;
+    s.rank[side] = s_left[side];
+  }
+  P[p] = s;
+}
+
+constexpr int kHist1Bins = 2048;  // bits 23..13 of the key
+constexpr int kHist1Blocks = 32;  // blocks per problem (each writes its own histogram pair)
+
+// Second digit: histograms of bits 23..13 of the keys whose top byte is
+// each side's byte. grid (kHist1Blocks, 2*nd); out [2*nd][blocks][2][2048].
+__global__ void __launch_bounds__(512) hist1_kernel(const SelProb* __restrict__ P, unsigned* __restrict__ out) {
+  __shared__ unsigned h[2][kHist1Bins];
+  const SelProb& S = P[blockIdx.y];
+  for (int i = threadIdx.x; i < 2 * kHist1Bins; i += blockDim.x) (&h[0][0])[i] = 0u;
+  __syncthreads();
+  const int64_t n = S.n;
+  const int64_t c0 = n * blockIdx.x / gridDim.x, c1 = n * (blockIdx.x + 1) / gridDim.x;
+  const uint32_t b0 = S.prefix[0] >> 24, b1 = S.prefix[1] >> 24;
+  const float* q = S.q;
+  // four independent loads in flight per thread
+  for (int64_t base = c0; base < c1; base += 4 * (int64_t)blockDim.x) {
+    float v[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int64_t i = base + u * (int64_t)blockDim.x + threadIdx.x;
+      v[u] = i < c1 ? __ldg(q + i) : 0.f;
+    }
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int64_t i = base + u * (int64_t)blockDim.x + threadIdx.x;
+      if (i >= c1) continue;
+      const uint32_t k = f32_key(v[u]);
+      const uint32_t top = k >> 24, dig = (k >> 13) & (kHist1Bins - 1);
+      if (top == b0) atomicAdd(&h[0][dig], 1u);
+      if (top == b1) atomicAdd(&h[1][dig], 1u);
+    }
+  }
+  __syncthreads();
+  unsigned* o = out + ((size_t)blockIdx.y * gridDim.x + blockIdx.x) * 2 * kHist1Bins;
+  for (int i = threadIdx.x; i < 2 * kHist1Bins; i += blockDim.x) o[i] = (&h[0][0])[i];
+}
+
+// One block per (problem, side): the 11-bit digit holding the side's rank
+// inside its byte, then the thresholds of the extraction pass. With [L, H]
+// the values of the 19-bit key prefix, the k-th smallest key T lies in
+// [L, H]: v < L - 2E is certainly among the k smallest (it is below
+// T - 2E), v > H + 2E certainly not (above T + 2E), and [L - 2E, H + 2E]
+// holds every point the band can need. The largest side mirrors this.
+__global__ void __launch_bounds__(256) pick1_kernel(SelProb* __restrict__ P, const unsigned* __restrict__ hist1) {
+  __shared__ unsigned h[kHist1Bins];
+  __shared__ int s_dig;
+  __shared__ int64_t s_left;
+  const int p = blockIdx.x >> 1, side = blockIdx.x & 1;
+  SelProb& S = P[p];
+  for (int i = threadIdx.x; i < kHist1Bins; i += blockDim.x) {
+    unsigned t = 0;
+    for (int b = 0; b < kHist1Blocks; ++b) t += hist1[(((size_t)p * kHist1Blocks + b) * 2 + side) * kHist1Bins + i];
+    h[i] = t;
+  }
+  if (threadIdx.x == 0) {
+    s_dig = side ? 0 : kHist1Bins - 1;
+    s_left = 0;
+  }
+  __syncthreads();
+  block_pick<kHist1Bins>(h, S.rank[side], side, &s_dig, &s_left);
+  if (threadIdx.x != 0) return;
+  const int dig = s_dig;
+  const uint32_t pre = S.prefix[side] | ((uint32_t)dig << 13);
+  const double L = (double)key_value_lo(pre), H = (double)key_value_hi(pre | 0x1fffu);
+  const double E2 = 2.0 * S.E;
+  if (side == 0) {
+    S.t_in[0] = f32_up(L - E2);     // v < t_in  <=>  (double)v < L - 2E
+    S.c_lim[0] = f32_down(H + E2);  // v <= c_lim <=> (double)v <= H + 2E
+  } else {
+    S.t_in[1] = f32_down(H + E2);   // v > t_in  <=>  (double)v > H + 2E
+    S.c_lim[1] = f32_up(L - E2);    // v >= c_lim <=> (double)v >= L - 2E
+  }
+  S.nband[side] = 0;
+  S.cin[side] = 0;
+}
+
+// One pass over the keys of every problem: certain members are marked and
+// counted, candidates listed per side as (index, key) in the band buffers
+// (side 1 stores the reversed key, so both sides look for a smallest key).
+// grid (chunks, 2*nd).
+__global__ void extract_kernel(SelProb* __restrict__ P) {
+  SelProb& S = P[blockIdx.y];
+  const int64_t n = S.n;
+  const float* q = S.q;
+  uint8_t* mask = S.mask;
+  const float t0 = S.t_in[0], c0 = S.c_lim[0], t1 = S.t_in[1], c1 = S.c_lim[1];
+  int32_t* b0 = S.band[0];
+  int32_t* b1 = S.band[1];
+  uint64_t* k0 = S.bkey[0];
+  uint64_t* k1 = S.bkey[1];
+  const int lane = threadIdx.x & 31;
+  unsigned long long in0c = 0, in1c = 0;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  const int64_t end = (n + 31) / 32 * 32;
+  for (int64_t base = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; base < end; base += 4 * stride) {
+   float vv[4];
+#pragma unroll
+   for (int u = 0; u < 4; ++u) {
+     const int64_t i = base + u * stride;
+     vv[u] = i < n ? __ldg(q + i) : 0.f;
+   }
+#pragma unroll
+   for (int u = 0; u < 4; ++u) {
+    const int64_t i = base + u * stride;
+    if (i - threadIdx.x % 32 >= end) break;  // the whole warp is past the end
+    bool in0 = false, cd0 = false, in1 = false, cd1 = false;
+    const float v = vv[u];
+    if (i < n) {
+      in0 = v < t0;
+      cd0 = !in0 && v <= c0;
+      in1 = v > t1;
+      cd1 = !in1 && v >= c1;
+      if (in0 || in1) mask[i] = 1;
+    }
+    in0c += in0;
+    in1c += in1;
+    const unsigned m0 = __ballot_sync(0xffffffffu, cd0), m1 = __ballot_sync(0xffffffffu, cd1);
+    unsigned long long base0 = 0, base1 = 0;
+    if (lane == 0 && m0)
+      base0 = atomicAdd(reinterpret_cast<unsigned long long*>(&S.nband[0]), (unsigned long long)__popc(m0));
+    if (lane == 0 && m1)
+      base1 = atomicAdd(reinterpret_cast<unsigned long long*>(&S.nband[1]), (unsigned long long)__popc(m1));
+    base0 = __shfl_sync(0xffffffffu, base0, 0);
+    base1 = __shfl_sync(0xffffffffu, base1, 0);
+    const unsigned below = (1u << lane) - 1;
+    const uint32_t key = f32_key(v);
+    if (cd0) {
+      const unsigned long long o = base0 + __popc(m0 & below);
+      b0[o] = (int32_t)i;
+      k0[o] = key;
+    }
+    if (cd1) {
+      const unsigned long long o = base1 + __popc(m1 & below);
+      b1[o] = (int32_t)i;
+      k1[o] = ~key;
+    }
+   }
+  }
+  in0c = warp_sum(in0c);
+  in1c = warp_sum(in1c);
+  if (lane == 0) {
+    if (in0c) atomicAdd(reinterpret_cast<unsigned long long*>(&S.cin[0]), in0c);
+    if (in1c) atomicAdd(reinterpret_cast<unsigned long long*>(&S.cin[1]), in1c);
+  }
+}
+
+constexpr int kCandThreads = 512;
+constexpr int kCandBins = 2048;
+
+// One block per (problem, side): the exact k-th key T among the candidates
+// (radix select over the 32-bit stored keys: 11 + 11 + 10 bits), then every
+// candidate below T - 2E is marked certain and those within [T - 2E, T + 2E]
+// are compacted, in order and in place, into the front of the band list.
+__global__ void __launch_bounds__(kCandThreads) cand_select_kernel(SelProb* __restrict__ P) {
+  __shared__ unsigned hist[kCandBins];
+  __shared__ unsigned wsum[kCandThreads / 32];
+  __shared__ int64_t s_rank;
+  __shared__ uint32_t s_prefix;
+  __shared__ int s_ok;
+  __shared__ unsigned long long s_cert, s_band;
+  const int p = blockIdx.x >> 1, side = blockIdx.x & 1;
+  SelProb& S = P[p];
+  const int64_t nc = S.nband[side];
+  const int64_t r = S.k - 1 - S.cin[side];
+  int32_t* lst = S.band[side];
+  const uint64_t* keys = S.bkey[side];
+  const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+  if (tid == 0) {
+    s_rank = r;
+    s_prefix = 0;
+    s_ok = (nc > 0 && r >= 0 && r < nc) ? 1 : 0;
+    s_cert = 0;
+    s_band = 0;
+  }
+  __syncthreads();
+  if (!s_ok) {
+    // no candidate holds rank k (only with non-finite keys, which the
+    // projection reports): nothing more is selected on this side
+    if (tid == 0) S.nband[side] = 0;
+    return;
+  }
+  for (int pass = 0; pass < 3; ++pass) {
+    const int shift = pass == 0 ? 21 : (pass == 1 ? 10 : 0);
+    const int width = pass == 2 ? 10 : 11;
+    const uint32_t dmask = (1u << width) - 1u;
+    const uint32_t him = pass == 0 ? 0u : (0xffffffffu << (shift + width));
+    for (int i = tid; i < kCandBins; i += kCandThreads) hist[i] = 0;
+    __syncthreads();
+    const uint32_t pre = s_prefix;
+    for (int64_t i = tid; i < nc; i += kCandThreads) {
+      const uint32_t k = (uint32_t)__ldg(keys + i);
+      if (((k ^ pre) & him) == 0) atomicAdd(&hist[(k >> shift) & dmask], 1u);
+    }
+    __syncthreads();
+    if (w == 0) {
+      // lane l owns bins 64 l .. 64 l + 63
+      unsigned tot = 0;
+      for (int j = 0; j < 64; ++j) tot += hist[lane * 64 + j];
+      unsigned incl = tot;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const unsigned v = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += v;
+      }
+      const unsigned excl = incl - tot;
+      const int64_t rr = s_rank;
+      const bool mine = (int64_t)excl <= rr && rr < (int64_t)incl;
+      if (mine) {
+        int64_t x = rr - (int64_t)excl;
+        int bin = lane * 64 + 63;
+        for (int j = 0; j < 64; ++j) {
+          const unsigned c = hist[lane * 64 + j];
+          if (x < (int64_t)c) {
+            bin = lane * 64 + j;
+            break;
+          }
+          x -= c;
+        }
+        s_prefix = pre | ((uint32_t)bin << shift);
+        s_rank = x;
+      }
+    }
+    __syncthreads();
+  }
+  const uint32_t kstar = s_prefix;
+  const double T = (double)key_f32(side ? ~kstar : kstar);
+  const double E2 = 2.0 * S.E;
+  // side 0: certain v < T - 2E, band v <= T + 2E; side 1: certain v > T + 2E,
+  // band v >= T - 2E (as float thresholds)
+  const float f_in = side ? f32_down(T + E2) : f32_up(T - E2);
+  const float f_band = side ? f32_up(T - E2) : f32_down(T + E2);
+  uint8_t* mask = S.mask;
+  unsigned long long cert = 0;
+  for (int64_t base = 0; base < nc; base += kCandThreads) {
+    const int64_t i = base + tid;
+    bool inb = false;
+    int32_t id = 0;
+    if (i < nc) {
+      const uint32_t k = (uint32_t)__ldg(keys + i);
+      const float v = key_f32(side ? ~k : k);
+      id = lst[i];
+      const bool in = side ? v > f_in : v < f_in;
+      inb = !in && (side ? v >= f_band : v <= f_band);
+      if (in) {
+        mask[id] = 1;
+        ++cert;
+      }
+    }
+    // ordered block-wide compaction of the band members
+    const unsigned m = __ballot_sync(0xffffffffu, inb);
+    if (lane == 0) wsum[w] = __popc(m);
+    __syncthreads();
+    unsigned before = 0, total = 0;
+    for (int j = 0; j < kCandThreads / 32; ++j) {
+      const unsigned c = wsum[j];
+      before += j < w ? c : 0u;
+      total += c;
+    }
+    const unsigned long long o = s_band + before + __popc(m & ((1u << lane) - 1));
+    __syncthreads();  // every read of this chunk is done before any write
+    if (inb) lst[o] = id;
+    if (tid == 0) s_band += total;
+    __syncthreads();
+  }
+  cert = warp_sum(cert);
+  if (lane == 0 && cert) atomicAdd(&s_cert, cert);
+  __syncthreads();
+  if (tid == 0) {
+    S.cin[side] += (int64_t)s_cert;
+    S.nband[side] = (int64_t)s_band;
+  }
+}
+
 // Marks certain members, counts them, and lists band members per side.
 // band lists: [2*nd][2][cap] int32
 __global__ void band_kernel(SelProb* __restrict__ P, int pbase) {
@@ -394,8 +775,11 @@ __global__ void band_kernel(SelProb* __restrict__ P, int pbase) {
 // FP64 projection exactly as the sequential definition.
 // FP64 keys of every band member, spread over many blocks (FP64 arithmetic is
 // scarce on this GPU: one block per band would serialise a large band's
-// sequential sums on one SM). grid (chunks, 4 * nd): y = problem * 2 + side.
-__global__ void band_keys_kernel(const SelProb* __restrict__ P) {
+// sequential sums on one SM). One warp per member: the warp stages the row
+// in shared memory with coalesced loads, then one lane forms the sequential
+// FP64 sum (the order of the definition; a parallel sum would round
+// differently). grid (chunks, 4 * nd): y = problem * 2 + side.
+__global__ void __launch_bounds__(256) band_keys_kernel(const SelProb* __restrict__ P) {
   const int p = blockIdx.y >> 1, side = blockIdx.y & 1;
   const float* X = P[p].X;
   const int D = P[p].D;
@@ -403,28 +787,32 @@ __global__ void band_keys_kernel(const SelProb* __restrict__ P) {
   const int64_t r = P[p].k - P[p].cin[side];
   if (b == 0 || r <= 0) return;
   __shared__ double us[1024];
+  __shared__ float rows[8][1024];
   const double* u = P[p].u;
-  const bool u_sm = D <= 1024;
-  if (u_sm)
+  const bool sm = D <= 1024;
+  if (sm)
     for (int k = threadIdx.x; k < D; k += blockDim.x) us[k] = u[k];
   __syncthreads();
-  const double* uu = u_sm ? us : u;
   const int32_t* lst = P[p].band[side];
   uint64_t* keys = P[p].bkey[side];
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < b; i += (int64_t)gridDim.x * blockDim.x) {
-    double s = 0.0;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t wstride = (int64_t)gridDim.x * (blockDim.x >> 5);
+  for (int64_t i = blockIdx.x * (int64_t)(blockDim.x >> 5) + warp; i < b; i += wstride) {
     const float* x = X + (int64_t)__ldg(lst + i) * D;
-    int k = 0;
-    for (; k + 8 <= D; k += 8) {
-      float xv[8];
-#pragma unroll
-      for (int j = 0; j < 8; ++j) xv[j] = __ldg(x + k + j);
-#pragma unroll
-      for (int j = 0; j < 8; ++j) s = __dadd_rn(s, __dmul_rn((double)xv[j], uu[k + j]));
+    double s = 0.0;
+    if (sm) {
+      for (int k = lane; k < D; k += 32) rows[warp][k] = __ldg(x + k);
+      __syncwarp();
+      if (lane == 0)
+        for (int k = 0; k < D; ++k) s = __dadd_rn(s, __dmul_rn((double)rows[warp][k], us[k]));
+      __syncwarp();
+    } else if (lane == 0) {
+      for (int k = 0; k < D; ++k) s = __dadd_rn(s, __dmul_rn((double)__ldg(x + k), u[k]));
     }
-    for (; k < D; ++k) s = __dadd_rn(s, __dmul_rn((double)__ldg(x + k), uu[k]));
-    const uint64_t kk = f64_key(s);
-    keys[i] = side ? ~kk : kk;
+    if (lane == 0) {
+      const uint64_t kk = f64_key(s);
+      keys[i] = side ? ~kk : kk;
+    }
   }
 }
 
@@ -706,6 +1094,7 @@ struct SelBufs {
   float* maxnorm = nullptr;  // [2]
   SelProb* P = nullptr;
   unsigned* hist = nullptr;
+  unsigned* hist1 = nullptr;  // second-digit histograms (one pair)
   int32_t* band = nullptr;
   uint64_t* bandkey = nullptr;
   uint8_t *maskA = nullptr, *maskB = nullptr;
@@ -722,6 +1111,7 @@ static void sel_layout(Arena& ws, int64_t nA, int64_t nB, int D, int nd, SelBufs
   b.maxnorm = ws.take<float>(2);
   b.P = ws.take<SelProb>((size_t)2 * nd);
   b.hist = ws.take<unsigned>((size_t)2 * nd * 512);
+  b.hist1 = ws.take<unsigned>((size_t)2 * nd * kHist1Blocks * 2 * kHist1Bins);
   b.band = ws.take<int32_t>((size_t)2 * nd * 2 * b.cap);
   b.bandkey = ws.take<uint64_t>((size_t)2 * nd * 2 * b.cap);
   b.maskA = ws.take<uint8_t>((size_t)nA);
@@ -736,17 +1126,37 @@ void select_layout(Arena& ws, int64_t nA, int64_t nB, int D, int ndirs) {
   sel_layout(ws, nA, nB, D, ndirs, b);
 }
 
+// hist0[d][b]: keys of direction d whose top byte is b, one 256-bin
+// histogram per direction (fallback path for the CUDA-core projection).
+__global__ void top_byte_hist_kernel(const float* __restrict__ q, int64_t n, unsigned* __restrict__ hist0) {
+  __shared__ unsigned h[256];
+  const int d = blockIdx.y;
+  for (int i = threadIdx.x; i < 256; i += blockDim.x) h[i] = 0;
+  __syncthreads();
+  const float* qd = q + (size_t)d * n;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    atomicAdd(&h[f32_key(__ldg(qd + i)) >> 24], 1u);
+  __syncthreads();
+  for (int i = threadIdx.x; i < 256; i += blockDim.x)
+    if (h[i]) atomicAdd(hist0 + (size_t)d * 256 + i, h[i]);
+}
+
 static cudaError_t launch_proj(const float* X, int64_t n, int D, const double* dirs, int nd, float* q, float* maxnorm,
-                               int* status, int num_sms, cudaStream_t st) {
+                               int* status, int num_sms, cudaStream_t st, unsigned* hist0) {
   const bool fast = (D % 4 == 0) && ((reinterpret_cast<uintptr_t>(X) & 15) == 0) && nd <= 32;
   if (!fast) {
     count_launch();
     proj_simple_kernel<<<num_sms * 8, 256, 0, st>>>(X, n, D, dirs, nd, q, maxnorm, status);
+    if (hist0) {
+      const unsigned chunks = (unsigned)std::max<int64_t>(1, std::min<int64_t>(ceil_div(n, 256 * 16), 4 * num_sms));
+      count_launch();
+      top_byte_hist_kernel<<<dim3(chunks, nd), 256, 0, st>>>(q, n, hist0);
+    }
     return cudaGetLastError();
   }
   const int Dq = (int)round_up(D, kProjK);
   auto go = [&](auto kern, int ND) -> cudaError_t {
-    size_t smem = (size_t)ND * Dq * 4 + (size_t)2 * kProjRows * kProjStride * 4;
+    size_t smem = (size_t)ND * Dq * 4 + (size_t)2 * kProjRows * kProjStride * 4 + (size_t)ND * 256 * 4;
     if (smem > 227 * 1024) return cudaErrorInvalidValue;
     cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     int per_sm = 0;
@@ -754,7 +1164,7 @@ static cudaError_t launch_proj(const float* X, int64_t n, int D, const double* d
     int64_t ntiles = ceil_div(n, kProjRows);
     int grid = (int)std::min<int64_t>(ntiles, (int64_t)std::max(1, per_sm) * num_sms);
     count_launch();
-    kern<<<grid, kProjThreads, smem, st>>>(X, n, D, dirs, nd, q, maxnorm, status);
+    kern<<<grid, kProjThreads, smem, st>>>(X, n, D, dirs, nd, q, maxnorm, status, hist0);
     return cudaGetLastError();
   };
   if (nd <= 3) return go(proj_kernel<3>, 3);
@@ -795,34 +1205,32 @@ cudaError_t select_run(prohd_ctx* ctx, const float* A, int64_t nA, const float* 
     kl.k[nd + d] = kB[d];
   }
   cudaMemsetAsync(b.maxnorm, 0, 2 * sizeof(float), st);
-  cudaMemsetAsync(b.hist, 0, sizeof(unsigned) * 2 * nd * 512, st);
+  cudaMemsetAsync(b.hist, 0, sizeof(unsigned) * 2 * nd * 256, st);
   cudaMemsetAsync(b.maskA, 0, (size_t)nA, st);
   cudaMemsetAsync(b.maskB, 0, (size_t)nB, st);
   {
     PhaseTimer pt(ctx, PROHD_PH_PROJECT, st);
-    if ((e = launch_proj(A, nA, D, dirs, nd, b.qA, b.maxnorm + 0, status_dev, nsm, st))) return e;
-    if ((e = launch_proj(B, nB, D, dirs, nd, b.qB, b.maxnorm + 1, status_dev, nsm, st))) return e;
+    if ((e = launch_proj(A, nA, D, dirs, nd, b.qA, b.maxnorm + 0, status_dev, nsm, st, b.hist))) return e;
+    if ((e = launch_proj(B, nB, D, dirs, nd, b.qB, b.maxnorm + 1, status_dev, nsm, st, b.hist + (size_t)nd * 256)))
+      return e;
   }
   PhaseTimer pt_sel(ctx, PROHD_PH_SELECT, st);
   count_launch();
-  sel_init_kernel<<<1, 128, 0, st>>>(b.P, nd, kl, A, b.qA, nA, b.maskA, B, b.qB, nB, b.maskB, D, dirs, b.maxnorm,
-                                     b.band, b.bandkey, b.cap);
-  // one set at a time: a set's keys (nd n 4 bytes) stay in L2 across its
-  // four histogram passes and the band pass
-  for (int set = 0; set < 2; ++set) {
-    const int64_t n = set ? nB : nA;
+  sel_init_pick_kernel<<<2 * nd, 256, 0, st>>>(b.P, nd, kl, A, b.qA, nA, b.maskA, B, b.qB, nB, b.maskB, D, dirs,
+                                               b.maxnorm, b.band, b.bandkey, b.cap, b.hist);
+  count_launch();
+  hist1_kernel<<<dim3(kHist1Blocks, 2 * nd), 512, 0, st>>>(b.P, b.hist1);
+  count_launch();
+  pick1_kernel<<<4 * nd, 256, 0, st>>>(b.P, b.hist1);
+  {
+    const int64_t nmax = std::max(nA, nB);
     const unsigned chunks =
-        (unsigned)std::max<int64_t>(1, std::min<int64_t>(ceil_div(n, 256 * 16), (nsm * 8 + nd - 1) / nd));
-    dim3 g(chunks, nd);
-    for (int pass = 0; pass < 4; ++pass) {
-      count_launch();
-      radix_hist_kernel<<<g, 256, 0, st>>>(b.P, pass, b.hist, set * nd);
-      count_launch();
-      radix_pick_kernel<<<(2 * nd * 32 + 127) / 128, 128, 0, st>>>(b.P, nd, pass, b.hist, set * nd);
-    }
+        (unsigned)std::max<int64_t>(1, std::min<int64_t>(ceil_div(nmax, 256 * 16), (nsm * 8 + nd - 1) / nd));
     count_launch();
-    band_kernel<<<g, 256, 0, st>>>(b.P, set * nd);
+    extract_kernel<<<dim3(chunks, 2 * nd), 256, 0, st>>>(b.P);
   }
+  count_launch();
+  cand_select_kernel<<<4 * nd, kCandThreads, 0, st>>>(b.P);
   count_launch();
   band_keys_kernel<<<dim3(16, 4 * nd), 256, 0, st>>>(b.P);
   count_launch();

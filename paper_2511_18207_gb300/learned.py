@@ -4,9 +4,12 @@ Host orchestration of library calls only (every arithmetic step of the
 features, the network, its gradient and update, the selection and the
 Hausdorff distances runs in the CUDA library):
 
-* training pairs: anisotropic Student-t (nu = 3) mixtures on the device;
+* training pairs: anisotropic Student-t (nu = 3) mixtures drawn on the
+  device (component rotations from a fixed pool, ``student_t_mixture_pool``);
   features from ``prohd_features``; label = the unit witness direction
-  (a* - b*)/||a* - b*|| of the exact HD (``hausdorff_exact``);
+  (a* - b*)/||a* - b*|| of the exact HD (``hausdorff_exact``), formed on the
+  device from the result's witness indices, so preparing a pair never waits
+  for the host;
 * training: Adam steps of ``prohd_mlp_train_step`` over shuffled minibatches;
 * evaluation at an equal candidate budget: plain ProHD keeps k_p per
   component on 8 components; the learned form adds the network's 4
@@ -33,8 +36,8 @@ def _pair(seed: int, n_lo: int, n_hi: int, D: int, device: str):
     nb = int(torch.randint(n_lo, n_hi + 1, (1,), generator=g))
     K = int(torch.randint(2, 9, (1,), generator=g))
     s = int(torch.randint(0, 2**31 - 1, (1,), generator=g))
-    A = W.student_t_mixture_device(na, D, K, seed=2 * s, device=device)
-    B = W.student_t_mixture_device(nb, D, K, seed=2 * s + 1, device=device)
+    A = W.student_t_mixture_pool(na, D, K, seed=2 * s, device=device)
+    B = W.student_t_mixture_pool(nb, D, K, seed=2 * s + 1, device=device)
     return A, B
 
 
@@ -46,9 +49,24 @@ def witness_label(ctx, A, B):
     return (d / n if n > 0 else d).float(), r
 
 
+def witness_label_into(ctx, A, B, out_row):
+    """The unit witness direction of the exact HD written into out_row [D]
+    without a host round trip: the witness indices are read on the device
+    from the result (wit_a and wit_b, int64 at bytes 24 and 32), clamped to
+    the sets for safety."""
+    res = ctx.hausdorff_exact(A, B, "fp16")
+    wit = res[24:40].view(dtype=__import__("torch").int64)
+    ia = wit[0:1].clamp(0, A.shape[0] - 1)
+    ib = wit[1:2].clamp(0, B.shape[0] - 1)
+    d = A.index_select(0, ia).double() - B.index_select(0, ib).double()
+    nrm = d.norm().clamp_min(1e-300)
+    out_row.copy_((d / nrm)[0].float())
+
+
 def make_dataset(ctx, npairs: int, n_lo: int = 5000, n_hi: int = 20000, D: int = 128, seed: int = 0,
                  device: str = "cuda"):
-    """(features [N, 10D], labels [N, D]) device tensors of npairs generated pairs."""
+    """(features [N, 10D], labels [N, D]) device tensors of npairs generated
+    pairs; one stream, no host synchronisation until the end."""
     import torch
 
     X = torch.empty((npairs, 10 * D), dtype=torch.float32, device=device)
@@ -56,7 +74,7 @@ def make_dataset(ctx, npairs: int, n_lo: int = 5000, n_hi: int = 20000, D: int =
     for i in range(npairs):
         A, B = _pair(seed * 1_000_003 + i, n_lo, n_hi, D, device)
         ctx.prohd_features(A, B, feat=X[i])
-        Y[i], _ = witness_label(ctx, A, B)
+        witness_label_into(ctx, A, B, Y[i])
     torch.cuda.synchronize()
     return X, Y
 
@@ -98,34 +116,54 @@ def alignment(dirs, w) -> float:
 def evaluate(ctx, net, npairs: int, n: int = 100_000, D: int = 128, alpha: float = 0.01, seed: int = 12345,
              precision: str = "bf16", device: str = "cuda") -> dict:
     """Held-out pairs of n points per set: relative error of plain ProHD and
-    of the learned form at an equal candidate budget, against the exact HD."""
+    of the learned form at an equal candidate budget, against the exact HD of
+    the full sets, and each form's time (CUDA events on the launching
+    stream) against the exact HD's. Plain: directions (centroid axis and 8
+    components) and Algorithm 3 with k_p per component. Learned: the same
+    directions, the network's forward pass, and Algorithm 3 on the 12
+    directions with k_p * 8/12 per direction."""
     import torch
 
     m = 8
     ap = alpha / m
     rows = []
+    st = torch.cuda.current_stream()
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(6)]
     for i in range(npairs):
         A, B = _pair(seed * 1_000_003 + i, n, n, D, device)
-        feat, dirs, eig = ctx.prohd_features(A, B)
-        w, ex = witness_label(ctx, A, B)
-        H = ex["H"]
         nA, nB = A.shape[0], B.shape[0]
         kc = [prohd.k_of(alpha, nA), prohd.k_of(alpha, nB)]
-        # plain: centroid axis + 8 components, alpha_p per component
         kpA, kpB = prohd.k_of(ap, nA), prohd.k_of(ap, nB)
-        rp = prohd.decode_result(ctx.prohd_estimate_dirs(A, B, dirs, [kc[0]] + [kpA] * m, [kc[1]] + [kpB] * m,
-                                                         precision="fp16"))
-        # learned: + 4 network directions, alpha_p * 8/12 on all 12
-        u = net.forward(feat[None, :], precision=precision, want64=True)[1][0]
-        all_dirs = torch.cat([dirs, u], dim=0)
         kqA, kqB = prohd.k_of(ap * m / (m + 4), nA), prohd.k_of(ap * m / (m + 4), nB)
-        rl = prohd.decode_result(ctx.prohd_estimate_dirs(A, B, all_dirs, [kc[0]] + [kqA] * (m + 4),
-                                                         [kc[1]] + [kqB] * (m + 4), precision="fp16"))
-        rows.append(dict(H=H, plain=rp["H"], learned=rl["H"], nsel_plain=rp["nsel_a"] + rp["nsel_b"],
+        # warm the kernels and the workspace on this pair's shapes, then time
+        for timed in (False, True):
+            ev[0].record(st)
+            exact = ctx.hausdorff_exact(A, B, "fp16")
+            ev[1].record(st)
+            feat, dirs, eig = ctx.prohd_features(A, B)
+            outp = ctx.prohd_estimate_dirs(A, B, dirs, [kc[0]] + [kpA] * m, [kc[1]] + [kpB] * m, precision="fp16")
+            ev[2].record(st)
+            feat2, dirs2, _ = ctx.prohd_features(A, B)
+            u = net.forward(feat2[None, :], precision=precision, want64=True)[1][0]
+            all_dirs = torch.cat([dirs2, u], dim=0)
+            outl = ctx.prohd_estimate_dirs(A, B, all_dirs, [kc[0]] + [kqA] * (m + 4), [kc[1]] + [kqB] * (m + 4),
+                                           precision="fp16")
+            ev[3].record(st)
+        torch.cuda.synchronize()
+        ex = prohd.decode_hd(exact)
+        rp, rl = prohd.decode_result(outp), prohd.decode_result(outl)
+        w = A[ex["wit_a"]].double() - B[ex["wit_b"]].double()
+        w = w / w.norm()
+        rows.append(dict(H=ex["H"], plain=rp["H"], learned=rl["H"], nsel_plain=rp["nsel_a"] + rp["nsel_b"],
                          nsel_learned=rl["nsel_a"] + rl["nsel_b"], align_plain=alignment(dirs[1:], w),
-                         align_learned=alignment(u, w)))
+                         align_learned=alignment(u, w), ms_exact=ev[0].elapsed_time(ev[1]),
+                         ms_plain=ev[1].elapsed_time(ev[2]), ms_learned=ev[2].elapsed_time(ev[3]),
+                         status=(ex["status"], rp["status"], rl["status"])))
     ep = np.array([abs(r["plain"] - r["H"]) / r["H"] for r in rows])
     el = np.array([abs(r["learned"] - r["H"]) / r["H"] for r in rows])
+    t_ex = np.array([r["ms_exact"] for r in rows])
+    t_p = np.array([r["ms_plain"] for r in rows])
+    t_l = np.array([r["ms_learned"] for r in rows])
     return dict(pairs=npairs, n=n, D=D, alpha=alpha,
                 rel_err_plain_mean=float(ep.mean()), rel_err_learned_mean=float(el.mean()),
                 rel_err_plain_max=float(ep.max()), rel_err_learned_max=float(el.max()),
@@ -134,6 +172,11 @@ def evaluate(ctx, net, npairs: int, n: int = 100_000, D: int = 128, alpha: float
                 align_learned_mean=float(np.mean([r["align_learned"] for r in rows])),
                 nsel_plain_mean=float(np.mean([r["nsel_plain"] for r in rows])),
                 nsel_learned_mean=float(np.mean([r["nsel_learned"] for r in rows])),
+                ms_exact_median=float(np.median(t_ex)), ms_plain_median=float(np.median(t_p)),
+                ms_learned_median=float(np.median(t_l)),
+                speedup_plain_vs_gpu_exact=float(np.median(t_ex / t_p)),
+                speedup_learned_vs_gpu_exact=float(np.median(t_ex / t_l)),
+                all_ok=all(r["status"] == ("OK", "OK", "OK") for r in rows),
                 rows=rows)
 
 
@@ -142,9 +185,9 @@ def main():
     import json
 
     ap = argparse.ArgumentParser(description="train the learned-direction network and evaluate its gain")
-    ap.add_argument("--pairs", type=int, default=2048)
-    ap.add_argument("--steps", type=int, default=2000)
-    ap.add_argument("--eval-pairs", type=int, default=16)
+    ap.add_argument("--pairs", type=int, default=50_000)
+    ap.add_argument("--steps", type=int, default=4000)
+    ap.add_argument("--eval-pairs", type=int, default=32)
     ap.add_argument("--eval-n", type=int, default=100_000)
     ap.add_argument("--lr", type=float, default=1e-3)
     ap.add_argument("--precision", default="bf16")

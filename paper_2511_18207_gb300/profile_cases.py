@@ -3,6 +3,8 @@
     python -m paper_2511_18207_gb300.profile_cases directions   # Gram + block iteration, 400k + 400k x 256
     python -m paper_2511_18207_gb300.profile_cases exact        # distance contraction, 100k x 100k x 256, FP16
     python -m paper_2511_18207_gb300.profile_cases pruned       # row-pruned exact distance, 2M x 2M x 256 (launch list)
+    python -m paper_2511_18207_gb300.profile_cases estimate     # one ProHD estimate, 2M x 2M x 256 (launch list)
+    python -m paper_2511_18207_gb300.profile_cases estimate_small  # one ProHD estimate, 400k x 400k x 256 (captures)
 
 Each case runs its call twice (the second launch is the one to capture, e.g.
 ``ncu --clock-control none -k regex:gram_tc_kernel -s 1 -c 1``), keeps the
@@ -59,7 +61,38 @@ def pruned():
     print("H", r["H"], r["status"], "rows kept", kept)
 
 
-CASES = {"directions": directions, "exact": exact, "pruned": pruned}
+def estimate():
+    # the benchmark's pair and estimate (m = 8, alpha = 0.01, FP16 tiles): two
+    # calls, the second is the one to list (about 5.5 GB on the device)
+    import torch
+
+    from . import prohd, workloads as W
+
+    A, B = W.anisotropic_pair(2_000_000, 2_000_000, 256, shift_sigma=0.1, t_frac=0.001, nu=3.0, seed=0)
+    At, Bt = torch.from_numpy(A).cuda(), torch.from_numpy(B).cuda()
+    r = None
+    for _ in range(2):
+        r = prohd.prohd_estimate_sync(At, Bt, m=8, alpha_c=0.01, precision="fp16")
+    print("H_hat", r["H"], r["status"], "|A_sel|", r["nsel_a"], "|B_sel|", r["nsel_b"])
+
+
+def estimate_small():
+    # the benchmark's law at 400k + 400k points (about 1.5 GB on the device),
+    # for full captures of the selection and distance kernels
+    import torch
+
+    from . import prohd, workloads as W
+
+    A, B = W.anisotropic_pair(400_000, 400_000, 256, shift_sigma=0.1, t_frac=0.001, nu=3.0, seed=0)
+    At, Bt = torch.from_numpy(A).cuda(), torch.from_numpy(B).cuda()
+    r = None
+    for _ in range(2):
+        r = prohd.prohd_estimate_sync(At, Bt, m=8, alpha_c=0.01, precision="fp16")
+    print("H_hat", r["H"], r["status"], "|A_sel|", r["nsel_a"], "|B_sel|", r["nsel_b"])
+
+
+CASES = {"directions": directions, "exact": exact, "pruned": pruned, "estimate": estimate,
+         "estimate_small": estimate_small}
 
 if __name__ == "__main__":
     if len(sys.argv) != 2 or sys.argv[1] not in CASES:

@@ -41,6 +41,7 @@ EXPORTS = [
     "prohd_mlp_loss_grad", "prohd_mlp_train_step", "prohd_mlp_adam_step",
     "prohd_estimate_adaptive_workspace_size", "prohd_estimate_adaptive",
     "hausdorff_exact_pruned_workspace_size", "hausdorff_exact_pruned", "prohd_set_prune_min_pairs",
+    "prohd_covariance_workspace_size", "prohd_covariance", "prohd_mlp_save", "prohd_mlp_load",
 ]
 
 #: prohd_phase names, in enum order
@@ -121,6 +122,15 @@ def load_library(path: str = LIB_PATH):
         lib.hausdorff_exact.restype = i32
         lib.prohd_directions.argtypes = [vp, vp, i64, vp, i64, i32, pp, vp, vp, vp, sz, vp]
         lib.prohd_directions.restype = i32
+        lib.prohd_mlp_save.argtypes = [vp, ctypes.c_char_p, i32, i64, vp, vp, i64, vp]
+        lib.prohd_mlp_save.restype = i32
+        lib.prohd_mlp_load.argtypes = [vp, ctypes.c_char_p, ctypes.POINTER(i32), ctypes.POINTER(i64), vp, vp, i64,
+                                       ctypes.POINTER(i64), vp]
+        lib.prohd_mlp_load.restype = i32
+        lib.prohd_covariance_workspace_size.argtypes = [i64, i64, i32]
+        lib.prohd_covariance_workspace_size.restype = sz
+        lib.prohd_covariance.argtypes = [vp, vp, i64, vp, i64, i32, vp, vp, vp, sz, vp]
+        lib.prohd_covariance.restype = i32
         lib.prohd_select.argtypes = [vp, vp, i64, vp, i64, i32, vp, i32, vp, vp, vp, vp, vp, vp, vp, sz, vp]
         lib.prohd_select.restype = i32
         lib.prohd_estimate.argtypes = [vp, vp, i64, vp, i64, i32, pp, vp, vp, vp, vp, vp, sz, vp]
@@ -358,6 +368,20 @@ class Context:
                                        _ptr(dirs), _ptr(eig), _ptr(ws), ws.numel(), self._stream(stream))
         self._raise(rc, "prohd_directions")
         return dirs, eig[:mm]
+
+    def prohd_covariance(self, A, B, stream=None):
+        """Union covariance C [D, D] and mean [D] of [A; B] (FP64 device tensors)."""
+        torch = _torch()
+        _check_points(A, "A")
+        _check_points(B, "B")
+        D = A.shape[1]
+        C = torch.empty((D, D), dtype=torch.float64, device=A.device)
+        mean = torch.empty(D, dtype=torch.float64, device=A.device)
+        ws = self.workspace(self.lib.prohd_covariance_workspace_size(A.shape[0], B.shape[0], D))
+        rc = self.lib.prohd_covariance(self.h, _ptr(A), A.shape[0], _ptr(B), B.shape[0], D, _ptr(C), _ptr(mean),
+                                       _ptr(ws), ws.numel(), self._stream(stream))
+        self._raise(rc, "prohd_covariance")
+        return C, mean
 
     def prohd_select(self, A, B, dirs, kA, kB, stream=None):
         """Returns (idxA, nselA, idxB, nselB) device tensors (int32 indices, int64 counts)."""
@@ -684,34 +708,31 @@ class Mlp:
 
     # ------------------------------------------------------------- checkpoints
 
-    def save(self, path: str, rng_state: bytes = b""):
-        """Versioned checkpoint: magic, D, step, parameter count, the host
-        RNG state of the training sampler, then params, Adam m, Adam v."""
-        import struct
-        body = self.state.detach().cpu().numpy().tobytes()
-        with open(path, "wb") as f:
-            f.write(self.MAGIC)
-            f.write(struct.pack("<iqqq", self.D, self.step, self.nparam, len(rng_state)))
-            f.write(rng_state)
-            f.write(body)
+    def save(self, path: str, rng_state: bytes = b"", stream=None):
+        """Versioned checkpoint through prohd_mlp_save: magic, D, step,
+        parameter count, the host RNG state of the training sampler, then
+        params, Adam m, Adam v."""
+        buf = ctypes.create_string_buffer(rng_state, len(rng_state)) if rng_state else None
+        rc = self.ctx.lib.prohd_mlp_save(self.ctx.h, os.fsencode(path), self.D, self.step, _ptr(self.state),
+                                         buf, len(rng_state), self.ctx._stream(stream))
+        self.ctx._raise(rc, "prohd_mlp_save")
 
     @classmethod
-    def load(cls, ctx: Context, path: str, device=None):
-        """Returns (network, rng_state)."""
-        import struct
-        torch = _torch()
-        with open(path, "rb") as f:
-            if f.read(8) != cls.MAGIC:
-                raise ValueError(f"{path}: not a network checkpoint of this version")
-            D, step, nparam, nrng = struct.unpack("<iqqq", f.read(28))
-            rng = f.read(nrng)
-            body = np.frombuffer(f.read(), dtype=np.float32)
-        net = cls(ctx, D, init=False, device=device)
-        if nparam != net.nparam or body.size != 3 * nparam:
-            raise ValueError(f"{path}: parameter count {nparam} does not match D = {D}")
-        net.state.copy_(torch.from_numpy(body.copy()))
-        net.step = step
-        return net, rng
+    def load(cls, ctx: Context, path: str, device=None, stream=None):
+        """Returns (network, rng_state), through prohd_mlp_load."""
+        D, step, nx = ctypes.c_int32(0), ctypes.c_int64(0), ctypes.c_int64(0)
+        rc = ctx.lib.prohd_mlp_load(ctx.h, os.fsencode(path), ctypes.byref(D), ctypes.byref(step), None, None, 0,
+                                    ctypes.byref(nx), ctx._stream(stream))
+        if rc != PROHD_OK:
+            raise ValueError(f"{path}: {ctx.lib.prohd_last_error(ctx.h).decode()}")
+        net = cls(ctx, D.value, init=False, device=device)
+        buf = ctypes.create_string_buffer(max(nx.value, 1))
+        rc = ctx.lib.prohd_mlp_load(ctx.h, os.fsencode(path), ctypes.byref(D), ctypes.byref(step), _ptr(net.state),
+                                    buf, nx.value, ctypes.byref(nx), ctx._stream(stream))
+        if rc != PROHD_OK:
+            raise ValueError(f"{path}: {ctx.lib.prohd_last_error(ctx.h).decode()}")
+        net.step = step.value
+        return net, buf.raw[: nx.value]
 
 
 # ----------------------------------------------------------------- decoding

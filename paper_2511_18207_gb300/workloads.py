@@ -221,6 +221,60 @@ def student_t_mixture_device(n: int, D: int = 128, K: int = 8, nu: float = 3.0, 
     return x.to(torch.float32).contiguous()
 
 
+_ROTATION_POOLS = {}
+
+
+def rotation_pool(D: int, size: int = 64, seed: int = 4242, device: str = "cuda"):
+    """A fixed pool of `size` random orthogonal D x D matrices (QR of seeded
+    Gaussian matrices, signs fixed by R's diagonal), FP32 on the device,
+    drawn once per (D, device)."""
+    import torch
+
+    key = (D, size, seed, str(device))
+    if key not in _ROTATION_POOLS:
+        g = torch.Generator(device="cpu")
+        g.manual_seed(int(seed))
+        G = torch.randn(size, D, D, generator=g, dtype=torch.float64)
+        Q, R = torch.linalg.qr(G)
+        Q = Q * torch.sign(torch.diagonal(R, dim1=1, dim2=2))[:, None, :]
+        _ROTATION_POOLS[key] = Q.to(device=device, dtype=torch.float32).contiguous()
+    return _ROTATION_POOLS[key]
+
+
+def student_t_mixture_pool(n: int, D: int = 128, K: int = 8, nu: int = 3, seed: int = 0, device: str = "cuda"):
+    """Anisotropic Student-t (integer nu) mixture drawn on the device in FP32,
+    without host synchronisation: K equally likely components with means
+    ~ N(0, 4I); component c draws z ~ N(0, I), x = z diag(1/sqrt(i)) R_c^T,
+    with R_c taken from the fixed rotation pool by a seeded index, divided
+    by sqrt(chi2_nu / nu). Component sizes are multinomial (seeded CPU
+    generator) and the points come in component blocks: the Hausdorff
+    distance and ProHD do not depend on the order of the points."""
+    import torch
+
+    gc = torch.Generator(device="cpu")
+    gc.manual_seed(int(seed))
+    counts = torch.bincount(torch.randint(0, K, (n,), generator=gc), minlength=K).tolist()
+    rot = torch.randint(0, rotation_pool(D, device=device).shape[0], (K,), generator=gc).tolist()
+    g = torch.Generator(device=device)
+    g.manual_seed(int(seed))
+    pool = rotation_pool(D, device=device)
+    scale = (1.0 / torch.arange(1, D + 1, dtype=torch.float32, device=device)).sqrt()
+    means = torch.randn(K, D, generator=g, device=device) * 2.0
+    z = torch.randn(n, D, generator=g, device=device)
+    w = (torch.randn(n, nu, generator=g, device=device) ** 2).sum(1) / nu
+    x = torch.empty(n, D, dtype=torch.float32, device=device)
+    off = 0
+    for c in range(K):
+        m = counts[c]
+        if m:
+            M = scale[:, None] * pool[rot[c]].t()  # x = z @ M
+            torch.matmul(z[off:off + m], M, out=x[off:off + m])
+            x[off:off + m] += means[c] * w[off:off + m, None].sqrt()
+        off += m
+    x /= w.sqrt()[:, None]
+    return x.contiguous()
+
+
 def _chi2_torch(n: int, nu: float, g, device):
     """Chi-squared(nu) draws as the sum of nu squared normals (integer nu) or
     a Gamma(nu/2, 2) draw otherwise."""

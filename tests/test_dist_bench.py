@@ -85,3 +85,7 @@ def test_reference_arm_line_on_a_small_pair(monkeypatch, capsys):
     assert line["e2e"]["h2d_bytes_per_step"] == 0 and line["e2e"]["value"] == line["value"]
     assert line["cpu_baseline"]["kind"] == "oracle" and line["cpu_baseline"]["cores"] >= 1
     assert "20,000" in line["config"]["workload"]
+    # the step time is what was measured; the full-pair figure is labelled as extrapolated
+    assert line["extrapolated"] is True and line["cpu_baseline"]["extrapolated"] is True
+    assert line["ms_per_step"] <= line["ms_per_full_pair_extrapolated"]
+    assert set(line["scale_factors"]) == {"covariance", "subset_hd"}

@@ -165,8 +165,15 @@ def test_checkpoint_resume_is_bit_identical(tmp_path):
         b.train_step(X[i * 64:(i + 1) * 64], Y[i * 64:(i + 1) * 64], lr=1e-3)
     torch.cuda.synchronize()
     assert torch.equal(a.state, b.state)
-    with open(path, "r+b") as f:
-        f.write(b"BADMAGIC")
+    # a truncated file and a foreign one are rejected by prohd_mlp_load
+    with open(path, "rb") as f:
+        whole = f.read()
+    with open(path, "wb") as f:
+        f.write(whole[: len(whole) - 4])
+    with pytest.raises(ValueError):
+        prohd.Mlp.load(c, path)
+    with open(path, "wb") as f:
+        f.write(b"BADMAGIC" + whole[8:])
     with pytest.raises(ValueError):
         prohd.Mlp.load(c, path)
 
