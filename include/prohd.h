@@ -52,7 +52,7 @@ typedef enum {
   PROHD_ENOTSUP = 6      /* valid request this build does not support (e.g. GPU older than sm_103a) */
 } prohd_status;
 
-/* Tile precision of the distance contraction (Sec. III-C, "exact HD on the subsets"). */
+/* Tile precision of the distance contraction (Methodology – Algorithms, "exact HD on the subsets"). */
 enum {
   PROHD_FP32 = 0, /* direct-difference FP32 on CUDA cores; exact to FP32 rounding */
   PROHD_FP16 = 1, /* FP16 tensor-core tiles, FP32 accumulation, rigorous margin + FP32 rescoring */
@@ -63,7 +63,7 @@ enum {
 typedef struct prohd_ctx prohd_ctx;
 
 /*
- * ProHD parameters (Algorithm 3 and Sec. IV-A).
+ * ProHD parameters (Algorithm 3 and Evaluation – Datasets and Experimental Setup).
  *   m            number of principal components; m < 0 selects floor(sqrt(D))
  *   alpha_c      fraction kept per side on the centroid axis, 0 < alpha_c < 1:
  *                k_c = max(1, floor(alpha_c * n)) per set (Algorithm 1)
@@ -153,7 +153,7 @@ size_t prohd_estimate_host_workspace_size(int64_t nA, int64_t nB, int D, const p
 
 /*
  * Exact Hausdorff distance H(A,B) (Eq. 1; the paper computes it with a Faiss
- * flat index, Sec. III-C and IV-A "ANN-Exact").
+ * flat index, Methodology – Algorithms and Evaluation – Datasets and Experimental Setup "ANN-Exact").
  *   A [nA*D], B [nB*D]   device FP32 point sets
  *   precision            PROHD_FP32, PROHD_FP16 or PROHD_BF16 (tile dtype)
  *   out                  device pointer to one prohd_hd_result
@@ -168,7 +168,7 @@ prohd_status hausdorff_exact(prohd_ctx* ctx, const float* A, int64_t nA, const f
 
 /*
  * The same exact distance with row pruning: the early-break idea of the exact
- * Hausdorff algorithms the paper compares with (Sec. II), as whole-set passes.
+ * Hausdorff algorithms the paper compares with (Related Work), as whole-set passes.
  * For each direction h(X, Y):
  *   1. an exact pass over 1,024 evenly spread rows of X gives a lower bound
  *      LB1 of h(X, Y);
@@ -397,7 +397,7 @@ prohd_status prohd_estimate_dirs(prohd_ctx* ctx, const float* A, int64_t nA, con
 
 /* ---------------------------------------------------------------- adaptive alpha
  *
- * The adaptive alpha schedule Sec. VI proposes for strict error budgets, read
+ * The adaptive alpha schedule Conclusion and Future Work proposes for strict error budgets, read
  * as doubling alpha on the one-sided refined estimate: the directions are
  * computed once (as prohd_estimate computes them); step t = 0, 1, ... keeps
  * alpha_t = alpha_c 2^t per side on the centroid axis and alpha_p 2^t on each
@@ -437,7 +437,7 @@ prohd_status prohd_estimate_adaptive(prohd_ctx* ctx, const float* A, int64_t nA,
 /* ---------------------------------------------------------------- learned directions
  *
  * A small network proposes 4 extra unit directions per pair from cheap set
- * statistics (the learned direction dictionary of Sec. V, future work in the
+ * statistics (the learned direction dictionary of Conclusion and Future Work, future work in the
  * paper). It only adds directions, so plain ProHD is its fallback.
  *
  * Features (prohd_features), x [10 D] FP32: the centroid difference

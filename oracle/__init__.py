@@ -13,7 +13,7 @@ paper's Algorithm 3 (ProjHausdorff) from its pieces:
                                     (top-m principal components of [A; B])
 * ``select``                        Algorithms 1-2 (bottom-k / top-k, union)
 * ``prohd``                         Algorithm 3
-* ``hd_1d`` / ``delta``             the quantities of the bounds in Sec. III-E
+* ``hd_1d`` / ``delta``             the quantities of the bounds in Methodology – Theoretical Properties
 """
 from __future__ import annotations
 
@@ -202,7 +202,7 @@ def power_iteration(C, m: int, seed: int = 0, tol: float = 1e-13, maxit: int = 1
 
 
 def default_m(D: int) -> int:
-    """m = floor(sqrt(D)) (Sec. III-A)."""
+    """m = floor(sqrt(D)) (Methodology – Background and Notation)."""
     return int(math.isqrt(D))
 
 
@@ -297,7 +297,7 @@ def prohd(A, B, alpha: float = 0.01, m: int | None = None, alpha_p: float | None
 
 
 def refined(A, B, idxA, idxB):
-    """One-sided refinement of a ProHD estimate (reading of Sec. III-E's
+    """One-sided refinement of a ProHD estimate (reading of the Theoretical Properties subsection's
     underestimation claim): max(h(A_sel, B), h(B_sel, A)), each selected
     point's nearest neighbour searched in the whole other set. Every term is
     a true nearest-neighbour distance of a point of A (or B), so the result
@@ -318,7 +318,7 @@ ADAPTIVE_MAX_STEPS = 32
 
 def adaptive(A, B, alpha: float, alpha_max: float, rel_tol: float, m: int | None = None,
              alpha_p: float | None = None, seed: int = 0, dirs=None, max_steps: int = ADAPTIVE_MAX_STEPS):
-    """Adaptive alpha schedule (the future direction of Sec. VI: alpha grown
+    """Adaptive alpha schedule (the future direction of Conclusion and Future Work: alpha grown
     until the estimate meets an error budget), read as a doubling schedule on
     the one-sided refined estimate.
 
@@ -367,7 +367,7 @@ def adaptive(A, B, alpha: float, alpha_max: float, rel_tol: float, m: int | None
 
 
 # --------------------------------------------------------------------------
-# Sec. III-E quantities
+# Methodology – Theoretical Properties quantities
 # --------------------------------------------------------------------------
 
 def hd_1d(pX, pY) -> float:

@@ -5,7 +5,7 @@ use this module; it shares no code with the CUDA path. It restates, in plain
 numpy FP64 (matrix products are library primitives, nothing is fused):
 
 * the input features of a pair (the future-work direction dictionary of
-  Sec. V, in the form this library implements): centroid difference, the 8
+  Conclusion and Future Work, in the form this library implements): centroid difference, the 8
   leading principal components scaled by sqrt(lambda), per-dimension union
   variances, scaled by s = sqrt(trace(C) / D) (variances by s^2);
 * the network h1 = relu(x W1 + b1), h2 = relu(h1 W2 + b2), z = h2 W3 + b3,

@@ -11,16 +11,16 @@
  * OpenMP only splits independent outer iterations (rows, directions).
  *
  * Functions and the passages they follow:
- *   oracle_directed_hd      Eq. 1 (h(A,B) = max_a min_b ||a-b||_2), Sec. III-A
+ *   oracle_directed_hd      Eq. 1 (h(A,B) = max_a min_b ||a-b||_2), Methodology – Background and Notation
  *   oracle_centroid         Algorithm 1, centroid step
  *   oracle_centroid_axis    Algorithm 1, direction step (1e-9 fallback to e_1)
  *   oracle_union_covariance Algorithm 2, "principal components of [X;Y]"
  *   oracle_power_iteration  Algorithm 2, top-m components (power iteration with
- *                           Gram-Schmidt deflation; Sec. III-D names truncated SVD)
- *   oracle_project          Sec. III-A projection pi_u(p) = p^T u
+ *                           Gram-Schmidt deflation; Methodology – Analysis names truncated SVD)
+ *   oracle_project          Methodology – Background and Notation projection pi_u(p) = p^T u
  *   oracle_select           Algorithms 1-2 (bottom-k and top-k per direction and
  *                           per set, union, unique)
- *   oracle_hd_1d            Sec. III-E, 1D directed HD along u
+ *   oracle_hd_1d            Methodology – Theoretical Properties, 1D directed HD along u
  *   oracle_delta            Eq. 2, delta(u) = max_p ||p - (p^T u) u||
  *   oracle_splitmix64_unit  the counter-based generator for power-iteration
  *                           start vectors (SplitMix64, Steele/Lea/Flood 2014)
@@ -243,7 +243,7 @@ int oracle_power_iteration(const double* C, int D, int m, uint64_t seed, double 
 /* ------------------------------------------------------------------------ */
 
 /* p_i = x_i^T u, summed sequentially over k = 0..D-1 in FP64, each product and
- * sum rounded separately (Sec. III-A projection). +0.0 is added last so that a
+ * sum rounded separately (Methodology – Background and Notation projection). +0.0 is added last so that a
  * result of -0.0 compares and sorts as +0.0. */
 void oracle_project(const float* X, int64_t n, int D, const double* u, double* p) {
 #pragma omp parallel for schedule(static)
@@ -326,7 +326,7 @@ int oracle_select(const float* X, int64_t n, int D, const double* dirs, int nd,
 }
 
 /* ------------------------------------------------------------------------ */
-/* Diagnostics for the bounds of Sec. III-E.                                 */
+/* Diagnostics for the bounds of Methodology – Theoretical Properties.                                 */
 /* ------------------------------------------------------------------------ */
 
 /* 1D directed HD: max_i min_j |pX[i] - pY[j]|, by brute force. */

@@ -27,7 +27,7 @@
 // CTA's points against the other's) are computed and ignored.
 //
 // Pipeline per CTA: a TMA warp streams FP32 tiles [64 points x 128 dims]
-// through a four-stage ring (dimensions past D arrive as zeros); eight
+// through a four-stage ring (dimensions past D arrive as zeros); sixteen
 // converter warps centre, split and transpose them into K-major,
 // 128B-swizzled BF16 tile pairs {h, 2m} [128 dims x 64 points] (the operand
 // layout of the distance contraction; two pairs, used by alternate steps, so
@@ -39,8 +39,8 @@
 // CTA's barriers with remote mbarrier arrives after fence.proxy.async (a
 // release at cluster scope costs a memory barrier per arrive, which stalled
 // every step).
-// Warps: 0..7 converters, 8 MMA issuer (even CTA) and TMEM owner, 9..12
-// epilogue, 13 TMA producer.
+// Warps: 0..15 converters, 16 MMA issuer (even CTA) and TMEM owner, 17..20
+// epilogue, 21 TMA producer.
 #include <cuda_bf16.h>
 #include <limits.h>
 #include <string.h>
@@ -54,7 +54,8 @@ namespace prohd {
 
 constexpr int kGcPts = 64;          // points per tile (one 128-byte K row of BF16)
 constexpr int kGcRows = 128;        // dimensions per CTA
-constexpr int kGcConv = 8;          // converter warps, 8 points each
+constexpr int kGcConv = 16;         // converter warps: 8 points x 64 dimensions each
+constexpr int kGcPg = kGcPts / 8;   // 8-point groups of a tile (one 16-byte unit of a BF16 row)
 constexpr int kGcEpi = 4;
 constexpr int kGcMmaWarp = kGcConv;
 constexpr int kGcTmaWarp = kGcConv + 1 + kGcEpi;
@@ -67,7 +68,7 @@ constexpr uint32_t kGcTileBytes = kGcRows * 128;             // one BF16 operand
 constexpr uint32_t kGcStageBytes = kGcPts * kGcRows * 4;     // one FP32 stage
 constexpr uint32_t kGcSumCol = 256;                          // TMEM column of the running sums
 constexpr int kGcSlotFloats = 2 * 256 * kGcRows;             // per pair: [rank][col][row] partial products
-constexpr int kGcSumsDoubles = 2 * kGcConv * 2 * kGcRows;    // per pair: [rank][warp][z | corr][dim]
+constexpr int kGcSumsDoubles = 2 * kGcPg * 2 * kGcRows;      // per pair: [rank][point group][z | corr][dim]
 
 // Packed round-to-nearest conversion of two FP32 values to BF16x2 (a in the
 // low half, b in the high half), and the FP32 values of the halves.
@@ -183,7 +184,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kGcThreads, 1)
     }
     for (int b = 0; b < kGcBufs; ++b)
       for (int s = 0; s < kGcSlices; ++s) {
-        mbar_init(&S.sfull[b][s], 2 * (kGcConv / kGcSlices));
+        mbar_init(&S.sfull[b][s], 2 * (kGcConv / kGcSlices));  // the slice's converter warps of both CTAs
         mbar_init(&S.sempty[b][s], 1);
       }
     mbar_init(&S.acc_full, 1);
@@ -284,14 +285,17 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kGcThreads, 1)
       }
     } else if (warp < kGcConv) {
       // ---------------- converters: centre, split, transpose ----------------
-      const int s = warp >> 1;
-      const float* st0 = stage + (size_t)(warp * 8) * kGcRows + lane;
-      uint8_t* dst0 = tiles + lane * 128 + ((warp ^ (lane & 7)) * 16);
-      float ss[4], sc[4], cr[4], shift[4];
+      // warp w: points 8 (w % 8) .. + 7 of the tile, dimensions lane + 32 t
+      // for t = 2 (w / 8), 2 (w / 8) + 1 (tile rows of this CTA)
+      const int pg = warp & (kGcPg - 1), th = warp / kGcPg;
+      const int s = pg >> 1;
+      const float* st0 = stage + (size_t)(pg * 8) * kGcRows + lane + 64 * th;
+      uint8_t* dst0 = tiles + lane * 128 + ((pg ^ (lane & 7)) * 16) + th * 2 * 4096;
+      float ss[2], sc[2], cr[2], shift[2];
 #pragma unroll
-      for (int t = 0; t < 4; ++t) {
+      for (int t = 0; t < 2; ++t) {
         ss[t] = sc[t] = cr[t] = 0.f;
-        const int d = dim0 + lane + 32 * t;
+        const int d = dim0 + lane + 32 * (2 * th + t);
         shift[t] = d < w.D ? w.s32[d] : 0.f;
       }
       for (int c = 0; c < nsteps; ++c) {
@@ -307,15 +311,15 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kGcThreads, 1)
         got = __shfl_sync(0xffffffffu, got, 0);
         if (!got) break;
         const float* st = st0 + (size_t)f * kGcPts * kGcRows;
-        const int64_t left = w.p1 - (w.p0 + (int64_t)c * span + cta_off + warp * 8);
+        const int64_t left = w.p1 - (w.p0 + (int64_t)c * span + cta_off + pg * 8);
         if (left >= 8) {
 #pragma unroll
-          for (int t = 0; t < 4; ++t)
+          for (int t = 0; t < 2; ++t)
             gc_convert_row<true>(st + 32 * t, dst + t * 4096, shift[t], ss[t], sc[t], cr[t], 8);
         } else {
           const int nv = left > 0 ? (int)left : 0;
 #pragma unroll
-          for (int t = 0; t < 4; ++t)
+          for (int t = 0; t < 2; ++t)
             gc_convert_row<false>(st + 32 * t, dst + t * 4096, shift[t], ss[t], sc[t], cr[t], nv);
         }
         fence_proxy_async();
@@ -329,12 +333,13 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kGcThreads, 1)
       // A non-finite coordinate makes its dimension's running sum non-finite
       // (so does an FP32 overflow of the sum, which would also ruin G).
       bool bad = false;
-      double* out = w.sums + (size_t)(rank * kGcConv + warp) * 2 * kGcRows;
+      double* out = w.sums + (size_t)(rank * kGcPg + pg) * 2 * kGcRows;
 #pragma unroll
-      for (int t = 0; t < 4; ++t) {
+      for (int t = 0; t < 2; ++t) {
+        const int dl = lane + 32 * (2 * th + t);
         bad |= !isfinite(ss[t]) || !isfinite(sc[t]) || !isfinite(cr[t]);
-        out[lane + 32 * t] = (double)ss[t] - (double)sc[t];
-        out[kGcRows + lane + 32 * t] = (double)cr[t];
+        out[dl] = (double)ss[t] - (double)sc[t];
+        out[kGcRows + dl] = (double)cr[t];
       }
       if (__any_sync(0xffffffffu, bad) && lane == 0) atomicMax(w.status, (int)PROHD_ENONFINITE);
     } else if (warp == kGcMmaWarp) {
@@ -392,15 +397,15 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kGcThreads, 1)
         }
         tc_fence_after();
         if (useful) {
-          for (int cc = 0; cc < ucols / 32; ++cc) {
-            float v[32], sum[32];
+          for (int cc = 0; cc < ucols / 16; ++cc) {
+            float v[16], sum[16];
             __syncwarp();
-            tc_ld_32x32b_x32(lane_base + (uint32_t)(ucol0 + cc * 32), v);
-            if (i > 0) tc_ld_32x32b_x32(lane_base + kGcSumCol + (uint32_t)(cc * 32), sum);
+            tc_ld_32x32b_x16(lane_base + (uint32_t)(ucol0 + cc * 16), v);
+            if (i > 0) tc_ld_32x32b_x16(lane_base + kGcSumCol + (uint32_t)(cc * 16), sum);
             tc_wait_ld();
 #pragma unroll
-            for (int j = 0; j < 32; ++j) sum[j] = i > 0 ? sum[j] + v[j] : v[j];
-            tc_st_32x32b_x32(lane_base + kGcSumCol + (uint32_t)(cc * 32), sum);
+            for (int j = 0; j < 16; ++j) sum[j] = i > 0 ? sum[j] + v[j] : v[j];
+            tc_st_32x32b_x16(lane_base + kGcSumCol + (uint32_t)(cc * 16), sum);
           }
           tc_wait_st();
         }
@@ -415,18 +420,18 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kGcThreads, 1)
       if (ok) {
         // the item's partial product: [col][row], useful columns only (zeros for an empty item)
         float* o = w.out + (size_t)rank * ucols * kGcRows;
-        for (int cc = 0; cc < ucols / 32; ++cc) {
-          float sum[32];
+        for (int cc = 0; cc < ucols / 16; ++cc) {
+          float sum[16];
           if (useful && nint > 0) {
             __syncwarp();
-            tc_ld_32x32b_x32(lane_base + kGcSumCol + (uint32_t)(cc * 32), sum);
+            tc_ld_32x32b_x16(lane_base + kGcSumCol + (uint32_t)(cc * 16), sum);
             tc_wait_ld();
           } else {
 #pragma unroll
-            for (int j = 0; j < 32; ++j) sum[j] = 0.f;
+            for (int j = 0; j < 16; ++j) sum[j] = 0.f;
           }
 #pragma unroll
-          for (int j = 0; j < 32; ++j) o[(size_t)(cc * 32 + j) * kGcRows + row] = sum[j];
+          for (int j = 0; j < 16; ++j) o[(size_t)(cc * 16 + j) * kGcRows + row] = sum[j];
         }
         tc_fence_before();
       }
@@ -526,8 +531,8 @@ __device__ __forceinline__ void gc_dims_pass(const SlotOf& slot_of, int nslots, 
       bool setA;
       slot_of(c, slot, sums, setA);
       for (int r = r0; r <= r1; ++r)
-        for (int w = 0; w < kGcConv; ++w) {
-          const double* sw = sums + (size_t)(r * kGcConv + w) * 2 * kGcRows;
+        for (int w = 0; w < kGcPg; ++w) {
+          const double* sw = sums + (size_t)(r * kGcPg + w) * 2 * kGcRows;
           const double z = __ldg(sw + dl);
           cr += __ldg(sw + kGcRows + dl);
           if (setA) sa += z;

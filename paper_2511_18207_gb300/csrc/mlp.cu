@@ -1,6 +1,6 @@
 // Learned projection directions: a small network that proposes extra
 // directions from cheap set statistics (the direction dictionary the paper
-// names as future work, Sec. V). It only ever adds directions to the
+// names as future work, Conclusion and Future Work). It only ever adds directions to the
 // centroid axis and the principal components, so plain ProHD stays the
 // fallback and the reference for its error.
 //

@@ -22,6 +22,7 @@
 //     the band in between is ranked by FP64 projections recomputed exactly as
 //     the sequential definition (__dmul_rn / __dadd_rn), ties by index.
 //  The largest side is the same on reversed keys.
+#include <limits.h>
 #include <string.h>
 
 #include <algorithm>
@@ -430,6 +431,20 @@ __global__ void __launch_bounds__(256)
   }
   __syncthreads();
   for (int side = 0; side < 2; ++side) block_pick<256>(h, k - 1, side, &s_bin[side], &s_left[side]);
+  // ||u||^2 in parallel (the serial FP64 sum in sel_reset is a long chain of
+  // dependent additions); any order gives a valid bound E
+  __shared__ double s_un[256];
+  double un = 0.0;
+  for (int j = threadIdx.x; j < D; j += blockDim.x) {
+    const double x = dirs[(size_t)d * D + j];
+    un += x * x;
+  }
+  s_un[threadIdx.x] = un;
+  __syncthreads();
+  for (int o = 128; o > 0; o >>= 1) {
+    if ((int)threadIdx.x < o) s_un[threadIdx.x] += s_un[threadIdx.x + o];
+    __syncthreads();
+  }
   if (threadIdx.x != 0) return;
   SelProb s;
   s.n = n;
@@ -443,7 +458,11 @@ __global__ void __launch_bounds__(256)
     s.band[side] = band + ((size_t)p * 2 + side) * cap;
     s.bkey[side] = bandkey + ((size_t)p * 2 + side) * cap;
   }
-  sel_reset(s, k);
+  s.prefix[0] = s.prefix[1] = 0;
+  s.k = k;
+  s.E = ((double)D + 8.0) * 5.9604644775390625e-8 * 1.0201 * (double)(*s.maxnorm) * sqrt(s_un[0]) + 1e-300;
+  s.cin[0] = s.cin[1] = 0;
+  s.nband[0] = s.nband[1] = 0;
   for (int side = 0; side < 2; ++side) {
     s.prefix[side] = (uint32_t)s_bin[side] << 24;
     s.rank[side] = s_left[side];
@@ -465,16 +484,16 @@ __global__ void __launch_bounds__(512) hist1_kernel(const SelProb* __restrict__ 
   const int64_t c0 = n * blockIdx.x / gridDim.x, c1 = n * (blockIdx.x + 1) / gridDim.x;
   const uint32_t b0 = S.prefix[0] >> 24, b1 = S.prefix[1] >> 24;
   const float* q = S.q;
-  // four independent loads in flight per thread
-  for (int64_t base = c0; base < c1; base += 4 * (int64_t)blockDim.x) {
-    float v[4];
+  // eight independent loads in flight per thread
+  for (int64_t base = c0; base < c1; base += 8 * (int64_t)blockDim.x) {
+    float v[8];
 #pragma unroll
-    for (int u = 0; u < 4; ++u) {
+    for (int u = 0; u < 8; ++u) {
       const int64_t i = base + u * (int64_t)blockDim.x + threadIdx.x;
       v[u] = i < c1 ? __ldg(q + i) : 0.f;
     }
 #pragma unroll
-    for (int u = 0; u < 4; ++u) {
+    for (int u = 0; u < 8; ++u) {
       const int64_t i = base + u * (int64_t)blockDim.x + threadIdx.x;
       if (i >= c1) continue;
       const uint32_t k = f32_key(v[u]);
@@ -545,49 +564,56 @@ __global__ void extract_kernel(SelProb* __restrict__ P) {
   unsigned long long in0c = 0, in1c = 0;
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   const int64_t end = (n + 31) / 32 * 32;
-  for (int64_t base = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; base < end; base += 4 * stride) {
-   float vv[4];
+  for (int64_t base = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; base < end; base += 8 * stride) {
+    // eight independent loads in flight, classified before any warp-wide step
+    float vv[8];
+    unsigned cand = 0;  // bit u: a candidate for side 0 (bit u) or side 1 (bit 8 + u)
 #pragma unroll
-   for (int u = 0; u < 4; ++u) {
-     const int64_t i = base + u * stride;
-     vv[u] = i < n ? __ldg(q + i) : 0.f;
-   }
+    for (int u = 0; u < 8; ++u) {
+      const int64_t i = base + u * stride;
+      vv[u] = i < n ? __ldg(q + i) : 0.f;
+    }
 #pragma unroll
-   for (int u = 0; u < 4; ++u) {
-    const int64_t i = base + u * stride;
-    if (i - threadIdx.x % 32 >= end) break;  // the whole warp is past the end
-    bool in0 = false, cd0 = false, in1 = false, cd1 = false;
-    const float v = vv[u];
-    if (i < n) {
-      in0 = v < t0;
-      cd0 = !in0 && v <= c0;
-      in1 = v > t1;
-      cd1 = !in1 && v >= c1;
+    for (int u = 0; u < 8; ++u) {
+      const int64_t i = base + u * stride;
+      if (i >= n) continue;
+      const float v = vv[u];
+      const bool in0 = v < t0, in1 = v > t1;
       if (in0 || in1) mask[i] = 1;
+      in0c += in0;
+      in1c += in1;
+      cand |= ((!in0 && v <= c0) ? 1u : 0u) << u;
+      cand |= ((!in1 && v >= c1) ? 1u : 0u) << (8 + u);
     }
-    in0c += in0;
-    in1c += in1;
-    const unsigned m0 = __ballot_sync(0xffffffffu, cd0), m1 = __ballot_sync(0xffffffffu, cd1);
-    unsigned long long base0 = 0, base1 = 0;
-    if (lane == 0 && m0)
-      base0 = atomicAdd(reinterpret_cast<unsigned long long*>(&S.nband[0]), (unsigned long long)__popc(m0));
-    if (lane == 0 && m1)
-      base1 = atomicAdd(reinterpret_cast<unsigned long long*>(&S.nband[1]), (unsigned long long)__popc(m1));
-    base0 = __shfl_sync(0xffffffffu, base0, 0);
-    base1 = __shfl_sync(0xffffffffu, base1, 0);
-    const unsigned below = (1u << lane) - 1;
-    const uint32_t key = f32_key(v);
-    if (cd0) {
-      const unsigned long long o = base0 + __popc(m0 & below);
-      b0[o] = (int32_t)i;
-      k0[o] = key;
+    // candidates are rare: the append path runs only where a lane has one
+    if (!__any_sync(0xffffffffu, cand != 0)) continue;
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      const int64_t i = base + u * stride;
+      if (i - lane >= end) break;  // the whole warp is past the end
+      const bool cd0 = (cand >> u) & 1u, cd1 = (cand >> (8 + u)) & 1u;
+      const unsigned m0 = __ballot_sync(0xffffffffu, cd0), m1 = __ballot_sync(0xffffffffu, cd1);
+      if (!(m0 | m1)) continue;
+      unsigned long long base0 = 0, base1 = 0;
+      if (lane == 0 && m0)
+        base0 = atomicAdd(reinterpret_cast<unsigned long long*>(&S.nband[0]), (unsigned long long)__popc(m0));
+      if (lane == 0 && m1)
+        base1 = atomicAdd(reinterpret_cast<unsigned long long*>(&S.nband[1]), (unsigned long long)__popc(m1));
+      base0 = __shfl_sync(0xffffffffu, base0, 0);
+      base1 = __shfl_sync(0xffffffffu, base1, 0);
+      const unsigned below = (1u << lane) - 1;
+      const uint32_t key = f32_key(vv[u]);
+      if (cd0) {
+        const unsigned long long o = base0 + __popc(m0 & below);
+        b0[o] = (int32_t)i;
+        k0[o] = key;
+      }
+      if (cd1) {
+        const unsigned long long o = base1 + __popc(m1 & below);
+        b1[o] = (int32_t)i;
+        k1[o] = ~key;
+      }
     }
-    if (cd1) {
-      const unsigned long long o = base1 + __popc(m1 & below);
-      b1[o] = (int32_t)i;
-      k1[o] = ~key;
-    }
-   }
   }
   in0c = warp_sum(in0c);
   in1c = warp_sum(in1c);
@@ -773,13 +799,12 @@ __global__ void band_kernel(SelProb* __restrict__ P, int pbase) {
 }
 
 // FP64 projection exactly as the sequential definition.
-// FP64 keys of every band member, spread over many blocks (FP64 arithmetic is
-// scarce on this GPU: one block per band would serialise a large band's
-// sequential sums on one SM). One warp per member: the warp stages the row
-// in shared memory with coalesced loads, then one lane forms the sequential
-// FP64 sum (the order of the definition; a parallel sum would round
-// differently). grid (chunks, 4 * nd): y = problem * 2 + side.
-__global__ void __launch_bounds__(256) band_keys_kernel(const SelProb* __restrict__ P) {
+// FP64 keys of every band member, one thread per member and many blocks:
+// the sequential FP64 sum is a chain of dependent additions whose latency is
+// long on this GPU, so as many chains as possible run side by side (a warp
+// per member, with one lane summing, was seven times slower).
+// grid (chunks, 4 * nd): y = problem * 2 + side.
+__global__ void band_keys_kernel(const SelProb* __restrict__ P) {
   const int p = blockIdx.y >> 1, side = blockIdx.y & 1;
   const float* X = P[p].X;
   const int D = P[p].D;
@@ -787,32 +812,28 @@ __global__ void __launch_bounds__(256) band_keys_kernel(const SelProb* __restric
   const int64_t r = P[p].k - P[p].cin[side];
   if (b == 0 || r <= 0) return;
   __shared__ double us[1024];
-  __shared__ float rows[8][1024];
   const double* u = P[p].u;
-  const bool sm = D <= 1024;
-  if (sm)
+  const bool u_sm = D <= 1024;
+  if (u_sm)
     for (int k = threadIdx.x; k < D; k += blockDim.x) us[k] = u[k];
   __syncthreads();
+  const double* uu = u_sm ? us : u;
   const int32_t* lst = P[p].band[side];
   uint64_t* keys = P[p].bkey[side];
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int64_t wstride = (int64_t)gridDim.x * (blockDim.x >> 5);
-  for (int64_t i = blockIdx.x * (int64_t)(blockDim.x >> 5) + warp; i < b; i += wstride) {
-    const float* x = X + (int64_t)__ldg(lst + i) * D;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < b; i += (int64_t)gridDim.x * blockDim.x) {
     double s = 0.0;
-    if (sm) {
-      for (int k = lane; k < D; k += 32) rows[warp][k] = __ldg(x + k);
-      __syncwarp();
-      if (lane == 0)
-        for (int k = 0; k < D; ++k) s = __dadd_rn(s, __dmul_rn((double)rows[warp][k], us[k]));
-      __syncwarp();
-    } else if (lane == 0) {
-      for (int k = 0; k < D; ++k) s = __dadd_rn(s, __dmul_rn((double)__ldg(x + k), u[k]));
+    const float* x = X + (int64_t)__ldg(lst + i) * D;
+    int k = 0;
+    for (; k + 8 <= D; k += 8) {
+      float xv[8];
+#pragma unroll
+      for (int j = 0; j < 8; ++j) xv[j] = __ldg(x + k + j);
+#pragma unroll
+      for (int j = 0; j < 8; ++j) s = __dadd_rn(s, __dmul_rn((double)xv[j], uu[k + j]));
     }
-    if (lane == 0) {
-      const uint64_t kk = f64_key(s);
-      keys[i] = side ? ~kk : kk;
-    }
+    for (; k < D; ++k) s = __dadd_rn(s, __dmul_rn((double)__ldg(x + k), uu[k]));
+    const uint64_t kk = f64_key(s);
+    keys[i] = side ? ~kk : kk;
   }
 }
 
@@ -836,18 +857,33 @@ __global__ void __launch_bounds__(512)
   const int32_t* lst = P[p].band[side];
   const uint64_t* keys = P[p].bkey[side];
   if (b <= kBandSmem) {
-    for (int64_t i = threadIdx.x; i < b; i += blockDim.x) {
-      si[i] = __ldg(lst + i);
-      sk[i] = __ldg(keys + i);
+    // bitonic sort of (key, index) pairs, padded with the largest pair up
+    // to a power of two; then the first r are the selected ones
+    int P2 = 1;
+    while (P2 < b) P2 <<= 1;
+    for (int i = threadIdx.x; i < P2; i += blockDim.x) {
+      si[i] = i < b ? __ldg(lst + i) : INT_MAX;
+      sk[i] = i < b ? __ldg(keys + i) : ~0ull;
     }
     __syncthreads();
-    for (int64_t i = threadIdx.x; i < b; i += blockDim.x) {
-      const uint64_t ki = sk[i];
-      const int32_t ii = si[i];
-      int64_t rank = 0;
-      for (int64_t j = 0; j < b; ++j) rank += (sk[j] < ki) || (sk[j] == ki && si[j] < ii);
-      if (rank < r) mask[ii] = 1;
-    }
+    for (int size = 2; size <= P2; size <<= 1)
+      for (int stride = size >> 1; stride > 0; stride >>= 1) {
+        for (int t = threadIdx.x; t < (P2 >> 1); t += blockDim.x) {
+          const int i = 2 * t - (t & (stride - 1)), j = i + stride;
+          const bool up = (i & size) == 0;
+          const uint64_t ka = sk[i], kb = sk[j];
+          const int32_t ia = si[i], ib = si[j];
+          const bool gt = ka > kb || (ka == kb && ia > ib);
+          if (gt == up) {
+            sk[i] = kb;
+            sk[j] = ka;
+            si[i] = ib;
+            si[j] = ia;
+          }
+        }
+        __syncthreads();
+      }
+    for (int64_t i = threadIdx.x; i < r && i < b; i += blockDim.x) mask[si[i]] = 1;
     return;
   }
 
@@ -1223,16 +1259,19 @@ cudaError_t select_run(prohd_ctx* ctx, const float* A, int64_t nA, const float* 
   count_launch();
   pick1_kernel<<<4 * nd, 256, 0, st>>>(b.P, b.hist1);
   {
+    // one wave: 4 blocks of 256 threads per SM (the register limit) over all 2 nd problems
     const int64_t nmax = std::max(nA, nB);
     const unsigned chunks =
-        (unsigned)std::max<int64_t>(1, std::min<int64_t>(ceil_div(nmax, 256 * 16), (nsm * 8 + nd - 1) / nd));
+        (unsigned)std::max<int64_t>(1, std::min<int64_t>(ceil_div(nmax, 256 * 8), (nsm * 4) / (2 * nd)));
     count_launch();
     extract_kernel<<<dim3(chunks, 2 * nd), 256, 0, st>>>(b.P);
   }
   count_launch();
   cand_select_kernel<<<4 * nd, kCandThreads, 0, st>>>(b.P);
+  // one warp per block: a large band's FP64 chains spread over many SMs
+  // (each SM's FP64 units are few)
   count_launch();
-  band_keys_kernel<<<dim3(16, 4 * nd), 256, 0, st>>>(b.P);
+  band_keys_kernel<<<dim3(64, 4 * nd), 32, 0, st>>>(b.P);
   count_launch();
   band_resolve_kernel<<<4 * nd, 512, 0, st>>>(b.P);
   if ((e = cudaGetLastError())) return e;

@@ -1,12 +1,12 @@
-"""Parameter sweeps of ProHD on random clouds (Sec. IV-A data: U[0,1]^D
+"""Parameter sweeps of ProHD on random clouds (Evaluation – Datasets and Experimental Setup data: U[0,1]^D
 against U[0,1]^D + 0.1), the synthetic halves of the paper's sensitivity and
-scalability studies (Sec. IV-D, IV-E):
+scalability studies (Evaluation – Parameter Sensitivity and Scalability Analysis):
 
 * ``alpha``: the selection fraction (Fig. 2's sweep, here on random clouds);
 * ``dim``: D in {2, ..., 256} at 100k + 100k points (Fig. 3);
 * ``ratio``: n_B / n_A in {0.125, 0.25, 0.5, 1} with n_A = 100k, D = 4 (Fig. 4);
 * ``size``: n_A = n_B from 100k to 1M, D = 4 (Fig. 5);
-* ``adaptive``: the adaptive alpha schedule of Sec. VI (doubling alpha on the
+* ``adaptive``: the adaptive alpha schedule of Conclusion and Future Work (doubling alpha on the
   refined estimate until it stabilises) at D = 4, 64, 256.
 
 Every point runs through the library: the estimate of Algorithm 3

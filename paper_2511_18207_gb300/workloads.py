@@ -5,7 +5,7 @@ CUDA path and the FP64 oracle are fed from it, so it imports neither.
 
 The paper's datasets (CIFAR-10, MNIST, Higgs) are not available; these
 generators stand in for them with the shapes and structures the paper's
-experiments use (Sec. IV-A: uniform random clouds with a 0.1 offset) and the
+experiments use (Evaluation – Datasets and Experimental Setup: uniform random clouds with a 0.1 offset) and the
 workload families this library is benchmarked on:
 
 * ``gaussian_outliers``  N(0, I) vs N(0.5*1, I) with 1% of B scaled x3
@@ -14,7 +14,7 @@ workload families this library is benchmarked on:
 * ``anisotropic_pair``   A ~ N(0, Q diag(1/i) Q^T); B the same law shifted by
                          0.1 sigma_r along a random unit r, plus a fraction of
                          multivariate Student-t (nu = 3) points
-* ``random_clouds``      U[0,1]^D vs U[0,1]^D + 0.1 (Sec. IV-A)
+* ``random_clouds``      U[0,1]^D vs U[0,1]^D + 0.1 (Evaluation – Datasets and Experimental Setup)
 * ``batched_pairs``      uneven pairs, log-uniform sizes, D in {64,128,256}
 * ``student_t_mixture``  anisotropic Student-t mixtures (learned-direction data)
 
@@ -120,7 +120,7 @@ def anisotropic_pair(n_a: int = 2_000_000, n_b: int = 2_000_000, D: int = 256,
 
 def random_clouds(n_a: int = 100_000, n_b: int = 100_000, D: int = 4, offset: float = 0.1,
                   seed: int = 0):
-    """U[0,1]^D vs U[0,1]^D + offset (Sec. IV-A random clouds)."""
+    """U[0,1]^D vs U[0,1]^D + offset (Evaluation – Datasets and Experimental Setup random clouds)."""
     rng = _rng(seed)
     A = rng.random((n_a, D), dtype=np.float32)
     B = rng.random((n_b, D), dtype=np.float32) + np.float32(offset)

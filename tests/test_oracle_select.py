@@ -1,5 +1,5 @@
 """Pins for the oracle's extreme selection (Algorithms 1-2), Algorithm 3, and
-the bounds of Sec. III-E."""
+the bounds of Methodology – Theoretical Properties."""
 import numpy as np
 import pytest
 
@@ -105,7 +105,7 @@ def test_sec3e_bounds(seed):
 
 
 def test_overestimate_is_possible_and_reported():
-    # Sec. III-B/III-E state H_hat <= H; with subset-vs-subset HD (Algorithm 3)
+    # Methodology – Intuition and Theoretical Properties state H_hat <= H; with subset-vs-subset HD (Algorithm 3)
     # it can exceed H. Count such cases on tiny random inputs: they exist.
     rng = np.random.default_rng(0)
     over = 0

@@ -1,4 +1,4 @@
-"""The random-cloud sweeps (Sec. IV-D/IV-E shapes): the sweep grid, the
+"""The random-cloud sweeps (Evaluation – Parameter Sensitivity and Scalability Analysis shapes): the sweep grid, the
 table formatting, and one small point end to end on the GPU."""
 import pytest
 
