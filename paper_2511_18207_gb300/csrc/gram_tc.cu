@@ -31,11 +31,13 @@
 // converter warps centre, split and transpose them into K-major,
 // 128B-swizzled BF16 tile pairs {h, 2m} [128 dims x 64 points] (the operand
 // layout of the distance contraction; two pairs, used by alternate steps, so
-// conversion runs a step ahead of the MMAs) and hand each 16-point slice to the
-// even CTA's MMA thread (a cluster-scope mbarrier arrive); that thread issues
-// the slice's two MMAs and hands the slice back to both CTAs' converters when
-// they complete; four epilogue warps per CTA fold each 512-point accumulator
-// into the running sum. The odd CTA's converters and epilogue signal the even
+// conversion runs a step ahead of the MMAs) and signal the even CTA's MMA
+// thread; that thread issues the step's eight MMAs (two per 16-point slice)
+// and hands the tile pair back to both CTAs' converters when they complete;
+// four epilogue warps per CTA fold each 512-point accumulator into the
+// running sum. The converters work on point pairs with two-wide FP32
+// arithmetic (f32x2), which halves their instruction count: conversion, not
+// HBM or the tensor pipe, bounded the step rate. The odd CTA's converters and epilogue signal the even
 // CTA's barriers with remote mbarrier arrives after fence.proxy.async (a
 // release at cluster scope costs a memory barrier per arrive, which stalled
 // every step).
@@ -90,8 +92,8 @@ __device__ __forceinline__ void kahan_add(float& s, float& c, float x) {
 
 struct GcSmem {
   uint64_t ffull[kGcStages], fempty[kGcStages];
-  uint64_t sfull[kGcBufs][kGcSlices];   // even CTA: slice converted by both CTAs (4 arrivals)
-  uint64_t sempty[kGcBufs][kGcSlices];  // slice's MMAs done (committed to both CTAs)
+  uint64_t sfull[kGcBufs];   // even CTA: tile pair converted by every converter warp of both CTAs
+  uint64_t sempty[kGcBufs];  // the tile pair's MMAs done (committed to both CTAs)
   uint64_t acc_full;           // accumulator holds a finished interval (committed to both CTAs)
   uint64_t acc_empty;          // even CTA: accumulator read by both CTAs' epilogues (8 arrivals)
   uint64_t drain;
@@ -121,35 +123,79 @@ struct GcParams {
   int* ticket;
 };
 
+// Two-wide FP32 arithmetic on point pairs (f32x2; lo = the first point).
+__device__ __forceinline__ uint64_t f2_pack(float a, float b) {
+  uint64_t r;
+  asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(a), "f"(b));
+  return r;
+}
+__device__ __forceinline__ void f2_unpack(uint64_t v, float& a, float& b) {
+  asm("mov.b64 {%0, %1}, %2;" : "=f"(a), "=f"(b) : "l"(v));
+}
+__device__ __forceinline__ uint64_t f2_add(uint64_t a, uint64_t b) {
+  uint64_t r;
+  asm("add.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+  return r;
+}
+__device__ __forceinline__ uint64_t f2_sub(uint64_t a, uint64_t b) {
+  uint64_t r;
+  asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+  return r;
+}
+__device__ __forceinline__ uint64_t f2_fma(uint64_t a, uint64_t b, uint64_t c) {
+  uint64_t r;
+  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(r) : "l"(a), "l"(b), "l"(c));
+  return r;
+}
+// The two BF16 halves of v as an FP32 pair (a BF16 is the top half of an FP32).
+__device__ __forceinline__ uint64_t f2_from_bf16x2(uint32_t v) {
+  return ((uint64_t)(v & 0xffff0000u) << 32) | (uint64_t)(v << 16);
+}
+
+// Per converter lane and dimension: the Kahan-compensated set sum of z, and
+// the two sums whose difference is the diagonal correction
+// sum (z^2 - h^2 - 2hm) = sum e (z + h) - sum h (2m), e = z - h; each holds
+// two points' lanes (f32x2).
+struct GcAcc {
+  float ss, sc;
+  uint64_t ezh, hm2;
+};
+
 // Splits eight points of one dimension into the {h, 2m} operand rows (16
-// bytes each, point i in the low half of pair i/2) and accumulates the set
-// sum (Kahan) and the diagonal correction sum (z^2 - h^2 - 2hm). Only the
-// first `nv` points are real when !FULL; the rest contribute zeros.
+// bytes each, point i in the low half of pair i/2) and accumulates GcAcc.
+// Only the first `nv` points are real when !FULL; the rest contribute zeros.
 template <bool FULL>
 __device__ __forceinline__ void gc_convert_row(const float* __restrict__ st, uint8_t* __restrict__ dst, float shift,
-                                               float& ss, float& sc, float& cr, int nv) {
-  float z[8];
+                                               GcAcc& a, int nv) {
+  float x[8];
 #pragma unroll
   for (int i = 0; i < 8; ++i) {
-    const float x = st[i * kGcRows];
-    z[i] = (FULL || i < nv) ? x - shift : 0.f;
+    const float v = st[i * kGcRows];
+    x[i] = (FULL || i < nv) ? v : shift;  // padding points centre to exactly zero
   }
-  kahan_add(ss, sc, ((z[0] + z[1]) + (z[2] + z[3])) + ((z[4] + z[5]) + (z[6] + z[7])));
+  const uint64_t sh = f2_pack(shift, shift);
+  uint64_t z[4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i) z[i] = f2_sub(f2_pack(x[2 * i], x[2 * i + 1]), sh);
+  {
+    float lo, hi;
+    f2_unpack(f2_add(f2_add(z[0], z[1]), f2_add(z[2], z[3])), lo, hi);
+    kahan_add(a.ss, a.sc, lo + hi);
+  }
   uint32_t h[4], m2[4];
-  float corr = 0.f;
 #pragma unroll
   for (int i = 0; i < 4; ++i) {
-    const float z0 = z[2 * i], z1 = z[2 * i + 1];
+    float z0, z1;
+    f2_unpack(z[i], z0, z1);
     h[i] = bf16x2_rn(z0, z1);
-    const float h0 = bf16_lo(h[i]), h1 = bf16_hi(h[i]);
-    const float e0 = z0 - h0, e1 = z1 - h1;  // exact
-    m2[i] = bf16x2_rn(2.f * e0, 2.f * e1);   // 2m, exact doubling of bf16(e)
-    // z^2 - h^2 - 2hm = e (z + h) - h (2m): h (2m) is exact in FP32, the
-    // fused multiply-add rounds once
-    corr += fmaf(e0, z0 + h0, -(h0 * bf16_lo(m2[i])));
-    corr += fmaf(e1, z1 + h1, -(h1 * bf16_hi(m2[i])));
+    const uint64_t hf = f2_from_bf16x2(h[i]);
+    const uint64_t e = f2_sub(z[i], hf);  // exact
+    float e20, e21;
+    f2_unpack(f2_add(e, e), e20, e21);    // 2e, exact
+    m2[i] = bf16x2_rn(e20, e21);          // 2m, the exact doubling of bf16(e)
+    a.ezh = f2_fma(e, f2_add(z[i], hf), a.ezh);
+    a.hm2 = f2_fma(hf, f2_from_bf16x2(m2[i]), a.hm2);  // h (2m) is exact
   }
-  cr += corr;
   *reinterpret_cast<uint4*>(dst) = make_uint4(h[0], h[1], h[2], h[3]);
   *reinterpret_cast<uint4*>(dst + kGcTileBytes) = make_uint4(m2[0], m2[1], m2[2], m2[3]);
 }
@@ -182,11 +228,10 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kGcThreads, 1)
       mbar_init(&S.ffull[s], 1);
       mbar_init(&S.fempty[s], kGcConv);
     }
-    for (int b = 0; b < kGcBufs; ++b)
-      for (int s = 0; s < kGcSlices; ++s) {
-        mbar_init(&S.sfull[b][s], 2 * (kGcConv / kGcSlices));  // the slice's converter warps of both CTAs
-        mbar_init(&S.sempty[b][s], 1);
-      }
+    for (int b = 0; b < kGcBufs; ++b) {
+      mbar_init(&S.sfull[b], 2 * kGcConv);  // every converter warp of both CTAs
+      mbar_init(&S.sempty[b], 1);
+    }
     mbar_init(&S.acc_full, 1);
     mbar_init(&S.acc_empty, 2 * kGcEpi);
     mbar_init(&S.drain, 1);
@@ -288,13 +333,14 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kGcThreads, 1)
       // warp w: points 8 (w % 8) .. + 7 of the tile, dimensions lane + 32 t
       // for t = 2 (w / 8), 2 (w / 8) + 1 (tile rows of this CTA)
       const int pg = warp & (kGcPg - 1), th = warp / kGcPg;
-      const int s = pg >> 1;
       const float* st0 = stage + (size_t)(pg * 8) * kGcRows + lane + 64 * th;
       uint8_t* dst0 = tiles + lane * 128 + ((pg ^ (lane & 7)) * 16) + th * 2 * 4096;
-      float ss[2], sc[2], cr[2], shift[2];
+      GcAcc acc[2];
+      float shift[2];
 #pragma unroll
       for (int t = 0; t < 2; ++t) {
-        ss[t] = sc[t] = cr[t] = 0.f;
+        acc[t].ss = acc[t].sc = 0.f;
+        acc[t].ezh = acc[t].hm2 = 0ull;
         const int d = dim0 + lane + 32 * (2 * th + t);
         shift[t] = d < w.D ? w.s32[d] : 0.f;
       }
@@ -306,7 +352,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kGcThreads, 1)
         uint8_t* dst = dst0 + (size_t)bf * 2 * kGcTileBytes;
         int got = 1;
         if (lane == 0)
-          got = gc_wait(&S.sempty[bf][s], (use & 1u) ^ 1u, abort, peer_abort, p.timeout_ns) &&
+          got = gc_wait(&S.sempty[bf], (use & 1u) ^ 1u, abort, peer_abort, p.timeout_ns) &&
                 gc_wait(&S.ffull[f], (g / kGcStages) & 1u, abort, peer_abort, p.timeout_ns);
         got = __shfl_sync(0xffffffffu, got, 0);
         if (!got) break;
@@ -314,20 +360,18 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kGcThreads, 1)
         const int64_t left = w.p1 - (w.p0 + (int64_t)c * span + cta_off + pg * 8);
         if (left >= 8) {
 #pragma unroll
-          for (int t = 0; t < 2; ++t)
-            gc_convert_row<true>(st + 32 * t, dst + t * 4096, shift[t], ss[t], sc[t], cr[t], 8);
+          for (int t = 0; t < 2; ++t) gc_convert_row<true>(st + 32 * t, dst + t * 4096, shift[t], acc[t], 8);
         } else {
           const int nv = left > 0 ? (int)left : 0;
 #pragma unroll
-          for (int t = 0; t < 2; ++t)
-            gc_convert_row<false>(st + 32 * t, dst + t * 4096, shift[t], ss[t], sc[t], cr[t], nv);
+          for (int t = 0; t < 2; ++t) gc_convert_row<false>(st + 32 * t, dst + t * 4096, shift[t], acc[t], nv);
         }
         fence_proxy_async();
         __syncwarp();
         if (lane == 0) {
           mbar_arrive(&S.fempty[f]);
-          if (leader) mbar_arrive(&S.sfull[bf][s]);
-          else mbar_arrive_remote(map_to_cta(&S.sfull[bf][s], 0));
+          if (leader) mbar_arrive(&S.sfull[bf]);
+          else mbar_arrive_remote(map_to_cta(&S.sfull[bf], 0));
         }
       }
       // A non-finite coordinate makes its dimension's running sum non-finite
@@ -337,9 +381,12 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kGcThreads, 1)
 #pragma unroll
       for (int t = 0; t < 2; ++t) {
         const int dl = lane + 32 * (2 * th + t);
-        bad |= !isfinite(ss[t]) || !isfinite(sc[t]) || !isfinite(cr[t]);
-        out[dl] = (double)ss[t] - (double)sc[t];
-        out[kGcRows + dl] = (double)cr[t];
+        float e0, e1, q0, q1;
+        f2_unpack(acc[t].ezh, e0, e1);
+        f2_unpack(acc[t].hm2, q0, q1);
+        bad |= !isfinite(acc[t].ss) || !isfinite(acc[t].sc) || !isfinite(e0 + e1);
+        out[dl] = (double)acc[t].ss - (double)acc[t].sc;
+        out[kGcRows + dl] = ((double)e0 + (double)e1) - ((double)q0 + (double)q1);
       }
       if (__any_sync(0xffffffffu, bad) && lane == 0) atomicMax(w.status, (int)PROHD_ENONFINITE);
     } else if (warp == kGcMmaWarp) {
@@ -354,23 +401,18 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kGcThreads, 1)
             if (!gc_wait(&S.acc_empty, (fi & 1u) ^ 1u, abort, peer_abort, p.timeout_ns)) break;
             tc_fence_after();
           }
-          bool ok = true;
           const int bf = (int)(g % kGcBufs);
           const uint32_t use = g / kGcBufs;
           const uint32_t th = smem_u32(tiles) + (uint32_t)bf * 2 * kGcTileBytes, tm2 = th + kGcTileBytes;
+          if (!gc_wait(&S.sfull[bf], use & 1u, abort, peer_abort, p.timeout_ns)) break;
+          tc_fence_after();
 #pragma unroll
           for (int k = 0; k < kGcSlices; ++k) {
-            if (!gc_wait(&S.sfull[bf][k], use & 1u, abort, peer_abort, p.timeout_ns)) {
-              ok = false;
-              break;
-            }
-            tc_fence_after();
             const uint64_t bh = smem_desc_sw128(th + k * 32);
             tc2_mma_f16(tmem, bh, bh, idesc, (in_acc | k) != 0);
             tc2_mma_f16(tmem, smem_desc_sw128(tm2 + k * 32), bh, idesc, 1u);
-            tc2_commit_mc(&S.sempty[bf][k], 0x3);  // slice k of this buffer may be overwritten in both CTAs
           }
-          if (!ok) break;
+          tc2_commit_mc(&S.sempty[bf], 0x3);  // this tile pair may be overwritten in both CTAs
           if (++in_acc == kGcFlush || c == nsteps - 1) {
             tc2_commit_mc(&S.acc_full, 0x3);
             in_acc = 0;

@@ -801,36 +801,60 @@ __global__ void __launch_bounds__(kSiThreads, 1)
                                    max(q.iters, 1), eps, sigma_rel, seed, q.U, q.iters_out);
 }
 
-// FP64 clean-up of the m Ritz vectors (one CTA): modified Gram-Schmidt twice,
-// normalisation, sign (largest |entry| positive, lowest index on ties).
+// FP64 clean-up of the m Ritz vectors (one CTA): classical Gram-Schmidt
+// applied twice against the vectors already cleaned (all of a pass's
+// projections come from one block-wide reduction; two passes orthogonalise
+// to working precision, as modified Gram-Schmidt twice does, with a third of
+// the sequential FP64 reductions), normalisation, sign (largest |entry|
+// positive, lowest index on ties).
 PROHD_DEV void subspace_finalize_body(const double* __restrict__ Uin, int D, int m, double* __restrict__ dirs) {
   __shared__ double u[kSiMaxD];
-  __shared__ double red[kSiFinThreads / 32];
+  __shared__ double red[kSiFinThreads / 32][kSiMaxM + 1];
+  __shared__ double dk[kSiMaxM + 1];
   __shared__ unsigned long long s_best[kSiFinThreads / 32];
   __shared__ int s_idx;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  auto block_dot = [&](const double* a, const double* bvec) -> double {
-    double s = 0.0;
-    for (int j = tid; j < D; j += blockDim.x) s = fma(a[j], bvec[j], s);
-    s = warp_sum(s);
+  constexpr int NW = kSiFinThreads / 32;
+  // dk[0..cnt) = u . dirs[1 + k] for k < cnt (cnt = 0: dk[0] = u . u)
+  auto block_dots = [&](int cnt) {
+    const int nv = cnt > 0 ? cnt : 1;
+    double part[kSiMaxM];
+#pragma unroll
+    for (int k = 0; k < kSiMaxM; ++k) part[k] = 0.0;
+    for (int j = tid; j < D; j += blockDim.x) {
+      const double x = u[j];
+#pragma unroll
+      for (int k = 0; k < kSiMaxM; ++k)
+        if (k < nv) part[k] = fma(x, cnt > 0 ? dirs[(size_t)(k + 1) * D + j] : x, part[k]);
+    }
+#pragma unroll
+    for (int k = 0; k < kSiMaxM; ++k)
+      if (k < nv) {
+        const double v = warp_sum(part[k]);
+        if (lane == 0) red[warp][k] = v;
+      }
     __syncthreads();
-    if (lane == 0) red[warp] = s;
+    if (tid < nv) {
+      double t = 0.0;
+      for (int w = 0; w < NW; ++w) t += red[w][tid];
+      dk[tid] = t;
+    }
     __syncthreads();
-    double tsum = 0.0;
-    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) tsum += red[w];
-    return tsum;
   };
   for (int l = 0; l < m; ++l) {
     for (int j = tid; j < D; j += blockDim.x) u[j] = Uin[(size_t)l * D + j];
     __syncthreads();
-    for (int pass = 0; pass < 2; ++pass)
-      for (int k = 0; k < l; ++k) {
-        const double* uk = dirs + (size_t)(k + 1) * D;
-        const double d = block_dot(u, uk);
-        for (int j = tid; j < D; j += blockDim.x) u[j] = fma(-d, uk[j], u[j]);
-        __syncthreads();
+    for (int pass = 0; pass < 2 && l > 0; ++pass) {
+      block_dots(l);
+      for (int j = tid; j < D; j += blockDim.x) {
+        double x = u[j];
+        for (int k = 0; k < l; ++k) x = fma(-dk[k], dirs[(size_t)(k + 1) * D + j], x);
+        u[j] = x;
       }
-    const double nn = block_dot(u, u);
+      __syncthreads();
+    }
+    block_dots(0);
+    const double nn = dk[0];
     const double inv = nn > 0.0 ? 1.0 / sqrt(nn) : 0.0;
     for (int j = tid; j < D; j += blockDim.x) u[j] *= inv;
     __syncthreads();
@@ -846,7 +870,7 @@ PROHD_DEV void subspace_finalize_body(const double* __restrict__ Uin, int D, int
     __syncthreads();
     if (tid == 0) {
       unsigned long long bb = 0ull;
-      for (int w = 0; w < (int)(blockDim.x >> 5); ++w) bb = s_best[w] > bb ? s_best[w] : bb;
+      for (int w = 0; w < NW; ++w) bb = s_best[w] > bb ? s_best[w] : bb;
       s_best[0] = bb;
       s_idx = D;
     }
