@@ -512,7 +512,7 @@ void prohd_params_default(prohd_params* p) {
   p->precision = PROHD_FP16;
   p->alpha_c = 0.01;
   p->alpha_p = -1.0;
-  p->power_max_iters = 1000;
+  p->power_max_iters = 96;
   p->power_tol = 1e-13;
   p->seed = 0;
   p->wait_timeout_ns = kDefaultTimeoutNs;

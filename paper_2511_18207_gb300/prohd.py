@@ -353,7 +353,7 @@ class Context:
         self._raise(rc, "hausdorff_exact_noalloc")
         return out
 
-    def prohd_directions(self, A, B, m=None, seed=0, max_iters=1000, tol=1e-13, stream=None):
+    def prohd_directions(self, A, B, m=None, seed=0, max_iters=None, tol=1e-13, stream=None):
         torch = _torch()
         _check_points(A, "A")
         _check_points(B, "B")

@@ -32,7 +32,7 @@ def test_host_only_helpers():
     assert prohd.k_of(0.01, 2000) == 20
     assert prohd.k_of(0.5, 1) == 1
     p = prohd.default_params()
-    assert p.m == -1 and p.precision == 1 and p.alpha_c == 0.01 and p.power_max_iters == 1000
+    assert p.m == -1 and p.precision == 1 and p.alpha_c == 0.01 and p.power_max_iters == 96
 
 
 def test_batch_workspace_size_is_host_only():
