@@ -663,7 +663,8 @@ prohd_status prohd_select(prohd_ctx* ctx, const float* A, int64_t nA, const floa
   a.cap = ws_bytes;
   int* status = a.take<int>(8);
   cudaError_t e = zero_i32(status, 8, st);
-  if (!e) e = select_run(ctx, A, nA, B, nB, D, dirs, ndirs, kA, kB, idxA, nselA, idxB, nselB, status, a, st);
+  if (!e) e = select_run(ctx, A, nA, B, nB, D, dirs, ndirs, kA, kB, idxA, nselA, idxB, nselB, status, a, st,
+                         kDefaultTimeoutNs);
   return e ? cuda_fail(ctx, e) : PROHD_OK;
 }
 
@@ -736,7 +737,7 @@ static prohd_status estimate_run(prohd_ctx* ctx, const float* A, int64_t nA, con
   if (!e) {
     Arena t = phase(L.mark_sel);
     e = select_run(ctx, A, nA, B, nB, D, use_dirs, L.nd, L.kA, L.kB, L.idxA, L.nselA, L.idxB, L.nselB, L.status, t,
-                   st);
+                   st, p->wait_timeout_ns);
   }
   {
     PhaseTimer pt(ctx, PROHD_PH_GATHER, st);
@@ -1047,7 +1048,7 @@ prohd_status prohd_estimate_adaptive(prohd_ctx* ctx, const float* A, int64_t nA,
     if (!e) {
       Arena t = phase(L.mark_sel);
       e = select_run(ctx, A, nA, B, nB, D, L.dirs, L.nd, L.kA, L.kB, L.idxA, L.nselA, L.idxB, L.nselB, L.status, t,
-                     st);
+                     st, p->wait_timeout_ns);
     }
     {
       PhaseTimer pt(ctx, PROHD_PH_GATHER, st);

@@ -101,7 +101,7 @@ void select_layout(Arena& ws, int64_t nA, int64_t nB, int D, int ndirs);
 cudaError_t select_run(prohd_ctx* ctx, const float* A, int64_t nA, const float* B, int64_t nB, int D,
                        const double* dirs, int ndirs, const int64_t* kA, const int64_t* kB, int32_t* idxA,
                        int64_t* nselA, int32_t* idxB, int64_t* nselB, int* status_dev, Arena& ws,
-                       cudaStream_t st);
+                       cudaStream_t st, int64_t timeout_ns);
 cudaError_t gather_rows(const float* X, int D, const int32_t* idx, const int64_t* n_dev, int64_t n_max, float* out,
                         int num_sms, cudaStream_t st);
 

@@ -6,8 +6,9 @@
 // k = 0..D-1 with separately rounded products and sums, ties broken by the
 // lower index at both ends. The GPU reaches it exactly without computing FP64
 // projections for every point:
-//  1. FP32 projections q (one HBM pass over the points, cp.async-staged tiles,
-//     all directions at once) and E = (D+8) 2^-24 max||x|| ||u|| (1.01)^2, a
+//  1. FP32 projections q (one HBM pass over the points, all directions at
+//     once; both sets in one TMA-fed launch, cp.async-staged tiles for the
+//     batched path and for more than 17 directions) and E = (D+8) 2^-24 max||x|| ||u|| (1.01)^2, a
 //     bound on |q - p64| for every point.
 //  2. The exact k-th smallest FP32 key T over order-preserving uint32 keys.
 //     One pair: the projection pass also counts every key's top byte, one
@@ -171,6 +172,191 @@ __global__ void __launch_bounds__(kProjThreads)
   const int64_t n = it.set ? q.nB : q.nA;
   proj_body<ND>(it.set ? q.B : q.A, n, q.D, q.dirs, q.nd, it.set ? q.qB : q.qA, q.maxnorm + it.set, q.status,
                 it.r0 / kProjRows, (it.r1 + kProjRows - 1) / kProjRows, 1, nullptr);
+}
+
+// ---------------------------------------------------------------- TMA projection of a pair
+
+// One persistent launch projects both sets: tiles of kPtRows rows, A's tiles
+// first, then B's. A producer warp streams each tile through a ring of
+// `stages` shared-memory stages, 32 dimensions (128 bytes) of every row per
+// stage, by TMA with the 128-byte swizzle (chunk j of row r lands at
+// position j ^ (r & 7) of the row, so the row-per-thread reads of a quarter
+// warp hit eight different bank groups); rows past n and dimensions past D
+// arrive as zeros. Each of the kPtThreads consumer threads owns kPtRpt rows
+// (r, r + kPtThreads, ...) and sums the products of dimension pairs with
+// packed FP32 FMAs (even and odd dimensions in the two halves, added at the
+// end). Any summation order stays within the bound E of the header (the
+// rounding error of a D-term dot product in FP32 is at most D 2^-24 sum
+// |x_k u_k| for every order of the terms).
+constexpr int kPtThreads = 256;                  // consumer threads
+constexpr int kPtRpt = 2;                        // rows per consumer thread
+constexpr int kPtRows = kPtThreads * kPtRpt;     // rows per tile
+constexpr int kPtBox = 256;                      // rows per TMA box
+constexpr uint32_t kPtStageBytes = kPtRows * 128;
+constexpr int kPtMaxStages = 4;
+
+struct ProjPairArgs {
+  int64_t nA, nB, tilesA, tiles;
+  int D, Dq, nd, nchunks, stages;
+  const double* dirs;
+  float *qA, *qB;
+  float* maxnorm;      // [2]
+  int* status;
+  unsigned* hist;      // [2][nd][256] top-byte counts, or null
+  int64_t timeout_ns;
+};
+
+__device__ __forceinline__ uint64_t pk_fma(uint64_t a, uint64_t b, uint64_t c) {
+  uint64_t r;
+  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(r) : "l"(a), "l"(b), "l"(c));
+  return r;
+}
+__device__ __forceinline__ float pk_sum(uint64_t v) {
+  float a, b;
+  asm("mov.b64 {%0, %1}, %2;" : "=f"(a), "=f"(b) : "l"(v));
+  return a + b;
+}
+
+template <int ND>
+__global__ void __launch_bounds__(kPtThreads + 32, 1)
+    proj_pair_tma_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
+                         const ProjPairArgs p) {
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* base = smem_align<1024>(smem_raw);
+  const int S = p.stages;
+  float* us = reinterpret_cast<float*>(base + (size_t)S * kPtStageBytes);  // [ND][Dq]
+  unsigned* hs = reinterpret_cast<unsigned*>(us + (size_t)ND * p.Dq);      // [2][ND][256]
+  uint64_t* full = reinterpret_cast<uint64_t*>(hs + 2 * ND * 256);
+  uint64_t* empty = full + kPtMaxStages;
+  volatile int* abort = reinterpret_cast<int*>(empty + kPtMaxStages);
+  const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
+
+  for (int i = t; i < ND * p.Dq; i += blockDim.x) {
+    const int d = i / p.Dq, k = i % p.Dq;
+    us[i] = (d < p.nd && k < p.D) ? (float)p.dirs[(size_t)d * p.D + k] : 0.f;
+  }
+  if (p.hist)
+    for (int i = t; i < 2 * ND * 256; i += blockDim.x) hs[i] = 0u;
+  if (t == 0) {
+    for (int s = 0; s < S; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&empty[s], kPtThreads / 32);
+    }
+    *abort = 0;
+    fence_mbar_init();
+  }
+  __syncthreads();
+
+  if (warp == kPtThreads / 32) {
+    // ---------------- TMA producer ----------------
+    if (lane == 0) {
+      tma_prefetch_desc(&tmA);
+      tma_prefetch_desc(&tmB);
+      uint32_t g = 0;  // stage uses issued
+      for (int64_t tile = blockIdx.x; tile < p.tiles && !*abort; tile += gridDim.x) {
+        const bool setB = tile >= p.tilesA;
+        const CUtensorMap* m = setB ? &tmB : &tmA;
+        const int y0 = (int)((setB ? tile - p.tilesA : tile) * kPtRows);
+        for (int c = 0; c < p.nchunks; ++c) {
+          const int s = (int)(g % (uint32_t)S);
+          if (!mbar_wait_bounded(&empty[s], ((g / (uint32_t)S) & 1u) ^ 1u, abort, (uint64_t)p.timeout_ns)) break;
+          mbar_arrive_expect_tx(&full[s], kPtStageBytes);
+          uint8_t* dst = base + (size_t)s * kPtStageBytes;
+#pragma unroll
+          for (int b = 0; b < kPtRows / kPtBox; ++b) tma_load_2d(dst + b * kPtBox * 128, m, c * 32, y0 + b * kPtBox, &full[s]);
+          ++g;
+        }
+      }
+      if (*abort) {
+        // error path: the copies already issued land before the CTA exits
+        for (uint32_t h = g >= (uint32_t)S ? g - (uint32_t)S : 0u; h < g; ++h) {
+          const uint64_t t0 = global_timer_ns();
+          while (!mbar_try_wait(&full[h % (uint32_t)S], (h / (uint32_t)S) & 1u) && global_timer_ns() - t0 < 2000000ull) {
+          }
+        }
+      }
+    }
+  } else {
+    // ---------------- consumers ----------------
+    float wmax0 = 0.f, wmax1 = 0.f;  // per set
+    bool bad0 = false, bad1 = false;
+    uint32_t g = 0;
+    for (int64_t tile = blockIdx.x; tile < p.tiles; tile += gridDim.x) {
+      const int setB = tile >= p.tilesA ? 1 : 0;
+      const int64_t r0 = (setB ? tile - p.tilesA : tile) * kPtRows;
+      uint64_t acc[kPtRpt][ND], nrm[kPtRpt];
+#pragma unroll
+      for (int j = 0; j < kPtRpt; ++j) {
+        nrm[j] = 0ull;
+#pragma unroll
+        for (int d = 0; d < ND; ++d) acc[j][d] = 0ull;
+      }
+      bool ok = true;
+      for (int c = 0; c < p.nchunks; ++c, ++g) {
+        const int s = (int)(g % (uint32_t)S);
+        ok = __all_sync(0xffffffffu, mbar_wait_bounded(&full[s], (g / (uint32_t)S) & 1u, abort, (uint64_t)p.timeout_ns));
+        if (!ok) break;
+        const float* xb = reinterpret_cast<const float*>(base + (size_t)s * kPtStageBytes);
+        const float* uc = us + c * 32;
+#pragma unroll
+        for (int f = 0; f < 8; ++f) {
+          ulonglong2 xv[kPtRpt];
+#pragma unroll
+          for (int j = 0; j < kPtRpt; ++j) {
+            const int row = t + j * kPtThreads;
+            xv[j] = *reinterpret_cast<const ulonglong2*>(xb + row * 32 + ((f ^ (row & 7)) << 2));
+            nrm[j] = pk_fma(xv[j].y, xv[j].y, pk_fma(xv[j].x, xv[j].x, nrm[j]));
+          }
+#pragma unroll
+          for (int d = 0; d < ND; ++d) {
+            const ulonglong2 u = *reinterpret_cast<const ulonglong2*>(uc + (size_t)d * p.Dq + 4 * f);
+#pragma unroll
+            for (int j = 0; j < kPtRpt; ++j) acc[j][d] = pk_fma(xv[j].y, u.y, pk_fma(xv[j].x, u.x, acc[j][d]));
+          }
+        }
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&empty[s]);
+      }
+      if (!ok) break;
+      const int64_t n = setB ? p.nB : p.nA;
+      float* q = setB ? p.qB : p.qA;
+#pragma unroll
+      for (int j = 0; j < kPtRpt; ++j) {
+        const int64_t r = r0 + t + j * kPtThreads;
+        if (r < n) {
+#pragma unroll
+          for (int d = 0; d < ND; ++d)
+            if (d < p.nd) {
+              const float v = pk_sum(acc[j][d]);
+              q[(size_t)d * n + r] = v;
+              if (p.hist) atomicAdd(&hs[(setB * ND + d) * 256 + (f32_key(v) >> 24)], 1u);
+            }
+          const float nn = pk_sum(nrm[j]);
+          if (setB) {
+            bad1 |= !isfinite(nn);
+            wmax1 = fmaxf(wmax1, sqrtf(nn));
+          } else {
+            bad0 |= !isfinite(nn);
+            wmax0 = fmaxf(wmax0, sqrtf(nn));
+          }
+        }
+      }
+    }
+    wmax0 = warp_max(wmax0);
+    wmax1 = warp_max(wmax1);
+    if (lane == 0) {
+      atomic_max_nonneg(p.maxnorm + 0, wmax0);
+      atomic_max_nonneg(p.maxnorm + 1, wmax1);
+    }
+    if (__any_sync(0xffffffffu, bad0 || bad1) && lane == 0) atomicMax(p.status, (int)PROHD_ENONFINITE);
+  }
+  __syncthreads();
+  if (p.hist)
+    for (int i = t; i < 2 * ND * 256; i += blockDim.x) {
+      const int s = i / (ND * 256), d = (i / 256) % ND;
+      if (d < p.nd && hs[i]) atomicAdd(p.hist + ((size_t)s * p.nd + d) * 256 + (i & 255), hs[i]);
+    }
+  if (t == 0 && *abort) atomicMax(p.status, (int)PROHD_ETIMEOUT);
 }
 
 // Fallback for D % 4 != 0 or unaligned bases: warp per row, lanes over dims.
@@ -1068,6 +1254,28 @@ __device__ __forceinline__ void gather_rows_body(const float* __restrict__ X, in
   const int lane = threadIdx.x & 31;
   const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
   const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  const bool vec = (D % 4) == 0 && ((reinterpret_cast<uintptr_t>(X) | reinterpret_cast<uintptr_t>(out)) & 15) == 0;
+  if (vec) {
+    // 16-byte moves, four rows' loads in flight per warp
+    const int D4 = D >> 2;
+    const float4* X4 = reinterpret_cast<const float4*>(X);
+    float4* out4 = reinterpret_cast<float4*>(out);
+    for (int64_t r0 = warp * 4; r0 < n; r0 += nw * 4) {
+      int64_t src[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) src[u] = r0 + u < n ? (int64_t)__ldg(idx + r0 + u) * D4 : -1;
+      for (int k = lane; k < D4; k += 32) {
+        float4 v[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+          if (src[u] >= 0) v[u] = __ldg(X4 + src[u] + k);
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+          if (src[u] >= 0) out4[(r0 + u) * D4 + k] = v[u];
+      }
+    }
+    return;
+  }
   for (int64_t r = warp; r < n; r += nw) {
     const float* src = X + (int64_t)__ldg(idx + r) * D;
     float* dst = out + r * D;
@@ -1212,6 +1420,64 @@ static cudaError_t launch_proj(const float* X, int64_t n, int D, const double* d
   return go(proj_kernel<32>, 32);
 }
 
+// Both sets' projections in one TMA-fed launch; returns false (nothing
+// launched) where it does not apply: D % 4 != 0, a base that is not 16-byte
+// aligned, more than 17 directions, fewer than two stages fitting in shared
+// memory, or no tensor-map encoder. More than 17 directions go to the
+// two-launch path (the per-thread accumulators would spill).
+static bool launch_proj_pair(prohd_ctx* ctx, const float* A, int64_t nA, const float* B, int64_t nB, int D,
+                             const double* dirs, int nd, float* qA, float* qB, float* maxnorm, int* status,
+                             unsigned* hist, int64_t timeout_ns, cudaStream_t st, cudaError_t* err) {
+  *err = cudaSuccess;
+  if (D % 4 != 0 || nd > 17 || ((reinterpret_cast<uintptr_t>(A) | reinterpret_cast<uintptr_t>(B)) & 15) != 0)
+    return false;
+  const int ND = nd <= 3 ? 3 : nd <= 5 ? 5 : nd <= 9 ? 9 : nd <= 13 ? 13 : 17;
+  const int Dq = (int)round_up(D, 32);
+  const size_t fixed = 1024 + (size_t)ND * Dq * 4 + (size_t)2 * ND * 256 * 4 + 2 * kPtMaxStages * 8 + 16;
+  const size_t cap = 227 * 1024;
+  if (fixed + 2 * (size_t)kPtStageBytes > cap) return false;
+  const int stages = (int)std::min<size_t>(kPtMaxStages, (cap - fixed) / kPtStageBytes);
+  CUtensorMap tA, tB;
+  if (!encode_2d(ctx, &tA, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, A, (uint64_t)D, (uint64_t)nA, (uint64_t)D * 4, 32, kPtBox,
+                 CU_TENSOR_MAP_SWIZZLE_128B) ||
+      !encode_2d(ctx, &tB, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, B, (uint64_t)D, (uint64_t)nB, (uint64_t)D * 4, 32, kPtBox,
+                 CU_TENSOR_MAP_SWIZZLE_128B))
+    return false;
+  ProjPairArgs a;
+  a.nA = nA;
+  a.nB = nB;
+  a.tilesA = ceil_div(nA, kPtRows);
+  a.tiles = a.tilesA + ceil_div(nB, kPtRows);
+  a.D = D;
+  a.Dq = Dq;
+  a.nd = nd;
+  a.nchunks = Dq / 32;
+  a.stages = stages;
+  a.dirs = dirs;
+  a.qA = qA;
+  a.qB = qB;
+  a.maxnorm = maxnorm;
+  a.status = status;
+  a.hist = hist;
+  a.timeout_ns = timeout_ns > 0 ? timeout_ns : kDefaultTimeoutNs;
+  const size_t smem = fixed + (size_t)stages * kPtStageBytes;
+  const int grid = (int)std::min<int64_t>(a.tiles, ctx->num_sms);
+  auto go = [&](auto kern) {
+    cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    count_launch();
+    kern<<<grid, kPtThreads + 32, smem, st>>>(tA, tB, a);
+    *err = cudaGetLastError();
+  };
+  switch (ND) {
+    case 3: go(proj_pair_tma_kernel<3>); break;
+    case 5: go(proj_pair_tma_kernel<5>); break;
+    case 9: go(proj_pair_tma_kernel<9>); break;
+    case 13: go(proj_pair_tma_kernel<13>); break;
+    default: go(proj_pair_tma_kernel<17>); break;
+  }
+  return true;
+}
+
 int64_t compact_blocks(int64_t n) { return ceil_div(n, kCompactItems); }
 
 cudaError_t mask_to_indices(const uint8_t* mask, int64_t n, int32_t* idx, int64_t* nsel, unsigned* counts,
@@ -1228,7 +1494,8 @@ cudaError_t mask_to_indices(const uint8_t* mask, int64_t n, int32_t* idx, int64_
 
 cudaError_t select_run(prohd_ctx* ctx, const float* A, int64_t nA, const float* B, int64_t nB, int D,
                        const double* dirs, int nd, const int64_t* kA, const int64_t* kB, int32_t* idxA,
-                       int64_t* nselA, int32_t* idxB, int64_t* nselB, int* status_dev, Arena& ws, cudaStream_t st) {
+                       int64_t* nselA, int32_t* idxB, int64_t* nselB, int* status_dev, Arena& ws, cudaStream_t st,
+                       int64_t timeout_ns) {
   SelBufs b;
   sel_layout(ws, nA, nB, D, nd, b);
   if (ws.overflow()) return cudaErrorMemoryAllocation;
@@ -1246,9 +1513,14 @@ cudaError_t select_run(prohd_ctx* ctx, const float* A, int64_t nA, const float* 
   cudaMemsetAsync(b.maskB, 0, (size_t)nB, st);
   {
     PhaseTimer pt(ctx, PROHD_PH_PROJECT, st);
-    if ((e = launch_proj(A, nA, D, dirs, nd, b.qA, b.maxnorm + 0, status_dev, nsm, st, b.hist))) return e;
-    if ((e = launch_proj(B, nB, D, dirs, nd, b.qB, b.maxnorm + 1, status_dev, nsm, st, b.hist + (size_t)nd * 256)))
-      return e;
+    if (launch_proj_pair(ctx, A, nA, B, nB, D, dirs, nd, b.qA, b.qB, b.maxnorm, status_dev, b.hist, timeout_ns, st,
+                         &e)) {
+      if (e) return e;
+    } else {
+      if ((e = launch_proj(A, nA, D, dirs, nd, b.qA, b.maxnorm + 0, status_dev, nsm, st, b.hist))) return e;
+      if ((e = launch_proj(B, nB, D, dirs, nd, b.qB, b.maxnorm + 1, status_dev, nsm, st, b.hist + (size_t)nd * 256)))
+        return e;
+    }
   }
   PhaseTimer pt_sel(ctx, PROHD_PH_SELECT, st);
   count_launch();

@@ -1,7 +1,7 @@
 """Bounded device waits: a limit that runs out is reported, and the context recovers.
 
-Every wait of the tensor-core kernels on an mbarrier is bounded by
-params.wait_timeout_ns, read from %globaltimer. When a wait runs out the
+Every wait on an mbarrier (the tensor-core kernels and the TMA-fed
+projection) is bounded by params.wait_timeout_ns, read from %globaltimer. When a wait runs out the
 kernel raises a CTA-wide abort flag, lets the copies it issued land (with a
 limit of its own), completes its issued MMAs, frees its tensor memory and
 returns; the result then carries PROHD_ETIMEOUT. A limit of 1 ns makes the
@@ -43,8 +43,8 @@ def test_contraction_timeout_is_reported_and_the_next_call_succeeds():
     kB = oracle.k_list(B.shape[0], 1 + m, alpha, alpha / m)
     idxA = torch.empty(A.shape[0], dtype=torch.int32, device="cuda")
     idxB = torch.empty(B.shape[0], dtype=torch.int32, device="cuda")
-    # selection onwards with the given directions: only the distance
-    # contraction has bounded waits
+    # selection onwards with the given directions: the projection's TMA
+    # ring and the distance contraction have bounded waits
     short = prohd.default_params(m=m, alpha_c=alpha, precision="fp16", wait_timeout_ns=1)
     out = c.prohd_estimate_dirs(At, Bt, d, kA, kB, params=short, idxA=idxA, idxB=idxB)
     torch.cuda.synchronize()
