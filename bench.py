@@ -42,9 +42,14 @@ N_POINTS = 2_000_000
 DIM = 256
 M_PCS = 8
 ALPHA = 0.01
-# DRAM bytes (read + write) per launch of gram_tc_kernel from one ncu capture
-# (None until the current kernel has been captured)
-GRAM_TRAFFIC = None
+# DRAM bytes (read + write) per full-size launch from one ncu capture of the
+# current kernel at 400k + 400k points: the reads (and the projection's key
+# writes) grow with the points (x5 to 2M + 2M); the Gram's writes (the CTA
+# pairs' partial products) do not. None: no capture of the current kernel.
+GRAM_TRAFFIC = 821.96e6 * 5 + 3.26e6
+PROJ_TRAFFIC = (819.41e6 + 26.96e6) * 5
+# the contraction's traffic per row of the two FP16 copies (100k + 100k capture)
+HD_TRAFFIC_PER_ROW = (138.28e6 + 5.13e6) / 200_000
 WORKLOAD = ("anisotropic Gaussian pair, n=m=2,000,000, D=256 (eigenvalues 1/i, random rotation); "
             "B shifted 0.1 sigma along a random unit vector with 0.1% Student-t (nu=3) points; "
             "ProHD with centroid axis + top-8 PCs, alpha=0.01 per side (alpha/8 per PC), FP16 tiles")
@@ -491,58 +496,65 @@ def gpu_arm(args):
         if cnt:
             cand[name] = (ms / cnt, cnt)
     single = {k: v for k, v in cand.items() if k in ("gram", "hd_contract", "power", "project")}
-    dom = max(single, key=lambda k: single[k][0] * (2 if k == "project" else 1)) if single else None
-    roof = None
+    dom = max(single, key=lambda k: single[k][0]) if single else None
     fp32_peak = 152 * 128 * 2 * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
-    if dom == "gram":
-        t = cand["gram"][0] / 1e3
-        # the method's work for the covariance (Algorithm 2): one read of both
-        # sets and 2 N D^2 flops for the D x D Gram of the N = 2n points; the
-        # roofline is the larger of the two bound times
-        by = 2.0 * n * DIM * 4
-        fl = 2.0 * (2 * n) * DIM * DIM
-        if DIM <= 256 and DIM % 4 == 0:
-            pk = peaks.get("bf16_tflops_sustained", peaks["bf16_tflops"])
-            t_hbm, t_tc = by / (peaks["hbm_gbs"] * 1e9), fl / (pk * 1e12)
-            # the tensor cores run two BF16 MMAs per point over the full
-            # 256 x 256 product (a two-part split, X = sum h h^T + 2 m h^T)
-            dp = 256 if DIM > 128 else 2 * ((DIM + 63) // 64) * 64
-            issued = 2.0 * 2 * 256 * dp * (2 * n) / (2 if DIM <= 128 else 1)
-            note = {"issued_tflops": issued / t / 1e12, "issued_frac_of_sustained_bf16": issued / t / 1e12 / pk,
-                    "issued_work": "2 BF16 MMAs per point over the CTA pair's 256-row product"}
-            if t_hbm >= t_tc:
-                roof = {"kernel": "gram_tc_kernel", "bound": "hbm", "achieved": by / t / 1e9,
-                        "peak": peaks["hbm_gbs"], "unit": "GB/s", "traffic": GRAM_TRAFFIC,
-                        "peak_source": f"{peak_src} copy bandwidth",
-                        "work": "one read of both sets (2 n D 4 bytes); 2 N D^2 flops take less time at the "
-                                "sustained BF16 peak", "tensor_view": {"achieved_tflops": fl / t / 1e12,
-                                                                      "peak_tflops": pk,
-                                                                      "frac": fl / t / 1e12 / pk},
-                        "split_products": note}
+    def roof_for(name):
+        roof = None
+        if name == "gram":
+            t = cand["gram"][0] / 1e3
+            # the method's work for the covariance (Algorithm 2): one read of both
+            # sets and 2 N D^2 flops for the D x D Gram of the N = 2n points; the
+            # roofline is the larger of the two bound times
+            by = 2.0 * n * DIM * 4
+            fl = 2.0 * (2 * n) * DIM * DIM
+            if DIM <= 256 and DIM % 4 == 0:
+                pk = peaks.get("bf16_tflops_sustained", peaks["bf16_tflops"])
+                t_hbm, t_tc = by / (peaks["hbm_gbs"] * 1e9), fl / (pk * 1e12)
+                # the tensor cores run two BF16 MMAs per point over the full
+                # 256 x 256 product (a two-part split, X = sum h h^T + 2 m h^T)
+                dp = 256 if DIM > 128 else 2 * ((DIM + 63) // 64) * 64
+                issued = 2.0 * 2 * 256 * dp * (2 * n) / (2 if DIM <= 128 else 1)
+                note = {"issued_tflops": issued / t / 1e12, "issued_frac_of_sustained_bf16": issued / t / 1e12 / pk,
+                        "issued_work": "2 BF16 MMAs per point over the CTA pair's 256-row product"}
+                if t_hbm >= t_tc:
+                    roof = {"kernel": "gram_tc_kernel", "bound": "hbm", "achieved": by / t / 1e9,
+                            "peak": peaks["hbm_gbs"], "unit": "GB/s", "traffic": GRAM_TRAFFIC,
+                            "peak_source": f"{peak_src} copy bandwidth",
+                            "work": "one read of both sets (2 n D 4 bytes); 2 N D^2 flops take less time at the "
+                                    "sustained BF16 peak", "tensor_view": {"achieved_tflops": fl / t / 1e12,
+                                                                          "peak_tflops": pk,
+                                                                          "frac": fl / t / 1e12 / pk},
+                            "split_products": note}
+                else:
+                    roof = {"kernel": "gram_tc_kernel", "bound": "tensor", "achieved": fl / t / 1e12, "peak": pk,
+                            "unit": "TFLOP/s", "traffic": GRAM_TRAFFIC, "peak_source": f"{peak_src} sustained BF16",
+                            "work": "2 N D^2 flops", "split_products": note}
             else:
-                roof = {"kernel": "gram_tc_kernel", "bound": "tensor", "achieved": fl / t / 1e12, "peak": pk,
-                        "unit": "TFLOP/s", "traffic": GRAM_TRAFFIC, "peak_source": f"{peak_src} sustained BF16",
-                        "work": "2 N D^2 flops", "split_products": note}
-        else:
-            roof = {"kernel": "gram_kernel", "bound": "alu", "achieved": fl / t / 1e12, "peak": fp32_peak,
-                    "unit": "TFLOP/s", "traffic": None,
-                    "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 flop x max SM clock"}
-    elif dom == "hd_contract":
-        t = cand["hd_contract"][0] / 1e3
-        fl = 2.0 * nsa * nsb * DIM
-        roof = {"kernel": "hd_tc_kernel", "bound": "tensor", "achieved": fl / t / 1e12,
-                "peak": peaks["bf16_tflops"], "unit": "TFLOP/s", "traffic": None,
-                "peak_source": f"{peak_src} bf16 burst (fp16 has the same nominal rate)"}
-    elif dom == "project":
-        t = cand["project"][0] / 2 / 1e3  # two launches (one per set) per phase
-        by = n * DIM * 4.0 + (1 + M_PCS) * n * 4.0
-        roof = {"kernel": "proj_kernel", "bound": "hbm", "achieved": by / t / 1e9, "peak": peaks["hbm_gbs"],
-                "unit": "GB/s", "traffic": None, "peak_source": f"{peak_src} copy bandwidth"}
-    elif dom == "power":
-        roof = {"kernel": "power_iter_kernel", "bound": "latency", "achieved": None, "peak": None, "unit": None,
-                "traffic": None}
-    if roof and roof.get("achieved") is not None:
-        roof["frac"] = roof["achieved"] / roof["peak"]
+                roof = {"kernel": "gram_kernel", "bound": "alu", "achieved": fl / t / 1e12, "peak": fp32_peak,
+                        "unit": "TFLOP/s", "traffic": None,
+                        "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 flop x max SM clock"}
+        elif name == "hd_contract":
+            t = cand["hd_contract"][0] / 1e3
+            fl = 2.0 * nsa * nsb * DIM
+            roof = {"kernel": "hd_tc_kernel", "bound": "tensor", "achieved": fl / t / 1e12,
+                    "peak": peaks["bf16_tflops"], "unit": "TFLOP/s", "traffic": HD_TRAFFIC_PER_ROW * (nsa + nsb),
+                    "peak_source": f"{peak_src} bf16 burst (fp16 has the same nominal rate)"}
+        elif name == "project":
+            t = cand["project"][0] / 1e3  # one launch projects both sets
+            by = 2 * (n * DIM * 4.0 + (1 + M_PCS) * n * 4.0)
+            roof = {"kernel": "proj_pair_tma_kernel", "bound": "hbm", "achieved": by / t / 1e9,
+                    "peak": peaks["hbm_gbs"], "unit": "GB/s", "traffic": PROJ_TRAFFIC,
+                    "peak_source": f"{peak_src} copy bandwidth",
+                    "work": "one read of both sets and one write of the 1 + m keys per point"}
+        elif name == "power":
+            roof = {"kernel": "subspace_kernel", "bound": "latency", "achieved": None, "peak": None, "unit": None,
+                    "traffic": None}
+        if roof and roof.get("achieved") is not None:
+            roof["frac"] = roof["achieved"] / roof["peak"]
+        return roof
+
+    roof = roof_for(dom)
+    stage_roofs = {k: roof_for(k) for k in ("gram", "project", "hd_contract") if k in cand}
 
     batched = None
     if not args.no_batched:
@@ -590,6 +602,7 @@ def gpu_arm(args):
                 "h2d_bytes_per_step": 2 * n * DIM * 4, "d2h_bytes_per_step": ctypes.sizeof(prohd.Result)},
         "gpu_launches": launches,
         "roofline": roof,
+        "stage_rooflines": stage_roofs,
         "cpu_baseline": cpu,
         "fp64_subsample_20k": subsample,
         "clocks": clk,

@@ -659,6 +659,19 @@ __global__ void __launch_bounds__(256)
 constexpr int kHist1Bins = 2048;  // bits 23..13 of the key
 constexpr int kHist1Blocks = 32;  // blocks per problem (each writes its own histogram pair)
 
+// The keys of one problem as a 16-byte aligned float4 body and scalar ends:
+// `head` keys before the first aligned one, nv float4s, then the rest.
+struct KeySpan {
+  int64_t head, nv;
+};
+__device__ __forceinline__ KeySpan key_span(const float* q, int64_t n) {
+  KeySpan k;
+  k.head = ((16 - (reinterpret_cast<uintptr_t>(q) & 15)) & 15) >> 2;
+  if (k.head > n) k.head = n;
+  k.nv = (n - k.head) >> 2;
+  return k;
+}
+
 // Second digit: histograms of bits 23..13 of the keys whose top byte is
 // each side's byte. grid (kHist1Blocks, 2*nd); out [2*nd][blocks][2][2048].
 __global__ void __launch_bounds__(512) hist1_kernel(const SelProb* __restrict__ P, unsigned* __restrict__ out) {
@@ -667,27 +680,39 @@ __global__ void __launch_bounds__(512) hist1_kernel(const SelProb* __restrict__ 
   for (int i = threadIdx.x; i < 2 * kHist1Bins; i += blockDim.x) (&h[0][0])[i] = 0u;
   __syncthreads();
   const int64_t n = S.n;
-  const int64_t c0 = n * blockIdx.x / gridDim.x, c1 = n * (blockIdx.x + 1) / gridDim.x;
   const uint32_t b0 = S.prefix[0] >> 24, b1 = S.prefix[1] >> 24;
   const float* q = S.q;
-  // eight independent loads in flight per thread
+  auto count = [&](float v) {
+    const uint32_t k = f32_key(v);
+    const uint32_t top = k >> 24, dig = (k >> 13) & (kHist1Bins - 1);
+    if (top == b0) atomicAdd(&h[0][dig], 1u);
+    if (top == b1) atomicAdd(&h[1][dig], 1u);
+  };
+  const KeySpan ks = key_span(q, n);
+  const float4* q4 = reinterpret_cast<const float4*>(q + ks.head);
+  const int64_t c0 = ks.nv * blockIdx.x / gridDim.x, c1 = ks.nv * (blockIdx.x + 1) / gridDim.x;
+  // eight independent 16-byte loads in flight per thread
   for (int64_t base = c0; base < c1; base += 8 * (int64_t)blockDim.x) {
-    float v[8];
+    float4 v[8];
 #pragma unroll
     for (int u = 0; u < 8; ++u) {
       const int64_t i = base + u * (int64_t)blockDim.x + threadIdx.x;
-      v[u] = i < c1 ? __ldg(q + i) : 0.f;
+      v[u] = i < c1 ? __ldg(q4 + i) : make_float4(0.f, 0.f, 0.f, 0.f);
     }
 #pragma unroll
     for (int u = 0; u < 8; ++u) {
       const int64_t i = base + u * (int64_t)blockDim.x + threadIdx.x;
       if (i >= c1) continue;
-      const uint32_t k = f32_key(v[u]);
-      const uint32_t top = k >> 24, dig = (k >> 13) & (kHist1Bins - 1);
-      if (top == b0) atomicAdd(&h[0][dig], 1u);
-      if (top == b1) atomicAdd(&h[1][dig], 1u);
+      count(v[u].x);
+      count(v[u].y);
+      count(v[u].z);
+      count(v[u].w);
     }
   }
+  if (blockIdx.x == 0)
+    for (int64_t i = threadIdx.x; i < ks.head; i += blockDim.x) count(__ldg(q + i));
+  if (blockIdx.x == gridDim.x - 1)
+    for (int64_t i = ks.head + 4 * ks.nv + threadIdx.x; i < n; i += blockDim.x) count(__ldg(q + i));
   __syncthreads();
   unsigned* o = out + ((size_t)blockIdx.y * gridDim.x + blockIdx.x) * 2 * kHist1Bins;
   for (int i = threadIdx.x; i < 2 * kHist1Bins; i += blockDim.x) o[i] = (&h[0][0])[i];
@@ -735,7 +760,8 @@ __global__ void __launch_bounds__(256) pick1_kernel(SelProb* __restrict__ P, con
 // One pass over the keys of every problem: certain members are marked and
 // counted, candidates listed per side as (index, key) in the band buffers
 // (side 1 stores the reversed key, so both sides look for a smallest key).
-// grid (chunks, 2*nd).
+// grid (chunks, 2*nd). The keys are read as float4s (and the few keys before
+// the first 16-byte boundary and after the last one as scalars).
 __global__ void extract_kernel(SelProb* __restrict__ P) {
   SelProb& S = P[blockIdx.y];
   const int64_t n = S.n;
@@ -748,58 +774,82 @@ __global__ void extract_kernel(SelProb* __restrict__ P) {
   uint64_t* k1 = S.bkey[1];
   const int lane = threadIdx.x & 31;
   unsigned long long in0c = 0, in1c = 0;
+  // classify one key; returns the candidate bits (1: side 0, 2: side 1)
+  auto classify = [&](float v, int64_t i) -> unsigned {
+    const bool in0 = v < t0, in1 = v > t1;
+    if (in0 || in1) mask[i] = 1;
+    in0c += in0;
+    in1c += in1;
+    return ((!in0 && v <= c0) ? 1u : 0u) | ((!in1 && v >= c1) ? 2u : 0u);
+  };
+  // append the warp's candidates of one slot (every lane of the warp calls it)
+  auto append = [&](unsigned cd, float v, int64_t i) {
+    const unsigned m0 = __ballot_sync(0xffffffffu, cd & 1u), m1 = __ballot_sync(0xffffffffu, cd & 2u);
+    if (!(m0 | m1)) return;
+    unsigned long long base0 = 0, base1 = 0;
+    if (lane == 0 && m0)
+      base0 = atomicAdd(reinterpret_cast<unsigned long long*>(&S.nband[0]), (unsigned long long)__popc(m0));
+    if (lane == 0 && m1)
+      base1 = atomicAdd(reinterpret_cast<unsigned long long*>(&S.nband[1]), (unsigned long long)__popc(m1));
+    base0 = __shfl_sync(0xffffffffu, base0, 0);
+    base1 = __shfl_sync(0xffffffffu, base1, 0);
+    const unsigned below = (1u << lane) - 1;
+    const uint32_t key = f32_key(v);
+    if (cd & 1u) {
+      const unsigned long long o = base0 + __popc(m0 & below);
+      b0[o] = (int32_t)i;
+      k0[o] = key;
+    }
+    if (cd & 2u) {
+      const unsigned long long o = base1 + __popc(m1 & below);
+      b1[o] = (int32_t)i;
+      k1[o] = ~key;
+    }
+  };
+  const KeySpan ks = key_span(q, n);
+  const float4* q4 = reinterpret_cast<const float4*>(q + ks.head);
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  const int64_t end = (n + 31) / 32 * 32;
-  for (int64_t base = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; base < end; base += 8 * stride) {
-    // eight independent loads in flight, classified before any warp-wide step
-    float vv[8];
-    unsigned cand = 0;  // bit u: a candidate for side 0 (bit u) or side 1 (bit 8 + u)
+  const int64_t end = (ks.nv + 31) / 32 * 32;  // whole warps step together
+  for (int64_t base = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; base < end; base += 4 * stride) {
+    // four independent 16-byte loads in flight, classified before any warp-wide step
+    float4 vv[4];
+    uint32_t cand = 0;  // 2 bits per key: slot u, component e at bit 2 (4u + e)
 #pragma unroll
-    for (int u = 0; u < 8; ++u) {
-      const int64_t i = base + u * stride;
-      vv[u] = i < n ? __ldg(q + i) : 0.f;
+    for (int u = 0; u < 4; ++u) {
+      const int64_t j = base + u * stride;
+      vv[u] = j < ks.nv ? __ldg(q4 + j) : make_float4(0.f, 0.f, 0.f, 0.f);
     }
 #pragma unroll
-    for (int u = 0; u < 8; ++u) {
-      const int64_t i = base + u * stride;
-      if (i >= n) continue;
-      const float v = vv[u];
-      const bool in0 = v < t0, in1 = v > t1;
-      if (in0 || in1) mask[i] = 1;
-      in0c += in0;
-      in1c += in1;
-      cand |= ((!in0 && v <= c0) ? 1u : 0u) << u;
-      cand |= ((!in1 && v >= c1) ? 1u : 0u) << (8 + u);
+    for (int u = 0; u < 4; ++u) {
+      const int64_t j = base + u * stride;
+      if (j >= ks.nv) continue;
+      const int64_t i = ks.head + 4 * j;
+      cand |= classify(vv[u].x, i) << (2 * (4 * u + 0));
+      cand |= classify(vv[u].y, i + 1) << (2 * (4 * u + 1));
+      cand |= classify(vv[u].z, i + 2) << (2 * (4 * u + 2));
+      cand |= classify(vv[u].w, i + 3) << (2 * (4 * u + 3));
     }
     // candidates are rare: the append path runs only where a lane has one
     if (!__any_sync(0xffffffffu, cand != 0)) continue;
 #pragma unroll
-    for (int u = 0; u < 8; ++u) {
-      const int64_t i = base + u * stride;
-      if (i - lane >= end) break;  // the whole warp is past the end
-      const bool cd0 = (cand >> u) & 1u, cd1 = (cand >> (8 + u)) & 1u;
-      const unsigned m0 = __ballot_sync(0xffffffffu, cd0), m1 = __ballot_sync(0xffffffffu, cd1);
-      if (!(m0 | m1)) continue;
-      unsigned long long base0 = 0, base1 = 0;
-      if (lane == 0 && m0)
-        base0 = atomicAdd(reinterpret_cast<unsigned long long*>(&S.nband[0]), (unsigned long long)__popc(m0));
-      if (lane == 0 && m1)
-        base1 = atomicAdd(reinterpret_cast<unsigned long long*>(&S.nband[1]), (unsigned long long)__popc(m1));
-      base0 = __shfl_sync(0xffffffffu, base0, 0);
-      base1 = __shfl_sync(0xffffffffu, base1, 0);
-      const unsigned below = (1u << lane) - 1;
-      const uint32_t key = f32_key(vv[u]);
-      if (cd0) {
-        const unsigned long long o = base0 + __popc(m0 & below);
-        b0[o] = (int32_t)i;
-        k0[o] = key;
-      }
-      if (cd1) {
-        const unsigned long long o = base1 + __popc(m1 & below);
-        b1[o] = (int32_t)i;
-        k1[o] = ~key;
-      }
+    for (int u = 0; u < 4; ++u) {
+      const int64_t j = base + u * stride;
+      if (j - lane >= end) break;  // the whole warp is past the end
+      const int64_t i = ks.head + 4 * j;
+      append((cand >> (2 * (4 * u + 0))) & 3u, vv[u].x, i);
+      append((cand >> (2 * (4 * u + 1))) & 3u, vv[u].y, i + 1);
+      append((cand >> (2 * (4 * u + 2))) & 3u, vv[u].z, i + 2);
+      append((cand >> (2 * (4 * u + 3))) & 3u, vv[u].w, i + 3);
     }
+  }
+  // the scalar ends (at most 3 keys each), by the first warp of block 0
+  if (blockIdx.x == 0 && threadIdx.x < 32) {
+    const int64_t tail0 = ks.head + 4 * ks.nv;
+    const int64_t i = lane < ks.head ? lane : tail0 + (lane - 4);
+    const bool mine = lane < ks.head || (lane >= 4 && lane < 8 && i < n);
+    const float v = mine ? __ldg(q + i) : 0.f;
+    const unsigned cd = mine ? classify(v, i) : 0u;
+    append(cd, v, i);
   }
   in0c = warp_sum(in0c);
   in1c = warp_sum(in1c);
