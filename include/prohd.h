@@ -205,6 +205,23 @@ prohd_status hausdorff_exact_pruned(prohd_ctx* ctx, const float* A, int64_t nA, 
  * plain path, whose fixed costs are lower: measured, the plain path is faster
  * at 1.9e9 pairs and the pruned one at 7.5e9. */
 prohd_status prohd_set_prune_min_pairs(prohd_ctx* ctx, double min_pairs);
+/* Pair threshold of the estimate's pruned subset distance (default 1e9;
+ * >= 0, else PROHD_EINVAL; 0 prunes whenever the subsets allow). The subset
+ * HD of prohd_estimate (and of prohd_estimate_dirs / _adaptive / _host) is
+ * Eq. 1 on A_sel and B_sel, computed exactly either way. With FP16/BF16 tiles,
+ * D <= 256 and both subset bounds (2 sum_d k_d per set) of at least 8,192
+ * rows, and their product at least this threshold, it leaves out the subset
+ * rows that cannot attain either directed maximum: every row of one subset is
+ * contracted against the first 2,048 rows of the other (an upper bound of its
+ * NN distance), the first 2,048 rows of each against the whole other subset
+ * (lower bounds of h by the intervals' lower ends), then 1,024 evenly spread
+ * rows among those whose upper bound reaches that bound (a larger lower
+ * bound), and only the rows whose upper bound reaches the larger bound (and
+ * row 0) run the full contraction, with the same intervals, candidates and
+ * FP32 rescoring. The
+ * result is the plain contraction's in every field (H, both directed
+ * distances, witnesses, H_lowp, rescored counts). */
+prohd_status prohd_set_subset_prune_min_pairs(prohd_ctx* ctx, double min_pairs);
 
 /*
  * Projection directions (Algorithm 1 step 2 and Algorithm 2 step 2):

@@ -385,6 +385,7 @@ struct EstLayout {
   size_t mark_dir, mark_sel, mark_hd;  // arena offsets where each phase's scratch starts
   // one-sided refinement: full-set sizes on the device and the two directed results
   bool refine = false, refine_pruned = false;
+  bool prune_sub = false;  // the subset distance may take the pruned form
   int64_t *nA_full = nullptr, *nB_full = nullptr;
   prohd_hd_result *r1 = nullptr, *r2 = nullptr;
   PruneLayout P;  // the refinement's row pruning (tensor-core precisions)
@@ -436,7 +437,8 @@ void est_layout_k(Arena& a, int64_t nA, int64_t nB, int D, int nd, const int64_t
   select_layout(t, nA, nB, D, L.nd);
   end = std::max(end, t.off);
   t = a;
-  hd_core_layout(t, L.boundA, L.boundB, D, precision);
+  hd_core_pruned_layout(t, L.boundA, L.boundB, D, precision);
+  L.prune_sub = hd_subset_prunable(L.boundA, L.boundB, D, precision);
   end = std::max(end, t.off);
   if (refine && !L.refine_pruned) {
     // h(A_sel, B) then h(B_sel, A): one after the other in the same region
@@ -747,8 +749,14 @@ static prohd_status estimate_run(prohd_ctx* ctx, const float* A, int64_t nA, con
   if (!e) {
     Arena t = phase(L.mark_hd);
     const int64_t to = p->wait_timeout_ns > 0 ? p->wait_timeout_ns : kDefaultTimeoutNs;
-    e = hd_core(ctx, L.As, L.nselA, L.boundA, L.Bs, L.nselB, L.boundB, D, p->precision, L.idxA, L.idxB, &out->hd,
-                L.status, t, to, st);
+    // the same result; the pruned form leaves out the subset rows that
+    // cannot attain either directed maximum
+    if (L.prune_sub && (double)L.boundA * (double)L.boundB >= ctx->subset_prune_min_pairs)
+      e = hd_core_pruned(ctx, L.As, L.nselA, L.boundA, L.Bs, L.nselB, L.boundB, D, p->precision, L.idxA, L.idxB,
+                         &out->hd, L.status, t, to, st);
+    else
+      e = hd_core(ctx, L.As, L.nselA, L.boundA, L.Bs, L.nselB, L.boundB, D, p->precision, L.idxA, L.idxB, &out->hd,
+                  L.status, t, to, st);
   }
   if (!e && L.refine) e = refine_run(ctx, A, nA, B, nB, D, p, L, out, wsb, ws_bytes, st);
   if (!e) {
@@ -965,6 +973,13 @@ prohd_status prohd_set_prune_min_pairs(prohd_ctx* ctx, double min_pairs) {
   if (!ctx) return PROHD_EINVAL;
   if (!(min_pairs >= 0.0)) return fail(ctx, PROHD_EINVAL, "min_pairs must be >= 0%s");
   ctx->prune_min_pairs = min_pairs;
+  return PROHD_OK;
+}
+
+prohd_status prohd_set_subset_prune_min_pairs(prohd_ctx* ctx, double min_pairs) {
+  if (!ctx) return PROHD_EINVAL;
+  if (!(min_pairs >= 0.0)) return fail(ctx, PROHD_EINVAL, "min_pairs must be >= 0%s");
+  ctx->subset_prune_min_pairs = min_pairs;
   return PROHD_OK;
 }
 

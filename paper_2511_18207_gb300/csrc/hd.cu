@@ -1356,19 +1356,13 @@ cudaError_t hd_shared_prepare(prohd_ctx* ctx, const float* X, const int64_t* nX_
   return cudaGetLastError();
 }
 
-// Rounded copies, norms and margins of A and B, then the tensor-core
-// contraction into b.rowmin / b.colmin (squared low-precision minima, scaled
-// units). c1 receives the margin constant of row_interval.
-static cudaError_t tc_prep_contract(prohd_ctx* ctx, const float* A, const int64_t* nA_dev, const float* B,
-                                    const int64_t* nB_dev, int D, int precision, HdBufs& b, int* status_dev,
-                                    int64_t timeout_ns, cudaStream_t st, double& c1, bool few_rows = false,
-                                    const HdShared* shared = nullptr) {
-  if (!tc_supported_dim(D)) return cudaErrorInvalidValue;
+// Rounded copies, norms and margins of A and B (one shift and scale for both,
+// or B's from a shared preparation).
+static cudaError_t tc_prep(prohd_ctx* ctx, const float* A, const int64_t* nA_dev, const float* B,
+                           const int64_t* nB_dev, int D, int precision, HdBufs& b, int* status_dev, cudaStream_t st,
+                           const HdShared* shared) {
   const int nsm = ctx->num_sms;
-  cudaError_t e;
   const int bf16 = precision == PROHD_BF16 ? 1 : 0;
-  const int KB = b.Dp / kTcBK;
-
   PhaseTimer pt_prep(ctx, PROHD_PH_HD_PREP, st);
   cudaMemsetAsync(b.sc, 0, sizeof(HdScalars), st);
   if (shared) {
@@ -1393,7 +1387,8 @@ static cudaError_t tc_prep_contract(prohd_ctx* ctx, const float* A, const int64_
                                                 (__half*)b.At, b.nA2, b.epsA, &b.sc->maxnormA, &b.sc->maxepsA,
                                                 b.nA8, 0);
     }
-  } else {
+    return cudaGetLastError();
+  }
   count_launch();
   hd_colsum_kernel<<<dim3((D + 31) / 32, 8, 2), 256, 0, st>>>(A, nA_dev, B, nB_dev, D, b.spart);
   count_launch();
@@ -1421,51 +1416,87 @@ static cudaError_t tc_prep_contract(prohd_ctx* ctx, const float* A, const int64_
                                               (__half*)b.Bt, b.nB2, b.epsB, &b.sc->maxnormB, &b.sc->maxepsB,
                                               b.nB8, 1);
   }
-  }  // own preparation of both sets
-  count_launch();
-  fill_u32_kernel<<<nsm * 2, 256, 0, st>>>(b.colmin, b.nB_pad, 0x7f800000u);
-  count_launch();
-  fill_u32_kernel<<<nsm, 256, 0, st>>>(reinterpret_cast<unsigned*>(b.rowmin), b.nA_pad, 0x7f800000u);
-  if ((e = cudaGetLastError())) return e;
+  return cudaGetLastError();
+}
 
-  CUtensorMap tmA, tmB;
-  const CUtensorMapDataType dt = bf16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT16;
-  CUtensorMap tmNA, tmNB;  // TF32 norm operands: rows of 8 values (32 bytes), 32-byte swizzle
-  if (!encode_2d(ctx, &tmA, dt, b.At, (uint64_t)b.Dp, (uint64_t)b.nA_pad, (uint64_t)b.Dp * 2, kTcBK, kTcBM,
-                 CU_TENSOR_MAP_SWIZZLE_128B) ||
-      !encode_2d(ctx, &tmB, dt, b.Bt, (uint64_t)b.Dp, (uint64_t)b.nB_pad, (uint64_t)b.Dp * 2, kTcBK, kTcBN,
-                 CU_TENSOR_MAP_SWIZZLE_128B) ||
-      !encode_2d(ctx, &tmNA, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, b.nA8, 8, (uint64_t)b.nA_pad, 32, 8, kTcBM,
-                 CU_TENSOR_MAP_SWIZZLE_32B) ||
-      !encode_2d(ctx, &tmNB, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, b.nB8, 8, (uint64_t)b.nB_pad, 32, 8, kTcBN,
-                 CU_TENSOR_MAP_SWIZZLE_32B))
-    return cudaErrorInvalidValue;
-  pt_prep.stop();
+// The four tensor maps of a contraction: rounded copies (K-major, 128-byte
+// swizzle) and the TF32 norm operands (rows of 8 values, 32-byte swizzle).
+struct TcMaps {
+  CUtensorMap A, B, NA, NB;
+};
+static bool tc_maps(prohd_ctx* ctx, int precision, const void* At, int64_t nA_pad, const float* nA8, const void* Bt,
+                    int64_t nB_pad, const float* nB8, int Dp, TcMaps& m) {
+  const CUtensorMapDataType dt =
+      precision == PROHD_BF16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT16;
+  return encode_2d(ctx, &m.A, dt, At, (uint64_t)Dp, (uint64_t)nA_pad, (uint64_t)Dp * 2, kTcBK, kTcBM,
+                   CU_TENSOR_MAP_SWIZZLE_128B) &&
+         encode_2d(ctx, &m.B, dt, Bt, (uint64_t)Dp, (uint64_t)nB_pad, (uint64_t)Dp * 2, kTcBK, kTcBN,
+                   CU_TENSOR_MAP_SWIZZLE_128B) &&
+         encode_2d(ctx, &m.NA, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, nA8, 8, (uint64_t)nA_pad, 32, 8, kTcBM,
+                   CU_TENSOR_MAP_SWIZZLE_32B) &&
+         encode_2d(ctx, &m.NB, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, nB8, 8, (uint64_t)nB_pad, 32, 8, kTcBN,
+                   CU_TENSOR_MAP_SWIZZLE_32B);
+}
+
+// One contraction of the rows [0, *nA_dev) of m.A against the rows
+// [0, *nB_dev) of m.B into rowmin / colmin (both must hold +inf where the
+// kernel combines with atomicMin: colmin always, rowmin when seg).
+static cudaError_t tc_contract(prohd_ctx* ctx, const TcMaps& m, const int64_t* nA_dev, const int64_t* nB_dev, int Dp,
+                               int precision, bool seg, float* rowmin, unsigned* colmin, int* status_dev,
+                               int64_t timeout_ns, cudaStream_t st) {
+  const int nsm = ctx->num_sms;
+  const int KB = Dp / kTcBK;
   const size_t smem = tc_smem_bytes(KB);
-  // few row blocks (by the bound, or as the caller expects from a device
-  // count): one CTA per SM with the columns cut into segments
-  const bool seg = few_rows || b.nA_pad / kTcBM < 2 * (int64_t)nsm;
-  const int grid = seg ? nsm : (int)std::min<int64_t>(nsm, b.nA_pad / kTcBM);
-  PhaseTimer pt_tc(ctx, PROHD_PH_HD_CONTRACT, st);
+  const int grid = nsm;
   auto go = [&](auto kern) {
     cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     count_launch();
-    kern<<<grid, kTcThreads, smem, st>>>(tmA, tmB, tmNA, tmNB, nA_dev, nB_dev, KB, b.rowmin, b.colmin, status_dev,
+    kern<<<grid, kTcThreads, smem, st>>>(m.A, m.B, m.NA, m.NB, nA_dev, nB_dev, KB, rowmin, colmin, status_dev,
                                          (uint64_t)timeout_ns);
   };
-  if (bf16) {
+  if (precision == PROHD_BF16) {
     if (seg) go(hd_tc_kernel<1, true>);
     else go(hd_tc_kernel<1, false>);
   } else {
     if (seg) go(hd_tc_kernel<0, true>);
     else go(hd_tc_kernel<0, false>);
   }
-  if ((e = cudaGetLastError())) return e;
+  return cudaGetLastError();
+}
 
-  pt_tc.stop();
-  // the norms enter the accumulator through a TF32 MMA of six positive
-  // exact parts (up to eight roundings of |d2|), hence 32 rather than 16
-  c1 = (2.0 * b.Dp + 2.0 * D + 32.0) * 5.9604644775390625e-8;
+// the margin constant of row_interval: the norms enter the accumulator
+// through a TF32 MMA of six positive exact parts (up to eight roundings of
+// |d2|), hence 32 rather than 16
+static double tc_c1(int Dp, int D) { return (2.0 * Dp + 2.0 * D + 32.0) * 5.9604644775390625e-8; }
+
+// Rounded copies, norms and margins of A and B, then the tensor-core
+// contraction into b.rowmin / b.colmin (squared low-precision minima, scaled
+// units). c1 receives the margin constant of row_interval.
+static cudaError_t tc_prep_contract(prohd_ctx* ctx, const float* A, const int64_t* nA_dev, const float* B,
+                                    const int64_t* nB_dev, int D, int precision, HdBufs& b, int* status_dev,
+                                    int64_t timeout_ns, cudaStream_t st, double& c1, bool few_rows = false,
+                                    const HdShared* shared = nullptr) {
+  if (!tc_supported_dim(D)) return cudaErrorInvalidValue;
+  const int nsm = ctx->num_sms;
+  cudaError_t e = tc_prep(ctx, A, nA_dev, B, nB_dev, D, precision, b, status_dev, st, shared);
+  if (e) return e;
+  count_launch();
+  fill_u32_kernel<<<nsm * 2, 256, 0, st>>>(b.colmin, b.nB_pad, 0x7f800000u);
+  count_launch();
+  fill_u32_kernel<<<nsm, 256, 0, st>>>(reinterpret_cast<unsigned*>(b.rowmin), b.nA_pad, 0x7f800000u);
+  if ((e = cudaGetLastError())) return e;
+  TcMaps m;
+  if (!tc_maps(ctx, precision, b.At, b.nA_pad, b.nA8, b.Bt, b.nB_pad, b.nB8, b.Dp, m)) return cudaErrorInvalidValue;
+  // few row blocks (by the bound, or as the caller expects from a device
+  // count): one CTA per SM with the columns cut into segments
+  const bool seg = few_rows || b.nA_pad / kTcBM < 2 * (int64_t)nsm;
+  {
+    PhaseTimer pt_tc(ctx, PROHD_PH_HD_CONTRACT, st);
+    if ((e = tc_contract(ctx, m, nA_dev, nB_dev, b.Dp, precision, seg, b.rowmin, b.colmin, status_dev, timeout_ns,
+                         st)))
+      return e;
+  }
+  c1 = tc_c1(b.Dp, D);
   return cudaSuccess;
 }
 
@@ -1513,6 +1544,356 @@ cudaError_t hd_core(prohd_ctx* ctx, const float* A, const int64_t* nA_dev, int64
   // rescore candidate rows of A against all of B, candidate rows of B against all of A:
   // short lists by rescore_few_kernel, longer ones by the tiled kernel (each
   // kernel leaves the other's case alone, the list length being on the device)
+  {
+    const size_t fsm = (size_t)kFewRows * 256 * sizeof(float) + (size_t)8 * kFewRows * sizeof(unsigned long long);
+    cudaFuncSetAttribute(rescore_few_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fsm);
+    count_launch();
+    rescore_few_kernel<<<nsm * 2, 256, fsm, st>>>(A, b.candA, &b.sc->ncandA, B, nB_dev, D, b.bestA);
+    count_launch();
+    rescore_few_kernel<<<nsm * 2, 256, fsm, st>>>(B, b.candB, &b.sc->ncandB, A, nA_dev, D, b.bestB);
+  }
+  if ((e = launch_simt(true, true, false, A, b.candA, &b.sc->ncandA, B, nB_dev, D, b.bestA, nullptr, nsm, st))) return e;
+  if ((e = launch_simt(true, true, false, B, b.candB, &b.sc->ncandB, A, nA_dev, D, b.bestB, nullptr, nsm, st))) return e;
+  count_launch();
+  hd_finalize_kernel<<<1, 1024, 0, st>>>(A, nA_dev, B, nB_dev, D, b.bestA, b.candA, &b.sc->ncandA, b.bestB, b.candB,
+                                         &b.sc->ncandB, mapA, mapB, b.sc, status_dev, out);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------- subset distance with row pruning
+
+// H(A, B) of two row sets by the same intervals, candidates and FP32
+// rescoring as hd_core, with the rows that cannot attain either directed
+// maximum left out of the full contractions. With the rounded copies made
+// once (one shift and scale):
+//  1. all rows of A against B's first P rows: row i's minimum over them gives
+//     hiA[i], an upper bound of its NN distance over B (a minimum over fewer
+//     columns is larger); the P columns' minima run over all of A, so their
+//     intervals' lower ends bound h(B, A) from below: LB_B.
+//  2. A's first P rows against all of B: LB_A from those rows likewise, and
+//     hiB[j] for every row of B.
+//  3. the rows of A with hiA >= LB_A (the hard rows) are where the maximum
+//     lies: kSubSample of them, evenly spread, against all of B give a
+//     larger lower bound (the largest lower end among them), and likewise
+//     for B. Keep the rows of A whose hiA reaches the larger of the two
+//     bounds, and the rows of B likewise (and row 0 of each, so that no list
+//     is empty); copy the kept rows' rounded copies, norms and margins into
+//     compact buffers.
+//  4. the kept rows of A against all of B (row minima), all of A against the
+//     kept rows of B (column minima): the full intervals of the kept rows.
+//  5. bounds, candidates, rescoring and the witnesses as in hd_core, the
+//     candidates mapped back to row numbers of A and B.
+// The result equals hd_core's: every lower bound used is a row's own lower
+// end, so at most hd_core's largest lower bound LB; the row attaining LB has
+// an upper end >= LB over all columns, so over the prefix too, and is kept,
+// and the kept rows give the same LB; a row hd_core flags has an upper end
+// >= LB and is kept; the largest low-precision minimum is a kept row's for
+// the same reason. The kept rows thus give the same candidate lists,
+// rescored the same way.
+constexpr int64_t kSubPrefix = 2048;  // rows of each set in the pruning passes
+constexpr int64_t kSubSample = 1024;  // hard rows per set for the second lower bound
+
+struct HdPruneBufs {
+  int64_t *nAp = nullptr, *nBp = nullptr, *nkA = nullptr, *nkB = nullptr, *nsA = nullptr, *nsB = nullptr;
+  int32_t *sA = nullptr, *sB = nullptr;  // sampled hard rows
+  double* lb = nullptr;  // [2]: LB_A, LB_B
+  float *hiA = nullptr, *hiB = nullptr;
+  uint8_t *maskA = nullptr, *maskB = nullptr;
+  int32_t *kA = nullptr, *kB = nullptr;
+  unsigned* counts = nullptr;
+  int64_t* offsets = nullptr;
+  void *AtK = nullptr, *BtK = nullptr;
+  float *nA2K = nullptr, *epsAK = nullptr, *nA8K = nullptr;
+  float *nB2K = nullptr, *epsBK = nullptr, *nB8K = nullptr;
+  float* rowx = nullptr;     // row minima of the pass against B's kept rows (not used)
+  unsigned* colK = nullptr;  // column minima of B's kept rows over all of A
+};
+
+static void prune_sub_layout(Arena& ws, int64_t nA_max, int64_t nB_max, const HdBufs& b, HdPruneBufs& q) {
+  q.nAp = ws.take<int64_t>(1);
+  q.nBp = ws.take<int64_t>(1);
+  q.nkA = ws.take<int64_t>(1);
+  q.nkB = ws.take<int64_t>(1);
+  q.nsA = ws.take<int64_t>(1);
+  q.nsB = ws.take<int64_t>(1);
+  q.sA = ws.take<int32_t>((size_t)kSubSample);
+  q.sB = ws.take<int32_t>((size_t)kSubSample);
+  q.lb = ws.take<double>(2);
+  q.hiA = ws.take<float>((size_t)nA_max);
+  q.hiB = ws.take<float>((size_t)nB_max);
+  q.maskA = ws.take<uint8_t>((size_t)nA_max);
+  q.maskB = ws.take<uint8_t>((size_t)nB_max);
+  q.kA = ws.take<int32_t>((size_t)nA_max);
+  q.kB = ws.take<int32_t>((size_t)nB_max);
+  const int64_t nblk = compact_blocks(std::max(nA_max, nB_max));
+  q.counts = ws.take<unsigned>((size_t)nblk);
+  q.offsets = ws.take<int64_t>((size_t)nblk);
+  q.AtK = ws.take<uint16_t>((size_t)b.nA_pad * b.Dp, 1024);
+  q.BtK = ws.take<uint16_t>((size_t)b.nB_pad * b.Dp, 1024);
+  q.nA2K = ws.take<float>((size_t)b.nA_pad);
+  q.epsAK = ws.take<float>((size_t)b.nA_pad);
+  q.nA8K = ws.take<float>((size_t)b.nA_pad * 8, 1024);
+  q.nB2K = ws.take<float>((size_t)b.nB_pad);
+  q.epsBK = ws.take<float>((size_t)b.nB_pad);
+  q.nB8K = ws.take<float>((size_t)b.nB_pad * 8, 1024);
+  q.rowx = ws.take<float>((size_t)b.nA_pad);
+  q.colK = ws.take<unsigned>((size_t)b.nB_pad);
+}
+
+bool hd_subset_prunable(int64_t nA_max, int64_t nB_max, int D, int precision) {
+  return precision != PROHD_FP32 && tc_supported_dim(D) && nA_max >= 4 * kSubPrefix && nB_max >= 4 * kSubPrefix;
+}
+
+void hd_core_pruned_layout(Arena& ws, int64_t nA_max, int64_t nB_max, int D, int precision) {
+  HdBufs b;
+  layout(ws, nA_max, nB_max, D, precision, b);
+  if (hd_subset_prunable(nA_max, nB_max, D, precision)) {
+    HdPruneBufs q;
+    prune_sub_layout(ws, nA_max, nB_max, b, q);
+  }
+}
+
+__global__ void prune_sub_init_kernel(const int64_t* __restrict__ nA, const int64_t* __restrict__ nB, int64_t P,
+                                      int64_t* __restrict__ nAp, int64_t* __restrict__ nBp, double* __restrict__ lb) {
+  *nAp = *nA < P ? *nA : P;
+  *nBp = *nB < P ? *nB : P;
+  lb[0] = 0.0;
+  lb[1] = 0.0;
+}
+
+// After a pass of rows [0, nr) against a prefix of the columns, or of a
+// prefix of the rows against all columns: hi[] of the side that saw a prefix,
+// and the largest lower end of the side that saw everything (over its first
+// nlb entries) into *lb. rows: which side saw the prefix (1: the rows).
+__global__ void prune_sub_pass_kernel(const float* __restrict__ rowmin, const float* __restrict__ nA2,
+                                      const float* __restrict__ epsA, const int64_t* __restrict__ nrow_dev,
+                                      const unsigned* __restrict__ colmin, const float* __restrict__ nB2,
+                                      const float* __restrict__ epsB, const int64_t* __restrict__ ncol_dev,
+                                      const HdScalars* __restrict__ sc, double c1, int rows_saw_prefix,
+                                      float* __restrict__ hi_out, double* __restrict__ lb) {
+  const int64_t nr = *nrow_dev, nc = *ncol_dev;
+  const double inv = ldexp(1.0, -scale_exponent(sc->maxabs));
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  double best = 0.0;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < nr; i += stride) {
+    double lo, hi;
+    row_interval(rowmin[i], nA2[i], sc->maxnormB, epsA[i], sc->maxepsB, c1, inv, lo, hi);
+    if (rows_saw_prefix) hi_out[i] = __double2float_ru(hi);
+    else best = fmax(best, lo);
+  }
+  for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < nc; j += stride) {
+    double lo, hi;
+    row_interval(__uint_as_float(colmin[j]), nB2[j], sc->maxnormA, epsB[j], sc->maxepsA, c1, inv, lo, hi);
+    if (rows_saw_prefix) best = fmax(best, lo);
+    else hi_out[j] = __double2float_ru(hi);
+  }
+  for (int o = 16; o > 0; o >>= 1) best = fmax(best, __shfl_xor_sync(0xffffffffu, best, o));
+  if ((threadIdx.x & 31) == 0) atomic_max_nonneg(lb, best);
+}
+
+// keep[i] for i < n_max: row i < n whose upper end reaches lb, and row 0
+__global__ void prune_sub_keep_kernel(const float* __restrict__ hi, const int64_t* __restrict__ n_dev, int64_t n_max,
+                                      const double* __restrict__ lb, uint8_t* __restrict__ keep) {
+  const int64_t n = *n_dev;
+  const double L = *lb;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n_max; i += stride)
+    keep[i] = (i < n && (i == 0 || (double)hi[i] >= L)) ? 1 : 0;
+}
+
+// Rounded copies, norms, margins and norm operands of the kept rows, packed
+// in order; one warp per kept row (Dp a multiple of 64: whole 16-byte moves).
+__global__ void prune_sub_gather_kernel(const uint16_t* __restrict__ Xt, const float* __restrict__ n2,
+                                        const float* __restrict__ eps, const float* __restrict__ n8, int Dp,
+                                        const int32_t* __restrict__ kidx, const int64_t* __restrict__ nk_dev,
+                                        uint16_t* __restrict__ XtK, float* __restrict__ n2K, float* __restrict__ epsK,
+                                        float* __restrict__ n8K) {
+  const int64_t nk = *nk_dev;
+  const int lane = threadIdx.x & 31;
+  const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  const int row16 = Dp / 8;  // 16-byte words per row
+  for (int64_t c = warp; c < nk; c += nw) {
+    const int64_t r = kidx[c];
+    const uint4* src = reinterpret_cast<const uint4*>(Xt + r * Dp);
+    uint4* dst = reinterpret_cast<uint4*>(XtK + c * Dp);
+    for (int k = lane; k < row16; k += 32) dst[k] = src[k];
+    if (lane < 8) n8K[c * 8 + lane] = n8[r * 8 + lane];
+    if (lane == 0) {
+      n2K[c] = n2[r];
+      epsK[c] = eps[r];
+    }
+  }
+}
+
+// S rows evenly spread over the nk listed ones: out[i] = kidx[i nk / S]
+__global__ void prune_sub_sample_kernel(const int32_t* __restrict__ kidx, const int64_t* __restrict__ nk_dev,
+                                        int64_t S, int32_t* __restrict__ out, int64_t* __restrict__ ns_dev) {
+  const int64_t nk = *nk_dev;
+  const int64_t ns = nk < S ? nk : S;
+  for (int64_t i = threadIdx.x; i < ns; i += blockDim.x) out[i] = kidx[nk <= S ? i : (i * nk) / S];
+  if (threadIdx.x == 0) *ns_dev = ns;
+}
+
+// The largest lower end over the first *n_dev minima (rows: float minima;
+// columns: the unsigned bits of non-negative floats) into *lb.
+__global__ void prune_sub_lb_kernel(const float* __restrict__ minv, const float* __restrict__ n2,
+                                    const float* __restrict__ eps, const int64_t* __restrict__ n_dev,
+                                    const HdScalars* __restrict__ sc, int rows, double c1, double* __restrict__ lb) {
+  const int64_t n = *n_dev;
+  const double inv = ldexp(1.0, -scale_exponent(sc->maxabs));
+  const float maxnorm_other = rows ? sc->maxnormB : sc->maxnormA;
+  const float maxeps_other = rows ? sc->maxepsB : sc->maxepsA;
+  double best = 0.0;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += stride) {
+    double lo, hi;
+    row_interval(minv[i], n2[i], maxnorm_other, eps[i], maxeps_other, c1, inv, lo, hi);
+    best = fmax(best, lo);
+  }
+  for (int o = 16; o > 0; o >>= 1) best = fmax(best, __shfl_xor_sync(0xffffffffu, best, o));
+  if ((threadIdx.x & 31) == 0) atomic_max_nonneg(lb, best);
+}
+
+// candidate positions in the kept lists -> row numbers
+__global__ void prune_sub_remap_kernel(int32_t* __restrict__ candA, const int64_t* __restrict__ ncA,
+                                       const int32_t* __restrict__ kA, int32_t* __restrict__ candB,
+                                       const int64_t* __restrict__ ncB, const int32_t* __restrict__ kB) {
+  const int64_t na = *ncA, nb = *ncB;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < na; c += stride) candA[c] = kA[candA[c]];
+  for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < nb; c += stride) candB[c] = kB[candB[c]];
+}
+
+cudaError_t hd_core_pruned(prohd_ctx* ctx, const float* A, const int64_t* nA_dev, int64_t nA_max, const float* B,
+                           const int64_t* nB_dev, int64_t nB_max, int D, int precision, const int32_t* mapA,
+                           const int32_t* mapB, prohd_hd_result* out, int* status_dev, Arena& ws, int64_t timeout_ns,
+                           cudaStream_t st) {
+  if (!hd_subset_prunable(nA_max, nB_max, D, precision)) return cudaErrorInvalidValue;
+  HdBufs b;
+  layout(ws, nA_max, nB_max, D, precision, b);
+  HdPruneBufs q;
+  prune_sub_layout(ws, nA_max, nB_max, b, q);
+  if (ws.overflow()) return cudaErrorMemoryAllocation;
+  const int nsm = ctx->num_sms;
+  cudaError_t e = tc_prep(ctx, A, nA_dev, B, nB_dev, D, precision, b, status_dev, st, nullptr);
+  if (e) return e;
+  const double c1 = tc_c1(b.Dp, D);
+  TcMaps full, keptA, keptB;
+  if (!tc_maps(ctx, precision, b.At, b.nA_pad, b.nA8, b.Bt, b.nB_pad, b.nB8, b.Dp, full) ||
+      !tc_maps(ctx, precision, q.AtK, b.nA_pad, q.nA8K, b.Bt, b.nB_pad, b.nB8, b.Dp, keptA) ||
+      !tc_maps(ctx, precision, b.At, b.nA_pad, b.nA8, q.BtK, b.nB_pad, q.nB8K, b.Dp, keptB))
+    return cudaErrorInvalidValue;
+  {
+    PhaseTimer pt(ctx, PROHD_PH_HD_CONTRACT, st);
+    count_launch();
+    prune_sub_init_kernel<<<1, 1, 0, st>>>(nA_dev, nB_dev, kSubPrefix, q.nAp, q.nBp, q.lb);
+    // 1. all of A against B's prefix
+    count_launch();
+    fill_u32_kernel<<<nsm * 2, 256, 0, st>>>(b.colmin, b.nB_pad, 0x7f800000u);
+    if ((e = cudaGetLastError())) return e;
+    if ((e = tc_contract(ctx, full, nA_dev, q.nBp, b.Dp, precision, false, b.rowmin, b.colmin, status_dev, timeout_ns,
+                         st)))
+      return e;
+    count_launch();
+    prune_sub_pass_kernel<<<nsm * 2, 256, 0, st>>>(b.rowmin, b.nA2, b.epsA, nA_dev, b.colmin, b.nB2, b.epsB, q.nBp,
+                                                    b.sc, c1, 1, q.hiA, q.lb + 1);
+    // 2. A's prefix against all of B
+    count_launch();
+    fill_u32_kernel<<<nsm * 2, 256, 0, st>>>(b.colmin, b.nB_pad, 0x7f800000u);
+    count_launch();
+    fill_u32_kernel<<<nsm, 256, 0, st>>>(reinterpret_cast<unsigned*>(b.rowmin), b.nA_pad, 0x7f800000u);
+    if ((e = cudaGetLastError())) return e;
+    if ((e = tc_contract(ctx, full, q.nAp, nB_dev, b.Dp, precision, true, b.rowmin, b.colmin, status_dev, timeout_ns,
+                         st)))
+      return e;
+    count_launch();
+    prune_sub_pass_kernel<<<nsm * 2, 256, 0, st>>>(b.rowmin, b.nA2, b.epsA, q.nAp, b.colmin, b.nB2, b.epsB, nB_dev,
+                                                    b.sc, c1, 0, q.hiB, q.lb);
+    // 3. the hard rows, a sample of them against everything, then the kept rows
+    auto keep = [&]() {
+      count_launch();
+      prune_sub_keep_kernel<<<nsm * 2, 256, 0, st>>>(q.hiA, nA_dev, nA_max, q.lb, q.maskA);
+      count_launch();
+      prune_sub_keep_kernel<<<nsm * 2, 256, 0, st>>>(q.hiB, nB_dev, nB_max, q.lb + 1, q.maskB);
+      cudaError_t e2 = cudaGetLastError();
+      if (!e2) e2 = mask_to_indices(q.maskA, nA_max, q.kA, q.nkA, q.counts, q.offsets, st);
+      if (!e2) e2 = mask_to_indices(q.maskB, nB_max, q.kB, q.nkB, q.counts, q.offsets, st);
+      return e2;
+    };
+    if ((e = keep())) return e;
+    count_launch();
+    prune_sub_sample_kernel<<<1, 1024, 0, st>>>(q.kA, q.nkA, kSubSample, q.sA, q.nsA);
+    count_launch();
+    prune_sub_sample_kernel<<<1, 1024, 0, st>>>(q.kB, q.nkB, kSubSample, q.sB, q.nsB);
+    count_launch();
+    prune_sub_gather_kernel<<<nsm * 4, 256, 0, st>>>(static_cast<const uint16_t*>(b.At), b.nA2, b.epsA, b.nA8, b.Dp,
+                                                      q.sA, q.nsA, static_cast<uint16_t*>(q.AtK), q.nA2K, q.epsAK,
+                                                      q.nA8K);
+    count_launch();
+    prune_sub_gather_kernel<<<nsm * 4, 256, 0, st>>>(static_cast<const uint16_t*>(b.Bt), b.nB2, b.epsB, b.nB8, b.Dp,
+                                                      q.sB, q.nsB, static_cast<uint16_t*>(q.BtK), q.nB2K, q.epsBK,
+                                                      q.nB8K);
+    count_launch();
+    fill_u32_kernel<<<nsm, 256, 0, st>>>(reinterpret_cast<unsigned*>(b.rowmin), b.nA_pad, 0x7f800000u);
+    count_launch();
+    fill_u32_kernel<<<nsm * 2, 256, 0, st>>>(b.colmin, b.nB_pad, 0x7f800000u);
+    count_launch();
+    fill_u32_kernel<<<nsm * 2, 256, 0, st>>>(q.colK, b.nB_pad, 0x7f800000u);
+    if ((e = cudaGetLastError())) return e;
+    if ((e = tc_contract(ctx, keptA, q.nsA, nB_dev, b.Dp, precision, true, b.rowmin, b.colmin, status_dev, timeout_ns,
+                         st)))
+      return e;
+    if ((e = tc_contract(ctx, keptB, nA_dev, q.nsB, b.Dp, precision, false, q.rowx, q.colK, status_dev, timeout_ns,
+                         st)))
+      return e;
+    count_launch();
+    prune_sub_lb_kernel<<<nsm, 256, 0, st>>>(b.rowmin, q.nA2K, q.epsAK, q.nsA, b.sc, 1, c1, q.lb);
+    count_launch();
+    prune_sub_lb_kernel<<<nsm, 256, 0, st>>>(reinterpret_cast<const float*>(q.colK), q.nB2K, q.epsBK, q.nsB, b.sc, 0,
+                                             c1, q.lb + 1);
+    if ((e = cudaGetLastError())) return e;
+    if ((e = keep())) return e;
+    count_launch();
+    prune_sub_gather_kernel<<<nsm * 4, 256, 0, st>>>(static_cast<const uint16_t*>(b.At), b.nA2, b.epsA, b.nA8, b.Dp,
+                                                      q.kA, q.nkA, static_cast<uint16_t*>(q.AtK), q.nA2K, q.epsAK,
+                                                      q.nA8K);
+    count_launch();
+    prune_sub_gather_kernel<<<nsm * 4, 256, 0, st>>>(static_cast<const uint16_t*>(b.Bt), b.nB2, b.epsB, b.nB8, b.Dp,
+                                                      q.kB, q.nkB, static_cast<uint16_t*>(q.BtK), q.nB2K, q.epsBK,
+                                                      q.nB8K);
+    // 4. full intervals of the kept rows: A's kept rows against all of B
+    // (row minima; the column minima are not used), all of A against B's
+    // kept rows (column minima)
+    count_launch();
+    fill_u32_kernel<<<nsm, 256, 0, st>>>(reinterpret_cast<unsigned*>(b.rowmin), b.nA_pad, 0x7f800000u);
+    count_launch();
+    fill_u32_kernel<<<nsm * 2, 256, 0, st>>>(b.colmin, b.nB_pad, 0x7f800000u);
+    count_launch();
+    fill_u32_kernel<<<nsm * 2, 256, 0, st>>>(q.colK, b.nB_pad, 0x7f800000u);
+    if ((e = cudaGetLastError())) return e;
+    if ((e = tc_contract(ctx, keptA, q.nkA, nB_dev, b.Dp, precision, true, b.rowmin, b.colmin, status_dev, timeout_ns,
+                         st)))
+      return e;
+    if ((e = tc_contract(ctx, keptB, nA_dev, q.nkB, b.Dp, precision, false, q.rowx, q.colK, status_dev, timeout_ns,
+                         st)))
+      return e;
+  }
+  // 5. as hd_core, on the kept rows
+  PhaseTimer pt_rs(ctx, PROHD_PH_HD_RESCORE, st);
+  count_launch();
+  hd_bounds_kernel<<<nsm * 2, 256, 0, st>>>(b.rowmin, q.nA2K, q.epsAK, q.nkA, q.colK, q.nB2K, q.epsBK, q.nkB, c1,
+                                            b.sc);
+  count_launch();
+  hd_flag_kernel<<<nsm * 2, 256, 0, st>>>(b.rowmin, q.nA2K, q.epsAK, q.nkA, q.colK, q.nB2K, q.epsBK, q.nkB, c1, b.sc,
+                                          b.candA, b.candB, &b.sc->ncandA, &b.sc->ncandB);
+  count_launch();
+  prune_sub_remap_kernel<<<nsm, 256, 0, st>>>(b.candA, &b.sc->ncandA, q.kA, b.candB, &b.sc->ncandB, q.kB);
+  count_launch();
+  fill_u64_kernel<<<nsm * 4, 256, 0, st>>>(b.bestA, nA_max, ~0ull);
+  count_launch();
+  fill_u64_kernel<<<nsm * 4, 256, 0, st>>>(b.bestB, nB_max, ~0ull);
+  if ((e = cudaGetLastError())) return e;
   {
     const size_t fsm = (size_t)kFewRows * 256 * sizeof(float) + (size_t)8 * kFewRows * sizeof(unsigned long long);
     cudaFuncSetAttribute(rescore_few_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fsm);

@@ -34,6 +34,10 @@ struct prohd_ctx {
   // row pruning of directed distances only for contractions of at least this
   // many (row, column) pairs (prohd_set_prune_min_pairs)
   double prune_min_pairs = 4e9;
+  // the estimate's subset distance takes the pruned form when the subset
+  // bounds give at least this many (row, column) pairs
+  // (prohd_set_subset_prune_min_pairs)
+  double subset_prune_min_pairs = 1e9;
 };
 
 namespace prohd {
@@ -95,6 +99,16 @@ cudaError_t hd_core(prohd_ctx* ctx, const float* A, const int64_t* nA_dev, int64
                     const int32_t* mapB, prohd_hd_result* out, int* status_dev, Arena& ws, int64_t timeout_ns,
                     cudaStream_t st, bool few_rows = false, const HdShared* shared = nullptr);
 bool tc_supported_dim(int D);
+// The same result as hd_core (tensor-core precisions), with the rows that
+// cannot attain either directed maximum left out of the full contractions;
+// applies where hd_subset_prunable holds (its layout: hd_core_pruned_layout,
+// which is hd_core_layout plus the pruning buffers where it applies).
+bool hd_subset_prunable(int64_t nA_max, int64_t nB_max, int D, int precision);
+void hd_core_pruned_layout(Arena& ws, int64_t nA_max, int64_t nB_max, int D, int precision);
+cudaError_t hd_core_pruned(prohd_ctx* ctx, const float* A, const int64_t* nA_dev, int64_t nA_max, const float* B,
+                           const int64_t* nB_dev, int64_t nB_max, int D, int precision, const int32_t* mapA,
+                           const int32_t* mapB, prohd_hd_result* out, int* status_dev, Arena& ws, int64_t timeout_ns,
+                           cudaStream_t st);
 
 // ---- selection (select.cu) ----
 void select_layout(Arena& ws, int64_t nA, int64_t nB, int D, int ndirs);

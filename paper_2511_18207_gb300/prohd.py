@@ -41,6 +41,7 @@ EXPORTS = [
     "prohd_mlp_loss_grad", "prohd_mlp_train_step", "prohd_mlp_adam_step",
     "prohd_estimate_adaptive_workspace_size", "prohd_estimate_adaptive",
     "hausdorff_exact_pruned_workspace_size", "hausdorff_exact_pruned", "prohd_set_prune_min_pairs",
+    "prohd_set_subset_prune_min_pairs",
     "prohd_covariance_workspace_size", "prohd_covariance", "prohd_mlp_save", "prohd_mlp_load",
 ]
 
@@ -177,6 +178,8 @@ def load_library(path: str = LIB_PATH):
         lib.hausdorff_exact_pruned.restype = i32
         lib.prohd_set_prune_min_pairs.argtypes = [vp, ctypes.c_double]
         lib.prohd_set_prune_min_pairs.restype = i32
+        lib.prohd_set_subset_prune_min_pairs.argtypes = [vp, ctypes.c_double]
+        lib.prohd_set_subset_prune_min_pairs.restype = i32
         lib.prohd_estimate_adaptive_workspace_size.argtypes = [i64, i64, i32, pp, ctypes.c_double]
         lib.prohd_estimate_adaptive_workspace_size.restype = sz
         lib.prohd_estimate_adaptive.argtypes = [vp, vp, i64, vp, i64, i32, pp, ctypes.c_double, ctypes.c_double, vp,
@@ -340,6 +343,12 @@ class Context:
         """Pair threshold of the row pruning (pruned exact distance and the
         refinement); 0 prunes whenever the row counts allow."""
         self._raise(self.lib.prohd_set_prune_min_pairs(self.h, float(min_pairs)), "prohd_set_prune_min_pairs")
+
+    def set_subset_prune_min_pairs(self, min_pairs: float):
+        """Pair threshold of the estimate's pruned subset distance (same
+        result as the plain contraction); 0 prunes whenever the subsets allow."""
+        self._raise(self.lib.prohd_set_subset_prune_min_pairs(self.h, float(min_pairs)),
+                    "prohd_set_subset_prune_min_pairs")
 
     def hausdorff_exact_noalloc(self, A, B, out=None, stream=None):
         """Enqueues hausdorff_exact_noalloc (FP32, library-internal scratch,
