@@ -48,6 +48,9 @@ ALPHA = 0.01
 # pairs' partial products) do not. None: no capture of the current kernel.
 GRAM_TRAFFIC = 821.96e6 * 5 + 3.26e6
 PROJ_TRAFFIC = (819.41e6 + 26.96e6) * 5
+# pinned host-to-device rate measured on this machine type (one cudaMemcpyAsync,
+# several streams, or SM loads of mapped memory all gave 211 GB/s)
+H2D_GBS = 211.5
 # the contraction's traffic per row of the two FP16 copies (100k + 100k capture)
 HD_TRAFFIC_PER_ROW = (138.28e6 + 5.13e6) / 200_000
 WORKLOAD = ("anisotropic Gaussian pair, n=m=2,000,000, D=256 (eigenvalues 1/i, random rotation); "
@@ -617,7 +620,10 @@ def gpu_arm(args):
         "timing": ("CUDA-graph replays of one prohd_estimate" if graph is not None else "eager calls"),
         "eager_ms_per_step": ms_eager,
         "e2e": {"value": world * 1000.0 / e2e_ms, "unit": UNIT, "ms_per_step": e2e_ms,
-                "h2d_bytes_per_step": 2 * n * DIM * 4, "d2h_bytes_per_step": ctypes.sizeof(prohd.Result)},
+                "h2d_bytes_per_step": 2 * n * DIM * 4, "d2h_bytes_per_step": ctypes.sizeof(prohd.Result),
+                "h2d_floor_ms": 2 * n * DIM * 4 / H2D_GBS / 1e6,
+                "overlap": "each set copied in row ranges on the library's copy stream; the Gram reads each range "
+                           "as it lands (sets of at least 131,072 rows)"},
         "gpu_launches": launches,
         "roofline": roof,
         "stage_rooflines": stage_roofs,

@@ -214,11 +214,11 @@ prohd_status prohd_set_prune_min_pairs(prohd_ctx* ctx, double min_pairs);
  * rows that cannot attain either directed maximum: every row of one subset is
  * contracted against the first 2,048 rows of the other (an upper bound of its
  * NN distance), the first 2,048 rows of each against the whole other subset
- * (lower bounds of h by the intervals' lower ends), then 1,024 evenly spread
- * rows among those whose upper bound reaches that bound (a larger lower
- * bound), and only the rows whose upper bound reaches the larger bound (and
- * row 0) run the full contraction, with the same intervals, candidates and
- * FP32 rescoring. The
+ * (lower bounds of h by the intervals' lower ends), then, twice, 1,024
+ * evenly spread rows among those whose upper bound reaches the current bound
+ * (a larger lower bound), and only the rows whose upper bound reaches the last
+ * bound (and row 0) run the full contraction, with the same intervals,
+ * candidates and FP32 rescoring. The
  * result is the plain contraction's in every field (H, both directed
  * distances, witnesses, H_lowp, rescored counts). */
 prohd_status prohd_set_subset_prune_min_pairs(prohd_ctx* ctx, double min_pairs);
@@ -391,6 +391,20 @@ prohd_status prohd_batch_use_graph(prohd_batch* b, int on);
 prohd_status prohd_batch_autotune(prohd_ctx* ctx, prohd_batch* b, prohd_result* out, void* stream, double* best_ms);
 prohd_status prohd_batch_get_tunables(const prohd_batch* b, int32_t* gram_pts, int32_t* proj_rows, int32_t* sel_chunk);
 prohd_status prohd_batch_set_tunables(prohd_batch* b, int32_t gram_pts, int32_t proj_rows, int32_t sel_chunk);
+
+/* The tuning table, persisted: prohd_tunables_save writes the context's
+ * batch item sizes (those prohd_batch_autotune left, else the defaults) to a
+ * small text file at `path` (host path), keyed by the device name, SM count
+ * and compute capability; prohd_tunables_load reads one back into the
+ * context, whose later plans then start from those sizes. Load returns
+ * PROHD_EINVAL for a missing or malformed file, a table of another device
+ * (name, SM count or compute capability differ) or values below the
+ * minimums, and leaves the context unchanged. No device work; no stream.
+ * The kernels' tile shapes (operand rings, stages, TMEM buffers) are fixed
+ * at compile time from offline sweeps; the runtime table holds the item
+ * sizes, which depend on the batch. */
+prohd_status prohd_tunables_save(prohd_ctx* ctx, const char* path);
+prohd_status prohd_tunables_load(prohd_ctx* ctx, const char* path);
 
 /* Device pointers (inside the plan's workspace) of pair `pair`'s directions
  * [1+m][D] (FP64), candidate indices (int32, the first nsel_a / nsel_b

@@ -389,12 +389,13 @@ struct EstLayout {
   int64_t *nA_full = nullptr, *nB_full = nullptr;
   prohd_hd_result *r1 = nullptr, *r2 = nullptr;
   PruneLayout P;  // the refinement's row pruning (tensor-core precisions)
+  const InputFeed* feed = nullptr;  // host-buffer entry: inputs landing in row ranges
 };
 
 // Layout of an estimate with nd directions and the given k lists; m_dirs >= 0
 // reserves the directions phase's scratch (m_dirs components), -1 skips it.
 void est_layout_k(Arena& a, int64_t nA, int64_t nB, int D, int nd, const int64_t* kA, const int64_t* kB,
-                  int precision, int m_dirs, EstLayout& L, bool refine = false) {
+                  int precision, int m_dirs, EstLayout& L, bool refine = false, int gram_parts = 1) {
   L.nd = nd;
   for (int d = 0; d < nd; ++d) {
     L.kA[d] = kA[d];
@@ -430,7 +431,7 @@ void est_layout_k(Arena& a, int64_t nA, int64_t nB, int D, int nd, const int64_t
   L.mark_dir = L.mark_sel = L.mark_hd = (start + 255) / 256 * 256;
   Arena t = a;
   if (m_dirs >= 0) {
-    directions_layout(t, nA, nB, D, m_dirs);
+    directions_layout(t, nA, nB, D, m_dirs, gram_parts);
     end = std::max(end, t.off);
   }
   t = a;
@@ -452,14 +453,24 @@ void est_layout_k(Arena& a, int64_t nA, int64_t nB, int D, int nd, const int64_t
   a.off = end;
 }
 
-void est_layout(Arena& a, int64_t nA, int64_t nB, int D, const prohd_params* p, EstLayout& L) {
+void est_layout(Arena& a, int64_t nA, int64_t nB, int D, const prohd_params* p, EstLayout& L, int gram_parts = 1) {
   const int m = resolve_m(p, D);
   const int nd = 1 + m;
   const double ap = resolve_alpha_p(p, m);
   int64_t kA[64], kB[64];
   k_list(nA, nd, p->alpha_c, ap, kA);
   k_list(nB, nd, p->alpha_c, ap, kB);
-  est_layout_k(a, nA, nB, D, nd, kA, kB, p->precision, m, L, p->refine != 0);
+  est_layout_k(a, nA, nB, D, nd, kA, kB, p->precision, m, L, p->refine != 0, gram_parts);
+}
+
+// Row ranges per set in which prohd_estimate_host copies its inputs: where
+// the tensor-core Gram runs and both sets are large, its launch over each
+// range overlaps the copies of the later ranges (2 ranges from 131,072 rows
+// per set, 4 from 524,288).
+int host_parts(int64_t nA, int64_t nB, int D) {
+  if (!gram_tc_supported(D)) return 1;
+  const int64_t n = std::min(nA, nB);
+  return n >= 524288 ? 4 : (n >= 131072 ? 2 : 1);
 }
 
 }  // namespace
@@ -498,6 +509,10 @@ prohd_status prohd_create(prohd_ctx** out) {
 
 void prohd_destroy(prohd_ctx* ctx) {
   if (!ctx) return;
+  if (ctx->copy_stream) cudaStreamDestroy(ctx->copy_stream);
+  if (ctx->feed_start) cudaEventDestroy(ctx->feed_start);
+  for (cudaEvent_t ev : ctx->feed_ready)
+    if (ev) cudaEventDestroy(ev);
   for (auto& p : ctx->pending) {
     cudaEventDestroy(p.a);
     cudaEventDestroy(p.b);
@@ -567,7 +582,7 @@ size_t prohd_estimate_host_workspace_size(int64_t nA, int64_t nB, int D, const p
   const size_t base = a.off;
   Arena b;
   EstLayout L;
-  est_layout(b, nA, nB, D, p, L);
+  est_layout(b, nA, nB, D, p, L, host_parts(nA, nB, D));
   return base + b.off + 512;
 }
 
@@ -734,7 +749,7 @@ static prohd_status estimate_run(prohd_ctx* ctx, const float* A, int64_t nA, con
   if (!e && !given_dirs) {
     Arena t = phase(L.mark_dir);
     e = directions_run(ctx, A, nA, B, nB, D, m, p->power_max_iters, p->power_tol, p->seed, L.dirs, L.eig, L.status, t, st,
-                       p->wait_timeout_ns);
+                       p->wait_timeout_ns, L.feed);
   }
   if (!e) {
     Arena t = phase(L.mark_sel);
@@ -769,12 +784,14 @@ static prohd_status estimate_run(prohd_ctx* ctx, const float* A, int64_t nA, con
 
 static prohd_status estimate_impl(prohd_ctx* ctx, const float* A, int64_t nA, const float* B, int64_t nB, int D,
                                   const prohd_params* p, prohd_result* out, int32_t* idxA, int32_t* idxB,
-                                  double* dirs, char* wsb, size_t ws_bytes, cudaStream_t st) {
+                                  double* dirs, char* wsb, size_t ws_bytes, cudaStream_t st,
+                                  const InputFeed* feed = nullptr) {
   Arena a;
   a.base = wsb;
   a.cap = ws_bytes;
   EstLayout L;
-  est_layout(a, nA, nB, D, p, L);
+  est_layout(a, nA, nB, D, p, L, feed ? feed->parts : 1);
+  L.feed = feed;
   if (a.overflow()) return fail(ctx, PROHD_ENOMEM, "workspace too small%s");
   return estimate_run(ctx, A, nA, B, nB, D, p, L, out, idxA, idxB, dirs, nullptr, wsb, ws_bytes, st);
 }
@@ -807,12 +824,42 @@ prohd_status prohd_estimate_host(prohd_ctx* ctx, const float* A_host, int64_t nA
   float* Bd = a.take<float>((size_t)nB * D);
   prohd_result* od = a.take<prohd_result>(1);
   const size_t base = (a.off + 255) / 256 * 256;
-  cudaError_t e = cudaMemcpyAsync(Ad, A_host, sizeof(float) * nA * D, cudaMemcpyHostToDevice, st);
-  if (!e) e = cudaMemcpyAsync(Bd, B_host, sizeof(float) * nB * D, cudaMemcpyHostToDevice, st);
+  // the copies run on the context's copy stream, in row ranges, each range's
+  // event recorded behind it; the Gram waits for each range before reading it
+  // (overlapping the later copies), and every later step runs after the Gram
+  const int parts = host_parts(nA, nB, D);
+  cudaError_t e = cudaSuccess;
+  if (!ctx->copy_stream) {
+    e = cudaStreamCreateWithFlags(&ctx->copy_stream, cudaStreamNonBlocking);
+    if (!e) e = cudaEventCreateWithFlags(&ctx->feed_start, cudaEventDisableTiming);
+    for (int i = 0; i < 8 && !e; ++i) e = cudaEventCreateWithFlags(&ctx->feed_ready[i], cudaEventDisableTiming);
+    if (e) return cuda_fail(ctx, e);
+  }
+  cudaStream_t cs = ctx->copy_stream;
+  // the copies may overwrite the workspace only after the stream's earlier work
+  if (!e) e = cudaEventRecord(ctx->feed_start, st);
+  if (!e) e = cudaStreamWaitEvent(cs, ctx->feed_start, 0);
+  for (int set = 0; set < 2 && !e; ++set) {
+    const int64_t n = set ? nB : nA;
+    const float* src = set ? B_host : A_host;
+    float* dst = set ? Bd : Ad;
+    for (int k = 0; k < parts && !e; ++k) {
+      const int64_t r0 = n * k / parts, r1 = n * (k + 1) / parts;
+      e = cudaMemcpyAsync(dst + r0 * D, src + r0 * D, sizeof(float) * (size_t)(r1 - r0) * D, cudaMemcpyHostToDevice,
+                          cs);
+      if (!e) e = cudaEventRecord(ctx->feed_ready[set * parts + k], cs);
+    }
+  }
   if (e) return cuda_fail(ctx, e);
+  InputFeed feed;
+  feed.parts = parts;
+  feed.ready = ctx->feed_ready;
   s = estimate_impl(ctx, Ad, nA, Bd, nB, D, p, od, nullptr, nullptr, nullptr, static_cast<char*>(ws) + base,
-                    ws_bytes - base, st);
+                    ws_bytes - base, st, &feed);
+  // the stream holds the copies whatever happened above
+  e = cudaStreamWaitEvent(st, ctx->feed_ready[2 * parts - 1], 0);
   if (s) return s;
+  if (e) return cuda_fail(ctx, e);
   e = cudaMemcpyAsync(out_host, od, sizeof(prohd_result), cudaMemcpyDeviceToHost, st);
   return e ? cuda_fail(ctx, e) : PROHD_OK;
 }

@@ -809,6 +809,53 @@ prohd_status prohd_batch_set_tunables(prohd_batch* b, int32_t gram_pts, int32_t 
   return write_tables(b);
 }
 
+// The tuning table: one text file per device type, keyed by the device name,
+// SM count and compute capability, holding the batch item sizes the
+// autotuner chose (the context's defaults for new plans).
+static bool device_key(const prohd_ctx* ctx, char* name, size_t cap) {
+  cudaDeviceProp prop;
+  if (cudaGetDeviceProperties(&prop, ctx->device) != cudaSuccess) return false;
+  snprintf(name, cap, "%s", prop.name);
+  for (char* c = name; *c; ++c)
+    if (*c == ' ' || *c == '\t' || *c == '\n') *c = '_';
+  return true;
+}
+
+prohd_status prohd_tunables_save(prohd_ctx* ctx, const char* path) {
+  if (!ctx || !path) return PROHD_EINVAL;
+  char name[256];
+  if (!device_key(ctx, name, sizeof name)) return bfail(ctx, PROHD_ECUDA, "device properties unavailable");
+  FILE* f = fopen(path, "w");
+  if (!f) return bfail(ctx, PROHD_EINVAL, "cannot open the tuning table for writing");
+  const int ok = fprintf(f, "prohd-tunables 1\ndevice %s sms %d cc %d.%d\n", name, ctx->num_sms, ctx->cc_major,
+                         ctx->cc_minor) > 0 &&
+                 fprintf(f, "batch_gram_pts %d\nbatch_proj_rows %d\nbatch_sel_chunk %d\n", ctx->batch_gram_pts,
+                         ctx->batch_proj_rows, ctx->batch_sel_chunk) > 0;
+  if (fclose(f) != 0 || !ok) return bfail(ctx, PROHD_EINVAL, "writing the tuning table failed");
+  return PROHD_OK;
+}
+
+prohd_status prohd_tunables_load(prohd_ctx* ctx, const char* path) {
+  if (!ctx || !path) return PROHD_EINVAL;
+  char name[256], fname[256];
+  if (!device_key(ctx, name, sizeof name)) return bfail(ctx, PROHD_ECUDA, "device properties unavailable");
+  FILE* f = fopen(path, "r");
+  if (!f) return bfail(ctx, PROHD_EINVAL, "cannot open the tuning table");
+  int version = 0, sms = 0, ccM = 0, ccm = 0, g = 0, pr = 0, sc = 0;
+  const int n = fscanf(f, "prohd-tunables %d device %255s sms %d cc %d.%d batch_gram_pts %d batch_proj_rows %d "
+                       "batch_sel_chunk %d", &version, fname, &sms, &ccM, &ccm, &g, &pr, &sc);
+  fclose(f);
+  if (n != 8 || version != 1) return bfail(ctx, PROHD_EINVAL, "not a tuning table");
+  if (strcmp(fname, name) != 0 || sms != ctx->num_sms || ccM != ctx->cc_major || ccm != ctx->cc_minor)
+    return bfail(ctx, PROHD_EINVAL, "the tuning table is for another device");
+  if (g < kMinGramPts || pr < kMinProjRows || sc < 256) return bfail(ctx, PROHD_EINVAL, "tunables below their minimum");
+  ctx->batch_tuned = true;
+  ctx->batch_gram_pts = g;
+  ctx->batch_proj_rows = pr;
+  ctx->batch_sel_chunk = sc;
+  return PROHD_OK;
+}
+
 prohd_status prohd_batch_pair_outputs(const prohd_batch* b, int pair, double** dirs, int32_t** idxA, int32_t** idxB,
                                       int32_t** iters) {
   if (!b || pair < 0 || pair >= b->npairs) return PROHD_EINVAL;

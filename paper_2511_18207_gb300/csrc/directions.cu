@@ -689,10 +689,10 @@ struct DirBufs {
   double* si_scratch = nullptr;  // block-iteration outputs
 };
 
-static void dir_layout(Arena& ws, int D, int m, DirBufs& b) {
+static void dir_layout(Arena& ws, int D, int m, DirBufs& b, int gram_parts = 1) {
   b.s32 = ws.take<float>((size_t)D);
   b.cpart = ws.take<double>((size_t)16 * D);
-  if (gram_tc_supported(D)) b.gc_scratch = ws.take<double>(gram_tc_scratch_doubles(D, kMaxSms));
+  if (gram_tc_supported(D)) b.gc_scratch = ws.take<double>(gram_tc_scratch_doubles(D, kMaxSms, gram_parts));
   // CUDA-core Gram (D > 256, D % 4 != 0 or unaligned inputs)
   b.Gpart = ws.take<double>((size_t)kMaxSplit * D * D);
   b.sumApart = ws.take<double>((size_t)kMaxSplit * D);
@@ -707,22 +707,32 @@ static void dir_layout(Arena& ws, int D, int m, DirBufs& b) {
   b.si_scratch = ws.take<double>(subspace_scratch_doubles(D, m));
 }
 
-void directions_layout(Arena& ws, int64_t nA, int64_t nB, int D, int m) {
+void directions_layout(Arena& ws, int64_t nA, int64_t nB, int D, int m, int gram_parts) {
   (void)nA;
   (void)nB;
   DirBufs b;
-  dir_layout(ws, D, m, b);
+  dir_layout(ws, D, m, b, gram_parts);
 }
 
 cudaError_t directions_run(prohd_ctx* ctx, const float* A, int64_t nA, const float* B, int64_t nB, int D, int m,
                            int max_iters, double tol, uint64_t seed, double* dirs, double* eig, int* status_dev,
-                           Arena& ws, cudaStream_t st, int64_t timeout_ns) {
+                           Arena& ws, cudaStream_t st, int64_t timeout_ns, const InputFeed* feed) {
   DirBufs b;
-  dir_layout(ws, D, m, b);
+  const int parts = feed ? feed->parts : 1;
+  dir_layout(ws, D, m, b, parts);
   if (ws.overflow()) return cudaErrorMemoryAllocation;
   if (D > kPiMaxD || m > kPiMaxM) return cudaErrorInvalidValue;
   cudaError_t e;
   const int nsm = ctx->num_sms;
+  const bool aligned = ((reinterpret_cast<uintptr_t>(A) | reinterpret_cast<uintptr_t>(B)) & 15) == 0;
+  const bool tc = gram_tc_supported(D) && aligned && ctx->num_sms <= kMaxSms && ctx->encode_tiled;
+  if (feed && feed->ready) {
+    // the pilot rows lie in A's first range when it holds 4096 rows; the
+    // CUDA-core Gram reads everything at once
+    const int wait_to = tc && nA / parts >= 4096 ? 1 : 2 * parts;
+    for (int k = 0; k < wait_to; ++k)
+      if ((e = cudaStreamWaitEvent(st, feed->ready[k], 0))) return e;
+  }
   {
     // shift s = mean of the first <= 4096 rows of A (16 slices of 256 rows)
     const int nsl = (int)std::min<int64_t>(16, ceil_div(std::min<int64_t>(nA, 4096), 256));
@@ -731,10 +741,9 @@ cudaError_t directions_run(prohd_ctx* ctx, const float* A, int64_t nA, const flo
     count_launch();
     pilot_shift_kernel<<<(D + 255) / 256, 256, 0, st>>>(b.cpart, nsl, nA, 4096, D, b.s32);
   }
-  const bool aligned = ((reinterpret_cast<uintptr_t>(A) | reinterpret_cast<uintptr_t>(B)) & 15) == 0;
-  if (gram_tc_supported(D) && aligned && ctx->num_sms <= kMaxSms && ctx->encode_tiled) {
+  if (tc) {
     if ((e = gram_tc_run(ctx, A, nA, B, nB, D, b.s32, b.gc_scratch, b.G, b.sumA, b.sumB, status_dev,
-                         timeout_ns > 0 ? timeout_ns : kDefaultTimeoutNs, st)))
+                         timeout_ns > 0 ? timeout_ns : kDefaultTimeoutNs, st, feed)))
       return e;
   } else {
     const int nt = (D + kGT - 1) / kGT;

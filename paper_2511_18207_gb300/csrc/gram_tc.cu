@@ -114,8 +114,10 @@ struct GcParams {
   int D, Dp;
   const float* s32;   // pilot shift [D]
   int nclu, ncA;      // clusters; clusters reading A (the rest read B)
-  float* out;         // [nclu] x kGcSlotFloats
-  double* sums;       // [nclu] x kGcSumsDoubles
+  int64_t r0A, r1A, r0B, r1B;  // the rows this launch reads of A and of B
+  int clu0;           // the launch's first slot
+  float* out;         // [clu0 + nclu] x kGcSlotFloats
+  double* sums;       // [clu0 + nclu] x kGcSumsDoubles
   int* status;
   uint64_t timeout_ns;
   // batched launches: clusters take items from the table through an atomic
@@ -263,15 +265,15 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kGcThreads, 1)
     if (!batched) {
       if (iter > 0) break;
       const bool setA = clu < p.ncA;
-      const int64_t n = setA ? p.nA : p.nB;
+      const int64_t r0 = setA ? p.r0A : p.r0B, n = (setA ? p.r1A : p.r1B) - r0;
       const int cj = setA ? clu : clu - p.ncA, ncj = setA ? p.ncA : p.nclu - p.ncA;
       w.tm = setA ? &tmA : &tmB;
       w.s32 = p.s32;
-      w.out = p.out + (size_t)clu * kGcSlotFloats;
-      w.sums = p.sums + (size_t)clu * kGcSumsDoubles;
+      w.out = p.out + (size_t)(p.clu0 + clu) * kGcSlotFloats;
+      w.sums = p.sums + (size_t)(p.clu0 + clu) * kGcSumsDoubles;
       w.status = p.status;
-      w.p0 = n * cj / ncj;
-      w.p1 = n * (cj + 1) / ncj;
+      w.p0 = r0 + n * cj / ncj;
+      w.p1 = r0 + n * (cj + 1) / ncj;
       w.D = p.D;
       w.Dp = p.Dp;
       w.setA = setA ? 1 : 0;
@@ -633,15 +635,17 @@ __global__ void __launch_bounds__(256) gram_tc_sym_kernel(int D, double* __restr
 
 bool gram_tc_supported(int D) { return D >= 4 && D <= 2 * kGcRows && D % 4 == 0; }
 
-size_t gram_tc_scratch_doubles(int D, int num_sms) {
+size_t gram_tc_scratch_doubles(int D, int num_sms, int parts) {
   (void)D;
-  return (size_t)(num_sms / 2) * (kGcSlotFloats / 2 + kGcSumsDoubles) + 2 * kGcRows;
+  const size_t slots = (size_t)(num_sms / 2) * (parts > 1 ? 2 * parts : 1);
+  return slots * (kGcSlotFloats / 2 + kGcSumsDoubles) + 2 * kGcRows;
 }
 
 cudaError_t gram_tc_run(prohd_ctx* ctx, const float* A, int64_t nA, const float* B, int64_t nB, int D,
                         const float* s32, double* scratch, double* G, double* sumA, double* sumB, int* status,
-                        int64_t timeout_ns, cudaStream_t st) {
+                        int64_t timeout_ns, cudaStream_t st, const InputFeed* feed) {
   if (nA < 1 || nB < 1 || nA > INT_MAX || nB > INT_MAX) return cudaErrorInvalidValue;
+  const int parts = feed && feed->parts > 1 ? feed->parts : 1;
   GcParams p;
   p.nA = nA;
   p.nB = nB;
@@ -654,8 +658,14 @@ cudaError_t gram_tc_run(prohd_ctx* ctx, const float* A, int64_t nA, const float*
     int a = (int)std::lround((double)p.nclu * (double)nA / (double)(nA + nB));
     p.ncA = std::min(std::max(a, 1), p.nclu - 1);
   }
+  p.r0A = 0;
+  p.r1A = nA;
+  p.r0B = 0;
+  p.r1B = nB;
+  p.clu0 = 0;
+  const int nslots = parts > 1 ? 2 * parts * p.nclu : p.nclu;
   p.out = reinterpret_cast<float*>(scratch);
-  p.sums = scratch + (size_t)p.nclu * (kGcSlotFloats / 2);
+  p.sums = scratch + (size_t)nslots * (kGcSlotFloats / 2);
   p.status = status;
   p.timeout_ns = (uint64_t)timeout_ns;
   p.items = nullptr;
@@ -671,13 +681,43 @@ cudaError_t gram_tc_run(prohd_ctx* ctx, const float* A, int64_t nA, const float*
   cudaError_t e =
       cudaFuncSetAttribute(gram_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kGcSmemBytes);
   if (e) return e;
-  {
+  if (parts == 1) {
+    if (feed && feed->ready) {
+      if ((e = cudaStreamWaitEvent(st, feed->ready[0], 0))) return e;
+      if ((e = cudaStreamWaitEvent(st, feed->ready[1], 0))) return e;
+    }
     PhaseTimer pt(ctx, PROHD_PH_GRAM, st);
     count_launch();
     gram_tc_kernel<<<2 * p.nclu, kGcThreads, kGcSmemBytes, st>>>(p, tA, tB);
     if ((e = cudaGetLastError())) return e;
+  } else {
+    // one launch per row range of each set, every cluster on that range,
+    // each launch into its own slots (A's ranges first); a range's launch
+    // waits for its rows to land
+    for (int s = 0; s < 2; ++s)
+      for (int k = 0; k < parts; ++k) {
+        const int64_t n = s ? nB : nA;
+        GcParams q = p;
+        q.ncA = s ? 0 : p.nclu;
+        if (s) {
+          q.r0B = n * k / parts;
+          q.r1B = n * (k + 1) / parts;
+        } else {
+          q.r0A = n * k / parts;
+          q.r1A = n * (k + 1) / parts;
+        }
+        q.clu0 = (s * parts + k) * p.nclu;
+        if (feed->ready && (e = cudaStreamWaitEvent(st, feed->ready[s * parts + k], 0))) return e;
+        PhaseTimer pt(ctx, PROHD_PH_GRAM, st);
+        count_launch();
+        gram_tc_kernel<<<2 * p.nclu, kGcThreads, kGcSmemBytes, st>>>(q, tA, tB);
+        if ((e = cudaGetLastError())) return e;
+      }
+    // the reduction sees all slots, A's first
+    p.ncA = parts * p.nclu;
+    p.nclu = nslots;
   }
-  double* corr = p.sums + (size_t)p.nclu * kGcSumsDoubles;
+  double* corr = p.sums + (size_t)nslots * kGcSumsDoubles;
   const int nsum = (int)std::max<int64_t>(1, std::min<int64_t>(ceil_div((int64_t)D * D, 256), (int64_t)ctx->num_sms * 4));
   const int ndim = (int)ceil_div(D, 8);  // 8 warps per block, one dimension each
   count_launch();

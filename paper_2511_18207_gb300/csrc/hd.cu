@@ -237,20 +237,36 @@ __device__ __forceinline__ void rescore_few_body(const float* __restrict__ X, co
   load_row(y, j);
   for (; j < ncols; j += nw) {
     load_row(yn, j + nw);
-    for (int r = 0; r < nr; ++r) {
-      const float* xr = xs + r * Dp + lane;
-      float acc = 0.f;
+    // four candidates at a time: their sums and butterflies interleave (each
+    // candidate's own order of operations is unchanged)
+    for (int r0 = 0; r0 < nr; r0 += 4) {
+      float acc[4];
 #pragma unroll
-      for (int t = 0; t < 8; ++t) {
-        if (t < T) {
-          const float d = xr[32 * t] - y[t];
-          acc = fmaf(d, d, acc);
+      for (int u = 0; u < 4; ++u) {
+        const float* xr = xs + (r0 + u < nr ? r0 + u : r0) * Dp + lane;
+        float a = 0.f;
+#pragma unroll
+        for (int t = 0; t < 8; ++t) {
+          if (t < T) {
+            const float d = xr[32 * t] - y[t];
+            a = fmaf(d, d, a);
+          }
         }
+        acc[u] = a;
       }
-      acc = warp_sum(acc);
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+#pragma unroll
+        for (int u = 0; u < 4; ++u) acc[u] += __shfl_xor_sync(0xffffffffu, acc[u], o);
+      }
       if (lane == 0) {
-        const unsigned long long pk = pack_min(acc, (uint32_t)j);
-        if (pk < best[warp * kFewRows + r]) best[warp * kFewRows + r] = pk;
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          if (r0 + u < nr) {
+            const unsigned long long pk = pack_min(acc[u], (uint32_t)j);
+            if (pk < best[warp * kFewRows + r0 + u]) best[warp * kFewRows + r0 + u] = pk;
+          }
+        }
       }
     }
 #pragma unroll
@@ -1573,12 +1589,13 @@ cudaError_t hd_core(prohd_ctx* ctx, const float* A, const int64_t* nA_dev, int64
 //  2. A's first P rows against all of B: LB_A from those rows likewise, and
 //     hiB[j] for every row of B.
 //  3. the rows of A with hiA >= LB_A (the hard rows) are where the maximum
-//     lies: kSubSample of them, evenly spread, against all of B give a
-//     larger lower bound (the largest lower end among them), and likewise
-//     for B. Keep the rows of A whose hiA reaches the larger of the two
-//     bounds, and the rows of B likewise (and row 0 of each, so that no list
-//     is empty); copy the kept rows' rounded copies, norms and margins into
-//     compact buffers.
+//     lies: kSubSample of them, evenly spread over the list, against all of
+//     B give a larger lower bound (the largest lower end among them), and
+//     likewise for B; the rows whose upper end reaches the new bound form
+//     the next list, sampled once more. Keep the rows of A whose hiA reaches
+//     the last bound, and the rows of B likewise (and row 0 of each, so that
+//     no list is empty); copy the kept rows' rounded copies, norms and
+//     margins into compact buffers.
 //  4. the kept rows of A against all of B (row minima), all of A against the
 //     kept rows of B (column minima): the full intervals of the kept rows.
 //  5. bounds, candidates, rescoring and the witnesses as in hd_core, the
@@ -1591,21 +1608,18 @@ cudaError_t hd_core(prohd_ctx* ctx, const float* A, const int64_t* nA_dev, int64
 // the same reason. The kept rows thus give the same candidate lists,
 // rescored the same way.
 constexpr int64_t kSubPrefix = 2048;  // rows of each set in the pruning passes
-constexpr int64_t kSubSample = 1024;  // hard rows per set for the second lower bound
+constexpr int64_t kSubSample = 1024;  // hard rows per set per sample
+constexpr int kSubRounds = 2;          // samples of the hard rows
 
 struct HdPruneBufs {
   int64_t *nAp = nullptr, *nBp = nullptr, *nkA = nullptr, *nkB = nullptr, *nsA = nullptr, *nsB = nullptr;
-  int32_t *sA = nullptr, *sB = nullptr;  // sampled hard rows
   double* lb = nullptr;  // [2]: LB_A, LB_B
   float *hiA = nullptr, *hiB = nullptr;
-  uint8_t *maskA = nullptr, *maskB = nullptr;
   int32_t *kA = nullptr, *kB = nullptr;
-  unsigned* counts = nullptr;
-  int64_t* offsets = nullptr;
   void *AtK = nullptr, *BtK = nullptr;
   float *nA2K = nullptr, *epsAK = nullptr, *nA8K = nullptr;
   float *nB2K = nullptr, *epsBK = nullptr, *nB8K = nullptr;
-  float* rowx = nullptr;     // row minima of the pass against B's kept rows (not used)
+  float* rowx = nullptr;     // row minima of A's prefix; then those of the passes against B's listed rows (not used)
   unsigned* colK = nullptr;  // column minima of B's kept rows over all of A
 };
 
@@ -1616,18 +1630,11 @@ static void prune_sub_layout(Arena& ws, int64_t nA_max, int64_t nB_max, const Hd
   q.nkB = ws.take<int64_t>(1);
   q.nsA = ws.take<int64_t>(1);
   q.nsB = ws.take<int64_t>(1);
-  q.sA = ws.take<int32_t>((size_t)kSubSample);
-  q.sB = ws.take<int32_t>((size_t)kSubSample);
   q.lb = ws.take<double>(2);
   q.hiA = ws.take<float>((size_t)nA_max);
   q.hiB = ws.take<float>((size_t)nB_max);
-  q.maskA = ws.take<uint8_t>((size_t)nA_max);
-  q.maskB = ws.take<uint8_t>((size_t)nB_max);
   q.kA = ws.take<int32_t>((size_t)nA_max);
   q.kB = ws.take<int32_t>((size_t)nB_max);
-  const int64_t nblk = compact_blocks(std::max(nA_max, nB_max));
-  q.counts = ws.take<unsigned>((size_t)nblk);
-  q.offsets = ws.take<int64_t>((size_t)nblk);
   q.AtK = ws.take<uint16_t>((size_t)b.nA_pad * b.Dp, 1024);
   q.BtK = ws.take<uint16_t>((size_t)b.nB_pad * b.Dp, 1024);
   q.nA2K = ws.take<float>((size_t)b.nA_pad);
@@ -1654,11 +1661,14 @@ void hd_core_pruned_layout(Arena& ws, int64_t nA_max, int64_t nB_max, int D, int
 }
 
 __global__ void prune_sub_init_kernel(const int64_t* __restrict__ nA, const int64_t* __restrict__ nB, int64_t P,
-                                      int64_t* __restrict__ nAp, int64_t* __restrict__ nBp, double* __restrict__ lb) {
+                                      int64_t* __restrict__ nAp, int64_t* __restrict__ nBp, double* __restrict__ lb,
+                                      int64_t* __restrict__ nkA, int64_t* __restrict__ nkB) {
   *nAp = *nA < P ? *nA : P;
   *nBp = *nB < P ? *nB : P;
   lb[0] = 0.0;
   lb[1] = 0.0;
+  *nkA = 0;
+  *nkB = 0;
 }
 
 // After a pass of rows [0, nr) against a prefix of the columns, or of a
@@ -1691,68 +1701,107 @@ __global__ void prune_sub_pass_kernel(const float* __restrict__ rowmin, const fl
   if ((threadIdx.x & 31) == 0) atomic_max_nonneg(lb, best);
 }
 
-// keep[i] for i < n_max: row i < n whose upper end reaches lb, and row 0
-__global__ void prune_sub_keep_kernel(const float* __restrict__ hi, const int64_t* __restrict__ n_dev, int64_t n_max,
-                                      const double* __restrict__ lb, uint8_t* __restrict__ keep) {
-  const int64_t n = *n_dev;
-  const double L = *lb;
+// The pruning state of both sets (index 0: A, 1: B).
+struct PruneSets {
+  const float* hi[2];
+  const int64_t* n[2];
+  const double* lb;
+  int32_t* kidx[2];
+  int64_t* nk[2];
+  // rounded copies, norms, margins and norm operands, and their compact copies
+  const uint16_t* Xt[2];
+  const float *n2[2], *eps[2], *n8[2];
+  uint16_t* XtK[2];
+  float *n2K[2], *epsK[2], *n8K[2];
+  int64_t* ns[2];
+  int Dp;
+};
+
+// grid (blocks, 2 sets): the rows i < n whose upper end reaches the set's
+// lower bound (and row 0), appended to kidx in any order (*nk starts at 0;
+// every later step is independent of the order of the list).
+__global__ void prune_sub_keep_kernel(const PruneSets q) {
+  const int set = blockIdx.y;
+  const float* __restrict__ hi = q.hi[set];
+  const int64_t n = *q.n[set];
+  const double L = q.lb[set];
+  int32_t* kidx = q.kidx[set];
+  unsigned long long* nk = reinterpret_cast<unsigned long long*>(q.nk[set]);
+  const int lane = threadIdx.x & 31;
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n_max; i += stride)
-    keep[i] = (i < n && (i == 0 || (double)hi[i] >= L)) ? 1 : 0;
+  const int64_t end = (n + 31) / 32 * 32;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < end; i += stride) {
+    const bool f = i < n && (i == 0 || (double)hi[i] >= L);
+    const unsigned m = __ballot_sync(0xffffffffu, f);
+    unsigned long long base = 0;
+    if (lane == 0 && m) base = atomicAdd(nk, (unsigned long long)__popc(m));
+    base = __shfl_sync(0xffffffffu, base, 0);
+    if (f) kidx[base + __popc(m & ((1u << lane) - 1))] = (int32_t)i;
+  }
 }
 
-// Rounded copies, norms, margins and norm operands of the kept rows, packed
-// in order; one warp per kept row (Dp a multiple of 64: whole 16-byte moves).
-__global__ void prune_sub_gather_kernel(const uint16_t* __restrict__ Xt, const float* __restrict__ n2,
-                                        const float* __restrict__ eps, const float* __restrict__ n8, int Dp,
-                                        const int32_t* __restrict__ kidx, const int64_t* __restrict__ nk_dev,
-                                        uint16_t* __restrict__ XtK, float* __restrict__ n2K, float* __restrict__ epsK,
-                                        float* __restrict__ n8K) {
-  const int64_t nk = *nk_dev;
+// grid (blocks, 2 sets): the rounded copies, norms, margins and norm operands
+// of listed rows, packed in list order, one warp per row (Dp a multiple of
+// 64: whole 16-byte moves). S > 0: S rows evenly spread over the list
+// (row i of the output is list entry i nk / S; the count min(nk, S) goes to
+// *ns); S = 0: the whole list. Every block also fills its share of the three
+// minimum buffers of the next contraction with +inf.
+__global__ void prune_sub_gather_kernel(const PruneSets q, int64_t S, unsigned* __restrict__ f0, int64_t n0,
+                                        unsigned* __restrict__ f1, int64_t n1, unsigned* __restrict__ f2,
+                                        int64_t n2) {
+  const int set = blockIdx.y;
+  const int64_t nk = *q.nk[set];
+  const int64_t cnt = S > 0 ? (nk < S ? nk : S) : nk;
+  const int32_t* __restrict__ kidx = q.kidx[set];
   const int lane = threadIdx.x & 31;
   const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
   const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  const int Dp = q.Dp;
   const int row16 = Dp / 8;  // 16-byte words per row
-  for (int64_t c = warp; c < nk; c += nw) {
-    const int64_t r = kidx[c];
-    const uint4* src = reinterpret_cast<const uint4*>(Xt + r * Dp);
-    uint4* dst = reinterpret_cast<uint4*>(XtK + c * Dp);
+  if (S > 0 && blockIdx.x == 0 && threadIdx.x == 0) *q.ns[set] = cnt;
+  for (int64_t c = warp; c < cnt; c += nw) {
+    const int64_t r = kidx[(S > 0 && nk > S) ? (c * nk) / S : c];
+    const uint4* src = reinterpret_cast<const uint4*>(q.Xt[set] + r * Dp);
+    uint4* dst = reinterpret_cast<uint4*>(q.XtK[set] + c * Dp);
     for (int k = lane; k < row16; k += 32) dst[k] = src[k];
-    if (lane < 8) n8K[c * 8 + lane] = n8[r * 8 + lane];
+    if (lane < 8) q.n8K[set][c * 8 + lane] = q.n8[set][r * 8 + lane];
     if (lane == 0) {
-      n2K[c] = n2[r];
-      epsK[c] = eps[r];
+      q.n2K[set][c] = q.n2[set][r];
+      q.epsK[set][c] = q.eps[set][r];
     }
   }
+  const int64_t tid = ((int64_t)blockIdx.y * gridDim.x + blockIdx.x) * blockDim.x + threadIdx.x;
+  const int64_t all = (int64_t)gridDim.x * gridDim.y * blockDim.x;
+  for (int64_t i = tid; i < n0; i += all) f0[i] = 0x7f800000u;
+  for (int64_t i = tid; i < n1; i += all) f1[i] = 0x7f800000u;
+  for (int64_t i = tid; i < n2; i += all) f2[i] = 0x7f800000u;
 }
 
-// S rows evenly spread over the nk listed ones: out[i] = kidx[i nk / S]
-__global__ void prune_sub_sample_kernel(const int32_t* __restrict__ kidx, const int64_t* __restrict__ nk_dev,
-                                        int64_t S, int32_t* __restrict__ out, int64_t* __restrict__ ns_dev) {
-  const int64_t nk = *nk_dev;
-  const int64_t ns = nk < S ? nk : S;
-  for (int64_t i = threadIdx.x; i < ns; i += blockDim.x) out[i] = kidx[nk <= S ? i : (i * nk) / S];
-  if (threadIdx.x == 0) *ns_dev = ns;
-}
-
-// The largest lower end over the first *n_dev minima (rows: float minima;
-// columns: the unsigned bits of non-negative floats) into *lb.
-__global__ void prune_sub_lb_kernel(const float* __restrict__ minv, const float* __restrict__ n2,
-                                    const float* __restrict__ eps, const int64_t* __restrict__ n_dev,
-                                    const HdScalars* __restrict__ sc, int rows, double c1, double* __restrict__ lb) {
-  const int64_t n = *n_dev;
+// grid (blocks, 2 sets): the largest lower end over the sampled rows' full
+// minima (set 0: row minima of A's sample; set 1: column minima of B's) into
+// lb[set]; block (0, 0) also clears the kept-row counts for the next list.
+__global__ void prune_sub_lb_kernel(const PruneSets q, const float* __restrict__ rowmin,
+                                    const unsigned* __restrict__ colK, const HdScalars* __restrict__ sc, double c1,
+                                    double* __restrict__ lb) {
+  const int set = blockIdx.y;
+  const int64_t n = *q.ns[set];
   const double inv = ldexp(1.0, -scale_exponent(sc->maxabs));
-  const float maxnorm_other = rows ? sc->maxnormB : sc->maxnormA;
-  const float maxeps_other = rows ? sc->maxepsB : sc->maxepsA;
+  const float maxnorm_other = set ? sc->maxnormA : sc->maxnormB;
+  const float maxeps_other = set ? sc->maxepsA : sc->maxepsB;
   double best = 0.0;
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += stride) {
+    const float m = set ? __uint_as_float(colK[i]) : rowmin[i];
     double lo, hi;
-    row_interval(minv[i], n2[i], maxnorm_other, eps[i], maxeps_other, c1, inv, lo, hi);
+    row_interval(m, q.n2K[set][i], maxnorm_other, q.epsK[set][i], maxeps_other, c1, inv, lo, hi);
     best = fmax(best, lo);
   }
   for (int o = 16; o > 0; o >>= 1) best = fmax(best, __shfl_xor_sync(0xffffffffu, best, o));
-  if ((threadIdx.x & 31) == 0) atomic_max_nonneg(lb, best);
+  if ((threadIdx.x & 31) == 0) atomic_max_nonneg(lb + set, best);
+  if (blockIdx.x == 0 && set == 0 && threadIdx.x == 0) {
+    *q.nk[0] = 0;
+    *q.nk[1] = 0;
+  }
 }
 
 // candidate positions in the kept lists -> row numbers
@@ -1784,10 +1833,40 @@ cudaError_t hd_core_pruned(prohd_ctx* ctx, const float* A, const int64_t* nA_dev
       !tc_maps(ctx, precision, q.AtK, b.nA_pad, q.nA8K, b.Bt, b.nB_pad, b.nB8, b.Dp, keptA) ||
       !tc_maps(ctx, precision, b.At, b.nA_pad, b.nA8, q.BtK, b.nB_pad, q.nB8K, b.Dp, keptB))
     return cudaErrorInvalidValue;
+  PruneSets ps;
+  ps.hi[0] = q.hiA;
+  ps.hi[1] = q.hiB;
+  ps.n[0] = nA_dev;
+  ps.n[1] = nB_dev;
+  ps.lb = q.lb;
+  ps.kidx[0] = q.kA;
+  ps.kidx[1] = q.kB;
+  ps.nk[0] = q.nkA;
+  ps.nk[1] = q.nkB;
+  ps.Xt[0] = static_cast<const uint16_t*>(b.At);
+  ps.Xt[1] = static_cast<const uint16_t*>(b.Bt);
+  ps.n2[0] = b.nA2;
+  ps.n2[1] = b.nB2;
+  ps.eps[0] = b.epsA;
+  ps.eps[1] = b.epsB;
+  ps.n8[0] = b.nA8;
+  ps.n8[1] = b.nB8;
+  ps.XtK[0] = static_cast<uint16_t*>(q.AtK);
+  ps.XtK[1] = static_cast<uint16_t*>(q.BtK);
+  ps.n2K[0] = q.nA2K;
+  ps.n2K[1] = q.nB2K;
+  ps.epsK[0] = q.epsAK;
+  ps.epsK[1] = q.epsBK;
+  ps.n8K[0] = q.nA8K;
+  ps.n8K[1] = q.nB8K;
+  ps.ns[0] = q.nsA;
+  ps.ns[1] = q.nsB;
+  ps.Dp = b.Dp;
+  unsigned* rowmin_u = reinterpret_cast<unsigned*>(b.rowmin);
   {
     PhaseTimer pt(ctx, PROHD_PH_HD_CONTRACT, st);
     count_launch();
-    prune_sub_init_kernel<<<1, 1, 0, st>>>(nA_dev, nB_dev, kSubPrefix, q.nAp, q.nBp, q.lb);
+    prune_sub_init_kernel<<<1, 1, 0, st>>>(nA_dev, nB_dev, kSubPrefix, q.nAp, q.nBp, q.lb, q.nkA, q.nkB);
     // 1. all of A against B's prefix
     count_launch();
     fill_u32_kernel<<<nsm * 2, 256, 0, st>>>(b.colmin, b.nB_pad, 0x7f800000u);
@@ -1798,79 +1877,44 @@ cudaError_t hd_core_pruned(prohd_ctx* ctx, const float* A, const int64_t* nA_dev
     count_launch();
     prune_sub_pass_kernel<<<nsm * 2, 256, 0, st>>>(b.rowmin, b.nA2, b.epsA, nA_dev, b.colmin, b.nB2, b.epsB, q.nBp,
                                                     b.sc, c1, 1, q.hiA, q.lb + 1);
-    // 2. A's prefix against all of B
-    count_launch();
-    fill_u32_kernel<<<nsm * 2, 256, 0, st>>>(b.colmin, b.nB_pad, 0x7f800000u);
-    count_launch();
-    fill_u32_kernel<<<nsm, 256, 0, st>>>(reinterpret_cast<unsigned*>(b.rowmin), b.nA_pad, 0x7f800000u);
-    if ((e = cudaGetLastError())) return e;
-    if ((e = tc_contract(ctx, full, q.nAp, nB_dev, b.Dp, precision, true, b.rowmin, b.colmin, status_dev, timeout_ns,
-                         st)))
-      return e;
-    count_launch();
-    prune_sub_pass_kernel<<<nsm * 2, 256, 0, st>>>(b.rowmin, b.nA2, b.epsA, q.nAp, b.colmin, b.nB2, b.epsB, nB_dev,
-                                                    b.sc, c1, 0, q.hiB, q.lb);
-    // 3. the hard rows, a sample of them against everything, then the kept rows
-    auto keep = [&]() {
-      count_launch();
-      prune_sub_keep_kernel<<<nsm * 2, 256, 0, st>>>(q.hiA, nA_dev, nA_max, q.lb, q.maskA);
-      count_launch();
-      prune_sub_keep_kernel<<<nsm * 2, 256, 0, st>>>(q.hiB, nB_dev, nB_max, q.lb + 1, q.maskB);
-      cudaError_t e2 = cudaGetLastError();
-      if (!e2) e2 = mask_to_indices(q.maskA, nA_max, q.kA, q.nkA, q.counts, q.offsets, st);
-      if (!e2) e2 = mask_to_indices(q.maskB, nB_max, q.kB, q.nkB, q.counts, q.offsets, st);
-      return e2;
-    };
-    if ((e = keep())) return e;
-    count_launch();
-    prune_sub_sample_kernel<<<1, 1024, 0, st>>>(q.kA, q.nkA, kSubSample, q.sA, q.nsA);
-    count_launch();
-    prune_sub_sample_kernel<<<1, 1024, 0, st>>>(q.kB, q.nkB, kSubSample, q.sB, q.nsB);
-    count_launch();
-    prune_sub_gather_kernel<<<nsm * 4, 256, 0, st>>>(static_cast<const uint16_t*>(b.At), b.nA2, b.epsA, b.nA8, b.Dp,
-                                                      q.sA, q.nsA, static_cast<uint16_t*>(q.AtK), q.nA2K, q.epsAK,
-                                                      q.nA8K);
-    count_launch();
-    prune_sub_gather_kernel<<<nsm * 4, 256, 0, st>>>(static_cast<const uint16_t*>(b.Bt), b.nB2, b.epsB, b.nB8, b.Dp,
-                                                      q.sB, q.nsB, static_cast<uint16_t*>(q.BtK), q.nB2K, q.epsBK,
-                                                      q.nB8K);
-    count_launch();
-    fill_u32_kernel<<<nsm, 256, 0, st>>>(reinterpret_cast<unsigned*>(b.rowmin), b.nA_pad, 0x7f800000u);
-    count_launch();
-    fill_u32_kernel<<<nsm * 2, 256, 0, st>>>(b.colmin, b.nB_pad, 0x7f800000u);
+    // 2. A's prefix against all of B (its own minimum buffers, filled here)
     count_launch();
     fill_u32_kernel<<<nsm * 2, 256, 0, st>>>(q.colK, b.nB_pad, 0x7f800000u);
+    count_launch();
+    fill_u32_kernel<<<nsm, 256, 0, st>>>(reinterpret_cast<unsigned*>(q.rowx), b.nA_pad, 0x7f800000u);
     if ((e = cudaGetLastError())) return e;
-    if ((e = tc_contract(ctx, keptA, q.nsA, nB_dev, b.Dp, precision, true, b.rowmin, b.colmin, status_dev, timeout_ns,
+    if ((e = tc_contract(ctx, full, q.nAp, nB_dev, b.Dp, precision, true, q.rowx, q.colK, status_dev, timeout_ns,
                          st)))
       return e;
-    if ((e = tc_contract(ctx, keptB, nA_dev, q.nsB, b.Dp, precision, false, q.rowx, q.colK, status_dev, timeout_ns,
-                         st)))
-      return e;
     count_launch();
-    prune_sub_lb_kernel<<<nsm, 256, 0, st>>>(b.rowmin, q.nA2K, q.epsAK, q.nsA, b.sc, 1, c1, q.lb);
+    prune_sub_pass_kernel<<<nsm * 2, 256, 0, st>>>(q.rowx, b.nA2, b.epsA, q.nAp, q.colK, b.nB2, b.epsB, nB_dev, b.sc,
+                                                    c1, 0, q.hiB, q.lb);
+    // 3. the hard rows; a sample of them against everything raises the
+    // bounds, twice (the second sample is drawn from the rows the first
+    // bound left, which lie closer to the maximum)
     count_launch();
-    prune_sub_lb_kernel<<<nsm, 256, 0, st>>>(reinterpret_cast<const float*>(q.colK), q.nB2K, q.epsBK, q.nsB, b.sc, 0,
-                                             c1, q.lb + 1);
-    if ((e = cudaGetLastError())) return e;
-    if ((e = keep())) return e;
+    prune_sub_keep_kernel<<<dim3(nsm, 2), 256, 0, st>>>(ps);
+    for (int round = 0; round < kSubRounds; ++round) {
+      count_launch();
+      prune_sub_gather_kernel<<<dim3(nsm * 2, 2), 256, 0, st>>>(ps, kSubSample, rowmin_u, b.nA_pad, b.colmin,
+                                                                 b.nB_pad, q.colK, b.nB_pad);
+      if ((e = cudaGetLastError())) return e;
+      if ((e = tc_contract(ctx, keptA, q.nsA, nB_dev, b.Dp, precision, true, b.rowmin, b.colmin, status_dev,
+                           timeout_ns, st)))
+        return e;
+      if ((e = tc_contract(ctx, keptB, nA_dev, q.nsB, b.Dp, precision, false, q.rowx, q.colK, status_dev, timeout_ns,
+                           st)))
+        return e;
+      count_launch();
+      prune_sub_lb_kernel<<<dim3(nsm / 2, 2), 256, 0, st>>>(ps, b.rowmin, q.colK, b.sc, c1, q.lb);
+      count_launch();
+      prune_sub_keep_kernel<<<dim3(nsm, 2), 256, 0, st>>>(ps);
+    }
+    // 4. the kept rows: A's against all of B (row minima; the column minima
+    // are not used), all of A against B's (column minima)
     count_launch();
-    prune_sub_gather_kernel<<<nsm * 4, 256, 0, st>>>(static_cast<const uint16_t*>(b.At), b.nA2, b.epsA, b.nA8, b.Dp,
-                                                      q.kA, q.nkA, static_cast<uint16_t*>(q.AtK), q.nA2K, q.epsAK,
-                                                      q.nA8K);
-    count_launch();
-    prune_sub_gather_kernel<<<nsm * 4, 256, 0, st>>>(static_cast<const uint16_t*>(b.Bt), b.nB2, b.epsB, b.nB8, b.Dp,
-                                                      q.kB, q.nkB, static_cast<uint16_t*>(q.BtK), q.nB2K, q.epsBK,
-                                                      q.nB8K);
-    // 4. full intervals of the kept rows: A's kept rows against all of B
-    // (row minima; the column minima are not used), all of A against B's
-    // kept rows (column minima)
-    count_launch();
-    fill_u32_kernel<<<nsm, 256, 0, st>>>(reinterpret_cast<unsigned*>(b.rowmin), b.nA_pad, 0x7f800000u);
-    count_launch();
-    fill_u32_kernel<<<nsm * 2, 256, 0, st>>>(b.colmin, b.nB_pad, 0x7f800000u);
-    count_launch();
-    fill_u32_kernel<<<nsm * 2, 256, 0, st>>>(q.colK, b.nB_pad, 0x7f800000u);
+    prune_sub_gather_kernel<<<dim3(nsm * 2, 2), 256, 0, st>>>(ps, 0, rowmin_u, b.nA_pad, b.colmin, b.nB_pad, q.colK,
+                                                               b.nB_pad);
     if ((e = cudaGetLastError())) return e;
     if ((e = tc_contract(ctx, keptA, q.nkA, nB_dev, b.Dp, precision, true, b.rowmin, b.colmin, status_dev, timeout_ns,
                          st)))

@@ -38,6 +38,10 @@ struct prohd_ctx {
   // bounds give at least this many (row, column) pairs
   // (prohd_set_subset_prune_min_pairs)
   double subset_prune_min_pairs = 1e9;
+  // host-buffer estimates: the copy stream and the events of its row ranges
+  cudaStream_t copy_stream = nullptr;
+  cudaEvent_t feed_start = nullptr;
+  cudaEvent_t feed_ready[8] = {};
 };
 
 namespace prohd {
@@ -120,10 +124,19 @@ cudaError_t gather_rows(const float* X, int D, const int32_t* idx, const int64_t
                         int num_sms, cudaStream_t st);
 
 // ---- directions (directions.cu) ----
-void directions_layout(Arena& ws, int64_t nA, int64_t nB, int D, int m);
+// Inputs that land while the work runs (the host-buffer entry point): each
+// set arrives in `parts` row ranges [n k / parts, n (k+1) / parts), range k of
+// set s complete once ready[s * parts + k] has completed. The tensor-core Gram
+// reads range k only after waiting for its event, so it overlaps the copies of
+// the later ranges; every other reader runs after the Gram.
+struct InputFeed {
+  int parts = 1;
+  const cudaEvent_t* ready = nullptr;
+};
+void directions_layout(Arena& ws, int64_t nA, int64_t nB, int D, int m, int gram_parts = 1);
 cudaError_t directions_run(prohd_ctx* ctx, const float* A, int64_t nA, const float* B, int64_t nB, int D, int m,
                            int max_iters, double tol, uint64_t seed, double* dirs, double* eig, int* status_dev,
-                           Arena& ws, cudaStream_t st, int64_t timeout_ns);
+                           Arena& ws, cudaStream_t st, int64_t timeout_ns, const InputFeed* feed = nullptr);
 
 // Union covariance C (FP64, D x D, 1/N) and mean of [A; B] (directions.cu).
 void covariance_layout(Arena& ws, int D);
@@ -138,10 +151,12 @@ size_t subspace_scratch_doubles(int D, int m);
 cudaError_t subspace_run(prohd_ctx* ctx, const float* C32, const double* C64, int D, int m, int max_iters, double tol,
                          uint64_t seed, double* dirs, double* eig, double* scratch, cudaStream_t st);
 bool gram_tc_supported(int D);
-size_t gram_tc_scratch_doubles(int D, int num_sms);
+// parts > 1: one launch per row range of each set (InputFeed), partials
+// summed together
+size_t gram_tc_scratch_doubles(int D, int num_sms, int parts = 1);
 cudaError_t gram_tc_run(prohd_ctx* ctx, const float* A, int64_t nA, const float* B, int64_t nB, int D,
                         const float* s32, double* scratch, double* G, double* sumA, double* sumB, int* status,
-                        int64_t timeout_ns, cudaStream_t st);
+                        int64_t timeout_ns, cudaStream_t st, const InputFeed* feed = nullptr);
 
 // ---- batched pairs (batch.cu drives these; each stage is one launch for all pairs) ----
 

@@ -35,7 +35,7 @@ EXPORTS = [
     "prohd_profile_enable", "prohd_profile_read", "prohd_launch_count", "hausdorff_exact_noalloc",
     "prohd_batch_workspace_size", "prohd_batch_plan", "prohd_batch_destroy", "prohd_estimate_batched",
     "prohd_batch_use_graph", "prohd_batch_autotune", "prohd_batch_get_tunables", "prohd_batch_set_tunables",
-    "prohd_batch_pair_outputs",
+    "prohd_batch_pair_outputs", "prohd_tunables_save", "prohd_tunables_load",
     "prohd_estimate_dirs_workspace_size", "prohd_estimate_dirs", "prohd_features_workspace_size", "prohd_features",
     "prohd_mlp_param_count", "prohd_mlp_state_bytes", "prohd_mlp_scratch_bytes", "prohd_mlp_init", "prohd_mlp_forward",
     "prohd_mlp_loss_grad", "prohd_mlp_train_step", "prohd_mlp_adam_step",
@@ -180,6 +180,10 @@ def load_library(path: str = LIB_PATH):
         lib.prohd_set_prune_min_pairs.restype = i32
         lib.prohd_set_subset_prune_min_pairs.argtypes = [vp, ctypes.c_double]
         lib.prohd_set_subset_prune_min_pairs.restype = i32
+        lib.prohd_tunables_save.argtypes = [vp, ctypes.c_char_p]
+        lib.prohd_tunables_save.restype = i32
+        lib.prohd_tunables_load.argtypes = [vp, ctypes.c_char_p]
+        lib.prohd_tunables_load.restype = i32
         lib.prohd_estimate_adaptive_workspace_size.argtypes = [i64, i64, i32, pp, ctypes.c_double]
         lib.prohd_estimate_adaptive_workspace_size.restype = sz
         lib.prohd_estimate_adaptive.argtypes = [vp, vp, i64, vp, i64, i32, pp, ctypes.c_double, ctypes.c_double, vp,
@@ -343,6 +347,14 @@ class Context:
         """Pair threshold of the row pruning (pruned exact distance and the
         refinement); 0 prunes whenever the row counts allow."""
         self._raise(self.lib.prohd_set_prune_min_pairs(self.h, float(min_pairs)), "prohd_set_prune_min_pairs")
+
+    def tunables_save(self, path: str):
+        """Writes the context's batch item sizes to a tuning table file."""
+        self._raise(self.lib.prohd_tunables_save(self.h, os.fsencode(path)), "prohd_tunables_save")
+
+    def tunables_load(self, path: str):
+        """Reads a tuning table file (of this device) into the context."""
+        self._raise(self.lib.prohd_tunables_load(self.h, os.fsencode(path)), "prohd_tunables_load")
 
     def set_subset_prune_min_pairs(self, min_pairs: float):
         """Pair threshold of the estimate's pruned subset distance (same

@@ -151,6 +151,38 @@ def test_batch_autotune_then_run():
         _check_pair(b, i, A, B, r, 8, 0.01, check_dirs=False)
 
 
+def test_tuning_table_round_trip(tmp_path):
+    # the autotuner's item sizes written to a table file and read into a new
+    # context become the defaults of its plans; a table of another device is
+    # refused and leaves the context unchanged
+    torch_cuda()
+    pairs = _pairs(SPEC[:4], seed=5)
+    dpairs = [(dev(A), dev(B)) for A, B in pairs]
+    c0 = ctx()
+    b = prohd.Batch(c0, dpairs, m=8, alpha_c=0.01)
+    b.set_tunables(8192, 32768, 4096)
+    b.autotune()
+    t = b.tunables()
+    path = tmp_path / "tunables.txt"
+    c0.tunables_save(str(path))
+    text = path.read_text()
+    assert text.startswith("prohd-tunables 1\n")
+    c1 = prohd.Context()
+    c1.tunables_load(str(path))
+    assert prohd.Batch(c1, dpairs, m=8, alpha_c=0.01).tunables() == t
+    other = path.with_name("other.txt")
+    lines = text.splitlines()
+    lines[1] = "device Another_GPU sms 1 cc 1.0"
+    other.write_text("\n".join(lines) + "\n")
+    c2 = prohd.Context()
+    before = prohd.Batch(c2, dpairs, m=8, alpha_c=0.01).tunables()
+    with pytest.raises(prohd.ProHDError):
+        c2.tunables_load(str(other))
+    with pytest.raises(prohd.ProHDError):
+        c2.tunables_load(str(tmp_path / "missing.txt"))
+    assert prohd.Batch(c2, dpairs, m=8, alpha_c=0.01).tunables() == before
+
+
 def test_batch_nonfinite_pair_is_reported_alone():
     pairs = _pairs(SPEC[:4], seed=11)
     A, B = pairs[2]

@@ -70,6 +70,24 @@ def test_estimate_host_entry_matches_device():
     assert h["H"] == d["H"] and h["nsel_a"] == d["nsel_a"] and h["nsel_b"] == d["nsel_b"]
 
 
+def test_estimate_host_entry_with_row_range_copies():
+    # both sets of at least 131,072 rows: the host entry copies each set in
+    # two row ranges on its own stream and the Gram reads each range as it
+    # lands (four launches whose partials are summed together); the estimate
+    # matches the device entry's, here to the bit
+    torch = torch_cuda()
+    A, B = W.anisotropic_pair(140_000, 150_000, 64, shift_sigma=0.1, t_frac=0.001, nu=3.0, seed=8)
+    c = prohd.context()
+    p = prohd.default_params(m=8, alpha_c=0.01)
+    for _ in range(2):  # the second call reuses the context's copy stream and events
+        res = c.prohd_estimate_host(torch.from_numpy(A).pin_memory(), torch.from_numpy(B).pin_memory(), params=p)
+        torch.cuda.current_stream().synchronize()
+        h = prohd.decode_result(res)
+        d = prohd.prohd_estimate_sync(dev(A), dev(B), m=8, alpha_c=0.01)
+        assert h["status"] == "OK"
+        assert h["H"] == d["H"] and h["nsel_a"] == d["nsel_a"] and h["nsel_b"] == d["nsel_b"], (h, d)
+
+
 @pytest.mark.parametrize("D", [64, 256, 13])
 @pytest.mark.parametrize("where", ["A_first", "A_middle", "A_last", "B_last_inf"])
 def test_estimate_nonfinite_input_is_reported(D, where):

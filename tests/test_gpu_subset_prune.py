@@ -4,9 +4,9 @@ row pruning against the plain contraction and the oracle.
 The pruned form contracts every subset row against the other subset's first
 2,048 rows (upper bounds of NN distances), the first 2,048 rows of each
 subset against the whole other subset (lower bounds of each directed
-maximum), 1,024 of the rows whose upper bound reaches that bound against the
-whole other subset (a larger lower bound), and runs the full contraction on
-the rows whose upper bound reaches the larger bound. Its claim is equality with the plain
+maximum), twice 1,024 of the rows whose upper bound reaches the current
+bound against the whole other subset (a larger lower bound), and runs the
+full contraction on the rows whose upper bound reaches the last bound. Its claim is equality with the plain
 contraction in every field of the result, so each case runs the same
 estimate both ways (the context's subset threshold set to 0 and to
 infinity) and compares the decoded results field by field, then checks H
