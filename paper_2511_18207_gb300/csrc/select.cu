@@ -457,11 +457,23 @@ __global__ void radix_hist_kernel(const SelProb* __restrict__ P, int pass, unsig
   const int shift = 24 - 8 * pass;
   const uint32_t himask = pass == 0 ? 0u : (0xffffffffu << (32 - 8 * pass));
   const uint32_t p0 = P[p].prefix[0], p1 = P[p].prefix[1];
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-    uint32_t key = f32_key(__ldg(q + i));
-    uint32_t bin = (key >> shift) & 255u;
-    if (((key ^ p0) & himask) == 0) atomicAdd(&h[0][bin], 1u);
-    if (((key ^ p1) & himask) == 0) atomicAdd(&h[1][bin], 1u);
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  // eight independent loads in flight per thread
+  for (int64_t base = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; base < n; base += 8 * stride) {
+    float v[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      const int64_t i = base + u * stride;
+      v[u] = i < n ? __ldg(q + i) : 0.f;
+    }
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      if (base + u * stride >= n) break;
+      const uint32_t key = f32_key(v[u]);
+      const uint32_t bin = (key >> shift) & 255u;
+      if (((key ^ p0) & himask) == 0) atomicAdd(&h[0][bin], 1u);
+      if (((key ^ p1) & himask) == 0) atomicAdd(&h[1][bin], 1u);
+    }
   }
   __syncthreads();
   unsigned* g = hist + (size_t)p * 512;
@@ -1004,27 +1016,47 @@ __global__ void band_kernel(SelProb* __restrict__ P, int pbase) {
   unsigned long long c0 = 0, c1 = 0;
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   const int64_t end = (n + 31) / 32 * 32;
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < end; i += stride) {
-    bool in0 = false, bd0 = false, in1 = false, bd1 = false;
-    if (i < n) {
-      const float v = __ldg(q + i);
-      in0 = v < f_lo_in;
-      bd0 = !in0 && v <= f_lo_band;
-      in1 = v > f_hi_in;
-      bd1 = !in1 && v >= f_hi_band;
-      if (in0 || in1) mask[i] = 1;
+  // eight independent loads in flight, classified before any warp-wide step
+  for (int64_t base = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; base < end; base += 8 * stride) {
+    float vv[8];
+    unsigned bd = 0;  // bit u: band member of side 0; bit 8 + u: of side 1
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      const int64_t i = base + u * stride;
+      vv[u] = i < n ? __ldg(q + i) : 0.f;
     }
-    c0 += in0;
-    c1 += in1;
-    unsigned m0 = __ballot_sync(0xffffffffu, bd0), m1 = __ballot_sync(0xffffffffu, bd1);
-    unsigned long long base0 = 0, base1 = 0;
-    if (lane == 0 && m0) base0 = atomicAdd(reinterpret_cast<unsigned long long*>(&P[p].nband[0]), (unsigned long long)__popc(m0));
-    if (lane == 0 && m1) base1 = atomicAdd(reinterpret_cast<unsigned long long*>(&P[p].nband[1]), (unsigned long long)__popc(m1));
-    base0 = __shfl_sync(0xffffffffu, base0, 0);
-    base1 = __shfl_sync(0xffffffffu, base1, 0);
-    const unsigned below = (1u << lane) - 1;
-    if (bd0) b0[base0 + __popc(m0 & below)] = (int32_t)i;
-    if (bd1) b1[base1 + __popc(m1 & below)] = (int32_t)i;
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      const int64_t i = base + u * stride;
+      if (i >= n) continue;
+      const float v = vv[u];
+      const bool in0 = v < f_lo_in, in1 = v > f_hi_in;
+      if (in0 || in1) mask[i] = 1;
+      c0 += in0;
+      c1 += in1;
+      bd |= ((!in0 && v <= f_lo_band) ? 1u : 0u) << u;
+      bd |= ((!in1 && v >= f_hi_band) ? 1u : 0u) << (8 + u);
+    }
+    // band members are rare: the append path runs only where a lane has one
+    if (!__any_sync(0xffffffffu, bd != 0)) continue;
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      const int64_t i = base + u * stride;
+      if (i - lane >= end) break;  // the whole warp is past the end
+      const bool bd0 = (bd >> u) & 1u, bd1 = (bd >> (8 + u)) & 1u;
+      const unsigned m0 = __ballot_sync(0xffffffffu, bd0), m1 = __ballot_sync(0xffffffffu, bd1);
+      if (!(m0 | m1)) continue;
+      unsigned long long base0 = 0, base1 = 0;
+      if (lane == 0 && m0)
+        base0 = atomicAdd(reinterpret_cast<unsigned long long*>(&P[p].nband[0]), (unsigned long long)__popc(m0));
+      if (lane == 0 && m1)
+        base1 = atomicAdd(reinterpret_cast<unsigned long long*>(&P[p].nband[1]), (unsigned long long)__popc(m1));
+      base0 = __shfl_sync(0xffffffffu, base0, 0);
+      base1 = __shfl_sync(0xffffffffu, base1, 0);
+      const unsigned below = (1u << lane) - 1;
+      if (bd0) b0[base0 + __popc(m0 & below)] = (int32_t)i;
+      if (bd1) b1[base1 + __popc(m1 & below)] = (int32_t)i;
+    }
   }
   c0 = warp_sum(c0);
   c1 = warp_sum(c1);

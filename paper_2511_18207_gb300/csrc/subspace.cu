@@ -49,8 +49,8 @@ constexpr int kSiFinThreads = 256;
 constexpr int kSiJacThreads = 256;  // the Jacobi rounds run on 8 warps (one warp alone is slower: the rounds are latency-bound)
 constexpr int kSiMaxD = 256;
 constexpr int kSiMaxB = 32;
-constexpr int kSiStallWin = 16;    // steps per window of the stall test
-constexpr int kSiStallStart = 48;  // no stall test before this step
+constexpr int kSiStallWin = 8;     // steps per window of the stall test
+constexpr int kSiStallStart = 16;  // no stall test before this step
 constexpr int kSiRRWarm = 4;       // steps with a Rayleigh-Ritz step every time
 
 // block size for D dimensions and m components (D <= 256, m <= 24)
