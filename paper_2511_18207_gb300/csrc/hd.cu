@@ -238,12 +238,14 @@ __device__ __forceinline__ void rescore_few_body(const float* __restrict__ X, co
   for (; j < ncols; j += nw) {
     load_row(yn, j + nw);
     // four candidates at a time: their sums and butterflies interleave (each
-    // candidate's own order of operations is unchanged)
-    for (int r0 = 0; r0 < nr; r0 += 4) {
+    // candidate's own order of operations is unchanged); the last one to
+    // three alone
+    int r0 = 0;
+    for (; r0 + 4 <= nr; r0 += 4) {
       float acc[4];
 #pragma unroll
       for (int u = 0; u < 4; ++u) {
-        const float* xr = xs + (r0 + u < nr ? r0 + u : r0) * Dp + lane;
+        const float* xr = xs + (r0 + u) * Dp + lane;
         float a = 0.f;
 #pragma unroll
         for (int t = 0; t < 8; ++t) {
@@ -262,11 +264,25 @@ __device__ __forceinline__ void rescore_few_body(const float* __restrict__ X, co
       if (lane == 0) {
 #pragma unroll
         for (int u = 0; u < 4; ++u) {
-          if (r0 + u < nr) {
-            const unsigned long long pk = pack_min(acc[u], (uint32_t)j);
-            if (pk < best[warp * kFewRows + r0 + u]) best[warp * kFewRows + r0 + u] = pk;
-          }
+          const unsigned long long pk = pack_min(acc[u], (uint32_t)j);
+          if (pk < best[warp * kFewRows + r0 + u]) best[warp * kFewRows + r0 + u] = pk;
         }
+      }
+    }
+    for (int r = r0; r < nr; ++r) {
+      const float* xr = xs + r * Dp + lane;
+      float acc = 0.f;
+#pragma unroll
+      for (int t = 0; t < 8; ++t) {
+        if (t < T) {
+          const float d = xr[32 * t] - y[t];
+          acc = fmaf(d, d, acc);
+        }
+      }
+      acc = warp_sum(acc);
+      if (lane == 0) {
+        const unsigned long long pk = pack_min(acc, (uint32_t)j);
+        if (pk < best[warp * kFewRows + r]) best[warp * kFewRows + r] = pk;
       }
     }
 #pragma unroll
