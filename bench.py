@@ -46,7 +46,7 @@ ALPHA = 0.01
 # current kernel at 400k + 400k points: the reads (and the projection's key
 # writes) grow with the points (x5 to 2M + 2M); the Gram's writes (the CTA
 # pairs' partial products) do not. None: no capture of the current kernel.
-GRAM_TRAFFIC = 821.96e6 * 5 + 3.26e6
+GRAM_TRAFFIC = 821.96e6 * 5 + 3.22e6
 PROJ_TRAFFIC = (819.41e6 + 26.96e6) * 5
 # pinned host-to-device rate measured on this machine type (one cudaMemcpyAsync,
 # several streams, or SM loads of mapped memory all gave 211 GB/s)
