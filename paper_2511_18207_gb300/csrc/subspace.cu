@@ -51,7 +51,7 @@ constexpr int kSiMaxD = 256;
 constexpr int kSiMaxB = 32;
 constexpr int kSiStallWin = 8;     // steps per window of the stall test
 constexpr int kSiStallStart = 16;  // no stall test before this step
-constexpr int kSiRRWarm = 4;       // steps with a Rayleigh-Ritz step every time
+constexpr int kSiRRWarm = 2;       // steps with a Rayleigh-Ritz step every time
 
 // block size for D dimensions and m components (D <= 256, m <= 24)
 __host__ __device__ inline int si_block(int D, int m) {
@@ -591,13 +591,14 @@ PROHD_DEV void subspace_body(SiSmemT<NC, ROWS, VLD>& S, const float* __restrict_
         }
       }
       __syncthreads();
-      // Plain steps: after kSiRRWarm steps, every other step skips the
-      // Rayleigh-Ritz part (H, Jacobi, Ritz vectors, residuals). The block
-      // spans C^t V_0 either way, so the subspace converges at the same rate
-      // per multiplication; the basis from the last Rayleigh-Ritz step keeps
-      // its column order and Ritz values for the scaling, and the last step
-      // before the cap, like every stop test, is a Rayleigh-Ritz step.
-      const bool plain = t > kSiRRWarm && (t & 1) && t < maxit;
+      // Plain steps: after kSiRRWarm steps, three steps of every four skip
+      // the Rayleigh-Ritz part (H, Jacobi, Ritz vectors, residuals). The
+      // block spans C^t V_0 either way, so the subspace converges at the same
+      // rate per multiplication; the basis from the last Rayleigh-Ritz step
+      // keeps its column order and Ritz values for the scaling, and the last
+      // step before the cap, like every stop test (steps 4, 8, ...; the stall
+      // test's every eighth among them), is a Rayleigh-Ritz step.
+      const bool plain = t > kSiRRWarm && (t & 3) && t < maxit;
       if (plain) {
         const float sigma_p = sigma_rel * fmaxf(S.theta[0], 0.f);
         for (int o = tid; o < nr * b; o += kSiThreads) {
