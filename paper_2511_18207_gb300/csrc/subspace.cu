@@ -738,8 +738,9 @@ PROHD_DEV void subspace_body(SiSmemT<NC, ROWS, VLD>& S, const float* __restrict_
     // orthogonality to FP32 rounding when the first one was not well
     // conditioned: the loss after one pass is about u kappa^2, and the
     // normalised Gram matrix I + E has kappa <= (1 + (b-1) e) / (1 - (b-1) e)
-    // for off-diagonal correlations |E_jk| <= e, so e <= 1e-2 / b keeps it
-    // within a few units of rounding.
+    // for off-diagonal correlations |E_jk| <= e: e <= 1e-2 gives kappa <= 1.36
+    // at b = 16 (1.9 at b = 32), so one pass stays within about 2u (4u) of
+    // orthogonality, and the next step's pass starts from there.
     float corr = 0.f, dummy = 0.f;
     for (int e = tid; e < kSiMaxB * kSiMaxB; e += kSiThreads) {
       const int j = e >> 5, k = e & 31;
@@ -749,7 +750,7 @@ PROHD_DEV void subspace_body(SiSmemT<NC, ROWS, VLD>& S, const float* __restrict_
       }
     }
     si_block_max2(corr, dummy, S.red);
-    const bool second = !(corr <= 1e-2f / (float)b);
+    const bool second = !(corr <= 1e-2f);
     if (warp == 0) si_chol_inv(S, b, lane);
     __syncthreads();
     si_apply_linv<ROWS>(S, S.Wr, S.W, nr, b);
