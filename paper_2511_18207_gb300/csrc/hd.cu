@@ -377,7 +377,35 @@ __device__ __forceinline__ void hd_maxabs_body(const float* __restrict__ X, cons
   const int64_t tid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x, nth = (int64_t)gridDim.x * blockDim.x;
   float m = 0.f;
   bool bad = false;
-  if ((D & 3) == 0 && (reinterpret_cast<uintptr_t>(X) & 15) == 0) {
+  if ((D & 3) == 0 && D <= 256 && (reinterpret_cast<uintptr_t>(X) & 15) == 0) {
+    // a warp per row, lane l on columns 4l.. and 128 + 4l..; the shift stays
+    // in registers and four rows' loads are in flight (columns past D read as
+    // the shift itself, |x - s| = 0)
+    const int c0 = 4 * lane, c1 = 128 + 4 * lane;
+    const float4 s0 = c0 < D ? make_float4(shift[c0], shift[c0 + 1], shift[c0 + 2], shift[c0 + 3])
+                             : make_float4(0.f, 0.f, 0.f, 0.f);
+    const float4 s1 = c1 < D ? make_float4(shift[c1], shift[c1 + 1], shift[c1 + 2], shift[c1 + 3])
+                             : make_float4(0.f, 0.f, 0.f, 0.f);
+    const int64_t warp = tid >> 5, nwarps = nth >> 5;
+    auto acc = [&](const float4 v, const float4 sv) {
+      bad |= !isfinite(v.x) || !isfinite(v.y) || !isfinite(v.z) || !isfinite(v.w);
+      m = fmaxf(m, fmaxf(fmaxf(fabsf(v.x - sv.x), fabsf(v.y - sv.y)), fmaxf(fabsf(v.z - sv.z), fabsf(v.w - sv.w))));
+    };
+    for (int64_t r = warp; r < n; r += 4 * nwarps) {
+      float4 v[4][2];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int64_t rr = r + u * nwarps;
+        v[u][0] = rr < n && c0 < D ? __ldg(reinterpret_cast<const float4*>(X + rr * D + c0)) : s0;
+        v[u][1] = rr < n && c1 < D ? __ldg(reinterpret_cast<const float4*>(X + rr * D + c1)) : s1;
+      }
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        acc(v[u][0], s0);
+        acc(v[u][1], s1);
+      }
+    }
+  } else if ((D & 3) == 0 && (reinterpret_cast<uintptr_t>(X) & 15) == 0) {
     // element stream in 128-bit loads, independent of the row structure
     const float4* X4 = reinterpret_cast<const float4*>(X);
     const int D4 = D >> 2;
@@ -468,6 +496,85 @@ __device__ __forceinline__ void hd_prep_body(const float* __restrict__ X, const 
   float wmaxn = 0.f, wmaxe = 0.f;
   // a lane's values of the next row are loaded while this row is converted
   // (Dp <= 256: at most 8 values per lane)
+  if ((D & 3) == 0 && (Dp & 3) == 0 && Dp <= 256 && (reinterpret_cast<uintptr_t>(X) & 15) == 0) {
+    // 128-bit loads (lane l: columns 4l.. and 128 + 4l..), two rows ahead in
+    // flight, four rounded values stored as one 8-byte word; per element the
+    // same arithmetic as the scalar form below
+    const int cc[2] = {4 * lane, 128 + 4 * lane};
+    float4 sv[2];
+#pragma unroll
+    for (int h = 0; h < 2; ++h)
+      sv[h] = cc[h] < D ? make_float4(shift[cc[h]], shift[cc[h] + 1], shift[cc[h] + 2], shift[cc[h] + 3])
+                        : make_float4(0.f, 0.f, 0.f, 0.f);
+    auto ld = [&](float4 (&d)[2], int64_t rr) {
+#pragma unroll
+      for (int h = 0; h < 2; ++h)
+        d[h] = rr < n && cc[h] < D ? __ldg(reinterpret_cast<const float4*>(X + rr * D + cc[h]))
+                                   : make_float4(0.f, 0.f, 0.f, 0.f);
+    };
+    float4 xa[2], xb[2], xc[2];
+    ld(xa, warp);
+    ld(xb, warp + nwarps);
+    for (int64_t r = warp; r < n_pad; r += nwarps) {
+      ld(xc, r + 2 * nwarps);
+      T* out = Xt + r * Dp;
+      if (r < n) {
+        float sn = 0.f, se = 0.f, st = 0.f;
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+          const int c = cc[h];
+          if (c >= Dp) continue;
+          __align__(8) T q4[4];
+          const float xs[4] = {xa[h].x, xa[h].y, xa[h].z, xa[h].w};
+          const float ss[4] = {sv[h].x, sv[h].y, sv[h].z, sv[h].w};
+#pragma unroll
+          for (int k = 0; k < 4; ++k) {
+            float hv = 0.f;
+            if (c < D) {  // D % 4 == 0: the four columns are all data or all padding
+              const float t = xs[k] - ss[k];
+              hv = TT::to(TT::from(t * scale));
+              const float rr = t - hv * inv;
+              sn = fmaf(hv, hv, sn);
+              se = fmaf(rr, rr, se);
+              st = fmaf(t, t, st);
+            }
+            q4[k] = TT::from(hv * mult);
+          }
+          *reinterpret_cast<uint2*>(out + c) = *reinterpret_cast<const uint2*>(q4);
+        }
+        sn = __shfl_sync(0xffffffffu, warp_sum(sn), 0);
+        se = warp_sum(se);
+        st = warp_sum(st);
+        if (lane < 8) nparts[r * 8 + lane] = norm_part(sn, side, lane);
+        if (lane == 0) {
+          const float e = 1.001f * (sqrtf(se) + 5.9604645e-8f * sqrtf(st)) + 1e-30f;
+          norm2[r] = sn;
+          eps[r] = e;
+          wmaxn = fmaxf(wmaxn, sqrtf(sn));
+          wmaxe = fmaxf(wmaxe, e);
+        }
+      } else {
+#pragma unroll
+        for (int h = 0; h < 2; ++h)
+          if (cc[h] < Dp) *reinterpret_cast<uint2*>(out + cc[h]) = make_uint2(0u, 0u);
+        if (lane == 0) {
+          norm2[r] = 1e30f;
+          eps[r] = 0.f;
+        }
+        if (lane < 8) nparts[r * 8 + lane] = norm_part(1e30f, side, lane);
+      }
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        xa[h] = xb[h];
+        xb[h] = xc[h];
+      }
+    }
+    if (lane == 0) {
+      atomic_max_nonneg(maxnorm, wmaxn);
+      atomic_max_nonneg(maxeps, wmaxe);
+    }
+    return;
+  }
   float xv[8], xn[8];
   auto load_row = [&](float (&dst)[8], int64_t rr) {
 #pragma unroll

@@ -803,86 +803,139 @@ __global__ void __launch_bounds__(kSiThreads, 1)
                                    max(q.iters, 1), eps, sigma_rel, seed, q.U, q.iters_out);
 }
 
-// FP64 clean-up of the m Ritz vectors (one CTA): classical Gram-Schmidt
-// applied twice against the vectors already cleaned (all of a pass's
-// projections come from one block-wide reduction; two passes orthogonalise
-// to working precision, as modified Gram-Schmidt twice does, with a third of
-// the sequential FP64 reductions), normalisation, sign (largest |entry|
-// positive, lowest index on ties).
-PROHD_DEV void subspace_finalize_body(const double* __restrict__ Uin, int D, int m, double* __restrict__ dirs) {
-  __shared__ double u[kSiMaxD];
-  __shared__ double red[kSiFinThreads / 32][kSiMaxM + 1];
-  __shared__ double dk[kSiMaxM + 1];
-  __shared__ unsigned long long s_best[kSiFinThreads / 32];
-  __shared__ int s_idx;
+// FP64 clean-up of the m Ritz vectors (one CTA of kSiFinThreads threads, D <=
+// kSiFinThreads): Cholesky-QR applied twice in FP64, then the sign rule
+// (largest |entry| positive, lowest index on ties). A pass forms the Gram
+// matrix G = U^T U (each entry summed over kFinSplit row blocks, the blocks
+// added in a fixed order), its Cholesky factor G = L L^T and U <- U L^-T.
+// The Ritz vectors arrive orthonormal to FP32 rounding, so G = I + E with
+// |E| ~ 1e-7: one pass leaves an orthogonality error of about u64 kappa(G)^2
+// and the second removes what rounding of the first left. Q = U R^-1 with R
+// upper triangular and a positive diagonal is the factorisation Gram-Schmidt
+// computes, so the result is the same basis up to FP64 rounding, from a few
+// block-wide steps instead of one reduction per vector and pass. A column
+// whose pivot is not positive (a zero input vector) comes out zero.
+constexpr int kFinSplit = 8;
+
+size_t subspace_finalize_smem(int D, int m) {
+  const size_t np = (size_t)m * (m + 1) / 2;
+  return ((size_t)m * D + (size_t)2 * m * m + np * kFinSplit + m) * sizeof(double);
+}
+
+PROHD_DEV void subspace_finalize_body(const double* __restrict__ Uin, int D, int m, double* __restrict__ dirs,
+                                      double* __restrict__ sm) {
+  double* U = sm;                          // [m][D]: column k of the basis at U + k D
+  double* G = U + (size_t)m * D;           // [m][m] Gram matrix, then L (lower)
+  double* Li = G + m * m;                  // [m][m] L^-1 (lower)
+  double* part = Li + m * m;               // [pairs][kFinSplit] partial sums
+  double* dinv = part + (m * (m + 1) / 2) * kFinSplit;  // [m] 1 / L[j][j] (0: dropped column)
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   constexpr int NW = kSiFinThreads / 32;
-  // dk[0..cnt) = u . dirs[1 + k] for k < cnt (cnt = 0: dk[0] = u . u)
-  auto block_dots = [&](int cnt) {
-    const int nv = cnt > 0 ? cnt : 1;
-    double part[kSiMaxM];
-#pragma unroll
-    for (int k = 0; k < kSiMaxM; ++k) part[k] = 0.0;
-    for (int j = tid; j < D; j += blockDim.x) {
-      const double x = u[j];
-#pragma unroll
-      for (int k = 0; k < kSiMaxM; ++k)
-        if (k < nv) part[k] = fma(x, cnt > 0 ? dirs[(size_t)(k + 1) * D + j] : x, part[k]);
-    }
-#pragma unroll
-    for (int k = 0; k < kSiMaxM; ++k)
-      if (k < nv) {
-        const double v = warp_sum(part[k]);
-        if (lane == 0) red[warp][k] = v;
+  for (int e = tid; e < m * D; e += kSiFinThreads) U[e] = Uin[e];
+  __syncthreads();
+  const int npair = m * (m + 1) / 2;
+  const int rb = (D + kFinSplit - 1) / kFinSplit;
+  for (int pass = 0; pass < 2; ++pass) {
+    // partial sums of G[k][l] (k <= l) over row block s (rows s, s + 8, ...)
+    for (int t = tid; t < npair * kFinSplit; t += kSiFinThreads) {
+      const int pr = t / kFinSplit, s = t - pr * kFinSplit;
+      int k = 0, rem = pr;  // pair index -> (k, l), k <= l, row-major over the upper triangle
+      while (rem >= m - k) {
+        rem -= m - k;
+        ++k;
       }
-    __syncthreads();
-    if (tid < nv) {
-      double t = 0.0;
-      for (int w = 0; w < NW; ++w) t += red[w][tid];
-      dk[tid] = t;
-    }
-    __syncthreads();
-  };
-  for (int l = 0; l < m; ++l) {
-    for (int j = tid; j < D; j += blockDim.x) u[j] = Uin[(size_t)l * D + j];
-    __syncthreads();
-    for (int pass = 0; pass < 2 && l > 0; ++pass) {
-      block_dots(l);
-      for (int j = tid; j < D; j += blockDim.x) {
-        double x = u[j];
-        for (int k = 0; k < l; ++k) x = fma(-dk[k], dirs[(size_t)(k + 1) * D + j], x);
-        u[j] = x;
+      const int l = k + rem;
+      const double* uk = U + (size_t)k * D;
+      const double* ul = U + (size_t)l * D;
+      double acc = 0.0;
+      for (int i = 0; i < rb; ++i) {
+        const int j = s + kFinSplit * i;
+        if (j < D) acc = fma(uk[j], ul[j], acc);
       }
-      __syncthreads();
+      part[t] = acc;
     }
-    block_dots(0);
-    const double nn = dk[0];
-    const double inv = nn > 0.0 ? 1.0 / sqrt(nn) : 0.0;
-    for (int j = tid; j < D; j += blockDim.x) u[j] *= inv;
     __syncthreads();
-    // magnitudes are read back from shared memory in both passes, so the
-    // maximum is always found again
+    for (int pr = tid; pr < npair; pr += kSiFinThreads) {
+      int k = 0, rem = pr;
+      while (rem >= m - k) {
+        rem -= m - k;
+        ++k;
+      }
+      const int l = k + rem;
+      double g = 0.0;
+#pragma unroll
+      for (int s = 0; s < kFinSplit; ++s) g += part[pr * kFinSplit + s];
+      G[k * m + l] = g;
+      G[l * m + k] = g;
+    }
+    __syncthreads();
+    // Cholesky (warp 0, lane i = row i; m <= 24 < 32), then column `lane` of L^-1
+    if (warp == 0) {
+      const int row = lane < m ? lane : m - 1;  // lanes past m shadow the last row, stores masked
+      for (int j = 0; j < m; ++j) {
+        double acc = G[row * m + j];
+        for (int k = 0; k < j; ++k) acc = fma(-G[row * m + k], G[j * m + k], acc);
+        const double piv = __shfl_sync(0xffffffffu, acc, j);
+        const bool ok = piv > 0.0;
+        const double r = ok ? 1.0 / sqrt(piv) : 0.0;
+        __syncwarp();
+        if (lane == j) {
+          G[j * m + j] = ok ? piv * r : 0.0;
+          dinv[j] = r;
+        }
+        if (lane > j && lane < m) G[lane * m + j] = acc * r;
+        __syncwarp();
+      }
+      const int col = lane < m ? lane : m - 1;
+      for (int i = 0; i < m; ++i) {
+        double acc = i == col ? 1.0 : 0.0;
+        for (int k = 0; k < i; ++k) acc = fma(-G[i * m + k], Li[k * m + col], acc);
+        const double x = i >= col ? acc * dinv[i] : 0.0;
+        __syncwarp();
+        if (lane < m) Li[i * m + lane] = x;
+        __syncwarp();
+      }
+    }
+    __syncthreads();
+    // U <- U L^-T, one row per thread: q[c] = sum_{k <= c} U[j][k] Li[c][k]
+    for (int j = tid; j < D; j += kSiFinThreads) {
+      double u[kSiMaxM];
+#pragma unroll
+      for (int k = 0; k < kSiMaxM; ++k) u[k] = k < m ? U[(size_t)k * D + j] : 0.0;
+#pragma unroll
+      for (int c = 0; c < kSiMaxM; ++c) {
+        if (c < m) {
+          double q = 0.0;
+#pragma unroll
+          for (int k = 0; k <= c; ++k) q = fma(u[k], Li[c * m + k], q);
+          U[(size_t)c * D + j] = q;
+        }
+      }
+    }
+    __syncthreads();
+  }
+  // sign: one warp per vector
+  for (int c = warp; c < m; c += NW) {
+    const double* uc = U + (size_t)c * D;
     unsigned long long best = 0ull;
-    for (int j = tid; j < D; j += blockDim.x) {
-      const unsigned long long mag = (unsigned long long)__double_as_longlong(fabs(u[j]));
-      best = mag > best ? mag : best;
+    int bi = D;
+    for (int j = lane; j < D; j += 32) {  // ascending j: a tie keeps the lower index
+      const unsigned long long mag = (unsigned long long)__double_as_longlong(fabs(uc[j]));
+      if (bi == D || mag > best) {
+        best = mag;
+        bi = j;
+      }
     }
-    best = warp_max_u64(best);
-    if (lane == 0) s_best[warp] = best;
-    __syncthreads();
-    if (tid == 0) {
-      unsigned long long bb = 0ull;
-      for (int w = 0; w < NW; ++w) bb = s_best[w] > bb ? s_best[w] : bb;
-      s_best[0] = bb;
-      s_idx = D;
+    for (int o = 16; o > 0; o >>= 1) {
+      const unsigned long long ob = __shfl_xor_sync(0xffffffffu, best, o);
+      const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+      if (ob > best || (ob == best && oi < bi)) {
+        best = ob;
+        bi = oi;
+      }
     }
-    __syncthreads();
-    for (int j = tid; j < D; j += blockDim.x)
-      if ((unsigned long long)__double_as_longlong(fabs(u[j])) == s_best[0]) atomicMin(&s_idx, j);
-    __syncthreads();
-    const double sgn = u[min(s_idx, D - 1)] < 0.0 ? -1.0 : 1.0;
-    for (int j = tid; j < D; j += blockDim.x) dirs[(size_t)(l + 1) * D + j] = sgn * u[j];
-    __syncthreads();
+    const double sgn = uc[min(bi, D - 1)] < 0.0 ? -1.0 : 1.0;
+    for (int j = lane; j < D; j += 32) dirs[(size_t)(c + 1) * D + j] = sgn * uc[j];
   }
 }
 
@@ -912,8 +965,10 @@ PROHD_DEV void rayleigh_sum_body(const double* __restrict__ part, int D, int m, 
   }
 }
 
-__global__ void subspace_finalize_kernel(const double* __restrict__ Uin, int D, int m, double* __restrict__ dirs) {
-  subspace_finalize_body(Uin, D, m, dirs);
+__global__ void __launch_bounds__(kSiFinThreads)
+    subspace_finalize_kernel(const double* __restrict__ Uin, int D, int m, double* __restrict__ dirs) {
+  extern __shared__ double fin_sm[];
+  subspace_finalize_body(Uin, D, m, dirs, fin_sm);
 }
 __global__ void rayleigh_rows_kernel(const double* __restrict__ C64, const double* __restrict__ dirs, int D, int m,
                                      double* __restrict__ part) {
@@ -924,9 +979,10 @@ __global__ void rayleigh_sum_kernel(const double* __restrict__ part, int D, int 
 }
 
 // Batched forms: one block (finalize, sums) or one grid row (row partials) per pair.
-__global__ void subspace_finalize_batched_kernel(const BPair* __restrict__ P) {
+__global__ void __launch_bounds__(kSiFinThreads) subspace_finalize_batched_kernel(const BPair* __restrict__ P) {
+  extern __shared__ double fin_sm[];
   const BPair& q = P[blockIdx.x];
-  if (q.m >= 1) subspace_finalize_body(q.U, q.D, q.m, q.dirs);
+  if (q.m >= 1) subspace_finalize_body(q.U, q.D, q.m, q.dirs, fin_sm);
 }
 __global__ void rayleigh_rows_batched_kernel(const BPair* __restrict__ P) {
   const BPair& q = P[blockIdx.y];
@@ -955,8 +1011,11 @@ cudaError_t subspace_run(prohd_ctx* ctx, const float* C32, const double* C64, in
   subspace_kernel<<<kSiCTAs, kSiThreads, smem, st>>>(C32, D, m, b, std::max(max_iters, 1), eps, 0.01f, seed, Uout,
                                                      nullptr);
   if ((e = cudaGetLastError())) return e;
+  const size_t fsm = subspace_finalize_smem(D, m);
+  if ((e = cudaFuncSetAttribute(subspace_finalize_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fsm)))
+    return e;
   count_launch();
-  subspace_finalize_kernel<<<1, kSiFinThreads, 0, st>>>(Uout, D, m, dirs);
+  subspace_finalize_kernel<<<1, kSiFinThreads, fsm, st>>>(Uout, D, m, dirs);
   if (eig) {
     count_launch();
     rayleigh_rows_kernel<<<(D + 7) / 8, 256, 0, st>>>(C64, dirs, D, m, part);
@@ -991,8 +1050,12 @@ cudaError_t subspace_batched(const BPair* P, const int* const cls_pairs[3], cons
 
 cudaError_t subspace_batched_finish(const BPair* P, int npairs, int Dmax, int mmax, cudaStream_t st) {
   if (mmax < 1) return cudaSuccess;
+  const size_t fsm = subspace_finalize_smem(Dmax, mmax);
+  cudaError_t e =
+      cudaFuncSetAttribute(subspace_finalize_batched_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fsm);
+  if (e) return e;
   count_launch();
-  subspace_finalize_batched_kernel<<<npairs, kSiFinThreads, 0, st>>>(P);
+  subspace_finalize_batched_kernel<<<npairs, kSiFinThreads, fsm, st>>>(P);
   count_launch();
   rayleigh_rows_batched_kernel<<<dim3((Dmax + 7) / 8, npairs), 256, 0, st>>>(P);
   count_launch();
