@@ -82,7 +82,8 @@ typedef struct prohd_ctx prohd_ctx;
  *                   each selected point against the whole other set. It never
  *                   exceeds H(A, B) (the selected points are points of A and B),
  *                   at the cost of two subset-vs-set contractions
- *                   (prohd_estimate / prohd_estimate_dirs / prohd_estimate_host)
+ *                   (prohd_estimate / prohd_estimate_dirs / prohd_estimate_host,
+ *                   and batched plans)
  *   wait_timeout_ns  limit of every bounded device wait (default 4e9 ns)
  */
 typedef struct {
@@ -324,7 +325,8 @@ typedef enum {
   PROHD_PH_GATHER = 4,    /* subset gather (two launches) */
   PROHD_PH_HD_PREP = 5,   /* centring, scale, rounded copies (several) */
   PROHD_PH_HD_CONTRACT = 6, /* the distance contraction: hd_tc_kernel, or the FP32 tile kernel */
-  PROHD_PH_HD_RESCORE = 7,  /* margins, candidate rescoring, FP64 witnesses (several) */
+  PROHD_PH_HD_RESCORE = 7,  /* margins, candidate rescoring, FP64 witnesses (several);
+                               batched plans: the one-sided refinement */
   PROHD_PH_COUNT = 8
 } prohd_phase;
 
@@ -371,7 +373,11 @@ size_t prohd_batch_workspace_size(const prohd_pair_desc* pairs, int npairs, cons
  * size above; owned by the caller and bound to the plan until it is
  * destroyed), encodes the tensor maps and uploads the tables. Planning
  * synchronises the device (synchronous copies); running does not.
- * params.refine must be 0 (PROHD_ENOTSUP otherwise). */
+ * params.refine = 1 adds, per pair, the one-sided refinement: the selected
+ * rows of each set against the whole other set, run as two more row-set
+ * pairs through the subset-distance stage; the workspace then also holds
+ * their rounded copies (tensor precisions: about 2 (nA + nB) Dp 2 bytes per
+ * pair). refine must be 0 or 1 (PROHD_EINVAL otherwise). */
 prohd_status prohd_batch_plan(prohd_ctx* ctx, const prohd_pair_desc* pairs, int npairs, const prohd_params* p,
                               void* ws, size_t ws_bytes, prohd_batch** out);
 void prohd_batch_destroy(prohd_batch* b);

@@ -79,6 +79,16 @@ struct BatchLayout {
   size_t slot_bytes;
   // per-pair regions (filled into the BPair table)
   std::vector<BPair> hp;
+  // one-sided refinement (params.refine = 1): per pair two virtual pairs, the
+  // selected rows of one set against the whole other set (v = 2 i: A_sel vs
+  // B; v = 2 i + 1: B_sel vs A), run through the subset-distance stage
+  BPair* R = nullptr;
+  int* rorder = nullptr;
+  int64_t* rprefix = nullptr;
+  int64_t* rn = nullptr;         // [2 np][2]: selected rows (set at run time), columns
+  prohd_result* rout = nullptr;  // [2 np]
+  unsigned long long* rticket = nullptr;
+  std::vector<BPair> hr;
   size_t end;
 };
 
@@ -86,8 +96,8 @@ struct BatchLayout {
 int64_t items_for(int64_t n, int pts) { return ceil_div(n, pts); }
 
 // Upper bounds of the tables that depend on the tunables.
-void table_caps(const std::vector<PairPlan>& pp, bool tensor, int64_t& max_items, int64_t& max_pitems,
-                size_t& slot_cap, int& nmaps) {
+void table_caps(const std::vector<PairPlan>& pp, bool tensor, bool refine, int64_t& max_items,
+                int64_t& max_pitems, size_t& slot_cap, int& nmaps) {
   max_items = 0;
   max_pitems = 0;
   slot_cap = 0;
@@ -98,16 +108,37 @@ void table_caps(const std::vector<PairPlan>& pp, bool tensor, int64_t& max_items
     slot_cap += (size_t)ni * gram_tc_item_slot_bytes(q.Dp);
     nmaps += 2;
     max_pitems += items_for(q.nA, kMinProjRows) + items_for(q.nB, kMinProjRows);
-    if (tensor) nmaps += 4;  // subset distance: A, B and their norm operands
+    if (tensor) nmaps += refine ? 12 : 4;  // subset distance: A, B and their norm operands (x3 refined)
   }
 }
 
-void batch_layout(Arena& a, const std::vector<PairPlan>& pp, const prohd_pair_desc* pairs, bool tensor, BatchLayout& L) {
+// Buffers of one contraction of `rows` (at most) rows against `cols` columns
+// on the tensor-core path, as the subset-distance stage reads them.
+void hd_bufs(Arena& a, BPair& b, int64_t rows, int64_t cols, int D, int Dp) {
+  b.hd_nA_pad = round_up(rows, 128);
+  b.hd_nB_pad = round_up(cols, 256);
+  b.hd_At = a.take<uint16_t>((size_t)b.hd_nA_pad * Dp, 1024);
+  b.hd_Bt = a.take<uint16_t>((size_t)b.hd_nB_pad * Dp, 1024);
+  b.hd_nA8 = a.take<float>((size_t)b.hd_nA_pad * 8, 1024);
+  b.hd_nB8 = a.take<float>((size_t)b.hd_nB_pad * 8, 1024);
+  b.hd_nA2 = a.take<float>((size_t)b.hd_nA_pad);
+  b.hd_nB2 = a.take<float>((size_t)b.hd_nB_pad);
+  b.hd_epsA = a.take<float>((size_t)b.hd_nA_pad);
+  b.hd_epsB = a.take<float>((size_t)b.hd_nB_pad);
+  b.hd_rowmin = a.take<float>((size_t)b.hd_nA_pad);
+  b.hd_candA = a.take<int32_t>((size_t)rows);
+  b.hd_candB = a.take<int32_t>((size_t)cols);
+  b.hd_shift = a.take<float>((size_t)D);
+  b.hd_spart = a.take<double>((size_t)16 * D);
+}
+
+void batch_layout(Arena& a, const std::vector<PairPlan>& pp, const prohd_pair_desc* pairs, bool tensor, bool refine,
+                  BatchLayout& L) {
   const int np = (int)pp.size();
   int64_t max_items, max_pitems;
   size_t slot_cap;
   int nmaps;
-  table_caps(pp, tensor, max_items, max_pitems, slot_cap, nmaps);
+  table_caps(pp, tensor, refine, max_items, max_pitems, slot_cap, nmaps);
   int64_t nprob = 0;
   for (const auto& q : pp) nprob += 2 * q.nd;
 
@@ -161,24 +192,36 @@ void batch_layout(Arena& a, const std::vector<PairPlan>& pp, const prohd_pair_de
     b.offsets = a.take<int64_t>((size_t)b.nblkA + b.nblkB);
     b.As = a.take<float>((size_t)q.boundA * q.D);
     b.Bs = a.take<float>((size_t)q.boundB * q.D);
-    if (tensor) {
-      // tensor-core subset distance: 16-bit copies padded to whole tiles
-      b.hd_nA_pad = round_up(q.boundA, 128);
-      b.hd_nB_pad = round_up(q.boundB, 256);
-      b.hd_At = a.take<uint16_t>((size_t)b.hd_nA_pad * q.Dp, 1024);
-      b.hd_Bt = a.take<uint16_t>((size_t)b.hd_nB_pad * q.Dp, 1024);
-      b.hd_nA8 = a.take<float>((size_t)b.hd_nA_pad * 8, 1024);
-      b.hd_nB8 = a.take<float>((size_t)b.hd_nB_pad * 8, 1024);
-      b.hd_nA2 = a.take<float>((size_t)b.hd_nA_pad);
-      b.hd_nB2 = a.take<float>((size_t)b.hd_nB_pad);
-      b.hd_epsA = a.take<float>((size_t)b.hd_nA_pad);
-      b.hd_epsB = a.take<float>((size_t)b.hd_nB_pad);
-      b.hd_rowmin = a.take<float>((size_t)b.hd_nA_pad);
-      b.hd_candA = a.take<int32_t>((size_t)q.boundA);
-      b.hd_candB = a.take<int32_t>((size_t)q.boundB);
-      b.hd_shift = a.take<float>((size_t)q.D);
-      b.hd_spart = a.take<double>((size_t)16 * q.D);
-    }
+    // tensor-core subset distance: 16-bit copies padded to whole tiles
+    if (tensor) hd_bufs(a, b, q.boundA, q.boundB, q.D, q.Dp);
+  }
+  L.hr.clear();
+  if (refine) {
+    L.R = a.take<BPair>((size_t)2 * np);
+    L.rorder = a.take<int>((size_t)2 * np);
+    L.rprefix = a.take<int64_t>((size_t)2 * np + 1);
+    L.rn = a.take<int64_t>((size_t)4 * np);
+    L.rout = a.take<prohd_result>((size_t)2 * np);
+    L.hr.assign((size_t)2 * np, BPair{});
+    for (int i = 0; i < np; ++i)
+      for (int s = 0; s < 2; ++s) {
+        const PairPlan& q = pp[i];
+        const BPair& bp = L.hp[i];
+        BPair& r = L.hr[(size_t)2 * i + s];
+        const int64_t rows = s ? q.boundB : q.boundA, cols = s ? q.nA : q.nB;
+        r.D = q.D;
+        r.Dp = q.Dp;
+        r.nA = rows;
+        r.nB = cols;
+        r.As = s ? bp.Bs : bp.As;
+        // the subset-distance stage only reads Bs
+        r.Bs = pairs ? const_cast<float*>(s ? pairs[i].A : pairs[i].B) : nullptr;
+        r.nsel = L.rn ? L.rn + (size_t)4 * i + 2 * s : nullptr;
+        r.idxA = s ? bp.idxB : bp.idxA;
+        r.idxB = nullptr;  // columns are rows of the whole set
+        r.out = L.rout ? L.rout + (size_t)2 * i + s : nullptr;
+        if (tensor) hd_bufs(a, r, rows, cols, q.D, q.Dp);
+      }
   }
   // band lists (any size up to the set's)
   L.end = 0;
@@ -188,6 +231,7 @@ void batch_layout(Arena& a, const std::vector<PairPlan>& pp, const prohd_pair_de
   const size_t z0 = a.off;
   L.gticket = a.take<int>(1, 16);
   L.hticket = a.take<unsigned long long>(1, 16);
+  L.rticket = a.take<unsigned long long>(1, 16);
   L.bstatus = a.take<int>(1, 16);
   for (int i = 0; i < np; ++i) {
     BPair& b = L.hp[i];
@@ -196,6 +240,8 @@ void batch_layout(Arena& a, const std::vector<PairPlan>& pp, const prohd_pair_de
     b.maxnorm = a.take<float>(2, 16);
     if (tensor) b.hd_sc = a.take<char>(hd_scalars_bytes(), 16);
   }
+  for (auto& r : L.hr)
+    if (tensor) r.hd_sc = a.take<char>(hd_scalars_bytes(), 16);
   for (int i = 0; i < np; ++i) {
     BPair& b = L.hp[i];
     b.maskA = a.take<uint8_t>((size_t)pp[i].nA, 16);
@@ -211,14 +257,22 @@ void batch_layout(Arena& a, const std::vector<PairPlan>& pp, const prohd_pair_de
     b.bestA = a.take<unsigned long long>((size_t)pp[i].boundA, 16);
     b.bestB = a.take<unsigned long long>((size_t)pp[i].boundB, 16);
   }
+  for (auto& r : L.hr) {
+    r.bestA = a.take<unsigned long long>((size_t)r.nA, 16);
+    r.bestB = a.take<unsigned long long>((size_t)r.nB, 16);
+  }
   a.off = round_up(a.off, 256);
   L.ones_bytes = a.off - o0;
   // column minima of the contraction, +inf (as bits) every run
   L.colmin_base = a.base ? reinterpret_cast<unsigned*>(a.base + a.off) : nullptr;
   const size_t c0 = a.off;
-  if (tensor)
+  if (tensor) {
     for (int i = 0; i < np; ++i) L.hp[i].hd_colmin = a.take<unsigned>((size_t)L.hp[i].hd_nB_pad, 4);
+    for (auto& r : L.hr) r.hd_colmin = a.take<unsigned>((size_t)r.hd_nB_pad, 4);
+  }
   L.colmin_count = (int64_t)((a.off - c0) / sizeof(unsigned));
+  // the virtual pairs report into their pair's status word
+  for (size_t v = 0; v < L.hr.size(); ++v) L.hr[v].status = L.hp[v / 2].status;
 }
 
 // Band lists per selection problem and side, n entries each (a band can hold
@@ -252,7 +306,7 @@ prohd_status check_batch(prohd_ctx* ctx, const prohd_pair_desc* pairs, int npair
   if (p->power_max_iters < 1) return bfail(ctx, PROHD_EINVAL, "power_max_iters must be >= 1");
   if (p->precision != PROHD_FP32 && p->precision != PROHD_FP16 && p->precision != PROHD_BF16)
     return bfail(ctx, PROHD_EINVAL, "unknown precision");
-  if (p->refine != 0) return bfail(ctx, PROHD_ENOTSUP, "the one-sided refinement is not batched; use prohd_estimate");
+  if (p->refine != 0 && p->refine != 1) return bfail(ctx, PROHD_EINVAL, "refine must be 0 or 1");
   pp.resize((size_t)npairs);
   int64_t nprob = 0;
   for (int i = 0; i < npairs; ++i) {
@@ -295,6 +349,39 @@ __global__ void finish_batched_kernel(const BPair* __restrict__ P, int npairs, c
   q.out->nsel_b = q.nsel[1];
   const int bs = *bstatus;
   if (bs > q.out->hd.status) q.out->hd.status = bs;
+}
+
+// Row counts of the refinement's virtual pairs: v = 2 i + s takes the size of
+// set s's selection of pair i.
+__global__ void refine_rows_batched_kernel(const BPair* __restrict__ P, int64_t* __restrict__ rn, int nv) {
+  const int v = blockIdx.x * blockDim.x + threadIdx.x;
+  if (v < nv) rn[2 * v] = P[v >> 1].nsel[v & 1];
+}
+
+// h(A_sel, B) from virtual pair 2 i and h(B_sel, A) from 2 i + 1 (each as its
+// rows' directed distance) into pair i's result.
+__global__ void refine_combine_batched_kernel(const BPair* __restrict__ P, const prohd_result* __restrict__ rout,
+                                              int npairs) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= npairs) return;
+  const prohd_hd_result a = rout[2 * i].hd, c = rout[2 * i + 1].hd;
+  prohd_hd_result& o = P[i].out->hd;
+  prohd_hd_result r;
+  r.h_ab = a.h_ab;
+  r.h_ba = c.h_ab;
+  r.ab_a = a.ab_a;
+  r.ab_b = a.ab_b;
+  r.ba_b = c.ab_a;
+  r.ba_a = c.ab_b;
+  r.dir = r.h_ab >= r.h_ba ? 0 : 1;
+  r.H = r.dir == 0 ? r.h_ab : r.h_ba;
+  r.wit_a = r.dir == 0 ? r.ab_a : r.ba_a;
+  r.wit_b = r.dir == 0 ? r.ab_b : r.ba_b;
+  r.status = max(max(a.status, c.status), o.status);
+  r.H_lowp = fmax(a.H_lowp, c.H_lowp);
+  r.n_rescored_a = a.n_rescored_a;
+  r.n_rescored_b = c.n_rescored_a;
+  o = r;
 }
 
 __global__ void set_out_kernel(BPair* __restrict__ P, int npairs, prohd_result* out) {
@@ -363,8 +450,8 @@ prohd_status write_tables(prohd_batch* b) {
   if (b->tensor) {
     const CUtensorMapDataType dt =
         b->p.precision == PROHD_BF16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT16;
-    for (int i = 0; i < np; ++i) {
-      BPair& q = L.hp[i];
+    for (size_t i = 0; i < (size_t)np + L.hr.size(); ++i) {
+      BPair& q = i < (size_t)np ? L.hp[i] : L.hr[i - np];
       CUtensorMap m[4];
       const uint64_t Dp = (uint64_t)q.Dp;
       if (!encode_2d(ctx, &m[0], dt, q.hd_At, Dp, (uint64_t)q.hd_nA_pad, Dp * 2, 64, 128, CU_TENSOR_MAP_SWIZZLE_128B) ||
@@ -501,6 +588,14 @@ prohd_status write_tables(prohd_batch* b) {
   std::stable_sort(order.begin(), order.end(), [&](int x, int y) {
     return pp[x].boundA * pp[x].boundB * pp[x].D > pp[y].boundA * pp[y].boundB * pp[y].D;
   });
+  // refinement: virtual pairs largest first; their column counts are fixed
+  std::vector<int> rorder(L.hr.size());
+  std::vector<int64_t> rn(L.hr.size() * 2, 0);
+  std::iota(rorder.begin(), rorder.end(), 0);
+  std::stable_sort(rorder.begin(), rorder.end(), [&](int x, int y) {
+    return L.hr[x].nA * L.hr[x].nB * L.hr[x].D > L.hr[y].nA * L.hr[y].nB * L.hr[y].D;
+  });
+  for (size_t v = 0; v < L.hr.size(); ++v) rn[2 * v + 1] = L.hr[v].nB;
   for (int i = 0; i < np; ++i) {
     L.hp[i].iters = b->p.power_max_iters;
     L.hp[i].out = nullptr;
@@ -518,6 +613,11 @@ prohd_status write_tables(prohd_batch* b) {
   up(L.probs, probs.data(), probs.size());
   up(L.alpha_of, alpha_of.data(), sizeof(double) * alpha_of.size());
   up(L.order, order.data(), sizeof(int) * order.size());
+  if (!L.hr.empty()) {
+    up(L.R, L.hr.data(), sizeof(BPair) * L.hr.size());
+    up(L.rorder, rorder.data(), sizeof(int) * rorder.size());
+    up(L.rn, rn.data(), sizeof(int64_t) * rn.size());
+  }
   up(L.cls, cls.data(), sizeof(int) * cls.size());
   if (e) {
     ctx->err = std::string("CUDA error while planning the batch: ") + cudaGetErrorString(e);
@@ -589,15 +689,37 @@ cudaError_t enqueue(prohd_batch* b, prohd_result* out, cudaStream_t st) {
       return e;
     }
   }
+  if (!L.hr.empty()) {
+    // one-sided refinement: the selected rows of each set against the whole
+    // other set, as 2 np virtual pairs through the same stage, then per pair
+    // h(A_sel, B) and h(B_sel, A) into its result
+    PhaseTimer pt(ctx, PROHD_PH_HD_RESCORE, st);
+    const int nv = 2 * np;
+    count_launch();
+    refine_rows_batched_kernel<<<(nv + 255) / 256, 256, 0, st>>>(L.P, L.rn, nv);
+    if ((e = cudaGetLastError())) return e;
+    if (b->tensor) {
+      // the column side holds whole sets: blocks per set for about 1,024 rows each
+      const int bx = (int)std::min<int64_t>(128, std::max<int64_t>(4, ceil_div(b->nmax, 1024)));
+      if ((e = hd_tc_batched(L.R, L.rorder, nv, L.rprefix, L.maps, b->Dmax, b->p.precision == PROHD_BF16 ? 1 : 0,
+                             L.bstatus, ctx->num_sms, b->p.wait_timeout_ns, st, bx)))
+        return e;
+    } else if ((e = hd_simt_batched(L.R, L.rorder, nv, L.rprefix, L.rticket, ctx->num_sms, st))) {
+      return e;
+    }
+    count_launch();
+    refine_combine_batched_kernel<<<(np + 255) / 256, 256, 0, st>>>(L.P, L.rout, np);
+    if ((e = cudaGetLastError())) return e;
+  }
   count_launch();
   finish_batched_kernel<<<(np + 255) / 256, 256, 0, st>>>(L.P, np, L.bstatus);
   return cudaGetLastError();
 }
 
-size_t batch_bytes(const std::vector<PairPlan>& pp, bool tensor) {
+size_t batch_bytes(const std::vector<PairPlan>& pp, bool tensor, bool refine) {
   Arena a;
   BatchLayout L;
-  batch_layout(a, pp, nullptr, tensor, L);
+  batch_layout(a, pp, nullptr, tensor, refine, L);
   std::vector<int32_t*> band;
   std::vector<uint64_t*> bkey;
   band_layout(a, pp, band, bkey);
@@ -611,7 +733,7 @@ extern "C" {
 size_t prohd_batch_workspace_size(const prohd_pair_desc* pairs, int npairs, const prohd_params* p) {
   std::vector<PairPlan> pp;
   if (check_batch(nullptr, pairs, npairs, p, pp) != PROHD_OK) return 0;
-  return batch_bytes(pp, p->precision != PROHD_FP32);
+  return batch_bytes(pp, p->precision != PROHD_FP32, p->refine == 1);
 }
 
 prohd_status prohd_batch_plan(prohd_ctx* ctx, const prohd_pair_desc* pairs, int npairs, const prohd_params* p,
@@ -625,7 +747,8 @@ prohd_status prohd_batch_plan(prohd_ctx* ctx, const prohd_pair_desc* pairs, int 
   if (ctx->num_sms > kMaxSms) return bfail(ctx, PROHD_ENOTSUP, "more SMs than this build sizes for");
   if (!ws || (reinterpret_cast<uintptr_t>(ws) & 255)) return bfail(ctx, PROHD_EINVAL, "workspace must be 256-byte aligned");
   const bool tensor = p->precision != PROHD_FP32;
-  if (ws_bytes < batch_bytes(pp, tensor)) return bfail(ctx, PROHD_ENOMEM, "workspace too small for the batch");
+  if (ws_bytes < batch_bytes(pp, tensor, p->refine == 1))
+    return bfail(ctx, PROHD_ENOMEM, "workspace too small for the batch");
   prohd_batch* b = new (std::nothrow) prohd_batch();
   if (!b) return PROHD_ENOMEM;
   b->ctx = ctx;
@@ -640,7 +763,7 @@ prohd_status prohd_batch_plan(prohd_ctx* ctx, const prohd_pair_desc* pairs, int 
   a.base = b->ws;
   a.cap = ws_bytes;
   b->tensor = tensor;
-  batch_layout(a, pp, pairs, tensor, b->L);
+  batch_layout(a, pp, pairs, tensor, p->refine == 1, b->L);
   b->L.end = a.off;
   for (const auto& q : pp) {
     b->Dmax = std::max(b->Dmax, q.D);

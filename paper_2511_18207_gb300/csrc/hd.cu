@@ -2204,17 +2204,18 @@ __global__ void hd_finalize_tc_batched_kernel(const BPair* __restrict__ P) {
 }
 
 cudaError_t hd_tc_batched(const BPair* P, const int* order, int npairs, int64_t* prefix, const CUtensorMap* maps,
-                          int Dmax, int bf16, int* batch_status, int num_sms, int64_t timeout_ns, cudaStream_t st) {
+                          int Dmax, int bf16, int* batch_status, int num_sms, int64_t timeout_ns, cudaStream_t st,
+                          int bx) {
   const int Dp_max = (int)round_up(Dmax, kTcBK), KBmax = Dp_max / kTcBK;
   cudaError_t e;
   count_launch(5);
   hd_colsum_batched_kernel<<<dim3((Dmax + 31) / 32, 8, 2 * npairs), 256, 0, st>>>(P);
   hd_shift_batched_kernel<<<dim3((Dmax + 255) / 256, npairs), 256, 0, st>>>(P);
-  hd_maxabs_batched_kernel<<<dim3(4, 2 * npairs), 256, 0, st>>>(P);
+  hd_maxabs_batched_kernel<<<dim3(bx, 2 * npairs), 256, 0, st>>>(P);
   if (bf16)
-    hd_prep_batched_kernel<1><<<dim3(4, 2 * npairs), 256, 0, st>>>(P);
+    hd_prep_batched_kernel<1><<<dim3(bx, 2 * npairs), 256, 0, st>>>(P);
   else
-    hd_prep_batched_kernel<0><<<dim3(4, 2 * npairs), 256, 0, st>>>(P);
+    hd_prep_batched_kernel<0><<<dim3(bx, 2 * npairs), 256, 0, st>>>(P);
   hd_tile_scan_kernel<<<1, 1024, 0, st>>>(P, order, npairs, prefix, 1);
   if ((e = cudaGetLastError())) return e;
   const size_t smem = tc_smem_bytes(KBmax);
@@ -2233,8 +2234,8 @@ cudaError_t hd_tc_batched(const BPair* P, const int* order, int npairs, int64_t*
   const size_t fsm = (size_t)kFewRows * 256 * sizeof(float) + (size_t)8 * kFewRows * sizeof(unsigned long long);
   cudaFuncSetAttribute(rescore_few_batched_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fsm);
   count_launch(5);
-  hd_bounds_batched_kernel<<<dim3(4, npairs), 256, 0, st>>>(P);
-  hd_flag_batched_kernel<<<dim3(4, npairs), 256, 0, st>>>(P);
+  hd_bounds_batched_kernel<<<dim3(bx, npairs), 256, 0, st>>>(P);
+  hd_flag_batched_kernel<<<dim3(bx, npairs), 256, 0, st>>>(P);
   rescore_few_batched_kernel<<<dim3(8, 2 * npairs), 256, fsm, st>>>(P);
   rescore_list_batched_kernel<<<dim3(8, 2 * npairs), 256, 0, st>>>(P);
   hd_finalize_tc_batched_kernel<<<npairs, 1024, 0, st>>>(P);

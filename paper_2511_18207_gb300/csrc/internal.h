@@ -279,9 +279,11 @@ cudaError_t compact_gather_batched(const BPair* P, int npairs, int nblk_max, int
 size_t hd_scalars_bytes();
 size_t hd_tc_row_block();   // rows of A per contraction item (128)
 // Tensor-core subset HD of every pair: prep, contraction over (pair, row block)
-// items, margins, FP32 rescoring of candidates, FP64 witnesses.
+// items, margins, FP32 rescoring of candidates, FP64 witnesses. `bx` blocks
+// per (pair, set) run the passes over rows (the largest set's rows decide).
 cudaError_t hd_tc_batched(const BPair* P, const int* order, int npairs, int64_t* prefix, const CUtensorMap* maps,
-                          int Dmax, int bf16, int* batch_status, int num_sms, int64_t timeout_ns, cudaStream_t st);
+                          int Dmax, int bf16, int* batch_status, int num_sms, int64_t timeout_ns, cudaStream_t st,
+                          int bx = 4);
 cudaError_t fill_u32_region(unsigned* p, int64_t n, unsigned v, int num_sms, cudaStream_t st);
 cudaError_t hd_simt_batched(const BPair* P, const int* order, int npairs, int64_t* prefix, unsigned long long* ticket,
                             int num_sms, cudaStream_t st);

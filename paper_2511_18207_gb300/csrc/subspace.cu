@@ -32,9 +32,9 @@
 // every CTA sums the exchanged partials in the same order and repeats the
 // small dense work (Jacobi, Cholesky), so all CTAs take the same decisions.
 // C V accumulates 8-term FFMA blocks with error-free (TwoSum) addition of the
-// blocks. The m Ritz vectors are then orthonormalised in FP64 (modified
-// Gram-Schmidt, twice), normalised, signed (largest |entry| positive, lowest
-// index on ties) and their Rayleigh quotients taken with the FP64 C.
+// blocks. The m Ritz vectors are then orthonormalised in FP64 (Cholesky-QR,
+// twice), signed (largest |entry| positive, lowest index on ties) and their
+// Rayleigh quotients taken with the FP64 C.
 #include <algorithm>
 #include <cmath>
 

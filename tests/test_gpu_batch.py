@@ -214,6 +214,57 @@ def test_batch_rejects_bad_pairs():
     A = dev(np.zeros((10, 16), np.float32))
     with pytest.raises(prohd.ProHDError, match="ENOTSUP"):
         prohd.Batch(ctx(), [(A, A)], m=30, alpha_c=0.1)
-    with pytest.raises(prohd.ProHDError, match="ENOTSUP"):
-        prohd.Batch(ctx(), [(A, A)], m=2, alpha_c=0.1, refine=1)
+    with pytest.raises(prohd.ProHDError, match="EINVAL"):
+        prohd.Batch(ctx(), [(A, A)], m=2, alpha_c=0.1, refine=2)
     torch.cuda.synchronize()
+
+
+@pytest.mark.parametrize("precision", ["fp16", "bf16", "fp32"])
+def test_batch_refined_matches_oracle_per_pair(precision):
+    # params.refine = 1 in a batch: per pair max(h(A_sel, B), h(B_sel, A))
+    # over the batch's own candidate sets, each within 1e-5 of the oracle's
+    # refinement of those sets; the witness is a selected point at distance
+    # H1 (FP64); H1 never exceeds the exact H of the pair; the candidate sets
+    # are those of the plain batch
+    spec = SPEC[:3] + [(1, 5, 64), (300, 20_000, 256), (2000, 3000, 8), (1500, 60_000, 96)]
+    pairs = _pairs(spec, seed=13)
+    torch = torch_cuda()
+    dpairs = [(dev(A), dev(B)) for A, B in pairs]
+    b0 = prohd.Batch(ctx(), dpairs, m=8, alpha_c=0.01, precision=precision)
+    b0.run()
+    b1 = prohd.Batch(ctx(), dpairs, m=8, alpha_c=0.01, precision=precision, refine=1)
+    b1.run()
+    torch.cuda.synchronize()
+    for i, ((A, B), r0, r) in enumerate(zip(pairs, b0.results(), b1.results())):
+        assert r["status"] == "OK", (i, r["status"])
+        assert (r["nsel_a"], r["nsel_b"]) == (r0["nsel_a"], r0["nsel_b"])
+        _, ia, ib = b1.pair_outputs(i, r["nsel_a"], r["nsel_b"])
+        _, ia0, ib0 = b0.pair_outputs(i, r0["nsel_a"], r0["nsel_b"])
+        np.testing.assert_array_equal(ia, ia0)
+        np.testing.assert_array_equal(ib, ib0)
+        o = oracle.refined(A, B, ia, ib)
+        assert rel(r["h_ab"], o["h_ab"]) <= 1e-5, (i, r["h_ab"], o["h_ab"])
+        assert rel(r["h_ba"], o["h_ba"]) <= 1e-5, (i, r["h_ba"], o["h_ba"])
+        assert rel(r["H"], o["H1"]) <= 1e-5, (i, r["H"], o["H1"])
+        d = np.sqrt(((A[r["wit_a"]].astype(np.float64) - B[r["wit_b"]]) ** 2).sum())
+        assert d == pytest.approx(r["H"], rel=1e-12)
+        sel = set(ia.tolist()) if r["dir"] == 0 else set(ib.tolist())
+        assert (r["wit_a"] if r["dir"] == 0 else r["wit_b"]) in sel
+        if A.shape[0] * B.shape[0] <= 2e7:
+            assert r["H"] <= oracle.hausdorff(A, B)["H"] * (1 + 1e-6)
+
+
+def test_batch_refined_graph_replay_is_deterministic():
+    pairs = _pairs(SPEC[:4], seed=17)
+    torch = torch_cuda()
+    dpairs = [(dev(A), dev(B)) for A, B in pairs]
+    b = prohd.Batch(ctx(), dpairs, m=8, alpha_c=0.01, refine=1)
+    b.use_graph(False)
+    b.run()
+    torch.cuda.synchronize()
+    r0 = b.results()
+    b.use_graph(True)
+    for _ in range(2):
+        b.run()
+    torch.cuda.synchronize()
+    assert b.results() == r0
