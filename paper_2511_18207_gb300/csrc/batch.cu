@@ -171,6 +171,7 @@ void batch_layout(Arena& a, const std::vector<PairPlan>& pp, const prohd_pair_de
     b.nd = q.nd;
     const size_t DD = (size_t)q.D * q.D, mD = (size_t)std::max(q.m, 1) * q.D;
     b.s32 = a.take<float>((size_t)q.D);
+    b.pilot_part = a.take<double>(pilot_part_doubles(q.D));
     b.G = a.take<double>(DD);
     b.sumA = a.take<double>((size_t)q.D);
     b.sumB = a.take<double>((size_t)q.D);
@@ -220,6 +221,7 @@ void batch_layout(Arena& a, const std::vector<PairPlan>& pp, const prohd_pair_de
         r.idxA = s ? bp.idxB : bp.idxA;
         r.idxB = nullptr;  // columns are rows of the whole set
         r.out = L.rout ? L.rout + (size_t)2 * i + s : nullptr;
+        r.rows_only = 1;
         if (tensor) hd_bufs(a, r, rows, cols, q.D, q.Dp);
       }
   }

@@ -292,31 +292,45 @@ __global__ void cov_finalize_kernel(const double* __restrict__ G, const double* 
 // Pilot shift of every pair: s = mean of the first <= 4096 rows of A. Any
 // shift gives the same C in exact arithmetic; a nearby one keeps the
 // centred values small, so FP32 column sums (combined in FP64) suffice.
-// One block per pair, thread (d, g) sums rows g, g + G, ... of column d.
+// Grid (kPilotSlices, pairs): block y sums the 256-row slice x of pair y's
+// first rows, thread (d, g) rows g, g + G, ... of column d; the slices'
+// sums are then added in order.
+constexpr int kPilotSlices = 16;
 __global__ void pilot_batched_kernel(const BPair* __restrict__ P) {
   __shared__ double sh[256];
-  const BPair& q = P[blockIdx.x];
+  const BPair& q = P[blockIdx.y];
   const int D = q.D;
   const int64_t rows = q.nA < 4096 ? q.nA : 4096;
+  const int64_t r0 = (int64_t)blockIdx.x * 256, r1 = min(rows, r0 + 256);
   const int G = D < 256 ? 256 / D : 1;
   const int d = threadIdx.x % D, g = threadIdx.x / D;
   float s0 = 0.f, s1 = 0.f, s2 = 0.f, s3 = 0.f;
   if (g < G && threadIdx.x < G * D) {
-    int64_t r = g;
-    for (; r + 3 * G < rows; r += 4 * G) {
+    int64_t r = r0 + g;
+    for (; r + 3 * G < r1; r += 4 * G) {
       s0 += __ldg(q.A + r * D + d);
       s1 += __ldg(q.A + (r + G) * D + d);
       s2 += __ldg(q.A + (r + 2 * G) * D + d);
       s3 += __ldg(q.A + (r + 3 * G) * D + d);
     }
-    for (; r < rows; r += G) s0 += __ldg(q.A + r * D + d);
+    for (; r < r1; r += G) s0 += __ldg(q.A + r * D + d);
   }
   sh[threadIdx.x] = ((double)s0 + (double)s1) + ((double)s2 + (double)s3);
   __syncthreads();
   if ((int)threadIdx.x < D) {
     double t = 0.0;
     for (int gg = 0; gg < G; ++gg) t += sh[gg * D + threadIdx.x];
-    q.s32[threadIdx.x] = (float)(t / (double)rows);
+    q.pilot_part[(size_t)blockIdx.x * D + threadIdx.x] = t;
+  }
+}
+
+__global__ void pilot_finish_batched_kernel(const BPair* __restrict__ P) {
+  const BPair& q = P[blockIdx.x];
+  const int64_t rows = q.nA < 4096 ? q.nA : 4096;
+  for (int d = threadIdx.x; d < q.D; d += blockDim.x) {
+    double t = 0.0;
+    for (int y = 0; y < kPilotSlices; ++y) t += q.pilot_part[(size_t)y * q.D + d];
+    q.s32[d] = (float)(t / (double)rows);
   }
 }
 
@@ -331,10 +345,13 @@ __global__ void cov_finalize_batched_kernel(const BPair* __restrict__ P) {
 }
 
 cudaError_t pilot_batched(const BPair* P, int npairs, cudaStream_t st) {
-  count_launch();
-  pilot_batched_kernel<<<npairs, 256, 0, st>>>(P);
+  count_launch(2);
+  pilot_batched_kernel<<<dim3(kPilotSlices, npairs), 256, 0, st>>>(P);
+  pilot_finish_batched_kernel<<<npairs, 256, 0, st>>>(P);
   return cudaGetLastError();
 }
+
+size_t pilot_part_doubles(int D) { return (size_t)kPilotSlices * D; }
 
 cudaError_t covariance_batched(const BPair* P, int npairs, int Dmax, cudaStream_t st) {
   count_launch();

@@ -324,22 +324,24 @@ __global__ void fill_u32_kernel(unsigned* p, int64_t n, unsigned v) {
 __device__ __forceinline__ void hd_colsum_body(const float* __restrict__ A, const int64_t* nA_dev,
                                                const float* __restrict__ B, const int64_t* nB_dev, int D,
                                                double* __restrict__ part /*[2][8][D]*/, int set) {
-  __shared__ double sh[8][33];
+  // FP32 sums of at most 32 values per thread and 256 per block (the shift
+  // only centres the rounded copies: any value is exact for the result)
+  __shared__ float sh[8][33];
   const float* X = set ? B : A;
   const int64_t n = set ? *nB_dev : *nA_dev;
   const int64_t rows = n < 2048 ? n : 2048;
   const int cl = threadIdx.x & 31, rg = threadIdx.x >> 5;
   const int c = blockIdx.x * 32 + cl;
   const int64_t r0 = (int64_t)blockIdx.y * 256;
-  double s = 0.0;
+  float s = 0.f;
   if (c < D)
-    for (int64_t i = r0 + rg; i < r0 + 256 && i < rows; i += 8) s += (double)X[i * D + c];
+    for (int64_t i = r0 + rg; i < r0 + 256 && i < rows; i += 8) s += X[i * D + c];
   sh[rg][cl] = s;
   __syncthreads();
   if (rg == 0 && c < D) {
-    double t = 0.0;
+    float t = 0.f;
     for (int g = 0; g < 8; ++g) t += sh[g][cl];
-    part[((size_t)set * 8 + blockIdx.y) * D + c] = t;
+    part[((size_t)set * 8 + blockIdx.y) * D + c] = (double)t;
   }
 }
 
@@ -1214,7 +1216,7 @@ __device__ __forceinline__ void hd_finalize_body(
     const unsigned long long* __restrict__ bestA, const int32_t* __restrict__ idsA, const int64_t* cntA_dev,
     const unsigned long long* __restrict__ bestB, const int32_t* __restrict__ idsB, const int64_t* cntB_dev,
     const int32_t* __restrict__ mapA, const int32_t* __restrict__ mapB, const HdScalars* sc, int* status,
-    prohd_hd_result* out) {
+    prohd_hd_result* out, bool rows_only = false) {
   __shared__ unsigned long long sh[32];
   __shared__ int64_t s_nn[2];
   __shared__ double s_d[2];
@@ -1268,7 +1270,7 @@ __device__ __forceinline__ void hd_finalize_body(
     r.H = r.dir == 0 ? r.h_ab : r.h_ba;
     r.wit_a = r.dir == 0 ? r.ab_a : r.ba_a;
     r.wit_b = r.dir == 0 ? r.ab_b : r.ba_b;
-    if (!(okA && okB) && *status == PROHD_OK) *status = PROHD_ENONFINITE;
+    if (!(okA && (okB || rows_only)) && *status == PROHD_OK) *status = PROHD_ENONFINITE;
     r.status = *status;
     if (sc) {
       r.H_lowp = ldexp(sqrt(fmax((double)sc->lowp_max, 0.0)), -scale_exponent(sc->maxabs));
@@ -2166,21 +2168,25 @@ __global__ void hd_prep_batched_kernel(const BPair* __restrict__ P) {
 __device__ __forceinline__ double hd_c1(const BPair& q) {
   return (2.0 * q.Dp + 2.0 * q.D + 32.0) * 5.9604644775390625e-8;
 }
+// Column count the margin passes visit: none when only the rows' distance is wanted.
+__device__ const int64_t kNoColumns = 0;
 __global__ void hd_bounds_batched_kernel(const BPair* __restrict__ P) {
   const BPair& q = P[blockIdx.y];
-  hd_bounds_body(q.hd_rowmin, q.hd_nA2, q.hd_epsA, q.nsel + 0, q.hd_colmin, q.hd_nB2, q.hd_epsB, q.nsel + 1, hd_c1(q),
-                 static_cast<HdScalars*>(q.hd_sc));
+  hd_bounds_body(q.hd_rowmin, q.hd_nA2, q.hd_epsA, q.nsel + 0, q.hd_colmin, q.hd_nB2, q.hd_epsB,
+                 q.rows_only ? &kNoColumns : q.nsel + 1, hd_c1(q), static_cast<HdScalars*>(q.hd_sc));
 }
 __global__ void hd_flag_batched_kernel(const BPair* __restrict__ P) {
   const BPair& q = P[blockIdx.y];
   HdScalars* sc = static_cast<HdScalars*>(q.hd_sc);
-  hd_flag_body(q.hd_rowmin, q.hd_nA2, q.hd_epsA, q.nsel + 0, q.hd_colmin, q.hd_nB2, q.hd_epsB, q.nsel + 1, hd_c1(q),
-               sc, q.hd_candA, q.hd_candB, &sc->ncandA, &sc->ncandB);
+  hd_flag_body(q.hd_rowmin, q.hd_nA2, q.hd_epsA, q.nsel + 0, q.hd_colmin, q.hd_nB2, q.hd_epsB,
+               q.rows_only ? &kNoColumns : q.nsel + 1, hd_c1(q), sc, q.hd_candA, q.hd_candB, &sc->ncandA,
+               &sc->ncandB);
 }
 // Candidate rows of A against all of B (set 0) and of B against all of A (set 1).
 __global__ void __launch_bounds__(256) rescore_few_batched_kernel(const BPair* __restrict__ P) {
   const BPair& q = P[blockIdx.y >> 1];
   const int set = blockIdx.y & 1;
+  if (set == 1 && q.rows_only) return;
   HdScalars* sc = static_cast<HdScalars*>(q.hd_sc);
   if (set == 0)
     rescore_few_body(q.As, q.hd_candA, &sc->ncandA, q.Bs, q.nsel + 1, q.D, q.bestA);
@@ -2190,6 +2196,7 @@ __global__ void __launch_bounds__(256) rescore_few_batched_kernel(const BPair* _
 __global__ void __launch_bounds__(256, 1) rescore_list_batched_kernel(const BPair* __restrict__ P) {
   const BPair& q = P[blockIdx.y >> 1];
   const int set = blockIdx.y & 1;
+  if (set == 1 && q.rows_only) return;
   HdScalars* sc = static_cast<HdScalars*>(q.hd_sc);
   if (set == 0)
     simt_dist_body<true, true, false>(q.As, q.hd_candA, &sc->ncandA, q.Bs, q.nsel + 1, q.D, q.bestA, nullptr);
@@ -2200,7 +2207,7 @@ __global__ void hd_finalize_tc_batched_kernel(const BPair* __restrict__ P) {
   const BPair& q = P[blockIdx.x];
   HdScalars* sc = static_cast<HdScalars*>(q.hd_sc);
   hd_finalize_body(q.As, q.nsel + 0, q.Bs, q.nsel + 1, q.D, q.bestA, q.hd_candA, &sc->ncandA, q.bestB, q.hd_candB,
-                   &sc->ncandB, q.idxA, q.idxB, sc, q.status, &q.out->hd);
+                   &sc->ncandB, q.idxA, q.idxB, sc, q.status, &q.out->hd, q.rows_only != 0);
 }
 
 cudaError_t hd_tc_batched(const BPair* P, const int* order, int npairs, int64_t* prefix, const CUtensorMap* maps,

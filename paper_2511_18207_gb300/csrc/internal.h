@@ -181,6 +181,7 @@ struct BPair {
   int D, Dp, m, nd;
   // directions
   float* s32;
+  double* pilot_part;  // [16][D] slice sums of the pilot shift
   double *G, *sumA, *sumB, *C64;
   double* gcorr;  // [D] diagonal corrections of the tensor-core Gram
   float* C32;
@@ -214,6 +215,7 @@ struct BPair {
   void* hd_sc;
   int64_t hd_nA_pad, hd_nB_pad;
   int hd_map;
+  int rows_only;  // only the rows' directed distance is wanted (refinement pairs)
   // Gram items of this pair (both sets), as positions in the batch's item-id list
   int gi0, gn0;
   int prob0;  // first selection problem of this pair (set-major: set * nd + d)
@@ -233,6 +235,7 @@ cudaError_t gram_tc_batched(const GcItem* items, int nitems, int* ticket, int* b
 cudaError_t gram_reduce_batched(const BPair* P, int npairs, const GcItem* items, const int* ids, int Dmax,
                                 cudaStream_t st);
 cudaError_t pilot_batched(const BPair* P, int npairs, cudaStream_t st);
+size_t pilot_part_doubles(int D);
 cudaError_t covariance_batched(const BPair* P, int npairs, int Dmax, cudaStream_t st);
 // Block iteration with one CTA per pair, one launch per D class (D <= 64, 128, 256),
 // each on its own stream; then the FP64 clean-up and Rayleigh quotients.
