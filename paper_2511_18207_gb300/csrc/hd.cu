@@ -700,11 +700,12 @@ __host__ __device__ constexpr size_t tc_smem_bytes(int KB) {
 // tiles of B starting at tile cb0, with the pair's operand maps, depth KB and
 // minima. seg: the row block's columns are split over several items, so its
 // row minima are combined with atomicMin (the buffer starts at +inf) rather
-// than stored.
+// than stored. cols: column minima wanted (else only the row minima).
 struct TcItem {
   const CUtensorMap *tmA, *tmB, *tmNA, *tmNB;
   int KB, CB, cb0, rb;
   bool seg;
+  bool cols = true;
   float* rowmin;
   unsigned* colmin;
 };
@@ -774,6 +775,7 @@ struct TcItemsBatch {
     it.rb = (int)(i - prefix[lo]);
     it.rowmin = q.hd_rowmin;
     it.colmin = q.hd_colmin;
+    it.cols = !q.rows_only;
     return true;
   }
 };
@@ -952,6 +954,7 @@ __device__ __forceinline__ void hd_tc_body(const Items& items, int KBmax, int* _
           tc_ld_red_min_32x32b_x32(taddr + ch * 32, v, vmin);
           tc_wait_ld();
           rmin = fminf(rmin, vmin);
+          if (!it.cols) continue;
           float cm[32];
 #pragma unroll
           for (int c = 0; c < 32; ++c) cm[c] = redux_min_f32(v[c]);
@@ -968,7 +971,7 @@ __device__ __forceinline__ void hd_tc_body(const Items& items, int KBmax, int* _
         if (lane == 0) mbar_arrive(&S.acc_empty[ab]);
       }
       named_bar_sync(1, 32 * kTcEpiWarps);
-      if (ok && et < kTcBN) {
+      if (ok && et < kTcBN && it.cols) {
         const int c = et;
         float m = fminf(fminf(S.col[ab][0][c], S.col[ab][1][c]), fminf(S.col[ab][2][c], S.col[ab][3][c]));
         m = fmaxf(m, 0.f);
