@@ -49,7 +49,7 @@ ALPHA = 0.01
 GRAM_TRAFFIC = 821.96e6 * 5 + 3.22e6
 PROJ_TRAFFIC = (819.41e6 + 26.96e6) * 5
 # the contraction's traffic per row of the two FP16 copies (100k + 100k capture)
-HD_TRAFFIC_PER_ROW = (138.28e6 + 5.13e6) / 200_000
+HD_TRAFFIC_PER_ROW = (136.72e6 + 4.64e6) / 200_000
 WORKLOAD = ("anisotropic Gaussian pair, n=m=2,000,000, D=256 (eigenvalues 1/i, random rotation); "
             "B shifted 0.1 sigma along a random unit vector with 0.1% Student-t (nu=3) points; "
             "ProHD with centroid axis + top-8 PCs, alpha=0.01 per side (alpha/8 per PC), FP16 tiles")

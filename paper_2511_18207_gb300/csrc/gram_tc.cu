@@ -11,9 +11,12 @@
 // points except on the diagonal, where m_i^2 is always positive; the
 // converters therefore add sum (z_i^2 - h_i^2 - 2 h_i m_i) to G_ii, computed
 // per point in FP32 with one rounding. The tensor core adds 512 points (64
-// MMAs) into a TMEM accumulator, which is added in FP32 into a running sum
-// kept in the other half of TMEM; each CTA writes its running sum once, and
-// two final kernels sum the CTAs in FP64 in a fixed order and symmetrise.
+// MMAs) into a TMEM accumulator; two accumulators (the two halves of TMEM)
+// alternate between such intervals, and each finished one is added in FP32
+// into a running sum that lives in the CTA's output slot (stored by the first
+// interval, then added at the L2 by bulk reduce-add copies, in interval
+// order), so the MMAs never wait for the running sum. Two final kernels sum
+// the CTAs' slots in FP64 in a fixed order and symmetrise.
 //
 // Work split. Two CTAs of a cluster work as a pair on one tile of 64 points
 // per step (cta_group::2, M = 256): for D > 128 each CTA stages and converts
@@ -36,8 +39,8 @@
 // x 4 TMA stages 1.07 ms, 3 x 3 0.92 ms, 4 x 2 1.01 ms) and signal the even CTA's MMA
 // thread; that thread issues the step's eight MMAs (two per 16-point slice)
 // and hands the tile pair back to both CTAs' converters when they complete;
-// four epilogue warps per CTA fold each 512-point accumulator into the
-// running sum. The converters work on point pairs with two-wide FP32
+// four epilogue warps per CTA drain each 512-point accumulator into the
+// running sum while the MMAs fill the other one. The converters work on point pairs with two-wide FP32
 // arithmetic (f32x2), which halves their instruction count: conversion, not
 // HBM or the tensor pipe, bounded the step rate. The odd CTA's converters and epilogue signal the even
 // CTA's barriers with remote mbarrier arrives after fence.proxy.async (a
@@ -70,7 +73,6 @@ constexpr int kGcFlush = 8;         // steps per TMEM accumulation (512 points p
 constexpr int kGcSlices = kGcPts / 16;
 constexpr uint32_t kGcTileBytes = kGcRows * 128;             // one BF16 operand tile
 constexpr uint32_t kGcStageBytes = kGcPts * kGcRows * 4;     // one FP32 stage
-constexpr uint32_t kGcSumCol = 256;                          // TMEM column of the running sums
 constexpr int kGcSlotFloats = 2 * 256 * kGcRows;             // per pair: [rank][col][row] partial products
 constexpr int kGcSumsDoubles = 2 * kGcPg * 2 * kGcRows;      // per pair: [rank][point group][z | corr][dim]
 
@@ -96,18 +98,21 @@ struct GcSmem {
   uint64_t ffull[kGcStages], fempty[kGcStages];
   uint64_t sfull[kGcBufs];   // even CTA: tile pair converted by every converter warp of both CTAs
   uint64_t sempty[kGcBufs];  // the tile pair's MMAs done (committed to both CTAs)
-  uint64_t acc_full;           // accumulator holds a finished interval (committed to both CTAs)
-  uint64_t acc_empty;          // even CTA: accumulator read by both CTAs' epilogues (8 arrivals)
+  uint64_t acc_full[2];        // accumulator b holds a finished interval (committed to both CTAs)
+  uint64_t acc_empty[2];       // even CTA: accumulator b read by both CTAs' epilogues (8 arrivals)
   uint64_t drain;
   uint32_t tmem_base;
   int abort;       // set by this CTA's waits or by the peer's
   int next;        // batched launches: the item both CTAs take next (written by the even CTA)
   int my_abort;    // abort snapshots exchanged between items
   int peer_abort;
+  int epi_go;      // the epilogue issuer's wait result for the current interval
 };
 
-constexpr size_t kGcSmemBytes =
-    1024 + (size_t)kGcBufs * 2 * kGcTileBytes + (size_t)kGcStages * kGcStageBytes + sizeof(GcSmem);
+constexpr int kGcOutCols = 16;  // columns of one drain chunk (kGcOutCols x 128 rows of FP32)
+constexpr uint32_t kGcOutBytes = kGcOutCols * kGcRows * 4;
+constexpr size_t kGcSmemBytes = 1024 + (size_t)kGcBufs * 2 * kGcTileBytes + (size_t)kGcStages * kGcStageBytes +
+                                2 * (size_t)kGcOutBytes + sizeof(GcSmem);
 
 struct GcParams {
   int64_t nA, nB;
@@ -218,8 +223,10 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kGcThreads, 1)
   uint8_t* base = smem_align<1024>(smem_raw);
   uint8_t* tiles = base;  // [kGcBufs][h, 2m]
   float* stage = reinterpret_cast<float*>(base + kGcBufs * 2 * kGcTileBytes);  // [kGcStages][64][128]
-  GcSmem& S =
-      *reinterpret_cast<GcSmem*>(base + kGcBufs * 2 * kGcTileBytes + (size_t)kGcStages * kGcStageBytes);
+  float* outst = reinterpret_cast<float*>(base + kGcBufs * 2 * kGcTileBytes +
+                                          (size_t)kGcStages * kGcStageBytes);  // [2][kGcOutCols][128]
+  GcSmem& S = *reinterpret_cast<GcSmem*>(base + kGcBufs * 2 * kGcTileBytes + (size_t)kGcStages * kGcStageBytes +
+                                         2 * (size_t)kGcOutBytes);
   const uint32_t rank = cluster_rank();
   const bool leader = rank == 0;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -236,8 +243,10 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kGcThreads, 1)
       mbar_init(&S.sfull[b], 2 * kGcConv);  // every converter warp of both CTAs
       mbar_init(&S.sempty[b], 1);
     }
-    mbar_init(&S.acc_full, 1);
-    mbar_init(&S.acc_empty, 2 * kGcEpi);
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(&S.acc_full[b], 1);
+      mbar_init(&S.acc_empty[b], 2 * kGcEpi);
+    }
     mbar_init(&S.drain, 1);
     S.abort = 0;
     S.next = 0;
@@ -401,10 +410,12 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kGcThreads, 1)
         uint32_t fi = f0;
         for (int c = 0; c < nsteps; ++c) {
           const uint32_t g = g0 + (uint32_t)c;
+          const uint32_t ab = fi & 1u;  // accumulators alternate between intervals
           if (in_acc == 0) {
-            if (!gc_wait(&S.acc_empty, (fi & 1u) ^ 1u, abort, peer_abort, p.timeout_ns)) break;
+            if (!gc_wait(&S.acc_empty[ab], ((fi >> 1) & 1u) ^ 1u, abort, peer_abort, p.timeout_ns)) break;
             tc_fence_after();
           }
+          const uint32_t dacc = tmem + ab * 256u;
           const int bf = (int)(g % kGcBufs);
           const uint32_t use = g / kGcBufs;
           const uint32_t th = smem_u32(tiles) + (uint32_t)bf * 2 * kGcTileBytes, tm2 = th + kGcTileBytes;
@@ -413,74 +424,97 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kGcThreads, 1)
 #pragma unroll
           for (int k = 0; k < kGcSlices; ++k) {
             const uint64_t bh = smem_desc_sw128(th + k * 32);
-            tc2_mma_f16(tmem, bh, bh, idesc, (in_acc | k) != 0);
-            tc2_mma_f16(tmem, smem_desc_sw128(tm2 + k * 32), bh, idesc, 1u);
+            tc2_mma_f16(dacc, bh, bh, idesc, (in_acc | k) != 0);
+            tc2_mma_f16(dacc, smem_desc_sw128(tm2 + k * 32), bh, idesc, 1u);
           }
           tc2_commit_mc(&S.sempty[bf], 0x3);  // this tile pair may be overwritten in both CTAs
           if (++in_acc == kGcFlush || c == nsteps - 1) {
-            tc2_commit_mc(&S.acc_full, 0x3);
+            tc2_commit_mc(&S.acc_full[ab], 0x3);
             in_acc = 0;
             ++fi;
           }
         }
       }
     } else {
-      // ---------------- epilogue: accumulator -> running sum -> global ----------------
+      // ---------------- epilogue: accumulator -> running sum in the item's slot ----------------
+      // The slot holds the running sum: the first interval's accumulator is
+      // stored, every later one added at the L2 (bulk reduce-add, FP32 round
+      // to nearest: the same sum as adding in registers). Chunks of 16
+      // columns x 128 rows go through two shared-memory buffers; one thread
+      // issues each chunk's bulk copy after the four warps have written it.
+      // The accumulator is handed back as soon as it is read, so the MMAs of
+      // the next interval (into the other accumulator) never wait for the
+      // slot. Intervals of one item reach the slot in order: the issuer
+      // waits for the previous interval's copies before the next.
       const int q = warp & 3;  // TMEM lane quarter this warp may access
       const int row = q * 32 + lane;
       const bool useful = q * 32 < urows;
-      const uint32_t acc_empty_leader = map_to_cta(&S.acc_empty, 0);
+      const bool issuer = warp == kGcConv + 1 && lane == 0;
+      const uint32_t acc_empty_leader0 = map_to_cta(&S.acc_empty[0], 0);
+      const uint32_t acc_empty_leader1 = map_to_cta(&S.acc_empty[1], 0);
       const uint32_t lane_base = tmem + ((uint32_t)(q * 32) << 16);
-      bool ok = true;
+      float* o = w.out + (size_t)rank * ucols * kGcRows;
+      const int nch = ucols / kGcOutCols;
+      uint32_t chunk = 0;  // drain chunks so far: staging buffer chunk & 1
       for (int i = 0; i < nint; ++i) {
         const uint32_t fi = f0 + (uint32_t)i;
-        int got = 0;
-        if (lane == 0) got = gc_wait(&S.acc_full, fi & 1u, abort, peer_abort, p.timeout_ns) ? 1 : 0;
-        got = __shfl_sync(0xffffffffu, got, 0);
-        if (!got) {
-          ok = false;
-          break;
+        const uint32_t ab = fi & 1u;
+        // one thread waits; the four warps take its verdict together (they
+        // meet at named barriers below, so they must all go on or all stop)
+        if (issuer) {
+          S.epi_go = gc_wait(&S.acc_full[ab], (fi >> 1) & 1u, abort, peer_abort, p.timeout_ns) ? 1 : 0;
+          if (i > 0) bulk_wait_all();  // the previous interval's adds are performed
         }
+        __syncwarp();  // each warp reaches the barrier converged
+        named_bar_sync(1, 32 * kGcEpi);
+        const int go = S.epi_go;
+        named_bar_sync(1, 32 * kGcEpi);  // S.epi_go is read before the next interval rewrites it
+        if (!go) break;
         tc_fence_after();
-        if (useful) {
-          for (int cc = 0; cc < ucols / 16; ++cc) {
-            float v[16], sum[16];
+        for (int cc = 0; cc < nch; ++cc, ++chunk) {
+          float v[kGcOutCols];
+          if (useful) {
             __syncwarp();
-            tc_ld_32x32b_x16(lane_base + (uint32_t)(ucol0 + cc * 16), v);
-            if (i > 0) tc_ld_32x32b_x16(lane_base + kGcSumCol + (uint32_t)(cc * 16), sum);
-            tc_wait_ld();
-#pragma unroll
-            for (int j = 0; j < 16; ++j) sum[j] = i > 0 ? sum[j] + v[j] : v[j];
-            tc_st_32x32b_x16(lane_base + kGcSumCol + (uint32_t)(cc * 16), sum);
-          }
-          tc_wait_st();
-        }
-        // this CTA's half of the accumulator is read: tell the MMA thread
-        tc_fence_before();
-        __syncwarp();
-        if (lane == 0) {
-          if (leader) mbar_arrive(&S.acc_empty);
-          else mbar_arrive_remote(acc_empty_leader);
-        }
-      }
-      if (ok) {
-        // the item's partial product: [col][row], useful columns only (zeros for an empty item)
-        float* o = w.out + (size_t)rank * ucols * kGcRows;
-        for (int cc = 0; cc < ucols / 16; ++cc) {
-          float sum[16];
-          if (useful && nint > 0) {
-            __syncwarp();
-            tc_ld_32x32b_x16(lane_base + kGcSumCol + (uint32_t)(cc * 16), sum);
+            tc_ld_32x32b_x16(lane_base + ab * 256u + (uint32_t)(ucol0 + cc * kGcOutCols), v);
             tc_wait_ld();
           } else {
 #pragma unroll
-            for (int j = 0; j < 16; ++j) sum[j] = 0.f;
+            for (int j = 0; j < kGcOutCols; ++j) v[j] = 0.f;
           }
+          if (cc == nch - 1) {
+            // this CTA's half of accumulator ab is read: tell the MMA thread
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) {
+              if (leader) mbar_arrive(&S.acc_empty[ab]);
+              else mbar_arrive_remote(ab ? acc_empty_leader1 : acc_empty_leader0);
+            }
+          }
+          float* buf = outst + (size_t)(chunk & 1u) * (kGcOutCols * kGcRows);
+          if (issuer) bulk_wait_read<1>();  // the copy that last used this buffer has read it
+          __syncwarp();
+          named_bar_sync(1, 32 * kGcEpi);
 #pragma unroll
-          for (int j = 0; j < 16; ++j) o[(size_t)(cc * 16 + j) * kGcRows + row] = sum[j];
+          for (int j = 0; j < kGcOutCols; ++j) buf[j * kGcRows + row] = v[j];
+          fence_proxy_async();
+          __syncwarp();
+          named_bar_sync(1, 32 * kGcEpi);
+          if (issuer) {
+            float* dst = o + (size_t)cc * kGcOutCols * kGcRows;
+            if (i == 0) bulk_store_s2g(dst, buf, kGcOutBytes);
+            else bulk_add_f32_s2g(dst, buf, kGcOutBytes);
+            bulk_commit();
+          }
+          __syncwarp();
         }
-        tc_fence_before();
       }
+      if (nint == 0) {
+        // an empty item's partial product is zero
+        for (int cc = 0; cc < nch; ++cc)
+#pragma unroll
+          for (int j = 0; j < kGcOutCols; ++j) o[(size_t)(cc * kGcOutCols + j) * kGcRows + row] = 0.f;
+      }
+      if (issuer) bulk_wait_all();
     }
     // the item is finished by every role of this CTA: the rings are idle
     __syncthreads();

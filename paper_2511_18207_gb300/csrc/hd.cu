@@ -2244,8 +2244,8 @@ cudaError_t hd_tc_batched(const BPair* P, const int* order, int npairs, int64_t*
   const size_t fsm = (size_t)kFewRows * 256 * sizeof(float) + (size_t)8 * kFewRows * sizeof(unsigned long long);
   cudaFuncSetAttribute(rescore_few_batched_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fsm);
   count_launch(5);
-  hd_bounds_batched_kernel<<<dim3(bx, npairs), 256, 0, st>>>(P);
-  hd_flag_batched_kernel<<<dim3(bx, npairs), 256, 0, st>>>(P);
+  hd_bounds_batched_kernel<<<dim3(4, npairs), 256, 0, st>>>(P);
+  hd_flag_batched_kernel<<<dim3(4, npairs), 256, 0, st>>>(P);
   rescore_few_batched_kernel<<<dim3(8, 2 * npairs), 256, fsm, st>>>(P);
   rescore_list_batched_kernel<<<dim3(8, 2 * npairs), 256, 0, st>>>(P);
   hd_finalize_tc_batched_kernel<<<npairs, 1024, 0, st>>>(P);

@@ -283,7 +283,8 @@ size_t hd_scalars_bytes();
 size_t hd_tc_row_block();   // rows of A per contraction item (128)
 // Tensor-core subset HD of every pair: prep, contraction over (pair, row block)
 // items, margins, FP32 rescoring of candidates, FP64 witnesses. `bx` blocks
-// per (pair, set) run the passes over rows (the largest set's rows decide).
+// per (pair, set) run the max |x - s| and rounded-copy passes (the largest
+// set's rows decide).
 cudaError_t hd_tc_batched(const BPair* P, const int* order, int npairs, int64_t* prefix, const CUtensorMap* maps,
                           int Dmax, int bf16, int* batch_status, int num_sms, int64_t timeout_ns, cudaStream_t st,
                           int bx = 4);

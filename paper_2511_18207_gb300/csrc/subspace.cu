@@ -591,14 +591,15 @@ PROHD_DEV void subspace_body(SiSmemT<NC, ROWS, VLD>& S, const float* __restrict_
         }
       }
       __syncthreads();
-      // Plain steps: after kSiRRWarm steps, three steps of every four skip
+      // Plain steps: after kSiRRWarm steps, seven steps of every eight skip
       // the Rayleigh-Ritz part (H, Jacobi, Ritz vectors, residuals). The
       // block spans C^t V_0 either way, so the subspace converges at the same
       // rate per multiplication; the basis from the last Rayleigh-Ritz step
       // keeps its column order and Ritz values for the scaling, and the last
-      // step before the cap, like every stop test (steps 4, 8, ...; the stall
-      // test's every eighth among them), is a Rayleigh-Ritz step.
-      const bool plain = t > kSiRRWarm && (t & 3) && t < maxit;
+      // step before the cap, like every stop test (steps 8, 16, ...: each is
+      // also a window boundary of the stall test), is a Rayleigh-Ritz step.
+      static_assert(kSiStallWin % 8 == 0, "stall-test windows end on Rayleigh-Ritz steps");
+      const bool plain = t > kSiRRWarm && (t & 7) && t < maxit;
       if (plain) {
         const float sigma_p = sigma_rel * fmaxf(S.theta[0], 0.f);
         for (int o = tid; o < nr * b; o += kSiThreads) {

@@ -5,6 +5,8 @@
     python -m paper_2511_18207_gb300.profile_cases pruned       # row-pruned exact distance, 2M x 2M x 256 (launch list)
     python -m paper_2511_18207_gb300.profile_cases estimate     # one ProHD estimate, 2M x 2M x 256 (launch list)
     python -m paper_2511_18207_gb300.profile_cases estimate_small  # one ProHD estimate, 400k x 400k x 256 (captures)
+    python -m paper_2511_18207_gb300.profile_cases batch        # the 512-pair batch, one direct run (launch list)
+    python -m paper_2511_18207_gb300.profile_cases batch_refined  # the same batch with refine = 1 (launch list)
 
 Each case runs its call twice (the second launch is the one to capture, e.g.
 ``ncu --clock-control none -k regex:gram_tc_kernel -s 1 -c 1``), keeps the
@@ -91,8 +93,37 @@ def estimate_small():
     print("H_hat", r["H"], r["status"], "|A_sel|", r["nsel_a"], "|B_sel|", r["nsel_b"])
 
 
+def _batch(refine: int):
+    # the benchmark's 512 uneven pairs (13 GB drawn on the device, about 8 GB
+    # of workspace, 16 GB with refine = 1) planned with the tuned item sizes and
+    # run once without the graph: one launch per stage, for a launch list
+    import torch
+
+    from . import prohd, workloads as W
+
+    pairs = W.batched_pairs_device(512, seed=7)
+    torch.cuda.synchronize()
+    st = torch.cuda.Stream()
+    with torch.cuda.stream(st):
+        b = prohd.Batch(prohd.context(), pairs, m=8, alpha_c=0.01, precision="fp16", refine=refine)
+        b.set_tunables(32768, 32768, 131072)
+        b.use_graph(False)
+        b.run(st)
+        st.synchronize()
+    res = b.results()
+    print("pairs", len(res), "H sum", sum(r["H"] for r in res))
+
+
+def batch():
+    _batch(0)
+
+
+def batch_refined():
+    _batch(1)
+
+
 CASES = {"directions": directions, "exact": exact, "pruned": pruned, "estimate": estimate,
-         "estimate_small": estimate_small}
+         "estimate_small": estimate_small, "batch": batch, "batch_refined": batch_refined}
 
 if __name__ == "__main__":
     if len(sys.argv) != 2 or sys.argv[1] not in CASES:
