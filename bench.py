@@ -44,9 +44,10 @@ M_PCS = 8
 ALPHA = 0.01
 # DRAM bytes (read + write) per full-size launch from one ncu capture of the
 # current kernel at 400k + 400k points: the reads (and the projection's key
-# writes) grow with the points (x5 to 2M + 2M); the Gram's writes (the CTA
-# pairs' partial products) do not. None: no capture of the current kernel.
-GRAM_TRAFFIC = 821.96e6 * 5 + 3.22e6
+# writes) grow with the points (x5 to 2M + 2M); the Gram's writes (its running
+# sums reaching DRAM) are scaled x5 too, an upper estimate. None: no capture of
+# the current kernel.
+GRAM_TRAFFIC = (826.25e6 + 22.39e6) * 5
 PROJ_TRAFFIC = (819.41e6 + 26.96e6) * 5
 # the contraction's traffic per row of the two FP16 copies (100k + 100k capture)
 HD_TRAFFIC_PER_ROW = (136.72e6 + 4.64e6) / 200_000
