@@ -390,6 +390,10 @@ struct EstLayout {
   prohd_hd_result *r1 = nullptr, *r2 = nullptr;
   PruneLayout P;  // the refinement's row pruning (tensor-core precisions)
   const InputFeed* feed = nullptr;  // host-buffer entry: inputs landing in row ranges
+  // the union centroid (from the covariance pass) and max |x - centroid| over
+  // the gathered subsets: the subset distance's centre and scale
+  float* center = nullptr;
+  float* gmax = nullptr;
 };
 
 // Layout of an estimate with nd directions and the given k lists; m_dirs >= 0
@@ -412,6 +416,8 @@ void est_layout_k(Arena& a, int64_t nA, int64_t nB, int D, int nd, const int64_t
   L.nselB = a.take<int64_t>(1);
   L.As = a.take<float>((size_t)L.boundA * D);
   L.Bs = a.take<float>((size_t)L.boundB * D);
+  L.center = a.take<float>((size_t)D);
+  L.gmax = a.take<float>(1);
   L.refine = refine;
   L.refine_pruned = refine && precision != PROHD_FP32;
   if (refine) {
@@ -749,17 +755,26 @@ static prohd_status estimate_run(prohd_ctx* ctx, const float* A, int64_t nA, con
   if (!e && !given_dirs) {
     Arena t = phase(L.mark_dir);
     e = directions_run(ctx, A, nA, B, nB, D, m, p->power_max_iters, p->power_tol, p->seed, L.dirs, L.eig, L.status, t, st,
-                       p->wait_timeout_ns, L.feed);
+                       p->wait_timeout_ns, L.feed, L.center, L.gmax);
   }
   if (!e) {
     Arena t = phase(L.mark_sel);
     e = select_run(ctx, A, nA, B, nB, D, use_dirs, L.nd, L.kA, L.kB, L.idxA, L.nselA, L.idxB, L.nselB, L.status, t,
                    st, p->wait_timeout_ns);
   }
+  // with the directions computed here, the gather also takes the subset
+  // distance's scale about the union centroid (no centring passes later)
+  const bool centred = !given_dirs && p->precision != PROHD_FP32;
+  const HdCenter hc{L.center, L.gmax};
   {
     PhaseTimer pt(ctx, PROHD_PH_GATHER, st);
-    if (!e) e = gather_rows(A, D, L.idxA, L.nselA, L.boundA, L.As, ctx->num_sms, st);
-    if (!e) e = gather_rows(B, D, L.idxB, L.nselB, L.boundB, L.Bs, ctx->num_sms, st);
+    if (centred) {
+      if (!e) e = gather_rows_center(A, D, L.idxA, L.nselA, L.boundA, L.As, L.center, L.gmax, L.status, ctx->num_sms, st);
+      if (!e) e = gather_rows_center(B, D, L.idxB, L.nselB, L.boundB, L.Bs, L.center, L.gmax, L.status, ctx->num_sms, st);
+    } else {
+      if (!e) e = gather_rows(A, D, L.idxA, L.nselA, L.boundA, L.As, ctx->num_sms, st);
+      if (!e) e = gather_rows(B, D, L.idxB, L.nselB, L.boundB, L.Bs, ctx->num_sms, st);
+    }
   }
   if (!e) {
     Arena t = phase(L.mark_hd);
@@ -768,10 +783,10 @@ static prohd_status estimate_run(prohd_ctx* ctx, const float* A, int64_t nA, con
     // cannot attain either directed maximum
     if (L.prune_sub && (double)L.boundA * (double)L.boundB >= ctx->subset_prune_min_pairs)
       e = hd_core_pruned(ctx, L.As, L.nselA, L.boundA, L.Bs, L.nselB, L.boundB, D, p->precision, L.idxA, L.idxB,
-                         &out->hd, L.status, t, to, st);
+                         &out->hd, L.status, t, to, st, centred ? &hc : nullptr);
     else
       e = hd_core(ctx, L.As, L.nselA, L.boundA, L.Bs, L.nselB, L.boundB, D, p->precision, L.idxA, L.idxB, &out->hd,
-                  L.status, t, to, st);
+                  L.status, t, to, st, false, nullptr, centred ? &hc : nullptr);
   }
   if (!e && L.refine) e = refine_run(ctx, A, nA, B, nB, D, p, L, out, wsb, ws_bytes, st);
   if (!e) {

@@ -245,8 +245,16 @@ __global__ void reduce_parts_kernel(const double* __restrict__ Gpart, const doub
 
 // dirs[0] = centroid axis; C64 = G/N - dmu dmu^T (full symmetric); C32 copy.
 __device__ __forceinline__ void centroid_axis_body(const double* __restrict__ sumA, const double* __restrict__ sumB,
-                                                   int64_t nA, int64_t nB, int D, double* __restrict__ dirs) {
+                                                   int64_t nA, int64_t nB, int D, double* __restrict__ dirs,
+                                                   const float* __restrict__ s32 = nullptr,
+                                                   float* __restrict__ center = nullptr, float* zero1 = nullptr) {
   __shared__ double sh[33];
+  if (center) {
+    // the union centroid: the shift plus the mean of the centred values
+    const double invN = 1.0 / (double)(nA + nB);
+    for (int c = threadIdx.x; c < D; c += blockDim.x) center[c] = (float)((double)s32[c] + (sumA[c] + sumB[c]) * invN);
+  }
+  if (zero1 && threadIdx.x == 0) *zero1 = 0.f;
   double part = 0.0;
   for (int c = threadIdx.x; c < D; c += blockDim.x) {
     double u = sumB[c] / (double)nB - sumA[c] / (double)nA;
@@ -260,8 +268,9 @@ __device__ __forceinline__ void centroid_axis_body(const double* __restrict__ su
 }
 
 __global__ void centroid_axis_kernel(const double* __restrict__ sumA, const double* __restrict__ sumB, int64_t nA,
-                                     int64_t nB, int D, double* __restrict__ dirs) {
-  centroid_axis_body(sumA, sumB, nA, nB, D, dirs);
+                                     int64_t nB, int D, double* __restrict__ dirs, const float* __restrict__ s32,
+                                     float* __restrict__ center, float* zero1) {
+  centroid_axis_body(sumA, sumB, nA, nB, D, dirs, s32, center, zero1);
 }
 
 __device__ __forceinline__ void cov_finalize_body(const double* __restrict__ G, const double* __restrict__ sumA,
@@ -733,7 +742,8 @@ void directions_layout(Arena& ws, int64_t nA, int64_t nB, int D, int m, int gram
 
 cudaError_t directions_run(prohd_ctx* ctx, const float* A, int64_t nA, const float* B, int64_t nB, int D, int m,
                            int max_iters, double tol, uint64_t seed, double* dirs, double* eig, int* status_dev,
-                           Arena& ws, cudaStream_t st, int64_t timeout_ns, const InputFeed* feed) {
+                           Arena& ws, cudaStream_t st, int64_t timeout_ns, const InputFeed* feed, float* center32,
+                           float* zero1) {
   DirBufs b;
   const int parts = feed ? feed->parts : 1;
   dir_layout(ws, D, m, b, parts);
@@ -780,7 +790,7 @@ cudaError_t directions_run(prohd_ctx* ctx, const float* A, int64_t nA, const flo
     if ((e = cudaGetLastError())) return e;
   }
   count_launch();
-  centroid_axis_kernel<<<1, 256, 0, st>>>(b.sumA, b.sumB, nA, nB, D, dirs);
+  centroid_axis_kernel<<<1, 256, 0, st>>>(b.sumA, b.sumB, nA, nB, D, dirs, b.s32, center32, zero1);
   count_launch();
   cov_finalize_kernel<<<nsm, 256, 0, st>>>(b.G, b.sumA, b.sumB, nA, nB, D, b.C64, b.C32);
   if ((e = cudaGetLastError())) return e;

@@ -1504,11 +1504,35 @@ cudaError_t hd_shared_prepare(prohd_ctx* ctx, const float* X, const int64_t* nX_
 // or B's from a shared preparation).
 static cudaError_t tc_prep(prohd_ctx* ctx, const float* A, const int64_t* nA_dev, const float* B,
                            const int64_t* nB_dev, int D, int precision, HdBufs& b, int* status_dev, cudaStream_t st,
-                           const HdShared* shared) {
+                           const HdShared* shared, const HdCenter* center = nullptr) {
   const int nsm = ctx->num_sms;
   const int bf16 = precision == PROHD_BF16 ? 1 : 0;
   PhaseTimer pt_prep(ctx, PROHD_PH_HD_PREP, st);
   cudaMemsetAsync(b.sc, 0, sizeof(HdScalars), st);
+  if (center && !shared) {
+    // the centre and the bound were taken before (the rows were scanned for
+    // non-finite values then): the copies only
+    b.shift = const_cast<float*>(center->shift);
+    cudaError_t e = cudaMemcpyAsync(&b.sc->maxabs, center->maxabs, sizeof(float), cudaMemcpyDeviceToDevice, st);
+    if (e) return e;
+    count_launch(2);
+    if (bf16) {
+      hd_prep_kernel<1><<<nsm * 4, 256, 0, st>>>(A, nA_dev, b.nA_pad, D, b.Dp, b.shift, &b.sc->maxabs, -2.f,
+                                                (__nv_bfloat16*)b.At, b.nA2, b.epsA, &b.sc->maxnormA, &b.sc->maxepsA,
+                                                b.nA8, 0);
+      hd_prep_kernel<1><<<nsm * 4, 256, 0, st>>>(B, nB_dev, b.nB_pad, D, b.Dp, b.shift, &b.sc->maxabs, 1.f,
+                                                (__nv_bfloat16*)b.Bt, b.nB2, b.epsB, &b.sc->maxnormB, &b.sc->maxepsB,
+                                                b.nB8, 1);
+    } else {
+      hd_prep_kernel<0><<<nsm * 4, 256, 0, st>>>(A, nA_dev, b.nA_pad, D, b.Dp, b.shift, &b.sc->maxabs, -2.f,
+                                                (__half*)b.At, b.nA2, b.epsA, &b.sc->maxnormA, &b.sc->maxepsA,
+                                                b.nA8, 0);
+      hd_prep_kernel<0><<<nsm * 4, 256, 0, st>>>(B, nB_dev, b.nB_pad, D, b.Dp, b.shift, &b.sc->maxabs, 1.f,
+                                                (__half*)b.Bt, b.nB2, b.epsB, &b.sc->maxnormB, &b.sc->maxepsB,
+                                                b.nB8, 1);
+    }
+    return cudaGetLastError();
+  }
   if (shared) {
     // B was prepared once (hd_shared_prepare) with a shift and scale that
     // cover every row set A is drawn from: take its copy, norms, margins and
@@ -1619,10 +1643,10 @@ static double tc_c1(int Dp, int D) { return (2.0 * Dp + 2.0 * D + 32.0) * 5.9604
 static cudaError_t tc_prep_contract(prohd_ctx* ctx, const float* A, const int64_t* nA_dev, const float* B,
                                     const int64_t* nB_dev, int D, int precision, HdBufs& b, int* status_dev,
                                     int64_t timeout_ns, cudaStream_t st, double& c1, bool few_rows = false,
-                                    const HdShared* shared = nullptr) {
+                                    const HdShared* shared = nullptr, const HdCenter* center = nullptr) {
   if (!tc_supported_dim(D)) return cudaErrorInvalidValue;
   const int nsm = ctx->num_sms;
-  cudaError_t e = tc_prep(ctx, A, nA_dev, B, nB_dev, D, precision, b, status_dev, st, shared);
+  cudaError_t e = tc_prep(ctx, A, nA_dev, B, nB_dev, D, precision, b, status_dev, st, shared, center);
   if (e) return e;
   count_launch();
   fill_u32_kernel<<<nsm * 2, 256, 0, st>>>(b.colmin, b.nB_pad, 0x7f800000u);
@@ -1647,7 +1671,7 @@ static cudaError_t tc_prep_contract(prohd_ctx* ctx, const float* A, const int64_
 cudaError_t hd_core(prohd_ctx* ctx, const float* A, const int64_t* nA_dev, int64_t nA_max, const float* B,
                     const int64_t* nB_dev, int64_t nB_max, int D, int precision, const int32_t* mapA,
                     const int32_t* mapB, prohd_hd_result* out, int* status_dev, Arena& ws, int64_t timeout_ns,
-                    cudaStream_t st, bool few_rows, const HdShared* shared) {
+                    cudaStream_t st, bool few_rows, const HdShared* shared, const HdCenter* center) {
   HdBufs b;
   layout(ws, nA_max, nB_max, D, precision, b);
   if (ws.overflow()) return cudaErrorMemoryAllocation;
@@ -1672,7 +1696,7 @@ cudaError_t hd_core(prohd_ctx* ctx, const float* A, const int64_t* nA_dev, int64
 
   double c1 = 0.0;
   if ((e = tc_prep_contract(ctx, A, nA_dev, B, nB_dev, D, precision, b, status_dev, timeout_ns, st, c1, few_rows,
-                            shared)))
+                            shared, center)))
     return e;
   PhaseTimer pt_rs(ctx, PROHD_PH_HD_RESCORE, st);
   count_launch();
@@ -1945,7 +1969,7 @@ __global__ void prune_sub_remap_kernel(int32_t* __restrict__ candA, const int64_
 cudaError_t hd_core_pruned(prohd_ctx* ctx, const float* A, const int64_t* nA_dev, int64_t nA_max, const float* B,
                            const int64_t* nB_dev, int64_t nB_max, int D, int precision, const int32_t* mapA,
                            const int32_t* mapB, prohd_hd_result* out, int* status_dev, Arena& ws, int64_t timeout_ns,
-                           cudaStream_t st) {
+                           cudaStream_t st, const HdCenter* center) {
   if (!hd_subset_prunable(nA_max, nB_max, D, precision)) return cudaErrorInvalidValue;
   HdBufs b;
   layout(ws, nA_max, nB_max, D, precision, b);
@@ -1953,7 +1977,7 @@ cudaError_t hd_core_pruned(prohd_ctx* ctx, const float* A, const int64_t* nA_dev
   prune_sub_layout(ws, nA_max, nB_max, b, q);
   if (ws.overflow()) return cudaErrorMemoryAllocation;
   const int nsm = ctx->num_sms;
-  cudaError_t e = tc_prep(ctx, A, nA_dev, B, nB_dev, D, precision, b, status_dev, st, nullptr);
+  cudaError_t e = tc_prep(ctx, A, nA_dev, B, nB_dev, D, precision, b, status_dev, st, nullptr, center);
   if (e) return e;
   const double c1 = tc_c1(b.Dp, D);
   TcMaps full, keptA, keptB;

@@ -98,10 +98,19 @@ constexpr int64_t kDefaultTimeoutNs = 4000000000LL;
 // index maps translate row numbers to caller indices for the witnesses.
 void hd_core_layout(Arena& ws, int64_t nA_max, int64_t nB_max, int D, int precision);
 struct HdShared;
+// A centre for the rounded copies and a bound max |x - shift| over both row
+// sets (FP32), known before the subset distance (the estimate: the union
+// centroid from the covariance pass, the bound taken while gathering the
+// subsets), so that the copies skip their own centring passes.
+struct HdCenter {
+  const float* shift;   // [D]
+  const float* maxabs;  // [1]
+};
 cudaError_t hd_core(prohd_ctx* ctx, const float* A, const int64_t* nA_dev, int64_t nA_max, const float* B,
                     const int64_t* nB_dev, int64_t nB_max, int D, int precision, const int32_t* mapA,
                     const int32_t* mapB, prohd_hd_result* out, int* status_dev, Arena& ws, int64_t timeout_ns,
-                    cudaStream_t st, bool few_rows = false, const HdShared* shared = nullptr);
+                    cudaStream_t st, bool few_rows = false, const HdShared* shared = nullptr,
+                    const HdCenter* center = nullptr);
 bool tc_supported_dim(int D);
 // The same result as hd_core (tensor-core precisions), with the rows that
 // cannot attain either directed maximum left out of the full contractions;
@@ -112,7 +121,7 @@ void hd_core_pruned_layout(Arena& ws, int64_t nA_max, int64_t nB_max, int D, int
 cudaError_t hd_core_pruned(prohd_ctx* ctx, const float* A, const int64_t* nA_dev, int64_t nA_max, const float* B,
                            const int64_t* nB_dev, int64_t nB_max, int D, int precision, const int32_t* mapA,
                            const int32_t* mapB, prohd_hd_result* out, int* status_dev, Arena& ws, int64_t timeout_ns,
-                           cudaStream_t st);
+                           cudaStream_t st, const HdCenter* center = nullptr);
 
 // ---- selection (select.cu) ----
 void select_layout(Arena& ws, int64_t nA, int64_t nB, int D, int ndirs);
@@ -122,6 +131,11 @@ cudaError_t select_run(prohd_ctx* ctx, const float* A, int64_t nA, const float* 
                        cudaStream_t st, int64_t timeout_ns);
 cudaError_t gather_rows(const float* X, int D, const int32_t* idx, const int64_t* n_dev, int64_t n_max, float* out,
                         int num_sms, cudaStream_t st);
+// The same gather, also raising *maxabs to max |x - center| over the gathered
+// values (FP32, atomic; *maxabs starts at 0) and flagging non-finite values.
+cudaError_t gather_rows_center(const float* X, int D, const int32_t* idx, const int64_t* n_dev, int64_t n_max,
+                               float* out, const float* center, float* maxabs, int* status, int num_sms,
+                               cudaStream_t st);
 
 // ---- directions (directions.cu) ----
 // Inputs that land while the work runs (the host-buffer entry point): each
@@ -134,9 +148,12 @@ struct InputFeed {
   const cudaEvent_t* ready = nullptr;
 };
 void directions_layout(Arena& ws, int64_t nA, int64_t nB, int D, int m, int gram_parts = 1);
+// center32 (optional): the union centroid in FP32 [D]; zero1 (optional): one
+// float set to 0 in the same launch.
 cudaError_t directions_run(prohd_ctx* ctx, const float* A, int64_t nA, const float* B, int64_t nB, int D, int m,
                            int max_iters, double tol, uint64_t seed, double* dirs, double* eig, int* status_dev,
-                           Arena& ws, cudaStream_t st, int64_t timeout_ns, const InputFeed* feed = nullptr);
+                           Arena& ws, cudaStream_t st, int64_t timeout_ns, const InputFeed* feed = nullptr,
+                           float* center32 = nullptr, float* zero1 = nullptr);
 
 // Union covariance C (FP64, D x D, 1/N) and mean of [A; B] (directions.cu).
 void covariance_layout(Arena& ws, int D);

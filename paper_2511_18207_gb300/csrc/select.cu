@@ -1370,6 +1370,64 @@ __global__ void gather_rows_kernel(const float* __restrict__ X, int D, const int
   gather_rows_body(X, D, idx, n_dev, out);
 }
 
+// The gather with max |x - center| over the moved values (FP32, the values
+// the rounded copies are made from) and the non-finite check, four rows in
+// flight per warp as above.
+__global__ void gather_rows_center_kernel(const float* __restrict__ X, int D, const int32_t* __restrict__ idx,
+                                          const int64_t* __restrict__ n_dev, float* __restrict__ out,
+                                          const float* __restrict__ center, float* __restrict__ maxabs,
+                                          int* __restrict__ status) {
+  const int64_t n = *n_dev;
+  const int lane = threadIdx.x & 31;
+  const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  float m = 0.f;
+  bool bad = false;
+  const bool vec = (D % 4) == 0 &&
+                   ((reinterpret_cast<uintptr_t>(X) | reinterpret_cast<uintptr_t>(out) |
+                     reinterpret_cast<uintptr_t>(center)) & 15) == 0;
+  if (vec) {
+    const int D4 = D >> 2;
+    const float4* X4 = reinterpret_cast<const float4*>(X);
+    const float4* C4 = reinterpret_cast<const float4*>(center);
+    float4* out4 = reinterpret_cast<float4*>(out);
+    for (int64_t r0 = warp * 4; r0 < n; r0 += nw * 4) {
+      int64_t src[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) src[u] = r0 + u < n ? (int64_t)__ldg(idx + r0 + u) * D4 : -1;
+      for (int k = lane; k < D4; k += 32) {
+        const float4 c = __ldg(C4 + k);
+        float4 v[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+          if (src[u] >= 0) v[u] = __ldg(X4 + src[u] + k);
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+          if (src[u] >= 0) {
+            out4[(r0 + u) * D4 + k] = v[u];
+            bad |= !isfinite(v[u].x) || !isfinite(v[u].y) || !isfinite(v[u].z) || !isfinite(v[u].w);
+            m = fmaxf(m, fmaxf(fmaxf(fabsf(v[u].x - c.x), fabsf(v[u].y - c.y)),
+                               fmaxf(fabsf(v[u].z - c.z), fabsf(v[u].w - c.w))));
+          }
+      }
+    }
+  } else {
+    for (int64_t r = warp; r < n; r += nw) {
+      const float* src = X + (int64_t)__ldg(idx + r) * D;
+      float* dst = out + r * D;
+      for (int k = lane; k < D; k += 32) {
+        const float v = __ldg(src + k);
+        dst[k] = v;
+        bad |= !isfinite(v);
+        m = fmaxf(m, fabsf(v - center[k]));
+      }
+    }
+  }
+  m = warp_max(m);
+  if (__any_sync(0xffffffffu, bad) && lane == 0) atomicMax(status, (int)PROHD_ENONFINITE);
+  if (lane == 0) atomic_max_nonneg(maxabs, m);
+}
+
 // Batched compaction and gather: segment blockIdx.y = 2 * pair + set.
 struct SegView {
   const uint8_t* mask;
@@ -1639,6 +1697,15 @@ cudaError_t gather_rows(const float* X, int D, const int32_t* idx, const int64_t
   (void)n_max;
   count_launch();
   gather_rows_kernel<<<num_sms * 8, 256, 0, st>>>(X, D, idx, n_dev, out);
+  return cudaGetLastError();
+}
+
+cudaError_t gather_rows_center(const float* X, int D, const int32_t* idx, const int64_t* n_dev, int64_t n_max,
+                               float* out, const float* center, float* maxabs, int* status, int num_sms,
+                               cudaStream_t st) {
+  (void)n_max;
+  count_launch();
+  gather_rows_center_kernel<<<num_sms * 8, 256, 0, st>>>(X, D, idx, n_dev, out, center, maxabs, status);
   return cudaGetLastError();
 }
 
