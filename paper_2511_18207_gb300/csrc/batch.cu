@@ -10,10 +10,13 @@
 //   CTA per pair, one launch per D class) -> FP64 clean-up + Rayleigh
 //   quotients -> projection (one block per item) -> radix select + band
 //   resolution (every (pair, set, direction) problem) -> compaction + gather
-//   -> subset HD -> finalize. The subset HD runs either on the tensor cores
-//   (FP16/BF16 tiles over (pair, row block) items, margins, FP32 rescoring of
-//   the candidates) or as FP32 direct differences (persistent, atomic ticket
-//   over 128 x 128 tiles), as params.precision asks.
+//   -> subset HD -> [one-sided refinement] -> finalize. The subset HD runs
+//   either on the tensor cores (FP16/BF16 tiles over (pair, row block) items,
+//   margins, FP32 rescoring of the candidates) or as FP32 direct differences
+//   (persistent, atomic ticket over 128 x 128 tiles), as params.precision
+//   asks. With params.refine = 1 each pair adds two row-set-vs-set pairs
+//   (its selected rows of A against all of B, of B against all of A) that
+//   the same stage runs after the subsets, rows' distances only.
 // The sequence is captured once into a CUDA graph and replayed. Item sizes
 // (Gram points per item, projection rows per item, selection keys per
 // block) come from an autotuner that times candidates on the batch itself.
