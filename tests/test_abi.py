@@ -50,6 +50,22 @@ def test_batch_workspace_size_is_host_only():
         assert lib.prohd_batch_workspace_size(bad, 1, ctypes.byref(p)) == 0, (D, a)
     p30 = prohd.default_params(m=30)
     assert lib.prohd_batch_workspace_size(ok, 2, ctypes.byref(p30)) == 0
+    # the one-sided refinement adds, per pair, rounded copies of both whole
+    # sets (tensor precisions) or the FP32 path's minima: more room, and more
+    # with the larger sets; refine must be 0 or 1
+    for prec in (1, 2, 0):
+        p0 = prohd.default_params(m=8, precision=prec)
+        p1 = prohd.default_params(m=8, precision=prec, refine=1)
+        n0 = lib.prohd_batch_workspace_size(ok, 2, ctypes.byref(p0))
+        n1 = lib.prohd_batch_workspace_size(ok, 2, ctypes.byref(p1))
+        assert n1 > n0 > 0, (prec, n0, n1)
+    p1 = prohd.default_params(m=8, refine=1)
+    n_small = lib.prohd_batch_workspace_size(ok, 2, ctypes.byref(p1)) - n
+    n_big = lib.prohd_batch_workspace_size(big, 1, ctypes.byref(p1)) - \
+        lib.prohd_batch_workspace_size(big, 1, ctypes.byref(p))
+    assert n_big > n_small > 0
+    p2 = prohd.default_params(m=8, refine=2)
+    assert lib.prohd_batch_workspace_size(ok, 2, ctypes.byref(p2)) == 0
 
 
 def test_new_entry_points_size_their_workspaces_on_the_host():
