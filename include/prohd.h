@@ -49,7 +49,7 @@ typedef enum {
   PROHD_ECUDA = 3,       /* a CUDA runtime call failed (message in prohd_last_error) */
   PROHD_ETIMEOUT = 4,    /* device-side: a bounded wait in a kernel ran out */
   PROHD_ENONFINITE = 5,  /* device-side: the input holds NaN or Inf */
-  PROHD_ENOTSUP = 6      /* valid request this build does not support (e.g. GPU older than sm_103a) */
+  PROHD_ENOTSUP = 6      /* valid request the library does not support (e.g. GPU older than sm_103a) */
 } prohd_status;
 
 /* Tile precision of the distance contraction (Methodology – Algorithms, "exact HD on the subsets"). */

@@ -749,7 +749,7 @@ prohd_status prohd_batch_plan(prohd_ctx* ctx, const prohd_pair_desc* pairs, int 
   prohd_status s = check_batch(ctx, pairs, npairs, p, pp);
   if (s != PROHD_OK) return s;
   if (!ctx->encode_tiled) return bfail(ctx, PROHD_ENOTSUP, "driver has no tensor-map encoder");
-  if (ctx->num_sms > kMaxSms) return bfail(ctx, PROHD_ENOTSUP, "more SMs than this build sizes for");
+  if (ctx->num_sms > kMaxSms) return bfail(ctx, PROHD_ENOTSUP, "more SMs than the library sizes its scratch for");
   if (!ws || (reinterpret_cast<uintptr_t>(ws) & 255)) return bfail(ctx, PROHD_EINVAL, "workspace must be 256-byte aligned");
   const bool tensor = p->precision != PROHD_FP32;
   if (ws_bytes < batch_bytes(pp, tensor, p->refine == 1))

@@ -459,7 +459,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kGcThreads, 1)
       for (int i = 0; i < nint; ++i) {
         const uint32_t fi = f0 + (uint32_t)i;
         const uint32_t ab = fi & 1u;
-        // one thread waits; the four warps take its verdict together (they
+        // one thread waits; the four warps take its result together (they
         // meet at named barriers below, so they must all go on or all stop)
         if (issuer) {
           S.epi_go = gc_wait(&S.acc_full[ab], (fi >> 1) & 1u, abort, peer_abort, p.timeout_ns) ? 1 : 0;
